@@ -1,0 +1,586 @@
+/*
+ * CPU oracle for cuGenOpt's per-solution search generation (arxiv 2603.19163).
+ *
+ * TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg load this file's library.  The CUDA library never does.
+ *
+ * Plain, slow and literal by design: every candidate is built on a copy of
+ * the current solution and its cost is evaluated in full.  Function headers
+ * name the passage of the paper each one restates; the fixed-point readings
+ * (marked [R#]) are the ones this project pins where the paper is silent.
+ */
+#include "oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------ RNG [R1]
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplications with
+ * the Weyl key schedule.  The paper names no generator (it fixes seeds only,
+ * Sec. 6.1); a counter-based one keyed by (instance, solution, generation)
+ * makes the trajectory independent of thread scheduling. */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; r++) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+    uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+    uint32_t y1 = (uint32_t)p1;
+    uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+    uint32_t y3 = (uint32_t)p0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* counter = (w0, tag, p, g), key = (lo32(seed), hi32(seed)) [R1] */
+static void draw(uint32_t w0, uint32_t tag, uint32_t p, uint32_t g, uint64_t seed,
+                 uint32_t out[4]) {
+  uint32_t ctr[4] = {w0, tag, p, g};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  orc_philox(ctr, key, out);
+}
+
+#define KIND_MOVE 0u
+#define KIND_ACCEPT 1u
+#define KIND_INIT 2u
+#define W0(cand, step, kind) ((uint32_t)(cand) | ((uint32_t)(step) << 20) | ((uint32_t)(kind) << 24))
+#define INIT_GEN 0xFFFFFFFFu
+
+/* -------------------------------------------------------- index mapping [R2] */
+/* pos(h16, m) = floor(h16 * m / 2^16): a 16-bit field scaled to [0, m). */
+uint32_t orc_pos(uint32_t h16, uint32_t m) { return (uint32_t)(((uint64_t)h16 * m) >> 16); }
+
+/* Roulette-wheel choice from weights (Sec. 4.2.1, "sample from w"):
+ * r = floor(word * sum(w) / 2^32); first i with r < w_0 + ... + w_i. */
+int32_t orc_wsample(const uint32_t *w, int32_t count, uint32_t word) {
+  uint64_t W = 0;
+  for (int32_t i = 0; i < count; i++) W += w[i];
+  uint64_t r = ((uint64_t)word * W) >> 32;
+  uint64_t acc = 0;
+  for (int32_t i = 0; i < count; i++) {
+    acc += w[i];
+    if (r < acc) return i;
+  }
+  return -1; /* all weights zero */
+}
+
+/* ------------------------------------------------- acceptance test [R7]
+ * Alg. "evolve" accepts the best candidate when delta < 0 or
+ * rand() < exp(-delta / T).  Restated in integers: with u = (A+1)/2^32,
+ * rand() < exp(-delta/T)  <=>  delta < T * (-ln u).  -log2(u) is computed in
+ * Q32 by the bit-by-bit squaring method (C. S. Turner, "A Fast Binary
+ * Logarithm Algorithm", IEEE Signal Processing Magazine, 2010), then scaled
+ * by ln 2 in Q32. */
+uint64_t orc_log2_q32(uint32_t A) {
+  /* returns -log2((A+1)/2^32) in Q32 */
+  uint64_t y = (uint64_t)A + 1;        /* 1 .. 2^32 */
+  int e = 0;
+  while ((y >> (e + 1)) != 0) e++;     /* e = floor(log2 y) */
+  uint64_t z = y << (62 - e);          /* y / 2^e in Q2.62, in [1, 2) */
+  uint32_t frac = 0;
+  for (int i = 1; i <= 32; i++) {
+    z = (uint64_t)(((u128)z * z) >> 62);
+    if (z >= (1ull << 63)) {
+      z >>= 1;
+      frac |= 1u << (32 - i);
+    }
+  }
+  uint64_t log2y = ((uint64_t)e << 32) + frac;   /* log2(y) in Q32 (truncated) */
+  return (32ull << 32) - log2y;                  /* 32 - log2(y) = -log2(u) */
+}
+
+#define LN2_Q32 2977044472ull /* round(ln 2 * 2^32) */
+
+uint64_t orc_exp_q32(uint32_t A) {
+  return (uint64_t)(((u128)orc_log2_q32(A) * LN2_Q32) >> 32); /* -ln(u), Q32 */
+}
+
+int32_t orc_accept(int64_t delta, uint64_t T, uint32_t A) {
+  if (delta <= 0) return 1;
+  u128 lhs = (u128)(uint64_t)delta << 64;       /* delta, Q64 */
+  u128 rhs = (u128)T * (u128)orc_exp_q32(A);    /* T (Q32) * E (Q32) */
+  return lhs < rhs;
+}
+
+/* geometric cooling T <- alpha * T (Alg. "evolve", last line) [R8] */
+uint64_t orc_cool(uint64_t T, uint64_t alpha) { return (uint64_t)(((u128)T * alpha) >> 32); }
+
+/* --------------------------------------------------------- instances [R16] */
+int32_t orc_solution_length(const orc_instance *in) {
+  if (in->model == ORC_CVRPTW) return in->n + in->vehicles - 1; /* separators */
+  return in->n;
+}
+
+static int32_t encoding_of(int32_t model) {
+  if (model == ORC_KNAPSACK) return 1;   /* binary (Sec. 3.1.1) */
+  if (model == ORC_GAP) return 2;        /* integer */
+  return 0;                              /* permutation */
+}
+
+static void int_bounds(const orc_instance *in, int32_t *lb, int32_t *ub) {
+  if (in->model == ORC_GAP) { *lb = 0; *ub = in->m - 1; return; }
+  *lb = in->lb; *ub = in->ub;
+}
+
+static int64_t over(int64_t x) { return x > 0 ? x : 0; }
+
+/* TSP: sum of D[a_k][a_(k+1) mod n] (Listing "tsp", in integers) */
+static int64_t cost_tsp(const orc_instance *in, const int32_t *x) {
+  int32_t n = in->n;
+  int64_t s = 0;
+  for (int32_t k = 0; k < n; k++) s += in->mat0[(int64_t)x[k] * n + x[(k + 1) % n]];
+  return s;
+}
+
+/* QAP (Koopmans-Beckmann): sum_i sum_j F[i][j] * D[a_i][a_j] */
+static int64_t cost_qap(const orc_instance *in, const int32_t *x) {
+  int32_t n = in->n;
+  int64_t s = 0;
+  for (int32_t i = 0; i < n; i++)
+    for (int32_t j = 0; j < n; j++)
+      s += (int64_t)in->mat0[(int64_t)i * n + j] * in->mat1[(int64_t)x[i] * n + x[j]];
+  return s;
+}
+
+/* knapsack as minimisation: -sum v x + lambda * max(0, sum w x - cap),
+ * lambda = 1 + max v unless given (objective + penalty, Sec. 3.1.3) */
+static int64_t cost_knapsack(const orc_instance *in, const int32_t *x) {
+  int64_t W = 0, V = 0, vmax = 0;
+  for (int32_t i = 0; i < in->n; i++) {
+    if (in->vec1[i] > vmax) vmax = in->vec1[i];
+    if (x[i]) { W += in->vec0[i]; V += in->vec1[i]; }
+  }
+  int64_t lam = in->penalty0 > 0 ? in->penalty0 : 1 + vmax;
+  return -V + lam * over(W - in->capacity);
+}
+
+/* GAP: sum_j c[x_j][j] + lambda * sum_a max(0, load_a - cap_a) */
+static int64_t cost_gap(const orc_instance *in, const int32_t *x) {
+  int32_t n = in->n, m = in->m;
+  int64_t cmax = 0;
+  for (int64_t i = 0; i < (int64_t)m * n; i++)
+    if (in->mat0[i] > cmax) cmax = in->mat0[i];
+  int64_t lam = in->penalty0 > 0 ? in->penalty0 : 1 + cmax;
+  int64_t s = 0;
+  for (int32_t j = 0; j < n; j++) s += in->mat0[(int64_t)x[j] * n + j];
+  for (int32_t a = 0; a < m; a++) {
+    int64_t load = 0;
+    for (int32_t j = 0; j < n; j++)
+      if (x[j] == a) load += in->mat1[(int64_t)a * n + j];
+    s += lam * over(load - in->vec0[a]);
+  }
+  return s;
+}
+
+/* CVRPTW, separator encoding: symbols < n are customers 1..n, symbols >= n
+ * end a route.  Per route from the depot at t = 0: arrive t = max(t + d,
+ * ready); late += max(0, t - due); t += service; load += demand; back at the
+ * depot t += d(last, 0), late += max(0, t - due_0).  A route with no customer
+ * costs nothing.
+ * cost = distance + lambda_cap * sum max(0, load - Q) + lambda_tw * late. */
+static int64_t cost_cvrptw(const orc_instance *in, const int32_t *x) {
+  int32_t n = in->n, len = orc_solution_length(in), N = n + 1;
+  const int32_t *d = in->mat0, *dem = in->vec0, *rdy = in->vec1, *due = in->vec2,
+                *svc = in->vec3;
+  int64_t lcap = in->penalty0 > 0 ? in->penalty0 : 100;
+  int64_t ltw = in->penalty1 > 0 ? in->penalty1 : 100;
+  int64_t dist = 0, capx = 0, late = 0;
+  int32_t k = 0;
+  while (k <= len) {
+    /* one route: symbols until a separator or the end */
+    int64_t t = 0, load = 0;
+    int32_t prev = 0;
+    while (k < len && x[k] < n) {
+      int32_t c = x[k] + 1;
+      int64_t dd = d[(int64_t)prev * N + c];
+      dist += dd;
+      t = t + dd > rdy[c] ? t + dd : rdy[c];
+      late += over(t - due[c]);
+      t += svc[c];
+      load += dem[c];
+      prev = c;
+      k++;
+    }
+    if (prev != 0) { /* a route that visits no customer costs nothing */
+      int64_t back = d[(int64_t)prev * N + 0];
+      dist += back;
+      t += back;
+      late += over(t - due[0]);
+      capx += over(load - in->capacity);
+    }
+    k++; /* skip the separator (or step past the end) */
+  }
+  return dist + lcap * capx + ltw * late;
+}
+
+int64_t orc_cost(const orc_instance *in, const int32_t *sol) {
+  switch (in->model) {
+    case ORC_TSP: return cost_tsp(in, sol);
+    case ORC_QAP: return cost_qap(in, sol);
+    case ORC_KNAPSACK: return cost_knapsack(in, sol);
+    case ORC_GAP: return cost_gap(in, sol);
+    case ORC_CVRPTW: return cost_cvrptw(in, sol);
+  }
+  return 0;
+}
+
+int32_t orc_valid(const orc_instance *in, const int32_t *sol) {
+  int32_t len = orc_solution_length(in), enc = encoding_of(in->model);
+  if (enc == 0) {
+    char *seen = (char *)calloc((size_t)len, 1);
+    int ok = 1;
+    for (int32_t i = 0; i < len && ok; i++) {
+      if (sol[i] < 0 || sol[i] >= len || seen[sol[i]]) ok = 0;
+      else seen[sol[i]] = 1;
+    }
+    free(seen);
+    return ok;
+  }
+  int32_t lb = 0, ub = 1;
+  if (enc == 2) int_bounds(in, &lb, &ub);
+  for (int32_t i = 0; i < len; i++)
+    if (sol[i] < lb || sol[i] > ub) return 0;
+  return 1;
+}
+
+/* Operators per encoding (Table "operators"): permutation -> swap, reverse
+ * (2-opt), insert, or-opt; binary -> flip; integer -> random reset. */
+int32_t orc_enabled_ops(const orc_instance *in, uint32_t op_mask, int32_t enabled[ORC_NOPS]) {
+  int32_t enc = encoding_of(in->model), len = orc_solution_length(in), count = 0;
+  for (int32_t i = 0; i < ORC_NOPS; i++) {
+    int32_t ok = 0;
+    if (enc == 0 && i <= ORC_OR_OPT) ok = (i == ORC_OR_OPT) ? (len >= 4) : 1; /* [R3] */
+    if (enc == 1 && i == ORC_FLIP) ok = 1;
+    if (enc == 2 && i == ORC_PERTURB) ok = 1;
+    enabled[i] = ok && ((op_mask >> i) & 1u);
+    count += enabled[i];
+  }
+  return count;
+}
+
+/* ------------------------------------------------------------- moves [R3,R4]
+ * Each operator reads two 16-bit position fields (a, b) and one extra word x
+ * and edits the array in place (a literal copy of the current solution). */
+static void pick_ij(uint32_t a, uint32_t b, int32_t len, int32_t *i, int32_t *j) {
+  *i = (int32_t)orc_pos(a, (uint32_t)len);
+  *j = (int32_t)orc_pos(b, (uint32_t)(len - 1));
+  if (*j >= *i) (*j)++; /* j != i */
+}
+
+int32_t orc_apply_move(const orc_instance *in, int32_t op, uint32_t a, uint32_t b, uint32_t x,
+                       int32_t *s, int32_t len) {
+  int32_t i, j;
+  switch (op) {
+    case ORC_SWAP: { /* exchange two elements */
+      pick_ij(a, b, len, &i, &j);
+      int32_t t = s[i]; s[i] = s[j]; s[j] = t;
+      return 0;
+    }
+    case ORC_TWO_OPT: { /* reverse the segment between them (inclusive) */
+      pick_ij(a, b, len, &i, &j);
+      int32_t lo = i < j ? i : j, hi = i < j ? j : i;
+      while (lo < hi) { int32_t t = s[lo]; s[lo] = s[hi]; s[hi] = t; lo++; hi--; }
+      return 0;
+    }
+    case ORC_INSERT: { /* remove s[i]; re-insert it so that it ends at index j */
+      pick_ij(a, b, len, &i, &j);
+      int32_t v = s[i];
+      for (int32_t k = i; k < len - 1; k++) s[k] = s[k + 1];   /* remove */
+      for (int32_t k = len - 1; k > j; k--) s[k] = s[k - 1];   /* open slot j */
+      s[j] = v;
+      return 0;
+    }
+    case ORC_OR_OPT: { /* move a block of L = 2 + (x & 1) elements */
+      if (len < 4) return -1;
+      int32_t L = 2 + (int32_t)(x & 1u);
+      i = (int32_t)orc_pos(a, (uint32_t)(len - L + 1));          /* block start */
+      int32_t q = (int32_t)orc_pos(b, (uint32_t)(len - L));       /* slot in rest */
+      if (q >= i) q++;                                           /* not back in place */
+      int32_t blk[3], *rest = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
+      for (int32_t k = 0; k < L; k++) blk[k] = s[i + k];
+      int32_t r = 0;
+      for (int32_t k = 0; k < len; k++)
+        if (k < i || k >= i + L) rest[r++] = s[k];
+      int32_t o = 0;
+      for (int32_t k = 0; k < q; k++) s[o++] = rest[k];           /* rest before q */
+      for (int32_t k = 0; k < L; k++) s[o++] = blk[k];            /* the block */
+      for (int32_t k = q; k < len - L; k++) s[o++] = rest[k];     /* rest from q */
+      free(rest);
+      return 0;
+    }
+    case ORC_FLIP: { /* x_i ^= 1 */
+      i = (int32_t)orc_pos(a, (uint32_t)len);
+      s[i] ^= 1;
+      return 0;
+    }
+    case ORC_PERTURB: { /* random reset to a different value in [lb, ub] */
+      int32_t lb, ub;
+      int_bounds(in, &lb, &ub);
+      int64_t R = (int64_t)ub - lb + 1;
+      i = (int32_t)orc_pos(a, (uint32_t)len);
+      int64_t d = 1 + (int64_t)orc_pos(b, (uint32_t)(R - 1));
+      s[i] = (int32_t)(lb + (((int64_t)s[i] - lb + d) % R));
+      return 0;
+    }
+  }
+  return -1;
+}
+
+/* ----------------------------------------------------------- AOS [R9-R12]
+ * Eq. "ema": w <- a*w + (1-a)*(v/(u+eps) + w_floor), clamped to
+ * [w_floor, min(w_cap, cap_i)] and normalised (Sec. 4.2.2), all in Q16 with
+ * eps = 1 (ratio = v*2^16 / (u+1)) and floor division. */
+void orc_aos_level(uint32_t *w, const uint32_t *u, const uint32_t *v, const int32_t *enabled,
+                   const uint32_t *cap_i, int32_t count, uint32_t a, uint32_t w_floor,
+                   uint32_t w_cap) {
+  uint64_t S = 0;
+  for (int32_t i = 0; i < count; i++) {
+    if (!enabled[i]) continue;
+    uint64_t ratio = ((uint64_t)v[i] << 16) / ((uint64_t)u[i] + 1);
+    uint64_t nw = ((uint64_t)a * w[i] + (uint64_t)(65536u - a) * (ratio + w_floor)) >> 16;
+    uint64_t hi = w_cap < cap_i[i] ? w_cap : cap_i[i];
+    if (nw > hi) nw = hi;
+    if (nw < w_floor) nw = w_floor;
+    w[i] = (uint32_t)nw;
+    S += nw;
+  }
+  for (int32_t i = 0; i < count; i++)
+    if (enabled[i]) w[i] = (uint32_t)(((uint64_t)w[i] << 16) / S);
+}
+
+/* K-step weights after a stagnation reset (Sec. 4.2.3): (0.8, 0.15, 0.05) */
+static const uint32_t K_RESET[3] = {52429u, 9830u, 3277u};
+
+/* Defaults [R11, R14].  L1 priors (Sec. 4.1, Table "weight_preset"): O(1)
+ * operators start at 1.0; or-opt at 0.80 / 0.70 / 0.30 for solution length
+ * <= 100 / <= 250 / > 250; normalised to Q16 by floor division.  K-step
+ * weights (0.8, 0.15, 0.05) (Sec. 4.2.3).  T0 = 100, alpha = 0.999,
+ * I = 10, EMA a = 0.8, floor 0.05, cap 0.6, stagnation after 5 updates,
+ * elite injection off. */
+void orc_params_default(const orc_instance *in, orc_params *pr) {
+  int32_t en[ORC_NOPS], len = orc_solution_length(in);
+  memset(pr, 0, sizeof *pr);
+  pr->P = 32;
+  pr->C = 128;
+  pr->op_mask = 0x3Fu;
+  orc_enabled_ops(in, pr->op_mask, en);
+  uint64_t S = 0;
+  for (int32_t i = 0; i < ORC_NOPS; i++) {
+    uint32_t w = 0;
+    if (en[i]) {
+      w = 65536u;
+      if (i == ORC_OR_OPT) w = len <= 100 ? 52429u : (len <= 250 ? 45875u : 19661u);
+    }
+    pr->w_op[i] = w;
+    S += w;
+    pr->op_cap[i] = 65536u;
+  }
+  for (int32_t i = 0; i < ORC_NOPS; i++) pr->w_op[i] = (uint32_t)(((uint64_t)pr->w_op[i] << 16) / S);
+  pr->w_k[0] = 52429u; pr->w_k[1] = 9830u; pr->w_k[2] = 3277u;
+  pr->T0 = 100ull << 32;
+  pr->alpha = 4290672329ull;
+  pr->U = 10;
+  pr->ema_a = 52429u;
+  pr->w_floor = 3277u;
+  pr->w_cap = 39322u;
+  pr->stag_limit = 5;
+  pr->elite_period = 0;
+}
+
+/* ------------------------------------------------------------- init [R15] */
+int32_t orc_init(const orc_instance *in, const orc_params *pr, uint64_t seed, orc_state *st) {
+  int32_t len = orc_solution_length(in), enc = encoding_of(in->model);
+  int32_t en[ORC_NOPS];
+  if (pr->P < 1 || len < 2) return -1;
+  orc_enabled_ops(in, pr->op_mask, en);
+  st->P = pr->P;
+  st->len = len;
+  st->g = 0;
+  st->T = pr->T0;
+  for (int32_t i = 0; i < ORC_NOPS; i++) {
+    st->w_op[i] = en[i] ? pr->w_op[i] : 0u;
+    st->u_op[i] = st->v_op[i] = 0;
+  }
+  for (int32_t i = 0; i < 3; i++) { st->w_k[i] = pr->w_k[i]; st->u_k[i] = st->v_k[i] = 0; }
+  st->stag = 0;
+  int32_t lb = 0, ub = 1;
+  if (enc == 2) int_bounds(in, &lb, &ub);
+  for (int32_t p = 0; p < pr->P; p++) {
+    int32_t *x = st->cur + (int64_t)p * len;
+    uint32_t R[4];
+    if (enc == 0) { /* Fisher-Yates, i = len-1 .. 1, j = floor(word*(i+1)/2^32) */
+      for (int32_t i = 0; i < len; i++) x[i] = i;
+      for (int32_t i = len - 1; i >= 1; i--) {
+        int32_t d = len - 1 - i;
+        draw(W0(d / 4, 0, KIND_INIT), in->tag, (uint32_t)p, INIT_GEN, seed, R);
+        int32_t j = (int32_t)(((uint64_t)R[d % 4] * (uint64_t)(i + 1)) >> 32);
+        int32_t t = x[i]; x[i] = x[j]; x[j] = t;
+      }
+    } else {
+      for (int32_t i = 0; i < len; i++) {
+        draw(W0(i / 4, 0, KIND_INIT), in->tag, (uint32_t)p, INIT_GEN, seed, R);
+        uint32_t w = R[i % 4];
+        if (enc == 1) x[i] = (int32_t)(w & 1u);
+        else x[i] = lb + (int32_t)(((uint64_t)w * (uint64_t)((int64_t)ub - lb + 1)) >> 32);
+      }
+    }
+    st->cost[p] = orc_cost(in, x);
+    st->best_cost[p] = st->cost[p];
+    memcpy(st->best_sol + (int64_t)p * len, x, sizeof(int32_t) * (size_t)len);
+  }
+  st->elite_prev = st->best_cost[orc_elite(st)];
+  return 0;
+}
+
+int32_t orc_elite(const orc_state *st) {
+  int32_t e = 0;
+  for (int32_t p = 1; p < st->P; p++)
+    if (st->best_cost[p] < st->best_cost[e]) e = p;
+  return e;
+}
+
+int32_t orc_threads(int32_t threads) {
+#ifdef _OPENMP
+  return threads > 0 ? threads : omp_get_max_threads();
+#else
+  (void)threads;
+  return 1;
+#endif
+}
+
+/* ---------------------------------------------------- one generation of one
+ * solution: Alg. "evolve" for block p.  Writes its AOS counts to u/v/uk/vk. */
+static void evolve_one(const orc_instance *in, const orc_params *pr, uint64_t seed,
+                       orc_state *st, int32_t p, const uint32_t *w_op, const uint32_t *w_k,
+                       uint64_t T, uint32_t g, int32_t *work, int64_t *delta, int32_t *ops,
+                       int32_t *ks, uint32_t *u, uint32_t *v, uint32_t *uk, uint32_t *vk) {
+  int32_t len = st->len, C = pr->C;
+  int32_t *s = st->cur + (int64_t)p * len;
+  int64_t fs = orc_cost(in, s);
+  uint32_t R[4], R0[4];
+  for (int32_t c = 0; c < C; c++) {
+    /* each "thread" t: sample k from w_K, copy s, apply k sampled operators */
+    memcpy(work, s, sizeof(int32_t) * (size_t)len);
+    draw(W0(c, 0, KIND_MOVE), in->tag, (uint32_t)p, g, seed, R0);
+    int32_t k = 1 + orc_wsample(w_k, 3, R0[3]);
+    for (int32_t t = 0; t < k; t++) {
+      if (t == 0) memcpy(R, R0, sizeof R);
+      else draw(W0(c, t, KIND_MOVE), in->tag, (uint32_t)p, g, seed, R);
+      int32_t op = orc_wsample(w_op, ORC_NOPS, R[0]);
+      orc_apply_move(in, op, R[1] >> 16, R[1] & 0xFFFFu, R[2], work, len);
+      ops[c * 3 + t] = op;
+    }
+    ks[c] = k;
+    delta[c] = orc_cost(in, work) - fs;   /* delta_t = f(s_t) - f(s) */
+  }
+  /* block reduction: t* = argmin delta, ties to the lowest index [R5] */
+  int32_t cs = 0;
+  for (int32_t c = 1; c < C; c++)
+    if (delta[c] < delta[cs]) cs = c;
+  /* AOS statistics: usage and improvement of every sampled operator [R6] */
+  for (int32_t c = 0; c < C; c++) {
+    int32_t imp = delta[c] < 0;
+    for (int32_t t = 0; t < ks[c]; t++) { u[ops[c * 3 + t]]++; v[ops[c * 3 + t]] += imp; }
+    uk[ks[c] - 1]++;
+    vk[ks[c] - 1] += imp;
+  }
+  /* thread 0: Metropolis acceptance */
+  draw(W0(0, 0, KIND_ACCEPT), in->tag, (uint32_t)p, g, seed, R);
+  if (orc_accept(delta[cs], T, R[0])) {
+    /* s <- s_t*: rebuild the winning candidate on s itself */
+    for (int32_t t = 0; t < ks[cs]; t++) {
+      if (t == 0) draw(W0(cs, 0, KIND_MOVE), in->tag, (uint32_t)p, g, seed, R);
+      else draw(W0(cs, t, KIND_MOVE), in->tag, (uint32_t)p, g, seed, R);
+      orc_apply_move(in, ops[cs * 3 + t], R[1] >> 16, R[1] & 0xFFFFu, R[2], s, len);
+    }
+    st->cost[p] += delta[cs];
+    if (st->cost[p] < st->best_cost[p]) { /* elite of this solution */
+      st->best_cost[p] = st->cost[p];
+      memcpy(st->best_sol + (int64_t)p * len, s, sizeof(int32_t) * (size_t)len);
+    }
+  }
+}
+
+/* Alg. "aos" body, run after every U-th generation */
+static void aos_update(const orc_instance *in, const orc_params *pr, orc_state *st) {
+  int32_t en[ORC_NOPS], enk[3] = {1, 1, 1};
+  uint32_t capk[3] = {65536u, 65536u, 65536u};
+  orc_enabled_ops(in, pr->op_mask, en);
+  orc_aos_level(st->w_op, st->u_op, st->v_op, en, pr->op_cap, ORC_NOPS, pr->ema_a, pr->w_floor,
+                pr->w_cap);
+  orc_aos_level(st->w_k, st->u_k, st->v_k, enk, capk, 3, pr->ema_a, pr->w_floor, pr->w_cap);
+  for (int32_t i = 0; i < ORC_NOPS; i++) st->u_op[i] = st->v_op[i] = 0;
+  for (int32_t i = 0; i < 3; i++) st->u_k[i] = st->v_k[i] = 0;
+  /* stagnation detection (Sec. 4.2.3) [R12] */
+  int64_t elite = st->best_cost[orc_elite(st)];
+  if (elite < st->elite_prev) st->stag = 0;
+  else st->stag++;
+  st->elite_prev = elite;
+  if (pr->stag_limit > 0 && st->stag >= pr->stag_limit) {
+    for (int32_t i = 0; i < 3; i++) st->w_k[i] = K_RESET[i];
+    st->stag = 0;
+  }
+}
+
+/* elite injection (Sec. 3.4.3): the worst current solution (highest cost,
+ * ties to the lowest index) becomes a copy of the instance elite [R13] */
+static void inject(orc_state *st) {
+  int32_t e = orc_elite(st), wv = 0, len = st->len;
+  for (int32_t p = 1; p < st->P; p++)
+    if (st->cost[p] > st->cost[wv]) wv = p;
+  memcpy(st->cur + (int64_t)wv * len, st->best_sol + (int64_t)e * len,
+         sizeof(int32_t) * (size_t)len);
+  st->cost[wv] = st->best_cost[e];
+  if (st->cost[wv] < st->best_cost[wv]) {
+    st->best_cost[wv] = st->cost[wv];
+    memcpy(st->best_sol + (int64_t)wv * len, st->cur + (int64_t)wv * len,
+           sizeof(int32_t) * (size_t)len);
+  }
+}
+
+int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc_state *st,
+                int64_t generations, int32_t threads) {
+  int32_t P = st->P, len = st->len, C = pr->C;
+  if (C < 1 || pr->U < 1) return -1;
+  uint32_t *cnt = (uint32_t *)calloc((size_t)P * 22, sizeof(uint32_t));
+  int32_t nthreads = orc_threads(threads);
+  for (int64_t it = 0; it < generations; it++) {
+    uint32_t g = (uint32_t)st->g;
+    memset(cnt, 0, sizeof(uint32_t) * (size_t)P * 22);
+#pragma omp parallel num_threads(nthreads)
+    {
+      int32_t *work = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
+      int64_t *delta = (int64_t *)malloc(sizeof(int64_t) * (size_t)C);
+      int32_t *ops = (int32_t *)malloc(sizeof(int32_t) * (size_t)C * 3);
+      int32_t *ks = (int32_t *)malloc(sizeof(int32_t) * (size_t)C);
+#pragma omp for schedule(dynamic, 1)
+      for (int32_t p = 0; p < P; p++) {
+        uint32_t *c = cnt + (int64_t)p * 22;
+        evolve_one(in, pr, seed, st, p, st->w_op, st->w_k, st->T, g, work, delta, ops, ks, c,
+                   c + 8, c + 16, c + 19);
+      }
+      free(work); free(delta); free(ops); free(ks);
+    }
+    for (int32_t p = 0; p < P; p++) {
+      const uint32_t *c = cnt + (int64_t)p * 22;
+      for (int32_t i = 0; i < ORC_NOPS; i++) { st->u_op[i] += c[i]; st->v_op[i] += c[8 + i]; }
+      for (int32_t i = 0; i < 3; i++) { st->u_k[i] += c[16 + i]; st->v_k[i] += c[19 + i]; }
+    }
+    st->T = orc_cool(st->T, pr->alpha);
+    st->g++;
+    if (st->g % pr->U == 0) aos_update(in, pr, st);
+    if (pr->elite_period > 0 && st->g % pr->elite_period == 0) inject(st);
+  }
+  free(cnt);
+  return 0;
+}

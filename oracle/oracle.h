@@ -1,0 +1,105 @@
+/*
+ * CPU oracle for the per-solution search generation of cuGenOpt
+ * (arxiv 2603.19163).  TEST INFRASTRUCTURE ONLY: the test-suite, the smoke
+ * check and the benchmark's CPU-baseline leg use it to check and time the
+ * CUDA library; the library itself never links, loads or calls it.
+ *
+ * It is a plain, slow, literal restatement of
+ *   - Alg. "evolve" (Sec. 3.2.3): per-candidate K-step move sampling, delta
+ *     f(s') - f(s), block argmin, Metropolis acceptance, cooling;
+ *   - Alg. "aos" and Eq. "ema" (Sec. 4.2.2): two-level AOS statistics, EMA
+ *     weight update, clamping, normalisation, stagnation reset (Sec. 4.2.3);
+ *   - elite tracking and elite injection (Sec. 3.4.3);
+ *   - the three encodings (Sec. 3.1.1) and the element/segment operators of
+ *     Table "operators" (swap, reverse, insert, or-opt, flip, random reset);
+ * with the fixed-point readings listed in the design notes (counter-based
+ * Philox4x32-10 random stream, Q32.32 temperature, Q16 weights, integer
+ * logarithm for the acceptance test).  Candidate deltas are computed by the
+ * definition: the candidate is built on a literal copy of the solution and
+ * both costs are evaluated in full.
+ *
+ * It shares no code, header or table with the CUDA library.
+ */
+#ifndef CGO_ORACLE_H
+#define CGO_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_TSP = 0, ORC_QAP = 1, ORC_KNAPSACK = 2, ORC_GAP = 3, ORC_CVRPTW = 4 };
+enum { ORC_SWAP = 0, ORC_TWO_OPT = 1, ORC_INSERT = 2, ORC_OR_OPT = 3,
+       ORC_FLIP = 4, ORC_PERTURB = 5, ORC_NOPS = 8 };
+
+typedef struct {
+  int32_t model;      /* ORC_TSP ... ORC_CVRPTW */
+  int32_t n;          /* cities / facilities / items / jobs / customers */
+  int32_t m;          /* GAP: agents */
+  int32_t vehicles;   /* CVRPTW: V */
+  const int32_t *mat0, *mat1;
+  const int32_t *vec0, *vec1, *vec2, *vec3;
+  int64_t capacity;   /* knapsack capacity, CVRPTW vehicle capacity Q */
+  int32_t lb, ub;     /* integer-encoding bounds (GAP: 0 .. m-1) */
+  int64_t penalty0, penalty1; /* 0 = default lambda */
+  uint32_t tag;       /* instance tag (Philox counter word 1) */
+} orc_instance;
+
+typedef struct {
+  int32_t P, C;
+  uint32_t op_mask;
+  uint32_t w_op[ORC_NOPS], w_k[3];
+  uint64_t T0, alpha;              /* Q32.32, Q0.32 */
+  uint32_t U, ema_a, w_floor, w_cap, op_cap[ORC_NOPS], stag_limit, elite_period;
+} orc_params;
+
+/* Complete search state.  Arrays are caller-owned: cur/best_sol P*len,
+ * cost/best_cost P. */
+typedef struct {
+  int32_t P, len;
+  int64_t g;                        /* generations completed */
+  uint64_t T;                       /* current temperature, Q32.32 */
+  uint32_t w_op[ORC_NOPS], w_k[3];  /* current AOS weights, Q16 */
+  uint32_t stag;                    /* updates without elite improvement */
+  int64_t elite_prev;               /* elite cost at the last AOS update */
+  uint32_t u_op[ORC_NOPS], v_op[ORC_NOPS], u_k[3], v_k[3]; /* open window */
+  int32_t *cur, *best_sol;
+  int64_t *cost, *best_cost;
+} orc_state;
+
+/* building blocks, exported for the oracle's own pin tests */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+uint32_t orc_pos(uint32_t h16, uint32_t m);
+int32_t orc_wsample(const uint32_t *w, int32_t count, uint32_t word);
+uint64_t orc_log2_q32(uint32_t A);
+uint64_t orc_exp_q32(uint32_t A);
+int32_t orc_accept(int64_t delta, uint64_t T, uint32_t A);
+uint64_t orc_cool(uint64_t T, uint64_t alpha);
+int32_t orc_apply_move(const orc_instance *in, int32_t op, uint32_t a, uint32_t b,
+                       uint32_t x, int32_t *sol, int32_t len);
+void orc_aos_level(uint32_t *w, const uint32_t *u, const uint32_t *v, const int32_t *enabled,
+                   const uint32_t *cap_i, int32_t count, uint32_t a, uint32_t w_floor,
+                   uint32_t w_cap);
+
+/* defaults: the L1 profile priors (Table "weight_preset") and the readings of
+ * the unstated AOS/annealing constants */
+void orc_params_default(const orc_instance *in, orc_params *pr);
+int32_t orc_solution_length(const orc_instance *in);
+int64_t orc_cost(const orc_instance *in, const int32_t *sol);
+int32_t orc_valid(const orc_instance *in, const int32_t *sol);
+int32_t orc_enabled_ops(const orc_instance *in, uint32_t op_mask, int32_t enabled[ORC_NOPS]);
+
+/* population init (seeded Philox) + exact costs; state arrays must be sized */
+int32_t orc_init(const orc_instance *in, const orc_params *pr, uint64_t seed, orc_state *st);
+/* run `generations` more generations from the state (threads <= 0: all cores) */
+int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc_state *st,
+                int64_t generations, int32_t threads);
+/* index of the instance elite (lowest best cost, ties to the lowest index) */
+int32_t orc_elite(const orc_state *st);
+/* OpenMP threads the oracle would use for `threads` */
+int32_t orc_threads(int32_t threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
