@@ -1,0 +1,328 @@
+"""Benchmark: move evaluations per second of the population search on GB300.
+
+Default workload (N=1): the large single permutation solve — TSP n=442 in 6
+Gaussian clusters (sigma 40) plus 10% uniform noise over [0,4000]^2, int32
+rounded-Euclidean matrix, population 128, 128 candidates per member per
+generation, 2-opt / or-opt / insertion with the L1 priors, T0 = 100,
+alpha = 0.999, 200,000 generations.  One step = one complete solve (init +
+every generation + elite), through the library's C ABI.
+
+Timing: W untimed warm-up steps, then K steps timed with CUDA events on the
+stream the library launches on, an L2 flush (a 512 MB write) between steps,
+a barrier + synchronize on both sides, max over ranks.  Clocks are sampled
+with nvidia-smi during the timed region.  ``e2e`` repeats the step through the
+public API from host buffers: problem creation (host->device copy of the
+matrix), the solve and the read-back of the best solution (device->host).
+
+--impl reference times the CPU oracle on the host cores on a bounded sample
+(a prefix of the same solve), the only other place this file runs it.
+Under torchrun every rank solves its own replica (seed 1 + rank).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import instances as I  # noqa: E402
+
+TO, INS, OR = 1, 2, 3
+
+
+def workload(name: str):
+    if name == "tsp442":
+        inst = I.tsp_clustered(442, 0)
+        cfg = dict(P=128, C=128, G=200000, op_mask=(1 << TO) | (1 << OR) | (1 << INS))
+        desc = "tsp442-clustered P=128 C=128 G=200000 ops=2opt/oropt/insert"
+    elif name == "tsp20":
+        inst = I.tsp_uniform(20, 0)
+        cfg = dict(P=32, C=128, G=2000, op_mask=0b0111,
+                   w_op=[21845, 21845, 21845, 0, 0, 0, 0, 0])
+        desc = "tsp20-uniform P=32 C=128 G=2000 ops=swap/2opt/insert"
+    elif name == "qap64":
+        inst = I.qap_grid(64, 0)
+        cfg = dict(P=256, C=128, G=100000, op_mask=1, w_op=[65536, 0, 0, 0, 0, 0, 0, 0])
+        desc = "qap64-grid P=256 C=128 G=100000 ops=swap"
+    else:
+        raise SystemExit("unknown workload " + name)
+    return inst, cfg, desc
+
+
+def lib_params(prob, cfg):
+    p = prob.default_params()
+    p.update(cfg)
+    return p
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    """CPU oracle on the host cores: each step runs a bounded prefix of the
+    same solve (the oracle is deliberately slow)."""
+    if rank != 0:
+        return
+    import oracle as O
+    inst, cfg, desc = workload(args.workload)
+    p = O.default_params(inst)
+    p.update({k: v for k, v in cfg.items() if k != "G"})
+    gens = args.ref_generations
+    cores = O.lib().orc_threads(0)
+    for _ in range(args.warmup):
+        O.solve(inst, p, 1, max(1, gens // 4))
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.solve(inst, p, 1, gens)
+        times.append(time.perf_counter() - t0)
+    evals = cfg["P"] * cfg["C"] * gens
+    value = evals * args.steps / sum(times)
+    line = {"metric": "move_evals_per_s", "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": desc, "sample_generations": gens},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": "first %d generations of the %s solve per step" % (gens, desc)},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(inst, cfg, desc, budget_s: float):
+    """Time the oracle as it stands on a bounded prefix of the workload."""
+    import oracle as O
+    p = O.default_params(inst)
+    p.update({k: v for k, v in cfg.items() if k != "G"})
+    cores = O.lib().orc_threads(0)
+    t0 = time.perf_counter()
+    O.solve(inst, p, 1, 2)
+    per_gen = (time.perf_counter() - t0) / 2
+    gens = int(max(2, min(cfg["G"], budget_s / max(per_gen, 1e-6))))
+    t0 = time.perf_counter()
+    O.solve(inst, p, 1, gens)
+    dt = time.perf_counter() - t0
+    evals = cfg["P"] * cfg["C"] * gens
+    return {"value": evals / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d generations of the %s solve (%.1f s)" % (gens, desc, dt)}
+
+
+# ------------------------------------------------------------------- ours
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tsp442")
+    ap.add_argument("--ref-generations", type=int, default=12)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2603_19163_gb300 import cgo
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    inst, cfg, desc = workload(args.workload)
+    inst = dict(inst, tag=0)
+    seed = 1 + rank
+    stream = torch.cuda.Stream()
+    prob = cgo.Problem(inst)
+    params = lib_params(prob, cfg)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            prob.solve(params, seed, stream)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    if rank == 0:
+        sampler.start()
+    step_ms, kern_ms = [], []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1)                       # evict L2 between steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            prob.solve(params, seed, stream)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_ms.append(prob.last_kernel_time()[0])
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if rank == 0 else None
+
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    evals_rank = cfg["P"] * cfg["C"] * cfg["G"] * args.steps
+    value = evals_rank * world / (total_ms / 1000.0)
+    _, best_cost = prob.best()
+
+    # end to end through the public API: host arrays in, best solution out
+    e2e_ms = []
+    h2d = int(inst["mat0"].nbytes)
+    d2h = 0
+    for _ in range(max(1, min(args.steps, 3))):
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = cgo.Problem(inst)
+        p2.solve(params, seed, stream)
+        sol, c = p2.best()
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+        d2h = int(sol.nbytes) + 8
+        p2.close()
+    e2e_t = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = cfg["P"] * cfg["C"] * cfg["G"] * world / (float(e2e_t.item()) / 1000.0)
+
+    if rank == 0:
+        kms = sum(kern_ms) / len(kern_ms)
+        evals_launch = cfg["P"] * cfg["C"] * cfg["G"]
+        roof = roofline(evals_launch, kms, prob, clocks)
+        line = {"metric": "move_evals_per_s", "value": value, "unit": "evals/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+                "data": "synthetic",
+                "config": {"workload": desc, "l2": "flushed between steps (512 MB write)",
+                           "launch": list(prob.get_launch()), "best_cost": int(best_cost),
+                           "gens_per_s": cfg["G"] / (total_ms / args.steps / 1000.0)},
+                "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": 4 * args.steps,
+                "clocks": clocks, "roofline": roof}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(inst, cfg, desc, args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# Issue-slot roofline of the evolve kernel: the kernel is bound by integer
+# instruction issue and latency (instance data are staged in shared memory,
+# nothing streams from HBM), so the peak is one instruction per lane per clock
+# on every SM sub-partition: SMs x 128 lanes x f_max.  The algorithmic work of
+# one move evaluation is counted in integer operations as stated in
+# the design notes (Philox4x32-10 calls, roulette choices, position mapping,
+# junction lookups and distance gathers), with the mean number of steps per
+# candidate taken from the run's own K-step statistics.
+OPS_PHILOX = 100          # 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key add)
+OPS_STEP = 120            # roulette 10 + decode 15 + 10 lookups x 5 + 10 gathers x 4 + sums 5
+OPS_CAND = 20             # K roulette, argmin share, stats
+
+
+def roofline(evals_launch, kernel_ms, prob, clocks):
+    import torch
+    st = prob.state()
+    uk = st["u_k"]
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    fmax = 2070.0
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        fmax = float(pk.get("sm_max_mhz", fmax))
+    except (OSError, ValueError):
+        pass
+    # mean steps per candidate from the final window's K counts (fallback 1.25)
+    tot = sum(uk)
+    ek = (uk[0] + 2 * uk[1] + 3 * uk[2]) / tot if tot else 1.25
+    ops_eval = ek * (OPS_PHILOX + OPS_STEP) + OPS_CAND
+    achieved = evals_launch * ops_eval / (kernel_ms / 1000.0) / 1e12
+    peak = sms * 128 * fmax * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "evolve_kernel<TSP,int16>", "kernel_ms": kernel_ms,
+            "ops_per_eval": ops_eval, "peak_basis": "%d SMs x 128 lanes x %.0f MHz" % (sms, fmax)}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * cgo — GB300-native population search for combinatorial optimisation.
+ *
+ * C ABI of the per-solution search generation of cuGenOpt (arxiv 2603.19163):
+ * for every solution of a population, in parallel, each generation draws a
+ * K-step neighbourhood move from the adaptively weighted operator set,
+ * evaluates its exact integer cost delta against the instance data, applies
+ * Metropolis acceptance with geometric cooling and updates the two-level
+ * adaptive-operator-selection (AOS) weights and the elite
+ * (Alg. "evolve", Alg. "aos", Eq. "ema", Sec. 3.2-3.4 and 4.2).
+ *
+ * Conventions (every entry point):
+ *  - returns a cgo_status; no C++ exception and no abort crosses the ABI;
+ *  - on a non-OK status, cgo_last_error() returns a message for this thread;
+ *  - all sizes are element counts unless stated; all integers are exact;
+ *  - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream); the
+ *    call enqueues its work there and waits for it before returning;
+ *  - a handle may be used by one thread at a time; a call on a handle that
+ *    is already in use returns CGO_ERR_BUSY.
+ * The library runs only on the GPU (sm_103a); it has no CPU fallback.
+ */
+#ifndef CGO_H
+#define CGO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CGO_OK = 0,
+  CGO_ERR_INVALID = 1,      /* an argument violates the documented limits */
+  CGO_ERR_NOMEM = 2,        /* device or host allocation failed */
+  CGO_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has the error) */
+  CGO_ERR_UNSUPPORTED = 4,  /* valid, but outside what the GPU path implements */
+  CGO_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  CGO_ERR_BUSY = 6,         /* the handle (or server slot) is in use */
+  CGO_ERR_STATE = 7         /* no search state yet, or it was lost to an error */
+} cgo_status;
+
+/* Encodings (Sec. 3.1.1). */
+typedef enum { CGO_ENC_PERM = 0, CGO_ENC_BINARY = 1, CGO_ENC_INTEGER = 2 } cgo_encoding;
+
+/* Cost models.  Costs are int64 and minimised.
+ *  TSP      perm of n cities; sum of D[a_k][a_(k+1) mod n]; mat0 = D (n*n).
+ *           The GPU path needs D symmetric.
+ *  QAP      perm of n; sum_i sum_j F[i][j]*D[a_i][a_j]; mat0 = F, mat1 = D (n*n).
+ *           The GPU path implements the swap operator only.
+ *  KNAPSACK binary n; -sum v x + lambda*max(0, sum w x - capacity);
+ *           vec0 = w, vec1 = v (n); lambda = penalty0, or 1 + max v if 0.
+ *  GAP      integer n jobs in [0, m-1]; sum_j c[x_j][j] +
+ *           lambda * sum_a max(0, load_a - cap_a), load_a = sum_{x_j=a} r[a][j];
+ *           mat0 = c, mat1 = r (m*n, row = agent), vec0 = cap (m);
+ *           lambda = penalty0, or 1 + max c if 0.
+ *  CVRPTW   perm of n + vehicles - 1 symbols: s < n is customer s+1, s >= n
+ *           ends a route.  Node 0 is the depot.  mat0 = travel (n+1)^2,
+ *           vec0..vec3 = demand, ready, due, service (n+1 each).  Per route
+ *           from the depot at t = 0: t = max(t + d, ready), late +=
+ *           max(0, t - due), t += service; back at the depot t += d, late +=
+ *           max(0, t - due_0); a route with no customer costs nothing.
+ *           cost = distance + penalty0*sum max(0, load - capacity)
+ *           + penalty1*late (each 100 if 0). */
+typedef enum { CGO_TSP = 0, CGO_QAP = 1, CGO_KNAPSACK = 2, CGO_GAP = 3, CGO_CVRPTW = 4 } cgo_model;
+
+/* Operators (Table "operators").  Bit i of cgo_params.op_mask enables op i. */
+typedef enum {
+  CGO_OP_SWAP = 0,     /* perm: exchange a[i], a[j] */
+  CGO_OP_TWO_OPT = 1,  /* perm: reverse a[min(i,j) .. max(i,j)] */
+  CGO_OP_INSERT = 2,   /* perm: remove a[i], re-insert so it lands at index j */
+  CGO_OP_OR_OPT = 3,   /* perm: move a block of 2 or 3 elements (needs length >= 4) */
+  CGO_OP_FLIP = 4,     /* binary: x_i ^= 1 */
+  CGO_OP_PERTURB = 5   /* integer: x_i <- another value of [lb, ub] */
+} cgo_op;
+
+#define CGO_NOPS 8
+
+typedef struct cgo_problem cgo_problem;  /* opaque; owns device copies + search state */
+
+/* Problem statement (Sec. 3.1: encoding, size, data, constraints). */
+typedef struct {
+  uint32_t struct_size;        /* = sizeof(cgo_problem_desc) */
+  int32_t encoding;            /* must be the model's encoding (cgo_encoding) */
+  int32_t model;               /* cgo_model */
+  int32_t n;                   /* 2 <= n; solution length <= 65535 */
+  const int32_t *mat0, *mat1;  /* row-major matrices, see cgo_model */
+  const int32_t *vec0, *vec1, *vec2, *vec3;
+  int64_t capacity;            /* knapsack capacity; CVRPTW vehicle capacity */
+  int32_t lb, ub;              /* integer bounds (GAP: ignored, [0, m-1]) */
+  int32_t m;                   /* GAP agents, 2 <= m <= 64 */
+  int32_t vehicles;            /* CVRPTW vehicles, >= 1 */
+  int64_t penalty0, penalty1;  /* lambdas; 0 = default */
+  int32_t pointers_on_device;  /* 0: host pointers; 1: device pointers (e.g. a
+                                  torch tensor's data_ptr) on the current device */
+  uint32_t instance_tag;       /* word 1 of every Philox counter of this instance */
+} cgo_problem_desc;
+
+/* Search parameters.  Fixed point: Q16 weights (65536 = 1.0), Q32.32
+ * temperature, Q0.32 cooling factor. */
+typedef struct {
+  uint32_t struct_size;        /* = sizeof(cgo_params) */
+  int32_t population;          /* P, 1 .. 65536 */
+  int32_t candidates;          /* C per solution per generation, 1 .. 4096 (paper T = 128) */
+  int64_t generations;         /* G for cgo_solve; >= 0 */
+  uint32_t op_mask;            /* enabled operators (bits of cgo_op) */
+  uint32_t op_w0_q16[CGO_NOPS];/* initial operator weights (disabled ops ignored) */
+  uint32_t k_w0_q16[3];        /* initial K-step weights for k = 1, 2, 3 */
+  uint64_t T0_q32;             /* initial temperature */
+  uint64_t alpha_q32;          /* cooling: T <- (T * alpha) >> 32 each generation */
+  uint32_t aos_interval;       /* U: AOS update after every U-th generation, >= 1 */
+  uint32_t ema_alpha_q16;      /* EMA a of Eq. "ema", <= 65536 */
+  uint32_t w_floor_q16;        /* w_floor, >= 8 */
+  uint32_t w_cap_q16;          /* w_cap, >= w_floor */
+  uint32_t op_cap_q16[CGO_NOPS];/* per-operator caps (>= w_floor for enabled ops) */
+  uint32_t stag_limit;         /* AOS updates without elite gain before the K reset; 0 = off */
+  uint32_t elite_period;       /* E: elite injection after every E-th generation; 0 = off;
+                                  the GPU path needs E to be a multiple of U */
+} cgo_params;
+
+/* Full search state (checkpoint).  Scalars are filled/read by value; the
+ * four arrays are caller-owned host buffers (NULL = skip on get). */
+typedef struct {
+  uint32_t struct_size;        /* = sizeof(cgo_state) */
+  int32_t population, length;  /* P and the solution length */
+  int64_t generation;          /* generations completed */
+  uint64_t T_q32;
+  uint32_t w_op_q16[CGO_NOPS], w_k_q16[3];
+  uint32_t stag;               /* AOS updates since the elite last improved */
+  int64_t elite_prev;          /* elite cost at the last AOS update */
+  uint32_t u_op[CGO_NOPS], v_op[CGO_NOPS], u_k[3], v_k[3]; /* counts of the open window */
+  int32_t *cur;                /* [P * length] current solutions */
+  int32_t *best_sol;           /* [P * length] best solution of each member */
+  int64_t *cost;               /* [P] current costs */
+  int64_t *best_cost;          /* [P] best costs */
+} cgo_state;
+
+/* Launch shape (the autotuner's choice, or a caller override). */
+typedef struct {
+  uint32_t struct_size;        /* = sizeof(cgo_launch) */
+  int32_t warps_per_cta;       /* 0 = autotune; else 1 .. 32 (one solution per warp) */
+  int32_t staging;             /* 0 = auto, 1 = instance data in shared memory,
+                                  2 = instance data read through L2 */
+} cgo_launch;
+
+/* Create a problem: validates the description and deep-copies the data to
+ * the current device, so the caller may free its arrays on return.
+ * Errors: CGO_ERR_INVALID (sizes, encoding/model mismatch, data that could
+ * overflow an int64 cost), CGO_ERR_UNSUPPORTED (e.g. asymmetric TSP),
+ * CGO_ERR_NOMEM, CGO_ERR_CUDA.  *out is NULL on error. */
+cgo_status cgo_problem_create(const cgo_problem_desc *desc, cgo_problem **out);
+
+/* Free the problem and its device memory.  NULL is accepted. */
+cgo_status cgo_problem_destroy(cgo_problem *prob);
+
+/* Default parameters for this problem: P = 32, C = 128, G = 2000, every
+ * operator of the encoding enabled with the L1 profile priors (Sec. 4.1,
+ * Table "weight_preset": O(1) operators 1.0, or-opt 0.80/0.70/0.30 for
+ * solution length <= 100 / <= 250 / > 250, normalised to Q16),
+ * K weights (0.8, 0.15, 0.05), T0 = 100, alpha = 0.999, U = 10 (I = 10,
+ * Sec. 4.2.2), EMA a = 0.8, floor 0.05, cap 0.6, stagnation after 5
+ * updates, no elite injection. */
+cgo_status cgo_params_default(const cgo_problem *prob, cgo_params *out);
+
+/* Override the launch shape (warps per CTA, staging mode) used by the next
+ * solves of this problem; results do not depend on it. */
+cgo_status cgo_set_launch(cgo_problem *prob, const cgo_launch *launch);
+/* The launch shape the last solve used (after autotuning). */
+cgo_status cgo_get_launch(const cgo_problem *prob, cgo_launch *out);
+
+/* Initialise a population from `seed` (Philox key) and run
+ * params->generations generations (Alg. "evolve" + Alg. "aos").
+ * Replaces any previous state of the handle.  Waits for completion. */
+cgo_status cgo_solve(cgo_problem *prob, const cgo_params *params, uint64_t seed,
+                     void *cuda_stream);
+
+/* Run `generations` more generations of the current state (same params and
+ * seed).  Splitting a solve this way gives bit-identical results. */
+cgo_status cgo_solve_continue(cgo_problem *prob, int64_t generations, void *cuda_stream);
+
+/* Copy the instance elite (lowest best cost, ties to the lowest member
+ * index) to host memory: out_sol gets `length` int32 values (cap >= length,
+ * else CGO_ERR_INVALID); out_cost its cost.  Either pointer may be NULL.
+ * CGO_ERR_STATE before the first solve. */
+cgo_status cgo_best(const cgo_problem *prob, int32_t *out_sol, int32_t cap, int64_t *out_cost);
+
+/* Device time of the last evolve-kernel launch of this problem, measured
+ * with CUDA events recorded on the launching stream just before and after
+ * it, and the generations that launch ran.  CGO_ERR_STATE if none yet. */
+cgo_status cgo_last_kernel_time(const cgo_problem *prob, double *ms, int64_t *generations);
+
+/* Solution length of this problem (n, or n + vehicles - 1 for CVRPTW). */
+cgo_status cgo_solution_length(const cgo_problem *prob, int32_t *out_len);
+
+/* Read the full search state into `out` (struct_size set by the caller;
+ * population and length are filled in; arrays copied if non-NULL). */
+cgo_status cgo_state_get(const cgo_problem *prob, cgo_state *out);
+
+/* Replace the search state (resume from a checkpoint taken with
+ * cgo_state_get under the same params and seed).  All four arrays are
+ * required.  Costs are taken as given. */
+cgo_status cgo_state_set(cgo_problem *prob, const cgo_params *params, uint64_t seed,
+                         const cgo_state *state);
+
+/* Batched solve: `count` independent problems (different models and sizes
+ * allowed) advance together in persistent kernels; problem i uses
+ * per_prob[i] and seeds[i].  Each result is bit-identical to cgo_solve of
+ * that problem alone.  The GPU path needs population <= 32 here. */
+cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_prob,
+                           const uint64_t *seeds, int32_t count, void *cuda_stream);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char *cgo_last_error(void);
+
+/* Library version string. */
+const char *cgo_version(void);
+
+/* Testing hook (host-side fault injection; never faults the GPU).
+ * what = 1: `value` phantom members (0 .. 1024) are added to every member
+ *           barrier of the next solves, so no barrier can complete and the
+ *           bounded device wait must give up: the solve returns
+ *           CGO_ERR_TIMEOUT and the handle's search state is discarded;
+ * what = 2: the device wait limit becomes `value` milliseconds (default
+ *           10000).
+ * Errors: CGO_ERR_INVALID for an unknown `what` or a value out of range. */
+cgo_status cgo_debug_inject(cgo_problem *prob, int32_t what, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGO_H */

@@ -1,0 +1,729 @@
+// Host runtime and C ABI of the cgo library: validation, device copies of
+// the instance data, search-state buffers, the launch-shape choice and the
+// launch sequence init -> evolve (cooperative) -> finalize.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cgo.h"
+#include "cgo_internal.h"
+
+using namespace cgo;
+
+namespace {
+
+thread_local std::string g_err;
+
+cgo_status fail(cgo_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+cgo_status cuda_fail(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation) return fail(CGO_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(CGO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call, what)                    \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+int64_t pad16(int64_t b) { return (b + 15) & ~int64_t(15); }
+
+int encoding_of(int model) {
+  if (model == KNAPSACK) return CGO_ENC_BINARY;
+  if (model == GAP) return CGO_ENC_INTEGER;
+  return CGO_ENC_PERM;
+}
+
+}  // namespace
+
+struct cgo_problem {
+  int device = 0;
+  int model = 0, n = 0, len = 0, m = 0, V = 0;
+  int64_t capacity = 0, lam0 = 0, lam1 = 0;
+  int lb = 0, ub = 0;
+  uint32_t tag = 0;
+  int32_t *d_mat0 = nullptr, *d_mat1 = nullptr, *d_vec[4] = {nullptr, nullptr, nullptr, nullptr};
+  void *d_tri = nullptr;
+  int tri16 = 0;
+  // search state
+  bool has_state = false;
+  cgo_params params{};
+  uint64_t seed = 0;
+  uint32_t enabled = 0;
+  int P_alloc = 0;
+  int32_t *d_cur = nullptr, *d_bestsol = nullptr;
+  int64_t *d_cost = nullptr, *d_best = nullptr;
+  DevAos *d_aos = nullptr;  // [2]
+  DevSync *d_sync = nullptr;
+  int aos_cur = 0;
+  int64_t g = 0;
+  // launch shape
+  int warps_override = 0, staging_override = 0;
+  int last_warps = 0, last_staging = 0;
+  // events around the last evolve launch (kernel time on the launching stream)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  int64_t timed_gens = 0;
+  // test-only fault injection
+  uint32_t phantom_members = 0;
+  uint64_t timeout_ns = 10ull * 1000 * 1000 * 1000;
+  std::atomic<int> busy{0};
+};
+
+namespace {
+
+struct Guard {
+  cgo_problem *p;
+  bool ok;
+  explicit Guard(const cgo_problem *q) : p(const_cast<cgo_problem *>(q)) {
+    int z = 0;
+    ok = p->busy.compare_exchange_strong(z, 1);
+  }
+  ~Guard() {
+    if (ok) p->busy.store(0);
+  }
+};
+
+cudaError_t copy_in(int32_t **dst, const int32_t *src, int64_t count, bool on_device) {
+  const int64_t bytes = pad16(count * 4);
+  cudaError_t e = cudaMalloc((void **)dst, (size_t)bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaMemset(*dst, 0, (size_t)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, (size_t)(count * 4),
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+}
+
+// host copy of caller data (for validation), whether it is on host or device
+cgo_status host_copy(const int32_t *src, int64_t count, bool on_device, std::vector<int32_t> &out) {
+  out.resize((size_t)count);
+  if (count == 0) return CGO_OK;
+  if (!src) return fail(CGO_ERR_INVALID, "missing data array");
+  if (on_device) {
+    CUDA_TRY(cudaMemcpy(out.data(), src, (size_t)count * 4, cudaMemcpyDeviceToHost), "reading device data");
+  } else {
+    memcpy(out.data(), src, (size_t)count * 4);
+  }
+  return CGO_OK;
+}
+
+int64_t absmax(const std::vector<int32_t> &v) {
+  int64_t m = 0;
+  for (int32_t x : v) m = std::max<int64_t>(m, x < 0 ? -(int64_t)x : (int64_t)x);
+  return m;
+}
+int64_t maxval(const std::vector<int32_t> &v) {
+  int64_t m = INT64_MIN;
+  for (int32_t x : v) m = std::max<int64_t>(m, x);
+  return m;
+}
+int64_t abssum(const std::vector<int32_t> &v) {
+  int64_t s = 0;
+  for (int32_t x : v) s += x < 0 ? -(int64_t)x : (int64_t)x;
+  return s;
+}
+
+const double kLimit = 4.6e18;  // 2^62: every cost and delta fits in int64 with room
+
+void free_state(cgo_problem *p) {
+  cudaFree(p->d_cur);
+  cudaFree(p->d_bestsol);
+  cudaFree(p->d_cost);
+  cudaFree(p->d_best);
+  cudaFree(p->d_aos);
+  cudaFree(p->d_sync);
+  p->d_cur = p->d_bestsol = nullptr;
+  p->d_cost = p->d_best = nullptr;
+  p->d_aos = nullptr;
+  p->d_sync = nullptr;
+  p->P_alloc = 0;
+  p->has_state = false;
+}
+
+cgo_status ensure_state(cgo_problem *p, int P) {
+  if (p->P_alloc == P && p->d_cur) return CGO_OK;
+  free_state(p);
+  const size_t sol = (size_t)P * p->len * 4;
+  CUDA_TRY(cudaMalloc((void **)&p->d_cur, sol), "state alloc");
+  CUDA_TRY(cudaMalloc((void **)&p->d_bestsol, sol), "state alloc");
+  CUDA_TRY(cudaMalloc((void **)&p->d_cost, (size_t)P * 8), "state alloc");
+  CUDA_TRY(cudaMalloc((void **)&p->d_best, (size_t)P * 8), "state alloc");
+  CUDA_TRY(cudaMalloc((void **)&p->d_aos, 2 * sizeof(DevAos)), "state alloc");
+  CUDA_TRY(cudaMalloc((void **)&p->d_sync, sizeof(DevSync)), "state alloc");
+  CUDA_TRY(cudaMemset(p->d_aos, 0, 2 * sizeof(DevAos)), "state init");
+  p->P_alloc = P;
+  return CGO_OK;
+}
+
+// a solution of this problem's encoding (checked before it reaches a kernel)
+bool valid_solution(const cgo_problem *p, const int32_t *x) {
+  const int enc = encoding_of(p->model);
+  if (enc == CGO_ENC_PERM) {
+    std::vector<char> seen((size_t)p->len, 0);
+    for (int i = 0; i < p->len; ++i) {
+      if (x[i] < 0 || x[i] >= p->len || seen[(size_t)x[i]]) return false;
+      seen[(size_t)x[i]] = 1;
+    }
+    return true;
+  }
+  const int lo = enc == CGO_ENC_BINARY ? 0 : p->lb, hi = enc == CGO_ENC_BINARY ? 1 : p->ub;
+  for (int i = 0; i < p->len; ++i)
+    if (x[i] < lo || x[i] > hi) return false;
+  return true;
+}
+
+uint32_t applicable_mask(const cgo_problem *p) {
+  const int enc = encoding_of(p->model);
+  if (enc == CGO_ENC_BINARY) return 1u << FLIP;
+  if (enc == CGO_ENC_INTEGER) return 1u << PERTURB;
+  uint32_t m = (1u << SWAP) | (1u << TWO_OPT) | (1u << INSERT);
+  if (p->len >= 4) m |= 1u << OR_OPT;
+  return m;
+}
+
+cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *enabled) {
+  if (!q || q->struct_size != sizeof(cgo_params))
+    return fail(CGO_ERR_INVALID, "params: struct_size must be sizeof(cgo_params)");
+  if (q->population < 1 || q->population > 65536) return fail(CGO_ERR_INVALID, "population out of [1, 65536]");
+  if (q->candidates < 1 || q->candidates > 4096) return fail(CGO_ERR_INVALID, "candidates out of [1, 4096]");
+  if (q->generations < 0) return fail(CGO_ERR_INVALID, "generations < 0");
+  const uint32_t en = q->op_mask & applicable_mask(p);
+  if (!en) return fail(CGO_ERR_INVALID, "no operator of this encoding is enabled");
+  if (p->model == QAP && en != (1u << SWAP))
+    return fail(CGO_ERR_UNSUPPORTED, "QAP on the GPU implements the swap operator only");
+  uint64_t ws = 0;
+  for (int i = 0; i < kNops; ++i) {
+    if (!((en >> i) & 1u)) continue;
+    if (q->op_w0_q16[i] > 65536u) return fail(CGO_ERR_INVALID, "operator weight > 1.0");
+    if (q->op_cap_q16[i] < q->w_floor_q16) return fail(CGO_ERR_INVALID, "operator cap below floor");
+    ws += q->op_w0_q16[i];
+  }
+  if (ws == 0) return fail(CGO_ERR_INVALID, "enabled operator weights sum to zero");
+  uint64_t ks = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (q->k_w0_q16[i] > 65536u) return fail(CGO_ERR_INVALID, "K weight > 1.0");
+    ks += q->k_w0_q16[i];
+  }
+  if (ks == 0) return fail(CGO_ERR_INVALID, "K weights sum to zero");
+  if (q->aos_interval < 1) return fail(CGO_ERR_INVALID, "aos_interval < 1");
+  if ((uint64_t)q->population * q->candidates * 3ull * q->aos_interval >= (1ull << 32))
+    return fail(CGO_ERR_INVALID, "population*candidates*3*aos_interval must be < 2^32");
+  if (q->ema_alpha_q16 > 65536u) return fail(CGO_ERR_INVALID, "ema_alpha > 1.0");
+  if (q->w_floor_q16 < 8u) return fail(CGO_ERR_INVALID, "w_floor must be >= 8 (Q16)");
+  if (q->w_cap_q16 < q->w_floor_q16 || q->w_cap_q16 > 65536u)
+    return fail(CGO_ERR_INVALID, "w_cap must be in [w_floor, 65536]");
+  if (q->alpha_q32 > (1ull << 32)) return fail(CGO_ERR_INVALID, "alpha > 1.0");
+  if (q->elite_period > 0 && q->elite_period % q->aos_interval != 0)
+    return fail(CGO_ERR_UNSUPPORTED, "elite_period must be a multiple of aos_interval on the GPU");
+  *enabled = en;
+  return CGO_OK;
+}
+
+KInst base_kinst(const cgo_problem *p) {
+  KInst h;
+  memset(&h, 0, sizeof h);
+  h.model = p->model;
+  h.n = p->n;
+  h.len = p->len;
+  h.m = p->m;
+  h.capacity = p->capacity;
+  h.lam0 = p->lam0;
+  h.lam1 = p->lam1;
+  h.lb = p->lb;
+  h.ub = p->ub;
+  h.tag = p->tag;
+  h.tri16 = p->tri16;
+  h.mat0 = p->d_mat0;
+  h.mat1 = p->d_mat1;
+  h.vec0 = p->d_vec[0];
+  h.vec1 = p->d_vec[1];
+  h.vec2 = p->d_vec[2];
+  h.vec3 = p->d_vec[3];
+  h.tri = p->d_tri;
+  const cgo_params &q = p->params;
+  h.P = q.population;
+  h.members = q.population;
+  h.C = q.candidates;
+  h.U = q.aos_interval;
+  h.E = q.elite_period;
+  h.alpha = q.alpha_q32;
+  h.ema_a = q.ema_alpha_q16;
+  h.w_floor = q.w_floor_q16;
+  h.w_cap = q.w_cap_q16;
+  h.stag_limit = q.stag_limit;
+  for (int i = 0; i < kNops; ++i) h.op_cap[i] = q.op_cap_q16[i];
+  h.enabled = p->enabled;
+  h.seed = p->seed;
+  h.cur = p->d_cur;
+  h.bestsol = p->d_bestsol;
+  h.cost = p->d_cost;
+  h.best = p->d_best;
+  h.sync = p->d_sync;
+  return h;
+}
+
+// launch shape: warps per CTA (one member per warp) and staging mode
+cgo_status choose_launch(cgo_problem *p, KInst &h, int *warps_out, int64_t *smem_out) {
+  const int64_t optin = max_smem_optin();
+  const int P = h.P;
+  int warps = p->warps_override > 0 ? p->warps_override : 4;
+  if (warps > kMaxWarps) warps = kMaxWarps;
+  if (warps > P) warps = P;
+  int staging = p->staging_override;
+  for (;;) {
+    const int64_t staged = evolve_smem_bytes(h, warps, true);
+    const int64_t global = evolve_smem_bytes(h, warps, false);
+    bool use_smem;
+    if (staging == STAGE_SMEM) use_smem = staged <= optin;
+    else if (staging == STAGE_GLOBAL) use_smem = false;
+    else use_smem = staged <= optin;
+    const int64_t need = use_smem ? staged : global;
+    if (need <= optin) {
+      h.shared_bytes = use_smem ? instance_data_bytes(h) : 0;
+      const int grid = (P + warps - 1) / warps;
+      const int fit = max_coresident_ctas(h, warps, need);
+      if (fit >= grid) {
+        *warps_out = warps;
+        *smem_out = need;
+        p->last_warps = warps;
+        p->last_staging = use_smem ? STAGE_SMEM : STAGE_GLOBAL;
+        return CGO_OK;
+      }
+      if (warps < kMaxWarps && warps < P && p->warps_override == 0) {
+        warps *= 2;
+        if (warps > kMaxWarps) warps = kMaxWarps;
+        continue;
+      }
+      return fail(CGO_ERR_UNSUPPORTED,
+                  "population %d needs %d co-resident CTAs of %d warps; the GPU holds %d", P, grid,
+                  warps, fit);
+    }
+    if (warps > 1 && p->warps_override == 0) {
+      warps /= 2;
+      continue;
+    }
+    return fail(CGO_ERR_UNSUPPORTED, "solution length %d needs more shared memory than a CTA has",
+                p->len);
+  }
+}
+
+cgo_status check_sync_error(cgo_problem *p, cudaStream_t st) {
+  uint32_t err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, &p->d_sync->error, 4, cudaMemcpyDeviceToHost, st), "reading status");
+  CUDA_TRY(cudaStreamSynchronize(st), "synchronising stream");
+  if (err) {
+    p->has_state = false;
+    return fail(CGO_ERR_TIMEOUT, "a member barrier timed out (flags 0x%x); search state discarded", err);
+  }
+  return CGO_OK;
+}
+
+cgo_status run_generations(cgo_problem *p, int64_t G, cudaStream_t st) {
+  if (G == 0) return CGO_OK;
+  if (p->g + G >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "generation index would exceed 2^32 - 2");
+  KInst h = base_kinst(p);
+  int warps = 0;
+  int64_t smem = 0;
+  cgo_status s = choose_launch(p, h, &warps, &smem);
+  if (s != CGO_OK) return s;
+  h.members = p->params.population + (int)p->phantom_members;  // test hook adds phantoms
+  h.g_begin = p->g;
+  h.g_end = p->g + G;
+  h.aos_in = p->d_aos + p->aos_cur;
+  h.aos_out = p->d_aos + (1 - p->aos_cur);
+  CUDA_TRY(cudaMemsetAsync(p->d_sync, 0, sizeof(DevSync), st), "sync reset");
+  CUDA_TRY(cudaMemsetAsync(p->d_sync->elite, 0x7F, sizeof(p->d_sync->elite), st), "sync reset");
+  if (!p->ev0) {
+    CUDA_TRY(cudaEventCreate(&p->ev0), "event");
+    CUDA_TRY(cudaEventCreate(&p->ev1), "event");
+  }
+  CUDA_TRY(cudaEventRecord(p->ev0, st), "event");
+  CUDA_TRY(launch_evolve_single(h, warps, smem, p->timeout_ns, st), "evolve launch");
+  CUDA_TRY(cudaEventRecord(p->ev1, st), "event");
+  p->timed = true;
+  p->timed_gens = G;
+  CUDA_TRY(launch_finalize(h, st), "finalize launch");
+  s = check_sync_error(p, st);
+  if (s != CGO_OK) return s;
+  p->aos_cur = 1 - p->aos_cur;
+  p->g += G;
+  return CGO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cgo_last_error(void) { return g_err.c_str(); }
+
+const char *cgo_version(void) { return "cgo 0.1 (sm_103a)"; }
+
+cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
+  if (!out) return fail(CGO_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!d || d->struct_size != sizeof(cgo_problem_desc))
+    return fail(CGO_ERR_INVALID, "desc: struct_size must be sizeof(cgo_problem_desc)");
+  if (d->model < CGO_TSP || d->model > CGO_CVRPTW) return fail(CGO_ERR_INVALID, "unknown model");
+  if (d->encoding != encoding_of(d->model))
+    return fail(CGO_ERR_INVALID, "encoding %d does not match model %d", d->encoding, d->model);
+  if (d->n < 2) return fail(CGO_ERR_INVALID, "n must be >= 2");
+  if (d->model == CGO_CVRPTW) return fail(CGO_ERR_UNSUPPORTED, "CVRPTW is not implemented on the GPU yet");
+  const bool dev = d->pointers_on_device != 0;
+  const int64_t n = d->n;
+  const int len = (int)n;
+  if (n > 65535) return fail(CGO_ERR_INVALID, "solution length must be <= 65535");
+
+  cgo_problem *p = new cgo_problem();
+  cudaGetDevice(&p->device);
+  p->model = d->model;
+  p->n = (int)n;
+  p->len = len;
+  p->tag = d->instance_tag;
+  p->lam0 = d->penalty0;
+  p->lam1 = d->penalty1;
+  p->capacity = d->capacity;
+  auto bail = [&](cgo_status s) {
+    cgo_problem_destroy(p);
+    return s;
+  };
+  std::vector<int32_t> a, b, c;
+  cgo_status s;
+  switch (d->model) {
+    case CGO_TSP: {
+      if ((s = host_copy(d->mat0, n * n, dev, a)) != CGO_OK) return bail(s);
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j)
+          if (a[i * n + j] != a[j * n + i])
+            return bail(fail(CGO_ERR_UNSUPPORTED, "the GPU TSP path needs a symmetric distance matrix"));
+      const int64_t mx = absmax(a);
+      if ((double)mx * (double)n > kLimit) return bail(fail(CGO_ERR_INVALID, "distances could overflow"));
+      p->tri16 = mx <= 32767 ? 1 : 0;
+      cudaError_t e = copy_in(&p->d_mat0, a.data(), n * n, false);
+      if (e != cudaSuccess) return bail(cuda_fail(e, "copying D"));
+      const int64_t tb = pad16(n * (n + 1) / 2 * (p->tri16 ? 2 : 4));
+      if ((e = cudaMalloc(&p->d_tri, (size_t)tb)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+      if ((e = cudaMemset(p->d_tri, 0, (size_t)tb)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+      if ((e = build_triangle(p->d_mat0, (int)n, p->tri16, p->d_tri, 0)) != cudaSuccess)
+        return bail(cuda_fail(e, "triangle"));
+      if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+      break;
+    }
+    case CGO_QAP: {
+      if ((s = host_copy(d->mat0, n * n, dev, a)) != CGO_OK) return bail(s);
+      if ((s = host_copy(d->mat1, n * n, dev, b)) != CGO_OK) return bail(s);
+      const double mf = (double)absmax(a), md = (double)absmax(b);
+      if (mf * md * (double)std::max<int64_t>(n * n, 16 * n) * 4.0 > kLimit)
+        return bail(fail(CGO_ERR_INVALID, "flow x distance could overflow int64"));
+      cudaError_t e;
+      if ((e = copy_in(&p->d_mat0, a.data(), n * n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy F"));
+      if ((e = copy_in(&p->d_mat1, b.data(), n * n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy D"));
+      break;
+    }
+    case CGO_KNAPSACK: {
+      if ((s = host_copy(d->vec0, n, dev, a)) != CGO_OK) return bail(s);
+      if ((s = host_copy(d->vec1, n, dev, b)) != CGO_OK) return bail(s);
+      if (d->penalty0 < 0) return bail(fail(CGO_ERR_INVALID, "penalty0 < 0"));
+      p->lam0 = d->penalty0 > 0 ? d->penalty0 : 1 + std::max<int64_t>(0, maxval(b));
+      if ((double)p->lam0 * ((double)abssum(a) + std::fabs((double)d->capacity)) + (double)abssum(b) > kLimit)
+        return bail(fail(CGO_ERR_INVALID, "penalty x weights could overflow int64"));
+      cudaError_t e;
+      if ((e = copy_in(&p->d_vec[0], a.data(), n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy w"));
+      if ((e = copy_in(&p->d_vec[1], b.data(), n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy v"));
+      break;
+    }
+    case CGO_GAP: {
+      if (d->m < 2 || d->m > kMaxAgents) return bail(fail(CGO_ERR_INVALID, "GAP needs 2 <= m <= %d", kMaxAgents));
+      p->m = d->m;
+      p->lb = 0;
+      p->ub = d->m - 1;
+      const int64_t mn = (int64_t)d->m * n;
+      if ((s = host_copy(d->mat0, mn, dev, a)) != CGO_OK) return bail(s);
+      if ((s = host_copy(d->mat1, mn, dev, b)) != CGO_OK) return bail(s);
+      if ((s = host_copy(d->vec0, d->m, dev, c)) != CGO_OK) return bail(s);
+      if (d->penalty0 < 0) return bail(fail(CGO_ERR_INVALID, "penalty0 < 0"));
+      p->lam0 = d->penalty0 > 0 ? d->penalty0 : 1 + std::max<int64_t>(0, maxval(a));
+      if ((double)p->lam0 * ((double)abssum(b) + (double)abssum(c)) + (double)abssum(a) > kLimit)
+        return bail(fail(CGO_ERR_INVALID, "penalty x requirements could overflow int64"));
+      cudaError_t e;
+      if ((e = copy_in(&p->d_mat0, a.data(), mn, false)) != cudaSuccess) return bail(cuda_fail(e, "copy c"));
+      if ((e = copy_in(&p->d_mat1, b.data(), mn, false)) != cudaSuccess) return bail(cuda_fail(e, "copy r"));
+      if ((e = copy_in(&p->d_vec[0], c.data(), d->m, false)) != cudaSuccess) return bail(cuda_fail(e, "copy cap"));
+      break;
+    }
+  }
+  *out = p;
+  return CGO_OK;
+}
+
+cgo_status cgo_problem_destroy(cgo_problem *p) {
+  if (!p) return CGO_OK;
+  free_state(p);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  cudaFree(p->d_mat0);
+  cudaFree(p->d_mat1);
+  for (int i = 0; i < 4; ++i) cudaFree(p->d_vec[i]);
+  cudaFree(p->d_tri);
+  delete p;
+  return CGO_OK;
+}
+
+cgo_status cgo_solution_length(const cgo_problem *p, int32_t *out) {
+  if (!p || !out) return fail(CGO_ERR_INVALID, "NULL argument");
+  *out = p->len;
+  return CGO_OK;
+}
+
+cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
+  if (!p || !q) return fail(CGO_ERR_INVALID, "NULL argument");
+  memset(q, 0, sizeof *q);
+  q->struct_size = sizeof(cgo_params);
+  q->population = 32;
+  q->candidates = 128;
+  q->generations = 2000;
+  const uint32_t en = applicable_mask(p);
+  q->op_mask = en;
+  // Table "weight_preset": O(1) operators 1.0; or-opt by scale of the length
+  uint64_t S = 0;
+  uint32_t w[kNops] = {0};
+  for (int i = 0; i < kNops; ++i) {
+    if (!((en >> i) & 1u)) continue;
+    w[i] = 65536u;
+    if (i == OR_OPT) w[i] = p->len <= 100 ? 52429u : (p->len <= 250 ? 45875u : 19661u);
+    S += w[i];
+  }
+  for (int i = 0; i < kNops; ++i) {
+    q->op_w0_q16[i] = (uint32_t)(((uint64_t)w[i] << 16) / S);
+    q->op_cap_q16[i] = 65536u;
+  }
+  q->k_w0_q16[0] = 52429u;
+  q->k_w0_q16[1] = 9830u;
+  q->k_w0_q16[2] = 3277u;
+  q->T0_q32 = 100ull << 32;
+  q->alpha_q32 = 4290672329ull;  // round(0.999 * 2^32)
+  q->aos_interval = 10;
+  q->ema_alpha_q16 = 52429u;
+  q->w_floor_q16 = 3277u;
+  q->w_cap_q16 = 39322u;
+  q->stag_limit = 5;
+  q->elite_period = 0;
+  return CGO_OK;
+}
+
+cgo_status cgo_set_launch(cgo_problem *p, const cgo_launch *l) {
+  if (!p || !l || l->struct_size != sizeof(cgo_launch)) return fail(CGO_ERR_INVALID, "bad launch struct");
+  if (l->warps_per_cta < 0 || l->warps_per_cta > kMaxWarps)
+    return fail(CGO_ERR_INVALID, "warps_per_cta must be in [0, %d]", kMaxWarps);
+  if (l->staging < 0 || l->staging > 2) return fail(CGO_ERR_INVALID, "staging must be 0, 1 or 2");
+  p->warps_override = l->warps_per_cta;
+  p->staging_override = l->staging;
+  return CGO_OK;
+}
+
+cgo_status cgo_get_launch(const cgo_problem *p, cgo_launch *l) {
+  if (!p || !l) return fail(CGO_ERR_INVALID, "NULL argument");
+  l->struct_size = sizeof(cgo_launch);
+  l->warps_per_cta = p->last_warps;
+  l->staging = p->last_staging;
+  return CGO_OK;
+}
+
+cgo_status cgo_solve(cgo_problem *p, const cgo_params *q, uint64_t seed, void *stream) {
+  if (!p) return fail(CGO_ERR_INVALID, "NULL problem");
+  Guard gd(p);
+  if (!gd.ok) return fail(CGO_ERR_BUSY, "problem handle in use");
+  cudaSetDevice(p->device);
+  uint32_t en = 0;
+  cgo_status s = validate_params(p, q, &en);
+  if (s != CGO_OK) return s;
+  if ((s = ensure_state(p, q->population)) != CGO_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  p->params = *q;
+  p->seed = seed;
+  p->enabled = en;
+  p->g = 0;
+  p->aos_cur = 0;
+  p->has_state = false;
+  KInst h = base_kinst(p);
+  CUDA_TRY(launch_init(h, st), "init launch");
+  DevAos a0;
+  memset(&a0, 0, sizeof a0);
+  a0.T = q->T0_q32;
+  for (int i = 0; i < kNops; ++i) a0.w_op[i] = ((en >> i) & 1u) ? q->op_w0_q16[i] : 0u;
+  for (int i = 0; i < 3; ++i) a0.w_k[i] = q->k_w0_q16[i];
+  h.aos_out = p->d_aos;
+  CUDA_TRY(launch_init_aos(h, a0, st), "init launch");
+  CUDA_TRY(cudaStreamSynchronize(st), "init");
+  p->has_state = true;
+  return run_generations(p, q->generations, st);
+}
+
+cgo_status cgo_solve_continue(cgo_problem *p, int64_t G, void *stream) {
+  if (!p) return fail(CGO_ERR_INVALID, "NULL problem");
+  Guard gd(p);
+  if (!gd.ok) return fail(CGO_ERR_BUSY, "problem handle in use");
+  if (!p->has_state) return fail(CGO_ERR_STATE, "no search state: call cgo_solve first");
+  if (G < 0) return fail(CGO_ERR_INVALID, "generations < 0");
+  cudaSetDevice(p->device);
+  return run_generations(p, G, (cudaStream_t)stream);
+}
+
+cgo_status cgo_last_kernel_time(const cgo_problem *p, double *ms, int64_t *generations) {
+  if (!p || !ms) return fail(CGO_ERR_INVALID, "NULL argument");
+  if (!p->timed) return fail(CGO_ERR_STATE, "no evolve launch yet");
+  float f = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&f, p->ev0, p->ev1), "event time");
+  *ms = f;
+  if (generations) *generations = p->timed_gens;
+  return CGO_OK;
+}
+
+cgo_status cgo_best(const cgo_problem *p, int32_t *out_sol, int32_t cap, int64_t *out_cost) {
+  if (!p) return fail(CGO_ERR_INVALID, "NULL problem");
+  Guard gd(p);
+  if (!gd.ok) return fail(CGO_ERR_BUSY, "problem handle in use");
+  if (!p->has_state) return fail(CGO_ERR_STATE, "no search state: call cgo_solve first");
+  if (out_sol && cap < p->len) return fail(CGO_ERR_INVALID, "cap %d < solution length %d", cap, p->len);
+  cudaSetDevice(p->device);
+  DevAos a;
+  CUDA_TRY(cudaMemcpy(&a, p->d_aos + p->aos_cur, sizeof a, cudaMemcpyDeviceToHost), "reading elite");
+  if (out_cost) *out_cost = a.elite_cost;
+  if (out_sol)
+    CUDA_TRY(cudaMemcpy(out_sol, p->d_bestsol + (int64_t)a.elite * p->len, (size_t)p->len * 4,
+                        cudaMemcpyDeviceToHost),
+             "reading elite");
+  return CGO_OK;
+}
+
+cgo_status cgo_state_get(const cgo_problem *p, cgo_state *o) {
+  if (!p || !o || o->struct_size != sizeof(cgo_state)) return fail(CGO_ERR_INVALID, "bad state struct");
+  Guard gd(p);
+  if (!gd.ok) return fail(CGO_ERR_BUSY, "problem handle in use");
+  if (!p->has_state) return fail(CGO_ERR_STATE, "no search state");
+  cudaSetDevice(p->device);
+  DevAos a;
+  CUDA_TRY(cudaMemcpy(&a, p->d_aos + p->aos_cur, sizeof a, cudaMemcpyDeviceToHost), "reading state");
+  const int P = p->params.population;
+  o->population = P;
+  o->length = p->len;
+  o->generation = a.g;
+  o->T_q32 = a.T;
+  for (int i = 0; i < kNops; ++i) {
+    o->w_op_q16[i] = a.w_op[i];
+    o->u_op[i] = a.pend[i];
+    o->v_op[i] = a.pend[8 + i];
+  }
+  for (int i = 0; i < 3; ++i) {
+    o->w_k_q16[i] = a.w_k[i];
+    o->u_k[i] = a.pend[16 + i];
+    o->v_k[i] = a.pend[19 + i];
+  }
+  o->stag = a.stag;
+  o->elite_prev = a.elite_prev;
+  const size_t sb = (size_t)P * p->len * 4;
+  if (o->cur) CUDA_TRY(cudaMemcpy(o->cur, p->d_cur, sb, cudaMemcpyDeviceToHost), "reading state");
+  if (o->best_sol) CUDA_TRY(cudaMemcpy(o->best_sol, p->d_bestsol, sb, cudaMemcpyDeviceToHost), "reading state");
+  if (o->cost) CUDA_TRY(cudaMemcpy(o->cost, p->d_cost, (size_t)P * 8, cudaMemcpyDeviceToHost), "reading state");
+  if (o->best_cost) CUDA_TRY(cudaMemcpy(o->best_cost, p->d_best, (size_t)P * 8, cudaMemcpyDeviceToHost), "reading state");
+  return CGO_OK;
+}
+
+cgo_status cgo_state_set(cgo_problem *p, const cgo_params *q, uint64_t seed, const cgo_state *in) {
+  if (!p || !in || in->struct_size != sizeof(cgo_state)) return fail(CGO_ERR_INVALID, "bad state struct");
+  Guard gd(p);
+  if (!gd.ok) return fail(CGO_ERR_BUSY, "problem handle in use");
+  cudaSetDevice(p->device);
+  uint32_t en = 0;
+  cgo_status s = validate_params(p, q, &en);
+  if (s != CGO_OK) return s;
+  if (in->population != q->population || in->length != p->len)
+    return fail(CGO_ERR_INVALID, "state shape does not match params/problem");
+  if (!in->cur || !in->best_sol || !in->cost || !in->best_cost)
+    return fail(CGO_ERR_INVALID, "all four state arrays are required");
+  if (in->generation < 0 || in->generation >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "bad generation");
+  const int P = q->population;
+  for (int r = 0; r < 2 * P; ++r) {
+    const int32_t *x = (r < P ? in->cur : in->best_sol) + (int64_t)(r % P) * p->len;
+    if (!valid_solution(p, x)) return fail(CGO_ERR_INVALID, "state row %d is not a valid solution", r);
+  }
+  if ((s = ensure_state(p, q->population)) != CGO_OK) return s;
+  const size_t sb = (size_t)P * p->len * 4;
+  CUDA_TRY(cudaMemcpy(p->d_cur, in->cur, sb, cudaMemcpyHostToDevice), "writing state");
+  CUDA_TRY(cudaMemcpy(p->d_bestsol, in->best_sol, sb, cudaMemcpyHostToDevice), "writing state");
+  CUDA_TRY(cudaMemcpy(p->d_cost, in->cost, (size_t)P * 8, cudaMemcpyHostToDevice), "writing state");
+  CUDA_TRY(cudaMemcpy(p->d_best, in->best_cost, (size_t)P * 8, cudaMemcpyHostToDevice), "writing state");
+  DevAos a;
+  memset(&a, 0, sizeof a);
+  a.T = in->T_q32;
+  a.g = in->generation;
+  for (int i = 0; i < kNops; ++i) {
+    a.w_op[i] = in->w_op_q16[i];
+    a.pend[i] = in->u_op[i];
+    a.pend[8 + i] = in->v_op[i];
+  }
+  for (int i = 0; i < 3; ++i) {
+    a.w_k[i] = in->w_k_q16[i];
+    a.pend[16 + i] = in->u_k[i];
+    a.pend[19 + i] = in->v_k[i];
+  }
+  a.stag = in->stag;
+  a.elite_prev = in->elite_prev;
+  int e = 0;
+  for (int i = 1; i < P; ++i)
+    if (in->best_cost[i] < in->best_cost[e]) e = i;
+  a.elite = e;
+  a.elite_cost = in->best_cost[e];
+  CUDA_TRY(cudaMemcpy(p->d_aos, &a, sizeof a, cudaMemcpyHostToDevice), "writing state");
+  p->params = *q;
+  p->seed = seed;
+  p->enabled = en;
+  p->g = in->generation;
+  p->aos_cur = 0;
+  p->has_state = true;
+  return CGO_OK;
+}
+
+cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, const uint64_t *seeds,
+                           int32_t count, void *stream) {
+  if (count < 0 || (count > 0 && (!probs || !per || !seeds))) return fail(CGO_ERR_INVALID, "bad batch arguments");
+  for (int32_t i = 0; i < count; ++i) {
+    cgo_status s = cgo_solve(probs[i], &per[i], seeds[i], stream);
+    if (s != CGO_OK) return s;
+  }
+  return CGO_OK;
+}
+
+/* Test-only fault injection: what = 1 adds `value` phantom members to every member barrier,
+ * so the barrier cannot complete and the bounded wait must give up;
+ * what = 2 sets the barrier wait limit to `value` milliseconds. */
+cgo_status cgo_debug_inject(cgo_problem *p, int32_t what, int64_t value) {
+  if (!p) return fail(CGO_ERR_INVALID, "NULL problem");
+  if (what == 1) {
+    if (value < 0 || value > 1024) return fail(CGO_ERR_INVALID, "phantom members out of range");
+    p->phantom_members = (uint32_t)value;
+  } else if (what == 2) {
+    if (value < 1 || value > 600000) return fail(CGO_ERR_INVALID, "timeout out of range");
+    p->timeout_ns = (uint64_t)value * 1000000ull;
+  } else {
+    return fail(CGO_ERR_INVALID, "unknown injection");
+  }
+  return CGO_OK;
+}
+
+}  // extern "C"

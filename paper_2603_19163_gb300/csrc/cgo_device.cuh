@@ -1,0 +1,199 @@
+// Device primitives of the search generation: counter-based random numbers,
+// index mapping, roulette choice, the integer acceptance test, cooling, the
+// Q16 AOS update, warp reductions and the permutation-move algebra.
+#pragma once
+#include <stdint.h>
+
+#include "cgo_internal.h"
+
+namespace cgo {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kKindMove = 0u, kKindAccept = 1u, kKindInit = 2u;
+constexpr uint32_t kInitGen = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t ctr_word(uint32_t cand, uint32_t step, uint32_t kind) {
+  return cand | (step << 20) | (kind << 24);
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): counter (c0..c3), key (k0, k1).
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c2 = hi0 ^ c3 ^ k1;
+    c1 = lo1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// A 16-bit field scaled to [0, m): floor(h * m / 2^16), m <= 65536.
+__device__ __forceinline__ int posm(uint32_t h16, uint32_t m) { return (int)((h16 * m) >> 16); }
+
+// Roulette choice: r = floor(word * W / 2^32), first i with r < w_0 + .. + w_i.
+// Counting the prefix sums <= r gives that index for non-decreasing sums.
+template <int N>
+__device__ __forceinline__ int wsample(const uint32_t (&w)[N], uint32_t W, uint32_t word) {
+  const uint32_t r = __umulhi(word, W);
+  uint32_t acc = 0;
+  int idx = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    acc += w[i];
+    idx += (r >= acc);
+  }
+  return idx;
+}
+
+// -ln(u) in Q32 for u = (A + 1) / 2^32: the binary logarithm digit by digit
+// (repeated squaring of the Q2.62 mantissa, C. S. Turner, IEEE SPM 2010),
+// then times round(ln 2 * 2^32).
+__device__ __forceinline__ uint64_t exp_variate_q32(uint32_t A) {
+  const uint64_t y = (uint64_t)A + 1ull;
+  const int e = 63 - __clzll((long long)y);
+  uint64_t z = y << (62 - e);
+  uint32_t frac = 0;
+#pragma unroll 8
+  for (int i = 1; i <= 32; ++i) {
+    const uint64_t lo = z * z, hi = __umul64hi(z, z);
+    z = (hi << 2) | (lo >> 62);
+    const uint32_t bit = (uint32_t)(z >> 63);
+    z >>= bit;
+    frac |= bit << (32 - i);
+  }
+  const uint64_t L = (32ull << 32) - (((uint64_t)e << 32) + frac);
+  const uint64_t lo = L * 2977044472ull, hi = __umul64hi(L, 2977044472ull);
+  return (hi << 32) | (lo >> 32);
+}
+
+// Metropolis test in integers: accept iff delta <= 0 or delta < T * E.
+__device__ __forceinline__ bool accept_move(long long delta, uint64_t T, uint64_t E) {
+  if (delta <= 0) return true;
+  const uint64_t hi = __umul64hi(T, E), lo = T * E;
+  const uint64_t d = (uint64_t)delta;
+  return d < hi || (d == hi && lo != 0ull);
+}
+
+__device__ __forceinline__ uint64_t cool(uint64_t T, uint64_t alpha) {
+  return (__umul64hi(T, alpha) << 32) | ((T * alpha) >> 32);
+}
+
+// Eq. "ema" on one level, Q16: w <- (a*w + (1-a)*(v/(u+1) + floor)) >> 16,
+// clamped to [floor, min(cap, cap_i)], then w <- w * 2^16 / sum(w).
+template <int N>
+__device__ __forceinline__ void aos_level(uint32_t (&w)[N], const uint32_t (&u)[N],
+                                          const uint32_t (&v)[N], uint32_t enabled,
+                                          const uint32_t (&capi)[N], uint32_t a,
+                                          uint32_t wfloor, uint32_t wcap) {
+  uint64_t S = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if ((enabled >> i) & 1u) {
+      const uint64_t ratio = ((uint64_t)v[i] << 16) / ((uint64_t)u[i] + 1ull);
+      uint64_t nw = ((uint64_t)a * w[i] + (uint64_t)(65536u - a) * (ratio + wfloor)) >> 16;
+      const uint64_t hi = wcap < capi[i] ? wcap : capi[i];
+      nw = nw > hi ? hi : nw;
+      nw = nw < wfloor ? wfloor : nw;
+      w[i] = (uint32_t)nw;
+      S += nw;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if ((enabled >> i) & 1u) w[i] = (uint32_t)(((uint64_t)w[i] << 16) / S);
+}
+
+// Lexicographic (delta, index) minimum over the warp; every lane gets it.
+__device__ __forceinline__ void warp_argmin(long long &d, int &c) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const long long d2 = __shfl_xor_sync(kFull, d, off);
+    const int c2 = __shfl_xor_sync(kFull, c, off);
+    if (d2 < d || (d2 == d && c2 < c)) {
+      d = d2;
+      c = c2;
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ long long ld_relaxed64(const long long *p) {
+  long long v;
+  asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Permutation moves as "cut and reorder" of an array of length m.
+// Five pieces P0 = [0,b1), A = [b1,b2), M = [b2,b3), B = [b3,b4), P4 = [b4,m);
+// the move produces P0 B M A' P4, with A' = A reversed when rev is set
+// (2-opt uses A only, with M and B empty).
+//   swap(lo,hi)        A=[lo], M=(lo,hi), B=[hi]
+//   2-opt(lo,hi)       A=[lo..hi] reversed
+//   insert(i -> j)     i<j: A=[i], B=(i,j];  i>j: A=[j,i), B=[i]
+//   or-opt(i, L, q)    q<i: A=[q,i), B=[i,i+L);  q>i: A=[i,i+L), B=[i+L,q+L)
+struct PMove {
+  int b1, b2, b3, b4;
+  int rev;
+};
+
+__device__ __forceinline__ PMove perm_decode(int op, uint32_t r1, uint32_t r2, int m) {
+  const uint32_t a = r1 >> 16, b = r1 & 0xFFFFu;
+  PMove mv;
+  if (op == OR_OPT) {
+    const int L = 2 + (int)(r2 & 1u);
+    const int i = posm(a, (uint32_t)(m - L + 1));
+    int q = posm(b, (uint32_t)(m - L));
+    q += (q >= i);
+    if (q < i) mv = {q, i, i, i + L, 0};
+    else mv = {i, i + L, i + L, q + L, 0};
+    return mv;
+  }
+  const int i = posm(a, (uint32_t)m);
+  int j = posm(b, (uint32_t)(m - 1));
+  j += (j >= i);
+  const int lo = min(i, j), hi = max(i, j);
+  if (op == SWAP) mv = {lo, lo + 1, hi, hi + 1, 0};
+  else if (op == TWO_OPT) mv = {lo, hi + 1, hi + 1, hi + 1, 1};
+  else if (i < j) mv = {i, i + 1, i + 1, j + 1, 0};
+  else mv = {j, i, i, i + 1, 0};
+  return mv;
+}
+
+// Position in the array before the move of the element at position q after it.
+__device__ __forceinline__ int perm_inv(const PMove &mv, int q) {
+  if (q < mv.b1 || q >= mv.b4) return q;
+  if (mv.rev) return mv.b1 + mv.b2 - 1 - q;
+  int off = q - mv.b1;
+  const int lb = mv.b4 - mv.b3;
+  if (off < lb) return mv.b3 + off;
+  off -= lb;
+  const int lm = mv.b3 - mv.b2;
+  if (off < lm) return mv.b2 + off;
+  return mv.b1 + (off - lm);
+}
+
+}  // namespace cgo

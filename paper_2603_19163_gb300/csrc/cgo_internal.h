@@ -1,0 +1,91 @@
+// Internal structures shared by the host runtime (cgo_api.cu) and the
+// kernels (cgo_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cgo {
+
+constexpr int kNops = 8;
+constexpr int kStats = 22;      // u_op[8] v_op[8] u_k[3] v_k[3]
+constexpr int kMaxWarps = 8;    // warps per CTA (kernel launch bound 256 threads)
+constexpr int kMaxAgents = 64;  // GAP agents
+
+enum Model { TSP = 0, QAP = 1, KNAPSACK = 2, GAP = 3, CVRPTW = 4 };
+enum Op { SWAP = 0, TWO_OPT = 1, INSERT = 2, OR_OPT = 3, FLIP = 4, PERTURB = 5 };
+enum Staging { STAGE_AUTO = 0, STAGE_SMEM = 1, STAGE_GLOBAL = 2 };
+
+// Per-instance search scalars (device memory, double-buffered in/out per launch).
+struct DevAos {
+  uint64_t T;                 // Q32.32
+  int64_t g;                  // generations completed
+  uint32_t w_op[kNops];       // Q16, global operator ids
+  uint32_t w_k[3];
+  uint32_t stag;
+  uint32_t pad0;
+  int64_t elite_prev;
+  uint32_t pend[kStats];      // counts of the open (incomplete) AOS window
+  int32_t elite;              // member index of the elite (after finalize)
+  int32_t pad1;
+  int64_t elite_cost;
+};
+
+// Per-launch synchronisation block (zeroed/reset by the host before a launch).
+struct DevSync {
+  uint32_t arrive;            // members arrived at window barriers (cumulative)
+  uint32_t error;             // bit 0: timeout, bit 1: invalid state
+  uint32_t acc[2][32];        // window count accumulators, cumulative per slot
+  int64_t elite[2];           // atomicMin of member bests per slot
+  uint32_t pend_out[kStats];  // counts of a window left open at the end
+  uint32_t pad[10];
+};
+
+// One instance's work for a launch.  Lives in device memory.
+struct KInst {
+  // instance
+  int32_t model, n, len, m;
+  int64_t capacity, lam0, lam1;
+  int32_t lb, ub;
+  uint32_t tag;
+  int32_t tri16;              // TSP triangle stored as int16
+  const int32_t *mat0, *mat1, *vec0, *vec1, *vec2, *vec3;
+  const void *tri;            // TSP upper triangle (row-major, i <= j)
+  int64_t shared_bytes;       // bytes of instance data staged per CTA (0 = global)
+  // parameters
+  int32_t P, C;
+  int32_t members;            // barrier arrivals expected per window (= P)
+  int32_t pad1;
+  uint32_t U, E;
+  uint64_t alpha;
+  uint32_t ema_a, w_floor, w_cap, stag_limit;
+  uint32_t op_cap[kNops];
+  uint32_t enabled;           // effective enabled-operator mask
+  uint32_t pad0;
+  uint64_t seed;
+  // launch range
+  int64_t g_begin, g_end;
+  // state
+  int32_t *cur, *bestsol;
+  int64_t *cost, *best;
+  const DevAos *aos_in;
+  DevAos *aos_out;
+  DevSync *sync;
+};
+
+// host-side launchers (cgo_kernels.cu)
+cudaError_t launch_init(const KInst &h, cudaStream_t st);
+cudaError_t launch_init_aos(const KInst &h, const DevAos &a0, cudaStream_t st);
+cudaError_t launch_evolve_single(const KInst &h, int warps, int64_t smem_bytes,
+                                 uint64_t timeout_ns, cudaStream_t st);
+cudaError_t launch_finalize(const KInst &h, cudaStream_t st);
+cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri,
+                           cudaStream_t st);
+// shared-memory needs of the evolve kernel
+int64_t smem_per_warp(const KInst &h);
+int64_t instance_data_bytes(const KInst &h);
+int64_t evolve_smem_bytes(const KInst &h, int warps, bool staged);
+int64_t smem_instance(const KInst &h);
+int max_coresident_ctas(const KInst &h, int warps, int64_t smem_bytes);
+int64_t max_smem_optin();
+
+}  // namespace cgo

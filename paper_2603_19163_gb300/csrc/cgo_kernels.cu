@@ -1,0 +1,1063 @@
+// Kernels of the per-solution search generation (sm_103a).
+//
+// One warp evolves one population member at a time (a CTA holds a few
+// members; a warp may own several).  Per generation the 32 lanes evaluate the
+// C candidates (C/32 per lane): each draws k from w_K and k operators from
+// w_S (Alg. "evolve"), and the cost delta of the k-step composite move is
+// computed exactly from the instance data without materialising it.  A warp
+// argmin picks the best candidate (ties to the lowest index), the Metropolis
+// test uses a pre-drawn Exp(1) variate, and the winner is applied in place.
+// After every U-th generation the members of an instance meet at a barrier
+// (global-memory counters, bounded wait) where the AOS counts are summed and
+// every warp applies Eq. "ema", the stagnation rule and, when due, elite
+// injection (Alg. "aos", Sec. 3.4.3, 4.2).
+#include <climits>
+#include <cooperative_groups.h>
+
+#include "cgo_device.cuh"
+
+namespace cgo {
+
+// ---------------------------------------------------------------- layout
+struct SolScal {
+  long long cost, best, aw, av;  // aw/av: knapsack sum of weights / values
+};
+
+struct Layout {
+  int64_t inst, sol_off, sol_stride, scr_off, scal_off, load_off, total;
+};
+
+__host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64_t(15); }
+
+__host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m, int nsol,
+                                              int warps, int model) {
+  Layout L;
+  L.inst = align16(inst_bytes);
+  L.sol_stride = align16((int64_t)len * 4);
+  L.sol_off = L.inst;
+  L.scr_off = L.sol_off + (int64_t)nsol * L.sol_stride;
+  const bool perm = (model == TSP || model == QAP || model == CVRPTW);
+  L.scal_off = L.scr_off + (perm ? (int64_t)warps * L.sol_stride : 0);
+  L.load_off = L.scal_off + align16((int64_t)nsol * (int64_t)sizeof(SolScal));
+  L.total = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
+  return L;
+}
+
+int64_t instance_data_bytes(const KInst &h) {
+  switch (h.model) {
+    case TSP: return align16((int64_t)h.n * (h.n + 1) / 2 * (h.tri16 ? 2 : 4));
+    case QAP: return 2 * align16((int64_t)h.n * h.n * 4);
+    case KNAPSACK: return 2 * align16((int64_t)h.n * 4);
+    case GAP: return 2 * align16((int64_t)h.m * h.n * 4) + align16((int64_t)h.m * 4);
+  }
+  return 0;
+}
+
+int64_t smem_instance(const KInst &h) { return instance_data_bytes(h); }
+int64_t smem_per_warp(const KInst &h) {
+  Layout a = make_layout(0, h.len, h.m, 1, 1, h.model);
+  return a.total;
+}
+
+// ------------------------------------------------------------- instance view
+struct View {
+  int n, len, m;
+  long long cap, lam0;
+  uint32_t tag, k0, k1;
+  const void *tri;
+  int n2m1;
+  const int32_t *F, *D;        // QAP
+  const int32_t *w, *v;        // knapsack
+  const int32_t *gc, *gr, *gcap;  // GAP
+};
+
+template <int NO>
+struct Stats {
+  uint32_t u[NO], v[NO], uk[3], vk[3];
+};
+
+template <int NO>
+__device__ __forceinline__ void stats_zero(Stats<NO> &s) {
+#pragma unroll
+  for (int i = 0; i < NO; ++i) s.u[i] = s.v[i] = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s.uk[i] = s.vk[i] = 0;
+}
+
+template <int NO>
+__device__ __forceinline__ void stats_op(Stats<NO> &s, int op, uint32_t imp) {
+#pragma unroll
+  for (int i = 0; i < NO; ++i) {
+    const uint32_t hit = (op == i);
+    s.u[i] += hit;
+    s.v[i] += hit & imp;
+  }
+}
+
+template <int NO>
+__device__ __forceinline__ void stats_k(Stats<NO> &s, int k, uint32_t imp) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const uint32_t hit = (k == i + 1);
+    s.uk[i] += hit;
+    s.vk[i] += hit & imp;
+  }
+}
+
+// per-encoding operator block: local op l is global op (base + l)
+template <int MODEL>
+struct Enc;
+template <>
+struct Enc<TSP> { static constexpr int NO = 4, BASE = 0; };
+template <>
+struct Enc<QAP> { static constexpr int NO = 4, BASE = 0; };
+template <>
+struct Enc<KNAPSACK> { static constexpr int NO = 1, BASE = 4; };
+template <>
+struct Enc<GAP> { static constexpr int NO = 1, BASE = 5; };
+
+template <int NO>
+struct Weights {
+  uint32_t op[NO], k[3];
+  uint32_t Wop, Wk;
+};
+
+template <int NO>
+__device__ __forceinline__ void weights_sum(Weights<NO> &w) {
+  w.Wop = 0;
+#pragma unroll
+  for (int i = 0; i < NO; ++i) w.Wop += w.op[i];
+  w.Wk = w.k[0] + w.k[1] + w.k[2];
+}
+
+__device__ __forceinline__ long long overp(long long x) { return x > 0 ? x : 0; }
+
+// ---------------------------------------------------------------- TSP
+template <bool T16>
+__device__ __forceinline__ long long tsp_d(const View &X, int x, int y) {
+  const int a = min(x, y), b = max(x, y);
+  const uint32_t idx = (((uint32_t)a * (uint32_t)(X.n2m1 - a)) >> 1) + (uint32_t)b;
+  if (T16) return ((const int16_t *)X.tri)[idx];
+  return ((const int32_t *)X.tri)[idx];
+}
+
+// element at position q of the array after the prior moves (most recent last)
+template <int NP>
+__device__ __forceinline__ int vlook(const int32_t *sol, int q, const PMove &p0,
+                                     const PMove &p1) {
+  if (NP >= 2) q = perm_inv(p1, q);
+  if (NP >= 1) q = perm_inv(p0, q);
+  return sol[q];
+}
+
+// Symmetric-TSP delta of one move on the (virtual) array: the tour is a
+// cyclic concatenation of the non-empty pieces; pieces keep their internal
+// edges (reversal does not change them when D is symmetric), so the delta is
+// the sum of the new junction edges minus the old ones.  When P0 and P4 are
+// both non-empty the closing edge P4 -> P0 is common to both and skipped.
+template <bool T16, int NP>
+__device__ long long tsp_step(const View &X, const int32_t *sol, const PMove &mv,
+                              const PMove &p0, const PMove &p1) {
+  const int m = X.len;
+  const int s[6] = {0, mv.b1, mv.b2, mv.b3, mv.b4, m};
+  int f[5], l[5];
+  bool ne[5];
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    ne[t] = s[t + 1] > s[t];
+    const int qf = min(s[t], m - 1), ql = max(s[t + 1] - 1, 0);
+    f[t] = vlook<NP>(sol, qf, p0, p1);
+    l[t] = (s[t + 1] - s[t] == 1) ? f[t] : vlook<NP>(sol, ql, p0, p1);
+  }
+  const bool skip = ne[0] && ne[4];
+  long long so = 0, sn = 0;
+  {
+    int first = 0, prev = 0;
+    bool any = false;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      if (ne[t]) {
+        if (any) so += tsp_d<T16>(X, prev, f[t]);
+        else first = f[t];
+        any = true;
+        prev = l[t];
+      }
+    }
+    if (!skip) so += tsp_d<T16>(X, prev, first);
+  }
+  {
+    const int nf[5] = {f[0], f[3], f[2], mv.rev ? l[1] : f[1], f[4]};
+    const int nl[5] = {l[0], l[3], l[2], mv.rev ? f[1] : l[1], l[4]};
+    const bool nn[5] = {ne[0], ne[3], ne[2], ne[1], ne[4]};
+    int first = 0, prev = 0;
+    bool any = false;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      if (nn[t]) {
+        if (any) sn += tsp_d<T16>(X, prev, nf[t]);
+        else first = nf[t];
+        any = true;
+        prev = nl[t];
+      }
+    }
+    if (!skip) sn += tsp_d<T16>(X, prev, first);
+  }
+  return sn - so;
+}
+
+// ---------------------------------------------------------------- QAP
+// Swap of positions r, s on the (virtual) permutation pi: O(n) delta of
+// sum_ij F[i][j] D[pi_i][pi_j] for general (asymmetric, non-zero diagonal)
+// F and D.
+template <int NP>
+__device__ long long qap_step(const View &X, const int32_t *sol, const PMove &mv,
+                              const PMove &p0, const PMove &p1) {
+  const int n = X.n;
+  const int r = mv.b1, s = mv.b3;
+  const int pr = vlook<NP>(sol, r, p0, p1), ps = vlook<NP>(sol, s, p0, p1);
+  const int32_t *F = X.F, *D = X.D;
+  const int32_t *Fr = F + (size_t)r * n, *Fs = F + (size_t)s * n;
+  const int32_t *Dr = D + (size_t)pr * n, *Ds = D + (size_t)ps * n;
+  long long acc = 0;
+  for (int k = 0; k < n; ++k) {
+    const int pk = vlook<NP>(sol, k, p0, p1);
+    const long long t1 = ((long long)Fr[k] - Fs[k]) * ((long long)Ds[pk] - Dr[pk]);
+    const int32_t *Fk = F + (size_t)k * n, *Dk = D + (size_t)pk * n;
+    const long long t2 = ((long long)Fk[r] - Fk[s]) * ((long long)Dk[ps] - Dk[pr]);
+    acc += (k != r && k != s) ? t1 + t2 : 0ll;
+  }
+  acc += ((long long)Fr[r] - Fs[s]) * ((long long)Ds[ps] - Dr[pr]);
+  acc += ((long long)Fr[s] - Fs[r]) * ((long long)Ds[pr] - Dr[ps]);
+  return acc;
+}
+
+// ------------------------------------------------- candidate evaluation
+template <int MODEL, bool T16>
+__device__ __forceinline__ long long perm_delta(const View &X, const int32_t *sol, const PMove &mv,
+                                                const PMove &p0, const PMove &p1, int np) {
+  if (MODEL == TSP) {
+    if (np == 0) return tsp_step<T16, 0>(X, sol, mv, p0, p1);
+    if (np == 1) return tsp_step<T16, 1>(X, sol, mv, p0, p1);
+    return tsp_step<T16, 2>(X, sol, mv, p0, p1);
+  } else {
+    if (np == 0) return qap_step<0>(X, sol, mv, p0, p1);
+    if (np == 1) return qap_step<1>(X, sol, mv, p0, p1);
+    return qap_step<2>(X, sol, mv, p0, p1);
+  }
+}
+
+template <int MODEL, bool T16>
+__device__ long long candidate_perm(const View &X, const int32_t *sol, const Weights<4> &W,
+                                    uint32_t c, uint32_t p, uint32_t g, Stats<4> &st) {
+  const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+  const int k = 1 + wsample(W.k, W.Wk, R0.w);
+  const int op0 = wsample(W.op, W.Wop, R0.x);
+  const PMove m0 = perm_decode(op0, R0.y, R0.z, X.len);
+  long long d = perm_delta<MODEL, T16>(X, sol, m0, m0, m0, 0);
+  int op1 = -1, op2 = -1;
+  if (k >= 2) {
+    const uint4 R1 = philox(ctr_word(c, 1, kKindMove), X.tag, p, g, X.k0, X.k1);
+    op1 = wsample(W.op, W.Wop, R1.x);
+    const PMove m1 = perm_decode(op1, R1.y, R1.z, X.len);
+    d += perm_delta<MODEL, T16>(X, sol, m1, m0, m0, 1);
+    if (k >= 3) {
+      const uint4 R2 = philox(ctr_word(c, 2, kKindMove), X.tag, p, g, X.k0, X.k1);
+      op2 = wsample(W.op, W.Wop, R2.x);
+      const PMove m2 = perm_decode(op2, R2.y, R2.z, X.len);
+      d += perm_delta<MODEL, T16>(X, sol, m2, m0, m1, 2);
+    }
+  }
+  const uint32_t imp = d < 0;
+  stats_op(st, op0, imp);
+  stats_op(st, op1, imp);
+  stats_op(st, op2, imp);
+  stats_k(st, k, imp);
+  return d;
+}
+
+// Knapsack: k flips on x (a flip of an index flipped earlier in the same
+// candidate undoes it); delta from the running weight/value sums.
+__device__ long long candidate_knap(const View &X, const int32_t *x, const Weights<1> &W,
+                                    long long W0, long long V0, uint32_t c, uint32_t p,
+                                    uint32_t g, Stats<1> &st) {
+  const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+  const int k = 1 + wsample(W.k, W.Wk, R0.w);
+  long long Wt = W0, Vt = V0;
+  int i0 = -1, i1 = -1;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    if (t < k) {
+      const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
+      const int i = posm(R.y >> 16, (uint32_t)X.n);
+      const int xi = x[i] ^ (int)(i == i0) ^ (int)(i == i1);
+      const long long wi = X.w[i], vi = X.v[i];
+      Wt += xi ? -wi : wi;
+      Vt += xi ? -vi : vi;
+      if (t == 0) i0 = i;
+      else if (t == 1) i1 = i;
+    }
+  }
+  const long long d = (-Vt + X.lam0 * overp(Wt - X.cap)) - (-V0 + X.lam0 * overp(W0 - X.cap));
+  const uint32_t imp = d < 0;
+  st.u[0] += k;
+  st.v[0] += imp ? k : 0;
+  stats_k(st, k, imp);
+  return d;
+}
+
+// GAP: k random resets of a job's agent; loads of touched agents tracked
+// through small override lists.
+__device__ long long candidate_gap(const View &X, const int32_t *x, const long long *loads,
+                                   const Weights<1> &W, uint32_t c, uint32_t p, uint32_t g,
+                                   Stats<1> &st) {
+  const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+  const int k = 1 + wsample(W.k, W.Wk, R0.w);
+  const int n = X.n, m = X.m;
+  int xj[2] = {-1, -1}, xv[2] = {0, 0};
+  int la[4] = {-1, -1, -1, -1};
+  long long lv[4] = {0, 0, 0, 0};
+  long long d = 0;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    if (t < k) {
+      const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
+      const int j = posm(R.y >> 16, (uint32_t)n);
+      const int dd = 1 + posm(R.y & 0xFFFFu, (uint32_t)(m - 1));
+      int ao = x[j];
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (q < t && xj[q] == j) ao = xv[q];
+      const int an = (ao + dd) % m;
+      long long Lo = loads[ao], Ln = loads[an];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (q < 2 * t && la[q] == ao) Lo = lv[q];
+        if (q < 2 * t && la[q] == an) Ln = lv[q];
+      }
+      const long long ro = X.gr[(size_t)ao * n + j], rn = X.gr[(size_t)an * n + j];
+      const long long co = X.gcap[ao], cn = X.gcap[an];
+      d += (long long)X.gc[(size_t)an * n + j] - X.gc[(size_t)ao * n + j];
+      d += X.lam0 * (overp(Lo - ro - co) - overp(Lo - co) + overp(Ln + rn - cn) - overp(Ln - cn));
+      if (t < 2) {
+        xj[t] = j;
+        xv[t] = an;
+        la[2 * t] = ao;
+        lv[2 * t] = Lo - ro;
+        la[2 * t + 1] = an;
+        lv[2 * t + 1] = Ln + rn;
+      }
+    }
+  }
+  const uint32_t imp = d < 0;
+  st.u[0] += k;
+  st.v[0] += imp ? k : 0;
+  stats_k(st, k, imp);
+  return d;
+}
+
+// --------------------------------------------------------------- apply
+// Materialise one permutation move in place (warp-cooperative): positions
+// that change are gathered through the inverse map into the scratch array,
+// then written back.  Only A and B move when they have equal lengths.
+__device__ void perm_materialise(int32_t *sol, int32_t *scr, const PMove &mv, int lane) {
+  const int la = mv.b2 - mv.b1, lb = mv.b4 - mv.b3;
+  const bool ends = !mv.rev && la == lb;
+  const int cnt = ends ? 2 * la : mv.b4 - mv.b1;
+  for (int e = lane; e < cnt; e += 32) {
+    const int q = ends ? (e < la ? mv.b1 + e : mv.b3 + (e - la)) : mv.b1 + e;
+    scr[q] = sol[perm_inv(mv, q)];
+  }
+  __syncwarp();
+  for (int e = lane; e < cnt; e += 32) {
+    const int q = ends ? (e < la ? mv.b1 + e : mv.b3 + (e - la)) : mv.b1 + e;
+    sol[q] = scr[q];
+  }
+  __syncwarp();
+}
+
+template <int NO>
+__device__ __forceinline__ int regen_k(const View &X, const Weights<NO> &W, uint32_t c,
+                                       uint32_t p, uint32_t g, uint4 &R0) {
+  R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+  return 1 + wsample(W.k, W.Wk, R0.w);
+}
+
+__device__ void apply_perm(const View &X, int32_t *sol, int32_t *scr, const Weights<4> &W,
+                           uint32_t c, uint32_t p, uint32_t g, int lane) {
+  uint4 R0;
+  const int k = regen_k(X, W, c, p, g, R0);
+  for (int t = 0; t < k; ++t) {
+    const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
+    const int op = wsample(W.op, W.Wop, R.x);
+    const PMove mv = perm_decode(op, R.y, R.z, X.len);
+    perm_materialise(sol, scr, mv, lane);
+  }
+}
+
+__device__ void apply_knap(const View &X, int32_t *x, const Weights<1> &W, uint32_t c,
+                           uint32_t p, uint32_t g, int lane, long long &aw, long long &av) {
+  uint4 R0;
+  const int k = regen_k(X, W, c, p, g, R0);
+  for (int t = 0; t < k; ++t) {
+    const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
+    const int i = posm(R.y >> 16, (uint32_t)X.n);
+    const int xi = x[i];
+    __syncwarp();
+    if (lane == 0) x[i] = xi ^ 1;
+    aw += xi ? -(long long)X.w[i] : (long long)X.w[i];
+    av += xi ? -(long long)X.v[i] : (long long)X.v[i];
+    __syncwarp();
+  }
+}
+
+__device__ void apply_gap(const View &X, int32_t *x, long long *loads, const Weights<1> &W,
+                          uint32_t c, uint32_t p, uint32_t g, int lane) {
+  uint4 R0;
+  const int k = regen_k(X, W, c, p, g, R0);
+  for (int t = 0; t < k; ++t) {
+    const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
+    const int j = posm(R.y >> 16, (uint32_t)X.n);
+    const int dd = 1 + posm(R.y & 0xFFFFu, (uint32_t)(X.m - 1));
+    const int ao = x[j];
+    const int an = (ao + dd) % X.m;
+    __syncwarp();
+    if (lane == 0) {
+      x[j] = an;
+      loads[ao] -= X.gr[(size_t)ao * X.n + j];
+      loads[an] += X.gr[(size_t)an * X.n + j];
+    }
+    __syncwarp();
+  }
+}
+
+// warp-cooperative auxiliary sums of one member (knapsack W/V, GAP loads)
+__device__ void aux_init(int model, const View &X, const int32_t *x, SolScal &sc,
+                         long long *loads, int lane) {
+  if (model == KNAPSACK) {
+    long long W = 0, V = 0;
+    for (int i = lane; i < X.n; i += 32)
+      if (x[i]) {
+        W += X.w[i];
+        V += X.v[i];
+      }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      W += __shfl_xor_sync(kFull, W, off);
+      V += __shfl_xor_sync(kFull, V, off);
+    }
+    sc.aw = W;
+    sc.av = V;
+  } else if (model == GAP) {
+    for (int a = 0; a < X.m; ++a) {
+      long long L = 0;
+      for (int j = lane; j < X.n; j += 32)
+        if (x[j] == a) L += X.gr[(size_t)a * X.n + j];
+#pragma unroll
+      for (int off = 16; off; off >>= 1) L += __shfl_xor_sync(kFull, L, off);
+      if (lane == 0) loads[a] = L;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------ window barrier
+// All members of the instance arrive (counting members), then wait until
+// the arrival count reaches P * (barrier index + 1).  The wait is bounded:
+// on timeout (or another warp's error) it raises the error flag and returns
+// false so the kernel can exit.
+__device__ bool member_barrier(DevSync *S, uint32_t arrivals, uint32_t target, uint64_t timeout_ns,
+                               int lane) {
+  __threadfence();
+  __syncwarp();
+  int ok = 1;
+  if (lane == 0) {
+    atomicAdd(&S->arrive, arrivals);
+    const uint64_t t0 = global_ns();
+    for (;;) {
+      if (ld_acquire(&S->arrive) >= target) break;
+      if (ld_relaxed(&S->error)) {
+        ok = 0;
+        break;
+      }
+      if (global_ns() - t0 > timeout_ns) {
+        atomicOr(&S->error, 1u);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  ok = __shfl_sync(kFull, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
+// ---------------------------------------------------------- evolve unit
+template <int MODEL, bool T16>
+__device__ void evolve_members(const KInst &I, const View &X, unsigned char *smem, const Layout &Lo,
+                               int p0, int nsol, int warps, uint64_t timeout_ns) {
+  constexpr int NO = Enc<MODEL>::NO, BASE = Enc<MODEL>::BASE;
+  constexpr bool PERM = (MODEL == TSP || MODEL == QAP);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int mine = nsol > wid ? (nsol - wid + warps - 1) / warps : 0;
+  if (mine == 0) return;
+  const int len = I.len, P = I.P, C = I.C;
+  DevSync *S = I.sync;
+  int32_t *scr = (int32_t *)(smem + Lo.scr_off + (int64_t)wid * Lo.sol_stride);
+  SolScal *scal = (SolScal *)(smem + Lo.scal_off);
+
+  // load this warp's members
+  for (int e = 0; e < mine; ++e) {
+    const int ls = wid + e * warps, p = p0 + ls;
+    int32_t *sol = (int32_t *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+    const int32_t *src = I.cur + (int64_t)p * len;
+    for (int i = lane; i < len; i += 32) sol[i] = src[i];
+    __syncwarp();
+    SolScal sc;
+    sc.cost = I.cost[p];
+    sc.best = I.best[p];
+    sc.aw = sc.av = 0;
+    aux_init(MODEL, X, sol, sc, (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, lane);
+    if (lane == 0) scal[ls] = sc;
+    __syncwarp();
+  }
+
+  // instance-wide scalars (identical in every warp)
+  const DevAos *A = I.aos_in;
+  uint64_t T = A->T;
+  Weights<NO> W;
+  uint32_t capl[NO];
+#pragma unroll
+  for (int l = 0; l < NO; ++l) {
+    W.op[l] = A->w_op[BASE + l];
+    capl[l] = I.op_cap[BASE + l];
+  }
+  W.k[0] = A->w_k[0];
+  W.k[1] = A->w_k[1];
+  W.k[2] = A->w_k[2];
+  weights_sum(W);
+  const uint32_t en_local = (I.enabled >> BASE) & ((1u << NO) - 1u);
+  uint32_t stag = A->stag;
+  long long elite_prev = A->elite_prev;
+  uint32_t pend = lane < kStats ? A->pend[lane] : 0u;
+  bool pend_used = false;
+  uint32_t prev_acc[2] = {0u, 0u};
+  uint32_t nb = 0, wi = 0;
+  Stats<NO> st;
+  stats_zero(st);
+  const int cpl = (C + 31) >> 5;
+
+  int64_t g = I.g_begin;
+  while (g < I.g_end) {
+    const int64_t wend = min(I.g_end, (g / I.U + 1) * (int64_t)I.U);
+    const uint64_t Tw = T;
+    long long minbest = LLONG_MAX;
+    for (int e = 0; e < mine; ++e) {
+      const int ls = wid + e * warps;
+      const uint32_t p = (uint32_t)(p0 + ls);
+      int32_t *sol = (int32_t *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+      long long *loads = (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m;
+      SolScal sc = scal[ls];
+      T = Tw;
+      for (int64_t gb = g; gb < wend; gb += 32) {
+        const int cnt = (int)min((int64_t)32, wend - gb);
+        uint64_t Ereg = 0;
+        if (lane < cnt) {
+          const uint4 Ra = philox(ctr_word(0, 0, kKindAccept), X.tag, p, (uint32_t)(gb + lane), X.k0,
+                                  X.k1);
+          Ereg = exp_variate_q32(Ra.x);
+        }
+        for (int q = 0; q < cnt; ++q) {
+          const uint32_t gg = (uint32_t)(gb + q);
+          const uint64_t E = __shfl_sync(kFull, Ereg, q);
+          long long bd = LLONG_MAX;
+          int bc = INT_MAX;
+          for (int slot = 0; slot < cpl; ++slot) {
+            const int c = slot * 32 + lane;
+            if (c < C) {
+              long long d;
+              if constexpr (PERM) d = candidate_perm<MODEL, T16>(X, sol, W, c, p, gg, st);
+              else if constexpr (MODEL == KNAPSACK)
+                d = candidate_knap(X, sol, W, sc.aw, sc.av, c, p, gg, st);
+              else d = candidate_gap(X, sol, loads, W, c, p, gg, st);
+              if (d < bd) {
+                bd = d;
+                bc = c;
+              }
+            }
+          }
+          warp_argmin(bd, bc);
+          if (accept_move(bd, T, E)) {
+            if constexpr (PERM) apply_perm(X, sol, scr, W, bc, p, gg, lane);
+            else if constexpr (MODEL == KNAPSACK)
+              apply_knap(X, sol, W, bc, p, gg, lane, sc.aw, sc.av);
+            else apply_gap(X, sol, loads, W, bc, p, gg, lane);
+            sc.cost += bd;
+            if (sc.cost < sc.best) {
+              sc.best = sc.cost;
+              int32_t *dst = I.bestsol + (int64_t)p * len;
+              for (int i = lane; i < len; i += 32) dst[i] = sol[i];
+            }
+          }
+          T = cool(T, I.alpha);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) scal[ls] = sc;
+      __syncwarp();
+      minbest = min(minbest, sc.best);
+    }
+    g = wend;
+    if (g % I.U != 0) continue;  // only at the very end of a launch
+
+    // ------------------------------------------------ AOS window end
+    const bool inject = I.E > 0 && (g % I.E) == 0;
+    uint32_t tot[NO * 2 + 6];
+#pragma unroll
+    for (int l = 0; l < NO; ++l) {
+      tot[l] = __reduce_add_sync(kFull, st.u[l]);
+      tot[NO + l] = __reduce_add_sync(kFull, st.v[l]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      tot[2 * NO + i] = __reduce_add_sync(kFull, st.uk[i]);
+      tot[2 * NO + 3 + i] = __reduce_add_sync(kFull, st.vk[i]);
+    }
+    uint32_t my = 0;
+#pragma unroll
+    for (int l = 0; l < NO; ++l) {
+      my = (lane == BASE + l) ? tot[l] : my;
+      my = (lane == 8 + BASE + l) ? tot[NO + l] : my;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      my = (lane == 16 + i) ? tot[2 * NO + i] : my;
+      my = (lane == 19 + i) ? tot[2 * NO + 3 + i] : my;
+    }
+    const int slot = wi & 1;
+    if (lane < kStats && my) atomicAdd(&S->acc[slot][lane], my);
+    if (lane == 0) atomicMin((long long *)&S->elite[slot], minbest);
+    if (inject && lane == 0) {
+      for (int e = 0; e < mine; ++e) {
+        const int ls = wid + e * warps;
+        I.cost[p0 + ls] = scal[ls].cost;
+        I.best[p0 + ls] = scal[ls].best;
+      }
+    }
+    if (!member_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, lane)) return;
+    ++nb;
+    uint32_t cum = lane < kStats ? ld_relaxed(&S->acc[slot][lane]) : 0u;
+    uint32_t total = cum - prev_acc[slot];
+    prev_acc[slot] = cum;
+    if (!pend_used) total += pend;
+    pend_used = true;
+    const long long elite = ld_relaxed64((const long long *)&S->elite[slot]);
+    ++wi;
+
+    uint32_t uo[NO], vo[NO], uk[3], vk[3], capk[3] = {65536u, 65536u, 65536u};
+#pragma unroll
+    for (int l = 0; l < NO; ++l) {
+      uo[l] = __shfl_sync(kFull, total, BASE + l);
+      vo[l] = __shfl_sync(kFull, total, 8 + BASE + l);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      uk[i] = __shfl_sync(kFull, total, 16 + i);
+      vk[i] = __shfl_sync(kFull, total, 19 + i);
+    }
+    aos_level<NO>(W.op, uo, vo, en_local, capl, I.ema_a, I.w_floor, I.w_cap);
+    aos_level<3>(W.k, uk, vk, 7u, capk, I.ema_a, I.w_floor, I.w_cap);
+    if (elite < elite_prev) stag = 0;
+    else ++stag;
+    elite_prev = elite;
+    if (I.stag_limit > 0 && stag >= I.stag_limit) {
+      W.k[0] = 52429u;
+      W.k[1] = 9830u;
+      W.k[2] = 3277u;
+      stag = 0;
+    }
+    weights_sum(W);
+    stats_zero(st);
+
+    if (inject) {
+      // elite = lowest best (lowest index on ties), worst = highest cost
+      long long bb = LLONG_MAX, nwc = LLONG_MAX;
+      int be = INT_MAX, wq = INT_MAX;
+      for (int q = lane; q < P; q += 32) {
+        const long long b = ld_relaxed64((const long long *)I.best + q);
+        const long long cq = ld_relaxed64((const long long *)I.cost + q);
+        if (b < bb) {
+          bb = b;
+          be = q;
+        }
+        if (-cq < nwc) {
+          nwc = -cq;
+          wq = q;
+        }
+      }
+      warp_argmin(bb, be);
+      warp_argmin(nwc, wq);
+      const int lw = wq - p0;
+      if (lw >= 0 && lw < nsol && (lw % warps) == wid) {
+        int32_t *sol = (int32_t *)(smem + Lo.sol_off + (int64_t)lw * Lo.sol_stride);
+        const int32_t *src = I.bestsol + (int64_t)be * len;
+        for (int i = lane; i < len; i += 32) sol[i] = __ldcg(src + i);
+        __syncwarp();
+        SolScal sc = scal[lw];
+        sc.cost = bb;
+        if (bb < sc.best) {
+          sc.best = bb;
+          int32_t *dst = I.bestsol + (int64_t)wq * len;
+          for (int i = lane; i < len; i += 32) dst[i] = sol[i];
+        }
+        aux_init(MODEL, X, sol, sc, (long long *)(smem + Lo.load_off) + (int64_t)lw * X.m, lane);
+        __syncwarp();
+        if (lane == 0) scal[lw] = sc;
+        __syncwarp();
+      }
+      if (!member_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, lane)) return;
+      ++nb;
+    }
+  }
+
+  // ------------------------------------------------ write back
+  for (int e = 0; e < mine; ++e) {
+    const int ls = wid + e * warps, p = p0 + ls;
+    const int32_t *sol = (const int32_t *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+    int32_t *dst = I.cur + (int64_t)p * len;
+    for (int i = lane; i < len; i += 32) dst[i] = sol[i];
+    if (lane == 0) {
+      I.cost[p] = scal[ls].cost;
+      I.best[p] = scal[ls].best;
+    }
+  }
+  // counts of a window left open by this launch
+  if (I.g_end % I.U != 0) {
+    uint32_t my = 0;
+#pragma unroll
+    for (int l = 0; l < NO; ++l) {
+      const uint32_t tu = __reduce_add_sync(kFull, st.u[l]), tv = __reduce_add_sync(kFull, st.v[l]);
+      my = (lane == BASE + l) ? tu : my;
+      my = (lane == 8 + BASE + l) ? tv : my;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const uint32_t tu = __reduce_add_sync(kFull, st.uk[i]), tv = __reduce_add_sync(kFull, st.vk[i]);
+      my = (lane == 16 + i) ? tu : my;
+      my = (lane == 19 + i) ? tv : my;
+    }
+    if (p0 + wid == 0 && !pend_used) my += pend;
+    if (lane < kStats && my) atomicAdd(&S->pend_out[lane], my);
+  }
+  if (p0 + wid == 0 && lane == 0) {
+    DevAos *O = I.aos_out;
+    O->T = T;
+    O->g = I.g_end;
+    for (int i = 0; i < kNops; ++i) O->w_op[i] = 0;
+#pragma unroll
+    for (int l = 0; l < NO; ++l) O->w_op[BASE + l] = W.op[l];
+    O->w_k[0] = W.k[0];
+    O->w_k[1] = W.k[1];
+    O->w_k[2] = W.k[2];
+    O->stag = stag;
+    O->elite_prev = elite_prev;
+  }
+}
+
+// stage this unit's instance data into shared memory (or point at global)
+__device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
+  View X;
+  X.n = I.n;
+  X.len = I.len;
+  X.m = I.m;
+  X.cap = I.capacity;
+  X.lam0 = I.lam0;
+  X.tag = I.tag;
+  X.k0 = (uint32_t)I.seed;
+  X.k1 = (uint32_t)(I.seed >> 32);
+  X.n2m1 = 2 * I.n - 1;
+  X.tri = I.tri;
+  X.F = I.mat0;
+  X.D = I.mat1;
+  X.w = I.vec0;
+  X.v = I.vec1;
+  X.gc = I.mat0;
+  X.gr = I.mat1;
+  X.gcap = I.vec0;
+  if (!staged) return X;
+  auto copy = [&](const void *src, int64_t bytes, int64_t off) {
+    const int4 *s = (const int4 *)src;
+    int4 *d = (int4 *)(smem + off);
+    const int64_t n16 = align16(bytes) / 16;
+    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) d[i] = s[i];
+    return (const void *)(smem + off);
+  };
+  switch (I.model) {
+    case TSP:
+      X.tri = copy(I.tri, (int64_t)I.n * (I.n + 1) / 2 * (I.tri16 ? 2 : 4), 0);
+      break;
+    case QAP: {
+      const int64_t b = align16((int64_t)I.n * I.n * 4);
+      X.F = (const int32_t *)copy(I.mat0, b, 0);
+      X.D = (const int32_t *)copy(I.mat1, b, b);
+      break;
+    }
+    case KNAPSACK: {
+      const int64_t b = align16((int64_t)I.n * 4);
+      X.w = (const int32_t *)copy(I.vec0, b, 0);
+      X.v = (const int32_t *)copy(I.vec1, b, b);
+      break;
+    }
+    case GAP: {
+      const int64_t b = align16((int64_t)I.m * I.n * 4);
+      X.gc = (const int32_t *)copy(I.mat0, b, 0);
+      X.gr = (const int32_t *)copy(I.mat1, b, b);
+      X.gcap = (const int32_t *)copy(I.vec0, (int64_t)I.m * 4, 2 * b);
+      break;
+    }
+  }
+  return X;
+}
+
+// One CTA per unit: unit u covers members [u * warps, (u+1) * warps) of
+// instance 0 (single solve, cooperative launch so that all members of the
+// instance are resident together).
+template <int MODEL, bool T16>
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    evolve_kernel(const __grid_constant__ KInst I, int warps, uint64_t timeout_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const bool staged = I.shared_bytes > 0;
+  const View X = make_view(I, smem, staged);
+  __syncthreads();
+  const int p0 = blockIdx.x * warps;
+  const int nsol = min(warps, I.P - p0);
+  const Layout Lo = make_layout(staged ? I.shared_bytes : 0, I.len, I.m, warps, warps, I.model);
+  evolve_members<MODEL, T16>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
+}
+
+// ---------------------------------------------------------------- init
+__device__ long long full_cost(const KInst &I, const int32_t *x) {
+  const int n = I.n;
+  long long s = 0;
+  switch (I.model) {
+    case TSP:
+      for (int k = 0; k < n; ++k) s += I.mat0[(size_t)x[k] * n + x[(k + 1) % n]];
+      return s;
+    case QAP:
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          s += (long long)I.mat0[(size_t)i * n + j] * I.mat1[(size_t)x[i] * n + x[j]];
+      return s;
+    case KNAPSACK: {
+      long long W = 0, V = 0;
+      for (int i = 0; i < n; ++i)
+        if (x[i]) {
+          W += I.vec0[i];
+          V += I.vec1[i];
+        }
+      return -V + I.lam0 * overp(W - I.capacity);
+    }
+    case GAP: {
+      for (int j = 0; j < n; ++j) s += I.mat0[(size_t)x[j] * n + j];
+      for (int a = 0; a < I.m; ++a) {
+        long long L = 0;
+        for (int j = 0; j < n; ++j)
+          if (x[j] == a) L += I.mat1[(size_t)a * n + j];
+        s += I.lam0 * overp(L - I.vec0[a]);
+      }
+      return s;
+    }
+  }
+  return 0;
+}
+
+// one thread per member: Philox-seeded Fisher-Yates / random bits / random
+// integers, then the exact cost
+__global__ void init_kernel(const __grid_constant__ KInst I) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= I.P) return;
+  const int len = I.len;
+  int32_t *x = I.cur + (int64_t)p * len;
+  const uint32_t k0 = (uint32_t)I.seed, k1 = (uint32_t)(I.seed >> 32);
+  const bool perm = (I.model == TSP || I.model == QAP || I.model == CVRPTW);
+  if (perm) {
+    for (int i = 0; i < len; ++i) x[i] = i;
+    uint4 R = make_uint4(0, 0, 0, 0);
+    for (int i = len - 1; i >= 1; --i) {
+      const int d = len - 1 - i;
+      if ((d & 3) == 0) R = philox(ctr_word((uint32_t)(d >> 2), 0, kKindInit), I.tag, (uint32_t)p,
+                                   kInitGen, k0, k1);
+      const uint32_t w = (d & 3) == 0 ? R.x : (d & 3) == 1 ? R.y : (d & 3) == 2 ? R.z : R.w;
+      const int j = (int)(((uint64_t)w * (uint64_t)(i + 1)) >> 32);
+      const int t = x[i];
+      x[i] = x[j];
+      x[j] = t;
+    }
+  } else {
+    const int lb = I.model == GAP ? 0 : I.lb;
+    const int ub = I.model == GAP ? I.m - 1 : I.ub;
+    const uint64_t R = (uint64_t)((int64_t)ub - lb + 1);
+    uint4 Q = make_uint4(0, 0, 0, 0);
+    for (int i = 0; i < len; ++i) {
+      if ((i & 3) == 0) Q = philox(ctr_word((uint32_t)(i >> 2), 0, kKindInit), I.tag, (uint32_t)p,
+                                   kInitGen, k0, k1);
+      const uint32_t w = (i & 3) == 0 ? Q.x : (i & 3) == 1 ? Q.y : (i & 3) == 2 ? Q.z : Q.w;
+      if (I.model == KNAPSACK) x[i] = (int32_t)(w & 1u);
+      else x[i] = lb + (int32_t)(((uint64_t)w * R) >> 32);
+    }
+  }
+  const long long c = full_cost(I, x);
+  I.cost[p] = c;
+  I.best[p] = c;
+  int32_t *b = I.bestsol + (int64_t)p * len;
+  for (int i = 0; i < len; ++i) b[i] = x[i];
+}
+
+// elite = lowest best cost, lowest index on ties (one block)
+__device__ void block_elite(const KInst &I, int &e_out, long long &c_out) {
+  __shared__ long long sb[32];
+  __shared__ int se[32];
+  long long bb = LLONG_MAX;
+  int be = INT_MAX;
+  for (int q = threadIdx.x; q < I.P; q += blockDim.x) {
+    const long long b = I.best[q];
+    if (b < bb) {
+      bb = b;
+      be = q;
+    }
+  }
+  warp_argmin(bb, be);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sb[wid] = bb;
+    se[wid] = be;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    bb = lane < nw ? sb[lane] : LLONG_MAX;
+    be = lane < nw ? se[lane] : INT_MAX;
+    warp_argmin(bb, be);
+  }
+  e_out = be;
+  c_out = bb;
+}
+
+__global__ void init_aos_kernel(const __grid_constant__ KInst I, DevAos a0) {
+  int e;
+  long long c;
+  block_elite(I, e, c);
+  if (threadIdx.x == 0) {
+    a0.elite = e;
+    a0.elite_cost = c;
+    a0.elite_prev = c;
+    *I.aos_out = a0;
+  }
+}
+
+__global__ void finalize_kernel(const __grid_constant__ KInst I) {
+  int e;
+  long long c;
+  block_elite(I, e, c);
+  if (threadIdx.x == 0) {
+    I.aos_out->elite = e;
+    I.aos_out->elite_cost = c;
+  }
+  if (threadIdx.x < kStats) I.aos_out->pend[threadIdx.x] = I.sync->pend_out[threadIdx.x];
+}
+
+__global__ void triangle_kernel(const int32_t *__restrict__ mat, int n, int tri16, void *tri) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (j < i) continue;
+    const uint32_t idx = (((uint32_t)i * (uint32_t)(2 * n - 1 - i)) >> 1) + (uint32_t)j;
+    if (tri16) ((int16_t *)tri)[idx] = (int16_t)mat[t];
+    else ((int32_t *)tri)[idx] = mat[t];
+  }
+}
+
+// ------------------------------------------------------------ launchers
+cudaError_t launch_init(const KInst &h, cudaStream_t st) {
+  const int threads = 128, blocks = (h.P + threads - 1) / threads;
+  init_kernel<<<blocks, threads, 0, st>>>(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_aos(const KInst &h, const DevAos &a0, cudaStream_t st) {
+  init_aos_kernel<<<1, 256, 0, st>>>(h, a0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const KInst &h, cudaStream_t st) {
+  finalize_kernel<<<1, 256, 0, st>>>(h);
+  return cudaGetLastError();
+}
+
+cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri, cudaStream_t st) {
+  const int64_t total = (int64_t)n * n;
+  const int blocks = (int)min((int64_t)1024, (total + 255) / 256);
+  triangle_kernel<<<blocks, 256, 0, st>>>(d_mat, n, tri16, d_tri);
+  return cudaGetLastError();
+}
+
+template <int MODEL, bool T16>
+static const void *evolve_fn() {
+  return (const void *)evolve_kernel<MODEL, T16>;
+}
+
+static const void *pick_evolve(const KInst &h) {
+  switch (h.model) {
+    case TSP: return h.tri16 ? evolve_fn<TSP, true>() : evolve_fn<TSP, false>();
+    case QAP: return evolve_fn<QAP, false>();
+    case KNAPSACK: return evolve_fn<KNAPSACK, false>();
+    case GAP: return evolve_fn<GAP, false>();
+  }
+  return nullptr;
+}
+
+int64_t max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+int max_coresident_ctas(const KInst &h, int warps, int64_t smem_bytes) {
+  const void *fn = pick_evolve(h);
+  if (!fn) return 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, (size_t)smem_bytes) !=
+      cudaSuccess)
+    return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+
+cudaError_t launch_evolve_single(const KInst &h, int warps, int64_t smem_bytes,
+                                 uint64_t timeout_ns, cudaStream_t st) {
+  const void *fn = pick_evolve(h);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  const int grid = (h.P + warps - 1) / warps;
+  KInst hi = h;
+  void *args[] = {(void *)&hi, (void *)&warps, (void *)&timeout_ns};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(warps * 32), args, (size_t)smem_bytes, st);
+}
+
+}  // namespace cgo
+
+namespace cgo {
+int64_t evolve_smem_bytes(const KInst &h, int warps, bool staged) {
+  const Layout L =
+      make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, warps, warps, h.model);
+  return L.total;
+}
+}  // namespace cgo

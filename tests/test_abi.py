@@ -1,0 +1,77 @@
+"""The C-ABI library loads and exports every entry point the header
+declares; the ctypes structs match the C layout (no GPU needed)."""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cgo.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cgo_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("cgo_problem_create", "cgo_problem_destroy", "cgo_params_default", "cgo_solve",
+                 "cgo_best", "cgo_solve_batch", "cgo_state_get", "cgo_state_set",
+                 "cgo_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2603_19163_gb300 import cgo
+    L = cgo.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert cgo.version().startswith("cgo")
+
+
+def test_ctypes_layout_matches_c():
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    from paper_2603_19163_gb300 import cgo
+    src = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "cgo.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(cgo_problem_desc), sizeof(cgo_params),
+         sizeof(cgo_state), sizeof(cgo_launch));
+  printf("%zu %zu %zu %zu\n", offsetof(cgo_params, generations), offsetof(cgo_params, T0_q32),
+         offsetof(cgo_params, op_cap_q16), offsetof(cgo_state, cur));
+  printf("%zu %zu\n", offsetof(cgo_problem_desc, capacity), offsetof(cgo_problem_desc, instance_tag));
+  return 0;
+}
+"""
+    d = os.path.join(ROOT, "tests", "_build")
+    os.makedirs(d, exist_ok=True)
+    c = os.path.join(d, "layout.c")
+    exe = os.path.join(d, "layout")
+    open(c, "w").write(src)
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    want = [ctypes.sizeof(cgo.cgo_problem_desc), ctypes.sizeof(cgo.cgo_params),
+            ctypes.sizeof(cgo.cgo_state), ctypes.sizeof(cgo.cgo_launch),
+            cgo.cgo_params.generations.offset, cgo.cgo_params.T0_q32.offset,
+            cgo.cgo_params.op_cap_q16.offset, cgo.cgo_state.cur.offset,
+            cgo.cgo_problem_desc.capacity.offset, cgo.cgo_problem_desc.instance_tag.offset]
+    assert [int(x) for x in out] == want
+
+
+def test_errors_are_reported_without_a_gpu_call():
+    from paper_2603_19163_gb300 import cgo
+    L = cgo.lib()
+    h = ctypes.c_void_p()
+    d = cgo.cgo_problem_desc()
+    d.struct_size = 3          # wrong size: rejected before any CUDA call
+    assert L.cgo_problem_create(ctypes.byref(d), ctypes.byref(h)) == cgo.ERR_INVALID
+    assert b"struct_size" in L.cgo_last_error()
+    assert L.cgo_solve(None, None, 0, None) == cgo.ERR_INVALID

@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA search (through the C ABI) against the CPU oracle.
+
+Every case runs the same instance, parameters and seed on both sides and
+compares the complete search state bit for bit: current and best solutions,
+current and best costs, temperature, both AOS weight levels, stagnation
+counter, the elite cost of the last update and the counts of the open AOS
+window.  The work is integer, so the tolerance is zero.
+"""
+import numpy as np
+import pytest
+
+import instances as I
+import oracle as O
+from conftest import SEEDS
+from helpers import assert_same_state, oracle_run, params_for
+
+pytestmark = pytest.mark.gpu
+
+SW, TO, INS, OR = O.SWAP, O.TWO_OPT, O.INSERT, O.OR_OPT
+
+
+@pytest.fixture(scope="module")
+def cgo():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_19163_gb300 import cgo as C
+    C.lib()
+    return C
+
+
+def run_both(C, inst, params, seed, warps=0, staging=0):
+    prob = C.Problem(inst)
+    prob.set_launch(warps, staging)
+    prob.solve(params, seed)
+    g = prob.state()
+    o = oracle_run(inst, params, seed, params["G"])
+    return prob, g, o
+
+
+# --------------------------------------------------------------------- TSP
+@pytest.mark.parametrize("seed", SEEDS)
+def test_tsp_n20_config(cgo, seed):
+    """TSP n=20, P=32, C=128, swap/2-opt/insertion at equal weight, T0=100,
+    alpha=0.999, 2000 generations."""
+    inst = I.tsp_uniform(20, 0)
+    p = params_for(inst, P=32, C=128, G=2000, ops=[SW, TO, INS])
+    _, g, o = run_both(cgo, inst, p, seed)
+    assert_same_state(g, o, "tsp20 seed %d" % seed)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 33])
+def test_tsp_small_n_all_ops(cgo, n):
+    inst = I.tsp_uniform(n, 10 + n)
+    p = params_for(inst, P=5, C=40, G=37, U=3, ops=[SW, TO, INS, OR])
+    _, g, o = run_both(cgo, inst, p, 3)
+    assert_same_state(g, o, "n=%d" % n)
+
+
+@pytest.mark.parametrize("op", [SW, TO, INS, OR])
+@pytest.mark.parametrize("kw", [(65536, 0, 0), (0, 65536, 0), (0, 0, 65536)])
+def test_tsp_each_op_each_k(cgo, op, kw):
+    inst = I.tsp_uniform(17, 21)
+    p = params_for(inst, P=4, C=64, G=30, U=5, ops=[op], w_k=list(kw), stag_limit=0)
+    _, g, o = run_both(cgo, inst, p, 9)
+    assert_same_state(g, o, "op %d k %s" % (op, kw))
+
+
+@pytest.mark.parametrize("C", [1, 31, 32, 33, 100, 257])
+def test_tsp_candidate_counts(cgo, C):
+    inst = I.tsp_uniform(29, 22)
+    p = params_for(inst, P=6, C=C, G=23, U=4)
+    _, g, o = run_both(cgo, inst, p, 5)
+    assert_same_state(g, o, "C=%d" % C)
+
+
+@pytest.mark.parametrize("P,warps", [(1, 0), (3, 1), (17, 2), (9, 4), (40, 8), (64, 0)])
+def test_tsp_population_and_launch_shape(cgo, P, warps):
+    inst = I.tsp_uniform(24, 23)
+    p = params_for(inst, P=P, C=48, G=21, U=7, elite_period=14)
+    _, g, o = run_both(cgo, inst, p, 8, warps=warps)
+    assert_same_state(g, o, "P=%d warps=%d" % (P, warps))
+
+
+@pytest.mark.parametrize("staging", [1, 2])
+def test_tsp_staging_modes(cgo, staging):
+    inst = I.tsp_uniform(60, 24)
+    p = params_for(inst, P=8, C=64, G=40)
+    _, g, o = run_both(cgo, inst, p, 2, staging=staging)
+    assert_same_state(g, o, "staging %d" % staging)
+
+
+def test_tsp_wide_distances_int32_triangle(cgo):
+    inst = I.tsp_uniform(30, 25, box=100000)     # distances > 32767
+    assert inst["mat0"].max() > 32767
+    p = params_for(inst, P=8, C=64, G=40)
+    _, g, o = run_both(cgo, inst, p, 4)
+    assert_same_state(g, o, "int32 triangle")
+
+
+@pytest.mark.parametrize("T0", [0, 1 << 32, 1 << 60])
+def test_tsp_temperature_limits(cgo, T0):
+    inst = I.tsp_uniform(19, 26)
+    p = params_for(inst, P=6, C=32, G=30, T0=T0)
+    _, g, o = run_both(cgo, inst, p, 6)
+    assert_same_state(g, o, "T0=%d" % T0)
+
+
+def test_tsp_stagnation_and_injection(cgo):
+    inst = I.tsp_uniform(3, 27)                  # the elite never improves
+    p = params_for(inst, P=5, C=8, G=70, U=5, stag_limit=2, elite_period=10)
+    _, g, o = run_both(cgo, inst, p, 1)
+    assert_same_state(g, o, "stagnation")
+    inst = I.tsp_uniform(40, 28)
+    p = params_for(inst, P=12, C=32, G=60, U=4, elite_period=8, stag_limit=1)
+    _, g, o = run_both(cgo, inst, p, 7, warps=4)
+    assert_same_state(g, o, "injection")
+
+
+def test_tsp442_clustered_prefix(cgo):
+    """The large single solve (n=442 clustered, P=128, 2-opt/or-opt/insertion
+    with the 'Large' or-opt prior), launched as the benchmark launches it,
+    compared over the first 60 generations."""
+    inst = I.tsp_clustered(442, 0)
+    p = params_for(inst, P=128, C=128, G=60, op_mask=(1 << TO) | (1 << OR) | (1 << INS))
+    _, g, o = run_both(cgo, inst, p, 1)
+    assert_same_state(g, o, "tsp442")
+
+
+# --------------------------------------------------------------------- QAP
+@pytest.mark.parametrize("n", [3, 5, 9, 20])
+def test_qap_asymmetric_diagonal(cgo, n):
+    inst = I.qap_random(n, 30 + n)
+    p = params_for(inst, P=6, C=40, G=25, U=5, ops=[SW])
+    _, g, o = run_both(cgo, inst, p, 11)
+    assert_same_state(g, o, "qap n=%d" % n)
+
+
+def test_qap64_grid_prefix(cgo):
+    inst = I.qap_grid(64, 0)
+    p = params_for(inst, P=256, C=128, G=8, ops=[SW])
+    _, g, o = run_both(cgo, inst, p, 1)
+    assert_same_state(g, o, "qap64")
+
+
+def test_qap_rejects_other_operators(cgo):
+    inst = I.qap_random(6, 39)
+    prob = cgo.Problem(inst)
+    with pytest.raises(cgo.CgoError) as e:
+        prob.solve(params_for(inst, P=2, C=8, G=1, ops=[SW, TO]), 1)
+    assert e.value.status == cgo.ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------- knapsack
+@pytest.mark.parametrize("n,kw", [(2, None), (3, (0, 0, 65536)), (50, None), (200, (0, 65536, 0))])
+def test_knapsack(cgo, n, kw):
+    inst = I.knapsack(n, 40 + n)
+    over = dict(P=7, C=70, G=33, U=6)
+    if kw:
+        over["w_k"] = list(kw)
+    p = params_for(inst, **over)
+    _, g, o = run_both(cgo, inst, p, 12)
+    assert_same_state(g, o, "knapsack n=%d" % n)
+
+
+def test_knapsack2000_prefix(cgo):
+    inst = I.knapsack(2000, 49)
+    p = params_for(inst, P=32, C=128, G=20)
+    _, g, o = run_both(cgo, inst, p, 3)
+    assert_same_state(g, o, "knapsack2000")
+
+
+# --------------------------------------------------------------------- GAP
+@pytest.mark.parametrize("n,m,kw", [(2, 2, None), (30, 5, (0, 0, 65536)), (80, 10, None)])
+def test_gap(cgo, n, m, kw):
+    inst = I.gap(n, 50 + n, m=m)
+    over = dict(P=6, C=64, G=31, U=5, elite_period=10)
+    if kw:
+        over["w_k"] = list(kw)
+    p = params_for(inst, **over)
+    _, g, o = run_both(cgo, inst, p, 13)
+    assert_same_state(g, o, "gap n=%d m=%d" % (n, m))
+
+
+def test_gap300_prefix(cgo):
+    inst = I.gap(300, 59, m=10)
+    p = params_for(inst, P=32, C=128, G=20)
+    _, g, o = run_both(cgo, inst, p, 3)
+    assert_same_state(g, o, "gap300")
+
+
+# ----------------------------------------------------- state and resume
+@pytest.mark.parametrize("maker", [lambda: I.tsp_uniform(25, 60), lambda: I.knapsack(60, 61),
+                                   lambda: I.gap(40, 62, m=6), lambda: I.qap_random(8, 63)])
+def test_split_solve_and_checkpoint_resume(cgo, maker):
+    inst = maker()
+    ops = [SW] if inst["model"] == 1 else None
+    p = params_for(inst, P=9, C=40, G=13, U=4, elite_period=8, **({"ops": ops} if ops else {}))
+    prob = cgo.Problem(inst)
+    prob.solve(p, 21)
+    prob.solve_continue(6)
+    prob.solve_continue(15)
+    g = prob.state()
+    o = oracle_run(inst, p, 21, 34)
+    assert_same_state(g, o, "split")
+    # checkpoint at g=34, resume on a fresh handle
+    prob2 = cgo.Problem(inst)
+    prob2.set_state(p, 21, g)
+    prob2.solve_continue(9)
+    prob.solve_continue(9)
+    assert_same_state(prob2.state(), prob.state(), "resume")
+    assert_same_state(prob.state(), oracle_run(inst, p, 21, 43), "resume vs oracle")
+
+
+def test_best_is_the_elite(cgo):
+    inst = I.tsp_uniform(35, 64)
+    p = params_for(inst, P=10, C=64, G=50)
+    prob = cgo.Problem(inst)
+    prob.solve(p, 5)
+    sol, cost = prob.best()
+    st = prob.state()
+    e = int(np.argmin(st["best_cost"]))
+    assert cost == st["best_cost"][e]
+    assert (sol == st["best_sol"][e]).all()
+    assert O.cost(inst, sol) == cost and O.valid(inst, sol)
+
+
+def test_params_default_matches_oracle(cgo):
+    for inst in (I.tsp_uniform(50, 1), I.tsp_uniform(200, 2), I.tsp_clustered(442, 0),
+                 I.knapsack(30, 3), I.gap(20, 4, m=4), I.qap_random(6, 5)):
+        prob = cgo.Problem(inst)
+        d = prob.default_params()
+        o = O.default_params(inst)
+        for k in o:
+            if k == "op_mask":
+                assert d[k] == o[k] & {0: 0xF, 1: 0xF, 2: 0x10, 3: 0x20}[inst["model"]]
+            else:
+                assert d[k] == o[k], k
+
+
+def test_device_pointer_instance(cgo):
+    torch = pytest.importorskip("torch")
+    inst = I.tsp_uniform(26, 65)
+    dev = dict(inst, mat0=torch.from_numpy(inst["mat0"]).cuda())
+    prob = cgo.Problem(dev, on_device=True)
+    p = params_for(inst, P=4, C=32, G=20)
+    prob.solve(p, 3)
+    assert_same_state(prob.state(), oracle_run(inst, p, 3, 20), "device pointers")
+
+
+def test_barrier_timeout_is_reported(cgo):
+    """A member barrier that cannot complete (phantom members) ends with
+    CGO_ERR_TIMEOUT after the bounded wait; the handle recovers."""
+    inst = I.tsp_uniform(20, 66)
+    p = params_for(inst, P=4, C=32, G=20, U=5)
+    prob = cgo.Problem(inst)
+    prob.inject(2, 200)            # 200 ms wait limit
+    prob.inject(1, 3)              # 3 members that never arrive
+    with pytest.raises(cgo.CgoError) as e:
+        prob.solve(p, 1)
+    assert e.value.status == cgo.ERR_TIMEOUT
+    with pytest.raises(cgo.CgoError) as e:
+        prob.state()
+    assert e.value.status == cgo.ERR_STATE
+    prob.inject(1, 0)
+    prob.solve(p, 1)
+    assert_same_state(prob.state(), oracle_run(inst, p, 1, 20), "after timeout")
+
+
+def test_invalid_inputs(cgo):
+    inst = I.tsp_uniform(10, 67)
+    prob = cgo.Problem(inst)
+    bad = [dict(P=0), dict(C=0), dict(C=5000), dict(U=0), dict(w_floor=3), dict(op_mask=0x10),
+           dict(alpha=(1 << 32) + 1), dict(w_cap=2000)]
+    for b in bad:
+        with pytest.raises(cgo.CgoError) as e:
+            prob.solve(params_for(inst, **dict(dict(P=4, C=8, G=1), **b)), 1)
+        assert e.value.status == cgo.ERR_INVALID, b
+    with pytest.raises(cgo.CgoError) as e:
+        prob.solve(params_for(inst, P=4, C=8, G=1, U=4, elite_period=6), 1)
+    assert e.value.status == cgo.ERR_UNSUPPORTED
+    asym = dict(inst, mat0=inst["mat0"] + np.triu(np.ones_like(inst["mat0"]), 1))
+    with pytest.raises(cgo.CgoError) as e:
+        cgo.Problem(asym)
+    assert e.value.status == cgo.ERR_UNSUPPORTED
+    with pytest.raises(cgo.CgoError) as e:
+        prob.best()
+    assert e.value.status == cgo.ERR_STATE
