@@ -177,9 +177,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tsp442")
-    ap.add_argument("--ref-generations", type=int, default=12)
+    ap.add_argument("--ref-generations", type=int, default=100)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--generations", type=int, default=0,
+                    help="override G (small cases for profiler captures)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -203,6 +205,9 @@ def main():
             dist.barrier()
 
     inst, cfg, desc = workload(args.workload)
+    if args.generations > 0:
+        cfg["G"] = args.generations
+        desc = desc.replace("G=", "G(full)=") + " G=%d" % cfg["G"]
     inst = dict(inst, tag=0)
     seed = 1 + rank
     stream = torch.cuda.Stream()

@@ -135,10 +135,13 @@ typedef struct {
   int64_t *best_cost;          /* [P] best costs */
 } cgo_state;
 
-/* Launch shape (the autotuner's choice, or a caller override). */
+/* Launch shape (the autotuner's choice, or a caller override).  The C
+ * candidates of a member are split over warps_per_member warps; a CTA holds
+ * warps_per_cta / warps_per_member members. */
 typedef struct {
   uint32_t struct_size;        /* = sizeof(cgo_launch) */
-  int32_t warps_per_cta;       /* 0 = autotune; else 1 .. 32 (one solution per warp) */
+  int32_t warps_per_cta;       /* 0 = auto; else 1 .. 8, a multiple of warps_per_member */
+  int32_t warps_per_member;    /* 0 = auto; else 1, 2 or 4 */
   int32_t staging;             /* 0 = auto, 1 = instance data in shared memory,
                                   2 = instance data read through L2 */
 } cgo_launch;

@@ -74,8 +74,8 @@ struct cgo_problem {
   int aos_cur = 0;
   int64_t g = 0;
   // launch shape
-  int warps_override = 0, staging_override = 0;
-  int last_warps = 0, last_staging = 0;
+  int warps_override = 0, wpm_override = 0, staging_override = 0;
+  int last_warps = 0, last_wpm = 0, last_staging = 0;
   // events around the last evolve launch (kernel time on the launching stream)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
@@ -278,49 +278,48 @@ KInst base_kinst(const cgo_problem *p) {
   return h;
 }
 
-// launch shape: warps per CTA (one member per warp) and staging mode
-cgo_status choose_launch(cgo_problem *p, KInst &h, int *warps_out, int64_t *smem_out) {
+// Launch shape: warps per member (candidates split across them), members
+// per CTA and staging mode.  Prefers one member per CTA (most SMs, least
+// shared-memory pressure) and grows the CTA only when the population would
+// not be co-resident otherwise.
+cgo_status choose_launch(cgo_problem *p, KInst &h, int *warps_out, int *wpm_out,
+                         int64_t *smem_out) {
   const int64_t optin = max_smem_optin();
-  const int P = h.P;
-  int warps = p->warps_override > 0 ? p->warps_override : 4;
-  if (warps > kMaxWarps) warps = kMaxWarps;
-  if (warps > P) warps = P;
-  int staging = p->staging_override;
-  for (;;) {
-    const int64_t staged = evolve_smem_bytes(h, warps, true);
-    const int64_t global = evolve_smem_bytes(h, warps, false);
-    bool use_smem;
-    if (staging == STAGE_SMEM) use_smem = staged <= optin;
-    else if (staging == STAGE_GLOBAL) use_smem = false;
-    else use_smem = staged <= optin;
+  const int P = h.P, C = h.C;
+  int wpm = p->wpm_override;
+  if (wpm == 0) wpm = C >= 128 ? 4 : (C >= 64 ? 2 : 1);
+  int fit_seen = 0, grid_seen = 0;
+  for (int mpc = 1; mpc * wpm <= kMaxWarps; mpc *= 2) {
+    const int warps = mpc * wpm;
+    if (p->warps_override > 0 && warps != p->warps_override) continue;
+    const int64_t staged = evolve_smem_bytes(h, warps, wpm, true);
+    const int64_t global = evolve_smem_bytes(h, warps, wpm, false);
+    bool use_smem = staged <= optin;
+    if (p->staging_override == STAGE_GLOBAL) use_smem = false;
+    if (p->staging_override == STAGE_SMEM && !use_smem) continue;
     const int64_t need = use_smem ? staged : global;
-    if (need <= optin) {
-      h.shared_bytes = use_smem ? instance_data_bytes(h) : 0;
-      const int grid = (P + warps - 1) / warps;
-      const int fit = max_coresident_ctas(h, warps, need);
-      if (fit >= grid) {
-        *warps_out = warps;
-        *smem_out = need;
-        p->last_warps = warps;
-        p->last_staging = use_smem ? STAGE_SMEM : STAGE_GLOBAL;
-        return CGO_OK;
-      }
-      if (warps < kMaxWarps && warps < P && p->warps_override == 0) {
-        warps *= 2;
-        if (warps > kMaxWarps) warps = kMaxWarps;
-        continue;
-      }
-      return fail(CGO_ERR_UNSUPPORTED,
-                  "population %d needs %d co-resident CTAs of %d warps; the GPU holds %d", P, grid,
-                  warps, fit);
+    if (need > optin) continue;
+    h.shared_bytes = use_smem ? instance_data_bytes(h) : 0;
+    const int grid = (P + mpc - 1) / mpc;
+    const int fit = max_coresident_ctas(h, warps, wpm, need);
+    fit_seen = fit;
+    grid_seen = grid;
+    if (fit >= grid) {
+      *warps_out = warps;
+      *wpm_out = wpm;
+      *smem_out = need;
+      p->last_warps = warps;
+      p->last_wpm = wpm;
+      p->last_staging = use_smem ? STAGE_SMEM : STAGE_GLOBAL;
+      return CGO_OK;
     }
-    if (warps > 1 && p->warps_override == 0) {
-      warps /= 2;
-      continue;
-    }
-    return fail(CGO_ERR_UNSUPPORTED, "solution length %d needs more shared memory than a CTA has",
-                p->len);
   }
+  if (grid_seen)
+    return fail(CGO_ERR_UNSUPPORTED, "population %d needs %d co-resident CTAs; the GPU holds %d", P,
+                grid_seen, fit_seen);
+  return fail(CGO_ERR_UNSUPPORTED,
+              "no launch shape fits (solution length %d, requested warps %d, staging %d)", p->len,
+              p->warps_override, p->staging_override);
 }
 
 cgo_status check_sync_error(cgo_problem *p, cudaStream_t st) {
@@ -338,9 +337,9 @@ cgo_status run_generations(cgo_problem *p, int64_t G, cudaStream_t st) {
   if (G == 0) return CGO_OK;
   if (p->g + G >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "generation index would exceed 2^32 - 2");
   KInst h = base_kinst(p);
-  int warps = 0;
+  int warps = 0, wpm = 1;
   int64_t smem = 0;
-  cgo_status s = choose_launch(p, h, &warps, &smem);
+  cgo_status s = choose_launch(p, h, &warps, &wpm, &smem);
   if (s != CGO_OK) return s;
   h.members = p->params.population + (int)p->phantom_members;  // test hook adds phantoms
   h.g_begin = p->g;
@@ -354,7 +353,7 @@ cgo_status run_generations(cgo_problem *p, int64_t G, cudaStream_t st) {
     CUDA_TRY(cudaEventCreate(&p->ev1), "event");
   }
   CUDA_TRY(cudaEventRecord(p->ev0, st), "event");
-  CUDA_TRY(launch_evolve_single(h, warps, smem, p->timeout_ns, st), "evolve launch");
+  CUDA_TRY(launch_evolve_single(h, warps, wpm, smem, p->timeout_ns, st), "evolve launch");
   CUDA_TRY(cudaEventRecord(p->ev1, st), "event");
   p->timed = true;
   p->timed_gens = G;
@@ -530,8 +529,14 @@ cgo_status cgo_set_launch(cgo_problem *p, const cgo_launch *l) {
   if (!p || !l || l->struct_size != sizeof(cgo_launch)) return fail(CGO_ERR_INVALID, "bad launch struct");
   if (l->warps_per_cta < 0 || l->warps_per_cta > kMaxWarps)
     return fail(CGO_ERR_INVALID, "warps_per_cta must be in [0, %d]", kMaxWarps);
+  if (l->warps_per_member != 0 && l->warps_per_member != 1 && l->warps_per_member != 2 &&
+      l->warps_per_member != 4)
+    return fail(CGO_ERR_INVALID, "warps_per_member must be 0, 1, 2 or 4");
+  if (l->warps_per_cta > 0 && l->warps_per_member > 0 && l->warps_per_cta % l->warps_per_member)
+    return fail(CGO_ERR_INVALID, "warps_per_cta must be a multiple of warps_per_member");
   if (l->staging < 0 || l->staging > 2) return fail(CGO_ERR_INVALID, "staging must be 0, 1 or 2");
   p->warps_override = l->warps_per_cta;
+  p->wpm_override = l->warps_per_member;
   p->staging_override = l->staging;
   return CGO_OK;
 }
@@ -540,6 +545,7 @@ cgo_status cgo_get_launch(const cgo_problem *p, cgo_launch *l) {
   if (!p || !l) return fail(CGO_ERR_INVALID, "NULL argument");
   l->struct_size = sizeof(cgo_launch);
   l->warps_per_cta = p->last_warps;
+  l->warps_per_member = p->last_wpm;
   l->staging = p->last_staging;
   return CGO_OK;
 }

@@ -24,22 +24,26 @@ struct SolScal {
 };
 
 struct Layout {
-  int64_t inst, sol_off, sol_stride, scr_off, scal_off, load_off, total;
+  int64_t inst, sol_off, sol_stride, scr_off, scal_off, load_off, part_off, total;
 };
 
 __host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64_t(15); }
 
+// Shared memory of one CTA: [instance data][members' solutions][one scratch
+// array per member group][member scalars][GAP loads][per-group partials]
 __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m, int nsol,
-                                              int warps, int model) {
+                                              int warps, int wpm, int model) {
   Layout L;
+  const int groups = warps / wpm;
   L.inst = align16(inst_bytes);
   L.sol_stride = align16((int64_t)len * 4);
   L.sol_off = L.inst;
   L.scr_off = L.sol_off + (int64_t)nsol * L.sol_stride;
   const bool perm = (model == TSP || model == QAP || model == CVRPTW);
-  L.scal_off = L.scr_off + (perm ? (int64_t)warps * L.sol_stride : 0);
-  L.load_off = L.scal_off + align16((int64_t)nsol * (int64_t)sizeof(SolScal));
-  L.total = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
+  L.scal_off = L.scr_off + (perm ? (int64_t)groups * L.sol_stride : 0);
+  L.load_off = L.scal_off + align16((int64_t)nsol * 32);
+  L.part_off = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
+  L.total = L.part_off + (int64_t)groups * (2 * wpm * 16 + 16);
   return L;
 }
 
@@ -55,7 +59,7 @@ int64_t instance_data_bytes(const KInst &h) {
 
 int64_t smem_instance(const KInst &h) { return instance_data_bytes(h); }
 int64_t smem_per_warp(const KInst &h) {
-  Layout a = make_layout(0, h.len, h.m, 1, 1, h.model);
+  Layout a = make_layout(0, h.len, h.m, 1, 1, 1, h.model);
   return a.total;
 }
 
@@ -141,12 +145,11 @@ __device__ __forceinline__ long long tsp_d(const View &X, int x, int y) {
   return ((const int32_t *)X.tri)[idx];
 }
 
-// element at position q of the array after the prior moves (most recent last)
-template <int NP>
-__device__ __forceinline__ int vlook(const int32_t *sol, int q, const PMove &p0,
-                                     const PMove &p1) {
-  if (NP >= 2) q = perm_inv(p1, q);
-  if (NP >= 1) q = perm_inv(p0, q);
+// element at position q of the array after the np prior moves (p0 first)
+__device__ __forceinline__ int vlook(const int32_t *sol, int q, const PMove &p0, const PMove &p1,
+                                     int np) {
+  if (np >= 2) q = perm_inv(p1, q);
+  if (np >= 1) q = perm_inv(p0, q);
   return sol[q];
 }
 
@@ -155,9 +158,9 @@ __device__ __forceinline__ int vlook(const int32_t *sol, int q, const PMove &p0,
 // edges (reversal does not change them when D is symmetric), so the delta is
 // the sum of the new junction edges minus the old ones.  When P0 and P4 are
 // both non-empty the closing edge P4 -> P0 is common to both and skipped.
-template <bool T16, int NP>
+template <bool T16>
 __device__ long long tsp_step(const View &X, const int32_t *sol, const PMove &mv,
-                              const PMove &p0, const PMove &p1) {
+                              const PMove &p0, const PMove &p1, int np) {
   const int m = X.len;
   const int s[6] = {0, mv.b1, mv.b2, mv.b3, mv.b4, m};
   int f[5], l[5];
@@ -166,8 +169,8 @@ __device__ long long tsp_step(const View &X, const int32_t *sol, const PMove &mv
   for (int t = 0; t < 5; ++t) {
     ne[t] = s[t + 1] > s[t];
     const int qf = min(s[t], m - 1), ql = max(s[t + 1] - 1, 0);
-    f[t] = vlook<NP>(sol, qf, p0, p1);
-    l[t] = (s[t + 1] - s[t] == 1) ? f[t] : vlook<NP>(sol, ql, p0, p1);
+    f[t] = vlook(sol, qf, p0, p1, np);
+    l[t] = (s[t + 1] - s[t] == 1) ? f[t] : vlook(sol, ql, p0, p1, np);
   }
   const bool skip = ne[0] && ne[4];
   long long so = 0, sn = 0;
@@ -209,18 +212,17 @@ __device__ long long tsp_step(const View &X, const int32_t *sol, const PMove &mv
 // Swap of positions r, s on the (virtual) permutation pi: O(n) delta of
 // sum_ij F[i][j] D[pi_i][pi_j] for general (asymmetric, non-zero diagonal)
 // F and D.
-template <int NP>
 __device__ long long qap_step(const View &X, const int32_t *sol, const PMove &mv,
-                              const PMove &p0, const PMove &p1) {
+                              const PMove &p0, const PMove &p1, int np) {
   const int n = X.n;
   const int r = mv.b1, s = mv.b3;
-  const int pr = vlook<NP>(sol, r, p0, p1), ps = vlook<NP>(sol, s, p0, p1);
+  const int pr = vlook(sol, r, p0, p1, np), ps = vlook(sol, s, p0, p1, np);
   const int32_t *F = X.F, *D = X.D;
   const int32_t *Fr = F + (size_t)r * n, *Fs = F + (size_t)s * n;
   const int32_t *Dr = D + (size_t)pr * n, *Ds = D + (size_t)ps * n;
   long long acc = 0;
   for (int k = 0; k < n; ++k) {
-    const int pk = vlook<NP>(sol, k, p0, p1);
+    const int pk = vlook(sol, k, p0, p1, np);
     const long long t1 = ((long long)Fr[k] - Fs[k]) * ((long long)Ds[pk] - Dr[pk]);
     const int32_t *Fk = F + (size_t)k * n, *Dk = D + (size_t)pk * n;
     const long long t2 = ((long long)Fk[r] - Fk[s]) * ((long long)Dk[ps] - Dk[pr]);
@@ -235,15 +237,8 @@ __device__ long long qap_step(const View &X, const int32_t *sol, const PMove &mv
 template <int MODEL, bool T16>
 __device__ __forceinline__ long long perm_delta(const View &X, const int32_t *sol, const PMove &mv,
                                                 const PMove &p0, const PMove &p1, int np) {
-  if (MODEL == TSP) {
-    if (np == 0) return tsp_step<T16, 0>(X, sol, mv, p0, p1);
-    if (np == 1) return tsp_step<T16, 1>(X, sol, mv, p0, p1);
-    return tsp_step<T16, 2>(X, sol, mv, p0, p1);
-  } else {
-    if (np == 0) return qap_step<0>(X, sol, mv, p0, p1);
-    if (np == 1) return qap_step<1>(X, sol, mv, p0, p1);
-    return qap_step<2>(X, sol, mv, p0, p1);
-  }
+  if constexpr (MODEL == TSP) return tsp_step<T16>(X, sol, mv, p0, p1, np);
+  else return qap_step(X, sol, mv, p0, p1, np);
 }
 
 template <int MODEL, bool T16>
@@ -251,20 +246,23 @@ __device__ long long candidate_perm(const View &X, const int32_t *sol, const Wei
                                     uint32_t c, uint32_t p, uint32_t g, Stats<4> &st) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
   const int k = 1 + wsample(W.k, W.Wk, R0.w);
-  const int op0 = wsample(W.op, W.Wop, R0.x);
-  const PMove m0 = perm_decode(op0, R0.y, R0.z, X.len);
-  long long d = perm_delta<MODEL, T16>(X, sol, m0, m0, m0, 0);
-  int op1 = -1, op2 = -1;
-  if (k >= 2) {
-    const uint4 R1 = philox(ctr_word(c, 1, kKindMove), X.tag, p, g, X.k0, X.k1);
-    op1 = wsample(W.op, W.Wop, R1.x);
-    const PMove m1 = perm_decode(op1, R1.y, R1.z, X.len);
-    d += perm_delta<MODEL, T16>(X, sol, m1, m0, m0, 1);
-    if (k >= 3) {
-      const uint4 R2 = philox(ctr_word(c, 2, kKindMove), X.tag, p, g, X.k0, X.k1);
-      op2 = wsample(W.op, W.Wop, R2.x);
-      const PMove m2 = perm_decode(op2, R2.y, R2.z, X.len);
-      d += perm_delta<MODEL, T16>(X, sol, m2, m0, m1, 2);
+  PMove pm0 = {0, 0, 0, 0, 0}, pm1 = {0, 0, 0, 0, 0};
+  int op0 = -1, op1 = -1, op2 = -1;
+  long long d = 0;
+#pragma unroll 1
+  for (int t = 0; t < k; ++t) {
+    const uint4 R = t == 0 ? R0 : philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
+    const int op = wsample(W.op, W.Wop, R.x);
+    const PMove mv = perm_decode(op, R.y, R.z, X.len);
+    d += perm_delta<MODEL, T16>(X, sol, mv, pm0, pm1, t);
+    if (t == 0) {
+      pm0 = mv;
+      op0 = op;
+    } else if (t == 1) {
+      pm1 = mv;
+      op1 = op;
+    } else {
+      op2 = op;
     }
   }
   const uint32_t imp = d < 0;
@@ -355,24 +353,36 @@ __device__ long long candidate_gap(const View &X, const int32_t *x, const long l
   return d;
 }
 
+// ------------------------------------------------------------ member group
+// WPM warps evolve one member together: each evaluates its share of the C
+// candidates, partial argmins meet in shared memory behind a named barrier,
+// and the winner is applied by the whole group.
+struct Group {
+  int wpm, gw, grp, tig, nthr;  // warps per member, warp in group, group, thread in group
+  __device__ __forceinline__ void sync() const {
+    if (wpm == 1) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(nthr) : "memory");
+  }
+};
+
 // --------------------------------------------------------------- apply
-// Materialise one permutation move in place (warp-cooperative): positions
+// Materialise one permutation move in place (group-cooperative): positions
 // that change are gathered through the inverse map into the scratch array,
 // then written back.  Only A and B move when they have equal lengths.
-__device__ void perm_materialise(int32_t *sol, int32_t *scr, const PMove &mv, int lane) {
+__device__ void perm_materialise(int32_t *sol, int32_t *scr, const PMove &mv, const Group &G) {
   const int la = mv.b2 - mv.b1, lb = mv.b4 - mv.b3;
   const bool ends = !mv.rev && la == lb;
   const int cnt = ends ? 2 * la : mv.b4 - mv.b1;
-  for (int e = lane; e < cnt; e += 32) {
+  for (int e = G.tig; e < cnt; e += G.nthr) {
     const int q = ends ? (e < la ? mv.b1 + e : mv.b3 + (e - la)) : mv.b1 + e;
     scr[q] = sol[perm_inv(mv, q)];
   }
-  __syncwarp();
-  for (int e = lane; e < cnt; e += 32) {
+  G.sync();
+  for (int e = G.tig; e < cnt; e += G.nthr) {
     const int q = ends ? (e < la ? mv.b1 + e : mv.b3 + (e - la)) : mv.b1 + e;
     sol[q] = scr[q];
   }
-  __syncwarp();
+  G.sync();
 }
 
 template <int NO>
@@ -383,35 +393,35 @@ __device__ __forceinline__ int regen_k(const View &X, const Weights<NO> &W, uint
 }
 
 __device__ void apply_perm(const View &X, int32_t *sol, int32_t *scr, const Weights<4> &W,
-                           uint32_t c, uint32_t p, uint32_t g, int lane) {
+                           uint32_t c, uint32_t p, uint32_t g, const Group &G) {
   uint4 R0;
   const int k = regen_k(X, W, c, p, g, R0);
   for (int t = 0; t < k; ++t) {
     const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
     const int op = wsample(W.op, W.Wop, R.x);
     const PMove mv = perm_decode(op, R.y, R.z, X.len);
-    perm_materialise(sol, scr, mv, lane);
+    perm_materialise(sol, scr, mv, G);
   }
 }
 
 __device__ void apply_knap(const View &X, int32_t *x, const Weights<1> &W, uint32_t c,
-                           uint32_t p, uint32_t g, int lane, long long &aw, long long &av) {
+                           uint32_t p, uint32_t g, const Group &G, long long &aw, long long &av) {
   uint4 R0;
   const int k = regen_k(X, W, c, p, g, R0);
   for (int t = 0; t < k; ++t) {
     const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
     const int i = posm(R.y >> 16, (uint32_t)X.n);
     const int xi = x[i];
-    __syncwarp();
-    if (lane == 0) x[i] = xi ^ 1;
+    G.sync();
+    if (G.tig == 0) x[i] = xi ^ 1;
     aw += xi ? -(long long)X.w[i] : (long long)X.w[i];
     av += xi ? -(long long)X.v[i] : (long long)X.v[i];
-    __syncwarp();
+    G.sync();
   }
 }
 
 __device__ void apply_gap(const View &X, int32_t *x, long long *loads, const Weights<1> &W,
-                          uint32_t c, uint32_t p, uint32_t g, int lane) {
+                          uint32_t c, uint32_t p, uint32_t g, const Group &G) {
   uint4 R0;
   const int k = regen_k(X, W, c, p, g, R0);
   for (int t = 0; t < k; ++t) {
@@ -420,51 +430,57 @@ __device__ void apply_gap(const View &X, int32_t *x, long long *loads, const Wei
     const int dd = 1 + posm(R.y & 0xFFFFu, (uint32_t)(X.m - 1));
     const int ao = x[j];
     const int an = (ao + dd) % X.m;
-    __syncwarp();
-    if (lane == 0) {
+    G.sync();
+    if (G.tig == 0) {
       x[j] = an;
       loads[ao] -= X.gr[(size_t)ao * X.n + j];
       loads[an] += X.gr[(size_t)an * X.n + j];
     }
-    __syncwarp();
+    G.sync();
   }
 }
 
-// warp-cooperative auxiliary sums of one member (knapsack W/V, GAP loads)
-__device__ void aux_init(int model, const View &X, const int32_t *x, SolScal &sc,
-                         long long *loads, int lane) {
-  if (model == KNAPSACK) {
-    long long W = 0, V = 0;
-    for (int i = lane; i < X.n; i += 32)
-      if (x[i]) {
-        W += X.w[i];
-        V += X.v[i];
+// auxiliary sums of one member (knapsack W/V, GAP loads), computed by the
+// group's first warp and left in shared memory
+__device__ void aux_init(int model, const View &X, const int32_t *x, SolScal *sc,
+                         long long *loads, const Group &G) {
+  const int lane = threadIdx.x & 31;
+  if (G.gw == 0) {
+    if (model == KNAPSACK) {
+      long long W = 0, V = 0;
+      for (int i = lane; i < X.n; i += 32)
+        if (x[i]) {
+          W += X.w[i];
+          V += X.v[i];
+        }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        W += __shfl_xor_sync(kFull, W, off);
+        V += __shfl_xor_sync(kFull, V, off);
       }
+      if (lane == 0) {
+        sc->aw = W;
+        sc->av = V;
+      }
+    } else if (model == GAP) {
+      for (int a = 0; a < X.m; ++a) {
+        long long L = 0;
+        for (int j = lane; j < X.n; j += 32)
+          if (x[j] == a) L += X.gr[(size_t)a * X.n + j];
 #pragma unroll
-    for (int off = 16; off; off >>= 1) {
-      W += __shfl_xor_sync(kFull, W, off);
-      V += __shfl_xor_sync(kFull, V, off);
+        for (int off = 16; off; off >>= 1) L += __shfl_xor_sync(kFull, L, off);
+        if (lane == 0) loads[a] = L;
+      }
     }
-    sc.aw = W;
-    sc.av = V;
-  } else if (model == GAP) {
-    for (int a = 0; a < X.m; ++a) {
-      long long L = 0;
-      for (int j = lane; j < X.n; j += 32)
-        if (x[j] == a) L += X.gr[(size_t)a * X.n + j];
-#pragma unroll
-      for (int off = 16; off; off >>= 1) L += __shfl_xor_sync(kFull, L, off);
-      if (lane == 0) loads[a] = L;
-    }
-    __syncwarp();
   }
+  G.sync();
 }
 
 // ------------------------------------------------------ window barrier
 // All members of the instance arrive (counting members), then wait until
-// the arrival count reaches P * (barrier index + 1).  The wait is bounded:
-// on timeout (or another warp's error) it raises the error flag and returns
-// false so the kernel can exit.
+// the arrival count reaches members * (barrier index + 1).  The wait is
+// bounded: on timeout (or another warp's error) it raises the error flag and
+// returns false so the kernel can exit.  Called by one warp per group.
 __device__ bool member_barrier(DevSync *S, uint32_t arrivals, uint32_t target, uint64_t timeout_ns,
                                int lane) {
   __threadfence();
@@ -484,7 +500,7 @@ __device__ bool member_barrier(DevSync *S, uint32_t arrivals, uint32_t target, u
         ok = 0;
         break;
       }
-      __nanosleep(64);
+      __nanosleep(32);
     }
   }
   ok = __shfl_sync(kFull, ok, 0);
@@ -492,34 +508,62 @@ __device__ bool member_barrier(DevSync *S, uint32_t arrivals, uint32_t target, u
   return ok != 0;
 }
 
+// group-wide barrier wait: the group's first warp waits, the group follows
+__device__ bool group_barrier(DevSync *S, uint32_t arrivals, uint32_t target, uint64_t timeout_ns,
+                              const Group &G, int *flag) {
+  __threadfence();
+  G.sync();
+  if (G.gw == 0) {
+    const bool ok = member_barrier(S, arrivals, target, timeout_ns, threadIdx.x & 31);
+    if ((threadIdx.x & 31) == 0) *flag = ok ? 1 : 0;
+  }
+  G.sync();
+  const int ok = *flag;
+  G.sync();
+  return ok != 0;
+}
+
+struct Partial {
+  long long d;
+  int c, pad;
+};
+
 // ---------------------------------------------------------- evolve unit
-template <int MODEL, bool T16>
+template <int MODEL, bool T16, int WPM>
 __device__ void evolve_members(const KInst &I, const View &X, unsigned char *smem, const Layout &Lo,
                                int p0, int nsol, int warps, uint64_t timeout_ns) {
   constexpr int NO = Enc<MODEL>::NO, BASE = Enc<MODEL>::BASE;
   constexpr bool PERM = (MODEL == TSP || MODEL == QAP);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int mine = nsol > wid ? (nsol - wid + warps - 1) / warps : 0;
+  Group G;
+  G.wpm = WPM;
+  G.gw = wid % WPM;
+  G.grp = wid / WPM;
+  G.nthr = WPM * 32;
+  G.tig = G.gw * 32 + lane;
+  const int ngroups = warps / WPM;
+  const int mine = nsol > G.grp ? (nsol - G.grp + ngroups - 1) / ngroups : 0;
   if (mine == 0) return;
   const int len = I.len, P = I.P, C = I.C;
   DevSync *S = I.sync;
-  int32_t *scr = (int32_t *)(smem + Lo.scr_off + (int64_t)wid * Lo.sol_stride);
+  int32_t *scr = (int32_t *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.sol_stride);
   SolScal *scal = (SolScal *)(smem + Lo.scal_off);
+  Partial *part = (Partial *)(smem + Lo.part_off) + (int64_t)G.grp * 2 * WPM;
+  int *flag = (int *)(part + 2 * WPM);
 
-  // load this warp's members
+  // load this group's members
   for (int e = 0; e < mine; ++e) {
-    const int ls = wid + e * warps, p = p0 + ls;
+    const int ls = G.grp + e * ngroups, p = p0 + ls;
     int32_t *sol = (int32_t *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
     const int32_t *src = I.cur + (int64_t)p * len;
-    for (int i = lane; i < len; i += 32) sol[i] = src[i];
-    __syncwarp();
-    SolScal sc;
-    sc.cost = I.cost[p];
-    sc.best = I.best[p];
-    sc.aw = sc.av = 0;
-    aux_init(MODEL, X, sol, sc, (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, lane);
-    if (lane == 0) scal[ls] = sc;
-    __syncwarp();
+    for (int i = G.tig; i < len; i += G.nthr) sol[i] = src[i];
+    if (G.tig == 0) {
+      scal[ls].cost = I.cost[p];
+      scal[ls].best = I.best[p];
+      scal[ls].aw = scal[ls].av = 0;
+    }
+    G.sync();
+    aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
   }
 
   // instance-wide scalars (identical in every warp)
@@ -542,10 +586,11 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   uint32_t pend = lane < kStats ? A->pend[lane] : 0u;
   bool pend_used = false;
   uint32_t prev_acc[2] = {0u, 0u};
-  uint32_t nb = 0, wi = 0;
+  uint32_t nb = 0, wi = 0, gpar = 0;
   Stats<NO> st;
   stats_zero(st);
-  const int cpl = (C + 31) >> 5;
+  const int span = WPM * 32;
+  const int cpl = (C + span - 1) / span;
 
   int64_t g = I.g_begin;
   while (g < I.g_end) {
@@ -553,7 +598,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     const uint64_t Tw = T;
     long long minbest = LLONG_MAX;
     for (int e = 0; e < mine; ++e) {
-      const int ls = wid + e * warps;
+      const int ls = G.grp + e * ngroups;
       const uint32_t p = (uint32_t)(p0 + ls);
       int32_t *sol = (int32_t *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
       long long *loads = (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m;
@@ -573,38 +618,55 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
           long long bd = LLONG_MAX;
           int bc = INT_MAX;
           for (int slot = 0; slot < cpl; ++slot) {
-            const int c = slot * 32 + lane;
+            const int c = slot * span + G.gw * 32 + lane;
             if (c < C) {
               long long d;
               if constexpr (PERM) d = candidate_perm<MODEL, T16>(X, sol, W, c, p, gg, st);
               else if constexpr (MODEL == KNAPSACK)
                 d = candidate_knap(X, sol, W, sc.aw, sc.av, c, p, gg, st);
               else d = candidate_gap(X, sol, loads, W, c, p, gg, st);
-              if (d < bd) {
+              if (d < bd || (d == bd && c < bc)) {
                 bd = d;
                 bc = c;
               }
             }
           }
           warp_argmin(bd, bc);
+          if constexpr (WPM > 1) {
+            Partial *pp = part + gpar * WPM;
+            if (lane == 0) {
+              pp[G.gw].d = bd;
+              pp[G.gw].c = bc;
+            }
+            G.sync();
+#pragma unroll
+            for (int w = 0; w < WPM; ++w) {
+              const long long d2 = pp[w].d;
+              const int c2 = pp[w].c;
+              if (d2 < bd || (d2 == bd && c2 < bc)) {
+                bd = d2;
+                bc = c2;
+              }
+            }
+            gpar ^= 1u;
+          }
           if (accept_move(bd, T, E)) {
-            if constexpr (PERM) apply_perm(X, sol, scr, W, bc, p, gg, lane);
-            else if constexpr (MODEL == KNAPSACK)
-              apply_knap(X, sol, W, bc, p, gg, lane, sc.aw, sc.av);
-            else apply_gap(X, sol, loads, W, bc, p, gg, lane);
+            if constexpr (PERM) apply_perm(X, sol, scr, W, bc, p, gg, G);
+            else if constexpr (MODEL == KNAPSACK) apply_knap(X, sol, W, bc, p, gg, G, sc.aw, sc.av);
+            else apply_gap(X, sol, loads, W, bc, p, gg, G);
             sc.cost += bd;
             if (sc.cost < sc.best) {
               sc.best = sc.cost;
               int32_t *dst = I.bestsol + (int64_t)p * len;
-              for (int i = lane; i < len; i += 32) dst[i] = sol[i];
+              for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
             }
           }
           T = cool(T, I.alpha);
         }
       }
-      __syncwarp();
-      if (lane == 0) scal[ls] = sc;
-      __syncwarp();
+      G.sync();
+      if (G.tig == 0) scal[ls] = sc;
+      G.sync();
       minbest = min(minbest, sc.best);
     }
     g = wend;
@@ -636,15 +698,16 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     }
     const int slot = wi & 1;
     if (lane < kStats && my) atomicAdd(&S->acc[slot][lane], my);
-    if (lane == 0) atomicMin((long long *)&S->elite[slot], minbest);
-    if (inject && lane == 0) {
+    if (G.gw == 0 && lane == 0) atomicMin((long long *)&S->elite[slot], minbest);
+    if (inject && G.tig == 0) {
       for (int e = 0; e < mine; ++e) {
-        const int ls = wid + e * warps;
+        const int ls = G.grp + e * ngroups;
         I.cost[p0 + ls] = scal[ls].cost;
         I.best[p0 + ls] = scal[ls].best;
       }
     }
-    if (!member_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, lane)) return;
+    if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag))
+      return;
     ++nb;
     uint32_t cum = lane < kStats ? ld_relaxed(&S->acc[slot][lane]) : 0u;
     uint32_t total = cum - prev_acc[slot];
@@ -698,35 +761,36 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       warp_argmin(bb, be);
       warp_argmin(nwc, wq);
       const int lw = wq - p0;
-      if (lw >= 0 && lw < nsol && (lw % warps) == wid) {
+      if (lw >= 0 && lw < nsol && (lw % ngroups) == G.grp) {
         int32_t *sol = (int32_t *)(smem + Lo.sol_off + (int64_t)lw * Lo.sol_stride);
         const int32_t *src = I.bestsol + (int64_t)be * len;
-        for (int i = lane; i < len; i += 32) sol[i] = __ldcg(src + i);
-        __syncwarp();
+        for (int i = G.tig; i < len; i += G.nthr) sol[i] = __ldcg(src + i);
+        G.sync();
         SolScal sc = scal[lw];
         sc.cost = bb;
         if (bb < sc.best) {
           sc.best = bb;
           int32_t *dst = I.bestsol + (int64_t)wq * len;
-          for (int i = lane; i < len; i += 32) dst[i] = sol[i];
+          for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
         }
-        aux_init(MODEL, X, sol, sc, (long long *)(smem + Lo.load_off) + (int64_t)lw * X.m, lane);
-        __syncwarp();
-        if (lane == 0) scal[lw] = sc;
-        __syncwarp();
+        G.sync();
+        if (G.tig == 0) scal[lw] = sc;
+        G.sync();
+        aux_init(MODEL, X, sol, &scal[lw], (long long *)(smem + Lo.load_off) + (int64_t)lw * X.m, G);
       }
-      if (!member_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, lane)) return;
+      if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag))
+        return;
       ++nb;
     }
   }
 
   // ------------------------------------------------ write back
   for (int e = 0; e < mine; ++e) {
-    const int ls = wid + e * warps, p = p0 + ls;
+    const int ls = G.grp + e * ngroups, p = p0 + ls;
     const int32_t *sol = (const int32_t *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
     int32_t *dst = I.cur + (int64_t)p * len;
-    for (int i = lane; i < len; i += 32) dst[i] = sol[i];
-    if (lane == 0) {
+    for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
+    if (G.tig == 0) {
       I.cost[p] = scal[ls].cost;
       I.best[p] = scal[ls].best;
     }
@@ -746,10 +810,10 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       my = (lane == 16 + i) ? tu : my;
       my = (lane == 19 + i) ? tv : my;
     }
-    if (p0 + wid == 0 && !pend_used) my += pend;
+    if (p0 + G.grp == 0 && G.gw == 0 && !pend_used) my += pend;
     if (lane < kStats && my) atomicAdd(&S->pend_out[lane], my);
   }
-  if (p0 + wid == 0 && lane == 0) {
+  if (p0 + G.grp == 0 && G.tig == 0) {
     DevAos *O = I.aos_out;
     O->T = T;
     O->g = I.g_end;
@@ -819,20 +883,22 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   return X;
 }
 
-// One CTA per unit: unit u covers members [u * warps, (u+1) * warps) of
-// instance 0 (single solve, cooperative launch so that all members of the
-// instance are resident together).
-template <int MODEL, bool T16>
+// Single solve: CTA b covers members [b * groups, (b+1) * groups) of the
+// instance, one member per group of WPM warps (cooperative launch, so that
+// all members are resident together for the window barriers).
+template <int MODEL, bool T16, int WPM>
 __global__ void __launch_bounds__(kMaxWarps * 32)
     evolve_kernel(const __grid_constant__ KInst I, int warps, uint64_t timeout_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const bool staged = I.shared_bytes > 0;
   const View X = make_view(I, smem, staged);
   __syncthreads();
-  const int p0 = blockIdx.x * warps;
-  const int nsol = min(warps, I.P - p0);
-  const Layout Lo = make_layout(staged ? I.shared_bytes : 0, I.len, I.m, warps, warps, I.model);
-  evolve_members<MODEL, T16>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
+  const int groups = warps / WPM;
+  const int p0 = blockIdx.x * groups;
+  const int nsol = min(groups, I.P - p0);
+  const Layout Lo =
+      make_layout(staged ? I.shared_bytes : 0, I.len, I.m, groups, warps, WPM, I.model);
+  evolve_members<MODEL, T16, WPM>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
 }
 
 // ---------------------------------------------------------------- init
@@ -1003,16 +1069,18 @@ cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri, 
 }
 
 template <int MODEL, bool T16>
-static const void *evolve_fn() {
-  return (const void *)evolve_kernel<MODEL, T16>;
+static const void *evolve_fn(int wpm) {
+  if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4>;
+  if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2>;
+  return (const void *)evolve_kernel<MODEL, T16, 1>;
 }
 
-static const void *pick_evolve(const KInst &h) {
+static const void *pick_evolve(const KInst &h, int wpm) {
   switch (h.model) {
-    case TSP: return h.tri16 ? evolve_fn<TSP, true>() : evolve_fn<TSP, false>();
-    case QAP: return evolve_fn<QAP, false>();
-    case KNAPSACK: return evolve_fn<KNAPSACK, false>();
-    case GAP: return evolve_fn<GAP, false>();
+    case TSP: return h.tri16 ? evolve_fn<TSP, true>(wpm) : evolve_fn<TSP, false>(wpm);
+    case QAP: return evolve_fn<QAP, false>(wpm);
+    case KNAPSACK: return evolve_fn<KNAPSACK, false>(wpm);
+    case GAP: return evolve_fn<GAP, false>(wpm);
   }
   return nullptr;
 }
@@ -1024,8 +1092,8 @@ int64_t max_smem_optin() {
   return v;
 }
 
-int max_coresident_ctas(const KInst &h, int warps, int64_t smem_bytes) {
-  const void *fn = pick_evolve(h);
+int max_coresident_ctas(const KInst &h, int warps, int wpm, int64_t smem_bytes) {
+  const void *fn = pick_evolve(h, wpm);
   if (!fn) return 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
       cudaSuccess)
@@ -1039,25 +1107,24 @@ int max_coresident_ctas(const KInst &h, int warps, int64_t smem_bytes) {
   return per_sm * sms;
 }
 
-cudaError_t launch_evolve_single(const KInst &h, int warps, int64_t smem_bytes,
+cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int64_t smem_bytes,
                                  uint64_t timeout_ns, cudaStream_t st) {
-  const void *fn = pick_evolve(h);
+  const void *fn = pick_evolve(h, wpm);
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
-  const int grid = (h.P + warps - 1) / warps;
+  const int groups = warps / wpm;
+  const int grid = (h.P + groups - 1) / groups;
   KInst hi = h;
   void *args[] = {(void *)&hi, (void *)&warps, (void *)&timeout_ns};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(warps * 32), args, (size_t)smem_bytes, st);
 }
 
-}  // namespace cgo
-
-namespace cgo {
-int64_t evolve_smem_bytes(const KInst &h, int warps, bool staged) {
-  const Layout L =
-      make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, warps, warps, h.model);
+int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, bool staged) {
+  const Layout L = make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, warps / wpm, warps,
+                               wpm, h.model);
   return L.total;
 }
+
 }  // namespace cgo

@@ -29,9 +29,9 @@ def cgo():
     return C
 
 
-def run_both(C, inst, params, seed, warps=0, staging=0):
+def run_both(C, inst, params, seed, warps=0, staging=0, wpm=0):
     prob = C.Problem(inst)
-    prob.set_launch(warps, staging)
+    prob.set_launch(warps, staging, wpm)
     prob.solve(params, seed)
     g = prob.state()
     o = oracle_run(inst, params, seed, params["G"])
@@ -74,12 +74,26 @@ def test_tsp_candidate_counts(cgo, C):
     assert_same_state(g, o, "C=%d" % C)
 
 
-@pytest.mark.parametrize("P,warps", [(1, 0), (3, 1), (17, 2), (9, 4), (40, 8), (64, 0)])
-def test_tsp_population_and_launch_shape(cgo, P, warps):
+@pytest.mark.parametrize("P,warps,wpm", [(1, 0, 0), (3, 1, 1), (17, 2, 1), (9, 4, 2), (40, 8, 4),
+                                         (64, 0, 0), (33, 8, 2), (5, 4, 4)])
+def test_tsp_population_and_launch_shape(cgo, P, warps, wpm):
+    """Results do not depend on warps per member or members per CTA."""
     inst = I.tsp_uniform(24, 23)
-    p = params_for(inst, P=P, C=48, G=21, U=7, elite_period=14)
-    _, g, o = run_both(cgo, inst, p, 8, warps=warps)
-    assert_same_state(g, o, "P=%d warps=%d" % (P, warps))
+    p = params_for(inst, P=P, C=100, G=21, U=7, elite_period=14)
+    _, g, o = run_both(cgo, inst, p, 8, warps=warps, wpm=wpm)
+    assert_same_state(g, o, "P=%d warps=%d wpm=%d" % (P, warps, wpm))
+
+
+@pytest.mark.parametrize("wpm", [1, 2, 4])
+def test_every_model_every_group_width(cgo, wpm):
+    for inst, ops in ((I.tsp_uniform(31, 70), None), (I.qap_random(11, 71), [SW]),
+                      (I.knapsack(90, 72), None), (I.gap(45, 73, m=7), None)):
+        over = dict(P=6, C=150, G=26, U=5, elite_period=10)
+        if ops:
+            over["ops"] = ops
+        p = params_for(inst, **over)
+        _, g, o = run_both(cgo, inst, p, 4, wpm=wpm)
+        assert_same_state(g, o, "model %d wpm %d" % (inst["model"], wpm))
 
 
 @pytest.mark.parametrize("staging", [1, 2])
