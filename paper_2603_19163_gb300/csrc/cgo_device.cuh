@@ -183,17 +183,17 @@ __device__ __forceinline__ PMove perm_decode(int op, uint32_t r1, uint32_t r2, i
   return mv;
 }
 
-// Position in the array before the move of the element at position q after it.
+// Position in the array before the move of the element at position q after
+// it (branch-free).
 __device__ __forceinline__ int perm_inv(const PMove &mv, int q) {
-  if (q < mv.b1 || q >= mv.b4) return q;
-  if (mv.rev) return mv.b1 + mv.b2 - 1 - q;
-  int off = q - mv.b1;
-  const int lb = mv.b4 - mv.b3;
-  if (off < lb) return mv.b3 + off;
-  off -= lb;
-  const int lm = mv.b3 - mv.b2;
-  if (off < lm) return mv.b2 + off;
-  return mv.b1 + (off - lm);
+  const int off = q - mv.b1;
+  const int lb = mv.b4 - mv.b3, lm = mv.b3 - mv.b2;
+  const int r_b = mv.b3 + off;
+  const int r_m = mv.b2 + off - lb;
+  const int r_a = mv.b1 + off - lb - lm;
+  int r = off < lb ? r_b : (off < lb + lm ? r_m : r_a);
+  r = mv.rev ? mv.b1 + mv.b2 - 1 - q : r;
+  return (q < mv.b1 || q >= mv.b4) ? q : r;
 }
 
 }  // namespace cgo

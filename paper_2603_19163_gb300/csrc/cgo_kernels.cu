@@ -29,6 +29,10 @@ struct Layout {
 
 __host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64_t(15); }
 
+// per member group: 2*wpm partial argmins (16 B), a flag (16 B) and the
+// winner's moves (4 x 16 B)
+__host__ __device__ inline int64_t group_bytes(int wpm) { return 2 * wpm * 16 + 16 + 64; }
+
 // Shared memory of one CTA: [instance data][members' solutions][one scratch
 // array per member group][member scalars][GAP loads][per-group partials]
 __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m, int nsol,
@@ -43,7 +47,7 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   L.scal_off = L.scr_off + (perm ? (int64_t)groups * L.sol_stride : 0);
   L.load_off = L.scal_off + align16((int64_t)nsol * 32);
   L.part_off = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
-  L.total = L.part_off + (int64_t)groups * (2 * wpm * 16 + 16);
+  L.total = L.part_off + (int64_t)groups * group_bytes(wpm);
   return L;
 }
 
@@ -153,59 +157,47 @@ __device__ __forceinline__ int vlook(const int32_t *sol, int q, const PMove &p0,
   return sol[q];
 }
 
-// Symmetric-TSP delta of one move on the (virtual) array: the tour is a
-// cyclic concatenation of the non-empty pieces; pieces keep their internal
-// edges (reversal does not change them when D is symmetric), so the delta is
-// the sum of the new junction edges minus the old ones.  When P0 and P4 are
-// both non-empty the closing edge P4 -> P0 is common to both and skipped.
+// Symmetric-TSP delta of one move on the (virtual) array.  The cyclic tour
+// is R A M B (R = P4 P0 joined around the end) and becomes R B M A (or
+// R A^r for 2-opt).  Pieces keep their internal edges (D is symmetric), so
+// only junction edges change.  With r_l / r_f the elements just before A and
+// just after B in the cyclic tour:
+//   2-opt:      d(r_l,A_l) + d(A_f,r_f) - d(r_l,A_f) - d(A_l,r_f)
+//   exchange:   d(r_l,B_f) + d(A_l,r_f) - d(r_l,A_f) - d(B_l,r_f) + mid,
+//     M empty:  mid = d(B_l,A_f) - d(A_l,B_f)
+//     M:        mid = d(B_l,M_f) + d(M_l,A_f) - d(A_l,M_f) - d(M_l,B_f)
+// When R is empty (A starts the array and B ends it) the tour is A M B and
+// the delta is 0 except for an exchange with M non-empty:
+//   d(B_l,M_f) + d(M_l,A_f) + d(A_l,B_f) - d(A_l,M_f) - d(M_l,B_f) - d(B_l,A_f).
 template <bool T16>
-__device__ long long tsp_step(const View &X, const int32_t *sol, const PMove &mv,
-                              const PMove &p0, const PMove &p1, int np) {
+__device__ __forceinline__ long long tsp_step(const View &X, const int32_t *sol, const PMove &mv,
+                                              const PMove &p0, const PMove &p1, int np) {
   const int m = X.len;
-  const int s[6] = {0, mv.b1, mv.b2, mv.b3, mv.b4, m};
-  int f[5], l[5];
-  bool ne[5];
-#pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    ne[t] = s[t + 1] > s[t];
-    const int qf = min(s[t], m - 1), ql = max(s[t + 1] - 1, 0);
-    f[t] = vlook(sol, qf, p0, p1, np);
-    l[t] = (s[t + 1] - s[t] == 1) ? f[t] : vlook(sol, ql, p0, p1, np);
+  const int b1 = mv.b1, b2 = mv.b2, b3 = mv.b3, b4 = mv.b4;
+  const bool rev = mv.rev != 0;
+  const bool mn = b3 > b2;                      // M non-empty
+  const bool rempty = (b1 == 0) && (b4 == m);
+  const int rl = vlook(sol, b1 == 0 ? m - 1 : b1 - 1, p0, p1, np);
+  const int rf = vlook(sol, b4 == m ? 0 : b4, p0, p1, np);
+  const int af = vlook(sol, b1, p0, p1, np);
+  const int al = vlook(sol, b2 - 1, p0, p1, np);
+  const int bf = vlook(sol, min(b3, m - 1), p0, p1, np);
+  const int bl = vlook(sol, max(b4 - 1, 0), p0, p1, np);
+  const int mf = vlook(sol, min(b2, m - 1), p0, p1, np);
+  const int ml = vlook(sol, max(b3 - 1, 0), p0, p1, np);
+  // junction terms shared by the exchange and the 2-opt forms
+  const int x1 = rev ? al : bf, y2 = rev ? af : al, z4 = rev ? al : bl;
+  long long d = tsp_d<T16>(X, rl, x1) + tsp_d<T16>(X, y2, rf) - tsp_d<T16>(X, rl, af) -
+                tsp_d<T16>(X, z4, rf);
+  // middle terms of the exchange
+  const long long mid_n = tsp_d<T16>(X, bl, mn ? mf : af) + (mn ? tsp_d<T16>(X, ml, af) : 0ll);
+  const long long mid_o = tsp_d<T16>(X, al, mn ? mf : bf) + (mn ? tsp_d<T16>(X, ml, bf) : 0ll);
+  d += rev ? 0ll : mid_n - mid_o;
+  if (rempty) {
+    d = 0;
+    if (!rev && mn) d = mid_n - mid_o + tsp_d<T16>(X, al, bf) - tsp_d<T16>(X, bl, af);
   }
-  const bool skip = ne[0] && ne[4];
-  long long so = 0, sn = 0;
-  {
-    int first = 0, prev = 0;
-    bool any = false;
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-      if (ne[t]) {
-        if (any) so += tsp_d<T16>(X, prev, f[t]);
-        else first = f[t];
-        any = true;
-        prev = l[t];
-      }
-    }
-    if (!skip) so += tsp_d<T16>(X, prev, first);
-  }
-  {
-    const int nf[5] = {f[0], f[3], f[2], mv.rev ? l[1] : f[1], f[4]};
-    const int nl[5] = {l[0], l[3], l[2], mv.rev ? f[1] : l[1], l[4]};
-    const bool nn[5] = {ne[0], ne[3], ne[2], ne[1], ne[4]};
-    int first = 0, prev = 0;
-    bool any = false;
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-      if (nn[t]) {
-        if (any) sn += tsp_d<T16>(X, prev, nf[t]);
-        else first = nf[t];
-        any = true;
-        prev = nl[t];
-      }
-    }
-    if (!skip) sn += tsp_d<T16>(X, prev, first);
-  }
-  return sn - so;
+  return d;
 }
 
 // ---------------------------------------------------------------- QAP
@@ -241,34 +233,39 @@ __device__ __forceinline__ long long perm_delta(const View &X, const int32_t *so
   else return qap_step(X, sol, mv, p0, p1, np);
 }
 
+// The moves of one candidate, kept by the lane that may win the argmin so
+// that the group can apply it without redrawing.
+struct CandMoves {
+  PMove m[3];
+  int k;
+};
+
+// Candidate c: all three steps are drawn and decoded, and the delta of every
+// step is computed (each needs only the decoded earlier moves, not their
+// deltas), so the steps overlap; k selects how many count.
 template <int MODEL, bool T16>
-__device__ long long candidate_perm(const View &X, const int32_t *sol, const Weights<4> &W,
-                                    uint32_t c, uint32_t p, uint32_t g, Stats<4> &st) {
+__device__ __forceinline__ long long candidate_perm(const View &X, const int32_t *sol,
+                                                    const Weights<4> &W, uint32_t c, uint32_t p,
+                                                    uint32_t g, Stats<4> &st, CandMoves &cm) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+  const uint4 R1 = philox(ctr_word(c, 1, kKindMove), X.tag, p, g, X.k0, X.k1);
+  const uint4 R2 = philox(ctr_word(c, 2, kKindMove), X.tag, p, g, X.k0, X.k1);
   const int k = 1 + wsample(W.k, W.Wk, R0.w);
-  PMove pm0 = {0, 0, 0, 0, 0}, pm1 = {0, 0, 0, 0, 0};
-  int op0 = -1, op1 = -1, op2 = -1;
-  long long d = 0;
-#pragma unroll 1
-  for (int t = 0; t < k; ++t) {
-    const uint4 R = t == 0 ? R0 : philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
-    const int op = wsample(W.op, W.Wop, R.x);
-    const PMove mv = perm_decode(op, R.y, R.z, X.len);
-    d += perm_delta<MODEL, T16>(X, sol, mv, pm0, pm1, t);
-    if (t == 0) {
-      pm0 = mv;
-      op0 = op;
-    } else if (t == 1) {
-      pm1 = mv;
-      op1 = op;
-    } else {
-      op2 = op;
-    }
-  }
+  const int op0 = wsample(W.op, W.Wop, R0.x);
+  const int op1 = wsample(W.op, W.Wop, R1.x);
+  const int op2 = wsample(W.op, W.Wop, R2.x);
+  cm.m[0] = perm_decode(op0, R0.y, R0.z, X.len);
+  cm.m[1] = perm_decode(op1, R1.y, R1.z, X.len);
+  cm.m[2] = perm_decode(op2, R2.y, R2.z, X.len);
+  cm.k = k;
+  const long long d0 = perm_delta<MODEL, T16>(X, sol, cm.m[0], cm.m[0], cm.m[0], 0);
+  const long long d1 = perm_delta<MODEL, T16>(X, sol, cm.m[1], cm.m[0], cm.m[0], 1);
+  const long long d2 = perm_delta<MODEL, T16>(X, sol, cm.m[2], cm.m[0], cm.m[1], 2);
+  const long long d = d0 + (k >= 2 ? d1 : 0ll) + (k >= 3 ? d2 : 0ll);
   const uint32_t imp = d < 0;
   stats_op(st, op0, imp);
-  stats_op(st, op1, imp);
-  stats_op(st, op2, imp);
+  stats_op(st, k >= 2 ? op1 : -1, imp);
+  stats_op(st, k >= 3 ? op2 : -1, imp);
   stats_k(st, k, imp);
   return d;
 }
@@ -392,16 +389,8 @@ __device__ __forceinline__ int regen_k(const View &X, const Weights<NO> &W, uint
   return 1 + wsample(W.k, W.Wk, R0.w);
 }
 
-__device__ void apply_perm(const View &X, int32_t *sol, int32_t *scr, const Weights<4> &W,
-                           uint32_t c, uint32_t p, uint32_t g, const Group &G) {
-  uint4 R0;
-  const int k = regen_k(X, W, c, p, g, R0);
-  for (int t = 0; t < k; ++t) {
-    const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
-    const int op = wsample(W.op, W.Wop, R.x);
-    const PMove mv = perm_decode(op, R.y, R.z, X.len);
-    perm_materialise(sol, scr, mv, G);
-  }
+__device__ void apply_perm(int32_t *sol, int32_t *scr, const CandMoves &cm, const Group &G) {
+  for (int t = 0; t < cm.k; ++t) perm_materialise(sol, scr, cm.m[t], G);
 }
 
 __device__ void apply_knap(const View &X, int32_t *x, const Weights<1> &W, uint32_t c,
@@ -548,8 +537,10 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   DevSync *S = I.sync;
   int32_t *scr = (int32_t *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.sol_stride);
   SolScal *scal = (SolScal *)(smem + Lo.scal_off);
-  Partial *part = (Partial *)(smem + Lo.part_off) + (int64_t)G.grp * 2 * WPM;
-  int *flag = (int *)(part + 2 * WPM);
+  unsigned char *gmem = smem + Lo.part_off + (int64_t)G.grp * group_bytes(WPM);
+  Partial *part = (Partial *)gmem;
+  int *flag = (int *)(gmem + 2 * WPM * sizeof(Partial));
+  CandMoves *mv_smem = (CandMoves *)(gmem + 2 * WPM * sizeof(Partial) + 16);
 
   // load this group's members
   for (int e = 0; e < mine; ++e) {
@@ -617,20 +608,24 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
           const uint64_t E = __shfl_sync(kFull, Ereg, q);
           long long bd = LLONG_MAX;
           int bc = INT_MAX;
+          CandMoves cbest;
           for (int slot = 0; slot < cpl; ++slot) {
             const int c = slot * span + G.gw * 32 + lane;
             if (c < C) {
               long long d;
-              if constexpr (PERM) d = candidate_perm<MODEL, T16>(X, sol, W, c, p, gg, st);
+              CandMoves cm;
+              if constexpr (PERM) d = candidate_perm<MODEL, T16>(X, sol, W, c, p, gg, st, cm);
               else if constexpr (MODEL == KNAPSACK)
                 d = candidate_knap(X, sol, W, sc.aw, sc.av, c, p, gg, st);
               else d = candidate_gap(X, sol, loads, W, c, p, gg, st);
               if (d < bd || (d == bd && c < bc)) {
                 bd = d;
                 bc = c;
+                if constexpr (PERM) cbest = cm;
               }
             }
           }
+          const int mybc = bc;
           warp_argmin(bd, bc);
           if constexpr (WPM > 1) {
             Partial *pp = part + gpar * WPM;
@@ -651,7 +646,12 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
             gpar ^= 1u;
           }
           if (accept_move(bd, T, E)) {
-            if constexpr (PERM) apply_perm(X, sol, scr, W, bc, p, gg, G);
+            if constexpr (PERM) {
+              if (mybc == bc) *mv_smem = cbest;  // the winner's lane publishes its moves
+              G.sync();
+              const CandMoves cm = *mv_smem;
+              apply_perm(sol, scr, cm, G);
+            }
             else if constexpr (MODEL == KNAPSACK) apply_knap(X, sol, W, bc, p, gg, G, sc.aw, sc.av);
             else apply_gap(X, sol, loads, W, bc, p, gg, G);
             sc.cost += bd;
@@ -887,7 +887,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
 // instance, one member per group of WPM warps (cooperative launch, so that
 // all members are resident together for the window barriers).
 template <int MODEL, bool T16, int WPM>
-__global__ void __launch_bounds__(kMaxWarps * 32)
+__global__ void __launch_bounds__(kMaxWarps * 32, 1)
     evolve_kernel(const __grid_constant__ KInst I, int warps, uint64_t timeout_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const bool staged = I.shared_bytes > 0;
