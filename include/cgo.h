@@ -212,6 +212,37 @@ cgo_status cgo_state_set(cgo_problem *prob, const cgo_params *params, uint64_t s
 cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_prob,
                            const uint64_t *seeds, int32_t count, void *cuda_stream);
 
+/* Allocation-free TSP solve, for callers that cannot allocate device memory
+ * themselves or through the library (for example code running where
+ * cudaMalloc is not allowed, or a host that must keep GPU memory use fixed
+ * after start-up).  The paper has no counterpart: it is an interface
+ * variant of cgo_solve for TSP.
+ *
+ * The caller passes the inputs and the outputs; this call allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).  Its working
+ * memory is one file-scope device array of 8 MiB inside the library, which
+ * every GPU that loads the library holds until the process exits.  The
+ * problem must fit in it: a request larger than the array (roughly
+ * 2n^2 + 8*population*n bytes) returns CGO_ERR_INVALID before any GPU work.
+ *
+ * desc:          TSP (CGO_ENC_PERM), pointers_on_device = 1, mat0 = the
+ *                n*n int32 distance matrix in device memory (symmetric,
+ *                else CGO_ERR_UNSUPPORTED); other fields as in
+ *                cgo_problem_create.
+ * params, seed:  as in cgo_solve; the result equals cgo_solve followed by
+ *                cgo_best for the same inputs.
+ * out_best_sol:  device buffer of n int32: the elite solution.
+ * out_best_cost: device buffer of one int64: its cost.
+ * The call waits for its work on cuda_stream before it returns.
+ *
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture.  Every call shares the same array and leaves
+ * its contents behind: calls that overlap on the GPU (other threads or
+ * streams) race with each other and must be serialised by the caller. */
+cgo_status cgo_solve_static(const cgo_problem_desc *desc, const cgo_params *params, uint64_t seed,
+                            int32_t *out_best_sol, int64_t *out_best_cost, void *cuda_stream);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char *cgo_last_error(void);
 

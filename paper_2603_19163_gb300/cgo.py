@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
                 "cgo_version": ([], c.c_char_p),
                 "cgo_debug_inject": ([vp, c.c_int32, c.c_int64], c.c_int),
                 "cgo_last_kernel_time": ([vp, P(c.c_double), _i64p], c.c_int),
+                "cgo_solve_static": ([P(cgo_problem_desc), P(cgo_params), c.c_uint64, vp, vp, vp],
+                                     c.c_int),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(L, name)

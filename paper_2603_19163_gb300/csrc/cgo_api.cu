@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -365,6 +366,39 @@ cgo_status run_generations(cgo_problem *p, int64_t G, cudaStream_t st) {
   return CGO_OK;
 }
 
+// ------------------------------------------------ allocation-free solve
+// Scratch of cgo_solve_static: a fixed device array that every GPU loading
+// this library holds until the process exits.  Host code must not use the
+// symbol's name as an address: it resolves the device address once per
+// device with cudaGetSymbolAddress and passes that pointer to the kernels.
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+cgo_status static_scratch(void **out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(CGO_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
+    g_static_ptr[dev] = ptr;
+  }
+  *out = g_static_ptr[dev];
+  return CGO_OK;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
 }  // namespace
 
 extern "C" {
@@ -712,6 +746,109 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
     cgo_status s = cgo_solve(probs[i], &per[i], seeds[i], stream);
     if (s != CGO_OK) return s;
   }
+  return CGO_OK;
+}
+
+cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint64_t seed,
+                            int32_t *out_best_sol, int64_t *out_best_cost, void *stream) {
+  if (!d || d->struct_size != sizeof(cgo_problem_desc))
+    return fail(CGO_ERR_INVALID, "desc: struct_size must be sizeof(cgo_problem_desc)");
+  if (d->model != CGO_TSP || d->encoding != CGO_ENC_PERM)
+    return fail(CGO_ERR_UNSUPPORTED, "the allocation-free solve supports TSP only");
+  if (!d->pointers_on_device || !d->mat0)
+    return fail(CGO_ERR_INVALID, "the allocation-free solve needs the distance matrix on the device");
+  if (!out_best_sol || !out_best_cost) return fail(CGO_ERR_INVALID, "output buffers are required");
+  if (d->n < 2 || d->n > 65535) return fail(CGO_ERR_INVALID, "n must be in [2, 65535]");
+  cgo_problem p;  // a description on the stack: no device state of its own
+  cudaGetDevice(&p.device);
+  p.model = TSP;
+  p.n = p.len = d->n;
+  p.tag = d->instance_tag;
+  uint32_t en = 0;
+  cgo_status s = validate_params(&p, q, &en);
+  if (s != CGO_OK) return s;
+  const int n = d->n, P = q->population;
+  // carve the scratch; the triangle is sized for int32 entries (worst case)
+  const size_t tri_b = up256((size_t)n * (n + 1) / 2 * 4 + 16);
+  const size_t sol_b = up256((size_t)P * n * 4);
+  const size_t need = tri_b + 2 * sol_b + 2 * up256((size_t)P * 8) + up256(2 * sizeof(DevAos)) +
+                      up256(sizeof(DevSync)) + 256;
+  if (need > kStaticScratchBytes)
+    return fail(CGO_ERR_INVALID,
+                "n=%d, population=%d need %zu bytes of scratch; the allocation-free solve has %zu", n,
+                P, need, kStaticScratchBytes);
+  void *base = nullptr;
+  if ((s = static_scratch(&base)) != CGO_OK) return s;
+  unsigned char *b = (unsigned char *)base;
+  void *tri = b;
+  b += tri_b;
+  int32_t *cur = (int32_t *)b;
+  b += sol_b;
+  int32_t *bestsol = (int32_t *)b;
+  b += sol_b;
+  int64_t *cost = (int64_t *)b;
+  b += up256((size_t)P * 8);
+  int64_t *best = (int64_t *)b;
+  b += up256((size_t)P * 8);
+  DevAos *aos = (DevAos *)b;
+  b += up256(2 * sizeof(DevAos));
+  DevSync *sync = (DevSync *)b;
+  b += up256(sizeof(DevSync));
+  uint32_t *flags = (uint32_t *)b;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: clear what starts at zero
+  CUDA_TRY(cudaMemsetAsync(flags, 0, 16, st), "scratch reset");
+  CUDA_TRY(launch_tsp_check(d->mat0, n, flags, st), "matrix check");
+  uint32_t hf[2] = {0, 0};
+  CUDA_TRY(cudaMemcpyAsync(hf, flags, sizeof hf, cudaMemcpyDeviceToHost, st), "matrix check");
+  CUDA_TRY(cudaStreamSynchronize(st), "matrix check");
+  if (hf[0]) return fail(CGO_ERR_UNSUPPORTED, "the GPU TSP path needs a symmetric distance matrix");
+  p.tri16 = hf[1] <= 32767u ? 1 : 0;
+  CUDA_TRY(cudaMemsetAsync(tri, 0, tri_b, st), "scratch reset");
+  CUDA_TRY(build_triangle(d->mat0, n, p.tri16, tri, st), "triangle");
+  p.d_mat0 = const_cast<int32_t *>(d->mat0);
+  p.d_tri = tri;
+  p.params = *q;
+  p.seed = seed;
+  p.enabled = en;
+  p.d_cur = cur;
+  p.d_bestsol = bestsol;
+  p.d_cost = cost;
+  p.d_best = best;
+  p.d_aos = aos;
+  p.d_sync = sync;
+  KInst h = base_kinst(&p);
+  CUDA_TRY(launch_init(h, st), "init launch");
+  DevAos a0;
+  memset(&a0, 0, sizeof a0);
+  a0.T = q->T0_q32;
+  for (int i = 0; i < kNops; ++i) a0.w_op[i] = ((en >> i) & 1u) ? q->op_w0_q16[i] : 0u;
+  for (int i = 0; i < 3; ++i) a0.w_k[i] = q->k_w0_q16[i];
+  h.aos_out = aos;
+  CUDA_TRY(launch_init_aos(h, a0, st), "init launch");
+  int cur_aos = 0;
+  if (q->generations > 0) {
+    if (q->generations >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "too many generations");
+    int warps = 0, wpm = 1;
+    int64_t smem = 0;
+    h = base_kinst(&p);
+    if ((s = choose_launch(&p, h, &warps, &wpm, &smem)) != CGO_OK) return s;
+    h.g_begin = 0;
+    h.g_end = q->generations;
+    h.aos_in = aos;
+    h.aos_out = aos + 1;
+    CUDA_TRY(cudaMemsetAsync(sync, 0, sizeof(DevSync), st), "scratch reset");
+    CUDA_TRY(cudaMemsetAsync(sync->elite, 0x7F, sizeof(sync->elite), st), "scratch reset");
+    CUDA_TRY(launch_evolve_single(h, warps, wpm, smem, p.timeout_ns, st), "evolve launch");
+    CUDA_TRY(launch_finalize(h, st), "finalize launch");
+    cur_aos = 1;
+  }
+  CUDA_TRY(launch_copy_elite(aos + cur_aos, bestsol, n, out_best_sol, out_best_cost, st), "copy elite");
+  uint32_t err = 0;
+  if (q->generations > 0)
+    CUDA_TRY(cudaMemcpyAsync(&err, &sync->error, 4, cudaMemcpyDeviceToHost, st), "reading status");
+  CUDA_TRY(cudaStreamSynchronize(st), "synchronising stream");
+  if (err) return fail(CGO_ERR_TIMEOUT, "a member barrier timed out (flags 0x%x)", err);
   return CGO_OK;
 }
 

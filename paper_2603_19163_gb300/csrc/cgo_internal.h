@@ -80,6 +80,9 @@ cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int64_t sme
 cudaError_t launch_finalize(const KInst &h, cudaStream_t st);
 cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri,
                            cudaStream_t st);
+cudaError_t launch_tsp_check(const int32_t *d_mat, int n, uint32_t *d_flags, cudaStream_t st);
+cudaError_t launch_copy_elite(const DevAos *d_aos, const int32_t *d_bestsol, int len,
+                              int32_t *out_sol, int64_t *out_cost, cudaStream_t st);
 // shared-memory needs of the evolve kernel
 int64_t smem_per_warp(const KInst &h);
 int64_t instance_data_bytes(const KInst &h);

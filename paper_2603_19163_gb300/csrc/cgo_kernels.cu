@@ -1044,7 +1044,44 @@ __global__ void triangle_kernel(const int32_t *__restrict__ mat, int n, int tri1
   }
 }
 
+// flags[0]: 1 if D is asymmetric; flags[1]: max |D| (for the triangle width)
+__global__ void tsp_check_kernel(const int32_t *__restrict__ mat, int n, uint32_t *flags) {
+  const int64_t total = (int64_t)n * n;
+  uint32_t asym = 0, mx = 0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    const int32_t v = mat[t];
+    asym |= (uint32_t)(v != mat[(int64_t)j * n + i]);
+    const uint32_t a = v < 0 ? (uint32_t)(-(int64_t)v) : (uint32_t)v;
+    mx = max(mx, a);
+  }
+  if (asym) atomicOr(&flags[0], 1u);
+  atomicMax(&flags[1], mx);
+}
+
+// copy the elite member's best solution and cost to caller buffers
+__global__ void copy_elite_kernel(const DevAos *aos, const int32_t *bestsol, int len, int32_t *out_sol,
+                                  int64_t *out_cost) {
+  const int e = aos->elite;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) out_sol[i] = bestsol[(int64_t)e * len + i];
+  if (threadIdx.x == 0) *out_cost = aos->elite_cost;
+}
+
 // ------------------------------------------------------------ launchers
+cudaError_t launch_tsp_check(const int32_t *d_mat, int n, uint32_t *d_flags, cudaStream_t st) {
+  const int64_t total = (int64_t)n * n;
+  const int blocks = (int)min((int64_t)1024, (total + 255) / 256);
+  tsp_check_kernel<<<blocks, 256, 0, st>>>(d_mat, n, d_flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_elite(const DevAos *d_aos, const int32_t *d_bestsol, int len,
+                              int32_t *out_sol, int64_t *out_cost, cudaStream_t st) {
+  copy_elite_kernel<<<1, 256, 0, st>>>(d_aos, d_bestsol, len, out_sol, out_cost);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init(const KInst &h, cudaStream_t st) {
   const int threads = 128, blocks = (h.P + threads - 1) / threads;
   init_kernel<<<blocks, threads, 0, st>>>(h);
