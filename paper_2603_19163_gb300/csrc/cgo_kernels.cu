@@ -54,7 +54,7 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
 int64_t instance_data_bytes(const KInst &h) {
   switch (h.model) {
     case TSP: return align16((int64_t)h.n * (h.n + 1) / 2 * (h.tri16 ? 2 : 4));
-    case QAP: return 2 * align16((int64_t)h.n * h.n * 4);
+    case QAP: return 2 * align16((int64_t)h.n * (h.n | 1) * 4);
     case KNAPSACK: return 2 * align16((int64_t)h.n * 4);
     case GAP: return 2 * align16((int64_t)h.m * h.n * 4) + align16((int64_t)h.m * 4);
   }
@@ -74,7 +74,8 @@ struct View {
   uint32_t tag, k0, k1;
   const void *tri;
   int n2m1;
-  const int32_t *F, *D;        // QAP
+  const int32_t *F, *D;        // QAP (row stride qs)
+  int qs;
   const int32_t *w, *v;        // knapsack
   const int32_t *gc, *gr, *gcap;  // GAP
 };
@@ -210,13 +211,14 @@ __device__ long long qap_step(const View &X, const int32_t *sol, const PMove &mv
   const int r = mv.b1, s = mv.b3;
   const int pr = vlook(sol, r, p0, p1, np), ps = vlook(sol, s, p0, p1, np);
   const int32_t *F = X.F, *D = X.D;
-  const int32_t *Fr = F + (size_t)r * n, *Fs = F + (size_t)s * n;
-  const int32_t *Dr = D + (size_t)pr * n, *Ds = D + (size_t)ps * n;
+  const int qs = X.qs;
+  const int32_t *Fr = F + (size_t)r * qs, *Fs = F + (size_t)s * qs;
+  const int32_t *Dr = D + (size_t)pr * qs, *Ds = D + (size_t)ps * qs;
   long long acc = 0;
   for (int k = 0; k < n; ++k) {
     const int pk = vlook(sol, k, p0, p1, np);
     const long long t1 = ((long long)Fr[k] - Fs[k]) * ((long long)Ds[pk] - Dr[pk]);
-    const int32_t *Fk = F + (size_t)k * n, *Dk = D + (size_t)pk * n;
+    const int32_t *Fk = F + (size_t)k * qs, *Dk = D + (size_t)pk * qs;
     const long long t2 = ((long long)Fk[r] - Fk[s]) * ((long long)Dk[ps] - Dk[pr]);
     acc += (k != r && k != s) ? t1 + t2 : 0ll;
   }
@@ -247,6 +249,30 @@ template <int MODEL, bool T16>
 __device__ __forceinline__ long long candidate_perm(const View &X, const int32_t *sol,
                                                     const Weights<4> &W, uint32_t c, uint32_t p,
                                                     uint32_t g, Stats<4> &st, CandMoves &cm) {
+  if constexpr (MODEL == QAP) {
+    // O(n) deltas: evaluate only the k steps that count
+    const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+    const int k = 1 + wsample(W.k, W.Wk, R0.w);
+    int ops[3] = {-1, -1, -1};
+    long long d = 0;
+    cm.k = k;
+    cm.m[1] = cm.m[2] = PMove{0, 0, 0, 0, 0};
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      if (t < k) {
+        const uint4 R = t == 0 ? R0 : philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
+        ops[t] = wsample(W.op, W.Wop, R.x);
+        cm.m[t] = perm_decode(ops[t], R.y, R.z, X.len);
+        d += qap_step(X, sol, cm.m[t], cm.m[0], cm.m[1], t);
+      }
+    }
+    const uint32_t imp = d < 0;
+    stats_op(st, ops[0], imp);
+    stats_op(st, ops[1], imp);
+    stats_op(st, ops[2], imp);
+    stats_k(st, k, imp);
+    return d;
+  }
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
   const uint4 R1 = philox(ctr_word(c, 1, kKindMove), X.tag, p, g, X.k0, X.k1);
   const uint4 R2 = philox(ctr_word(c, 2, kKindMove), X.tag, p, g, X.k0, X.k1);
@@ -843,6 +869,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.tri = I.tri;
   X.F = I.mat0;
   X.D = I.mat1;
+  X.qs = I.n;
   X.w = I.vec0;
   X.v = I.vec1;
   X.gc = I.mat0;
@@ -861,9 +888,19 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
       X.tri = copy(I.tri, (int64_t)I.n * (I.n + 1) / 2 * (I.tri16 ? 2 : 4), 0);
       break;
     case QAP: {
-      const int64_t b = align16((int64_t)I.n * I.n * 4);
-      X.F = (const int32_t *)copy(I.mat0, b, 0);
-      X.D = (const int32_t *)copy(I.mat1, b, b);
+      // rows re-strided to an odd length so that lanes reading different rows
+      // at the same column hit different banks
+      const int n = I.n, qs = I.n | 1;
+      const int64_t b = align16((int64_t)n * qs * 4);
+      int32_t *Fs = (int32_t *)smem, *Ds = (int32_t *)(smem + b);
+      for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t % n);
+        Fs[(int64_t)i * qs + j] = I.mat0[t];
+        Ds[(int64_t)i * qs + j] = I.mat1[t];
+      }
+      X.F = Fs;
+      X.D = Ds;
+      X.qs = qs;
       break;
     }
     case KNAPSACK: {
