@@ -255,7 +255,10 @@ const char *cgo_version(void);
  *           bounded device wait must give up: the solve returns
  *           CGO_ERR_TIMEOUT and the handle's search state is discarded;
  * what = 2: the device wait limit becomes `value` milliseconds (default
- *           10000).
+ *           10000);
+ * what = 3: batched solves advance in time slices of `value` generations
+ *           (default 2000; process-wide, prob may be NULL).  Results do not
+ *           depend on it.
  * Errors: CGO_ERR_INVALID for an unknown `what` or a value out of range. */
 cgo_status cgo_debug_inject(cgo_problem *prob, int32_t what, int64_t value);
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -140,7 +141,8 @@ int64_t abssum(const std::vector<int32_t> &v) {
   return s;
 }
 
-const double kLimit = 4.6e18;  // 2^62: every cost and delta fits in int64 with room
+const double kLimit = 4.6e18;
+int64_t g_batch_slice = 2000;  // generations per batched time slice  // 2^62: every cost and delta fits in int64 with room
 
 void free_state(cgo_problem *p) {
   cudaFree(p->d_cur);
@@ -742,10 +744,204 @@ cgo_status cgo_state_set(cgo_problem *p, const cgo_params *q, uint64_t seed, con
 cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, const uint64_t *seeds,
                            int32_t count, void *stream) {
   if (count < 0 || (count > 0 && (!probs || !per || !seeds))) return fail(CGO_ERR_INVALID, "bad batch arguments");
+  if (count == 0) return CGO_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // every handle distinct and free
+  std::vector<std::unique_ptr<Guard>> guards;
+  guards.reserve((size_t)count);
   for (int32_t i = 0; i < count; ++i) {
-    cgo_status s = cgo_solve(probs[i], &per[i], seeds[i], stream);
-    if (s != CGO_OK) return s;
+    if (!probs[i]) return fail(CGO_ERR_INVALID, "problem %d is NULL", i);
+    guards.emplace_back(new Guard(probs[i]));
+    if (!guards.back()->ok) return fail(CGO_ERR_BUSY, "problem %d is in use (or repeated in the batch)", i);
   }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int64_t optin = max_smem_optin() - 1024;  // the kernel's static shared memory
+  // validate, allocate state, and describe each problem
+  std::vector<KInst> hk((size_t)count);
+  std::vector<DevAos> a0((size_t)count);
+  std::vector<int> bucket_of((size_t)count);
+  struct Bucket {
+    int model, tri16, wpm, warps;
+    int64_t smem;
+    std::vector<int> members;
+  };
+  std::vector<Bucket> buckets;
+  int64_t Gmax = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    cgo_problem *p = probs[i];
+    if (p->device != dev) return fail(CGO_ERR_INVALID, "problem %d lives on another device", i);
+    uint32_t en = 0;
+    cgo_status s = validate_params(p, &per[i], &en);
+    if (s != CGO_OK) return s;
+    if (per[i].generations >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "problem %d: too many generations", i);
+    if ((s = ensure_state(p, per[i].population)) != CGO_OK) return s;
+    p->params = per[i];
+    p->seed = seeds[i];
+    p->enabled = en;
+    p->g = 0;
+    p->aos_cur = 0;
+    p->has_state = false;
+    KInst h = base_kinst(p);
+    h.aos_in = h.aos_out = p->d_aos;
+    h.G_total = per[i].generations;
+    h.local_sync = 1;
+    // launch shape: one warp per member (many members per CTA keep the
+    // SMs busy), every member of the instance in the CTA
+    int wpm = p->wpm_override > 0 ? p->wpm_override : 1;
+    int warps = p->warps_override > 0 ? p->warps_override : kMaxWarps;
+    warps = std::max(wpm, std::min(warps, ((per[i].population * wpm + wpm - 1) / wpm) * wpm));
+    warps = std::min(warps, kMaxWarps) / wpm * wpm;
+    const int64_t staged = batch_smem_bytes(h, warps, wpm, true);
+    const int64_t global = batch_smem_bytes(h, warps, wpm, false);
+    bool use_smem = staged <= optin && p->staging_override != STAGE_GLOBAL;
+    if (p->staging_override == STAGE_SMEM && !use_smem)
+      return fail(CGO_ERR_UNSUPPORTED, "problem %d: instance data do not fit in shared memory", i);
+    const int64_t need = use_smem ? staged : global;
+    if (need > optin)
+      return fail(CGO_ERR_UNSUPPORTED, "problem %d: population %d x length %d does not fit in one CTA", i,
+                  per[i].population, p->len);
+    h.shared_bytes = use_smem ? instance_data_bytes(h) : 0;
+    // shared-memory size class: 1/8, 1/4, 1/2 or all of the budget
+    int64_t cls = optin;
+    for (int64_t c = optin / 8; c < optin; c *= 2)
+      if (need <= c) {
+        cls = c;
+        break;
+      }
+    int b = -1;
+    for (size_t k = 0; k < buckets.size(); ++k)
+      if (buckets[k].model == p->model && buckets[k].tri16 == p->tri16 && buckets[k].wpm == wpm &&
+          buckets[k].warps == warps && buckets[k].smem == cls)
+        b = (int)k;
+    if (b < 0) {
+      buckets.push_back(Bucket{p->model, p->tri16, wpm, warps, cls, {}});
+      b = (int)buckets.size() - 1;
+    }
+    buckets[(size_t)b].members.push_back(i);
+    hk[(size_t)i] = h;
+    DevAos &a = a0[(size_t)i];
+    memset(&a, 0, sizeof a);
+    a.T = per[i].T0_q32;
+    for (int k = 0; k < kNops; ++k) a.w_op[k] = ((en >> k) & 1u) ? per[i].op_w0_q16[k] : 0u;
+    for (int k = 0; k < 3; ++k) a.w_k[k] = per[i].k_w0_q16[k];
+    Gmax = std::max<int64_t>(Gmax, per[i].generations);
+  }
+  // device copies of the descriptions, work lists and counters
+  const size_t nb = buckets.size();
+  KInst *d_k = nullptr;
+  DevAos *d_a0 = nullptr;
+  int *d_lists = nullptr, *d_next = nullptr;
+  auto release = [&]() {
+    cudaFree(d_k);
+    cudaFree(d_a0);
+    cudaFree(d_lists);
+    cudaFree(d_next);
+  };
+  std::vector<int> lists;
+  std::vector<size_t> list_off;
+  for (auto &bk : buckets) {
+    // longest first: larger instances start early, small ones fill the tail
+    std::stable_sort(bk.members.begin(), bk.members.end(), [&](int x, int y) {
+      const double wx = (double)probs[x]->len * per[x].population * per[x].generations;
+      const double wy = (double)probs[y]->len * per[y].population * per[y].generations;
+      return wx > wy;
+    });
+    list_off.push_back(lists.size());
+    lists.insert(lists.end(), bk.members.begin(), bk.members.end());
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc((void **)&d_k, sizeof(KInst) * (size_t)count)) != cudaSuccess ||
+      (e = cudaMalloc((void **)&d_a0, sizeof(DevAos) * (size_t)count)) != cudaSuccess ||
+      (e = cudaMalloc((void **)&d_lists, sizeof(int) * lists.size())) != cudaSuccess ||
+      (e = cudaMalloc((void **)&d_next, sizeof(int) * nb)) != cudaSuccess) {
+    release();
+    return cuda_fail(e, "batch descriptors");
+  }
+  if ((e = cudaMemcpyAsync(d_k, hk.data(), sizeof(KInst) * (size_t)count, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_a0, a0.data(), sizeof(DevAos) * (size_t)count, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_lists, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = launch_init_batch(d_k, d_a0, count, st)) != cudaSuccess) {
+    release();
+    return cuda_fail(e, "batch init");
+  }
+  // one slice: every bucket's persistent kernel, concurrently on forked
+  // streams; captured once as a CUDA graph and replayed
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t slice = std::max<int64_t>(1, std::min<int64_t>(Gmax, g_batch_slice));
+  const int64_t nslices = Gmax > 0 ? (Gmax + slice - 1) / slice : 0;
+  std::vector<cudaStream_t> side(nb, nullptr);
+  std::vector<cudaEvent_t> evs(nb + 1, nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto &x : side)
+      if (x) cudaStreamDestroy(x);
+    for (auto &x : evs)
+      if (x) cudaEventDestroy(x);
+    release();
+  };
+  for (size_t b = 0; b < nb; ++b) {
+    if ((e = cudaStreamCreateWithFlags(&side[b], cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaEventCreateWithFlags(&evs[b], cudaEventDisableTiming)) != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evs[nb], cudaEventDisableTiming);
+  // grid per bucket: as many CTAs as fit, at most one per instance
+  std::vector<int> grids(nb, 0);
+  for (size_t b = 0; b < nb && e == cudaSuccess; ++b) {
+    const Bucket &bk = buckets[b];
+    const int per_sm = batch_ctas_per_sm(bk.model, bk.tri16, bk.warps, bk.wpm, bk.smem);
+    if (per_sm <= 0) {
+      cleanup();
+      return fail(CGO_ERR_UNSUPPORTED, "no CTA of the batched kernel fits (model %d)", bk.model);
+    }
+    grids[b] = std::max(1, std::min<int>((int)bk.members.size(), per_sm * sms));
+  }
+  if (e == cudaSuccess && nslices > 0) {
+    cudaStream_t cap = nullptr;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaEvent_t fork = evs[nb];
+      cudaError_t ce = cudaEventRecord(fork, cap);
+      for (size_t b = 0; b < nb && ce == cudaSuccess; ++b) {
+        const Bucket &bk = buckets[b];
+        ce = cudaStreamWaitEvent(side[b], fork, 0);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(d_next + b, 0, sizeof(int), side[b]);
+        if (ce == cudaSuccess)
+          ce = launch_batch(bk.model, bk.tri16, d_k, d_lists + list_off[b], (int)bk.members.size(),
+                            d_next + b, bk.warps, bk.wpm, bk.smem, grids[b], slice,
+                            probs[0]->timeout_ns, side[b]);
+        if (ce == cudaSuccess) ce = cudaEventRecord(evs[b], side[b]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, evs[b], 0);
+      }
+      const cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+      e = ce != cudaSuccess ? ce : ee;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    for (int64_t k = 0; k < nslices && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, st);
+    if (cap) cudaStreamDestroy(cap);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "batched solve");
+  }
+  cleanup();
+  for (int32_t i = 0; i < count; ++i) {
+    probs[i]->g = per[i].generations;
+    probs[i]->has_state = true;
+    probs[i]->last_warps = buckets[(size_t)0].warps;
+  }
+  for (size_t b = 0; b < nb; ++b)
+    for (int i : buckets[b].members) {
+      probs[i]->last_warps = buckets[b].warps;
+      probs[i]->last_wpm = buckets[b].wpm;
+      probs[i]->last_staging = hk[(size_t)i].shared_bytes > 0 ? STAGE_SMEM : STAGE_GLOBAL;
+    }
   return CGO_OK;
 }
 
@@ -856,13 +1052,16 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
  * so the barrier cannot complete and the bounded wait must give up;
  * what = 2 sets the barrier wait limit to `value` milliseconds. */
 cgo_status cgo_debug_inject(cgo_problem *p, int32_t what, int64_t value) {
-  if (!p) return fail(CGO_ERR_INVALID, "NULL problem");
+  if (!p && what != 3) return fail(CGO_ERR_INVALID, "NULL problem");
   if (what == 1) {
     if (value < 0 || value > 1024) return fail(CGO_ERR_INVALID, "phantom members out of range");
     p->phantom_members = (uint32_t)value;
   } else if (what == 2) {
     if (value < 1 || value > 600000) return fail(CGO_ERR_INVALID, "timeout out of range");
     p->timeout_ns = (uint64_t)value * 1000000ull;
+  } else if (what == 3) {
+    if (value < 1 || value > (1ll << 31)) return fail(CGO_ERR_INVALID, "slice out of range");
+    g_batch_slice = value;
   } else {
     return fail(CGO_ERR_INVALID, "unknown injection");
   }

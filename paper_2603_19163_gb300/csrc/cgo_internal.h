@@ -64,6 +64,9 @@ struct KInst {
   uint64_t seed;
   // launch range
   int64_t g_begin, g_end;
+  int64_t G_total;            // batched slices: generations of the whole solve
+  int32_t local_sync;         // 1: all members in one CTA, barriers are CTA-local
+  int32_t pad2;
   // state
   int32_t *cur, *bestsol;
   int64_t *cost, *best;
@@ -83,6 +86,12 @@ cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri,
 cudaError_t launch_tsp_check(const int32_t *d_mat, int n, uint32_t *d_flags, cudaStream_t st);
 cudaError_t launch_copy_elite(const DevAos *d_aos, const int32_t *d_bestsol, int len,
                               int32_t *out_sol, int64_t *out_cost, cudaStream_t st);
+cudaError_t launch_init_batch(const KInst *d_insts, const DevAos *d_a0s, int count, cudaStream_t st);
+int batch_ctas_per_sm(int model, int tri16, int warps, int wpm, int64_t smem_bytes);
+cudaError_t launch_batch(int model, int tri16, const KInst *d_insts, const int *d_list, int count,
+                         int *d_next, int warps, int wpm, int64_t smem_bytes, int grid,
+                         int64_t slice, uint64_t timeout_ns, cudaStream_t st);
+int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged);
 // shared-memory needs of the evolve kernel
 int64_t smem_per_warp(const KInst &h);
 int64_t instance_data_bytes(const KInst &h);

@@ -523,10 +523,22 @@ __device__ bool member_barrier(DevSync *S, uint32_t arrivals, uint32_t target, u
   return ok != 0;
 }
 
-// group-wide barrier wait: the group's first warp waits, the group follows
+__device__ __forceinline__ void cta_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Barrier id of the members of a CTA-local instance (groups use 1..8).
+constexpr int kLocalBar = 15;
+
+// group-wide barrier wait: the group's first warp waits, the group follows.
+// CTA-local instances (nact > 0) meet at a named barrier of all active threads.
 __device__ bool group_barrier(DevSync *S, uint32_t arrivals, uint32_t target, uint64_t timeout_ns,
-                              const Group &G, int *flag) {
+                              const Group &G, int *flag, int nact) {
   __threadfence();
+  if (nact > 0) {
+    cta_bar(kLocalBar, nact);
+    return true;
+  }
   G.sync();
   if (G.gw == 0) {
     const bool ok = member_barrier(S, arrivals, target, timeout_ns, threadIdx.x & 31);
@@ -584,6 +596,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   }
 
   // instance-wide scalars (identical in every warp)
+  // CTA-local instance: every active thread of the CTA takes part in barriers
+  const int nact = I.local_sync ? min(ngroups, nsol) * WPM * 32 : 0;
   const DevAos *A = I.aos_in;
   uint64_t T = A->T;
   Weights<NO> W;
@@ -601,6 +615,9 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   uint32_t stag = A->stag;
   long long elite_prev = A->elite_prev;
   uint32_t pend = lane < kStats ? A->pend[lane] : 0u;
+  // the instance scalars are updated in place by a CTA-local unit: everyone
+  // reads them before anyone can write them back
+  if (nact > 0) cta_bar(kLocalBar, nact);
   bool pend_used = false;
   uint32_t prev_acc[2] = {0u, 0u};
   uint32_t nb = 0, wi = 0, gpar = 0;
@@ -732,7 +749,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         I.best[p0 + ls] = scal[ls].best;
       }
     }
-    if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag))
+    if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
       return;
     ++nb;
     uint32_t cum = lane < kStats ? ld_relaxed(&S->acc[slot][lane]) : 0u;
@@ -804,7 +821,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         G.sync();
         aux_init(MODEL, X, sol, &scal[lw], (long long *)(smem + Lo.load_off) + (int64_t)lw * X.m, G);
       }
-      if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag))
+      if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
         return;
       ++nb;
     }
@@ -838,6 +855,28 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     }
     if (p0 + G.grp == 0 && G.gw == 0 && !pend_used) my += pend;
     if (lane < kStats && my) atomicAdd(&S->pend_out[lane], my);
+  }
+  if (nact > 0) {
+    // CTA-local finalize: elite and the open window's counts
+    __threadfence();
+    cta_bar(kLocalBar, nact);
+    if (p0 + G.grp == 0 && G.gw == 0) {
+      long long bb = LLONG_MAX;
+      int be = INT_MAX;
+      for (int q = lane; q < P; q += 32) {
+        const long long b = ld_relaxed64((const long long *)I.best + q);
+        if (b < bb) {
+          bb = b;
+          be = q;
+        }
+      }
+      warp_argmin(bb, be);
+      if (lane < kStats) I.aos_out->pend[lane] = ld_relaxed(&S->pend_out[lane]);
+      if (lane == 0) {
+        I.aos_out->elite = be;
+        I.aos_out->elite_cost = bb;
+      }
+    }
   }
   if (p0 + G.grp == 0 && G.tig == 0) {
     DevAos *O = I.aos_out;
@@ -938,6 +977,53 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
   evolve_members<MODEL, T16, WPM>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
 }
 
+// Batched persistent kernel: each CTA takes the next instance of the work
+// list, stages its data, and evolves all of its members (groups of WPM warps
+// loop over them) for up to `slice` generations, with CTA-local window
+// barriers; the instance's scalars are updated in place.  Instances that
+// have reached their generation budget are skipped.
+template <int MODEL, bool T16, int WPM>
+__global__ void __launch_bounds__(kMaxWarps * 32, 1)
+    batch_kernel(const KInst *__restrict__ insts, const int *__restrict__ list, int count,
+                 int *next, int warps, int64_t slice, uint64_t timeout_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ KInst sI;
+  __shared__ int su;
+  for (;;) {
+    if (threadIdx.x == 0) su = atomicAdd(next, 1);
+    __syncthreads();
+    const int u = su;
+    if (u >= count) return;
+    if (threadIdx.x == 0) {
+      sI = insts[list[u]];
+      const int64_t g0 = sI.aos_in->g;
+      sI.g_begin = g0;
+      sI.g_end = min(sI.G_total, g0 + slice);
+      sI.local_sync = 1;
+      // reset this instance's window-barrier block
+      DevSync *S = sI.sync;
+      S->error = 0;
+      for (int i = 0; i < 32; ++i) S->acc[0][i] = S->acc[1][i] = 0;
+      S->elite[0] = S->elite[1] = LLONG_MAX;
+      for (int i = 0; i < kStats; ++i) S->pend_out[i] = 0;
+      __threadfence();
+    }
+    __syncthreads();
+    const KInst &I = sI;
+    if (I.g_begin < I.g_end) {
+      const bool staged = I.shared_bytes > 0;
+      const View X = make_view(I, smem, staged);
+      __syncthreads();
+      const int groups = warps / WPM;
+      const Layout Lo =
+          make_layout(staged ? I.shared_bytes : 0, I.len, I.m, I.P, warps, WPM, I.model);
+      evolve_members<MODEL, T16, WPM>(I, X, smem, Lo, 0, I.P, warps, timeout_ns);
+      (void)groups;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- init
 __device__ long long full_cost(const KInst &I, const int32_t *x) {
   const int n = I.n;
@@ -974,11 +1060,9 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
   return 0;
 }
 
-// one thread per member: Philox-seeded Fisher-Yates / random bits / random
-// integers, then the exact cost
-__global__ void init_kernel(const __grid_constant__ KInst I) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= I.P) return;
+// Philox-seeded Fisher-Yates / random bits / random integers for member p,
+// then its exact cost
+__device__ void init_member(const KInst &I, int p) {
   const int len = I.len;
   int32_t *x = I.cur + (int64_t)p * len;
   const uint32_t k0 = (uint32_t)I.seed, k1 = (uint32_t)(I.seed >> 32);
@@ -1016,6 +1100,18 @@ __global__ void init_kernel(const __grid_constant__ KInst I) {
   for (int i = 0; i < len; ++i) b[i] = x[i];
 }
 
+// one thread per member
+__global__ void init_kernel(const __grid_constant__ KInst I) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < I.P) init_member(I, p);
+}
+
+// batched: one block per instance, threads over its members
+__global__ void init_batch_kernel(const KInst *__restrict__ insts) {
+  const KInst &I = insts[blockIdx.x];
+  for (int p = threadIdx.x; p < I.P; p += blockDim.x) init_member(I, p);
+}
+
 // elite = lowest best cost, lowest index on ties (one block)
 __device__ void block_elite(const KInst &I, int &e_out, long long &c_out) {
   __shared__ long long sb[32];
@@ -1044,6 +1140,21 @@ __device__ void block_elite(const KInst &I, int &e_out, long long &c_out) {
   }
   e_out = be;
   c_out = bb;
+}
+
+// batched: one block per instance; a0s[b] holds the initial scalars
+__global__ void init_aos_batch_kernel(const KInst *__restrict__ insts, const DevAos *__restrict__ a0s) {
+  const KInst &I = insts[blockIdx.x];
+  int e;
+  long long c;
+  block_elite(I, e, c);
+  if (threadIdx.x == 0) {
+    DevAos a0 = a0s[blockIdx.x];
+    a0.elite = e;
+    a0.elite_cost = c;
+    a0.elite_prev = c;
+    *I.aos_out = a0;
+  }
 }
 
 __global__ void init_aos_kernel(const __grid_constant__ KInst I, DevAos a0) {
@@ -1130,6 +1241,15 @@ cudaError_t launch_init_aos(const KInst &h, const DevAos &a0, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_init_batch(const KInst *d_insts, const DevAos *d_a0s, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  init_batch_kernel<<<count, 128, 0, st>>>(d_insts);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  init_aos_batch_kernel<<<count, 256, 0, st>>>(d_insts, d_a0s);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const KInst &h, cudaStream_t st) {
   finalize_kernel<<<1, 256, 0, st>>>(h);
   return cudaGetLastError();
@@ -1193,6 +1313,56 @@ cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int64_t sme
   KInst hi = h;
   void *args[] = {(void *)&hi, (void *)&warps, (void *)&timeout_ns};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(warps * 32), args, (size_t)smem_bytes, st);
+}
+
+template <int MODEL, bool T16>
+static const void *batch_fn(int wpm) {
+  if (wpm == 4) return (const void *)batch_kernel<MODEL, T16, 4>;
+  if (wpm == 2) return (const void *)batch_kernel<MODEL, T16, 2>;
+  return (const void *)batch_kernel<MODEL, T16, 1>;
+}
+
+static const void *pick_batch(int model, int tri16, int wpm) {
+  switch (model) {
+    case TSP: return tri16 ? batch_fn<TSP, true>(wpm) : batch_fn<TSP, false>(wpm);
+    case QAP: return batch_fn<QAP, false>(wpm);
+    case KNAPSACK: return batch_fn<KNAPSACK, false>(wpm);
+    case GAP: return batch_fn<GAP, false>(wpm);
+  }
+  return nullptr;
+}
+
+int batch_ctas_per_sm(int model, int tri16, int warps, int wpm, int64_t smem_bytes) {
+  const void *fn = pick_batch(model, tri16, wpm);
+  if (!fn) return 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, (size_t)smem_bytes) !=
+      cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
+cudaError_t launch_batch(int model, int tri16, const KInst *d_insts, const int *d_list, int count,
+                         int *d_next, int warps, int wpm, int64_t smem_bytes, int grid,
+                         int64_t slice, uint64_t timeout_ns, cudaStream_t st) {
+  const void *fn = pick_batch(model, tri16, wpm);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  void *args[] = {(void *)&d_insts, (void *)&d_list, (void *)&count, (void *)&d_next,
+                  (void *)&warps, (void *)&slice, (void *)&timeout_ns};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(warps * 32), args, (size_t)smem_bytes, st);
+}
+
+// shared memory of a batched unit: all P members of an instance in one CTA
+int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged) {
+  const Layout L =
+      make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, h.P, warps, wpm, h.model);
+  return L.total;
 }
 
 int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, bool staged) {

@@ -1,0 +1,108 @@
+"""GPU parity of the batched persistent kernel (cgo_solve_batch).
+
+A batch mixes models, sizes, populations and parameters; every problem's
+final state must equal the CPU oracle's for the same inputs and seed, and
+equal cgo_solve of that problem alone, bit for bit.  Time slices that cut AOS
+windows in the middle must not change anything.
+"""
+import numpy as np
+import pytest
+
+import instances as I
+import oracle as O
+from helpers import assert_same_state, oracle_run, params_for
+
+pytestmark = pytest.mark.gpu
+SW = O.SWAP
+
+
+@pytest.fixture(scope="module")
+def cgo():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_19163_gb300 import cgo as C
+    C.lib()
+    return C
+
+
+def mixed_batch():
+    items = []
+    for i, n in enumerate((9, 24, 57, 130)):
+        items.append((dict(I.tsp_uniform(n, 200 + i), tag=i), dict(P=8 + 3 * i, C=64, G=37 + 11 * i)))
+    items.append((dict(I.tsp_uniform(40, 210, box=90000), tag=9), dict(P=6, C=40, G=29)))  # int32 triangle
+    items.append((dict(I.qap_random(10, 220), tag=10), dict(P=5, C=48, G=23, ops=[SW])))
+    items.append((dict(I.qap_grid(16, 221), tag=11), dict(P=12, C=128, G=17, ops=[SW])))
+    for i, n in enumerate((3, 70, 400)):
+        items.append((dict(I.knapsack(n, 230 + i), tag=20 + i), dict(P=7 + i, C=96, G=31 + 5 * i, U=6)))
+    for i, (n, m) in enumerate(((12, 3), (60, 10))):
+        items.append((dict(I.gap(n, 240 + i, m=m), tag=30 + i), dict(P=9, C=80, G=41, U=4,
+                                                                        elite_period=8)))
+    items.append((dict(I.tsp_uniform(20, 250), tag=40), dict(P=4, C=32, G=0)))  # init only
+    return items
+
+
+def run_batch(C, items, seeds):
+    probs = [C.Problem(inst) for inst, _ in items]
+    params = [params_for(inst, **over) for inst, over in items]
+    C.solve_batch(probs, params, seeds)
+    return probs, params
+
+
+@pytest.mark.parametrize("slice_len", [2000, 7])
+def test_batch_matches_oracle(cgo, slice_len):
+    cgo.lib().cgo_debug_inject(None, 3, slice_len)
+    try:
+        items = mixed_batch()
+        seeds = [100 + i for i in range(len(items))]
+        probs, params = run_batch(cgo, items, seeds)
+        for (inst, _), prob, p, seed in zip(items, probs, params, seeds):
+            assert_same_state(prob.state(), oracle_run(inst, p, seed, p["G"]),
+                              "model %d n %d slice %d" % (inst["model"], inst["n"], slice_len))
+    finally:
+        cgo.lib().cgo_debug_inject(None, 3, 2000)
+
+
+def test_batch_equals_alone(cgo):
+    items = mixed_batch()[:6]
+    seeds = [7 * i + 1 for i in range(len(items))]
+    probs, params = run_batch(cgo, items, seeds)
+    for (inst, _), prob, p, seed in zip(items, probs, params, seeds):
+        alone = cgo.Problem(inst)
+        alone.solve(p, seed)
+        assert_same_state(prob.state(), alone.state(), "alone vs batch")
+        assert prob.best()[1] == alone.best()[1]
+
+
+def test_batch_then_continue(cgo):
+    """A batched solve leaves a normal state: continuing it alone equals the
+    oracle run for the total generations."""
+    inst = dict(I.tsp_uniform(33, 260), tag=3)
+    p = params_for(inst, P=10, C=64, G=25)
+    prob = cgo.Problem(inst)
+    cgo.solve_batch([prob], [p], [5])
+    prob.solve_continue(14)
+    assert_same_state(prob.state(), oracle_run(inst, p, 5, 39), "batch + continue")
+
+
+def test_batch_rejects_repeated_handles(cgo):
+    inst = I.tsp_uniform(10, 261)
+    prob = cgo.Problem(inst)
+    p = params_for(inst, P=4, C=8, G=3)
+    with pytest.raises(cgo.CgoError) as e:
+        cgo.solve_batch([prob, prob], [p, p], [1, 2])
+    assert e.value.status == cgo.ERR_BUSY
+
+
+def test_config4_mix_sample_prefix(cgo):
+    """Instances of the uneven 512-instance mix (TSP n~U[50,500], knapsack
+    n~U[100,2000], GAP n~U[50,300]) in one batch, over a prefix of the
+    generation budget, against the oracle."""
+    mix = I.batch_mix(512, 0)
+    pick = [0, 1, 2, 3, 5, 8, 13, 21, 34, 55]
+    items = [(mix[i], dict(P=32, C=128, G=12)) for i in pick]
+    seeds = [1 + i for i in pick]
+    probs, params = run_batch(cgo, items, seeds)
+    for (inst, _), prob, p, seed in zip(items, probs, params, seeds):
+        assert_same_state(prob.state(), oracle_run(inst, p, seed, p["G"]),
+                          "mix model %d n %d" % (inst["model"], inst["n"]))
