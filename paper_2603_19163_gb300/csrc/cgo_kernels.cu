@@ -19,6 +19,26 @@
 namespace cgo {
 
 // ---------------------------------------------------------------- layout
+// Solutions in shared memory use compact elements: permutation symbols
+// (< 65536) as uint16, binary values and agent indices (< 256) as uint8.
+using PermEl = uint16_t;
+using ByteEl = uint8_t;
+__host__ __device__ inline int sol_esize(int model) {
+  return (model == KNAPSACK || model == GAP) ? 1 : 2;
+}
+template <int MODEL>
+struct SolEl {
+  using T = PermEl;
+};
+template <>
+struct SolEl<KNAPSACK> {
+  using T = ByteEl;
+};
+template <>
+struct SolEl<GAP> {
+  using T = ByteEl;
+};
+
 struct SolScal {
   long long cost, best, aw, av;  // aw/av: knapsack sum of weights / values
 };
@@ -40,7 +60,7 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   Layout L;
   const int groups = warps / wpm;
   L.inst = align16(inst_bytes);
-  L.sol_stride = align16((int64_t)len * 4);
+  L.sol_stride = align16((int64_t)len * sol_esize(model));
   L.sol_off = L.inst;
   L.scr_off = L.sol_off + (int64_t)nsol * L.sol_stride;
   const bool perm = (model == TSP || model == QAP || model == CVRPTW);
@@ -151,7 +171,7 @@ __device__ __forceinline__ long long tsp_d(const View &X, int x, int y) {
 }
 
 // element at position q of the array after the np prior moves (p0 first)
-__device__ __forceinline__ int vlook(const int32_t *sol, int q, const PMove &p0, const PMove &p1,
+__device__ __forceinline__ int vlook(const PermEl *sol, int q, const PMove &p0, const PMove &p1,
                                      int np) {
   if (np >= 2) q = perm_inv(p1, q);
   if (np >= 1) q = perm_inv(p0, q);
@@ -171,7 +191,7 @@ __device__ __forceinline__ int vlook(const int32_t *sol, int q, const PMove &p0,
 // the delta is 0 except for an exchange with M non-empty:
 //   d(B_l,M_f) + d(M_l,A_f) + d(A_l,B_f) - d(A_l,M_f) - d(M_l,B_f) - d(B_l,A_f).
 template <bool T16>
-__device__ __forceinline__ long long tsp_step(const View &X, const int32_t *sol, const PMove &mv,
+__device__ __forceinline__ long long tsp_step(const View &X, const PermEl *sol, const PMove &mv,
                                               const PMove &p0, const PMove &p1, int np) {
   const int m = X.len;
   const int b1 = mv.b1, b2 = mv.b2, b3 = mv.b3, b4 = mv.b4;
@@ -205,7 +225,7 @@ __device__ __forceinline__ long long tsp_step(const View &X, const int32_t *sol,
 // Swap of positions r, s on the (virtual) permutation pi: O(n) delta of
 // sum_ij F[i][j] D[pi_i][pi_j] for general (asymmetric, non-zero diagonal)
 // F and D.
-__device__ long long qap_step(const View &X, const int32_t *sol, const PMove &mv,
+__device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
                               const PMove &p0, const PMove &p1, int np) {
   const int n = X.n;
   const int r = mv.b1, s = mv.b3;
@@ -229,7 +249,7 @@ __device__ long long qap_step(const View &X, const int32_t *sol, const PMove &mv
 
 // ------------------------------------------------- candidate evaluation
 template <int MODEL, bool T16>
-__device__ __forceinline__ long long perm_delta(const View &X, const int32_t *sol, const PMove &mv,
+__device__ __forceinline__ long long perm_delta(const View &X, const PermEl *sol, const PMove &mv,
                                                 const PMove &p0, const PMove &p1, int np) {
   if constexpr (MODEL == TSP) return tsp_step<T16>(X, sol, mv, p0, p1, np);
   else return qap_step(X, sol, mv, p0, p1, np);
@@ -246,7 +266,7 @@ struct CandMoves {
 // step is computed (each needs only the decoded earlier moves, not their
 // deltas), so the steps overlap; k selects how many count.
 template <int MODEL, bool T16>
-__device__ __forceinline__ long long candidate_perm(const View &X, const int32_t *sol,
+__device__ __forceinline__ long long candidate_perm(const View &X, const PermEl *sol,
                                                     const Weights<4> &W, uint32_t c, uint32_t p,
                                                     uint32_t g, Stats<4> &st, CandMoves &cm) {
   if constexpr (MODEL == QAP) {
@@ -298,7 +318,7 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const int32_t
 
 // Knapsack: k flips on x (a flip of an index flipped earlier in the same
 // candidate undoes it); delta from the running weight/value sums.
-__device__ long long candidate_knap(const View &X, const int32_t *x, const Weights<1> &W,
+__device__ long long candidate_knap(const View &X, const ByteEl *x, const Weights<1> &W,
                                     long long W0, long long V0, uint32_t c, uint32_t p,
                                     uint32_t g, Stats<1> &st) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
@@ -328,7 +348,7 @@ __device__ long long candidate_knap(const View &X, const int32_t *x, const Weigh
 
 // GAP: k random resets of a job's agent; loads of touched agents tracked
 // through small override lists.
-__device__ long long candidate_gap(const View &X, const int32_t *x, const long long *loads,
+__device__ long long candidate_gap(const View &X, const ByteEl *x, const long long *loads,
                                    const Weights<1> &W, uint32_t c, uint32_t p, uint32_t g,
                                    Stats<1> &st) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
@@ -392,7 +412,7 @@ struct Group {
 // Materialise one permutation move in place (group-cooperative): positions
 // that change are gathered through the inverse map into the scratch array,
 // then written back.  Only A and B move when they have equal lengths.
-__device__ void perm_materialise(int32_t *sol, int32_t *scr, const PMove &mv, const Group &G) {
+__device__ void perm_materialise(PermEl *sol, PermEl *scr, const PMove &mv, const Group &G) {
   const int la = mv.b2 - mv.b1, lb = mv.b4 - mv.b3;
   const bool ends = !mv.rev && la == lb;
   const int cnt = ends ? 2 * la : mv.b4 - mv.b1;
@@ -415,11 +435,11 @@ __device__ __forceinline__ int regen_k(const View &X, const Weights<NO> &W, uint
   return 1 + wsample(W.k, W.Wk, R0.w);
 }
 
-__device__ void apply_perm(int32_t *sol, int32_t *scr, const CandMoves &cm, const Group &G) {
+__device__ void apply_perm(PermEl *sol, PermEl *scr, const CandMoves &cm, const Group &G) {
   for (int t = 0; t < cm.k; ++t) perm_materialise(sol, scr, cm.m[t], G);
 }
 
-__device__ void apply_knap(const View &X, int32_t *x, const Weights<1> &W, uint32_t c,
+__device__ void apply_knap(const View &X, ByteEl *x, const Weights<1> &W, uint32_t c,
                            uint32_t p, uint32_t g, const Group &G, long long &aw, long long &av) {
   uint4 R0;
   const int k = regen_k(X, W, c, p, g, R0);
@@ -428,14 +448,14 @@ __device__ void apply_knap(const View &X, int32_t *x, const Weights<1> &W, uint3
     const int i = posm(R.y >> 16, (uint32_t)X.n);
     const int xi = x[i];
     G.sync();
-    if (G.tig == 0) x[i] = xi ^ 1;
+    if (G.tig == 0) x[i] = (ByteEl)(xi ^ 1);
     aw += xi ? -(long long)X.w[i] : (long long)X.w[i];
     av += xi ? -(long long)X.v[i] : (long long)X.v[i];
     G.sync();
   }
 }
 
-__device__ void apply_gap(const View &X, int32_t *x, long long *loads, const Weights<1> &W,
+__device__ void apply_gap(const View &X, ByteEl *x, long long *loads, const Weights<1> &W,
                           uint32_t c, uint32_t p, uint32_t g, const Group &G) {
   uint4 R0;
   const int k = regen_k(X, W, c, p, g, R0);
@@ -447,7 +467,7 @@ __device__ void apply_gap(const View &X, int32_t *x, long long *loads, const Wei
     const int an = (ao + dd) % X.m;
     G.sync();
     if (G.tig == 0) {
-      x[j] = an;
+      x[j] = (ByteEl)an;
       loads[ao] -= X.gr[(size_t)ao * X.n + j];
       loads[an] += X.gr[(size_t)an * X.n + j];
     }
@@ -457,7 +477,8 @@ __device__ void apply_gap(const View &X, int32_t *x, long long *loads, const Wei
 
 // auxiliary sums of one member (knapsack W/V, GAP loads), computed by the
 // group's first warp and left in shared memory
-__device__ void aux_init(int model, const View &X, const int32_t *x, SolScal *sc,
+template <class El>
+__device__ void aux_init(int model, const View &X, const El *x, SolScal *sc,
                          long long *loads, const Group &G) {
   const int lane = threadIdx.x & 31;
   if (G.gw == 0) {
@@ -561,6 +582,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
                                int p0, int nsol, int warps, uint64_t timeout_ns) {
   constexpr int NO = Enc<MODEL>::NO, BASE = Enc<MODEL>::BASE;
   constexpr bool PERM = (MODEL == TSP || MODEL == QAP);
+  using El = typename SolEl<MODEL>::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   Group G;
   G.wpm = WPM;
@@ -573,7 +595,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   if (mine == 0) return;
   const int len = I.len, P = I.P, C = I.C;
   DevSync *S = I.sync;
-  int32_t *scr = (int32_t *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.sol_stride);
+  El *scr = (El *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.sol_stride);
   SolScal *scal = (SolScal *)(smem + Lo.scal_off);
   unsigned char *gmem = smem + Lo.part_off + (int64_t)G.grp * group_bytes(WPM);
   Partial *part = (Partial *)gmem;
@@ -583,9 +605,9 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   // load this group's members
   for (int e = 0; e < mine; ++e) {
     const int ls = G.grp + e * ngroups, p = p0 + ls;
-    int32_t *sol = (int32_t *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+    El *sol = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
     const int32_t *src = I.cur + (int64_t)p * len;
-    for (int i = G.tig; i < len; i += G.nthr) sol[i] = src[i];
+    for (int i = G.tig; i < len; i += G.nthr) sol[i] = (El)src[i];
     if (G.tig == 0) {
       scal[ls].cost = I.cost[p];
       scal[ls].best = I.best[p];
@@ -634,7 +656,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     for (int e = 0; e < mine; ++e) {
       const int ls = G.grp + e * ngroups;
       const uint32_t p = (uint32_t)(p0 + ls);
-      int32_t *sol = (int32_t *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+      El *sol = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
       long long *loads = (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m;
       SolScal sc = scal[ls];
       T = Tw;
@@ -805,9 +827,9 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       warp_argmin(nwc, wq);
       const int lw = wq - p0;
       if (lw >= 0 && lw < nsol && (lw % ngroups) == G.grp) {
-        int32_t *sol = (int32_t *)(smem + Lo.sol_off + (int64_t)lw * Lo.sol_stride);
+        El *sol = (El *)(smem + Lo.sol_off + (int64_t)lw * Lo.sol_stride);
         const int32_t *src = I.bestsol + (int64_t)be * len;
-        for (int i = G.tig; i < len; i += G.nthr) sol[i] = __ldcg(src + i);
+        for (int i = G.tig; i < len; i += G.nthr) sol[i] = (El)__ldcg(src + i);
         G.sync();
         SolScal sc = scal[lw];
         sc.cost = bb;
@@ -830,7 +852,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   // ------------------------------------------------ write back
   for (int e = 0; e < mine; ++e) {
     const int ls = G.grp + e * ngroups, p = p0 + ls;
-    const int32_t *sol = (const int32_t *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+    const El *sol = (const El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
     int32_t *dst = I.cur + (int64_t)p * len;
     for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
     if (G.tig == 0) {
