@@ -418,17 +418,19 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
   if (d->encoding != encoding_of(d->model))
     return fail(CGO_ERR_INVALID, "encoding %d does not match model %d", d->encoding, d->model);
   if (d->n < 2) return fail(CGO_ERR_INVALID, "n must be >= 2");
-  if (d->model == CGO_CVRPTW) return fail(CGO_ERR_UNSUPPORTED, "CVRPTW is not implemented on the GPU yet");
   const bool dev = d->pointers_on_device != 0;
   const int64_t n = d->n;
-  const int len = (int)n;
-  if (n > 65535) return fail(CGO_ERR_INVALID, "solution length must be <= 65535");
+  if (d->model == CGO_CVRPTW && d->vehicles < 1) return fail(CGO_ERR_INVALID, "CVRPTW needs vehicles >= 1");
+  const int64_t len64 = d->model == CGO_CVRPTW ? n + d->vehicles - 1 : n;
+  if (len64 > 65535) return fail(CGO_ERR_INVALID, "solution length must be <= 65535");
+  const int len = (int)len64;
 
   cgo_problem *p = new cgo_problem();
   cudaGetDevice(&p->device);
   p->model = d->model;
   p->n = (int)n;
   p->len = len;
+  p->V = d->vehicles;
   p->tag = d->instance_tag;
   p->lam0 = d->penalty0;
   p->lam1 = d->penalty1;
@@ -480,6 +482,28 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
       cudaError_t e;
       if ((e = copy_in(&p->d_vec[0], a.data(), n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy w"));
       if ((e = copy_in(&p->d_vec[1], b.data(), n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy v"));
+      break;
+    }
+    case CGO_CVRPTW: {
+      const int64_t N = n + 1;
+      std::vector<int32_t> v[4];
+      if ((s = host_copy(d->mat0, N * N, dev, a)) != CGO_OK) return bail(s);
+      const int32_t *src[4] = {d->vec0, d->vec1, d->vec2, d->vec3};
+      for (int k = 0; k < 4; ++k)
+        if ((s = host_copy(src[k], N, dev, v[k])) != CGO_OK) return bail(s);
+      if (d->penalty0 < 0 || d->penalty1 < 0) return bail(fail(CGO_ERR_INVALID, "penalties < 0"));
+      p->lam0 = d->penalty0 > 0 ? d->penalty0 : 100;
+      p->lam1 = d->penalty1 > 0 ? d->penalty1 : 100;
+      // bound every route quantity: time, lateness, distance, load
+      const double maxd = (double)absmax(a), tmax = (double)absmax(v[1]) + (double)N * (maxd + (double)absmax(v[3]));
+      const double late = (double)N * (tmax + (double)absmax(v[2]));
+      if ((double)p->lam1 * late + (double)p->lam0 * ((double)abssum(v[0]) + std::fabs((double)d->capacity) * N) +
+              (double)(len + 1) * maxd > kLimit)
+        return bail(fail(CGO_ERR_INVALID, "CVRPTW data could overflow an int64 cost"));
+      cudaError_t e;
+      if ((e = copy_in(&p->d_mat0, a.data(), N * N, false)) != cudaSuccess) return bail(cuda_fail(e, "copy d"));
+      for (int k = 0; k < 4; ++k)
+        if ((e = copy_in(&p->d_vec[k], v[k].data(), N, false)) != cudaSuccess) return bail(cuda_fail(e, "copy vectors"));
       break;
     }
     case CGO_GAP: {

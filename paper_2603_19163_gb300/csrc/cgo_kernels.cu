@@ -77,6 +77,10 @@ int64_t instance_data_bytes(const KInst &h) {
     case QAP: return 2 * align16((int64_t)h.n * (h.n | 1) * 4);
     case KNAPSACK: return 2 * align16((int64_t)h.n * 4);
     case GAP: return 2 * align16((int64_t)h.m * h.n * 4) + align16((int64_t)h.m * 4);
+    case CVRPTW: {
+      const int64_t N = h.n + 1;
+      return align16(N * N * 4) + 4 * align16(N * 4);
+    }
   }
   return 0;
 }
@@ -98,6 +102,8 @@ struct View {
   int qs;
   const int32_t *w, *v;        // knapsack
   const int32_t *gc, *gr, *gcap;  // GAP
+  const int32_t *rd, *dem, *rdy, *due, *svc;  // CVRPTW: travel (n+1)^2, vectors n+1
+  long long lam1;
 };
 
 template <int NO>
@@ -140,6 +146,8 @@ template <>
 struct Enc<TSP> { static constexpr int NO = 4, BASE = 0; };
 template <>
 struct Enc<QAP> { static constexpr int NO = 4, BASE = 0; };
+template <>
+struct Enc<CVRPTW> { static constexpr int NO = 4, BASE = 0; };
 template <>
 struct Enc<KNAPSACK> { static constexpr int NO = 1, BASE = 4; };
 template <>
@@ -247,11 +255,65 @@ __device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
   return acc;
 }
 
+// ---------------------------------------------------------------- CVRPTW
+// Cost of the whole routes in positions [L, R) of a separator-encoded
+// sequence (symbols < n are customers 1..n, others end a route); R acts as
+// a separator.  Per route from the depot at t = 0: t = max(t + d, ready),
+// late += max(0, t - due), t += service; back at the depot t += d and
+// late += max(0, t - due_0); empty routes cost nothing.
+template <class Look>
+__device__ long long cvrptw_routes(const View &X, Look V, int L, int R) {
+  const int n = X.n, N = n + 1;
+  long long total = 0, t = 0, load = 0, dist = 0, late = 0;
+  int prev = 0;
+  for (int q = L; q <= R; ++q) {
+    const int sym = q < R ? V(q) : n;
+    if (sym >= n) {
+      if (prev != 0) {
+        const long long back = X.rd[(size_t)prev * N];
+        dist += back;
+        t += back;
+        late += overp(t - X.due[0]);
+        total += dist + X.lam0 * overp(load - X.cap) + X.lam1 * late;
+      }
+      t = load = dist = late = 0;
+      prev = 0;
+    } else {
+      const int c = sym + 1;
+      const long long dd = X.rd[(size_t)prev * N + c];
+      dist += dd;
+      t = max(t + dd, (long long)X.rdy[c]);
+      late += overp(t - X.due[c]);
+      t += X.svc[c];
+      load += X.dem[c];
+      prev = c;
+    }
+  }
+  return total;
+}
+
+// Delta of one move on the (virtual) sequence: only the routes that overlap
+// the moved range [b1, b4) change, and the move keeps its symbols (and so its
+// separators) inside that range, so [L, R) — widened to the enclosing
+// separators — covers whole routes before and after.
+__device__ long long cvrptw_step(const View &X, const PermEl *sol, const PMove &mv,
+                                 const PMove &p0, const PMove &p1, int np) {
+  const int n = X.n, m = X.len;
+  auto Vo = [&](int q) { return vlook(sol, q, p0, p1, np); };
+  auto Vn = [&](int q) { return vlook(sol, perm_inv(mv, q), p0, p1, np); };
+  int L = mv.b1;
+  while (L > 0 && Vo(L - 1) < n) --L;
+  int R = mv.b4;
+  while (R < m && Vo(R) < n) ++R;
+  return cvrptw_routes(X, Vn, L, R) - cvrptw_routes(X, Vo, L, R);
+}
+
 // ------------------------------------------------- candidate evaluation
 template <int MODEL, bool T16>
 __device__ __forceinline__ long long perm_delta(const View &X, const PermEl *sol, const PMove &mv,
                                                 const PMove &p0, const PMove &p1, int np) {
   if constexpr (MODEL == TSP) return tsp_step<T16>(X, sol, mv, p0, p1, np);
+  else if constexpr (MODEL == CVRPTW) return cvrptw_step(X, sol, mv, p0, p1, np);
   else return qap_step(X, sol, mv, p0, p1, np);
 }
 
@@ -269,8 +331,8 @@ template <int MODEL, bool T16>
 __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl *sol,
                                                     const Weights<4> &W, uint32_t c, uint32_t p,
                                                     uint32_t g, Stats<4> &st, CandMoves &cm) {
-  if constexpr (MODEL == QAP) {
-    // O(n) deltas: evaluate only the k steps that count
+  if constexpr (MODEL == QAP || MODEL == CVRPTW) {
+    // O(n) / O(route) deltas: evaluate only the k steps that count
     const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
     const int k = 1 + wsample(W.k, W.Wk, R0.w);
     int ops[3] = {-1, -1, -1};
@@ -283,7 +345,7 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
         const uint4 R = t == 0 ? R0 : philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
         ops[t] = wsample(W.op, W.Wop, R.x);
         cm.m[t] = perm_decode(ops[t], R.y, R.z, X.len);
-        d += qap_step(X, sol, cm.m[t], cm.m[0], cm.m[1], t);
+        d += perm_delta<MODEL, T16>(X, sol, cm.m[t], cm.m[0], cm.m[1], t);
       }
     }
     const uint32_t imp = d < 0;
@@ -581,7 +643,7 @@ template <int MODEL, bool T16, int WPM>
 __device__ void evolve_members(const KInst &I, const View &X, unsigned char *smem, const Layout &Lo,
                                int p0, int nsol, int warps, uint64_t timeout_ns) {
   constexpr int NO = Enc<MODEL>::NO, BASE = Enc<MODEL>::BASE;
-  constexpr bool PERM = (MODEL == TSP || MODEL == QAP);
+  constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW);
   using El = typename SolEl<MODEL>::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   Group G;
@@ -936,6 +998,12 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.gc = I.mat0;
   X.gr = I.mat1;
   X.gcap = I.vec0;
+  X.rd = I.mat0;
+  X.dem = I.vec0;
+  X.rdy = I.vec1;
+  X.due = I.vec2;
+  X.svc = I.vec3;
+  X.lam1 = I.lam1;
   if (!staged) return X;
   auto copy = [&](const void *src, int64_t bytes, int64_t off) {
     const int4 *s = (const int4 *)src;
@@ -968,6 +1036,15 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
       const int64_t b = align16((int64_t)I.n * 4);
       X.w = (const int32_t *)copy(I.vec0, b, 0);
       X.v = (const int32_t *)copy(I.vec1, b, b);
+      break;
+    }
+    case CVRPTW: {
+      const int64_t N = I.n + 1, b = align16(N * N * 4), v = align16(N * 4);
+      X.rd = (const int32_t *)copy(I.mat0, b, 0);
+      X.dem = (const int32_t *)copy(I.vec0, v, b);
+      X.rdy = (const int32_t *)copy(I.vec1, v, b + v);
+      X.due = (const int32_t *)copy(I.vec2, v, b + 2 * v);
+      X.svc = (const int32_t *)copy(I.vec3, v, b + 3 * v);
       break;
     }
     case GAP: {
@@ -1067,6 +1144,19 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
           V += I.vec1[i];
         }
       return -V + I.lam0 * overp(W - I.capacity);
+    }
+    case CVRPTW: {
+      View X;
+      X.n = n;
+      X.cap = I.capacity;
+      X.lam0 = I.lam0;
+      X.lam1 = I.lam1;
+      X.rd = I.mat0;
+      X.dem = I.vec0;
+      X.rdy = I.vec1;
+      X.due = I.vec2;
+      X.svc = I.vec3;
+      return cvrptw_routes(X, [&](int q) { return (int)x[q]; }, 0, I.len);
     }
     case GAP: {
       for (int j = 0; j < n; ++j) s += I.mat0[(size_t)x[j] * n + j];
@@ -1295,6 +1385,7 @@ static const void *pick_evolve(const KInst &h, int wpm) {
   switch (h.model) {
     case TSP: return h.tri16 ? evolve_fn<TSP, true>(wpm) : evolve_fn<TSP, false>(wpm);
     case QAP: return evolve_fn<QAP, false>(wpm);
+    case CVRPTW: return evolve_fn<CVRPTW, false>(wpm);
     case KNAPSACK: return evolve_fn<KNAPSACK, false>(wpm);
     case GAP: return evolve_fn<GAP, false>(wpm);
   }
@@ -1348,6 +1439,7 @@ static const void *pick_batch(int model, int tri16, int wpm) {
   switch (model) {
     case TSP: return tri16 ? batch_fn<TSP, true>(wpm) : batch_fn<TSP, false>(wpm);
     case QAP: return batch_fn<QAP, false>(wpm);
+    case CVRPTW: return batch_fn<CVRPTW, false>(wpm);
     case KNAPSACK: return batch_fn<KNAPSACK, false>(wpm);
     case GAP: return batch_fn<GAP, false>(wpm);
   }

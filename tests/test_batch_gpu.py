@@ -39,6 +39,7 @@ def mixed_batch():
         items.append((dict(I.gap(n, 240 + i, m=m), tag=30 + i), dict(P=9, C=80, G=41, U=4,
                                                                         elite_period=8)))
     items.append((dict(I.tsp_uniform(20, 250), tag=40), dict(P=4, C=32, G=0)))  # init only
+    items.append((dict(I.cvrptw(25, 251, vehicles=5, capacity=120), tag=41), dict(P=8, C=64, G=33)))
     return items
 
 

@@ -203,9 +203,31 @@ def test_gap300_prefix(cgo):
     assert_same_state(g, o, "gap300")
 
 
+# ------------------------------------------------------------------ CVRPTW
+@pytest.mark.parametrize("n,V,kw", [(2, 1, None), (5, 2, None), (12, 3, (0, 0, 65536)),
+                                    (30, 6, None)])
+def test_cvrptw(cgo, n, V, kw):
+    inst = I.cvrptw(n, 80 + n, vehicles=V, capacity=60, box=60, horizon=400, width=80)
+    over = dict(P=6, C=64, G=29, U=5, elite_period=10)
+    if kw:
+        over["w_k"] = list(kw)
+    p = params_for(inst, **over)
+    _, g, o = run_both(cgo, inst, p, 17)
+    assert_same_state(g, o, "cvrptw n=%d V=%d" % (n, V))
+
+
+def test_cvrptw100_prefix(cgo):
+    """The serving workload's routing class: 100 customers, 25 vehicles."""
+    inst = I.cvrptw(100, 90)
+    p = params_for(inst, P=16, C=128, G=15)
+    _, g, o = run_both(cgo, inst, p, 2)
+    assert_same_state(g, o, "cvrptw100")
+
+
 # ----------------------------------------------------- state and resume
 @pytest.mark.parametrize("maker", [lambda: I.tsp_uniform(25, 60), lambda: I.knapsack(60, 61),
-                                   lambda: I.gap(40, 62, m=6), lambda: I.qap_random(8, 63)])
+                                   lambda: I.gap(40, 62, m=6), lambda: I.qap_random(8, 63),
+                                   lambda: I.cvrptw(15, 68, vehicles=4, capacity=80)])
 def test_split_solve_and_checkpoint_resume(cgo, maker):
     inst = maker()
     ops = [SW] if inst["model"] == 1 else None
