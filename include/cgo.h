@@ -243,6 +243,59 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_prob
 cgo_status cgo_solve_static(const cgo_problem_desc *desc, const cgo_params *params, uint64_t seed,
                             int32_t *out_best_sol, int64_t *out_best_cost, void *cuda_stream);
 
+/* ------------------------------------------------------------- serving
+ * Continuous batching of solve requests (a request loop on a host thread of
+ * the library).  Submitted requests are admitted first come, first served,
+ * into device slots as slots and device memory free up; all resident
+ * requests advance together by `slice_generations` per time slice in
+ * persistent batched kernels replayed from a CUDA graph, and requests that
+ * arrive during a slice join at the next slice boundary.  Populations, AOS
+ * state and generation counters stay in device memory across slices.  Each
+ * result is bit-identical to cgo_solve of the same problem alone. */
+typedef struct cgo_server cgo_server;
+
+typedef struct {
+  uint32_t struct_size;        /* = sizeof(cgo_server_cfg) */
+  int32_t max_slots;           /* requests resident on the device at once, 1 .. 65536 */
+  int64_t hbm_budget_bytes;    /* device memory (instance data + search state) of
+                                  resident requests; a request waits until it fits
+                                  (one request is always admitted when none is resident) */
+  int64_t smem_budget_bytes;   /* largest shared-memory footprint of one request (0 = the
+                                  CTA limit); larger requests are refused at submit */
+  int64_t slice_generations;   /* generations per time slice, >= 1 */
+} cgo_server_cfg;
+
+typedef struct {
+  uint32_t struct_size;        /* = sizeof(cgo_server_info) */
+  int32_t queued, active, buckets;
+  int64_t slices, completed, hbm_used_bytes;
+} cgo_server_info;
+
+/* Start a server on the current device (its thread owns a non-blocking
+ * stream).  Errors: CGO_ERR_INVALID, CGO_ERR_NOMEM, CGO_ERR_CUDA. */
+cgo_status cgo_server_create(const cgo_server_cfg *cfg, cgo_server **out);
+
+/* Queue a solve of `prob` (created on the server's device) with params and
+ * seed; the handle is in use (CGO_ERR_BUSY for other calls) until the
+ * request finishes, after which it holds the final state (cgo_best,
+ * cgo_state_get).  Validation errors are returned here; a request whose
+ * shared-memory footprint exceeds the budget returns CGO_ERR_UNSUPPORTED. */
+cgo_status cgo_submit(cgo_server *srv, cgo_problem *prob, const cgo_params *params, uint64_t seed,
+                      uint64_t *ticket);
+
+/* Wait for a ticket (timeout_ms < 0: forever).  On CGO_OK fills the elite
+ * cost and the latency from submit to completion (seconds) and forgets the
+ * ticket; CGO_ERR_TIMEOUT leaves it pending.  Each ticket is waited once. */
+cgo_status cgo_wait(cgo_server *srv, uint64_t ticket, int32_t timeout_ms, int64_t *cost,
+                    double *latency_s);
+
+/* Counters of the request loop. */
+cgo_status cgo_server_stats(const cgo_server *srv, cgo_server_info *out);
+
+/* Finish every queued and resident request, stop the loop and free the
+ * server.  Tickets not yet waited are forgotten.  NULL is accepted. */
+cgo_status cgo_server_destroy(cgo_server *srv);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char *cgo_last_error(void);
 

@@ -62,6 +62,19 @@ class cgo_state(ctypes.Structure):
                 ("cost", _i64p), ("best_cost", _i64p)]
 
 
+class cgo_server_cfg(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("max_slots", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("smem_budget_bytes", ctypes.c_int64),
+                ("slice_generations", ctypes.c_int64)]
+
+
+class cgo_server_info(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("queued", ctypes.c_int32),
+                ("active", ctypes.c_int32), ("buckets", ctypes.c_int32),
+                ("slices", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("hbm_used_bytes", ctypes.c_int64)]
+
+
 class cgo_launch(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("warps_per_cta", ctypes.c_int32),
                 ("warps_per_member", ctypes.c_int32), ("staging", ctypes.c_int32)]
@@ -103,6 +116,11 @@ def lib() -> ctypes.CDLL:
                 "cgo_last_kernel_time": ([vp, P(c.c_double), _i64p], c.c_int),
                 "cgo_solve_static": ([P(cgo_problem_desc), P(cgo_params), c.c_uint64, vp, vp, vp],
                                      c.c_int),
+                "cgo_server_create": ([P(cgo_server_cfg), P(vp)], c.c_int),
+                "cgo_submit": ([vp, vp, P(cgo_params), c.c_uint64, P(c.c_uint64)], c.c_int),
+                "cgo_wait": ([vp, c.c_uint64, c.c_int32, _i64p, P(c.c_double)], c.c_int),
+                "cgo_server_stats": ([vp, P(cgo_server_info)], c.c_int),
+                "cgo_server_destroy": ([vp], c.c_int),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(L, name)
@@ -309,3 +327,47 @@ def solve_batch(problems: list, params: list, seeds: list, stream=None) -> None:
 
 def version() -> str:
     return lib().cgo_version().decode()
+
+
+class Server:
+    """A cgo_server: continuous batching of solve requests."""
+
+    def __init__(self, max_slots: int = 1024, hbm_budget_bytes: int = 64 << 30,
+                 smem_budget_bytes: int = 0, slice_generations: int = 2000):
+        cfg = cgo_server_cfg(ctypes.sizeof(cgo_server_cfg), max_slots, hbm_budget_bytes,
+                             smem_budget_bytes, slice_generations)
+        h = ctypes.c_void_p()
+        check(lib().cgo_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cgo_server_create")
+        self.h = h
+
+    def submit(self, prob: "Problem", params: dict, seed: int) -> int:
+        q = params_struct(params)
+        t = ctypes.c_uint64()
+        check(lib().cgo_submit(self.h, prob.h, ctypes.byref(q), int(seed), ctypes.byref(t)),
+              "cgo_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> tuple[int, float]:
+        c = ctypes.c_int64()
+        lat = ctypes.c_double()
+        check(lib().cgo_wait(self.h, int(ticket), int(timeout_ms), ctypes.byref(c),
+                             ctypes.byref(lat)), "cgo_wait")
+        return c.value, lat.value
+
+    def stats(self) -> dict:
+        i = cgo_server_info()
+        i.struct_size = ctypes.sizeof(cgo_server_info)
+        check(lib().cgo_server_stats(self.h, ctypes.byref(i)), "cgo_server_stats")
+        return dict(queued=i.queued, active=i.active, buckets=i.buckets, slices=i.slices,
+                    completed=i.completed, hbm_used_bytes=i.hbm_used_bytes)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().cgo_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -14,12 +14,13 @@
 #include <string>
 #include <vector>
 
-#include "cgo.h"
-#include "cgo_internal.h"
+#include "cgo_host.h"
 
 using namespace cgo;
+using namespace cgo::host;
 
-namespace {
+namespace cgo {
+namespace host {
 
 thread_local std::string g_err;
 
@@ -38,12 +39,6 @@ cgo_status cuda_fail(cudaError_t e, const char *what) {
   return fail(CGO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CUDA_TRY(call, what)                    \
-  do {                                          \
-    cudaError_t e_ = (call);                    \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-  } while (0)
-
 int64_t pad16(int64_t b) { return (b + 15) & ~int64_t(15); }
 
 int encoding_of(int model) {
@@ -52,55 +47,13 @@ int encoding_of(int model) {
   return CGO_ENC_PERM;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace cgo
 
-struct cgo_problem {
-  int device = 0;
-  int model = 0, n = 0, len = 0, m = 0, V = 0;
-  int64_t capacity = 0, lam0 = 0, lam1 = 0;
-  int lb = 0, ub = 0;
-  uint32_t tag = 0;
-  int32_t *d_mat0 = nullptr, *d_mat1 = nullptr, *d_vec[4] = {nullptr, nullptr, nullptr, nullptr};
-  void *d_tri = nullptr;
-  int tri16 = 0;
-  // search state
-  bool has_state = false;
-  cgo_params params{};
-  uint64_t seed = 0;
-  uint32_t enabled = 0;
-  int P_alloc = 0;
-  int32_t *d_cur = nullptr, *d_bestsol = nullptr;
-  int64_t *d_cost = nullptr, *d_best = nullptr;
-  DevAos *d_aos = nullptr;  // [2]
-  DevSync *d_sync = nullptr;
-  int aos_cur = 0;
-  int64_t g = 0;
-  // launch shape
-  int warps_override = 0, wpm_override = 0, staging_override = 0;
-  int last_warps = 0, last_wpm = 0, last_staging = 0;
-  // events around the last evolve launch (kernel time on the launching stream)
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  bool timed = false;
-  int64_t timed_gens = 0;
-  // test-only fault injection
-  uint32_t phantom_members = 0;
-  uint64_t timeout_ns = 10ull * 1000 * 1000 * 1000;
-  std::atomic<int> busy{0};
-};
 
-namespace {
+namespace cgo {
+namespace host {
 
-struct Guard {
-  cgo_problem *p;
-  bool ok;
-  explicit Guard(const cgo_problem *q) : p(const_cast<cgo_problem *>(q)) {
-    int z = 0;
-    ok = p->busy.compare_exchange_strong(z, 1);
-  }
-  ~Guard() {
-    if (ok) p->busy.store(0);
-  }
-};
 
 cudaError_t copy_in(int32_t **dst, const int32_t *src, int64_t count, bool on_device) {
   const int64_t bytes = pad16(count * 4);
@@ -141,8 +94,8 @@ int64_t abssum(const std::vector<int32_t> &v) {
   return s;
 }
 
-const double kLimit = 4.6e18;
-int64_t g_batch_slice = 2000;  // generations per batched time slice  // 2^62: every cost and delta fits in int64 with room
+const double kLimit = 4.6e18;  // 2^62: every cost and delta fits in int64 with room
+int64_t g_batch_slice = 2000;  // generations per batched time slice
 
 void free_state(cgo_problem *p) {
   cudaFree(p->d_cur);
@@ -378,11 +331,55 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void *g_static_ptr[kMaxDevices] = {};
 
-}  // namespace
+// Batched instances: every member in one CTA; one warp per member by
+// default (many members per CTA keep the SMs busy).  The shared-memory size
+// class (1/8, 1/4, 1/2 or all of the budget) groups instances into launches.
+cgo_status batch_shape(cgo_problem *p, const cgo_params &q, KInst &h, int *wpm_out, int *warps_out,
+                       int64_t *smem_out, int64_t *class_out) {
+  const int64_t optin = max_smem_optin() - 1024;  // the kernel's static shared memory
+  const int wpm = p->wpm_override > 0 ? p->wpm_override : 1;
+  int warps = p->warps_override > 0 ? p->warps_override : kMaxWarps;
+  warps = std::max(wpm, std::min(warps, q.population * wpm));
+  warps = std::min(warps, kMaxWarps) / wpm * wpm;
+  const int64_t staged = batch_smem_bytes(h, warps, wpm, true);
+  const int64_t global = batch_smem_bytes(h, warps, wpm, false);
+  const bool use_smem = staged <= optin && p->staging_override != STAGE_GLOBAL;
+  if (p->staging_override == STAGE_SMEM && !use_smem)
+    return fail(CGO_ERR_UNSUPPORTED, "instance data do not fit in shared memory");
+  const int64_t need = use_smem ? staged : global;
+  if (need > optin)
+    return fail(CGO_ERR_UNSUPPORTED, "population %d x length %d does not fit in one CTA", q.population,
+                p->len);
+  h.shared_bytes = use_smem ? instance_data_bytes(h) : 0;
+  int64_t cls = optin;
+  for (int64_t c = optin / 8; c < optin; c *= 2)
+    if (need <= c) {
+      cls = c;
+      break;
+    }
+  *wpm_out = wpm;
+  *warps_out = warps;
+  *smem_out = need;
+  *class_out = cls;
+  return CGO_OK;
+}
+
+DevAos initial_aos(const cgo_params &q, uint32_t en) {
+  DevAos a;
+  memset(&a, 0, sizeof a);
+  a.T = q.T0_q32;
+  for (int k = 0; k < kNops; ++k) a.w_op[k] = ((en >> k) & 1u) ? q.op_w0_q16[k] : 0u;
+  for (int k = 0; k < 3; ++k) a.w_k[k] = q.k_w0_q16[k];
+  return a;
+}
+
+}  // namespace host
+}  // namespace cgo
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-namespace {
+namespace cgo {
+namespace host {
 
 cgo_status static_scratch(void **out) {
   int dev = 0;
@@ -401,7 +398,8 @@ cgo_status static_scratch(void **out) {
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
-}  // namespace
+}  // namespace host
+}  // namespace cgo
 
 extern "C" {
 
@@ -456,9 +454,9 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
       const int64_t tb = pad16(n * (n + 1) / 2 * (p->tri16 ? 2 : 4));
       if ((e = cudaMalloc(&p->d_tri, (size_t)tb)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
       if ((e = cudaMemset(p->d_tri, 0, (size_t)tb)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
-      if ((e = build_triangle(p->d_mat0, (int)n, p->tri16, p->d_tri, 0)) != cudaSuccess)
+      if ((e = build_triangle(p->d_mat0, (int)n, p->tri16, p->d_tri, cudaStreamPerThread)) != cudaSuccess)
         return bail(cuda_fail(e, "triangle"));
-      if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+      if ((e = cudaStreamSynchronize(cudaStreamPerThread)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
       break;
     }
     case CGO_QAP: {
@@ -628,11 +626,7 @@ cgo_status cgo_solve(cgo_problem *p, const cgo_params *q, uint64_t seed, void *s
   p->has_state = false;
   KInst h = base_kinst(p);
   CUDA_TRY(launch_init(h, st), "init launch");
-  DevAos a0;
-  memset(&a0, 0, sizeof a0);
-  a0.T = q->T0_q32;
-  for (int i = 0; i < kNops; ++i) a0.w_op[i] = ((en >> i) & 1u) ? q->op_w0_q16[i] : 0u;
-  for (int i = 0; i < 3; ++i) a0.w_k[i] = q->k_w0_q16[i];
+  const DevAos a0 = initial_aos(*q, en);
   h.aos_out = p->d_aos;
   CUDA_TRY(launch_init_aos(h, a0, st), "init launch");
   CUDA_TRY(cudaStreamSynchronize(st), "init");
@@ -780,7 +774,6 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
   }
   int dev = 0;
   cudaGetDevice(&dev);
-  const int64_t optin = max_smem_optin() - 1024;  // the kernel's static shared memory
   // validate, allocate state, and describe each problem
   std::vector<KInst> hk((size_t)count);
   std::vector<DevAos> a0((size_t)count);
@@ -810,29 +803,10 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
     h.aos_in = h.aos_out = p->d_aos;
     h.G_total = per[i].generations;
     h.local_sync = 1;
-    // launch shape: one warp per member (many members per CTA keep the
-    // SMs busy), every member of the instance in the CTA
-    int wpm = p->wpm_override > 0 ? p->wpm_override : 1;
-    int warps = p->warps_override > 0 ? p->warps_override : kMaxWarps;
-    warps = std::max(wpm, std::min(warps, ((per[i].population * wpm + wpm - 1) / wpm) * wpm));
-    warps = std::min(warps, kMaxWarps) / wpm * wpm;
-    const int64_t staged = batch_smem_bytes(h, warps, wpm, true);
-    const int64_t global = batch_smem_bytes(h, warps, wpm, false);
-    bool use_smem = staged <= optin && p->staging_override != STAGE_GLOBAL;
-    if (p->staging_override == STAGE_SMEM && !use_smem)
-      return fail(CGO_ERR_UNSUPPORTED, "problem %d: instance data do not fit in shared memory", i);
-    const int64_t need = use_smem ? staged : global;
-    if (need > optin)
-      return fail(CGO_ERR_UNSUPPORTED, "problem %d: population %d x length %d does not fit in one CTA", i,
-                  per[i].population, p->len);
-    h.shared_bytes = use_smem ? instance_data_bytes(h) : 0;
-    // shared-memory size class: 1/8, 1/4, 1/2 or all of the budget
-    int64_t cls = optin;
-    for (int64_t c = optin / 8; c < optin; c *= 2)
-      if (need <= c) {
-        cls = c;
-        break;
-      }
+    int wpm = 1, warps = 1;
+    int64_t need = 0, cls = 0;
+    if ((s = batch_shape(p, per[i], h, &wpm, &warps, &need, &cls)) != CGO_OK)
+      return fail(s, "problem %d: %s", i, cgo_last_error());
     int b = -1;
     for (size_t k = 0; k < buckets.size(); ++k)
       if (buckets[k].model == p->model && buckets[k].tri16 == p->tri16 && buckets[k].wpm == wpm &&
@@ -844,25 +818,22 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
     }
     buckets[(size_t)b].members.push_back(i);
     hk[(size_t)i] = h;
-    DevAos &a = a0[(size_t)i];
-    memset(&a, 0, sizeof a);
-    a.T = per[i].T0_q32;
-    for (int k = 0; k < kNops; ++k) a.w_op[k] = ((en >> k) & 1u) ? per[i].op_w0_q16[k] : 0u;
-    for (int k = 0; k < 3; ++k) a.w_k[k] = per[i].k_w0_q16[k];
+    a0[(size_t)i] = initial_aos(per[i], en);
     Gmax = std::max<int64_t>(Gmax, per[i].generations);
   }
   // device copies of the descriptions, work lists and counters
   const size_t nb = buckets.size();
   KInst *d_k = nullptr;
   DevAos *d_a0 = nullptr;
-  int *d_lists = nullptr, *d_next = nullptr;
+  int *d_lists = nullptr, *d_next = nullptr, *d_counts = nullptr;
   auto release = [&]() {
     cudaFree(d_k);
     cudaFree(d_a0);
     cudaFree(d_lists);
     cudaFree(d_next);
+    cudaFree(d_counts);
   };
-  std::vector<int> lists;
+  std::vector<int> lists, counts;
   std::vector<size_t> list_off;
   for (auto &bk : buckets) {
     // longest first: larger instances start early, small ones fill the tail
@@ -872,19 +843,22 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
       return wx > wy;
     });
     list_off.push_back(lists.size());
+    counts.push_back((int)bk.members.size());
     lists.insert(lists.end(), bk.members.begin(), bk.members.end());
   }
   cudaError_t e;
   if ((e = cudaMalloc((void **)&d_k, sizeof(KInst) * (size_t)count)) != cudaSuccess ||
       (e = cudaMalloc((void **)&d_a0, sizeof(DevAos) * (size_t)count)) != cudaSuccess ||
       (e = cudaMalloc((void **)&d_lists, sizeof(int) * lists.size())) != cudaSuccess ||
-      (e = cudaMalloc((void **)&d_next, sizeof(int) * nb)) != cudaSuccess) {
+      (e = cudaMalloc((void **)&d_next, sizeof(int) * nb)) != cudaSuccess ||
+      (e = cudaMalloc((void **)&d_counts, sizeof(int) * nb)) != cudaSuccess) {
     release();
     return cuda_fail(e, "batch descriptors");
   }
   if ((e = cudaMemcpyAsync(d_k, hk.data(), sizeof(KInst) * (size_t)count, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_a0, a0.data(), sizeof(DevAos) * (size_t)count, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_lists, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_counts, counts.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = launch_init_batch(d_k, d_a0, count, st)) != cudaSuccess) {
     release();
     return cuda_fail(e, "batch init");
@@ -936,7 +910,7 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
         ce = cudaStreamWaitEvent(side[b], fork, 0);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(d_next + b, 0, sizeof(int), side[b]);
         if (ce == cudaSuccess)
-          ce = launch_batch(bk.model, bk.tri16, d_k, d_lists + list_off[b], (int)bk.members.size(),
+          ce = launch_batch(bk.model, bk.tri16, d_k, d_lists + list_off[b], d_counts + b,
                             d_next + b, bk.warps, bk.wpm, bk.smem, grids[b], slice,
                             probs[0]->timeout_ns, side[b]);
         if (ce == cudaSuccess) ce = cudaEventRecord(evs[b], side[b]);

@@ -1,0 +1,85 @@
+// Host-runtime internals shared by the C-ABI translation units (the single
+// and batched solves in cgo_api.cu, the serving loop in cgo_server.cu).
+#pragma once
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include "cgo.h"
+#include "cgo_internal.h"
+
+// A problem handle: device copies of the instance, the search state of its
+// last solve, launch-shape overrides and test hooks.
+struct cgo_problem {
+  int device = 0;
+  int model = 0, n = 0, len = 0, m = 0, V = 0;
+  int64_t capacity = 0, lam0 = 0, lam1 = 0;
+  int lb = 0, ub = 0;
+  uint32_t tag = 0;
+  int32_t *d_mat0 = nullptr, *d_mat1 = nullptr, *d_vec[4] = {nullptr, nullptr, nullptr, nullptr};
+  void *d_tri = nullptr;
+  int tri16 = 0;
+  // search state
+  bool has_state = false;
+  cgo_params params{};
+  uint64_t seed = 0;
+  uint32_t enabled = 0;
+  int P_alloc = 0;
+  int32_t *d_cur = nullptr, *d_bestsol = nullptr;
+  int64_t *d_cost = nullptr, *d_best = nullptr;
+  cgo::DevAos *d_aos = nullptr;  // [2]
+  cgo::DevSync *d_sync = nullptr;
+  int aos_cur = 0;
+  int64_t g = 0;
+  // launch shape
+  int warps_override = 0, wpm_override = 0, staging_override = 0;
+  int last_warps = 0, last_wpm = 0, last_staging = 0;
+  // events around the last evolve launch (kernel time on the launching stream)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  int64_t timed_gens = 0;
+  // test-only fault injection
+  uint32_t phantom_members = 0;
+  uint64_t timeout_ns = 10ull * 1000 * 1000 * 1000;
+  std::atomic<int> busy{0};
+};
+
+namespace cgo {
+namespace host {
+
+cgo_status fail(cgo_status s, const char *fmt, ...);
+cgo_status cuda_fail(cudaError_t e, const char *what);
+int encoding_of(int model);
+int64_t pad16(int64_t b);
+extern int64_t g_batch_slice;
+
+// Exclusive use of a handle for the duration of a call (ok = false if busy).
+struct Guard {
+  cgo_problem *p;
+  bool ok;
+  explicit Guard(const cgo_problem *q) : p(const_cast<cgo_problem *>(q)) {
+    int z = 0;
+    ok = p->busy.compare_exchange_strong(z, 1);
+  }
+  ~Guard() {
+    if (ok) p->busy.store(0);
+  }
+};
+
+cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *enabled);
+cgo_status ensure_state(cgo_problem *p, int P);
+KInst base_kinst(const cgo_problem *p);
+// launch shape of a batched (CTA-local) instance: warps per member, warps
+// per CTA, shared memory of a unit; fails if the instance cannot fit a CTA
+cgo_status batch_shape(cgo_problem *p, const cgo_params &q, KInst &h, int *wpm, int *warps,
+                       int64_t *smem, int64_t *smem_class);
+DevAos initial_aos(const cgo_params &q, uint32_t enabled);
+
+}  // namespace host
+}  // namespace cgo
+
+#define CUDA_TRY(call, what)                              \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cgo::host::cuda_fail(e_, what); \
+  } while (0)

@@ -88,9 +88,9 @@ cudaError_t launch_copy_elite(const DevAos *d_aos, const int32_t *d_bestsol, int
                               int32_t *out_sol, int64_t *out_cost, cudaStream_t st);
 cudaError_t launch_init_batch(const KInst *d_insts, const DevAos *d_a0s, int count, cudaStream_t st);
 int batch_ctas_per_sm(int model, int tri16, int warps, int wpm, int64_t smem_bytes);
-cudaError_t launch_batch(int model, int tri16, const KInst *d_insts, const int *d_list, int count,
-                         int *d_next, int warps, int wpm, int64_t smem_bytes, int grid,
-                         int64_t slice, uint64_t timeout_ns, cudaStream_t st);
+cudaError_t launch_batch(int model, int tri16, const KInst *d_insts, const int *d_list,
+                         const int *d_count, int *d_next, int warps, int wpm, int64_t smem_bytes,
+                         int grid, int64_t slice, uint64_t timeout_ns, cudaStream_t st);
 int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged);
 // shared-memory needs of the evolve kernel
 int64_t smem_per_warp(const KInst &h);

@@ -1083,11 +1083,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
 // have reached their generation budget are skipped.
 template <int MODEL, bool T16, int WPM>
 __global__ void __launch_bounds__(kMaxWarps * 32, 1)
-    batch_kernel(const KInst *__restrict__ insts, const int *__restrict__ list, int count,
-                 int *next, int warps, int64_t slice, uint64_t timeout_ns) {
+    batch_kernel(const KInst *__restrict__ insts, const int *__restrict__ list,
+                 const int *__restrict__ count_ptr, int *next, int warps, int64_t slice,
+                 uint64_t timeout_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ KInst sI;
   __shared__ int su;
+  const int count = *count_ptr;
   for (;;) {
     if (threadIdx.x == 0) su = atomicAdd(next, 1);
     __syncthreads();
@@ -1459,15 +1461,15 @@ int batch_ctas_per_sm(int model, int tri16, int warps, int wpm, int64_t smem_byt
   return per_sm;
 }
 
-cudaError_t launch_batch(int model, int tri16, const KInst *d_insts, const int *d_list, int count,
-                         int *d_next, int warps, int wpm, int64_t smem_bytes, int grid,
-                         int64_t slice, uint64_t timeout_ns, cudaStream_t st) {
+cudaError_t launch_batch(int model, int tri16, const KInst *d_insts, const int *d_list,
+                         const int *d_count, int *d_next, int warps, int wpm, int64_t smem_bytes,
+                         int grid, int64_t slice, uint64_t timeout_ns, cudaStream_t st) {
   const void *fn = pick_batch(model, tri16, wpm);
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
-  void *args[] = {(void *)&d_insts, (void *)&d_list, (void *)&count, (void *)&d_next,
+  void *args[] = {(void *)&d_insts, (void *)&d_list, (void *)&d_count, (void *)&d_next,
                   (void *)&warps, (void *)&slice, (void *)&timeout_ns};
   return cudaLaunchKernel(fn, dim3(grid), dim3(warps * 32), args, (size_t)smem_bytes, st);
 }
