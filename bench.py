@@ -53,6 +53,8 @@ def workload(name: str):
         inst = I.qap_grid(64, 0)
         cfg = dict(P=256, C=128, G=100000, op_mask=1, w_op=[65536, 0, 0, 0, 0, 0, 0, 0])
         desc = "qap64-grid P=256 C=128 G=100000 ops=swap"
+    elif name == "serve":
+        return None, dict(P=32, C=128, G=20000), "serve-poisson200x60s mix+15%cvrptw P=32 C=128 G=20000"
     elif name == "batch512":
         return None, dict(P=32, C=128, G=20000), "batch512-mix P=32 C=128 G=20000"
     else:
@@ -182,6 +184,11 @@ def main():
     ap.add_argument("--ref-generations", type=int, default=100)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--batch-class", default="mix")
+    ap.add_argument("--wpm", type=int, default=0, help="warps per member override (batched)")
+    ap.add_argument("--slice", type=int, default=2000)
+    ap.add_argument("--seq-sample", type=int, default=24)
     ap.add_argument("--generations", type=int, default=0,
                     help="override G (small cases for profiler captures)")
     args = ap.parse_args()
@@ -206,8 +213,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    if args.workload == "batch512":
-        bench_batch(args, rank, world, local, cgo, torch, dist, barrier)
+    if args.workload in ("batch512", "serve"):
+        fn = bench_batch if args.workload == "batch512" else bench_serve
+        fn(args, rank, world, local, cgo, torch, dist, barrier)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -309,7 +317,17 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
     _, cfg, desc = workload("batch512")
     G = args.generations if args.generations > 0 else cfg["G"]
     mix = [dict(x, tag=i) for i, x in enumerate(I.batch_mix(512, 0))]
+    if args.batch_class != "mix":
+        cls = {"tsp": I.TSP, "knapsack": I.KNAPSACK, "gap": I.GAP, "cvrptw": I.CVRPTW}[args.batch_class]
+        if cls == I.CVRPTW:
+            mix = [dict(x, tag=i) for i, x in enumerate(I.serving_pool(0)[512:])]
+        else:
+            mix = [x for x in mix if x["model"] == cls]
+        desc = desc.replace("batch512-mix", "batch-%s%d" % (args.batch_class, len(mix)))
     probs = [cgo.Problem(x) for x in mix]
+    if args.wpm:
+        for pr in probs:
+            pr.set_launch(0, 0, args.wpm)
     params = []
     for pr in probs:
         q = pr.default_params()
@@ -373,9 +391,138 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
                            "solves_per_s_batched": solves_s,
                            "solves_per_s_one_launch_per_solve": seq_solves_s,
                            "batched_over_sequential": solves_s / seq_solves_s,
-                           "sequential_sample": "%d of 512 instances" % len(sample)},
+                           "sequential_sample": "%d of %d instances" % (len(sample), len(mix)),
+                           "launch": list(probs[0].get_launch())},
                 "e2e": {"value": evals * world / e2e_s, "unit": "evals/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": None, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
+def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
+    """Serving: Poisson arrivals at 200 requests/s for 60 s (sizes from the
+    batch mix, 15% CVRPTW with 100 customers); each request is created from
+    host arrays when it arrives (host->device copy), submitted to the
+    continuous-batching server and waited for; latency = completion - arrival.
+    The one-launch-per-solve form is timed on sampled requests (cgo_solve of
+    each in turn) and its queueing under the same arrival trace follows from
+    the Lindley recursion W_i = max(0, W_(i-1) + S_(i-1) - A_i) with those
+    measured service times."""
+    import threading
+    _, cfg, desc = workload("serve")
+    G = args.generations if args.generations > 0 else cfg["G"]
+    duration = args.serve_seconds
+    pool = I.serving_pool(0)
+    trace = I.poisson_arrivals(200.0, duration, 7)
+    params_of = {}
+
+    def params_for(k):
+        if k not in params_of:
+            pr = cgo.Problem(dict(pool[k], tag=k))
+            q = pr.default_params()
+            q.update(P=cfg["P"], C=cfg["C"], G=G)
+            params_of[k] = q
+            pr.close()
+        return params_of[k]
+
+    for k in set(k for _, k in trace):
+        params_for(k)
+    srv = cgo.Server(max_slots=4096, hbm_budget_bytes=96 << 30, slice_generations=args.slice)
+    # warm-up: a few requests end to end
+    warm = [cgo.Problem(dict(pool[k], tag=k)) for k in (0, 1, 2, 512)]
+    for pr, k in zip(warm, (0, 1, 2, 512)):
+        srv.wait(srv.submit(pr, params_for(k), 1), -1)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    probs = [None] * len(trace)
+    tickets = [None] * len(trace)
+    results = [None] * len(trace)
+    t_start = time.perf_counter()
+
+    def producer():
+        for i, (ta, k) in enumerate(trace):
+            now = time.perf_counter() - t_start
+            if ta > now:
+                time.sleep(ta - now)
+            pr = cgo.Problem(dict(pool[k], tag=i))
+            probs[i] = pr
+            tickets[i] = srv.submit(pr, params_for(k), 1 + i)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    done_at = [0.0] * len(trace)
+    for i in range(len(trace)):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        cost, lat = srv.wait(tickets[i], -1)
+        results[i] = (cost, lat)
+        done_at[i] = time.perf_counter() - t_start
+    th.join()
+    wall = max(done_at) - trace[0][0]
+    clocks = sampler.stop() if rank == 0 else None
+    stats = srv.stats()
+    srv.close()
+    lats = np.array([r[1] for r in results])
+    served_solves_s = len(trace) / wall
+    evals = sum(params_for(k)["P"] * params_for(k)["C"] * G for _, k in trace)
+    # one launch per solve: per-class service times measured on a stratified
+    # sample of the trace's requests, queueing by the Lindley recursion
+    def cls_of(k):
+        return "cvrptw" if k >= 512 else ("tsp", "qap", "knapsack", "gap")[pool[k]["model"]]
+    by_cls = {}
+    for i, (_, k) in enumerate(trace):
+        by_cls.setdefault(cls_of(k), []).append(i)
+    per = max(2, args.seq_sample // max(1, len(by_cls)))
+    service = {}
+    for c, idx in by_cls.items():
+        for i in idx[::max(1, len(idx) // per)][:per]:
+            k = trace[i][1]
+            pr = cgo.Problem(dict(pool[k], tag=i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pr.solve(params_for(k), 1 + i)
+            service.setdefault(c, []).append(time.perf_counter() - t0)
+            pr.close()
+    mean_cls = {c: float(np.mean(v)) for c, v in service.items()}
+    overall = float(np.mean([mean_cls[cls_of(k)] for _, k in trace]))
+    rng_pick = [x for v in service.values() for x in v]
+    W, prev_t, prev_s, seq_lat = 0.0, None, 0.0, []
+    for ta, k in trace:
+        s_i = mean_cls[cls_of(k)]
+        if prev_t is not None:
+            W = max(0.0, W + prev_s - (ta - prev_t))
+        seq_lat.append(W + s_i)
+        prev_t, prev_s = ta, s_i
+    seq_lat = np.array(seq_lat)
+    seq_solves_s = 1.0 / overall
+    for pr in probs + warm:
+        if pr is not None:
+            pr.close()
+    if rank == 0:
+        line = {"metric": "served_solves_per_s", "value": served_solves_s, "unit": "solves/s",
+                "n_gpus": world, "steps": 1, "warmup": len(warm), "ms_per_step": 1000 * wall,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic",
+                "config": {"workload": desc.replace("G=20000", "G=%d" % G).replace(
+                               "x60s", "x%ds" % int(duration)),
+                           "requests": len(trace), "slice_generations": args.slice,
+                           "move_evals_per_s": evals / wall,
+                           "latency_p50_s": float(np.percentile(lats, 50)),
+                           "latency_p99_s": float(np.percentile(lats, 99)),
+                           "latency_max_s": float(lats.max()),
+                           "one_launch_per_solve": {
+                               "solves_per_s": seq_solves_s,
+                               "latency_p50_s": float(np.percentile(seq_lat, 50)),
+                               "latency_p99_s": float(np.percentile(seq_lat, 99)),
+                               "service_s_by_class": mean_cls,
+                               "how": "per-class service times of %d sampled requests, Lindley "
+                                      "recursion over the same arrivals" % len(rng_pick)},
+                           "served_over_one_launch_per_solve": served_solves_s / seq_solves_s,
+                           "server": stats},
+                "e2e": {"value": served_solves_s, "unit": "solves/s",
+                        "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
                 "gpu_launches": None, "clocks": clocks}
         print(json.dumps(line), flush=True)
 

@@ -228,6 +228,39 @@ def batch_mix(count: int = 512, index: int = 0) -> list[dict]:
     return out
 
 
+def serving_pool(index: int = 0, cvrptw_count: int = 96) -> list[dict]:
+    """Instance pool of the serving workload: the 512-instance batch mix
+    (TSP / knapsack / GAP) followed by `cvrptw_count` CVRPTW instances with
+    100 customers."""
+    pool = batch_mix(512, index)
+    for i in range(cvrptw_count):
+        pool.append(cvrptw(100, 700000 + 1000 * index + i))
+    return pool
+
+
+def poisson_arrivals(rate: float = 200.0, duration: float = 60.0, index: int = 7,
+                     cvrptw_frac: float = 0.15, pool_mix: int = 512,
+                     pool_cvrptw: int = 96) -> list[tuple[float, int]]:
+    """Arrival times (exponential inter-arrivals at `rate` per second over
+    `duration` seconds) and, for each, an index into serving_pool(): a
+    CVRPTW instance with probability `cvrptw_frac`, else a uniformly drawn
+    member of the batch mix."""
+    st = Stream(index, 10)
+    out = []
+    t = 0.0
+    while True:
+        t += -math.log(float(st.unit(1)[0])) / rate
+        if t >= duration:
+            break
+        u = int(st.ints(0, 999, 1)[0])
+        if u < int(round(cvrptw_frac * 1000)):
+            k = pool_mix + int(st.ints(0, pool_cvrptw - 1, 1)[0])
+        else:
+            k = int(st.ints(0, pool_mix - 1, 1)[0])
+        out.append((t, k))
+    return out
+
+
 def poisson_trace(rate: float = 200.0, duration: float = 60.0, index: int = 7,
                   cvrptw_frac: float = 0.15) -> list[dict]:
     """Serving trace: exponential inter-arrivals (rate per second) over
