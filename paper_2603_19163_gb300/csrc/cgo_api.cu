@@ -212,6 +212,8 @@ KInst base_kinst(const cgo_problem *p) {
   h.vec2 = p->d_vec[2];
   h.vec3 = p->d_vec[3];
   h.tri = p->d_tri;
+  h.node = p->d_node;
+  h.cv32 = p->cv32;
   const cgo_params &q = p->params;
   h.P = q.population;
   h.members = q.population;
@@ -498,10 +500,16 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
       if ((double)p->lam1 * late + (double)p->lam0 * ((double)abssum(v[0]) + std::fabs((double)d->capacity) * N) +
               (double)(len + 1) * maxd > kLimit)
         return bail(fail(CGO_ERR_INVALID, "CVRPTW data could overflow an int64 cost"));
+      // route quantities (time, lateness, distance, load) fit in int32?
+      p->cv32 = (late < 2.0e9 && (double)abssum(v[0]) < 2.0e9 && (double)N * maxd < 2.0e9) ? 1 : 0;
+      std::vector<int4> node((size_t)N);
+      for (int64_t k = 0; k < N; ++k) node[(size_t)k] = make_int4(v[1][(size_t)k], v[2][(size_t)k], v[3][(size_t)k], v[0][(size_t)k]);
       cudaError_t e;
       if ((e = copy_in(&p->d_mat0, a.data(), N * N, false)) != cudaSuccess) return bail(cuda_fail(e, "copy d"));
       for (int k = 0; k < 4; ++k)
         if ((e = copy_in(&p->d_vec[k], v[k].data(), N, false)) != cudaSuccess) return bail(cuda_fail(e, "copy vectors"));
+      if ((e = copy_in((int32_t **)&p->d_node, (const int32_t *)node.data(), 4 * N, false)) != cudaSuccess)
+        return bail(cuda_fail(e, "copy nodes"));
       break;
     }
     case CGO_GAP: {
@@ -537,6 +545,7 @@ cgo_status cgo_problem_destroy(cgo_problem *p) {
   cudaFree(p->d_mat1);
   for (int i = 0; i < 4; ++i) cudaFree(p->d_vec[i]);
   cudaFree(p->d_tri);
+  cudaFree(p->d_node);
   delete p;
   return CGO_OK;
 }

@@ -19,6 +19,8 @@ struct cgo_problem {
   int32_t *d_mat0 = nullptr, *d_mat1 = nullptr, *d_vec[4] = {nullptr, nullptr, nullptr, nullptr};
   void *d_tri = nullptr;
   int tri16 = 0;
+  int4 *d_node = nullptr;  // CVRPTW packed node data
+  int cv32 = 0;
   // search state
   bool has_state = false;
   cgo_params params{};

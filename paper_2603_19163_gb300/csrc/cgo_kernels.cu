@@ -79,7 +79,7 @@ int64_t instance_data_bytes(const KInst &h) {
     case GAP: return 2 * align16((int64_t)h.m * h.n * 4) + align16((int64_t)h.m * 4);
     case CVRPTW: {
       const int64_t N = h.n + 1;
-      return align16(N * N * 4) + 4 * align16(N * 4);
+      return align16(N * N * 4) + N * 16;
     }
   }
   return 0;
@@ -103,7 +103,9 @@ struct View {
   const int32_t *w, *v;        // knapsack
   const int32_t *gc, *gr, *gcap;  // GAP
   const int32_t *rd, *dem, *rdy, *due, *svc;  // CVRPTW: travel (n+1)^2, vectors n+1
+  const int4 *node;                           // CVRPTW: {ready, due, service, demand}
   long long lam1;
+  bool cv32;
 };
 
 template <int NO>
@@ -261,35 +263,43 @@ __device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
 // a separator.  Per route from the depot at t = 0: t = max(t + d, ready),
 // late += max(0, t - due), t += service; back at the depot t += d and
 // late += max(0, t - due_0); empty routes cost nothing.
-template <class Look>
-__device__ long long cvrptw_routes(const View &X, Look V, int L, int R) {
+template <class Look, class Q>
+__device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int L, int R) {
   const int n = X.n, N = n + 1;
-  long long total = 0, t = 0, load = 0, dist = 0, late = 0;
+  long long total = 0;
+  Q t = 0, load = 0, dist = 0, late = 0;
   int prev = 0;
+  const Q due0 = (Q)X.node[0].y;
   for (int q = L; q <= R; ++q) {
     const int sym = q < R ? V(q) : n;
     if (sym >= n) {
       if (prev != 0) {
-        const long long back = X.rd[(size_t)prev * N];
+        const Q back = (Q)X.rd[(size_t)prev * N];
         dist += back;
         t += back;
-        late += overp(t - X.due[0]);
-        total += dist + X.lam0 * overp(load - X.cap) + X.lam1 * late;
+        late += max(t - due0, (Q)0);
+        total += (long long)dist + X.lam0 * overp((long long)load - X.cap) + X.lam1 * (long long)late;
       }
       t = load = dist = late = 0;
       prev = 0;
     } else {
       const int c = sym + 1;
-      const long long dd = X.rd[(size_t)prev * N + c];
+      const int4 nd = X.node[c];  // ready, due, service, demand
+      const Q dd = (Q)X.rd[(size_t)prev * N + c];
       dist += dd;
-      t = max(t + dd, (long long)X.rdy[c]);
-      late += overp(t - X.due[c]);
-      t += X.svc[c];
-      load += X.dem[c];
+      t = max(t + dd, (Q)nd.x);
+      late += max(t - (Q)nd.y, (Q)0);
+      t += (Q)nd.z;
+      load += (Q)nd.w;
       prev = c;
     }
   }
   return total;
+}
+
+template <class Look>
+__device__ __forceinline__ long long cvrptw_routes(const View &X, Look V, int L, int R, bool q32) {
+  return q32 ? cvrptw_routes_t<Look, int>(X, V, L, R) : cvrptw_routes_t<Look, long long>(X, V, L, R);
 }
 
 // Delta of one move on the (virtual) sequence: only the routes that overlap
@@ -305,7 +315,7 @@ __device__ long long cvrptw_step(const View &X, const PermEl *sol, const PMove &
   while (L > 0 && Vo(L - 1) < n) --L;
   int R = mv.b4;
   while (R < m && Vo(R) < n) ++R;
-  return cvrptw_routes(X, Vn, L, R) - cvrptw_routes(X, Vo, L, R);
+  return cvrptw_routes(X, Vn, L, R, X.cv32) - cvrptw_routes(X, Vo, L, R, X.cv32);
 }
 
 // ------------------------------------------------- candidate evaluation
@@ -1003,6 +1013,8 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.rdy = I.vec1;
   X.due = I.vec2;
   X.svc = I.vec3;
+  X.node = I.node;
+  X.cv32 = I.cv32 != 0;
   X.lam1 = I.lam1;
   if (!staged) return X;
   auto copy = [&](const void *src, int64_t bytes, int64_t off) {
@@ -1039,12 +1051,9 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
       break;
     }
     case CVRPTW: {
-      const int64_t N = I.n + 1, b = align16(N * N * 4), v = align16(N * 4);
+      const int64_t N = I.n + 1, b = align16(N * N * 4);
       X.rd = (const int32_t *)copy(I.mat0, b, 0);
-      X.dem = (const int32_t *)copy(I.vec0, v, b);
-      X.rdy = (const int32_t *)copy(I.vec1, v, b + v);
-      X.due = (const int32_t *)copy(I.vec2, v, b + 2 * v);
-      X.svc = (const int32_t *)copy(I.vec3, v, b + 3 * v);
+      X.node = (const int4 *)copy(I.node, N * 16, b);
       break;
     }
     case GAP: {
@@ -1154,11 +1163,8 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
       X.lam0 = I.lam0;
       X.lam1 = I.lam1;
       X.rd = I.mat0;
-      X.dem = I.vec0;
-      X.rdy = I.vec1;
-      X.due = I.vec2;
-      X.svc = I.vec3;
-      return cvrptw_routes(X, [&](int q) { return (int)x[q]; }, 0, I.len);
+      X.node = I.node;
+      return cvrptw_routes(X, [&](int q) { return (int)x[q]; }, 0, I.len, false);
     }
     case GAP: {
       for (int j = 0; j < n; ++j) s += I.mat0[(size_t)x[j] * n + j];
