@@ -229,6 +229,9 @@ def main():
     stream = torch.cuda.Stream()
     prob = cgo.Problem(inst)
     params = lib_params(prob, cfg)
+    from paper_2603_19163_gb300.autotune import Autotuner
+    tuner = Autotuner(trial_generations=min(cfg["G"], 500))
+    shape = tuner.tune_solve(prob, params, seed)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     with torch.cuda.stream(stream):
@@ -295,7 +298,11 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64",
                 "data": "synthetic",
                 "config": {"workload": desc, "l2": "flushed between steps (512 MB write)",
-                           "launch": list(prob.get_launch()), "best_cost": int(best_cost),
+                           "launch": {"warps_per_cta": shape[0], "warps_per_member": shape[1],
+                                      "staging": ["auto", "smem", "global"][shape[2]],
+                                      "chosen_by": "autotuner (%d trial shapes)" % len(
+                                          tuner.solve_shapes(params))},
+                           "best_cost": int(best_cost),
                            "gens_per_s": cfg["G"] / (total_ms / args.steps / 1000.0)},
                 "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
@@ -325,15 +332,21 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
             mix = [x for x in mix if x["model"] == cls]
         desc = desc.replace("batch512-mix", "batch-%s%d" % (args.batch_class, len(mix)))
     probs = [cgo.Problem(x) for x in mix]
-    if args.wpm:
-        for pr in probs:
-            pr.set_launch(0, 0, args.wpm)
     params = []
     for pr in probs:
         q = pr.default_params()
         q.update(P=cfg["P"], C=cfg["C"], G=G)
         params.append(q)
     seeds = [1000 * rank + 1 + i for i in range(len(mix))]
+    if args.wpm:
+        for pr in probs:
+            pr.set_launch(0, 0, args.wpm)
+        tuned = {"fixed_wpm": args.wpm}
+    else:
+        from paper_2603_19163_gb300.autotune import Autotuner
+        tuned = {str(k): {"warps_per_member": v[0], "trial_evals_per_s": v[1]}
+                 for k, v in Autotuner(trial_generations=min(G, 300)).tune_batch(
+                     probs, params).items()}
     stream = torch.cuda.Stream()
     for _ in range(args.warmup):
         cgo.solve_batch(probs, params, seeds, stream)
@@ -392,7 +405,7 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
                            "solves_per_s_one_launch_per_solve": seq_solves_s,
                            "batched_over_sequential": solves_s / seq_solves_s,
                            "sequential_sample": "%d of %d instances" % (len(sample), len(mix)),
-                           "launch": list(probs[0].get_launch())},
+                           "autotuner": tuned},
                 "e2e": {"value": evals * world / e2e_s, "unit": "evals/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": None, "clocks": clocks}
@@ -425,11 +438,39 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
             pr.close()
         return params_of[k]
 
+    # autotuner: batched throughput per class (trial batches), then the
+    # population per class from the load the trace offers
+    from paper_2603_19163_gb300.autotune import Autotuner, population_for_load
+    tuner = Autotuner(trial_generations=200)
+    models = {}
     for k in set(k for _, k in trace):
-        params_for(k)
+        models.setdefault(pool[k]["model"], []).append(k)
+    sample_probs, sample_params = [], []
+    for mdl, ks in models.items():
+        for k in ks[:: max(1, len(ks) // 8)][:8]:
+            sample_probs.append(cgo.Problem(dict(pool[k], tag=k)))
+            sample_params.append(params_for(k))
+    t_phase = time.perf_counter()
+    tuned = tuner.tune_batch(sample_probs, sample_params, sample=8)
+    print("serve: autotune %.1f s" % (time.perf_counter() - t_phase), file=sys.stderr, flush=True)
+    for pr in sample_probs:
+        pr.close()
+    share = {}
+    for _, k in trace:
+        share[pool[k]["model"]] = share.get(pool[k]["model"], 0) + 1.0 / len(trace)
+    pops, load = population_for_load({m: tuned[m][1] for m in tuned}, share,
+                                     len(trace) / duration, G, cfg["C"])
+    wpm_of = {m: tuned[m][0] for m in tuned}
+    for k in params_of:
+        params_of[k]["P"] = pops[pool[k]["model"]]
     srv = cgo.Server(max_slots=4096, hbm_budget_bytes=96 << 30, slice_generations=args.slice)
     # warm-up: a few requests end to end
-    warm = [cgo.Problem(dict(pool[k], tag=k)) for k in (0, 1, 2, 512)]
+    def make(k, tag):
+        pr = cgo.Problem(dict(pool[k], tag=tag))
+        pr.set_launch(0, 0, wpm_of[pool[k]["model"]])
+        return pr
+
+    warm = [make(k, k) for k in (0, 1, 2, 512)]
     for pr, k in zip(warm, (0, 1, 2, 512)):
         srv.wait(srv.submit(pr, params_for(k), 1), -1)
     torch.cuda.synchronize()
@@ -446,12 +487,22 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
             now = time.perf_counter() - t_start
             if ta > now:
                 time.sleep(ta - now)
-            pr = cgo.Problem(dict(pool[k], tag=i))
+            pr = make(k, i)
             probs[i] = pr
             tickets[i] = srv.submit(pr, params_for(k), 1 + i)
 
     th = threading.Thread(target=producer)
     th.start()
+    stop_mon = [False]
+
+    def monitor():
+        while not stop_mon[0]:
+            time.sleep(5.0)
+            print("serve: t=%.0f s %s" % (time.perf_counter() - t_start, srv.stats()),
+                  file=sys.stderr, flush=True)
+
+    mon = threading.Thread(target=monitor, daemon=True)
+    mon.start()
     done_at = [0.0] * len(trace)
     for i in range(len(trace)):
         while tickets[i] is None:
@@ -460,7 +511,9 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
         results[i] = (cost, lat)
         done_at[i] = time.perf_counter() - t_start
     th.join()
+    stop_mon[0] = True
     wall = max(done_at) - trace[0][0]
+    print("serve: trace done %.1f s" % (time.perf_counter() - t_start), file=sys.stderr, flush=True)
     clocks = sampler.stop() if rank == 0 else None
     stats = srv.stats()
     srv.close()
@@ -508,6 +561,10 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
                 "config": {"workload": desc.replace("G=20000", "G=%d" % G).replace(
                                "x60s", "x%ds" % int(duration)),
                            "requests": len(trace), "slice_generations": args.slice,
+                           "autotuner": {"population_by_model": {str(m): v for m, v in pops.items()},
+                                         "predicted_load": load,
+                                         "warps_per_member_by_model": {str(m): v for m, v in wpm_of.items()},
+                                         "trial_evals_per_s_by_model": {str(m): tuned[m][1] for m in tuned}},
                            "move_evals_per_s": evals / wall,
                            "latency_p50_s": float(np.percentile(lats, 50)),
                            "latency_p99_s": float(np.percentile(lats, 99)),

@@ -1,0 +1,125 @@
+"""Autotuner: launch shapes and serving populations, chosen by measurement.
+
+Search results never depend on the launch shape (warps per member, members
+per CTA, staging mode), so the tuner simply times short trial runs through
+the C ABI and keeps the fastest shape; choices are cached by a shape key.
+For serving it also picks the population per instance class: the largest
+population from a ladder whose predicted device load at the offered arrival
+rate stays under a utilisation target (the largest classes are halved first),
+using the batched throughput measured per class.
+"""
+from __future__ import annotations
+
+import time
+
+from . import cgo as C
+
+SMEM, GLOBAL = 1, 2
+
+
+def _key(prob: "C.Problem", params: dict) -> tuple:
+    inst = prob.inst
+    return (int(inst["model"]), int(inst["n"]), int(inst.get("m", 0)), int(params["P"]),
+            int(params["C"]))
+
+
+class Autotuner:
+    def __init__(self, trial_generations: int = 200):
+        self.trial = int(trial_generations)
+        self.cache_solve: dict = {}
+        self.cache_batch: dict = {}
+        self.log: list = []
+
+    # ------------------------------------------------------------- single
+    def solve_shapes(self, params: dict) -> list[tuple[int, int, int]]:
+        out = []
+        for wpm in (4, 2, 1):
+            if wpm * 32 > max(32, params["C"]) * 2:
+                continue
+            for mpc in (1, 2):
+                if wpm * mpc <= 8:
+                    for staging in (SMEM, GLOBAL):
+                        out.append((wpm * mpc, wpm, staging))
+        return out
+
+    def tune_solve(self, prob: "C.Problem", params: dict, seed: int = 1) -> tuple[int, int, int]:
+        """Pick (warps per CTA, warps per member, staging) for cgo_solve of
+        this problem and apply it; returns the choice."""
+        key = _key(prob, params)
+        if key not in self.cache_solve:
+            trial = dict(params, G=self.trial)
+            best = None
+            for shape in self.solve_shapes(params):
+                try:
+                    prob.set_launch(shape[0], staging=shape[2], wpm=shape[1])
+                    prob.solve(trial, seed)
+                    ms, gens = prob.last_kernel_time()
+                except C.CgoError:
+                    continue
+                rate = gens / max(ms, 1e-6)
+                self.log.append(("solve", key, shape, rate))
+                if best is None or rate > best[0]:
+                    best = (rate, shape)
+            if best is None:
+                raise RuntimeError("no launch shape runs for %r" % (key,))
+            self.cache_solve[key] = best[1]
+        shape = self.cache_solve[key]
+        prob.set_launch(shape[0], staging=shape[2], wpm=shape[1])
+        return shape
+
+    # ------------------------------------------------------------ batched
+    def tune_batch(self, probs: list, params: list, sample: int = 16, seed0: int = 1) -> dict:
+        """Pick warps per member for every model class of a batch (trial
+        batches of a sample of each class) and apply it to every problem;
+        returns {model: (wpm, evals_per_s)}."""
+        classes: dict = {}
+        for i, pr in enumerate(probs):
+            classes.setdefault(int(pr.inst["model"]), []).append(i)
+        out = {}
+        for model, idx in classes.items():
+            pick = idx[:: max(1, len(idx) // sample)][:sample]
+            key = (model, len(pick), tuple(sorted(set(params[i]["P"] for i in pick))))
+            if key not in self.cache_batch:
+                best = None
+                for wpm in (1, 2, 4):
+                    sub = [probs[i] for i in pick]
+                    for pr in sub:
+                        pr.set_launch(0, 0, wpm)
+                    trial = [dict(params[i], G=self.trial) for i in pick]
+                    evals = sum(t["P"] * t["C"] * t["G"] for t in trial)
+                    C.solve_batch(sub, trial, [seed0 + i for i in pick])    # warm
+                    t0 = time.perf_counter()
+                    C.solve_batch(sub, trial, [seed0 + i for i in pick])
+                    rate = evals / (time.perf_counter() - t0)
+                    self.log.append(("batch", key, wpm, rate))
+                    if best is None or rate > best[1]:
+                        best = (wpm, rate)
+                self.cache_batch[key] = best
+            wpm, rate = self.cache_batch[key]
+            for i in idx:
+                probs[i].set_launch(0, 0, wpm)
+            out[model] = (wpm, rate)
+        return out
+
+
+def population_for_load(class_rate: dict, share: dict, arrivals_per_s: float,
+                        generations: int, candidates: int, ladder=(32, 16, 8),
+                        utilisation: float = 0.8) -> tuple[dict, float]:
+    """Serving populations: start every class at the top of the ladder and,
+    while the predicted device load (fraction of one GPU) exceeds the target,
+    step down the class that contributes most.  class_rate: measured batched
+    move evaluations per second of each class; share: its fraction of
+    arrivals.  Returns ({class: P}, predicted load)."""
+    P = {c: ladder[0] for c in class_rate}
+
+    def load_of(c):
+        return arrivals_per_s * share[c] * P[c] * candidates * generations / class_rate[c]
+
+    while True:
+        load = sum(load_of(c) for c in P)
+        if load <= utilisation:
+            return P, load
+        c = max((c for c in P if P[c] > ladder[-1]), key=load_of, default=None)
+        if c is None:
+            return P, load
+        P[c] = ladder[ladder.index(P[c]) + 1]

@@ -55,14 +55,54 @@ namespace cgo {
 namespace host {
 
 
+// Per-thread, per-device non-blocking stream for the library's own
+// allocations, copies and frees.  Allocation is stream-ordered
+// (cudaMallocAsync from the device pool, which keeps freed memory cached),
+// so creating or destroying a problem never waits for kernels other threads
+// have in flight (a serving loop, for one).
+cudaStream_t host_stream() {
+  thread_local cudaStream_t streams[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!streams[dev]) {
+    cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    static std::mutex mu;
+    static bool pool_set[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pool_set[dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+      pool_set[dev] = true;
+    }
+  }
+  return streams[dev];
+}
+
+cudaError_t copy_sync(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, host_stream());
+  return e != cudaSuccess ? e : cudaStreamSynchronize(host_stream());
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes) { return cudaMallocAsync(p, bytes, host_stream()); }
+void dev_free(void *p) {
+  if (p) cudaFreeAsync(p, host_stream());
+}
+
 cudaError_t copy_in(int32_t **dst, const int32_t *src, int64_t count, bool on_device) {
   const int64_t bytes = pad16(count * 4);
-  cudaError_t e = cudaMalloc((void **)dst, (size_t)bytes);
+  cudaStream_t hs = host_stream();
+  cudaError_t e = cudaMallocAsync((void **)dst, (size_t)bytes, hs);
   if (e != cudaSuccess) return e;
-  e = cudaMemset(*dst, 0, (size_t)bytes);
+  e = cudaMemsetAsync(*dst, 0, (size_t)bytes, hs);
   if (e != cudaSuccess) return e;
-  return cudaMemcpy(*dst, src, (size_t)(count * 4),
-                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  e = cudaMemcpyAsync(*dst, src, (size_t)(count * 4),
+                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, hs);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(hs);
 }
 
 // host copy of caller data (for validation), whether it is on host or device
@@ -71,7 +111,9 @@ cgo_status host_copy(const int32_t *src, int64_t count, bool on_device, std::vec
   if (count == 0) return CGO_OK;
   if (!src) return fail(CGO_ERR_INVALID, "missing data array");
   if (on_device) {
-    CUDA_TRY(cudaMemcpy(out.data(), src, (size_t)count * 4, cudaMemcpyDeviceToHost), "reading device data");
+    CUDA_TRY(cudaMemcpyAsync(out.data(), src, (size_t)count * 4, cudaMemcpyDeviceToHost, host_stream()),
+             "reading device data");
+    CUDA_TRY(cudaStreamSynchronize(host_stream()), "reading device data");
   } else {
     memcpy(out.data(), src, (size_t)count * 4);
   }
@@ -98,12 +140,12 @@ const double kLimit = 4.6e18;  // 2^62: every cost and delta fits in int64 with 
 int64_t g_batch_slice = 2000;  // generations per batched time slice
 
 void free_state(cgo_problem *p) {
-  cudaFree(p->d_cur);
-  cudaFree(p->d_bestsol);
-  cudaFree(p->d_cost);
-  cudaFree(p->d_best);
-  cudaFree(p->d_aos);
-  cudaFree(p->d_sync);
+  dev_free(p->d_cur);
+  dev_free(p->d_bestsol);
+  dev_free(p->d_cost);
+  dev_free(p->d_best);
+  dev_free(p->d_aos);
+  dev_free(p->d_sync);
   p->d_cur = p->d_bestsol = nullptr;
   p->d_cost = p->d_best = nullptr;
   p->d_aos = nullptr;
@@ -116,13 +158,14 @@ cgo_status ensure_state(cgo_problem *p, int P) {
   if (p->P_alloc == P && p->d_cur) return CGO_OK;
   free_state(p);
   const size_t sol = (size_t)P * p->len * 4;
-  CUDA_TRY(cudaMalloc((void **)&p->d_cur, sol), "state alloc");
-  CUDA_TRY(cudaMalloc((void **)&p->d_bestsol, sol), "state alloc");
-  CUDA_TRY(cudaMalloc((void **)&p->d_cost, (size_t)P * 8), "state alloc");
-  CUDA_TRY(cudaMalloc((void **)&p->d_best, (size_t)P * 8), "state alloc");
-  CUDA_TRY(cudaMalloc((void **)&p->d_aos, 2 * sizeof(DevAos)), "state alloc");
-  CUDA_TRY(cudaMalloc((void **)&p->d_sync, sizeof(DevSync)), "state alloc");
-  CUDA_TRY(cudaMemset(p->d_aos, 0, 2 * sizeof(DevAos)), "state init");
+  CUDA_TRY(dev_alloc((void **)&p->d_cur, sol), "state alloc");
+  CUDA_TRY(dev_alloc((void **)&p->d_bestsol, sol), "state alloc");
+  CUDA_TRY(dev_alloc((void **)&p->d_cost, (size_t)P * 8), "state alloc");
+  CUDA_TRY(dev_alloc((void **)&p->d_best, (size_t)P * 8), "state alloc");
+  CUDA_TRY(dev_alloc((void **)&p->d_aos, 2 * sizeof(DevAos)), "state alloc");
+  CUDA_TRY(dev_alloc((void **)&p->d_sync, sizeof(DevSync)), "state alloc");
+  CUDA_TRY(cudaMemsetAsync(p->d_aos, 0, 2 * sizeof(DevAos), host_stream()), "state init");
+  CUDA_TRY(cudaStreamSynchronize(host_stream()), "state alloc");
   p->P_alloc = P;
   return CGO_OK;
 }
@@ -454,11 +497,11 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
       cudaError_t e = copy_in(&p->d_mat0, a.data(), n * n, false);
       if (e != cudaSuccess) return bail(cuda_fail(e, "copying D"));
       const int64_t tb = pad16(n * (n + 1) / 2 * (p->tri16 ? 2 : 4));
-      if ((e = cudaMalloc(&p->d_tri, (size_t)tb)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
-      if ((e = cudaMemset(p->d_tri, 0, (size_t)tb)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
-      if ((e = build_triangle(p->d_mat0, (int)n, p->tri16, p->d_tri, cudaStreamPerThread)) != cudaSuccess)
+      if ((e = dev_alloc(&p->d_tri, (size_t)tb)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+      if ((e = cudaMemsetAsync(p->d_tri, 0, (size_t)tb, host_stream())) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+      if ((e = build_triangle(p->d_mat0, (int)n, p->tri16, p->d_tri, host_stream())) != cudaSuccess)
         return bail(cuda_fail(e, "triangle"));
-      if ((e = cudaStreamSynchronize(cudaStreamPerThread)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+      if ((e = cudaStreamSynchronize(host_stream())) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
       break;
     }
     case CGO_QAP: {
@@ -541,11 +584,11 @@ cgo_status cgo_problem_destroy(cgo_problem *p) {
   free_state(p);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
-  cudaFree(p->d_mat0);
-  cudaFree(p->d_mat1);
-  for (int i = 0; i < 4; ++i) cudaFree(p->d_vec[i]);
-  cudaFree(p->d_tri);
-  cudaFree(p->d_node);
+  dev_free(p->d_mat0);
+  dev_free(p->d_mat1);
+  for (int i = 0; i < 4; ++i) dev_free(p->d_vec[i]);
+  dev_free(p->d_tri);
+  dev_free(p->d_node);
   delete p;
   return CGO_OK;
 }
@@ -671,10 +714,10 @@ cgo_status cgo_best(const cgo_problem *p, int32_t *out_sol, int32_t cap, int64_t
   if (out_sol && cap < p->len) return fail(CGO_ERR_INVALID, "cap %d < solution length %d", cap, p->len);
   cudaSetDevice(p->device);
   DevAos a;
-  CUDA_TRY(cudaMemcpy(&a, p->d_aos + p->aos_cur, sizeof a, cudaMemcpyDeviceToHost), "reading elite");
+  CUDA_TRY(copy_sync(&a, p->d_aos + p->aos_cur, sizeof a, cudaMemcpyDeviceToHost), "reading elite");
   if (out_cost) *out_cost = a.elite_cost;
   if (out_sol)
-    CUDA_TRY(cudaMemcpy(out_sol, p->d_bestsol + (int64_t)a.elite * p->len, (size_t)p->len * 4,
+    CUDA_TRY(copy_sync(out_sol, p->d_bestsol + (int64_t)a.elite * p->len, (size_t)p->len * 4,
                         cudaMemcpyDeviceToHost),
              "reading elite");
   return CGO_OK;
@@ -687,7 +730,7 @@ cgo_status cgo_state_get(const cgo_problem *p, cgo_state *o) {
   if (!p->has_state) return fail(CGO_ERR_STATE, "no search state");
   cudaSetDevice(p->device);
   DevAos a;
-  CUDA_TRY(cudaMemcpy(&a, p->d_aos + p->aos_cur, sizeof a, cudaMemcpyDeviceToHost), "reading state");
+  CUDA_TRY(copy_sync(&a, p->d_aos + p->aos_cur, sizeof a, cudaMemcpyDeviceToHost), "reading state");
   const int P = p->params.population;
   o->population = P;
   o->length = p->len;
@@ -706,10 +749,10 @@ cgo_status cgo_state_get(const cgo_problem *p, cgo_state *o) {
   o->stag = a.stag;
   o->elite_prev = a.elite_prev;
   const size_t sb = (size_t)P * p->len * 4;
-  if (o->cur) CUDA_TRY(cudaMemcpy(o->cur, p->d_cur, sb, cudaMemcpyDeviceToHost), "reading state");
-  if (o->best_sol) CUDA_TRY(cudaMemcpy(o->best_sol, p->d_bestsol, sb, cudaMemcpyDeviceToHost), "reading state");
-  if (o->cost) CUDA_TRY(cudaMemcpy(o->cost, p->d_cost, (size_t)P * 8, cudaMemcpyDeviceToHost), "reading state");
-  if (o->best_cost) CUDA_TRY(cudaMemcpy(o->best_cost, p->d_best, (size_t)P * 8, cudaMemcpyDeviceToHost), "reading state");
+  if (o->cur) CUDA_TRY(copy_sync(o->cur, p->d_cur, sb, cudaMemcpyDeviceToHost), "reading state");
+  if (o->best_sol) CUDA_TRY(copy_sync(o->best_sol, p->d_bestsol, sb, cudaMemcpyDeviceToHost), "reading state");
+  if (o->cost) CUDA_TRY(copy_sync(o->cost, p->d_cost, (size_t)P * 8, cudaMemcpyDeviceToHost), "reading state");
+  if (o->best_cost) CUDA_TRY(copy_sync(o->best_cost, p->d_best, (size_t)P * 8, cudaMemcpyDeviceToHost), "reading state");
   return CGO_OK;
 }
 
@@ -733,10 +776,10 @@ cgo_status cgo_state_set(cgo_problem *p, const cgo_params *q, uint64_t seed, con
   }
   if ((s = ensure_state(p, q->population)) != CGO_OK) return s;
   const size_t sb = (size_t)P * p->len * 4;
-  CUDA_TRY(cudaMemcpy(p->d_cur, in->cur, sb, cudaMemcpyHostToDevice), "writing state");
-  CUDA_TRY(cudaMemcpy(p->d_bestsol, in->best_sol, sb, cudaMemcpyHostToDevice), "writing state");
-  CUDA_TRY(cudaMemcpy(p->d_cost, in->cost, (size_t)P * 8, cudaMemcpyHostToDevice), "writing state");
-  CUDA_TRY(cudaMemcpy(p->d_best, in->best_cost, (size_t)P * 8, cudaMemcpyHostToDevice), "writing state");
+  CUDA_TRY(copy_sync(p->d_cur, in->cur, sb, cudaMemcpyHostToDevice), "writing state");
+  CUDA_TRY(copy_sync(p->d_bestsol, in->best_sol, sb, cudaMemcpyHostToDevice), "writing state");
+  CUDA_TRY(copy_sync(p->d_cost, in->cost, (size_t)P * 8, cudaMemcpyHostToDevice), "writing state");
+  CUDA_TRY(copy_sync(p->d_best, in->best_cost, (size_t)P * 8, cudaMemcpyHostToDevice), "writing state");
   DevAos a;
   memset(&a, 0, sizeof a);
   a.T = in->T_q32;
@@ -758,7 +801,7 @@ cgo_status cgo_state_set(cgo_problem *p, const cgo_params *q, uint64_t seed, con
     if (in->best_cost[i] < in->best_cost[e]) e = i;
   a.elite = e;
   a.elite_cost = in->best_cost[e];
-  CUDA_TRY(cudaMemcpy(p->d_aos, &a, sizeof a, cudaMemcpyHostToDevice), "writing state");
+  CUDA_TRY(copy_sync(p->d_aos, &a, sizeof a, cudaMemcpyHostToDevice), "writing state");
   p->params = *q;
   p->seed = seed;
   p->enabled = en;
@@ -836,11 +879,11 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
   DevAos *d_a0 = nullptr;
   int *d_lists = nullptr, *d_next = nullptr, *d_counts = nullptr;
   auto release = [&]() {
-    cudaFree(d_k);
-    cudaFree(d_a0);
-    cudaFree(d_lists);
-    cudaFree(d_next);
-    cudaFree(d_counts);
+    if (d_k) cudaFreeAsync(d_k, st);
+    if (d_a0) cudaFreeAsync(d_a0, st);
+    if (d_lists) cudaFreeAsync(d_lists, st);
+    if (d_next) cudaFreeAsync(d_next, st);
+    if (d_counts) cudaFreeAsync(d_counts, st);
   };
   std::vector<int> lists, counts;
   std::vector<size_t> list_off;
@@ -856,11 +899,11 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
     lists.insert(lists.end(), bk.members.begin(), bk.members.end());
   }
   cudaError_t e;
-  if ((e = cudaMalloc((void **)&d_k, sizeof(KInst) * (size_t)count)) != cudaSuccess ||
-      (e = cudaMalloc((void **)&d_a0, sizeof(DevAos) * (size_t)count)) != cudaSuccess ||
-      (e = cudaMalloc((void **)&d_lists, sizeof(int) * lists.size())) != cudaSuccess ||
-      (e = cudaMalloc((void **)&d_next, sizeof(int) * nb)) != cudaSuccess ||
-      (e = cudaMalloc((void **)&d_counts, sizeof(int) * nb)) != cudaSuccess) {
+  if ((e = cudaMallocAsync((void **)&d_k, sizeof(KInst) * (size_t)count, st)) != cudaSuccess ||
+      (e = cudaMallocAsync((void **)&d_a0, sizeof(DevAos) * (size_t)count, st)) != cudaSuccess ||
+      (e = cudaMallocAsync((void **)&d_lists, sizeof(int) * lists.size(), st)) != cudaSuccess ||
+      (e = cudaMallocAsync((void **)&d_next, sizeof(int) * nb, st)) != cudaSuccess ||
+      (e = cudaMallocAsync((void **)&d_counts, sizeof(int) * nb, st)) != cudaSuccess) {
     release();
     return cuda_fail(e, "batch descriptors");
   }

@@ -68,6 +68,7 @@ struct Guard {
   }
 };
 
+cudaStream_t host_stream();
 cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *enabled);
 cgo_status ensure_state(cgo_problem *p, int P);
 KInst base_kinst(const cgo_problem *p);

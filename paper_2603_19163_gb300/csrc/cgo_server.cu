@@ -256,11 +256,13 @@ void server_loop(cgo_server *S) {
       r->g = std::min<int64_t>(r->params.generations, r->g + S->cfg.slice_generations);
       if (r->g >= r->params.generations) finished.push_back(r);
     }
-    for (Req *r : finished) {
-      DevAos a;
-      e = cudaMemcpy(&a, r->prob->d_aos, sizeof a, cudaMemcpyDeviceToHost);
-      r->cost = a.elite_cost;
-      r->status = e == cudaSuccess ? CGO_OK : CGO_ERR_CUDA;
+    std::vector<DevAos> aos(finished.size());
+    for (size_t i = 0; i < finished.size() && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(&aos[i], finished[i]->prob->d_aos, sizeof(DevAos), cudaMemcpyDeviceToHost, S->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+    for (size_t i = 0; i < finished.size(); ++i) {
+      finished[i]->cost = aos[i].elite_cost;
+      finished[i]->status = e == cudaSuccess ? CGO_OK : CGO_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lk(S->mu);
     for (Req *r : finished) {

@@ -1,0 +1,24 @@
+"""Host logic of the autotuner's serving-population rule (no GPU)."""
+from paper_2603_19163_gb300.autotune import population_for_load
+
+
+def test_population_rule_keeps_everything_at_the_top_when_it_fits():
+    P, load = population_for_load({"a": 1e10, "b": 1e10}, {"a": 0.5, "b": 0.5}, 10.0, 1000, 128)
+    assert P == {"a": 32, "b": 32} and load < 0.8
+
+
+def test_population_rule_steps_down_the_heaviest_class_first():
+    rate = {"fast": 2e10, "slow": 2e8}
+    share = {"fast": 0.85, "slow": 0.15}
+    P, load = population_for_load(rate, share, 200.0, 20000, 128)
+    # the slow class dominates the load, so it reaches the bottom of the
+    # ladder before the fast one moves
+    assert P["slow"] == 8
+    assert P["fast"] in (32, 16, 8)
+    loads = {c: 200 * share[c] * P[c] * 128 * 20000 / rate[c] for c in rate}
+    assert abs(sum(loads.values()) - load) < 1e-9
+
+
+def test_population_rule_reports_overload_at_the_bottom():
+    P, load = population_for_load({"x": 1e6}, {"x": 1.0}, 1000.0, 20000, 128)
+    assert P == {"x": 8} and load > 0.8
