@@ -376,6 +376,8 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
     solves_s = len(probs) * args.steps * world / (total_ms / 1000.0)
     # one launch per solve, on a stratified sample (every 8th instance)
     sample = list(range(0, len(probs), 8))
+    for i in sample:
+        probs[i].set_launch(0, 0, 0)        # one launch per solve: its own default shape
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in sample:
@@ -446,12 +448,15 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
     for k in set(k for _, k in trace):
         models.setdefault(pool[k]["model"], []).append(k)
     sample_probs, sample_params = [], []
+    fill = 2 * torch.cuda.get_device_properties(local).multi_processor_count
     for mdl, ks in models.items():
-        for k in ks[:: max(1, len(ks) // 8)][:8]:
-            sample_probs.append(cgo.Problem(dict(pool[k], tag=k)))
+        pick = ks[:: max(1, len(ks) // 8)][:8]
+        for j in range(fill):           # a trial batch large enough to fill the GPU
+            k = pick[j % len(pick)]
+            sample_probs.append(cgo.Problem(dict(pool[k], tag=j)))
             sample_params.append(params_for(k))
     t_phase = time.perf_counter()
-    tuned = tuner.tune_batch(sample_probs, sample_params, sample=8)
+    tuned = tuner.tune_batch(sample_probs, sample_params, sample=fill)
     print("serve: autotune %.1f s" % (time.perf_counter() - t_phase), file=sys.stderr, flush=True)
     for pr in sample_probs:
         pr.close()
@@ -496,8 +501,10 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
     stop_mon = [False]
 
     def monitor():
-        while not stop_mon[0]:
+        while True:
             time.sleep(5.0)
+            if stop_mon[0]:
+                return
             print("serve: t=%.0f s %s" % (time.perf_counter() - t_start, srv.stats()),
                   file=sys.stderr, flush=True)
 
