@@ -33,6 +33,41 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
   return make_uint4(c0, c1, c2, c3);
 }
 
+// Three Philox4x32-10 blocks whose counters differ only in word 0, advanced
+// round by round so that the three dependency chains sit next to each other
+// in program order (warps issue in order; this is what lets them overlap).
+__device__ __forceinline__ void philox3(uint32_t a0, uint32_t b0, uint32_t e0, uint32_t c1,
+                                        uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                                        uint4 &A, uint4 &B, uint4 &E) {
+  uint32_t a[4] = {a0, c1, c2, c3}, b[4] = {b0, c1, c2, c3}, e[4] = {e0, c1, c2, c3};
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t alo0 = 0xD2511F53u * a[0], ahi0 = __umulhi(0xD2511F53u, a[0]);
+    const uint32_t blo0 = 0xD2511F53u * b[0], bhi0 = __umulhi(0xD2511F53u, b[0]);
+    const uint32_t elo0 = 0xD2511F53u * e[0], ehi0 = __umulhi(0xD2511F53u, e[0]);
+    const uint32_t alo1 = 0xCD9E8D57u * a[2], ahi1 = __umulhi(0xCD9E8D57u, a[2]);
+    const uint32_t blo1 = 0xCD9E8D57u * b[2], bhi1 = __umulhi(0xCD9E8D57u, b[2]);
+    const uint32_t elo1 = 0xCD9E8D57u * e[2], ehi1 = __umulhi(0xCD9E8D57u, e[2]);
+    a[0] = ahi1 ^ a[1] ^ k0;
+    b[0] = bhi1 ^ b[1] ^ k0;
+    e[0] = ehi1 ^ e[1] ^ k0;
+    a[2] = ahi0 ^ a[3] ^ k1;
+    b[2] = bhi0 ^ b[3] ^ k1;
+    e[2] = ehi0 ^ e[3] ^ k1;
+    a[1] = alo1;
+    b[1] = blo1;
+    e[1] = elo1;
+    a[3] = alo0;
+    b[3] = blo0;
+    e[3] = elo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  A = make_uint4(a[0], a[1], a[2], a[3]);
+  B = make_uint4(b[0], b[1], b[2], b[3]);
+  E = make_uint4(e[0], e[1], e[2], e[3]);
+}
+
 // A 16-bit field scaled to [0, m): floor(h * m / 2^16), m <= 65536.
 __device__ __forceinline__ int posm(uint32_t h16, uint32_t m) { return (int)((h16 * m) >> 16); }
 
@@ -161,25 +196,33 @@ struct PMove {
 };
 
 __device__ __forceinline__ PMove perm_decode(int op, uint32_t r1, uint32_t r2, int m) {
+  // every variant is computed and the operator selects one (no branches:
+  // lanes of a warp draw different operators)
   const uint32_t a = r1 >> 16, b = r1 & 0xFFFFu;
-  PMove mv;
-  if (op == OR_OPT) {
-    const int L = 2 + (int)(r2 & 1u);
-    const int i = posm(a, (uint32_t)(m - L + 1));
-    int q = posm(b, (uint32_t)(m - L));
-    q += (q >= i);
-    if (q < i) mv = {q, i, i, i + L, 0};
-    else mv = {i, i + L, i + L, q + L, 0};
-    return mv;
-  }
+  const int L = 2 + (int)(r2 & 1u);
+  const int io = posm(a, (uint32_t)(m - L + 1));
+  int q = posm(b, (uint32_t)(m - L));
+  q += (q >= io);
   const int i = posm(a, (uint32_t)m);
   int j = posm(b, (uint32_t)(m - 1));
   j += (j >= i);
   const int lo = min(i, j), hi = max(i, j);
-  if (op == SWAP) mv = {lo, lo + 1, hi, hi + 1, 0};
-  else if (op == TWO_OPT) mv = {lo, hi + 1, hi + 1, hi + 1, 1};
-  else if (i < j) mv = {i, i + 1, i + 1, j + 1, 0};
-  else mv = {j, i, i, i + 1, 0};
+  const bool ob = q < io;
+  PMove mv;
+  if (op == OR_OPT) {
+    mv.b1 = ob ? q : io;
+    mv.b2 = ob ? io : io + L;
+    mv.b3 = mv.b2;
+    mv.b4 = ob ? io + L : q + L;
+    mv.rev = 0;
+  } else {
+    const bool sw = op == SWAP, two = op == TWO_OPT, fw = i < j;
+    mv.b1 = (sw || two) ? lo : (fw ? i : j);
+    mv.b2 = sw ? lo + 1 : (two ? hi + 1 : (fw ? i + 1 : i));
+    mv.b3 = sw ? hi : (two ? hi + 1 : (fw ? i + 1 : i));
+    mv.b4 = sw ? hi + 1 : (two ? hi + 1 : (fw ? j + 1 : i + 1));
+    mv.rev = two ? 1 : 0;
+  }
   return mv;
 }
 

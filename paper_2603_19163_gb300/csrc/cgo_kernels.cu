@@ -12,6 +12,7 @@
 // every warp applies Eq. "ema", the stagnation rule and, when due, elite
 // injection (Alg. "aos", Sec. 3.4.3, 4.2).
 #include <climits>
+#include <type_traits>
 #include <cooperative_groups.h>
 
 #include "cgo_device.cuh"
@@ -334,6 +335,78 @@ struct CandMoves {
   int k;
 };
 
+// The three steps of a TSP candidate, evaluated in phases across the steps
+// (positions, inverse maps, solution loads, triangle gathers, sums) so that
+// independent work is adjacent in program order.  With the int16 triangle
+// every junction sum fits comfortably in 32 bits.
+template <bool T16>
+__device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl *sol,
+                                                     const CandMoves &cm, int k) {
+  using Acc = typename std::conditional<T16, int, long long>::type;
+  const int m = X.len;
+  int pos[3][8];
+  bool rev[3], mn[3], remp[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const PMove &mv = cm.m[t];
+    rev[t] = mv.rev != 0;
+    mn[t] = mv.b3 > mv.b2;
+    remp[t] = (mv.b1 == 0) && (mv.b4 == m);
+    pos[t][0] = mv.b1 == 0 ? m - 1 : mv.b1 - 1;  // r_l
+    pos[t][1] = mv.b4 == m ? 0 : mv.b4;          // r_f
+    pos[t][2] = mv.b1;                           // A_f
+    pos[t][3] = mv.b2 - 1;                       // A_l
+    pos[t][4] = min(mv.b3, m - 1);               // B_f
+    pos[t][5] = max(mv.b4 - 1, 0);               // B_l
+    pos[t][6] = min(mv.b2, m - 1);               // M_f
+    pos[t][7] = max(mv.b3 - 1, 0);               // M_l
+  }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    pos[1][e] = perm_inv(cm.m[0], pos[1][e]);
+    pos[2][e] = perm_inv(cm.m[0], perm_inv(cm.m[1], pos[2][e]));
+  }
+  int v[3][8];
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[t][e] = sol[pos[t][e]];
+  // gather pairs: (rl,x1) (y2,rf) (rl,af) (z4,rf) (bl,mf|af) (ml,af) (al,mf|bf) (ml,bf)
+  uint32_t idx[3][8];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int rl = v[t][0], rf = v[t][1], af = v[t][2], al = v[t][3], bf = v[t][4], bl = v[t][5],
+              mf = v[t][6], ml = v[t][7];
+    const int px[8] = {rl, rev[t] ? af : al, rl, rev[t] ? al : bl, bl, ml, al, ml};
+    const int py[8] = {rev[t] ? al : bf, rf, af, rf, mn[t] ? mf : af, af, mn[t] ? mf : bf, bf};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int a = min(px[e], py[e]), b = max(px[e], py[e]);
+      idx[t][e] = (((uint32_t)a * (uint32_t)(X.n2m1 - a)) >> 1) + (uint32_t)b;
+    }
+  }
+  Acc dv[3][8];
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      dv[t][e] = T16 ? (Acc)((const int16_t *)X.tri)[idx[t][e]] : (Acc)((const int32_t *)X.tri)[idx[t][e]];
+  long long total = 0;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const Acc mid_n = dv[t][4] + (mn[t] ? dv[t][5] : (Acc)0);
+    const Acc mid_o = dv[t][6] + (mn[t] ? dv[t][7] : (Acc)0);
+    Acc d = dv[t][0] + dv[t][1] - dv[t][2] - dv[t][3] + (rev[t] ? (Acc)0 : mid_n - mid_o);
+    if (remp[t]) {
+      d = 0;
+      if (!rev[t] && mn[t]) d = mid_n - mid_o + (Acc)tsp_d<T16>(X, v[t][3], v[t][4]) -
+                              (Acc)tsp_d<T16>(X, v[t][5], v[t][2]);
+    }
+    total += (t < k) ? (long long)d : 0ll;
+  }
+  return total;
+}
+
 // Candidate c: all three steps are drawn and decoded, and the delta of every
 // step is computed (each needs only the decoded earlier moves, not their
 // deltas), so the steps overlap; k selects how many count.
@@ -365,9 +438,9 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
     stats_k(st, k, imp);
     return d;
   }
-  const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
-  const uint4 R1 = philox(ctr_word(c, 1, kKindMove), X.tag, p, g, X.k0, X.k1);
-  const uint4 R2 = philox(ctr_word(c, 2, kKindMove), X.tag, p, g, X.k0, X.k1);
+  uint4 R0, R1, R2;
+  philox3(ctr_word(c, 0, kKindMove), ctr_word(c, 1, kKindMove), ctr_word(c, 2, kKindMove), X.tag,
+          p, g, X.k0, X.k1, R0, R1, R2);
   const int k = 1 + wsample(W.k, W.Wk, R0.w);
   const int op0 = wsample(W.op, W.Wop, R0.x);
   const int op1 = wsample(W.op, W.Wop, R1.x);
@@ -376,10 +449,7 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
   cm.m[1] = perm_decode(op1, R1.y, R1.z, X.len);
   cm.m[2] = perm_decode(op2, R2.y, R2.z, X.len);
   cm.k = k;
-  const long long d0 = perm_delta<MODEL, T16>(X, sol, cm.m[0], cm.m[0], cm.m[0], 0);
-  const long long d1 = perm_delta<MODEL, T16>(X, sol, cm.m[1], cm.m[0], cm.m[0], 1);
-  const long long d2 = perm_delta<MODEL, T16>(X, sol, cm.m[2], cm.m[0], cm.m[1], 2);
-  const long long d = d0 + (k >= 2 ? d1 : 0ll) + (k >= 3 ? d2 : 0ll);
+  const long long d = tsp_three_steps<T16>(X, sol, cm, k);
   const uint32_t imp = d < 0;
   stats_op(st, op0, imp);
   stats_op(st, k >= 2 ? op1 : -1, imp);
