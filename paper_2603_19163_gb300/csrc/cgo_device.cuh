@@ -144,6 +144,64 @@ __device__ __forceinline__ void aos_level(uint32_t (&w)[N], const uint32_t (&u)[
     if ((enabled >> i) & 1u) w[i] = (uint32_t)(((uint64_t)w[i] << 16) / S);
 }
 
+// floor(num / den) for num, den < 2^53, den >= 1: the double-precision
+// quotient is within one unit of the exact one, and two correction steps
+// make it exact.
+__device__ __forceinline__ uint64_t udiv_exact(uint64_t num, uint64_t den) {
+  uint64_t q = (uint64_t)((double)num / (double)den);
+  if (q * den > num) --q;
+  if (q * den > num) --q;
+  if ((q + 1) * den <= num) ++q;
+  if ((q + 1) * den <= num) ++q;
+  return q;
+}
+
+// Eq. "ema" for both levels at once, one lane per weight: lanes 0..NO-1
+// hold the operator weights, lanes 24..26 the K weights; u/v are read from
+// the lanes that hold the window totals (u_op at lane o, v_op at 8+o, u_k at
+// 16+i, v_k at 19+i).  Every lane ends with the new weights.
+template <int NO, int BASE>
+__device__ __forceinline__ void aos_update_lanes(uint32_t (&wop)[NO], uint32_t (&wk)[3],
+                                                 uint32_t total, uint32_t en_local,
+                                                 const uint32_t (&capl)[NO], uint32_t a,
+                                                 uint32_t wfloor, uint32_t wcap) {
+  const int lane = threadIdx.x & 31;
+  const bool is_op = lane < NO, is_k = lane >= 24 && lane < 27;
+  const int li = is_op ? lane : lane - 24;
+  const uint32_t u = __shfl_sync(kFull, total, is_op ? BASE + li : (is_k ? 16 + li : 0));
+  const uint32_t v = __shfl_sync(kFull, total, is_op ? 8 + BASE + li : (is_k ? 19 + li : 0));
+  uint32_t w = 0, cap = 65536u;
+  bool en = false;
+#pragma unroll
+  for (int l = 0; l < NO; ++l)
+    if (is_op && li == l) {
+      w = wop[l];
+      cap = capl[l];
+      en = (en_local >> l) & 1u;
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (is_k && li == i) {
+      w = wk[i];
+      en = true;
+    }
+  uint64_t nw = 0;
+  if (en) {
+    const uint64_t ratio = udiv_exact((uint64_t)v << 16, (uint64_t)u + 1ull);
+    nw = ((uint64_t)a * w + (uint64_t)(65536u - a) * (ratio + wfloor)) >> 16;
+    const uint64_t hi = wcap < cap ? wcap : cap;
+    nw = nw > hi ? hi : nw;
+    nw = nw < wfloor ? wfloor : nw;
+  }
+  const uint32_t s_op = __reduce_add_sync(kFull, is_op ? (uint32_t)nw : 0u);
+  const uint32_t s_k = __reduce_add_sync(kFull, is_k ? (uint32_t)nw : 0u);
+  const uint32_t mine = en ? (uint32_t)udiv_exact(nw << 16, is_op ? s_op : s_k) : w;
+#pragma unroll
+  for (int l = 0; l < NO; ++l) wop[l] = __shfl_sync(kFull, mine, l);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) wk[i] = __shfl_sync(kFull, mine, 24 + i);
+}
+
 // Lexicographic (delta, index) minimum over the warp; every lane gets it.
 __device__ __forceinline__ void warp_argmin(long long &d, int &c) {
 #pragma unroll

@@ -50,9 +50,9 @@ struct Layout {
 
 __host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64_t(15); }
 
-// per member group: 2*wpm partial argmins (16 B), a flag (16 B) and the
-// winner's moves (4 x 16 B)
-__host__ __device__ inline int64_t group_bytes(int wpm) { return 2 * wpm * 16 + 16 + 64; }
+// per member group: 2*wpm partial argmins (16 B), a flag (16 B), the
+// winner's moves (4 x 16 B) and each warp's window counts (32 x 4 B)
+__host__ __device__ inline int64_t group_bytes(int wpm) { return 2 * wpm * 16 + 16 + 64 + wpm * 128; }
 
 // Shared memory of one CTA: [instance data][members' solutions][one scratch
 // array per member group][member scalars][GAP loads][per-group partials]
@@ -743,6 +743,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   Partial *part = (Partial *)gmem;
   int *flag = (int *)(gmem + 2 * WPM * sizeof(Partial));
   CandMoves *mv_smem = (CandMoves *)(gmem + 2 * WPM * sizeof(Partial) + 16);
+  uint32_t *cnt_smem = (uint32_t *)(gmem + 2 * WPM * sizeof(Partial) + 16 + 64);
 
   // load this group's members
   for (int e = 0; e < mine; ++e) {
@@ -904,7 +905,17 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       my = (lane == 19 + i) ? tot[2 * NO + 3 + i] : my;
     }
     const int slot = wi & 1;
-    if (lane < kStats && my) atomicAdd(&S->acc[slot][lane], my);
+    if constexpr (WPM > 1) {
+      // the group's warps add their counts in shared memory; one warp publishes
+      cnt_smem[G.gw * 32 + lane] = my;
+      G.sync();
+      if (G.gw == 0) {
+#pragma unroll
+        for (int w = 1; w < WPM; ++w) my += cnt_smem[w * 32 + lane];
+      }
+      G.sync();
+    }
+    if (G.gw == 0 && lane < kStats && my) atomicAdd(&S->acc[slot][lane], my);
     if (G.gw == 0 && lane == 0) atomicMin((long long *)&S->elite[slot], minbest);
     if (inject && G.tig == 0) {
       for (int e = 0; e < mine; ++e) {
@@ -924,19 +935,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     const long long elite = ld_relaxed64((const long long *)&S->elite[slot]);
     ++wi;
 
-    uint32_t uo[NO], vo[NO], uk[3], vk[3], capk[3] = {65536u, 65536u, 65536u};
-#pragma unroll
-    for (int l = 0; l < NO; ++l) {
-      uo[l] = __shfl_sync(kFull, total, BASE + l);
-      vo[l] = __shfl_sync(kFull, total, 8 + BASE + l);
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      uk[i] = __shfl_sync(kFull, total, 16 + i);
-      vk[i] = __shfl_sync(kFull, total, 19 + i);
-    }
-    aos_level<NO>(W.op, uo, vo, en_local, capl, I.ema_a, I.w_floor, I.w_cap);
-    aos_level<3>(W.k, uk, vk, 7u, capk, I.ema_a, I.w_floor, I.w_cap);
+    aos_update_lanes<NO, BASE>(W.op, W.k, total, en_local, capl, I.ema_a, I.w_floor, I.w_cap);
     if (elite < elite_prev) stag = 0;
     else ++stag;
     elite_prev = elite;
