@@ -260,13 +260,9 @@ def main():
     barrier()
     clocks = sampler.stop() if rank == 0 else None
 
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
     evals_rank = cfg["P"] * cfg["C"] * cfg["G"] * args.steps
-    value = evals_rank * world / (total_ms / 1000.0)
+    agg = aggregate(sum(step_ms), evals_rank, dist if world > 1 else None, "cuda")
+    total_ms, value = agg["max_ms"], agg["per_s"]
     _, best_cost = prob.best()
 
     # end to end through the public API: host arrays in, best solution out
@@ -589,6 +585,22 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
                         "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
                 "gpu_launches": None, "clocks": clocks}
         print(json.dumps(line), flush=True)
+
+
+def aggregate(local_ms: float, local_units: float, dist=None, device="cpu") -> dict:
+    """Whole-job figures of a timed region over all ranks: the time is the
+    maximum over ranks, the units (move evaluations, solves) their sum."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        world = dist.get_world_size()
+    ms = float(t.item())
+    return {"max_ms": ms, "units": float(u.item()), "per_s": float(u.item()) / (ms / 1000.0),
+            "world": world}
 
 
 # Issue-slot roofline of the evolve kernel: the kernel is bound by integer
