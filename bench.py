@@ -245,6 +245,7 @@ def main():
     if rank == 0:
         sampler.start()
     step_ms, kern_ms = [], []
+    launches0 = cgo.kernel_launches()
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
             flush.fill_(1)                       # evict L2 between steps
@@ -257,6 +258,7 @@ def main():
             step_ms.append(e0.elapsed_time(e1))
             kern_ms.append(prob.last_kernel_time()[0])
     torch.cuda.synchronize()
+    launches = cgo.kernel_launches() - launches0
     barrier()
     clocks = sampler.stop() if rank == 0 else None
 
@@ -302,7 +304,7 @@ def main():
                            "gens_per_s": cfg["G"] / (total_ms / args.steps / 1000.0)},
                 "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": 4 * args.steps,
+                "gpu_launches": launches,
                 "clocks": clocks, "roofline": roof}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(inst, cfg, desc, args.cpu_budget)
@@ -352,6 +354,7 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
     if rank == 0:
         sampler.start()
     ms = []
+    launches0 = cgo.kernel_launches()
     for _ in range(args.steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -361,6 +364,7 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    launches = cgo.kernel_launches() - launches0
     barrier()
     clocks = sampler.stop() if rank == 0 else None
     t = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
@@ -387,8 +391,9 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
     cgo.solve_batch(p2, params, seeds, stream)
     outs = [pp.best() for pp in p2]
     e2e_s = time.perf_counter() - t0
-    h2d = sum(int(sum(np.asarray(x[k]).nbytes for k in ("mat0", "mat1", "vec0", "vec1")
-                      if x.get(k) is not None)) for x in mix)
+    h2d = sum(int(sum(np.asarray(x[k]).nbytes for k in ("mat0", "mat1", "vec0", "vec1", "vec2",
+                                                         "vec3") if x.get(k) is not None))
+              for x in mix)
     d2h = sum(int(o[0].nbytes) + 8 for o in outs)
     for pp in p2:
         pp.close()
@@ -406,7 +411,7 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
                            "autotuner": tuned},
                 "e2e": {"value": evals * world / e2e_s, "unit": "evals/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": None, "clocks": clocks}
+                "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
@@ -481,6 +486,7 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
     probs = [None] * len(trace)
     tickets = [None] * len(trace)
     results = [None] * len(trace)
+    launches0 = cgo.kernel_launches()
     t_start = time.perf_counter()
 
     def producer():
@@ -514,8 +520,15 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
         results[i] = (cost, lat)
         done_at[i] = time.perf_counter() - t_start
     th.join()
+    launches = cgo.kernel_launches() - launches0
     stop_mon[0] = True
     wall = max(done_at) - trace[0][0]
+    # every request's instance arrays go host -> device when it arrives; its
+    # elite cost (int64) comes back when it completes
+    h2d = sum(int(sum(np.asarray(pool[k][f]).nbytes for f in ("mat0", "mat1", "vec0", "vec1", "vec2",
+                                                               "vec3") if pool[k].get(f) is not None))
+              for _, k in trace)
+    d2h = 8 * len(trace)
     print("serve: trace done %.1f s" % (time.perf_counter() - t_start), file=sys.stderr, flush=True)
     clocks = sampler.stop() if rank == 0 else None
     stats = srv.stats()
@@ -582,8 +595,8 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
                            "served_over_one_launch_per_solve": served_solves_s / seq_solves_s,
                            "server": stats},
                 "e2e": {"value": served_solves_s, "unit": "solves/s",
-                        "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
-                "gpu_launches": None, "clocks": clocks}
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 

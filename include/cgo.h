@@ -302,6 +302,12 @@ const char *cgo_last_error(void);
 /* Library version string. */
 const char *cgo_version(void);
 
+/* Number of kernels this library has launched in this process, on any
+ * device and from any thread (a replayed graph adds its kernel nodes).  A
+ * monotone counter for accounting; it has no counterpart in the method.
+ * out: host pointer; CGO_ERR_INVALID if NULL. */
+cgo_status cgo_kernel_launches(uint64_t *out);
+
 /* Testing hook (host-side fault injection; never faults the GPU).
  * what = 1: `value` phantom members (0 .. 1024) are added to every member
  *           barrier of the next solves, so no barrier can complete and the

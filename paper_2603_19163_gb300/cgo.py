@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
                 "cgo_solve_batch": ([P(vp), P(cgo_params), P(c.c_uint64), c.c_int32, vp], c.c_int),
                 "cgo_last_error": ([], c.c_char_p),
                 "cgo_version": ([], c.c_char_p),
+                "cgo_kernel_launches": ([P(c.c_uint64)], c.c_int),
                 "cgo_debug_inject": ([vp, c.c_int32, c.c_int64], c.c_int),
                 "cgo_last_kernel_time": ([vp, P(c.c_double), _i64p], c.c_int),
                 "cgo_solve_static": ([P(cgo_problem_desc), P(cgo_params), c.c_uint64, vp, vp, vp],
@@ -141,6 +142,13 @@ class CgoError(RuntimeError):
 def check(status: int, where: str) -> None:
     if status != OK:
         raise CgoError(status, where)
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    v = ctypes.c_uint64(0)
+    check(lib().cgo_kernel_launches(ctypes.byref(v)), "cgo_kernel_launches")
+    return int(v.value)
 
 
 # ------------------------------------------------------------------ params

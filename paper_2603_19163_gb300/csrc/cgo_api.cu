@@ -452,6 +452,12 @@ const char *cgo_last_error(void) { return g_err.c_str(); }
 
 const char *cgo_version(void) { return "cgo 0.1 (sm_103a)"; }
 
+cgo_status cgo_kernel_launches(uint64_t *out) {
+  if (!out) return fail(CGO_ERR_INVALID, "out is NULL");
+  *out = launches_total();
+  return CGO_OK;
+}
+
 cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
   if (!out) return fail(CGO_ERR_INVALID, "out is NULL");
   *out = nullptr;
@@ -972,7 +978,10 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
       e = ce != cudaSuccess ? ce : ee;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    for (int64_t k = 0; k < nslices && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, st);
+    for (int64_t k = 0; k < nslices && e == cudaSuccess; ++k) {
+      e = cudaGraphLaunch(exec, st);
+      if (e == cudaSuccess) note_launches(nb);
+    }
     if (cap) cudaStreamDestroy(cap);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

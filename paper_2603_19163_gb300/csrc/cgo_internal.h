@@ -102,5 +102,8 @@ int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, bool staged);
 int64_t smem_instance(const KInst &h);
 int max_coresident_ctas(const KInst &h, int warps, int wpm, int64_t smem_bytes);
 int64_t max_smem_optin();
+// process-wide count of kernels launched by the library
+void note_launches(uint64_t n);
+uint64_t launches_total();
 
 }  // namespace cgo

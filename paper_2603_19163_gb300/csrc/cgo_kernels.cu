@@ -11,8 +11,12 @@
 // (global-memory counters, bounded wait) where the AOS counts are summed and
 // every warp applies Eq. "ema", the stagnation rule and, when due, elite
 // injection (Alg. "aos", Sec. 3.4.3, 4.2).
+#include <atomic>
 #include <climits>
 #include <type_traits>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <cooperative_groups.h>
 
 #include "cgo_device.cuh"
@@ -1203,6 +1207,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
   }
 }
 
+// the host reserves 1 KB of each CTA's shared memory for these statics
+static_assert(sizeof(KInst) + 16 <= 1024, "static shared memory of batch_kernel exceeds its reserve");
+
 // ---------------------------------------------------------------- init
 __device__ long long full_cost(const KInst &I, const int32_t *x) {
   const int n = I.n;
@@ -1406,28 +1413,38 @@ __global__ void copy_elite_kernel(const DevAos *aos, const int32_t *bestsol, int
 }
 
 // ------------------------------------------------------------ launchers
+// Kernels this library has put on a device (every launch that returned
+// success; the kernels of a replayed graph are added by the replaying code).
+static std::atomic<uint64_t> g_launches{0};
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+static cudaError_t counted(cudaError_t e, uint64_t n = 1) {
+  if (e == cudaSuccess) note_launches(n);
+  return e;
+}
+
 cudaError_t launch_tsp_check(const int32_t *d_mat, int n, uint32_t *d_flags, cudaStream_t st) {
   const int64_t total = (int64_t)n * n;
   const int blocks = (int)min((int64_t)1024, (total + 255) / 256);
   tsp_check_kernel<<<blocks, 256, 0, st>>>(d_mat, n, d_flags);
-  return cudaGetLastError();
+  return counted(cudaGetLastError());
 }
 
 cudaError_t launch_copy_elite(const DevAos *d_aos, const int32_t *d_bestsol, int len,
                               int32_t *out_sol, int64_t *out_cost, cudaStream_t st) {
   copy_elite_kernel<<<1, 256, 0, st>>>(d_aos, d_bestsol, len, out_sol, out_cost);
-  return cudaGetLastError();
+  return counted(cudaGetLastError());
 }
 
 cudaError_t launch_init(const KInst &h, cudaStream_t st) {
   const int threads = 128, blocks = (h.P + threads - 1) / threads;
   init_kernel<<<blocks, threads, 0, st>>>(h);
-  return cudaGetLastError();
+  return counted(cudaGetLastError());
 }
 
 cudaError_t launch_init_aos(const KInst &h, const DevAos &a0, cudaStream_t st) {
   init_aos_kernel<<<1, 256, 0, st>>>(h, a0);
-  return cudaGetLastError();
+  return counted(cudaGetLastError());
 }
 
 cudaError_t launch_init_batch(const KInst *d_insts, const DevAos *d_a0s, int count, cudaStream_t st) {
@@ -1436,19 +1453,19 @@ cudaError_t launch_init_batch(const KInst *d_insts, const DevAos *d_a0s, int cou
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   init_aos_batch_kernel<<<count, 256, 0, st>>>(d_insts, d_a0s);
-  return cudaGetLastError();
+  return counted(cudaGetLastError(), 2);
 }
 
 cudaError_t launch_finalize(const KInst &h, cudaStream_t st) {
   finalize_kernel<<<1, 256, 0, st>>>(h);
-  return cudaGetLastError();
+  return counted(cudaGetLastError());
 }
 
 cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri, cudaStream_t st) {
   const int64_t total = (int64_t)n * n;
   const int blocks = (int)min((int64_t)1024, (total + 255) / 256);
   triangle_kernel<<<blocks, 256, 0, st>>>(d_mat, n, tri16, d_tri);
-  return cudaGetLastError();
+  return counted(cudaGetLastError());
 }
 
 template <int MODEL, bool T16>
@@ -1476,12 +1493,31 @@ int64_t max_smem_optin() {
   return v;
 }
 
+// A kernel function's dynamic shared-memory limit is process-wide state, so
+// it is raised once per device to the most the device allows and never set
+// per launch: launches of one function with different sizes (the nodes of a
+// captured graph, other host threads, a profiler replaying a node) must not
+// see a smaller limit that was set for someone else.
+static cudaError_t open_smem(const void *fn) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void *>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({dev, fn})) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(max_smem_optin() - (int64_t)fa.sharedSizeBytes));
+  if (e == cudaSuccess) done.insert({dev, fn});
+  return e;
+}
+
 int max_coresident_ctas(const KInst &h, int warps, int wpm, int64_t smem_bytes) {
   const void *fn = pick_evolve(h, wpm);
   if (!fn) return 0;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
-      cudaSuccess)
-    return 0;
+  if (open_smem(fn) != cudaSuccess) return 0;
   int per_sm = 0, dev = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, (size_t)smem_bytes) !=
       cudaSuccess)
@@ -1495,14 +1531,14 @@ cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int64_t sme
                                  uint64_t timeout_ns, cudaStream_t st) {
   const void *fn = pick_evolve(h, wpm);
   if (!fn) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes);
+  cudaError_t e = open_smem(fn);
   if (e != cudaSuccess) return e;
   const int groups = warps / wpm;
   const int grid = (h.P + groups - 1) / groups;
   KInst hi = h;
   void *args[] = {(void *)&hi, (void *)&warps, (void *)&timeout_ns};
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(warps * 32), args, (size_t)smem_bytes, st);
+  return counted(
+      cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(warps * 32), args, (size_t)smem_bytes, st));
 }
 
 template <int MODEL, bool T16>
@@ -1526,9 +1562,7 @@ static const void *pick_batch(int model, int tri16, int wpm) {
 int batch_ctas_per_sm(int model, int tri16, int warps, int wpm, int64_t smem_bytes) {
   const void *fn = pick_batch(model, tri16, wpm);
   if (!fn) return 0;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
-      cudaSuccess)
-    return 0;
+  if (open_smem(fn) != cudaSuccess) return 0;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, (size_t)smem_bytes) !=
       cudaSuccess)
@@ -1541,8 +1575,7 @@ cudaError_t launch_batch(int model, int tri16, const KInst *d_insts, const int *
                          int grid, int64_t slice, uint64_t timeout_ns, cudaStream_t st) {
   const void *fn = pick_batch(model, tri16, wpm);
   if (!fn) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes);
+  cudaError_t e = open_smem(fn);
   if (e != cudaSuccess) return e;
   void *args[] = {(void *)&d_insts, (void *)&d_list, (void *)&d_count, (void *)&d_next,
                   (void *)&warps, (void *)&slice, (void *)&timeout_ns};

@@ -242,6 +242,7 @@ void server_loop(cgo_server *S) {
                           S->st);
     if (e == cudaSuccess && S->dirty) e = capture_slice(S);
     if (e == cudaSuccess) e = cudaGraphLaunch(S->exec, S->st);
+    if (e == cudaSuccess) note_launches(S->buckets.size());
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
     if (e != cudaSuccess) {
       fail_all(S, CGO_ERR_CUDA, cudaGetErrorString(e));

@@ -75,3 +75,12 @@ def test_errors_are_reported_without_a_gpu_call():
     assert L.cgo_problem_create(ctypes.byref(d), ctypes.byref(h)) == cgo.ERR_INVALID
     assert b"struct_size" in L.cgo_last_error()
     assert L.cgo_solve(None, None, 0, None) == cgo.ERR_INVALID
+
+
+def test_launch_counter_without_a_gpu():
+    from paper_2603_19163_gb300 import cgo
+    L = cgo.lib()
+    assert L.cgo_kernel_launches(None) == cgo.ERR_INVALID
+    before = cgo.kernel_launches()
+    assert before >= 0
+    assert cgo.kernel_launches() == before      # nothing launched in between
