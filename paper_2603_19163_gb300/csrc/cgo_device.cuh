@@ -3,6 +3,7 @@
 // Q16 AOS update, warp reductions and the permutation-move algebra.
 #pragma once
 #include <stdint.h>
+#include <climits>
 
 #include "cgo_internal.h"
 
@@ -203,16 +204,17 @@ __device__ __forceinline__ void aos_update_lanes(uint32_t (&wop)[NO], uint32_t (
 }
 
 // Lexicographic (delta, index) minimum over the warp; every lane gets it.
+// Signed 64-bit order is (signed high word, unsigned low word), so three
+// warp reductions (high, low among the lanes holding the high minimum, index
+// among the lanes holding both) give the minimum pair.
 __device__ __forceinline__ void warp_argmin(long long &d, int &c) {
-#pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    const long long d2 = __shfl_xor_sync(kFull, d, off);
-    const int c2 = __shfl_xor_sync(kFull, c, off);
-    if (d2 < d || (d2 == d && c2 < c)) {
-      d = d2;
-      c = c2;
-    }
-  }
+  const int hi = (int)(d >> 32);
+  const uint32_t lo = (uint32_t)d;
+  const int hmin = __reduce_min_sync(kFull, hi);
+  const uint32_t lmin = __reduce_min_sync(kFull, hi == hmin ? lo : 0xFFFFFFFFu);
+  const int cmin = __reduce_min_sync(kFull, (hi == hmin && lo == lmin) ? c : INT_MAX);
+  d = (long long)(((uint64_t)(uint32_t)hmin << 32) | lmin);
+  c = cmin;
 }
 
 __device__ __forceinline__ uint64_t global_ns() {

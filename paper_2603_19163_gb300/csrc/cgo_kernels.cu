@@ -699,9 +699,12 @@ constexpr int kLocalBar = 15;
 
 // group-wide barrier wait: the group's first warp waits, the group follows.
 // CTA-local instances (nact > 0) meet at a named barrier of all active threads.
+// Ordering: bar.sync orders every thread's prior memory accesses for the
+// threads of the CTA, so a CTA-local barrier needs no fence; across CTAs the
+// arriving warp fences (gpu scope, cumulative over what the group's named
+// barrier made it observe) before it arrives, and polls with acquire loads.
 __device__ bool group_barrier(DevSync *S, uint32_t arrivals, uint32_t target, uint64_t timeout_ns,
                               const Group &G, int *flag, int nact) {
-  __threadfence();
   if (nact > 0) {
     cta_bar(kLocalBar, nact);
     return true;
@@ -794,10 +797,19 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   stats_zero(st);
   const int span = WPM * 32;
   const int cpl = (C + span - 1) / span;
+  const bool packed = 96ull * (uint64_t)cpl * (uint64_t)I.U * (uint64_t)mine < 65536ull;
 
-  int64_t g = I.g_begin;
-  while (g < I.g_end) {
-    const int64_t wend = min(I.g_end, (g / I.U + 1) * (int64_t)I.U);
+  // generations are below 2^32 (checked on the host), so window arithmetic
+  // is 32-bit
+  const uint32_t U = (uint32_t)I.U, gend = (uint32_t)I.g_end;
+  // acceptance variates of one aligned block of 32 generations, lane q
+  // holding generation 32 * eblk + q; kept across windows while the group
+  // evolves a single member
+  uint64_t Ereg = 0;
+  int64_t eblk = -1;
+  uint32_t g = (uint32_t)I.g_begin;
+  while (g < gend) {
+    const uint32_t wend = min(gend, (g / U + 1u) * U);
     const uint64_t Tw = T;
     long long minbest = LLONG_MAX;
     for (int e = 0; e < mine; ++e) {
@@ -807,17 +819,18 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       long long *loads = (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m;
       SolScal sc = scal[ls];
       T = Tw;
-      for (int64_t gb = g; gb < wend; gb += 32) {
-        const int cnt = (int)min((int64_t)32, wend - gb);
-        uint64_t Ereg = 0;
-        if (lane < cnt) {
-          const uint4 Ra = philox(ctr_word(0, 0, kKindAccept), X.tag, p, (uint32_t)(gb + lane), X.k0,
-                                  X.k1);
-          Ereg = exp_variate_q32(Ra.x);
-        }
-        for (int q = 0; q < cnt; ++q) {
-          const uint32_t gg = (uint32_t)(gb + q);
-          const uint64_t E = __shfl_sync(kFull, Ereg, q);
+      if (mine > 1) eblk = -1;
+      {
+        for (uint32_t gg = g; gg < wend; ++gg) {
+          if ((int64_t)(gg >> 5) != eblk) {
+            eblk = gg >> 5;
+            const uint4 Ra = philox(ctr_word(0, 0, kKindAccept), X.tag, p, (gg & ~31u) + lane, X.k0,
+                                    X.k1);
+            Ereg = exp_variate_q32(Ra.x);
+          }
+          const uint64_t E = __shfl_sync(kFull, Ereg, gg & 31u);
+          // the next temperature does not depend on this generation
+          const uint64_t Tn = cool(T, I.alpha);
           long long bd = LLONG_MAX;
           int bc = INT_MAX;
           CandMoves cbest;
@@ -873,7 +886,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
               for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
             }
           }
-          T = cool(T, I.alpha);
+          T = Tn;
         }
       }
       G.sync();
@@ -882,20 +895,37 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       minbest = min(minbest, sc.best);
     }
     g = wend;
-    if (g % I.U != 0) continue;  // only at the very end of a launch
+    if (g % U != 0) continue;  // only at the very end of a launch
 
     // ------------------------------------------------ AOS window end
-    const bool inject = I.E > 0 && (g % I.E) == 0;
+    const bool inject = I.E > 0 && (g % (uint32_t)I.E) == 0;
     uint32_t tot[NO * 2 + 6];
+    if (packed) {
+      // a lane counts at most 3 * cpl * U * mine uses per window, so the warp
+      // totals of a (uses, improvements) pair fit 16 bits each
 #pragma unroll
-    for (int l = 0; l < NO; ++l) {
-      tot[l] = __reduce_add_sync(kFull, st.u[l]);
-      tot[NO + l] = __reduce_add_sync(kFull, st.v[l]);
-    }
+      for (int l = 0; l < NO; ++l) {
+        const uint32_t t = __reduce_add_sync(kFull, st.u[l] | (st.v[l] << 16));
+        tot[l] = t & 0xFFFFu;
+        tot[NO + l] = t >> 16;
+      }
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      tot[2 * NO + i] = __reduce_add_sync(kFull, st.uk[i]);
-      tot[2 * NO + 3 + i] = __reduce_add_sync(kFull, st.vk[i]);
+      for (int i = 0; i < 3; ++i) {
+        const uint32_t t = __reduce_add_sync(kFull, st.uk[i] | (st.vk[i] << 16));
+        tot[2 * NO + i] = t & 0xFFFFu;
+        tot[2 * NO + 3 + i] = t >> 16;
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < NO; ++l) {
+        tot[l] = __reduce_add_sync(kFull, st.u[l]);
+        tot[NO + l] = __reduce_add_sync(kFull, st.v[l]);
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        tot[2 * NO + i] = __reduce_add_sync(kFull, st.uk[i]);
+        tot[2 * NO + 3 + i] = __reduce_add_sync(kFull, st.vk[i]);
+      }
     }
     uint32_t my = 0;
 #pragma unroll
