@@ -298,6 +298,7 @@ def main():
                 "config": {"workload": desc, "l2": "flushed between steps (512 MB write)",
                            "launch": {"warps_per_cta": shape[0], "warps_per_member": shape[1],
                                       "staging": ["auto", "smem", "global"][shape[2]],
+                                      "gens_in_flight": shape[3],
                                       "chosen_by": "autotuner (%d trial shapes)" % len(
                                           tuner.solve_shapes(params))},
                            "best_cost": int(best_cost),

@@ -136,14 +136,23 @@ typedef struct {
 } cgo_state;
 
 /* Launch shape (the autotuner's choice, or a caller override).  The C
- * candidates of a member are split over warps_per_member warps; a CTA holds
- * warps_per_cta / warps_per_member members. */
+ * candidates of a member's generation are split over warps_per_member warps.
+ * With gens_in_flight = 2 a member has two such warp sets: one evaluates
+ * generation g, the other generation g + 1 against the same solution, which
+ * stands unless g accepts a move (then g + 1 is evaluated again); the
+ * results are the same either way.  A CTA holds
+ * warps_per_cta / (warps_per_member * gens_in_flight) members.  Launch
+ * shapes never change results. */
 typedef struct {
   uint32_t struct_size;        /* = sizeof(cgo_launch) */
-  int32_t warps_per_cta;       /* 0 = auto; else 1 .. 8, a multiple of warps_per_member */
+  int32_t warps_per_cta;       /* 0 = auto; else 1 .. 8, a multiple of
+                                  warps_per_member * gens_in_flight */
   int32_t warps_per_member;    /* 0 = auto; else 1, 2 or 4 */
   int32_t staging;             /* 0 = auto, 1 = instance data in shared memory,
                                   2 = instance data read through L2 */
+  int32_t gens_in_flight;      /* 0 = auto; 1; or 2 (single solves with at most
+                                  32 * warps_per_member candidates; batched
+                                  solves use 1) */
 } cgo_launch;
 
 /* Create a problem: validates the description and deep-copies the data to

@@ -31,27 +31,33 @@ class Autotuner:
         self.log: list = []
 
     # ------------------------------------------------------------- single
-    def solve_shapes(self, params: dict) -> list[tuple[int, int, int]]:
+    def solve_shapes(self, params: dict) -> list[tuple[int, int, int, int]]:
+        """(warps per CTA, warps per member generation, staging, generations
+        in flight) candidates for a single solve."""
         out = []
         for wpm in (4, 2, 1):
             if wpm * 32 > max(32, params["C"]) * 2:
                 continue
-            for mpc in (1, 2):
-                if wpm * mpc <= 8:
-                    for staging in (SMEM, GLOBAL):
-                        out.append((wpm * mpc, wpm, staging))
+            for ns in (2, 1):
+                if ns == 2 and params["C"] > 32 * wpm:
+                    continue
+                for mpc in (1, 2):
+                    if wpm * ns * mpc <= 8:
+                        for staging in (SMEM, GLOBAL):
+                            out.append((wpm * ns * mpc, wpm, staging, ns))
         return out
 
-    def tune_solve(self, prob: "C.Problem", params: dict, seed: int = 1) -> tuple[int, int, int]:
-        """Pick (warps per CTA, warps per member, staging) for cgo_solve of
-        this problem and apply it; returns the choice."""
+    def tune_solve(self, prob: "C.Problem", params: dict, seed: int = 1) -> tuple[int, int, int, int]:
+        """Pick (warps per CTA, warps per member generation, staging,
+        generations in flight) for cgo_solve of this problem and apply it;
+        returns the choice."""
         key = _key(prob, params)
         if key not in self.cache_solve:
             trial = dict(params, G=self.trial)
             best = None
             for shape in self.solve_shapes(params):
                 try:
-                    prob.set_launch(shape[0], staging=shape[2], wpm=shape[1])
+                    prob.set_launch(shape[0], staging=shape[2], wpm=shape[1], ns=shape[3])
                     prob.solve(trial, seed)
                     ms, gens = prob.last_kernel_time()
                 except C.CgoError:
@@ -64,7 +70,7 @@ class Autotuner:
                 raise RuntimeError("no launch shape runs for %r" % (key,))
             self.cache_solve[key] = best[1]
         shape = self.cache_solve[key]
-        prob.set_launch(shape[0], staging=shape[2], wpm=shape[1])
+        prob.set_launch(shape[0], staging=shape[2], wpm=shape[1], ns=shape[3])
         return shape
 
     # ------------------------------------------------------------ batched

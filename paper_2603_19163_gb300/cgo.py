@@ -77,7 +77,8 @@ class cgo_server_info(ctypes.Structure):
 
 class cgo_launch(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("warps_per_cta", ctypes.c_int32),
-                ("warps_per_member", ctypes.c_int32), ("staging", ctypes.c_int32)]
+                ("warps_per_member", ctypes.c_int32), ("staging", ctypes.c_int32),
+                ("gens_in_flight", ctypes.c_int32)]
 
 
 _LIB = None
@@ -240,15 +241,18 @@ class Problem:
         check(lib().cgo_params_default(self.h, ctypes.byref(q)), "cgo_params_default")
         return params_dict(q)
 
-    def set_launch(self, warps: int = 0, staging: int = 0, wpm: int = 0):
-        l = cgo_launch(ctypes.sizeof(cgo_launch), warps, wpm, staging)
+    def set_launch(self, warps: int = 0, staging: int = 0, wpm: int = 0, ns: int = 0):
+        """Launch override (0 = automatic): warps per CTA, staging mode,
+        warps per member generation, generations in flight."""
+        l = cgo_launch(ctypes.sizeof(cgo_launch), warps, wpm, staging, ns)
         check(lib().cgo_set_launch(self.h, ctypes.byref(l)), "cgo_set_launch")
 
-    def get_launch(self) -> tuple[int, int, int]:
-        """(warps per CTA, warps per member, staging) of the last solve."""
+    def get_launch(self) -> tuple[int, int, int, int]:
+        """(warps per CTA, warps per member generation, staging, generations
+        in flight) of the last solve."""
         l = cgo_launch()
         check(lib().cgo_get_launch(self.h, ctypes.byref(l)), "cgo_get_launch")
-        return l.warps_per_cta, l.warps_per_member, l.staging
+        return l.warps_per_cta, l.warps_per_member, l.staging, l.gens_in_flight
 
     def solve(self, params: dict, seed: int, stream=None):
         q = params_struct(params)

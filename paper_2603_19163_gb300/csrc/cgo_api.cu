@@ -279,40 +279,59 @@ KInst base_kinst(const cgo_problem *p) {
   return h;
 }
 
-// Launch shape: warps per member (candidates split across them), members
-// per CTA and staging mode.  Prefers one member per CTA (most SMs, least
-// shared-memory pressure) and grows the CTA only when the population would
-// not be co-resident otherwise.
-cgo_status choose_launch(cgo_problem *p, KInst &h, int *warps_out, int *wpm_out,
+// Launch shape: warps per member generation (candidates split across
+// them), generations in flight, members per CTA and staging mode.  Prefers
+// two generations in flight where a lane holds one candidate, and one member
+// per CTA (most SMs, least shared-memory pressure); grows the CTA only when
+// the population would not be co-resident otherwise.
+cgo_status choose_launch(cgo_problem *p, KInst &h, int *warps_out, int *wpm_out, int *ns_out,
                          int64_t *smem_out) {
   const int64_t optin = max_smem_optin();
   const int P = h.P, C = h.C;
   int wpm = p->wpm_override;
   if (wpm == 0) wpm = C >= 128 ? 4 : (C >= 64 ? 2 : 1);
+  // a second generation in flight holds one candidate's counts per lane
+  const bool two_ok = C <= 32 * wpm && 2 * wpm <= kMaxWarps;
+  int ns_try[2] = {2, 1}, nns = 2;
+  if (p->ns_override == 2) {
+    if (!two_ok)
+      return fail(CGO_ERR_UNSUPPORTED,
+                  "two generations in flight need C <= 32 * warps_per_member and 2 * warps_per_member <= %d",
+                  kMaxWarps);
+    nns = 1;
+  } else if (p->ns_override == 1 || !two_ok) {
+    ns_try[0] = 1;
+    nns = 1;
+  }
   int fit_seen = 0, grid_seen = 0;
-  for (int mpc = 1; mpc * wpm <= kMaxWarps; mpc *= 2) {
-    const int warps = mpc * wpm;
-    if (p->warps_override > 0 && warps != p->warps_override) continue;
-    const int64_t staged = evolve_smem_bytes(h, warps, wpm, true);
-    const int64_t global = evolve_smem_bytes(h, warps, wpm, false);
-    bool use_smem = staged <= optin;
-    if (p->staging_override == STAGE_GLOBAL) use_smem = false;
-    if (p->staging_override == STAGE_SMEM && !use_smem) continue;
-    const int64_t need = use_smem ? staged : global;
-    if (need > optin) continue;
-    h.shared_bytes = use_smem ? instance_data_bytes(h) : 0;
-    const int grid = (P + mpc - 1) / mpc;
-    const int fit = max_coresident_ctas(h, warps, wpm, need);
-    fit_seen = fit;
-    grid_seen = grid;
-    if (fit >= grid) {
-      *warps_out = warps;
-      *wpm_out = wpm;
-      *smem_out = need;
-      p->last_warps = warps;
-      p->last_wpm = wpm;
-      p->last_staging = use_smem ? STAGE_SMEM : STAGE_GLOBAL;
-      return CGO_OK;
+  for (int t = 0; t < nns; ++t) {
+    const int ns = ns_try[t];
+    for (int mpc = 1; mpc * wpm * ns <= kMaxWarps; mpc *= 2) {
+      const int warps = mpc * wpm * ns;
+      if (p->warps_override > 0 && warps != p->warps_override) continue;
+      const int64_t staged = evolve_smem_bytes(h, warps, wpm, ns, true);
+      const int64_t global = evolve_smem_bytes(h, warps, wpm, ns, false);
+      bool use_smem = staged <= optin;
+      if (p->staging_override == STAGE_GLOBAL) use_smem = false;
+      if (p->staging_override == STAGE_SMEM && !use_smem) continue;
+      const int64_t need = use_smem ? staged : global;
+      if (need > optin) continue;
+      h.shared_bytes = use_smem ? instance_data_bytes(h) : 0;
+      const int grid = (P + mpc - 1) / mpc;
+      const int fit = max_coresident_ctas(h, warps, wpm, ns, need);
+      fit_seen = fit;
+      grid_seen = grid;
+      if (fit >= grid) {
+        *warps_out = warps;
+        *wpm_out = wpm;
+        *ns_out = ns;
+        *smem_out = need;
+        p->last_warps = warps;
+        p->last_wpm = wpm;
+        p->last_ns = ns;
+        p->last_staging = use_smem ? STAGE_SMEM : STAGE_GLOBAL;
+        return CGO_OK;
+      }
     }
   }
   if (grid_seen)
@@ -338,9 +357,9 @@ cgo_status run_generations(cgo_problem *p, int64_t G, cudaStream_t st) {
   if (G == 0) return CGO_OK;
   if (p->g + G >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "generation index would exceed 2^32 - 2");
   KInst h = base_kinst(p);
-  int warps = 0, wpm = 1;
+  int warps = 0, wpm = 1, ns = 1;
   int64_t smem = 0;
-  cgo_status s = choose_launch(p, h, &warps, &wpm, &smem);
+  cgo_status s = choose_launch(p, h, &warps, &wpm, &ns, &smem);
   if (s != CGO_OK) return s;
   h.members = p->params.population + (int)p->phantom_members;  // test hook adds phantoms
   h.g_begin = p->g;
@@ -354,7 +373,7 @@ cgo_status run_generations(cgo_problem *p, int64_t G, cudaStream_t st) {
     CUDA_TRY(cudaEventCreate(&p->ev1), "event");
   }
   CUDA_TRY(cudaEventRecord(p->ev0, st), "event");
-  CUDA_TRY(launch_evolve_single(h, warps, wpm, smem, p->timeout_ns, st), "evolve launch");
+  CUDA_TRY(launch_evolve_single(h, warps, wpm, ns, smem, p->timeout_ns, st), "evolve launch");
   CUDA_TRY(cudaEventRecord(p->ev1, st), "event");
   p->timed = true;
   p->timed_gens = G;
@@ -648,12 +667,17 @@ cgo_status cgo_set_launch(cgo_problem *p, const cgo_launch *l) {
   if (l->warps_per_member != 0 && l->warps_per_member != 1 && l->warps_per_member != 2 &&
       l->warps_per_member != 4)
     return fail(CGO_ERR_INVALID, "warps_per_member must be 0, 1, 2 or 4");
-  if (l->warps_per_cta > 0 && l->warps_per_member > 0 && l->warps_per_cta % l->warps_per_member)
-    return fail(CGO_ERR_INVALID, "warps_per_cta must be a multiple of warps_per_member");
+  if (l->gens_in_flight < 0 || l->gens_in_flight > 2)
+    return fail(CGO_ERR_INVALID, "gens_in_flight must be 0, 1 or 2");
+  const int unit = (l->warps_per_member > 0 ? l->warps_per_member : 1) *
+                   (l->gens_in_flight > 0 ? l->gens_in_flight : 1);
+  if (l->warps_per_cta > 0 && l->warps_per_cta % unit)
+    return fail(CGO_ERR_INVALID, "warps_per_cta must be a multiple of warps_per_member * gens_in_flight");
   if (l->staging < 0 || l->staging > 2) return fail(CGO_ERR_INVALID, "staging must be 0, 1 or 2");
   p->warps_override = l->warps_per_cta;
   p->wpm_override = l->warps_per_member;
   p->staging_override = l->staging;
+  p->ns_override = l->gens_in_flight;
   return CGO_OK;
 }
 
@@ -663,6 +687,7 @@ cgo_status cgo_get_launch(const cgo_problem *p, cgo_launch *l) {
   l->warps_per_cta = p->last_warps;
   l->warps_per_member = p->last_wpm;
   l->staging = p->last_staging;
+  l->gens_in_flight = p->last_ns;
   return CGO_OK;
 }
 
@@ -999,6 +1024,7 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
     for (int i : buckets[b].members) {
       probs[i]->last_warps = buckets[b].warps;
       probs[i]->last_wpm = buckets[b].wpm;
+      probs[i]->last_ns = 1;
       probs[i]->last_staging = hk[(size_t)i].shared_bytes > 0 ? STAGE_SMEM : STAGE_GLOBAL;
     }
   return CGO_OK;
@@ -1084,17 +1110,17 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
   int cur_aos = 0;
   if (q->generations > 0) {
     if (q->generations >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "too many generations");
-    int warps = 0, wpm = 1;
+    int warps = 0, wpm = 1, ns = 1;
     int64_t smem = 0;
     h = base_kinst(&p);
-    if ((s = choose_launch(&p, h, &warps, &wpm, &smem)) != CGO_OK) return s;
+    if ((s = choose_launch(&p, h, &warps, &wpm, &ns, &smem)) != CGO_OK) return s;
     h.g_begin = 0;
     h.g_end = q->generations;
     h.aos_in = aos;
     h.aos_out = aos + 1;
     CUDA_TRY(cudaMemsetAsync(sync, 0, sizeof(DevSync), st), "scratch reset");
     CUDA_TRY(cudaMemsetAsync(sync->elite, 0x7F, sizeof(sync->elite), st), "scratch reset");
-    CUDA_TRY(launch_evolve_single(h, warps, wpm, smem, p.timeout_ns, st), "evolve launch");
+    CUDA_TRY(launch_evolve_single(h, warps, wpm, ns, smem, p.timeout_ns, st), "evolve launch");
     CUDA_TRY(launch_finalize(h, st), "finalize launch");
     cur_aos = 1;
   }

@@ -34,8 +34,8 @@ struct cgo_problem {
   int aos_cur = 0;
   int64_t g = 0;
   // launch shape
-  int warps_override = 0, wpm_override = 0, staging_override = 0;
-  int last_warps = 0, last_wpm = 0, last_staging = 0;
+  int warps_override = 0, wpm_override = 0, staging_override = 0, ns_override = 0;
+  int last_warps = 0, last_wpm = 0, last_staging = 0, last_ns = 0;
   // events around the last evolve launch (kernel time on the launching stream)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;

@@ -81,7 +81,7 @@ struct KInst {
 // host-side launchers (cgo_kernels.cu)
 cudaError_t launch_init(const KInst &h, cudaStream_t st);
 cudaError_t launch_init_aos(const KInst &h, const DevAos &a0, cudaStream_t st);
-cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int64_t smem_bytes,
+cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int ns, int64_t smem_bytes,
                                  uint64_t timeout_ns, cudaStream_t st);
 cudaError_t launch_finalize(const KInst &h, cudaStream_t st);
 cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri,
@@ -98,9 +98,9 @@ int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged);
 // shared-memory needs of the evolve kernel
 int64_t smem_per_warp(const KInst &h);
 int64_t instance_data_bytes(const KInst &h);
-int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, bool staged);
+int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, int ns, bool staged);
 int64_t smem_instance(const KInst &h);
-int max_coresident_ctas(const KInst &h, int warps, int wpm, int64_t smem_bytes);
+int max_coresident_ctas(const KInst &h, int warps, int wpm, int ns, int64_t smem_bytes);
 int64_t max_smem_optin();
 // process-wide count of kernels launched by the library
 void note_launches(uint64_t n);

@@ -54,9 +54,10 @@ struct Layout {
 
 __host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64_t(15); }
 
-// per member group: 2*wpm partial argmins (16 B), a flag (16 B), the
-// winner's moves (4 x 16 B) and each warp's window counts (32 x 4 B)
-__host__ __device__ inline int64_t group_bytes(int wpm) { return 2 * wpm * 16 + 16 + 64 + wpm * 128; }
+// per member group of nw warps: two buffers of per-warp partial argmins
+// (16 B each), a flag (16 B), two buffers of per-warp winner moves (64 B
+// each) and each warp's window counts (32 x 4 B)
+__host__ __device__ inline int64_t group_bytes(int nw) { return 2 * nw * 16 + 16 + 2 * nw * 64 + nw * 128; }
 
 // Shared memory of one CTA: [instance data][members' solutions][one scratch
 // array per member group][member scalars][GAP loads][per-group partials]
@@ -126,21 +127,35 @@ __device__ __forceinline__ void stats_zero(Stats<NO> &s) {
   for (int i = 0; i < 3; ++i) s.uk[i] = s.vk[i] = 0;
 }
 
-template <int NO>
-__device__ __forceinline__ void stats_op(Stats<NO> &s, int op, uint32_t imp) {
-#pragma unroll
-  for (int i = 0; i < NO; ++i) {
-    const uint32_t hit = (op == i);
-    s.u[i] += hit;
-    s.v[i] += hit & imp;
-  }
+// What one candidate adds to the window counts, packed in a word: the local
+// operator of each of its three steps (bits 3t..3t+2, 7 = step not taken),
+// its step count k (bits 9-10) and whether it improves (bit 11).  A record
+// is added to the counts only once its generation is decided on the solution
+// it was evaluated against.
+__device__ __forceinline__ uint32_t stats_record(int op0, int op1, int op2, int k, uint32_t imp) {
+  const uint32_t a = op0 < 0 ? 7u : (uint32_t)op0, b = op1 < 0 ? 7u : (uint32_t)op1,
+                 c = op2 < 0 ? 7u : (uint32_t)op2;
+  return a | (b << 3) | (c << 6) | ((uint32_t)k << 9) | (imp << 11);
 }
 
+constexpr uint32_t kNoRecord = 0x1FFu;  // no step taken, k = 0
+
 template <int NO>
-__device__ __forceinline__ void stats_k(Stats<NO> &s, int k, uint32_t imp) {
+__device__ __forceinline__ void stats_add(Stats<NO> &s, uint32_t rec) {
+  const uint32_t imp = (rec >> 11) & 1u, k = (rec >> 9) & 3u;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const uint32_t op = (rec >> (3 * t)) & 7u;
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+      const uint32_t hit = (op == (uint32_t)i);
+      s.u[i] += hit;
+      s.v[i] += hit & imp;
+    }
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const uint32_t hit = (k == i + 1);
+    const uint32_t hit = (k == (uint32_t)(i + 1));
     s.uk[i] += hit;
     s.vk[i] += hit & imp;
   }
@@ -417,7 +432,7 @@ __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl
 template <int MODEL, bool T16>
 __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl *sol,
                                                     const Weights<4> &W, uint32_t c, uint32_t p,
-                                                    uint32_t g, Stats<4> &st, CandMoves &cm) {
+                                                    uint32_t g, uint32_t &rec, CandMoves &cm) {
   if constexpr (MODEL == QAP || MODEL == CVRPTW) {
     // O(n) / O(route) deltas: evaluate only the k steps that count
     const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
@@ -435,11 +450,7 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
         d += perm_delta<MODEL, T16>(X, sol, cm.m[t], cm.m[0], cm.m[1], t);
       }
     }
-    const uint32_t imp = d < 0;
-    stats_op(st, ops[0], imp);
-    stats_op(st, ops[1], imp);
-    stats_op(st, ops[2], imp);
-    stats_k(st, k, imp);
+    rec = stats_record(ops[0], ops[1], ops[2], k, d < 0);
     return d;
   }
   uint4 R0, R1, R2;
@@ -454,11 +465,7 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
   cm.m[2] = perm_decode(op2, R2.y, R2.z, X.len);
   cm.k = k;
   const long long d = tsp_three_steps<T16>(X, sol, cm, k);
-  const uint32_t imp = d < 0;
-  stats_op(st, op0, imp);
-  stats_op(st, k >= 2 ? op1 : -1, imp);
-  stats_op(st, k >= 3 ? op2 : -1, imp);
-  stats_k(st, k, imp);
+  rec = stats_record(op0, k >= 2 ? op1 : -1, k >= 3 ? op2 : -1, k, d < 0);
   return d;
 }
 
@@ -466,7 +473,7 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
 // candidate undoes it); delta from the running weight/value sums.
 __device__ long long candidate_knap(const View &X, const ByteEl *x, const Weights<1> &W,
                                     long long W0, long long V0, uint32_t c, uint32_t p,
-                                    uint32_t g, Stats<1> &st) {
+                                    uint32_t g, uint32_t &rec) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
   const int k = 1 + wsample(W.k, W.Wk, R0.w);
   long long Wt = W0, Vt = V0;
@@ -485,10 +492,7 @@ __device__ long long candidate_knap(const View &X, const ByteEl *x, const Weight
     }
   }
   const long long d = (-Vt + X.lam0 * overp(Wt - X.cap)) - (-V0 + X.lam0 * overp(W0 - X.cap));
-  const uint32_t imp = d < 0;
-  st.u[0] += k;
-  st.v[0] += imp ? k : 0;
-  stats_k(st, k, imp);
+  rec = stats_record(0, k >= 2 ? 0 : -1, k >= 3 ? 0 : -1, k, d < 0);
   return d;
 }
 
@@ -496,7 +500,7 @@ __device__ long long candidate_knap(const View &X, const ByteEl *x, const Weight
 // through small override lists.
 __device__ long long candidate_gap(const View &X, const ByteEl *x, const long long *loads,
                                    const Weights<1> &W, uint32_t c, uint32_t p, uint32_t g,
-                                   Stats<1> &st) {
+                                   uint32_t &rec) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
   const int k = 1 + wsample(W.k, W.Wk, R0.w);
   const int n = X.n, m = X.m;
@@ -535,10 +539,7 @@ __device__ long long candidate_gap(const View &X, const ByteEl *x, const long lo
       }
     }
   }
-  const uint32_t imp = d < 0;
-  st.u[0] += k;
-  st.v[0] += imp ? k : 0;
-  stats_k(st, k, imp);
+  rec = stats_record(0, k >= 2 ? 0 : -1, k >= 3 ? 0 : -1, k, d < 0);
   return d;
 }
 
@@ -726,31 +727,35 @@ struct Partial {
 };
 
 // ---------------------------------------------------------- evolve unit
-template <int MODEL, bool T16, int WPM>
+template <int MODEL, bool T16, int WPM, int NS>
 __device__ void evolve_members(const KInst &I, const View &X, unsigned char *smem, const Layout &Lo,
                                int p0, int nsol, int warps, uint64_t timeout_ns) {
   constexpr int NO = Enc<MODEL>::NO, BASE = Enc<MODEL>::BASE;
   constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW);
   using El = typename SolEl<MODEL>::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // a member group: NS generation slots of WPM warps each (slot s evaluates
+  // generation g + s of every step against the same solution)
+  constexpr int NW = WPM * NS;
   Group G;
-  G.wpm = WPM;
-  G.gw = wid % WPM;
-  G.grp = wid / WPM;
-  G.nthr = WPM * 32;
+  G.wpm = NW;
+  G.gw = wid % NW;
+  G.grp = wid / NW;
+  G.nthr = NW * 32;
   G.tig = G.gw * 32 + lane;
-  const int ngroups = warps / WPM;
+  const int gslot = G.gw / WPM, gwi = G.gw % WPM;
+  const int ngroups = warps / NW;
   const int mine = nsol > G.grp ? (nsol - G.grp + ngroups - 1) / ngroups : 0;
   if (mine == 0) return;
   const int len = I.len, P = I.P, C = I.C;
   DevSync *S = I.sync;
   El *scr = (El *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.sol_stride);
   SolScal *scal = (SolScal *)(smem + Lo.scal_off);
-  unsigned char *gmem = smem + Lo.part_off + (int64_t)G.grp * group_bytes(WPM);
+  unsigned char *gmem = smem + Lo.part_off + (int64_t)G.grp * group_bytes(NW);
   Partial *part = (Partial *)gmem;
-  int *flag = (int *)(gmem + 2 * WPM * sizeof(Partial));
-  CandMoves *mv_smem = (CandMoves *)(gmem + 2 * WPM * sizeof(Partial) + 16);
-  uint32_t *cnt_smem = (uint32_t *)(gmem + 2 * WPM * sizeof(Partial) + 16 + 64);
+  int *flag = (int *)(gmem + 2 * NW * sizeof(Partial));
+  CandMoves *mvw = (CandMoves *)(gmem + 2 * NW * sizeof(Partial) + 16);
+  uint32_t *cnt_smem = (uint32_t *)(gmem + 2 * NW * sizeof(Partial) + 16 + 2 * NW * sizeof(CandMoves));
 
   // load this group's members
   for (int e = 0; e < mine; ++e) {
@@ -769,7 +774,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
 
   // instance-wide scalars (identical in every warp)
   // CTA-local instance: every active thread of the CTA takes part in barriers
-  const int nact = I.local_sync ? min(ngroups, nsol) * WPM * 32 : 0;
+  const int nact = I.local_sync ? min(ngroups, nsol) * NW * 32 : 0;
   const DevAos *A = I.aos_in;
   uint64_t T = A->T;
   Weights<NO> W;
@@ -820,29 +825,34 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       SolScal sc = scal[ls];
       T = Tw;
       if (mine > 1) eblk = -1;
-      {
-        for (uint32_t gg = g; gg < wend; ++gg) {
-          if ((int64_t)(gg >> 5) != eblk) {
-            eblk = gg >> 5;
-            const uint4 Ra = philox(ctr_word(0, 0, kKindAccept), X.tag, p, (gg & ~31u) + lane, X.k0,
-                                    X.k1);
-            Ereg = exp_variate_q32(Ra.x);
-          }
-          const uint64_t E = __shfl_sync(kFull, Ereg, gg & 31u);
-          // the next temperature does not depend on this generation
-          const uint64_t Tn = cool(T, I.alpha);
-          long long bd = LLONG_MAX;
-          int bc = INT_MAX;
-          CandMoves cbest;
+      uint32_t gg = g;
+      while (gg < wend) {
+        // evaluate: slot s takes generation gg + s (slots past the window idle)
+        const uint32_t gm = gg + (uint32_t)gslot;
+        // temperatures of the step's generations do not depend on it
+        uint64_t Tq[NS + 1];
+        Tq[0] = T;
+#pragma unroll
+        for (int s2 = 0; s2 < NS; ++s2) Tq[s2 + 1] = cool(Tq[s2], I.alpha);
+        long long bd = LLONG_MAX;
+        int bc = INT_MAX;
+        CandMoves cbest;
+        // a later slot's counts wait for its generation to be decided (lanes
+        // without a candidate hold the empty record)
+        uint32_t held = kNoRecord;
+        if (gm < wend) {
           for (int slot = 0; slot < cpl; ++slot) {
-            const int c = slot * span + G.gw * 32 + lane;
+            const int c = slot * span + gwi * 32 + lane;
             if (c < C) {
               long long d;
+              uint32_t rec;
               CandMoves cm;
-              if constexpr (PERM) d = candidate_perm<MODEL, T16>(X, sol, W, c, p, gg, st, cm);
+              if constexpr (PERM) d = candidate_perm<MODEL, T16>(X, sol, W, c, p, gm, rec, cm);
               else if constexpr (MODEL == KNAPSACK)
-                d = candidate_knap(X, sol, W, sc.aw, sc.av, c, p, gg, st);
-              else d = candidate_gap(X, sol, loads, W, c, p, gg, st);
+                d = candidate_knap(X, sol, W, sc.aw, sc.av, c, p, gm, rec);
+              else d = candidate_gap(X, sol, loads, W, c, p, gm, rec);
+              if (gslot == 0) stats_add(st, rec);
+              else held = rec;  // NS > 1 runs with one candidate per lane
               if (d < bd || (d == bd && c < bc)) {
                 bd = d;
                 bc = c;
@@ -850,44 +860,71 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
               }
             }
           }
-          const int mybc = bc;
-          warp_argmin(bd, bc);
-          if constexpr (WPM > 1) {
-            Partial *pp = part + gpar * WPM;
-            if (lane == 0) {
-              pp[G.gw].d = bd;
-              pp[G.gw].c = bc;
-            }
-            G.sync();
+        }
+        const int mybc = bc;
+        warp_argmin(bd, bc);
+        // each warp publishes its minimum and (permutations) the moves of the
+        // lane that holds it
+        Partial *pp = part + gpar * NW;
+        CandMoves *mv = mvw + gpar * NW;
+        if constexpr (PERM)
+          if (mybc == bc && bc != INT_MAX) mv[G.gw] = cbest;
+        if constexpr (NW > 1) {
+          if (lane == 0) {
+            pp[G.gw].d = bd;
+            pp[G.gw].c = bc;
+          }
+        }
+        G.sync();
+        gpar ^= 1u;
+        // decide generations gg, gg + 1, ... in order; an accepted move ends
+        // the step (later slots evaluated the old solution)
+        uint32_t adv = 0;
 #pragma unroll
-            for (int w = 0; w < WPM; ++w) {
-              const long long d2 = pp[w].d;
-              const int c2 = pp[w].c;
-              if (d2 < bd || (d2 == bd && c2 < bc)) {
-                bd = d2;
-                bc = c2;
+        for (int s2 = 0; s2 < NS; ++s2) {
+          const uint32_t gs = gg + (uint32_t)s2;
+          if (gs >= wend) break;
+          long long d = bd;
+          int c = bc, w = G.gw;
+          if constexpr (NW > 1) {
+            d = LLONG_MAX;
+            c = INT_MAX;
+#pragma unroll
+            for (int q = 0; q < WPM; ++q) {
+              const long long d2 = pp[s2 * WPM + q].d;
+              const int c2 = pp[s2 * WPM + q].c;
+              if (d2 < d || (d2 == d && c2 < c)) {
+                d = d2;
+                c = c2;
+                w = s2 * WPM + q;
               }
             }
-            gpar ^= 1u;
           }
-          if (accept_move(bd, T, E)) {
-            if constexpr (PERM) {
-              if (mybc == bc) *mv_smem = cbest;  // the winner's lane publishes its moves
-              G.sync();
-              const CandMoves cm = *mv_smem;
-              apply_perm(sol, scr, cm, G);
-            }
-            else if constexpr (MODEL == KNAPSACK) apply_knap(X, sol, W, bc, p, gg, G, sc.aw, sc.av);
-            else apply_gap(X, sol, loads, W, bc, p, gg, G);
-            sc.cost += bd;
+          if (s2 > 0 && gslot == s2) stats_add(st, held);
+          if ((int64_t)(gs >> 5) != eblk) {
+            eblk = gs >> 5;
+            const uint4 Ra = philox(ctr_word(0, 0, kKindAccept), X.tag, p, (gs & ~31u) + lane, X.k0,
+                                    X.k1);
+            Ereg = exp_variate_q32(Ra.x);
+          }
+          const uint64_t E = __shfl_sync(kFull, Ereg, gs & 31u);
+          const bool acc = accept_move(d, Tq[s2], E);
+          T = Tq[s2 + 1];
+          adv = (uint32_t)s2 + 1u;
+          if (acc) {
+            if constexpr (PERM) apply_perm(sol, scr, mv[w], G);
+            else if constexpr (MODEL == KNAPSACK) apply_knap(X, sol, W, c, p, gs, G, sc.aw, sc.av);
+            else apply_gap(X, sol, loads, W, c, p, gs, G);
+            sc.cost += d;
             if (sc.cost < sc.best) {
               sc.best = sc.cost;
               int32_t *dst = I.bestsol + (int64_t)p * len;
               for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
             }
+            break;
           }
-          T = Tn;
         }
+        gg += adv;
       }
       G.sync();
       if (G.tig == 0) scal[ls] = sc;
@@ -939,13 +976,13 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       my = (lane == 19 + i) ? tot[2 * NO + 3 + i] : my;
     }
     const int slot = wi & 1;
-    if constexpr (WPM > 1) {
+    if constexpr (NW > 1) {
       // the group's warps add their counts in shared memory; one warp publishes
       cnt_smem[G.gw * 32 + lane] = my;
       G.sync();
       if (G.gw == 0) {
 #pragma unroll
-        for (int w = 1; w < WPM; ++w) my += cnt_smem[w * 32 + lane];
+        for (int w = 1; w < NW; ++w) my += cnt_smem[w * 32 + lane];
       }
       G.sync();
     }
@@ -1173,19 +1210,19 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
 // Single solve: CTA b covers members [b * groups, (b+1) * groups) of the
 // instance, one member per group of WPM warps (cooperative launch, so that
 // all members are resident together for the window barriers).
-template <int MODEL, bool T16, int WPM>
+template <int MODEL, bool T16, int WPM, int NS>
 __global__ void __launch_bounds__(kMaxWarps * 32, 1)
     evolve_kernel(const __grid_constant__ KInst I, int warps, uint64_t timeout_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const bool staged = I.shared_bytes > 0;
   const View X = make_view(I, smem, staged);
   __syncthreads();
-  const int groups = warps / WPM;
+  const int groups = warps / (WPM * NS);
   const int p0 = blockIdx.x * groups;
   const int nsol = min(groups, I.P - p0);
   const Layout Lo =
-      make_layout(staged ? I.shared_bytes : 0, I.len, I.m, groups, warps, WPM, I.model);
-  evolve_members<MODEL, T16, WPM>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
+      make_layout(staged ? I.shared_bytes : 0, I.len, I.m, groups, warps, WPM * NS, I.model);
+  evolve_members<MODEL, T16, WPM, NS>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
 }
 
 // Batched persistent kernel: each CTA takes the next instance of the work
@@ -1230,7 +1267,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
       const int groups = warps / WPM;
       const Layout Lo =
           make_layout(staged ? I.shared_bytes : 0, I.len, I.m, I.P, warps, WPM, I.model);
-      evolve_members<MODEL, T16, WPM>(I, X, smem, Lo, 0, I.P, warps, timeout_ns);
+      evolve_members<MODEL, T16, WPM, 1>(I, X, smem, Lo, 0, I.P, warps, timeout_ns);
       (void)groups;
     }
     __syncthreads();
@@ -1499,19 +1536,24 @@ cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri, 
 }
 
 template <int MODEL, bool T16>
-static const void *evolve_fn(int wpm) {
-  if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4>;
-  if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2>;
-  return (const void *)evolve_kernel<MODEL, T16, 1>;
+static const void *evolve_fn(int wpm, int ns) {
+  if (ns == 2) {
+    if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2>;
+    if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 2>;
+    return (const void *)evolve_kernel<MODEL, T16, 1, 2>;
+  }
+  if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 1>;
+  if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 1>;
+  return (const void *)evolve_kernel<MODEL, T16, 1, 1>;
 }
 
-static const void *pick_evolve(const KInst &h, int wpm) {
+static const void *pick_evolve(const KInst &h, int wpm, int ns) {
   switch (h.model) {
-    case TSP: return h.tri16 ? evolve_fn<TSP, true>(wpm) : evolve_fn<TSP, false>(wpm);
-    case QAP: return evolve_fn<QAP, false>(wpm);
-    case CVRPTW: return evolve_fn<CVRPTW, false>(wpm);
-    case KNAPSACK: return evolve_fn<KNAPSACK, false>(wpm);
-    case GAP: return evolve_fn<GAP, false>(wpm);
+    case TSP: return h.tri16 ? evolve_fn<TSP, true>(wpm, ns) : evolve_fn<TSP, false>(wpm, ns);
+    case QAP: return evolve_fn<QAP, false>(wpm, ns);
+    case CVRPTW: return evolve_fn<CVRPTW, false>(wpm, ns);
+    case KNAPSACK: return evolve_fn<KNAPSACK, false>(wpm, ns);
+    case GAP: return evolve_fn<GAP, false>(wpm, ns);
   }
   return nullptr;
 }
@@ -1544,8 +1586,8 @@ static cudaError_t open_smem(const void *fn) {
   return e;
 }
 
-int max_coresident_ctas(const KInst &h, int warps, int wpm, int64_t smem_bytes) {
-  const void *fn = pick_evolve(h, wpm);
+int max_coresident_ctas(const KInst &h, int warps, int wpm, int ns, int64_t smem_bytes) {
+  const void *fn = pick_evolve(h, wpm, ns);
   if (!fn) return 0;
   if (open_smem(fn) != cudaSuccess) return 0;
   int per_sm = 0, dev = 0, sms = 0;
@@ -1557,13 +1599,13 @@ int max_coresident_ctas(const KInst &h, int warps, int wpm, int64_t smem_bytes) 
   return per_sm * sms;
 }
 
-cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int64_t smem_bytes,
+cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int ns, int64_t smem_bytes,
                                  uint64_t timeout_ns, cudaStream_t st) {
-  const void *fn = pick_evolve(h, wpm);
+  const void *fn = pick_evolve(h, wpm, ns);
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = open_smem(fn);
   if (e != cudaSuccess) return e;
-  const int groups = warps / wpm;
+  const int groups = warps / (wpm * ns);
   const int grid = (h.P + groups - 1) / groups;
   KInst hi = h;
   void *args[] = {(void *)&hi, (void *)&warps, (void *)&timeout_ns};
@@ -1619,9 +1661,9 @@ int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged) {
   return L.total;
 }
 
-int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, bool staged) {
-  const Layout L = make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, warps / wpm, warps,
-                               wpm, h.model);
+int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, int ns, bool staged) {
+  const Layout L = make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, warps / (wpm * ns),
+                               warps, wpm * ns, h.model);
   return L.total;
 }
 

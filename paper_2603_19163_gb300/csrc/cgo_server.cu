@@ -271,6 +271,7 @@ void server_loop(cgo_server *S) {
       p->g = r->params.generations;
       p->has_state = r->status == CGO_OK;
       p->last_wpm = S->buckets[(size_t)r->bucket].wpm;
+      p->last_ns = 1;
       p->last_warps = S->buckets[(size_t)r->bucket].warps;
       p->last_staging = r->h.shared_bytes > 0 ? STAGE_SMEM : STAGE_GLOBAL;
       p->busy.store(0);

@@ -29,9 +29,9 @@ def cgo():
     return C
 
 
-def run_both(C, inst, params, seed, warps=0, staging=0, wpm=0):
+def run_both(C, inst, params, seed, warps=0, staging=0, wpm=0, ns=0):
     prob = C.Problem(inst)
-    prob.set_launch(warps, staging, wpm)
+    prob.set_launch(warps, staging, wpm, ns)
     prob.solve(params, seed)
     g = prob.state()
     o = oracle_run(inst, params, seed, params["G"])
@@ -39,14 +39,16 @@ def run_both(C, inst, params, seed, warps=0, staging=0, wpm=0):
 
 
 # --------------------------------------------------------------------- TSP
+@pytest.mark.parametrize("ns", [1, 2])
 @pytest.mark.parametrize("seed", SEEDS)
-def test_tsp_n20_config(cgo, seed):
+def test_tsp_n20_config(cgo, seed, ns):
     """TSP n=20, P=32, C=128, swap/2-opt/insertion at equal weight, T0=100,
-    alpha=0.999, 2000 generations."""
+    alpha=0.999, 2000 generations; one or two generations in flight."""
     inst = I.tsp_uniform(20, 0)
     p = params_for(inst, P=32, C=128, G=2000, ops=[SW, TO, INS])
-    _, g, o = run_both(cgo, inst, p, seed)
-    assert_same_state(g, o, "tsp20 seed %d" % seed)
+    prob, g, o = run_both(cgo, inst, p, seed, ns=ns)
+    assert prob.get_launch()[3] == ns
+    assert_same_state(g, o, "tsp20 seed %d ns %d" % (seed, ns))
 
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 33])
@@ -82,6 +84,48 @@ def test_tsp_population_and_launch_shape(cgo, P, warps, wpm):
     p = params_for(inst, P=P, C=100, G=21, U=7, elite_period=14)
     _, g, o = run_both(cgo, inst, p, 8, warps=warps, wpm=wpm)
     assert_same_state(g, o, "P=%d warps=%d wpm=%d" % (P, warps, wpm))
+
+
+@pytest.mark.parametrize("T0", [0, 40 << 32, 1 << 44])
+@pytest.mark.parametrize("C,wpm,warps", [(1, 1, 0), (29, 1, 2), (32, 1, 8), (33, 2, 4), (64, 2, 8),
+                                         (100, 4, 8)])
+def test_two_generations_in_flight(cgo, C, wpm, warps, T0):
+    """Generation g + 1 evaluated beside g: its result stands when g keeps
+    the solution and is redone when g accepts (acceptance rare, mixed and
+    almost certain across T0), over odd window lengths, windows that cross
+    32-generation blocks and launches that end mid-window."""
+    inst = I.tsp_uniform(37, 80)
+    p = params_for(inst, P=9, C=C, G=45, U=7, elite_period=14, T0=T0, ops=[SW, TO, INS, OR])
+    prob, g, o = run_both(cgo, inst, p, 11, warps=warps, wpm=wpm, ns=2)
+    assert prob.get_launch()[3] == 2
+    assert_same_state(g, o, "C=%d wpm=%d T0=%d" % (C, wpm, T0))
+    prob.solve_continue(13)
+    prob.solve_continue(1)
+    prob.solve_continue(22)
+    assert_same_state(prob.state(), oracle_run(inst, p, 11, 81), "continued")
+
+
+def test_two_generations_in_flight_every_model(cgo):
+    for inst, ops in ((I.tsp_uniform(31, 81), None), (I.qap_random(11, 82), [SW]),
+                      (I.knapsack(90, 83), None), (I.gap(45, 84, m=7), None),
+                      (I.cvrptw(14, 85, vehicles=4, capacity=80), None)):
+        for T0 in (0, 30 << 32):
+            over = dict(P=6, C=61, G=33, U=5, elite_period=10, T0=T0)
+            if ops:
+                over["ops"] = ops
+            p = params_for(inst, **over)
+            prob, g, o = run_both(cgo, inst, p, 4, wpm=2, ns=2)
+            assert prob.get_launch()[3] == 2
+            assert_same_state(g, o, "model %d T0 %d" % (inst["model"], T0))
+
+
+def test_two_generations_need_one_candidate_per_lane(cgo):
+    inst = I.tsp_uniform(20, 86)
+    p = params_for(inst, P=4, C=65, G=5)
+    prob = cgo.Problem(inst)
+    prob.set_launch(0, 0, 2, 2)
+    with pytest.raises(cgo.CgoError):
+        prob.solve(p, 1)
 
 
 @pytest.mark.parametrize("wpm", [1, 2, 4])
