@@ -230,7 +230,7 @@ def main():
     prob = cgo.Problem(inst)
     params = lib_params(prob, cfg)
     from paper_2603_19163_gb300.autotune import Autotuner
-    tuner = Autotuner(trial_generations=min(cfg["G"], 500))
+    tuner = Autotuner(trial_generations=min(cfg["G"], 2000))
     shape = tuner.tune_solve(prob, params, seed)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 

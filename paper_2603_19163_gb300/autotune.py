@@ -50,15 +50,24 @@ class Autotuner:
     def tune_solve(self, prob: "C.Problem", params: dict, seed: int = 1) -> tuple[int, int, int, int]:
         """Pick (warps per CTA, warps per member generation, staging,
         generations in flight) for cgo_solve of this problem and apply it;
-        returns the choice."""
+        returns the choice.  Each shape is timed on the same stretch of the
+        search, taken after a warm start of a tenth of the budget (the
+        acceptance rate, and with it the cost of a generation, changes as the
+        temperature falls)."""
         key = _key(prob, params)
         if key not in self.cache_solve:
-            trial = dict(params, G=self.trial)
+            G = int(params["G"])
+            warm = min(G // 10, 20000)
+            trial = max(1, min(self.trial, G - warm))
+            prob.set_launch(0, 0, 0, 0)
+            prob.solve(dict(params, G=warm), seed)
+            start = prob.state()
             best = None
             for shape in self.solve_shapes(params):
                 try:
                     prob.set_launch(shape[0], staging=shape[2], wpm=shape[1], ns=shape[3])
-                    prob.solve(trial, seed)
+                    prob.set_state(params, seed, start)
+                    prob.solve_continue(trial)
                     ms, gens = prob.last_kernel_time()
                 except C.CgoError:
                     continue

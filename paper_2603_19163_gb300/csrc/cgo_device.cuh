@@ -108,6 +108,9 @@ __device__ __forceinline__ uint64_t exp_variate_q32(uint32_t A) {
   return (hi << 32) | (lo >> 32);
 }
 
+// The largest value exp_variate_q32 returns (A = 0: log2 term 32).
+constexpr uint64_t kExpVariateMax = 32ull * 2977044472ull;
+
 // Metropolis test in integers: accept iff delta <= 0 or delta < T * E.
 __device__ __forceinline__ bool accept_move(long long delta, uint64_t T, uint64_t E) {
   if (delta <= 0) return true;
@@ -145,16 +148,11 @@ __device__ __forceinline__ void aos_level(uint32_t (&w)[N], const uint32_t (&u)[
     if ((enabled >> i) & 1u) w[i] = (uint32_t)(((uint64_t)w[i] << 16) / S);
 }
 
-// floor(num / den) for num, den < 2^53, den >= 1: the double-precision
-// quotient is within one unit of the exact one, and two correction steps
-// make it exact.
+// floor(num / den), den >= 1, in integer arithmetic (double precision is
+// a slow unit on this GPU)
 __device__ __forceinline__ uint64_t udiv_exact(uint64_t num, uint64_t den) {
-  uint64_t q = (uint64_t)((double)num / (double)den);
-  if (q * den > num) --q;
-  if (q * den > num) --q;
-  if ((q + 1) * den <= num) ++q;
-  if ((q + 1) * den <= num) ++q;
-  return q;
+  return num <= 0xFFFFFFFFull && den <= 0xFFFFFFFFull ? (uint64_t)((uint32_t)num / (uint32_t)den)
+                                                      : num / den;
 }
 
 // Eq. "ema" for both levels at once, one lane per weight: lanes 0..NO-1
@@ -223,6 +221,12 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// arrival at a barrier: everything this thread (and, through the barrier
+// that preceded it, its warp) did before is visible to whoever observes the add
+__device__ __forceinline__ void add_release(uint32_t *p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -268,35 +272,34 @@ __device__ __forceinline__ PMove perm_decode(int op, uint32_t r1, uint32_t r2, i
   j += (j >= i);
   const int lo = min(i, j), hi = max(i, j);
   const bool ob = q < io;
+  const bool oo = op == OR_OPT, sw = op == SWAP, two = op == TWO_OPT, fw = i < j;
   PMove mv;
-  if (op == OR_OPT) {
-    mv.b1 = ob ? q : io;
-    mv.b2 = ob ? io : io + L;
-    mv.b3 = mv.b2;
-    mv.b4 = ob ? io + L : q + L;
-    mv.rev = 0;
-  } else {
-    const bool sw = op == SWAP, two = op == TWO_OPT, fw = i < j;
-    mv.b1 = (sw || two) ? lo : (fw ? i : j);
-    mv.b2 = sw ? lo + 1 : (two ? hi + 1 : (fw ? i + 1 : i));
-    mv.b3 = sw ? hi : (two ? hi + 1 : (fw ? i + 1 : i));
-    mv.b4 = sw ? hi + 1 : (two ? hi + 1 : (fw ? j + 1 : i + 1));
-    mv.rev = two ? 1 : 0;
-  }
+  const int o1 = ob ? q : io, o2 = ob ? io : io + L, o4 = ob ? io + L : q + L;
+  const int p1 = (sw || two) ? lo : (fw ? i : j);
+  const int p2 = sw ? lo + 1 : (two ? hi + 1 : (fw ? i + 1 : i));
+  const int p3 = sw ? hi : (two ? hi + 1 : (fw ? i + 1 : i));
+  const int p4 = sw ? hi + 1 : (two ? hi + 1 : (fw ? j + 1 : i + 1));
+  mv.b1 = oo ? o1 : p1;
+  mv.b2 = oo ? o2 : p2;
+  mv.b3 = oo ? o2 : p3;
+  mv.b4 = oo ? o4 : p4;
+  mv.rev = (!oo && two) ? 1 : 0;
   return mv;
 }
 
 // Position in the array before the move of the element at position q after
 // it (branch-free).
+// Inside [b1, b4) the new array reads B, then M, then A: position q comes
+// from q + (b3 - b1) below b1 + |B|, from q + (b2 - b1 - |B|) below
+// b1 + |B| + |M|, else from q - |B| - |M|; a reversal reads b1 + b2 - 1 - q.
 __device__ __forceinline__ int perm_inv(const PMove &mv, int q) {
-  const int off = q - mv.b1;
   const int lb = mv.b4 - mv.b3, lm = mv.b3 - mv.b2;
-  const int r_b = mv.b3 + off;
-  const int r_m = mv.b2 + off - lb;
-  const int r_a = mv.b1 + off - lb - lm;
-  int r = off < lb ? r_b : (off < lb + lm ? r_m : r_a);
-  r = mv.rev ? mv.b1 + mv.b2 - 1 - q : r;
-  return (q < mv.b1 || q >= mv.b4) ? q : r;
+  const int t1 = mv.b1 + lb, t2 = t1 + lm;
+  const bool in = q >= mv.b1 && q < mv.b4;
+  int add = q < t1 ? mv.b3 - mv.b1 : (q < t2 ? mv.b2 - mv.b1 - lb : -(lb + lm));
+  add = in ? add : 0;
+  const int r = q + add;
+  return (in && mv.rev) ? mv.b1 + mv.b2 - 1 - q : r;
 }
 
 }  // namespace cgo

@@ -390,14 +390,18 @@ __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl
   for (int t = 0; t < 3; ++t)
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[t][e] = sol[pos[t][e]];
-  // gather pairs: (rl,x1) (y2,rf) (rl,af) (z4,rf) (bl,mf|af) (ml,af) (al,mf|bf) (ml,bf)
+  // gather pairs: (rl,x1) (y2,rf) (rl,af) (z4,rf) (bl,mf|af) (ml,af) (al,mf|bf) (ml,bf).
+  // With R empty (the move spans the whole tour) the junctions with R do not
+  // exist: pairs 0 and 2 become (al,bf) and (bl,af), pairs 1 and 3 cancel.
   uint32_t idx[3][8];
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
     const int rl = v[t][0], rf = v[t][1], af = v[t][2], al = v[t][3], bf = v[t][4], bl = v[t][5],
               mf = v[t][6], ml = v[t][7];
-    const int px[8] = {rl, rev[t] ? af : al, rl, rev[t] ? al : bl, bl, ml, al, ml};
-    const int py[8] = {rev[t] ? al : bf, rf, af, rf, mn[t] ? mf : af, af, mn[t] ? mf : bf, bf};
+    const bool re = remp[t];
+    const int px[8] = {re ? al : rl, rev[t] ? af : al, re ? bl : rl, re ? (rev[t] ? af : al) : (rev[t] ? al : bl),
+                       bl, ml, al, ml};
+    const int py[8] = {re ? bf : (rev[t] ? al : bf), rf, af, rf, mn[t] ? mf : af, af, mn[t] ? mf : bf, bf};
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int a = min(px[e], py[e]), b = max(px[e], py[e]);
@@ -416,11 +420,9 @@ __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl
     const Acc mid_n = dv[t][4] + (mn[t] ? dv[t][5] : (Acc)0);
     const Acc mid_o = dv[t][6] + (mn[t] ? dv[t][7] : (Acc)0);
     Acc d = dv[t][0] + dv[t][1] - dv[t][2] - dv[t][3] + (rev[t] ? (Acc)0 : mid_n - mid_o);
-    if (remp[t]) {
-      d = 0;
-      if (!rev[t] && mn[t]) d = mid_n - mid_o + (Acc)tsp_d<T16>(X, v[t][3], v[t][4]) -
-                              (Acc)tsp_d<T16>(X, v[t][5], v[t][2]);
-    }
+    // R empty: a reversal or an exchange of two pieces is a rotation of the
+    // cycle (no change); three pieces B M A change three junctions
+    d = (remp[t] && (rev[t] || !mn[t])) ? (Acc)0 : d;
     total += (t < k) ? (long long)d : 0ll;
   }
   return total;
@@ -666,11 +668,10 @@ __device__ void aux_init(int model, const View &X, const El *x, SolScal *sc,
 // returns false so the kernel can exit.  Called by one warp per group.
 __device__ bool member_barrier(DevSync *S, uint32_t arrivals, uint32_t target, uint64_t timeout_ns,
                                int lane) {
-  __threadfence();
   __syncwarp();
   int ok = 1;
   if (lane == 0) {
-    atomicAdd(&S->arrive, arrivals);
+    add_release(&S->arrive, arrivals);
     const uint64_t t0 = global_ns();
     for (;;) {
       if (ld_acquire(&S->arrive) >= target) break;
@@ -701,9 +702,10 @@ constexpr int kLocalBar = 15;
 // group-wide barrier wait: the group's first warp waits, the group follows.
 // CTA-local instances (nact > 0) meet at a named barrier of all active threads.
 // Ordering: bar.sync orders every thread's prior memory accesses for the
-// threads of the CTA, so a CTA-local barrier needs no fence; across CTAs the
-// arriving warp fences (gpu scope, cumulative over what the group's named
-// barrier made it observe) before it arrives, and polls with acquire loads.
+// threads of the CTA (release/acquire at CTA scope), so a CTA-local barrier
+// needs no fence; across CTAs the arriving thread adds with release semantics
+// at gpu scope (cumulative over what the group's barriers ordered before it)
+// and the poller reads with acquire loads.
 __device__ bool group_barrier(DevSync *S, uint32_t arrivals, uint32_t target, uint64_t timeout_ns,
                               const Group &G, int *flag, int nact) {
   if (nact > 0) {
@@ -877,6 +879,29 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         }
         G.sync();
         gpar ^= 1u;
+        // every slot's minimum over its warps (read together)
+        long long ds[NS];
+        int cs[NS], ws[NS];
+#pragma unroll
+        for (int s2 = 0; s2 < NS; ++s2) {
+          ds[s2] = bd;
+          cs[s2] = bc;
+          ws[s2] = G.gw;
+          if constexpr (NW > 1) {
+            ds[s2] = LLONG_MAX;
+            cs[s2] = INT_MAX;
+#pragma unroll
+            for (int q = 0; q < WPM; ++q) {
+              const long long d2 = pp[s2 * WPM + q].d;
+              const int c2 = pp[s2 * WPM + q].c;
+              if (d2 < ds[s2] || (d2 == ds[s2] && c2 < cs[s2])) {
+                ds[s2] = d2;
+                cs[s2] = c2;
+                ws[s2] = s2 * WPM + q;
+              }
+            }
+          }
+        }
         // decide generations gg, gg + 1, ... in order; an accepted move ends
         // the step (later slots evaluated the old solution)
         uint32_t adv = 0;
@@ -884,31 +909,21 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         for (int s2 = 0; s2 < NS; ++s2) {
           const uint32_t gs = gg + (uint32_t)s2;
           if (gs >= wend) break;
-          long long d = bd;
-          int c = bc, w = G.gw;
-          if constexpr (NW > 1) {
-            d = LLONG_MAX;
-            c = INT_MAX;
-#pragma unroll
-            for (int q = 0; q < WPM; ++q) {
-              const long long d2 = pp[s2 * WPM + q].d;
-              const int c2 = pp[s2 * WPM + q].c;
-              if (d2 < d || (d2 == d && c2 < c)) {
-                d = d2;
-                c = c2;
-                w = s2 * WPM + q;
-              }
-            }
-          }
+          const long long d = ds[s2];
+          const int c = cs[s2], w = ws[s2];
           if (s2 > 0 && gslot == s2) stats_add(st, held);
-          if ((int64_t)(gs >> 5) != eblk) {
-            eblk = gs >> 5;
-            const uint4 Ra = philox(ctr_word(0, 0, kKindAccept), X.tag, p, (gs & ~31u) + lane, X.k0,
-                                    X.k1);
-            Ereg = exp_variate_q32(Ra.x);
+          // the variate is drawn only when it can decide: a worsening move that
+          // even the largest variate would reject is rejected without it
+          bool acc = d <= 0;
+          if (!acc && accept_move(d, Tq[s2], kExpVariateMax)) {
+            if ((int64_t)(gs >> 5) != eblk) {
+              eblk = gs >> 5;
+              const uint4 Ra = philox(ctr_word(0, 0, kKindAccept), X.tag, p, (gs & ~31u) + lane,
+                                      X.k0, X.k1);
+              Ereg = exp_variate_q32(Ra.x);
+            }
+            acc = accept_move(d, Tq[s2], __shfl_sync(kFull, Ereg, gs & 31u));
           }
-          const uint64_t E = __shfl_sync(kFull, Ereg, gs & 31u);
-          const bool acc = accept_move(d, Tq[s2], E);
           T = Tq[s2 + 1];
           adv = (uint32_t)s2 + 1u;
           if (acc) {
