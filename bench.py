@@ -188,6 +188,9 @@ def main():
     ap.add_argument("--batch-class", default="mix")
     ap.add_argument("--wpm", type=int, default=0, help="warps per member override (batched)")
     ap.add_argument("--slice", type=int, default=2000)
+    ap.add_argument("--launch", default="",
+                    help="single solve: fixed launch shape 'warps,wpm,staging,gens_in_flight' "
+                         "instead of the autotuner (profiling runs)")
     ap.add_argument("--seq-sample", type=int, default=24)
     ap.add_argument("--generations", type=int, default=0,
                     help="override G (small cases for profiler captures)")
@@ -231,7 +234,11 @@ def main():
     params = lib_params(prob, cfg)
     from paper_2603_19163_gb300.autotune import Autotuner
     tuner = Autotuner(trial_generations=min(cfg["G"], 2000))
-    shape = tuner.tune_solve(prob, params, seed)
+    if args.launch:
+        shape = tuple(int(x) for x in args.launch.split(","))
+        prob.set_launch(shape[0], staging=shape[2], wpm=shape[1], ns=shape[3])
+    else:
+        shape = tuner.tune_solve(prob, params, seed)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     with torch.cuda.stream(stream):
@@ -299,7 +306,8 @@ def main():
                            "launch": {"warps_per_cta": shape[0], "warps_per_member": shape[1],
                                       "staging": ["auto", "smem", "global"][shape[2]],
                                       "gens_in_flight": shape[3],
-                                      "chosen_by": "autotuner (%d trial shapes)" % len(
+                                      "chosen_by": "fixed (--launch)" if args.launch else
+                                      "autotuner (%d trial shapes)" % len(
                                           tuner.solve_shapes(params))},
                            "best_cost": int(best_cost),
                            "gens_per_s": cfg["G"] / (total_ms / args.steps / 1000.0)},
@@ -630,6 +638,23 @@ OPS_STEP = 120            # roulette 10 + decode 15 + 10 lookups x 5 + 10 gather
 OPS_CAND = 20             # K roulette, argmin share, stats
 
 
+# DRAM bytes (read + write) of one full launch of the single-solve kernel on
+# the tsp442 workload, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass; profiles/evolve_tsp442_g200000_dram.md),
+# valid only for the kernel sources it was taken on.
+TRAFFIC_BYTES = 1.31e6 + 13.82e3
+TRAFFIC_SOURCES = "4dcadff11e6fea0f"
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("cgo_kernels.cu", "cgo_device.cuh", "cgo_internal.h"):
+        with open(os.path.join(ROOT, "paper_2603_19163_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def roofline(evals_launch, kernel_ms, prob, clocks):
     import torch
     st = prob.state()
@@ -648,10 +673,19 @@ def roofline(evals_launch, kernel_ms, prob, clocks):
     ops_eval = ek * (OPS_PHILOX + OPS_STEP) + OPS_CAND
     achieved = evals_launch * ops_eval / (kernel_ms / 1000.0) / 1e12
     peak = sms * 128 * fmax * 1e6 / 1e12
+    traffic = TRAFFIC_BYTES if kernel_sources_hash() == TRAFFIC_SOURCES else None
+    # the gather view: per counted step 8 tour positions and 8 distances
+    # (int32 each), against the shared-memory bandwidth of all SMs
+    gbytes = 64.0 * ek
+    g_achieved = evals_launch * gbytes / (kernel_ms / 1000.0) / 1e9
+    g_peak = sms * 128 * fmax * 1e6 / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
             "kernel": "evolve_kernel<TSP,int16>", "kernel_ms": kernel_ms,
-            "ops_per_eval": ops_eval, "peak_basis": "%d SMs x 128 lanes x %.0f MHz" % (sms, fmax)}
+            "ops_per_eval": ops_eval, "peak_basis": "%d SMs x 128 lanes x %.0f MHz" % (sms, fmax),
+            "gather": {"achieved": g_achieved, "peak": g_peak, "unit": "GB/s",
+                       "frac": g_achieved / g_peak, "bytes_per_eval": gbytes,
+                       "peak_basis": "%d SMs x 128 B/clk shared memory x %.0f MHz" % (sms, fmax)}}
 
 
 if __name__ == "__main__":

@@ -723,7 +723,7 @@ __device__ bool group_barrier(DevSync *S, uint32_t arrivals, uint32_t target, ui
   return ok != 0;
 }
 
-struct Partial {
+struct __align__(16) Partial {
   long long d;
   int c, pad;
 };
@@ -836,6 +836,14 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         Tq[0] = T;
 #pragma unroll
         for (int s2 = 0; s2 < NS; ++s2) Tq[s2 + 1] = cool(Tq[s2], I.alpha);
+        // largest worsening each generation could accept (with the largest
+        // variate): delta * 2^64 < T * Emax  <=>  delta <= hi - (lo == 0)
+        long long thr[NS];
+#pragma unroll
+        for (int s2 = 0; s2 < NS; ++s2) {
+          const uint64_t hi = __umul64hi(Tq[s2], kExpVariateMax), lo = Tq[s2] * kExpVariateMax;
+          thr[s2] = (long long)(hi - (lo == 0ull ? 1ull : 0ull));
+        }
         long long bd = LLONG_MAX;
         int bc = INT_MAX;
         CandMoves cbest;
@@ -879,7 +887,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         }
         G.sync();
         gpar ^= 1u;
-        // every slot's minimum over its warps (read together)
+        // every slot's minimum over its warps: all partials read at once
+        // (one 16-byte load each), then a pairwise tree
         long long ds[NS];
         int cs[NS], ws[NS];
 #pragma unroll
@@ -888,18 +897,27 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
           cs[s2] = bc;
           ws[s2] = G.gw;
           if constexpr (NW > 1) {
-            ds[s2] = LLONG_MAX;
-            cs[s2] = INT_MAX;
+            long long dq[WPM];
+            int cq[WPM], wq[WPM];
 #pragma unroll
             for (int q = 0; q < WPM; ++q) {
-              const long long d2 = pp[s2 * WPM + q].d;
-              const int c2 = pp[s2 * WPM + q].c;
-              if (d2 < ds[s2] || (d2 == ds[s2] && c2 < cs[s2])) {
-                ds[s2] = d2;
-                cs[s2] = c2;
-                ws[s2] = s2 * WPM + q;
-              }
+              const int4 v = *reinterpret_cast<const int4 *>(pp + s2 * WPM + q);
+              dq[q] = (long long)(((uint64_t)(uint32_t)v.y << 32) | (uint32_t)v.x);
+              cq[q] = v.z;
+              wq[q] = s2 * WPM + q;
             }
+#pragma unroll
+            for (int h = 1; h < WPM; h *= 2)
+#pragma unroll
+              for (int q = 0; q + h < WPM; q += 2 * h)
+                if (dq[q + h] < dq[q] || (dq[q + h] == dq[q] && cq[q + h] < cq[q])) {
+                  dq[q] = dq[q + h];
+                  cq[q] = cq[q + h];
+                  wq[q] = wq[q + h];
+                }
+            ds[s2] = dq[0];
+            cs[s2] = cq[0];
+            ws[s2] = wq[0];
           }
         }
         // decide generations gg, gg + 1, ... in order; an accepted move ends
@@ -915,7 +933,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
           // the variate is drawn only when it can decide: a worsening move that
           // even the largest variate would reject is rejected without it
           bool acc = d <= 0;
-          if (!acc && accept_move(d, Tq[s2], kExpVariateMax)) {
+          if (!acc && d <= thr[s2]) {
             if ((int64_t)(gs >> 5) != eblk) {
               eblk = gs >> 5;
               const uint4 Ra = philox(ctr_word(0, 0, kKindAccept), X.tag, p, (gs & ~31u) + lane,
