@@ -49,7 +49,7 @@ struct SolScal {
 };
 
 struct Layout {
-  int64_t inst, sol_off, sol_stride, scr_off, scal_off, load_off, part_off, total;
+  int64_t inst, sol_off, sol_stride, scr_off, scal_off, load_off, aux_off, aux_stride, part_off, total;
 };
 
 __host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64_t(15); }
@@ -59,8 +59,15 @@ __host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64
 // each) and each warp's window counts (32 x 4 B)
 __host__ __device__ inline int64_t group_bytes(int nw) { return 2 * nw * 16 + 16 + 2 * nw * 64 + nw * 128; }
 
+// CVRPTW route cache of one member: route-cost prefix sums (len + 2 int64)
+// and the next / previous separator of every position (len + 1, len int32)
+__host__ __device__ inline int64_t cv_aux_bytes(int len) {
+  return align16(8 * (int64_t)(len + 2) + 4 * (int64_t)(len + 1) + 4 * (int64_t)len);
+}
+
 // Shared memory of one CTA: [instance data][members' solutions][one scratch
-// array per member group][member scalars][GAP loads][per-group partials]
+// array per member group][member scalars][GAP loads][CVRPTW route caches]
+// [per-group partials]
 __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m, int nsol,
                                               int warps, int wpm, int model) {
   Layout L;
@@ -72,7 +79,9 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   const bool perm = (model == TSP || model == QAP || model == CVRPTW);
   L.scal_off = L.scr_off + (perm ? (int64_t)groups * L.sol_stride : 0);
   L.load_off = L.scal_off + align16((int64_t)nsol * 32);
-  L.part_off = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
+  L.aux_off = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
+  L.aux_stride = model == CVRPTW ? cv_aux_bytes(len) : 0;
+  L.part_off = L.aux_off + (int64_t)nsol * L.aux_stride;
   L.total = L.part_off + (int64_t)groups * group_bytes(wpm);
   return L;
 }
@@ -192,13 +201,8 @@ __device__ __forceinline__ void weights_sum(Weights<NO> &w) {
 __device__ __forceinline__ long long overp(long long x) { return x > 0 ? x : 0; }
 
 // ---------------------------------------------------------------- TSP
-template <bool T16>
-__device__ __forceinline__ long long tsp_d(const View &X, int x, int y) {
-  const int a = min(x, y), b = max(x, y);
-  const uint32_t idx = (((uint32_t)a * (uint32_t)(X.n2m1 - a)) >> 1) + (uint32_t)b;
-  if (T16) return ((const int16_t *)X.tri)[idx];
-  return ((const int32_t *)X.tri)[idx];
-}
+// D(x, y) of the symmetric matrix is the upper-triangle entry of
+// (min, max) at offset a (2n - 1 - a) / 2 + b.
 
 // element at position q of the array after the np prior moves (p0 first)
 __device__ __forceinline__ int vlook(const PermEl *sol, int q, const PMove &p0, const PMove &p1,
@@ -208,7 +212,8 @@ __device__ __forceinline__ int vlook(const PermEl *sol, int q, const PMove &p0, 
   return sol[q];
 }
 
-// Symmetric-TSP delta of one move on the (virtual) array.  The cyclic tour
+// Symmetric-TSP delta of one move on the (virtual) array (evaluated by
+// tsp_three_steps below for all three steps at once).  The cyclic tour
 // is R A M B (R = P4 P0 joined around the end) and becomes R B M A (or
 // R A^r for 2-opt).  Pieces keep their internal edges (D is symmetric), so
 // only junction edges change.  With r_l / r_f the elements just before A and
@@ -220,36 +225,6 @@ __device__ __forceinline__ int vlook(const PermEl *sol, int q, const PMove &p0, 
 // When R is empty (A starts the array and B ends it) the tour is A M B and
 // the delta is 0 except for an exchange with M non-empty:
 //   d(B_l,M_f) + d(M_l,A_f) + d(A_l,B_f) - d(A_l,M_f) - d(M_l,B_f) - d(B_l,A_f).
-template <bool T16>
-__device__ __forceinline__ long long tsp_step(const View &X, const PermEl *sol, const PMove &mv,
-                                              const PMove &p0, const PMove &p1, int np) {
-  const int m = X.len;
-  const int b1 = mv.b1, b2 = mv.b2, b3 = mv.b3, b4 = mv.b4;
-  const bool rev = mv.rev != 0;
-  const bool mn = b3 > b2;                      // M non-empty
-  const bool rempty = (b1 == 0) && (b4 == m);
-  const int rl = vlook(sol, b1 == 0 ? m - 1 : b1 - 1, p0, p1, np);
-  const int rf = vlook(sol, b4 == m ? 0 : b4, p0, p1, np);
-  const int af = vlook(sol, b1, p0, p1, np);
-  const int al = vlook(sol, b2 - 1, p0, p1, np);
-  const int bf = vlook(sol, min(b3, m - 1), p0, p1, np);
-  const int bl = vlook(sol, max(b4 - 1, 0), p0, p1, np);
-  const int mf = vlook(sol, min(b2, m - 1), p0, p1, np);
-  const int ml = vlook(sol, max(b3 - 1, 0), p0, p1, np);
-  // junction terms shared by the exchange and the 2-opt forms
-  const int x1 = rev ? al : bf, y2 = rev ? af : al, z4 = rev ? al : bl;
-  long long d = tsp_d<T16>(X, rl, x1) + tsp_d<T16>(X, y2, rf) - tsp_d<T16>(X, rl, af) -
-                tsp_d<T16>(X, z4, rf);
-  // middle terms of the exchange
-  const long long mid_n = tsp_d<T16>(X, bl, mn ? mf : af) + (mn ? tsp_d<T16>(X, ml, af) : 0ll);
-  const long long mid_o = tsp_d<T16>(X, al, mn ? mf : bf) + (mn ? tsp_d<T16>(X, ml, bf) : 0ll);
-  d += rev ? 0ll : mid_n - mid_o;
-  if (rempty) {
-    d = 0;
-    if (!rev && mn) d = mid_n - mid_o + tsp_d<T16>(X, al, bf) - tsp_d<T16>(X, bl, af);
-  }
-  return d;
-}
 
 // ---------------------------------------------------------------- QAP
 // Swap of positions r, s on the (virtual) permutation pi: O(n) delta of
@@ -283,8 +258,15 @@ __device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
 // a separator.  Per route from the depot at t = 0: t = max(t + d, ready),
 // late += max(0, t - due), t += service; back at the depot t += d and
 // late += max(0, t - due_0); empty routes cost nothing.
+// Up to three jumps (from separator position jf_i to separator position
+// jt_i, in increasing order) leave out whole routes known to cancel.
+struct Jumps {
+  int f0 = INT_MAX, t0 = 0, f1 = INT_MAX, t1 = 0, f2 = INT_MAX, t2 = 0;
+};
+
 template <class Look, class Q>
-__device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int L, int R) {
+__device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int L, int R,
+                                                     Jumps J = Jumps()) {
   const int n = X.n, N = n + 1;
   long long total = 0;
   Q t = 0, load = 0, dist = 0, late = 0;
@@ -302,6 +284,14 @@ __device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int 
       }
       t = load = dist = late = 0;
       prev = 0;
+      if (q == J.f0) {
+        q = J.t0;
+        J.f0 = J.f1;
+        J.t0 = J.t1;
+        J.f1 = J.f2;
+        J.t1 = J.t2;
+        J.f2 = INT_MAX;
+      }
     } else {
       const int c = sym + 1;
       const int4 nd = X.node[c];  // ready, due, service, demand
@@ -318,35 +308,137 @@ __device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int 
 }
 
 template <class Look>
-__device__ __forceinline__ long long cvrptw_routes(const View &X, Look V, int L, int R, bool q32) {
-  return q32 ? cvrptw_routes_t<Look, int>(X, V, L, R) : cvrptw_routes_t<Look, long long>(X, V, L, R);
+__device__ __forceinline__ long long cvrptw_routes(const View &X, Look V, int L, int R, bool q32,
+                                                   Jumps J = Jumps()) {
+  return q32 ? cvrptw_routes_t<Look, int>(X, V, L, R, J)
+             : cvrptw_routes_t<Look, long long>(X, V, L, R, J);
 }
 
-// Delta of one move on the (virtual) sequence: only the routes that overlap
-// the moved range [b1, b4) change, and the move keeps its symbols (and so its
-// separators) inside that range, so [L, R) — widened to the enclosing
-// separators — covers whole routes before and after.
-__device__ long long cvrptw_step(const View &X, const PermEl *sol, const PMove &mv,
-                                 const PMove &p0, const PMove &p1, int np) {
-  const int n = X.n, m = X.len;
-  auto Vo = [&](int q) { return vlook(sol, q, p0, p1, np); };
-  auto Vn = [&](int q) { return vlook(sol, perm_inv(mv, q), p0, p1, np); };
-  int L = mv.b1;
-  while (L > 0 && Vo(L - 1) < n) --L;
-  int R = mv.b4;
-  while (R < m && Vo(R) < n) ++R;
-  return cvrptw_routes(X, Vn, L, R, X.cv32) - cvrptw_routes(X, Vo, L, R, X.cv32);
+// Route cache of one member's (actual) sequence: cum[q] = cost of the routes
+// ended by a terminator (separator, or the virtual one at len) before q;
+// nxt[q] = first separator at or after q (len if none, nxt[len] = len);
+// prv[q] = last separator at or before q (-1 if none).
+struct CvAux {
+  long long *cum;
+  int *nxt, *prv;
+};
+
+__device__ __forceinline__ CvAux cv_aux_at(unsigned char *p, int len) {
+  CvAux a;
+  a.cum = (long long *)p;
+  a.nxt = (int *)(p + 8 * (int64_t)(len + 2));
+  a.prv = a.nxt + (len + 1);
+  return a;
+}
+
+// Rebuild the cache after the member's sequence changed (one warp of the
+// group; the group waits for it).
+template <class El, class G_t>
+__device__ void cv_build(const View &X, const El *sol, const CvAux &a, const G_t &G) {
+  const int m = X.len, n = X.n, lane = threadIdx.x & 31;
+  if (G.gw == 0) {
+    int carry = -1;
+    for (int base = 0; base < m; base += 32) {
+      const int q = base + lane;
+      int v = (q < m && (int)sol[q] >= n) ? q : -1;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(kFull, v, off);
+        if (lane >= off) v = max(v, u);
+      }
+      v = max(v, carry);
+      if (q < m) a.prv[q] = v;
+      carry = __shfl_sync(kFull, v, 31);
+    }
+    carry = m;
+    for (int top = m - 1; top >= 0; top -= 32) {
+      const int q = top - lane;
+      int v = (q >= 0 && (int)sol[q] >= n) ? q : m;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(kFull, v, off);
+        if (lane >= off) v = min(v, u);
+      }
+      v = min(v, carry);
+      if (q >= 0) a.nxt[q] = v;
+      carry = __shfl_sync(kFull, v, 31);
+    }
+    if (lane == 0) a.nxt[m] = m;
+    for (int q = lane; q <= m + 1; q += 32) a.cum[q] = 0;
+    __syncwarp();
+    // each non-empty route's cost, stored one past its terminator
+    for (int q = lane; q < m; q += 32) {
+      if ((q == 0 || (int)sol[q - 1] >= n) && (int)sol[q] < n) {
+        const int s = a.nxt[q];
+        a.cum[s + 1] = cvrptw_routes(X, [&](int r) { return (int)sol[r]; }, q, s, X.cv32);
+      }
+    }
+    __syncwarp();
+    long long c2 = 0;
+    for (int base = 0; base <= m + 1; base += 32) {
+      const int q = base + lane;
+      long long v = q <= m + 1 ? a.cum[q] : 0ll;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const long long u = __shfl_up_sync(kFull, v, off);
+        if (lane >= off) v += u;
+      }
+      v += c2;
+      __syncwarp();
+      if (q <= m + 1) a.cum[q] = v;
+      c2 = __shfl_sync(kFull, v, 31);
+    }
+  }
+  G.sync();
+}
+
+// Delta of a first step (on the actual sequence) from the cache: the old
+// routes' cost is a difference of prefix sums; when no piece is reversed,
+// the routes that lie wholly inside one moved piece are the same before and
+// after and are left out of both sides; only the new routes are walked.
+__device__ long long cvrptw_step0(const View &X, const PermEl *sol, const PMove &mv,
+                                  const CvAux &a) {
+  const int b1 = mv.b1, b2 = mv.b2, b3 = mv.b3, b4 = mv.b4;
+  const int L = b1 > 0 ? a.prv[b1 - 1] + 1 : 0;
+  const int R = a.nxt[b4];
+  long long old = a.cum[R + 1] - a.cum[L];
+  Jumps J;
+  if (!mv.rev) {
+    const int lb = b4 - b3, lm = b3 - b2;
+    // new order: B at b1, M at b1 + lb, A at b1 + lb + lm
+    int nj = 0;
+    const int x1s[3] = {b3, b2, b1}, x2s[3] = {b4, b3, b2}, nb[3] = {b1, b1 + lb, b1 + lb + lm};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int x1 = x1s[i], x2 = x2s[i];
+      if (x2 > x1) {
+        const int f = a.nxt[x1];
+        if (f < x2) {
+          const int l = a.prv[x2 - 1];
+          if (l > f) {
+            old -= a.cum[l + 1] - a.cum[f + 1];
+            const int jf = nb[i] + (f - x1), jt = nb[i] + (l - x1);
+            if (nj == 0) {
+              J.f0 = jf;
+              J.t0 = jt;
+            } else if (nj == 1) {
+              J.f1 = jf;
+              J.t1 = jt;
+            } else {
+              J.f2 = jf;
+              J.t2 = jt;
+            }
+            ++nj;
+          }
+        }
+      }
+    }
+  }
+  auto Vn = [&](int q) { return (int)sol[perm_inv(mv, q)]; };
+  return cvrptw_routes(X, Vn, L, R, X.cv32, J) - old;
 }
 
 // ------------------------------------------------- candidate evaluation
-template <int MODEL, bool T16>
-__device__ __forceinline__ long long perm_delta(const View &X, const PermEl *sol, const PMove &mv,
-                                                const PMove &p0, const PMove &p1, int np) {
-  if constexpr (MODEL == TSP) return tsp_step<T16>(X, sol, mv, p0, p1, np);
-  else if constexpr (MODEL == CVRPTW) return cvrptw_step(X, sol, mv, p0, p1, np);
-  else return qap_step(X, sol, mv, p0, p1, np);
-}
-
 // The moves of one candidate, kept by the lane that may win the argmin so
 // that the group can apply it without redrawing.
 struct CandMoves {
@@ -428,15 +520,67 @@ __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl
   return total;
 }
 
+// Delta of a CVRPTW candidate of k >= 2 steps on the actual sequence: the
+// routes over the hull of the moves' ranges, walked in the final sequence
+// (position q of it holds sol[inv_1(.. inv_k(q))]), minus their cached cost.
+__device__ long long cvrptw_composite(const View &X, const PermEl *sol, const CandMoves &cm,
+                                      const CvAux &a) {
+  const int k = cm.k;
+  int lo = min(cm.m[0].b1, cm.m[1].b1), hi = max(cm.m[0].b4, cm.m[1].b4);
+  if (k >= 3) {
+    lo = min(lo, cm.m[2].b1);
+    hi = max(hi, cm.m[2].b4);
+  }
+  const int L = lo > 0 ? a.prv[lo - 1] + 1 : 0;
+  const int R = a.nxt[hi];
+  const long long old = a.cum[R + 1] - a.cum[L];
+  auto Vf = [&](int q) {
+    if (k >= 3) q = perm_inv(cm.m[2], q);
+    q = perm_inv(cm.m[1], q);
+    return (int)sol[perm_inv(cm.m[0], q)];
+  };
+  return cvrptw_routes(X, Vf, L, R, X.cv32) - old;
+}
+
 // Candidate c: all three steps are drawn and decoded, and the delta of every
 // step is computed (each needs only the decoded earlier moves, not their
 // deltas), so the steps overlap; k selects how many count.
 template <int MODEL, bool T16>
 __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl *sol,
                                                     const Weights<4> &W, uint32_t c, uint32_t p,
-                                                    uint32_t g, uint32_t &rec, CandMoves &cm) {
-  if constexpr (MODEL == QAP || MODEL == CVRPTW) {
-    // O(n) / O(route) deltas: evaluate only the k steps that count
+                                                    uint32_t g, uint32_t &rec, CandMoves &cm,
+                                                    const CvAux &aux) {
+  if constexpr (MODEL == CVRPTW) {
+    // one step: from the route cache; k steps: every changed position lies in
+    // the hull of the moves' ranges (a move permutes only inside its own
+    // range), so the routes over that hull are walked once in the final
+    // sequence against their cached old cost
+    const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+    const int k = 1 + wsample(W.k, W.Wk, R0.w);
+    int ops[3] = {-1, -1, -1};
+    cm.k = k;
+    cm.m[1] = cm.m[2] = PMove{0, 0, 0, 0, 0};
+    ops[0] = wsample(W.op, W.Wop, R0.x);
+    cm.m[0] = perm_decode(ops[0], R0.y, R0.z, X.len);
+    long long d;
+    if (k == 1) {
+      d = cvrptw_step0(X, sol, cm.m[0], aux);
+    } else {
+#pragma unroll
+      for (int t = 1; t < 3; ++t) {
+        if (t < k) {
+          const uint4 R = philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
+          ops[t] = wsample(W.op, W.Wop, R.x);
+          cm.m[t] = perm_decode(ops[t], R.y, R.z, X.len);
+        }
+      }
+      d = cvrptw_composite(X, sol, cm, aux);
+    }
+    rec = stats_record(ops[0], ops[1], ops[2], k, d < 0);
+    return d;
+  }
+  if constexpr (MODEL == QAP) {
+    // O(n) deltas: evaluate only the k steps that count
     const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
     const int k = 1 + wsample(W.k, W.Wk, R0.w);
     int ops[3] = {-1, -1, -1};
@@ -449,7 +593,7 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
         const uint4 R = t == 0 ? R0 : philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
         ops[t] = wsample(W.op, W.Wop, R.x);
         cm.m[t] = perm_decode(ops[t], R.y, R.z, X.len);
-        d += perm_delta<MODEL, T16>(X, sol, cm.m[t], cm.m[0], cm.m[1], t);
+        d += qap_step(X, sol, cm.m[t], cm.m[0], cm.m[1], t);
       }
     }
     rec = stats_record(ops[0], ops[1], ops[2], k, d < 0);
@@ -772,6 +916,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     }
     G.sync();
     aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
+    if constexpr (MODEL == CVRPTW)
+      cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len), G);
   }
 
   // instance-wide scalars (identical in every warp)
@@ -824,6 +970,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       const uint32_t p = (uint32_t)(p0 + ls);
       El *sol = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
       long long *loads = (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m;
+      const CvAux cva = cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len);
       SolScal sc = scal[ls];
       T = Tw;
       if (mine > 1) eblk = -1;
@@ -857,7 +1004,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
               long long d;
               uint32_t rec;
               CandMoves cm;
-              if constexpr (PERM) d = candidate_perm<MODEL, T16>(X, sol, W, c, p, gm, rec, cm);
+              if constexpr (PERM) d = candidate_perm<MODEL, T16>(X, sol, W, c, p, gm, rec, cm, cva);
               else if constexpr (MODEL == KNAPSACK)
                 d = candidate_knap(X, sol, W, sc.aw, sc.av, c, p, gm, rec);
               else d = candidate_gap(X, sol, loads, W, c, p, gm, rec);
@@ -945,7 +1092,10 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
           T = Tq[s2 + 1];
           adv = (uint32_t)s2 + 1u;
           if (acc) {
-            if constexpr (PERM) apply_perm(sol, scr, mv[w], G);
+            if constexpr (PERM) {
+              apply_perm(sol, scr, mv[w], G);
+              if constexpr (MODEL == CVRPTW) cv_build(X, sol, cva, G);
+            }
             else if constexpr (MODEL == KNAPSACK) apply_knap(X, sol, W, c, p, gs, G, sc.aw, sc.av);
             else apply_gap(X, sol, loads, W, c, p, gs, G);
             sc.cost += d;
@@ -1087,6 +1237,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         if (G.tig == 0) scal[lw] = sc;
         G.sync();
         aux_init(MODEL, X, sol, &scal[lw], (long long *)(smem + Lo.load_off) + (int64_t)lw * X.m, G);
+        if constexpr (MODEL == CVRPTW)
+          cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)lw * Lo.aux_stride, len), G);
       }
       if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
         return;
