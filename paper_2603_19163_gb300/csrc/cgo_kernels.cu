@@ -542,6 +542,40 @@ __device__ long long cvrptw_composite(const View &X, const PermEl *sol, const Ca
   return cvrptw_routes(X, Vf, L, R, X.cv32) - old;
 }
 
+// CVRPTW candidate.  One step: from the route cache; k steps: every changed
+// position lies in the hull of the moves' ranges (a move permutes only inside
+// its own range), so the routes over that hull are walked once in the final
+// sequence against their cached old cost.  With `defer` set, a candidate of
+// k >= 2 steps is not evaluated and false is returned.
+__device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *sol,
+                                                 const Weights<4> &W, uint32_t c, uint32_t p,
+                                                 uint32_t g, bool defer, long long &d,
+                                                 uint32_t &rec, CandMoves &cm, const CvAux &aux) {
+  const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+  const int k = 1 + wsample(W.k, W.Wk, R0.w);
+  if (defer && k >= 2) return false;
+  int ops[3] = {-1, -1, -1};
+  cm.k = k;
+  cm.m[1] = cm.m[2] = PMove{0, 0, 0, 0, 0};
+  ops[0] = wsample(W.op, W.Wop, R0.x);
+  cm.m[0] = perm_decode(ops[0], R0.y, R0.z, X.len);
+  if (k == 1) {
+    d = cvrptw_step0(X, sol, cm.m[0], aux);
+  } else {
+#pragma unroll
+    for (int t = 1; t < 3; ++t) {
+      if (t < k) {
+        const uint4 R = philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
+        ops[t] = wsample(W.op, W.Wop, R.x);
+        cm.m[t] = perm_decode(ops[t], R.y, R.z, X.len);
+      }
+    }
+    d = cvrptw_composite(X, sol, cm, aux);
+  }
+  rec = stats_record(ops[0], ops[1], ops[2], k, d < 0);
+  return true;
+}
+
 // Candidate c: all three steps are drawn and decoded, and the delta of every
 // step is computed (each needs only the decoded earlier moves, not their
 // deltas), so the steps overlap; k selects how many count.
@@ -551,32 +585,8 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
                                                     uint32_t g, uint32_t &rec, CandMoves &cm,
                                                     const CvAux &aux) {
   if constexpr (MODEL == CVRPTW) {
-    // one step: from the route cache; k steps: every changed position lies in
-    // the hull of the moves' ranges (a move permutes only inside its own
-    // range), so the routes over that hull are walked once in the final
-    // sequence against their cached old cost
-    const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
-    const int k = 1 + wsample(W.k, W.Wk, R0.w);
-    int ops[3] = {-1, -1, -1};
-    cm.k = k;
-    cm.m[1] = cm.m[2] = PMove{0, 0, 0, 0, 0};
-    ops[0] = wsample(W.op, W.Wop, R0.x);
-    cm.m[0] = perm_decode(ops[0], R0.y, R0.z, X.len);
-    long long d;
-    if (k == 1) {
-      d = cvrptw_step0(X, sol, cm.m[0], aux);
-    } else {
-#pragma unroll
-      for (int t = 1; t < 3; ++t) {
-        if (t < k) {
-          const uint4 R = philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
-          ops[t] = wsample(W.op, W.Wop, R.x);
-          cm.m[t] = perm_decode(ops[t], R.y, R.z, X.len);
-        }
-      }
-      d = cvrptw_composite(X, sol, cm, aux);
-    }
-    rec = stats_record(ops[0], ops[1], ops[2], k, d < 0);
+    long long d = 0;
+    candidate_cvrptw(X, sol, W, c, p, g, false, d, rec, cm, aux);
     return d;
   }
   if constexpr (MODEL == QAP) {
@@ -997,7 +1007,67 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         // a later slot's counts wait for its generation to be decided (lanes
         // without a candidate hold the empty record)
         uint32_t held = kNoRecord;
-        if (gm < wend) {
+        bool done = false;
+        if constexpr (MODEL == CVRPTW && NS == 1) {
+          if (gm < wend && cpl > 1 && cpl <= 8) {
+            // one-step candidates in place; the multi-step ones (a fifth or
+            // so) gathered over the warp's lanes, so that the long walks are
+            // paid in about one round rather than in every slot
+            uint32_t bal[8];
+#pragma unroll
+            for (int slot = 0; slot < 8; ++slot) {
+              bal[slot] = 0u;
+              if (slot < cpl) {
+                const int c = slot * span + gwi * 32 + lane;
+                bool later = false;
+                if (c < C) {
+                  long long d;
+                  uint32_t rec;
+                  CandMoves cm;
+                  if (candidate_cvrptw(X, sol, W, c, p, gm, true, d, rec, cm, cva)) {
+                    stats_add(st, rec);
+                    if (d < bd || (d == bd && c < bc)) {
+                      bd = d;
+                      bc = c;
+                      cbest = cm;
+                    }
+                  } else {
+                    later = true;
+                  }
+                }
+                bal[slot] = __ballot_sync(kFull, later);
+              }
+            }
+            int n2 = 0;
+#pragma unroll
+            for (int slot = 0; slot < 8; ++slot) n2 += __popc(bal[slot]);
+            for (int base = 0; base < n2; base += 32) {
+              const int i = base + lane;
+              if (i < n2) {
+                int c = 0, acc = 0;
+#pragma unroll
+                for (int slot = 0; slot < 8; ++slot) {
+                  const int cnt = __popc(bal[slot]);
+                  if (i >= acc && i < acc + cnt)
+                    c = slot * span + gwi * 32 + (int)__fns(bal[slot], 0u, i - acc + 1);
+                  acc += cnt;
+                }
+                long long d;
+                uint32_t rec;
+                CandMoves cm;
+                candidate_cvrptw(X, sol, W, c, p, gm, false, d, rec, cm, cva);
+                stats_add(st, rec);
+                if (d < bd || (d == bd && c < bc)) {
+                  bd = d;
+                  bc = c;
+                  cbest = cm;
+                }
+              }
+            }
+            done = true;
+          }
+        }
+        if (gm < wend && !done) {
           for (int slot = 0; slot < cpl; ++slot) {
             const int c = slot * span + gwi * 32 + lane;
             if (c < C) {

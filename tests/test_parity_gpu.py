@@ -260,6 +260,20 @@ def test_cvrptw(cgo, n, V, kw):
     assert_same_state(g, o, "cvrptw n=%d V=%d" % (n, V))
 
 
+@pytest.mark.parametrize("C,wpm,kw", [(150, 1, None), (150, 2, (20000, 30000, 15536)),
+                                       (100, 4, None), (300, 1, (0, 0, 65536)), (256, 1, (0, 65536, 0))])
+def test_cvrptw_candidates_per_lane(cgo, C, wpm, kw):
+    """Several candidates per lane: one-step candidates in place, multi-step
+    ones gathered over the warp (up to 8 per lane), else one by one."""
+    inst = I.cvrptw(40, 91, vehicles=9, capacity=90)
+    over = dict(P=5, C=C, G=31, U=6, elite_period=12, T0=20 << 32)
+    if kw:
+        over["w_k"] = list(kw)
+    p = params_for(inst, **over)
+    _, g, o = run_both(cgo, inst, p, 23, wpm=wpm, ns=1)
+    assert_same_state(g, o, "cvrptw C=%d wpm=%d" % (C, wpm))
+
+
 def test_cvrptw100_prefix(cgo):
     """The serving workload's routing class: 100 customers, 25 vehicles."""
     inst = I.cvrptw(100, 90)
