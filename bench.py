@@ -675,17 +675,25 @@ def roofline(evals_launch, kernel_ms, prob, clocks):
     peak = sms * 128 * fmax * 1e6 / 1e12
     traffic = TRAFFIC_BYTES if kernel_sources_hash() == TRAFFIC_SOURCES else None
     # the gather view: per counted step 8 tour positions and 8 distances
-    # (int32 each), against the shared-memory bandwidth of all SMs
-    gbytes = 64.0 * ek
-    g_achieved = evals_launch * gbytes / (kernel_ms / 1000.0) / 1e9
-    g_peak = sms * 128 * fmax * 1e6 / 1e9
+    # (algorithmic; the kernel executes all 3 steps of every candidate: 48),
+    # against the random-gather rate measured on this GPU from a shared
+    # buffer (the triangle and tours are staged in shared memory)
+    from paper_2603_19163_gb300 import cgo
+    g_peak, _ = cgo.gather_peak(0, 16)
+    l2_peak, _ = cgo.gather_peak(1, 18)
+    gathers_eval = 16.0 * ek
+    g_achieved = evals_launch * gathers_eval / (kernel_ms / 1000.0)
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": traffic,
             "kernel": "evolve_kernel<TSP,int16>", "kernel_ms": kernel_ms,
             "ops_per_eval": ops_eval, "peak_basis": "%d SMs x 128 lanes x %.0f MHz" % (sms, fmax),
-            "gather": {"achieved": g_achieved, "peak": g_peak, "unit": "GB/s",
-                       "frac": g_achieved / g_peak, "bytes_per_eval": gbytes,
-                       "peak_basis": "%d SMs x 128 B/clk shared memory x %.0f MHz" % (sms, fmax)}}
+            "gather": {"achieved": g_achieved / 1e9, "peak": g_peak / 1e9, "unit": "G gathers/s",
+                       "frac": g_achieved / g_peak, "gathers_per_eval": gathers_eval,
+                       "executed_per_eval": 48.0,
+                       "executed_frac": evals_launch * 48.0 / (kernel_ms / 1000.0) / g_peak,
+                       "peak_basis": "measured: random 16-bit gathers from a 128 KB shared buffer, "
+                                     "one 1024-thread CTA per SM (cgo_gather_peak kind 0)",
+                       "l2_random_gather_peak": l2_peak / 1e9}}
 
 
 if __name__ == "__main__":

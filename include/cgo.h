@@ -311,6 +311,19 @@ const char *cgo_last_error(void);
 /* Library version string. */
 const char *cgo_version(void);
 
+/* Random-gather rate of this GPU, the denominator of the gather roofline
+ * the benchmark reports; it has no counterpart in the method.  kind 0:
+ * 16-bit gathers from a shared-memory buffer of 2^log2_elements entries
+ * (10 <= log2_elements <= 16), one 1024-thread CTA per SM; kind 1: 32-bit
+ * gathers from a global buffer of 2^log2_elements entries (10 .. 28; served
+ * by L2 when it fits).  Indices are independent linear-congruential
+ * sequences, eight per thread.  Synchronous on the calling thread's device;
+ * allocates and frees its own buffers.  gathers_per_s, kernel_ms: host
+ * pointers (kernel_ms may be NULL).  CGO_ERR_INVALID for other sizes or
+ * kinds, CGO_ERR_CUDA on a CUDA error. */
+cgo_status cgo_gather_peak(int32_t kind, int32_t log2_elements, double *gathers_per_s,
+                           double *kernel_ms);
+
 /* Number of kernels this library has launched in this process, on any
  * device and from any thread (a replayed graph adds its kernel nodes).  A
  * monotone counter for accounting; it has no counterpart in the method.

@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
                 "cgo_last_error": ([], c.c_char_p),
                 "cgo_version": ([], c.c_char_p),
                 "cgo_kernel_launches": ([P(c.c_uint64)], c.c_int),
+                "cgo_gather_peak": ([c.c_int32, c.c_int32, P(c.c_double), P(c.c_double)], c.c_int),
                 "cgo_debug_inject": ([vp, c.c_int32, c.c_int64], c.c_int),
                 "cgo_last_kernel_time": ([vp, P(c.c_double), _i64p], c.c_int),
                 "cgo_solve_static": ([P(cgo_problem_desc), P(cgo_params), c.c_uint64, vp, vp, vp],
@@ -143,6 +144,15 @@ class CgoError(RuntimeError):
 def check(status: int, where: str) -> None:
     if status != OK:
         raise CgoError(status, where)
+
+
+def gather_peak(kind: int, log2_elements: int) -> tuple[float, float]:
+    """(gathers/s, kernel ms) of the random-gather microbenchmark: kind 0
+    shared memory (16-bit entries), kind 1 global memory (32-bit entries)."""
+    g, ms = ctypes.c_double(0), ctypes.c_double(0)
+    check(lib().cgo_gather_peak(int(kind), int(log2_elements), ctypes.byref(g), ctypes.byref(ms)),
+          "cgo_gather_peak")
+    return float(g.value), float(ms.value)
 
 
 def kernel_launches() -> int:

@@ -471,6 +471,16 @@ const char *cgo_last_error(void) { return g_err.c_str(); }
 
 const char *cgo_version(void) { return "cgo 0.1 (sm_103a)"; }
 
+cgo_status cgo_gather_peak(int32_t kind, int32_t log2_elements, double *gathers_per_s,
+                           double *kernel_ms) {
+  if (!gathers_per_s) return fail(CGO_ERR_INVALID, "gathers_per_s is NULL");
+  if (kind == 0 ? (log2_elements < 10 || log2_elements > 16)
+                : (kind != 1 || log2_elements < 10 || log2_elements > 28))
+    return fail(CGO_ERR_INVALID, "kind %d with 2^%d elements is not measured", kind, log2_elements);
+  CUDA_TRY(measure_gather_peak(kind, log2_elements, gathers_per_s, kernel_ms), "gather peak");
+  return CGO_OK;
+}
+
 cgo_status cgo_kernel_launches(uint64_t *out) {
   if (!out) return fail(CGO_ERR_INVALID, "out is NULL");
   *out = launches_total();

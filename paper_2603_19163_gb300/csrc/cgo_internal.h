@@ -102,6 +102,10 @@ int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, int ns, bool stage
 int64_t smem_instance(const KInst &h);
 int max_coresident_ctas(const KInst &h, int warps, int wpm, int ns, int64_t smem_bytes);
 int64_t max_smem_optin();
+// random-gather rate microbenchmark (kind 0: 16-bit gathers from a shared
+// buffer of 2^log2n elements, one CTA per SM; kind 1: 32-bit gathers from a
+// global buffer of 2^log2n elements)
+cudaError_t measure_gather_peak(int kind, int log2n, double *per_s, double *ms);
 // process-wide count of kernels launched by the library
 void note_launches(uint64_t n);
 uint64_t launches_total();

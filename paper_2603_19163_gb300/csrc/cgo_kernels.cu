@@ -271,17 +271,23 @@ __device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int 
   long long total = 0;
   Q t = 0, load = 0, dist = 0, late = 0;
   int prev = 0;
-  const Q due0 = (Q)X.node[0].y;
   for (int q = L; q <= R; ++q) {
+    // one body for customers and separators (a separator is the trip back
+    // to the depot, node 0), so lanes at either kind of position stay together
     const int sym = q < R ? V(q) : n;
-    if (sym >= n) {
-      if (prev != 0) {
-        const Q back = (Q)X.rd[(size_t)prev * N];
-        dist += back;
-        t += back;
-        late += max(t - due0, (Q)0);
+    const bool sep = sym >= n;
+    const int c = sep ? 0 : sym + 1;
+    const int4 nd = X.node[c];  // ready, due, service, demand (depot: its due)
+    const Q dd = (Q)X.rd[(size_t)prev * N + c];
+    dist += dd;
+    const Q arr = t + dd;
+    t = sep ? arr : max(arr, (Q)nd.x);
+    late += max(t - (Q)nd.y, (Q)0);
+    t += sep ? (Q)0 : (Q)nd.z;
+    load += sep ? (Q)0 : (Q)nd.w;
+    if (sep) {
+      if (prev != 0)
         total += (long long)dist + X.lam0 * overp((long long)load - X.cap) + X.lam1 * (long long)late;
-      }
       t = load = dist = late = 0;
       prev = 0;
       if (q == J.f0) {
@@ -293,14 +299,6 @@ __device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int 
         J.f2 = INT_MAX;
       }
     } else {
-      const int c = sym + 1;
-      const int4 nd = X.node[c];  // ready, due, service, demand
-      const Q dd = (Q)X.rd[(size_t)prev * N + c];
-      dist += dd;
-      t = max(t + dd, (Q)nd.x);
-      late += max(t - (Q)nd.y, (Q)0);
-      t += (Q)nd.z;
-      load += (Q)nd.w;
       prev = c;
     }
   }

@@ -84,3 +84,13 @@ def test_launch_counter_without_a_gpu():
     before = cgo.kernel_launches()
     assert before >= 0
     assert cgo.kernel_launches() == before      # nothing launched in between
+
+
+def test_gather_peak_rejects_bad_sizes_without_a_gpu():
+    from paper_2603_19163_gb300 import cgo
+    L = cgo.lib()
+    g = ctypes.c_double(0)
+    assert L.cgo_gather_peak(0, 17, ctypes.byref(g), None) == cgo.ERR_INVALID   # > 128 KB shared
+    assert L.cgo_gather_peak(1, 29, ctypes.byref(g), None) == cgo.ERR_INVALID
+    assert L.cgo_gather_peak(2, 12, ctypes.byref(g), None) == cgo.ERR_INVALID
+    assert L.cgo_gather_peak(0, 12, None, None) == cgo.ERR_INVALID
