@@ -440,12 +440,13 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
     pool = I.serving_pool(0)
     trace = I.poisson_arrivals(200.0, duration, 7)
     params_of = {}
+    pop_of_model = {}      # the autotuner's population per class, once chosen
 
     def params_for(k):
         if k not in params_of:
             pr = cgo.Problem(dict(pool[k], tag=k))
             q = pr.default_params()
-            q.update(P=cfg["P"], C=cfg["C"], G=G)
+            q.update(P=pop_of_model.get(pool[k]["model"], cfg["P"]), C=cfg["C"], G=G)
             params_of[k] = q
             pr.close()
         return params_of[k]
@@ -476,6 +477,7 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
     pops, load = population_for_load({m: tuned[m][1] for m in tuned}, share,
                                      len(trace) / duration, G, cfg["C"])
     wpm_of = {m: tuned[m][0] for m in tuned}
+    pop_of_model.update(pops)
     for k in params_of:
         params_of[k]["P"] = pops[pool[k]["model"]]
     srv = cgo.Server(max_slots=4096, hbm_budget_bytes=96 << 30, slice_generations=args.slice)
