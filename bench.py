@@ -636,8 +636,9 @@ def aggregate(local_ms: float, local_units: float, dist=None, device="cpu") -> d
 # junction lookups and distance gathers), with the mean number of steps per
 # candidate taken from the run's own K-step statistics.
 OPS_PHILOX = 100          # 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key add)
-OPS_STEP = 120            # roulette 10 + decode 15 + 10 lookups x 5 + 10 gathers x 4 + sums 5
+OPS_STEP = 120            # TSP: roulette 10 + decode 15 + 10 lookups x 5 + 10 gathers x 4 + sums 5
 OPS_CAND = 20             # K roulette, argmin share, stats
+OPS_QAP_K = 17            # QAP, per k of the O(n) swap delta: 9 loads, 2 multiplies, 6 add/sub
 
 
 # DRAM bytes (read + write) of one full launch of the single-solve kernel on
@@ -672,7 +673,11 @@ def roofline(evals_launch, kernel_ms, prob, clocks):
     # mean steps per candidate from the final window's K counts (fallback 1.25)
     tot = sum(uk)
     ek = (uk[0] + 2 * uk[1] + 3 * uk[2]) / tot if tot else 1.25
-    ops_eval = ek * (OPS_PHILOX + OPS_STEP) + OPS_CAND
+    model = int(prob.inst["model"])
+    n = int(prob.inst["n"])
+    qap = model == 1
+    step_ops = 25 + OPS_QAP_K * n if qap else OPS_STEP
+    ops_eval = ek * (OPS_PHILOX + step_ops) + OPS_CAND
     achieved = evals_launch * ops_eval / (kernel_ms / 1000.0) / 1e12
     peak = sms * 128 * fmax * 1e6 / 1e12
     traffic = TRAFFIC_BYTES if kernel_sources_hash() == TRAFFIC_SOURCES else None
@@ -683,16 +688,23 @@ def roofline(evals_launch, kernel_ms, prob, clocks):
     from paper_2603_19163_gb300 import cgo
     g_peak, _ = cgo.gather_peak(0, 16)
     l2_peak, _ = cgo.gather_peak(1, 18)
-    gathers_eval = 16.0 * ek
+    # (QAP: 9 shared loads per k of the O(n) delta)
+    per_step = 9.0 * n + 2 if qap else 16.0
+    gathers_eval = per_step * ek
+    executed = per_step * (ek if qap else 3.0)
     g_achieved = evals_launch * gathers_eval / (kernel_ms / 1000.0)
+    if not qap and kernel_sources_hash() != TRAFFIC_SOURCES:
+        traffic = None
+    if qap:
+        traffic = None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "evolve_kernel<TSP,int16>", "kernel_ms": kernel_ms,
+            "kernel": "evolve_kernel<%s>" % ("QAP" if qap else "TSP,int16"), "kernel_ms": kernel_ms,
             "ops_per_eval": ops_eval, "peak_basis": "%d SMs x 128 lanes x %.0f MHz" % (sms, fmax),
             "gather": {"achieved": g_achieved / 1e9, "peak": g_peak / 1e9, "unit": "G gathers/s",
                        "frac": g_achieved / g_peak, "gathers_per_eval": gathers_eval,
-                       "executed_per_eval": 48.0,
-                       "executed_frac": evals_launch * 48.0 / (kernel_ms / 1000.0) / g_peak,
+                       "executed_per_eval": executed,
+                       "executed_frac": evals_launch * executed / (kernel_ms / 1000.0) / g_peak,
                        "peak_basis": "measured: random 16-bit gathers from a 128 KB shared buffer, "
                                      "one 1024-thread CTA per SM (cgo_gather_peak kind 0)",
                        "l2_random_gather_peak": l2_peak / 1e9}}

@@ -545,6 +545,8 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
       const double mf = (double)absmax(a), md = (double)absmax(b);
       if (mf * md * (double)std::max<int64_t>(n * n, 16 * n) * 4.0 > kLimit)
         return bail(fail(CGO_ERR_INVALID, "flow x distance could overflow int64"));
+      // a swap delta is 2n + 2 products of differences (each |.| <= 4 mf md)
+      p->cv32 = (double)(2 * n + 2) * 4.0 * mf * md < 2.0e9 ? 1 : 0;
       cudaError_t e;
       if ((e = copy_in(&p->d_mat0, a.data(), n * n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy F"));
       if ((e = copy_in(&p->d_mat1, b.data(), n * n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy D"));

@@ -51,7 +51,8 @@ struct KInst {
   const int32_t *mat0, *mat1, *vec0, *vec1, *vec2, *vec3;
   const void *tri;            // TSP upper triangle (row-major, i <= j)
   const int4 *node;           // CVRPTW: per node {ready, due, service, demand}
-  int32_t cv32;               // CVRPTW: every route quantity fits in int32
+  int32_t cv32;               // 32-bit delta arithmetic is exact: CVRPTW route
+                              // quantities, QAP swap deltas
   int32_t pad3;
   int64_t shared_bytes;       // bytes of instance data staged per CTA (0 = global)
   // parameters

@@ -230,8 +230,10 @@ __device__ __forceinline__ int vlook(const PermEl *sol, int q, const PMove &p0, 
 // Swap of positions r, s on the (virtual) permutation pi: O(n) delta of
 // sum_ij F[i][j] D[pi_i][pi_j] for general (asymmetric, non-zero diagonal)
 // F and D.
-__device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
-                              const PMove &p0, const PMove &p1, int np) {
+// Q: the arithmetic type (int when the host proved every partial sum fits).
+template <class Q>
+__device__ __forceinline__ long long qap_step_t(const View &X, const PermEl *sol, const PMove &mv,
+                                                const PMove &p0, const PMove &p1, int np) {
   const int n = X.n;
   const int r = mv.b1, s = mv.b3;
   const int pr = vlook(sol, r, p0, p1, np), ps = vlook(sol, s, p0, p1, np);
@@ -239,17 +241,23 @@ __device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
   const int qs = X.qs;
   const int32_t *Fr = F + (size_t)r * qs, *Fs = F + (size_t)s * qs;
   const int32_t *Dr = D + (size_t)pr * qs, *Ds = D + (size_t)ps * qs;
-  long long acc = 0;
+  Q acc = 0;
   for (int k = 0; k < n; ++k) {
     const int pk = vlook(sol, k, p0, p1, np);
-    const long long t1 = ((long long)Fr[k] - Fs[k]) * ((long long)Ds[pk] - Dr[pk]);
+    const Q t1 = ((Q)Fr[k] - (Q)Fs[k]) * ((Q)Ds[pk] - (Q)Dr[pk]);
     const int32_t *Fk = F + (size_t)k * qs, *Dk = D + (size_t)pk * qs;
-    const long long t2 = ((long long)Fk[r] - Fk[s]) * ((long long)Dk[ps] - Dk[pr]);
-    acc += (k != r && k != s) ? t1 + t2 : 0ll;
+    const Q t2 = ((Q)Fk[r] - (Q)Fk[s]) * ((Q)Dk[ps] - (Q)Dk[pr]);
+    acc += (k != r && k != s) ? t1 + t2 : (Q)0;
   }
-  acc += ((long long)Fr[r] - Fs[s]) * ((long long)Ds[ps] - Dr[pr]);
-  acc += ((long long)Fr[s] - Fs[r]) * ((long long)Ds[pr] - Dr[ps]);
-  return acc;
+  acc += ((Q)Fr[r] - (Q)Fs[s]) * ((Q)Ds[ps] - (Q)Dr[pr]);
+  acc += ((Q)Fr[s] - (Q)Fs[r]) * ((Q)Ds[pr] - (Q)Dr[ps]);
+  return (long long)acc;
+}
+
+__device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
+                              const PMove &p0, const PMove &p1, int np) {
+  return X.cv32 ? qap_step_t<int>(X, sol, mv, p0, p1, np)
+                : qap_step_t<long long>(X, sol, mv, p0, p1, np);
 }
 
 // ---------------------------------------------------------------- CVRPTW

@@ -194,6 +194,16 @@ def test_qap_asymmetric_diagonal(cgo, n):
     assert_same_state(g, o, "qap n=%d" % n)
 
 
+@pytest.mark.parametrize("hi", [50, 200000])
+def test_qap_wide_entries_take_64_bit_deltas(cgo, hi):
+    """Small entries take the 32-bit swap delta, large ones the 64-bit one;
+    both match the oracle."""
+    inst = I.qap_random(23, 45, lo=-hi, hi=hi)
+    p = params_for(inst, P=7, C=70, G=21, U=4, ops=[SW], T0=1 << 40)
+    _, g, o = run_both(cgo, inst, p, 13)
+    assert_same_state(g, o, "qap entries up to %d" % hi)
+
+
 def test_qap64_grid_prefix(cgo):
     inst = I.qap_grid(64, 0)
     p = params_for(inst, P=256, C=128, G=8, ops=[SW])
