@@ -116,6 +116,11 @@ typedef struct {
   uint32_t stag_limit;         /* AOS updates without elite gain before the K reset; 0 = off */
   uint32_t elite_period;       /* E: elite injection after every E-th generation; 0 = off;
                                   the GPU path needs E to be a multiple of U */
+  uint32_t init_oversample;    /* K of the oversampled start (Sec. 3.4.1): K*P random
+                                  starts, the P cheapest kept; 0 or 1 = plain start;
+                                  K <= 64 and K*P <= 16384 */
+  uint32_t init_heuristic;     /* 1: the row/column-sum permutations of each square
+                                  data matrix (Sec. 3.4.2; TSP, QAP) join the pool */
 } cgo_params;
 
 /* Full search state (checkpoint).  Scalars are filled/read by value; the

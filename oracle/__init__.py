@@ -37,7 +37,8 @@ class OrcParams(ctypes.Structure):
                 ("T0", ctypes.c_uint64), ("alpha", ctypes.c_uint64),
                 ("U", ctypes.c_uint32), ("ema_a", ctypes.c_uint32), ("w_floor", ctypes.c_uint32),
                 ("w_cap", ctypes.c_uint32), ("op_cap", ctypes.c_uint32 * NOPS),
-                ("stag_limit", ctypes.c_uint32), ("elite_period", ctypes.c_uint32)]
+                ("stag_limit", ctypes.c_uint32), ("elite_period", ctypes.c_uint32),
+                ("init_oversample", ctypes.c_uint32), ("init_heuristic", ctypes.c_uint32)]
 
 
 class OrcState(ctypes.Structure):
@@ -90,6 +91,8 @@ def lib() -> ctypes.CDLL:
             L.orc_init.argtypes = [ctypes.POINTER(OrcInstance), ctypes.POINTER(OrcParams), u64,
                                    ctypes.POINTER(OrcState)]
             L.orc_init.restype = i32
+            L.orc_heuristic_perms.argtypes = [ctypes.POINTER(OrcInstance), _i32p]
+            L.orc_heuristic_perms.restype = i32
             L.orc_run.argtypes = [ctypes.POINTER(OrcInstance), ctypes.POINTER(OrcParams), u64,
                                   ctypes.POINTER(OrcState), i64, i32]
             L.orc_run.restype = i32
@@ -141,7 +144,7 @@ class Instance:
 
 
 PARAM_KEYS = ("P", "C", "op_mask", "w_op", "w_k", "T0", "alpha", "U", "ema_a", "w_floor",
-              "w_cap", "op_cap", "stag_limit", "elite_period")
+              "w_cap", "op_cap", "stag_limit", "elite_period", "init_oversample", "init_heuristic")
 
 
 def default_params(inst: dict) -> dict:
@@ -222,6 +225,15 @@ class Solver:
 
 def solve(inst: dict, params: dict, seed: int, generations: int, threads: int = 0) -> dict:
     return Solver(inst, params, seed).run(generations, threads).state()
+
+
+def heuristic_perms(inst: dict) -> np.ndarray:
+    """The attribute-agnostic start permutations (H x n; H = 0 for models
+    without square data matrices)."""
+    I = Instance(inst)
+    out = np.zeros(8 * int(inst["n"]), np.int32)
+    H = int(lib().orc_heuristic_perms(I.ref, out.ctypes.data_as(_i32p)))
+    return out[:H * int(inst["n"])].reshape(H, int(inst["n"]))
 
 
 def cost(inst: dict, sol) -> int:

@@ -395,9 +395,69 @@ void orc_params_default(const orc_instance *in, orc_params *pr) {
   pr->w_cap = 39322u;
   pr->stag_limit = 5;
   pr->elite_period = 0;
+  pr->init_oversample = 1;
+  pr->init_heuristic = 0;
 }
 
 /* ------------------------------------------------------------- init [R15] */
+/* Random start j (member j of a plain start, candidate j of an oversampled
+ * one): Fisher-Yates for permutations, one draw per entry otherwise. */
+static void random_start(const orc_instance *in, uint32_t j, uint64_t seed, int32_t enc,
+                         int32_t lb, int32_t ub, int32_t *x, int32_t len) {
+  uint32_t R[4];
+  if (enc == 0) { /* Fisher-Yates, i = len-1 .. 1, j = floor(word*(i+1)/2^32) */
+    for (int32_t i = 0; i < len; i++) x[i] = i;
+    for (int32_t i = len - 1; i >= 1; i--) {
+      int32_t d = len - 1 - i;
+      draw(W0(d / 4, 0, KIND_INIT), in->tag, j, INIT_GEN, seed, R);
+      int32_t r = (int32_t)(((uint64_t)R[d % 4] * (uint64_t)(i + 1)) >> 32);
+      int32_t t = x[i]; x[i] = x[r]; x[r] = t;
+    }
+  } else {
+    for (int32_t i = 0; i < len; i++) {
+      draw(W0(i / 4, 0, KIND_INIT), in->tag, j, INIT_GEN, seed, R);
+      uint32_t w = R[i % 4];
+      if (enc == 1) x[i] = (int32_t)(w & 1u);
+      else x[i] = lb + (int32_t)(((uint64_t)w * (uint64_t)((int64_t)ub - lb + 1)) >> 32);
+    }
+  }
+}
+
+/* sort keys: (key, index) ascending */
+typedef struct { int64_t key; int64_t idx; } orc_keyed;
+static int keyed_less(const void *a, const void *b) {
+  const orc_keyed *x = (const orc_keyed *)a, *y = (const orc_keyed *)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return x->idx < y->idx ? -1 : (x->idx > y->idx ? 1 : 0);
+}
+
+/* Sec. 3.4.2: per n x n data matrix, sort the elements by row sum and by
+ * column sum, ascending and descending (ties: lower index first). */
+int32_t orc_heuristic_perms(const orc_instance *in, int32_t *out) {
+  const int32_t n = in->n;
+  const int32_t *mats[2] = {in->mat0, in->mat1};
+  int32_t nm = in->model == ORC_TSP ? 1 : (in->model == ORC_QAP ? 2 : 0), H = 0;
+  orc_keyed *k = (orc_keyed *)malloc(sizeof(orc_keyed) * (size_t)n);
+  for (int32_t t = 0; t < nm; t++) {
+    const int32_t *M = mats[t];
+    for (int32_t by_col = 0; by_col < 2; by_col++) {
+      for (int32_t desc = 0; desc < 2; desc++) {
+        for (int32_t i = 0; i < n; i++) {
+          int64_t s = 0;
+          for (int32_t j = 0; j < n; j++) s += by_col ? M[(int64_t)j * n + i] : M[(int64_t)i * n + j];
+          k[i].key = desc ? -s : s;
+          k[i].idx = i;
+        }
+        qsort(k, (size_t)n, sizeof(orc_keyed), keyed_less);
+        for (int32_t i = 0; i < n; i++) out[(int64_t)H * n + i] = (int32_t)k[i].idx;
+        H++;
+      }
+    }
+  }
+  free(k);
+  return H;
+}
+
 int32_t orc_init(const orc_instance *in, const orc_params *pr, uint64_t seed, orc_state *st) {
   int32_t len = orc_solution_length(in), enc = encoding_of(in->model);
   int32_t en[ORC_NOPS];
@@ -415,29 +475,45 @@ int32_t orc_init(const orc_instance *in, const orc_params *pr, uint64_t seed, or
   st->stag = 0;
   int32_t lb = 0, ub = 1;
   if (enc == 2) int_bounds(in, &lb, &ub);
-  for (int32_t p = 0; p < pr->P; p++) {
-    int32_t *x = st->cur + (int64_t)p * len;
-    uint32_t R[4];
-    if (enc == 0) { /* Fisher-Yates, i = len-1 .. 1, j = floor(word*(i+1)/2^32) */
-      for (int32_t i = 0; i < len; i++) x[i] = i;
-      for (int32_t i = len - 1; i >= 1; i--) {
-        int32_t d = len - 1 - i;
-        draw(W0(d / 4, 0, KIND_INIT), in->tag, (uint32_t)p, INIT_GEN, seed, R);
-        int32_t j = (int32_t)(((uint64_t)R[d % 4] * (uint64_t)(i + 1)) >> 32);
-        int32_t t = x[i]; x[i] = x[j]; x[j] = t;
-      }
-    } else {
-      for (int32_t i = 0; i < len; i++) {
-        draw(W0(i / 4, 0, KIND_INIT), in->tag, (uint32_t)p, INIT_GEN, seed, R);
-        uint32_t w = R[i % 4];
-        if (enc == 1) x[i] = (int32_t)(w & 1u);
-        else x[i] = lb + (int32_t)(((uint64_t)w * (uint64_t)((int64_t)ub - lb + 1)) >> 32);
-      }
-    }
-    st->cost[p] = orc_cost(in, x);
-    st->best_cost[p] = st->cost[p];
-    memcpy(st->best_sol + (int64_t)p * len, x, sizeof(int32_t) * (size_t)len);
+  const int64_t K = pr->init_oversample > 1 ? pr->init_oversample : 1;
+  int32_t *heur = NULL, H = 0;
+  if (pr->init_heuristic) {
+    heur = (int32_t *)malloc(sizeof(int32_t) * 8 * (size_t)in->n);
+    H = orc_heuristic_perms(in, heur);
   }
+  if (K == 1 && H == 0) {
+    /* plain start: member p is random start p */
+    for (int32_t p = 0; p < pr->P; p++) {
+      int32_t *x = st->cur + (int64_t)p * len;
+      random_start(in, (uint32_t)p, seed, enc, lb, ub, x, len);
+      st->cost[p] = orc_cost(in, x);
+      st->best_cost[p] = st->cost[p];
+      memcpy(st->best_sol + (int64_t)p * len, x, sizeof(int32_t) * (size_t)len);
+    }
+  } else {
+    /* Sec. 3.4.1: K*P random starts and the heuristic permutations form a
+     * pool; the members are its P cheapest, in order of (cost, pool index) */
+    const int64_t N = K * pr->P + H;
+    int32_t *pool = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N * len));
+    orc_keyed *order = (orc_keyed *)malloc(sizeof(orc_keyed) * (size_t)N);
+    for (int64_t j = 0; j < N; j++) {
+      int32_t *x = pool + j * len;
+      if (j < K * pr->P) random_start(in, (uint32_t)j, seed, enc, lb, ub, x, len);
+      else memcpy(x, heur + (j - K * pr->P) * in->n, sizeof(int32_t) * (size_t)len);
+      order[j].key = orc_cost(in, x);
+      order[j].idx = j;
+    }
+    qsort(order, (size_t)N, sizeof(orc_keyed), keyed_less);
+    for (int32_t p = 0; p < pr->P; p++) {
+      const int32_t *x = pool + order[p].idx * len;
+      memcpy(st->cur + (int64_t)p * len, x, sizeof(int32_t) * (size_t)len);
+      memcpy(st->best_sol + (int64_t)p * len, x, sizeof(int32_t) * (size_t)len);
+      st->cost[p] = st->best_cost[p] = order[p].key;
+    }
+    free(pool);
+    free(order);
+  }
+  free(heur);
   st->elite_prev = st->best_cost[orc_elite(st)];
   return 0;
 }

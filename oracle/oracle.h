@@ -51,6 +51,8 @@ typedef struct {
   uint32_t w_op[ORC_NOPS], w_k[3];
   uint64_t T0, alpha;              /* Q32.32, Q0.32 */
   uint32_t U, ema_a, w_floor, w_cap, op_cap[ORC_NOPS], stag_limit, elite_period;
+  uint32_t init_oversample;        /* K of the oversampled start (Sec. 3.4.1); 0 or 1 = off */
+  uint32_t init_heuristic;         /* 1 = add the row/column-sum permutations (Sec. 3.4.2) */
 } orc_params;
 
 /* Complete search state.  Arrays are caller-owned: cur/best_sol P*len,
@@ -96,6 +98,11 @@ int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc
                 int64_t generations, int32_t threads);
 /* index of the instance elite (lowest best cost, ties to the lowest index) */
 int32_t orc_elite(const orc_state *st);
+/* the attribute-agnostic start permutations of an instance (TSP: D; QAP: F,
+ * then D): per matrix the orders of ascending and descending row sums, then
+ * ascending and descending column sums.  out: 8 * n entries; returns their
+ * number of permutations (0 for other models). */
+int32_t orc_heuristic_perms(const orc_instance *in, int32_t *out);
 /* OpenMP threads the oracle would use for `threads` */
 int32_t orc_threads(int32_t threads);
 

@@ -48,7 +48,8 @@ class cgo_params(ctypes.Structure):
                 ("alpha_q32", ctypes.c_uint64), ("aos_interval", ctypes.c_uint32),
                 ("ema_alpha_q16", ctypes.c_uint32), ("w_floor_q16", ctypes.c_uint32),
                 ("w_cap_q16", ctypes.c_uint32), ("op_cap_q16", ctypes.c_uint32 * NOPS),
-                ("stag_limit", ctypes.c_uint32), ("elite_period", ctypes.c_uint32)]
+                ("stag_limit", ctypes.c_uint32), ("elite_period", ctypes.c_uint32),
+                ("init_oversample", ctypes.c_uint32), ("init_heuristic", ctypes.c_uint32)]
 
 
 class cgo_state(ctypes.Structure):
@@ -168,7 +169,8 @@ PARAM_MAP = [("P", "population"), ("C", "candidates"), ("G", "generations"),
              ("T0", "T0_q32"), ("alpha", "alpha_q32"), ("U", "aos_interval"),
              ("ema_a", "ema_alpha_q16"), ("w_floor", "w_floor_q16"), ("w_cap", "w_cap_q16"),
              ("op_cap", "op_cap_q16"), ("stag_limit", "stag_limit"),
-             ("elite_period", "elite_period")]
+             ("elite_period", "elite_period"), ("init_oversample", "init_oversample"),
+             ("init_heuristic", "init_heuristic")]
 
 
 def params_struct(d: dict) -> cgo_params:

@@ -154,6 +154,50 @@ void free_state(cgo_problem *p) {
   p->has_state = false;
 }
 
+// Sec. 3.4.2: the orders of ascending and descending row sums, then of
+// ascending and descending column sums, of an n x n matrix (ties: lower
+// index first), appended to out.
+void heuristic_perms(const std::vector<int32_t> &M, int64_t n, std::vector<int32_t> &out) {
+  std::vector<int64_t> s((size_t)n);
+  std::vector<int32_t> idx((size_t)n);
+  for (int by_col = 0; by_col < 2; ++by_col) {
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t t = 0;
+      for (int64_t j = 0; j < n; ++j) t += by_col ? M[(size_t)(j * n + i)] : M[(size_t)(i * n + j)];
+      s[(size_t)i] = t;
+    }
+    for (int desc = 0; desc < 2; ++desc) {
+      for (int64_t i = 0; i < n; ++i) idx[(size_t)i] = (int32_t)i;
+      std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+        return desc ? s[(size_t)x] > s[(size_t)y] : s[(size_t)x] < s[(size_t)y];
+      });
+      out.insert(out.end(), idx.begin(), idx.end());
+    }
+  }
+}
+
+// entries of the start pool (0: plain start)
+int64_t pool_size(const cgo_problem *p, const cgo_params &q) {
+  const int64_t K = q.init_oversample > 1 ? q.init_oversample : 1;
+  const int64_t H = q.init_heuristic ? p->n_heur : 0;
+  return (K > 1 || H > 0) ? K * q.population + H : 0;
+}
+
+cgo_status ensure_pool(cgo_problem *p, const cgo_params &q) {
+  const int64_t N = pool_size(p, q);
+  if (N <= p->pool_cap) return CGO_OK;
+  dev_free(p->d_pool);
+  dev_free(p->d_pool_cost);
+  p->d_pool = nullptr;
+  p->d_pool_cost = nullptr;
+  p->pool_cap = 0;
+  CUDA_TRY(dev_alloc((void **)&p->d_pool, (size_t)N * p->len * 4), "start pool");
+  CUDA_TRY(dev_alloc((void **)&p->d_pool_cost, (size_t)N * 8), "start pool");
+  CUDA_TRY(cudaStreamSynchronize(host_stream()), "start pool");
+  p->pool_cap = N;
+  return CGO_OK;
+}
+
 cgo_status ensure_state(cgo_problem *p, int P) {
   if (p->P_alloc == P && p->d_cur) return CGO_OK;
   free_state(p);
@@ -230,6 +274,10 @@ cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *
   if (q->alpha_q32 > (1ull << 32)) return fail(CGO_ERR_INVALID, "alpha > 1.0");
   if (q->elite_period > 0 && q->elite_period % q->aos_interval != 0)
     return fail(CGO_ERR_UNSUPPORTED, "elite_period must be a multiple of aos_interval on the GPU");
+  if (q->init_oversample > 64) return fail(CGO_ERR_INVALID, "init_oversample must be <= 64");
+  if ((uint64_t)(q->init_oversample > 1 ? q->init_oversample : 1) * q->population > 16384u)
+    return fail(CGO_ERR_INVALID, "init_oversample * population must be <= 16384");
+  if (q->init_heuristic > 1) return fail(CGO_ERR_INVALID, "init_heuristic must be 0 or 1");
   *enabled = en;
   return CGO_OK;
 }
@@ -276,6 +324,11 @@ KInst base_kinst(const cgo_problem *p) {
   h.cost = p->d_cost;
   h.best = p->d_best;
   h.sync = p->d_sync;
+  h.K_over = q.init_oversample > 1 ? (int32_t)q.init_oversample : 1;
+  h.n_heur = q.init_heuristic ? p->n_heur : 0;
+  h.heur = p->d_heur;
+  h.pool_sol = p->d_pool;
+  h.pool_cost = p->d_pool_cost;
   return h;
 }
 
@@ -537,6 +590,11 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
       if ((e = build_triangle(p->d_mat0, (int)n, p->tri16, p->d_tri, host_stream())) != cudaSuccess)
         return bail(cuda_fail(e, "triangle"));
       if ((e = cudaStreamSynchronize(host_stream())) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+      std::vector<int32_t> hp;
+      heuristic_perms(a, n, hp);
+      if ((e = copy_in(&p->d_heur, hp.data(), (int64_t)hp.size(), false)) != cudaSuccess)
+        return bail(cuda_fail(e, "start permutations"));
+      p->n_heur = 4;
       break;
     }
     case CGO_QAP: {
@@ -547,6 +605,14 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
         return bail(fail(CGO_ERR_INVALID, "flow x distance could overflow int64"));
       // a swap delta is 2n + 2 products of differences (each |.| <= 4 mf md)
       p->cv32 = (double)(2 * n + 2) * 4.0 * mf * md < 2.0e9 ? 1 : 0;
+      {
+        std::vector<int32_t> hp;
+        heuristic_perms(a, n, hp);
+        heuristic_perms(b, n, hp);
+        cudaError_t e = copy_in(&p->d_heur, hp.data(), (int64_t)hp.size(), false);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "start permutations"));
+        p->n_heur = 8;
+      }
       cudaError_t e;
       if ((e = copy_in(&p->d_mat0, a.data(), n * n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy F"));
       if ((e = copy_in(&p->d_mat1, b.data(), n * n, false)) != cudaSuccess) return bail(cuda_fail(e, "copy D"));
@@ -626,6 +692,9 @@ cgo_status cgo_problem_destroy(cgo_problem *p) {
   for (int i = 0; i < 4; ++i) dev_free(p->d_vec[i]);
   dev_free(p->d_tri);
   dev_free(p->d_node);
+  dev_free(p->d_heur);
+  dev_free(p->d_pool);
+  dev_free(p->d_pool_cost);
   delete p;
   return CGO_OK;
 }
@@ -669,6 +738,8 @@ cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
   q->w_cap_q16 = 39322u;
   q->stag_limit = 5;
   q->elite_period = 0;
+  q->init_oversample = 1;
+  q->init_heuristic = 0;
   return CGO_OK;
 }
 
@@ -712,6 +783,7 @@ cgo_status cgo_solve(cgo_problem *p, const cgo_params *q, uint64_t seed, void *s
   cgo_status s = validate_params(p, q, &en);
   if (s != CGO_OK) return s;
   if ((s = ensure_state(p, q->population)) != CGO_OK) return s;
+  if ((s = ensure_pool(p, *q)) != CGO_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   p->params = *q;
   p->seed = seed;
@@ -888,6 +960,7 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
     if (s != CGO_OK) return s;
     if (per[i].generations >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "problem %d: too many generations", i);
     if ((s = ensure_state(p, per[i].population)) != CGO_OK) return s;
+    if ((s = ensure_pool(p, per[i])) != CGO_OK) return s;
     p->params = per[i];
     p->seed = seeds[i];
     p->enabled = en;
@@ -1060,6 +1133,8 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
   uint32_t en = 0;
   cgo_status s = validate_params(&p, q, &en);
   if (s != CGO_OK) return s;
+  if (q->init_oversample > 1 || q->init_heuristic)
+    return fail(CGO_ERR_UNSUPPORTED, "the allocation-free solve starts from the plain random population");
   const int n = d->n, P = q->population;
   // carve the scratch; the triangle is sized for int32 entries (worst case)
   const size_t tri_b = up256((size_t)n * (n + 1) / 2 * 4 + 16);

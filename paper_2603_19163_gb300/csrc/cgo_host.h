@@ -31,6 +31,12 @@ struct cgo_problem {
   int64_t *d_cost = nullptr, *d_best = nullptr;
   cgo::DevAos *d_aos = nullptr;  // [2]
   cgo::DevSync *d_sync = nullptr;
+  // start pool (oversampled / heuristic start)
+  int32_t *d_heur = nullptr;     // heuristic start permutations, n_heur x n
+  int n_heur = 0;
+  int32_t *d_pool = nullptr;
+  int64_t *d_pool_cost = nullptr;
+  int64_t pool_cap = 0;
   int aos_cur = 0;
   int64_t g = 0;
   // launch shape
@@ -71,6 +77,8 @@ struct Guard {
 cudaStream_t host_stream();
 cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *enabled);
 cgo_status ensure_state(cgo_problem *p, int P);
+int64_t pool_size(const cgo_problem *p, const cgo_params &q);
+cgo_status ensure_pool(cgo_problem *p, const cgo_params &q);
 KInst base_kinst(const cgo_problem *p);
 // launch shape of a batched (CTA-local) instance: warps per member, warps
 // per CTA, shared memory of a unit; fails if the instance cannot fit a CTA

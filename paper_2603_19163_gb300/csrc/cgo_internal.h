@@ -77,6 +77,12 @@ struct KInst {
   const DevAos *aos_in;
   DevAos *aos_out;
   DevSync *sync;
+  // oversampled / heuristic start (pool of K*P random starts + n_heur
+  // permutations, the P cheapest become the members)
+  int32_t K_over, n_heur;
+  const int32_t *heur;        // n_heur x n
+  int32_t *pool_sol;          // (K*P + n_heur) x len
+  int64_t *pool_cost;
 };
 
 // host-side launchers (cgo_kernels.cu)

@@ -1586,9 +1586,10 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
 
 // Philox-seeded Fisher-Yates / random bits / random integers for member p,
 // then its exact cost
-__device__ void init_member(const KInst &I, int p) {
+// Random start j (member j of a plain start, candidate j of a start pool):
+// Fisher-Yates for permutations, one draw per entry otherwise.
+__device__ void random_start(const KInst &I, int p, int32_t *x) {
   const int len = I.len;
-  int32_t *x = I.cur + (int64_t)p * len;
   const uint32_t k0 = (uint32_t)I.seed, k1 = (uint32_t)(I.seed >> 32);
   const bool perm = (I.model == TSP || I.model == QAP || I.model == CVRPTW);
   if (perm) {
@@ -1617,11 +1618,47 @@ __device__ void init_member(const KInst &I, int p) {
       else x[i] = lb + (int32_t)(((uint64_t)w * R) >> 32);
     }
   }
+}
+
+__device__ void init_member(const KInst &I, int p) {
+  const int len = I.len;
+  int32_t *x = I.cur + (int64_t)p * len;
+  random_start(I, p, x);
   const long long c = full_cost(I, x);
   I.cost[p] = c;
   I.best[p] = c;
   int32_t *b = I.bestsol + (int64_t)p * len;
   for (int i = 0; i < len; ++i) b[i] = x[i];
+}
+
+// Start pool (Sec. 3.4.1-3.4.2): K*P random starts, then the heuristic
+// permutations; the members are the P cheapest in order of (cost, index).
+__device__ __forceinline__ bool pool_start(const KInst &I) { return I.K_over > 1 || I.n_heur > 0; }
+__device__ __forceinline__ int pool_entries(const KInst &I) { return I.K_over * I.P + I.n_heur; }
+
+__device__ void pool_fill(const KInst &I, int j) {
+  const int len = I.len, R = I.K_over * I.P;
+  int32_t *x = I.pool_sol + (int64_t)j * len;
+  if (j < R) random_start(I, j, x);
+  else
+    for (int i = 0; i < len; ++i) x[i] = I.heur[(int64_t)(j - R) * I.n + i];
+  I.pool_cost[j] = full_cost(I, x);
+}
+
+// entry j's rank among all entries; the P best become members 0 .. P-1
+__device__ void pool_select(const KInst &I, int j) {
+  const int N = pool_entries(I), len = I.len;
+  const long long cj = I.pool_cost[j];
+  int rank = 0;
+  for (int i = 0; i < N; ++i) {
+    const long long ci = I.pool_cost[i];
+    rank += (ci < cj || (ci == cj && i < j)) ? 1 : 0;
+  }
+  if (rank >= I.P) return;
+  const int32_t *x = I.pool_sol + (int64_t)j * len;
+  int32_t *c = I.cur + (int64_t)rank * len, *b = I.bestsol + (int64_t)rank * len;
+  for (int i = 0; i < len; ++i) c[i] = b[i] = x[i];
+  I.cost[rank] = I.best[rank] = cj;
 }
 
 // one thread per member
@@ -1630,10 +1667,28 @@ __global__ void init_kernel(const __grid_constant__ KInst I) {
   if (p < I.P) init_member(I, p);
 }
 
-// batched: one block per instance, threads over its members
+// one thread per pool entry: build and cost it, then (second launch) rank it
+__global__ void init_pool_fill_kernel(const __grid_constant__ KInst I) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < pool_entries(I)) pool_fill(I, j);
+}
+
+__global__ void init_pool_select_kernel(const __grid_constant__ KInst I) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < pool_entries(I)) pool_select(I, j);
+}
+
+// batched: one block per instance, threads over its members (or its pool)
 __global__ void init_batch_kernel(const KInst *__restrict__ insts) {
   const KInst &I = insts[blockIdx.x];
-  for (int p = threadIdx.x; p < I.P; p += blockDim.x) init_member(I, p);
+  if (pool_start(I)) {
+    const int N = pool_entries(I);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) pool_fill(I, j);
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) pool_select(I, j);
+  } else {
+    for (int p = threadIdx.x; p < I.P; p += blockDim.x) init_member(I, p);
+  }
 }
 
 // elite = lowest best cost, lowest index on ties (one block)
@@ -1765,7 +1820,16 @@ cudaError_t launch_copy_elite(const DevAos *d_aos, const int32_t *d_bestsol, int
 }
 
 cudaError_t launch_init(const KInst &h, cudaStream_t st) {
-  const int threads = 128, blocks = (h.P + threads - 1) / threads;
+  const int threads = 128;
+  if (h.K_over > 1 || h.n_heur > 0) {
+    const int N = h.K_over * h.P + h.n_heur, blocks = (N + threads - 1) / threads;
+    init_pool_fill_kernel<<<blocks, threads, 0, st>>>(h);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    init_pool_select_kernel<<<blocks, threads, 0, st>>>(h);
+    return counted(cudaGetLastError(), 2);
+  }
+  const int blocks = (h.P + threads - 1) / threads;
   init_kernel<<<blocks, threads, 0, st>>>(h);
   return counted(cudaGetLastError());
 }

@@ -98,7 +98,9 @@ int64_t request_bytes(const cgo_problem *p, const cgo_params &q) {
     case GAP: data = 2ll * p->m * p->n * 4 + 4ll * p->m; break;
     case CVRPTW: data = (int64_t)(p->n + 1) * (p->n + 1) * 4 + 16ll * (p->n + 1); break;
   }
-  return data + 2 * P * len * 4 + 16 * P + 2 * (int64_t)sizeof(DevAos) + (int64_t)sizeof(DevSync);
+  const int64_t pool = pool_size(p, q) * (len * 4 + 8);
+  return data + 2 * P * len * 4 + 16 * P + 2 * (int64_t)sizeof(DevAos) + (int64_t)sizeof(DevSync) +
+         pool;
 }
 
 cudaError_t capture_slice(cgo_server *S) {
@@ -196,6 +198,7 @@ void server_loop(cgo_server *S) {
     for (Req *r : admitted) {
       cgo_problem *p = r->prob;
       cgo_status s = ensure_state(p, r->params.population);
+      if (s == CGO_OK) s = ensure_pool(p, r->params);
       if (s != CGO_OK) {
         fail_all(S, s, "state allocation failed");
         return;

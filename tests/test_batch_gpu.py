@@ -40,6 +40,12 @@ def mixed_batch():
                                                                         elite_period=8)))
     items.append((dict(I.tsp_uniform(20, 250), tag=40), dict(P=4, C=32, G=0)))  # init only
     items.append((dict(I.cvrptw(25, 251, vehicles=5, capacity=120), tag=41), dict(P=8, C=64, G=33)))
+    # oversampled and heuristic starts (Sec. 3.4.1-3.4.2)
+    items.append((dict(I.tsp_clustered(90, 252), tag=42),
+                  dict(P=6, C=64, G=21, init_oversample=3, init_heuristic=1)))
+    items.append((dict(I.qap_random(12, 253), tag=43),
+                  dict(P=5, C=48, G=19, ops=[SW], init_oversample=2, init_heuristic=1)))
+    items.append((dict(I.knapsack(80, 254), tag=44), dict(P=7, C=64, G=15, init_oversample=4)))
     return items
 
 

@@ -292,6 +292,36 @@ def test_cvrptw100_prefix(cgo):
     assert_same_state(g, o, "cvrptw100")
 
 
+# ------------------------------------------------- oversampled / heuristic start
+@pytest.mark.parametrize("K,heur", [(2, 0), (4, 0), (1, 1), (3, 1), (64, 1)])
+def test_pool_start_every_model(cgo, K, heur):
+    """Sec. 3.4.1-3.4.2: the P cheapest of K*P random starts (plus the
+    row/column-sum permutations for TSP and QAP) start the search."""
+    cases = [(I.tsp_clustered(60, 300), None), (I.qap_random(13, 301), [SW]),
+             (I.knapsack(70, 302), None), (I.gap(30, 303, m=5), None),
+             (I.cvrptw(16, 304, vehicles=4, capacity=80), None)]
+    for inst, ops in cases:
+        P = 3 if K == 64 else 7
+        over = dict(P=P, C=48, G=13, U=4, init_oversample=K, init_heuristic=heur)
+        if ops:
+            over["ops"] = ops
+        p = params_for(inst, **over)
+        _, g, o = run_both(cgo, inst, p, 9)
+        assert_same_state(g, o, "model %d K %d heur %d" % (inst["model"], K, heur))
+
+
+def test_pool_start_init_only_and_limits(cgo):
+    inst = I.tsp_clustered(200, 305)
+    p = params_for(inst, P=20, C=32, G=0, init_oversample=5, init_heuristic=1)
+    prob, g, o = run_both(cgo, inst, p, 2)
+    assert_same_state(g, o, "init only")
+    prob2 = cgo.Problem(inst)
+    for bad in (dict(init_oversample=65), dict(init_oversample=64, P=257), dict(init_heuristic=2)):
+        with pytest.raises(cgo.CgoError) as e:
+            prob2.solve(dict(p, **bad), 1)
+        assert e.value.status == cgo.ERR_INVALID
+
+
 # ----------------------------------------------------- state and resume
 @pytest.mark.parametrize("maker", [lambda: I.tsp_uniform(25, 60), lambda: I.knapsack(60, 61),
                                    lambda: I.gap(40, 62, m=6), lambda: I.qap_random(8, 63),

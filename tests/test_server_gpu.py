@@ -37,6 +37,10 @@ def request_mix():
         (dict(I.tsp_uniform(90, 305), tag=6), dict(P=4, C=128, G=52)),
         (dict(I.tsp_uniform(12, 306), tag=7), dict(P=3, C=32, G=0)),
         (dict(I.knapsack(7, 307), tag=8), dict(P=2, C=16, G=9)),
+        # oversampled and heuristic starts
+        (dict(I.tsp_clustered(70, 308), tag=9), dict(P=5, C=64, G=31, init_oversample=4,
+                                                     init_heuristic=1)),
+        (dict(I.gap(25, 309, m=4), tag=10), dict(P=6, C=48, G=22, init_oversample=3)),
     ]
 
 
