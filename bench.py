@@ -188,6 +188,10 @@ def main():
     ap.add_argument("--batch-class", default="mix")
     ap.add_argument("--wpm", type=int, default=0, help="warps per member override (batched)")
     ap.add_argument("--slice", type=int, default=2000)
+    ap.add_argument("--init-oversample", type=int, default=1,
+                    help="single solve: K of the oversampled start (1 = plain start)")
+    ap.add_argument("--init-heuristic", type=int, default=0,
+                    help="single solve: 1 = add the row/column-sum start permutations")
     ap.add_argument("--launch", default="",
                     help="single solve: fixed launch shape 'warps,wpm,staging,gens_in_flight' "
                          "instead of the autotuner (profiling runs)")
@@ -230,6 +234,10 @@ def main():
     inst = dict(inst, tag=0)
     seed = 1 + rank
     stream = torch.cuda.Stream()
+    if args.init_oversample > 1 or args.init_heuristic:
+        cfg["init_oversample"] = args.init_oversample
+        cfg["init_heuristic"] = args.init_heuristic
+        desc += " start=K%d%s" % (args.init_oversample, "+heuristic" if args.init_heuristic else "")
     prob = cgo.Problem(inst)
     params = lib_params(prob, cfg)
     from paper_2603_19163_gb300.autotune import Autotuner
@@ -273,6 +281,11 @@ def main():
     agg = aggregate(sum(step_ms), evals_rank, dist if world > 1 else None, "cuda")
     total_ms, value = agg["max_ms"], agg["per_s"]
     _, best_cost = prob.best()
+    # the elite of the start population alone (no generation)
+    p0 = cgo.Problem(inst)
+    p0.solve(dict(params, G=0), seed, stream)
+    _, start_cost = p0.best()
+    p0.close()
 
     # end to end through the public API: host arrays in, best solution out
     e2e_ms = []
@@ -309,7 +322,7 @@ def main():
                                       "chosen_by": "fixed (--launch)" if args.launch else
                                       "autotuner (%d trial shapes)" % len(
                                           tuner.solve_shapes(params))},
-                           "best_cost": int(best_cost),
+                           "best_cost": int(best_cost), "start_best_cost": int(start_cost),
                            "gens_per_s": cfg["G"] / (total_ms / args.steps / 1000.0)},
                 "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
