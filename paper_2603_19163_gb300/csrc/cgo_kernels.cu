@@ -149,6 +149,44 @@ __device__ __forceinline__ uint32_t stats_record(int op0, int op1, int op2, int 
 
 constexpr uint32_t kNoRecord = 0x1FFu;  // no step taken, k = 0
 
+// Window counts of one member kept in bytes while it evolves (one byte per
+// operator or k level, uses and improvements apart), added to the full
+// counts when its window ends; valid while a lane counts at most 255 uses of
+// one kind in a member window (3 * candidates per lane * U <= 255).
+struct PackedStats {
+  uint32_t u, v, uk, vk;
+};
+
+__device__ __forceinline__ void packed_add(PackedStats &s, uint32_t rec) {
+  const uint32_t imp = (rec >> 11) & 1u, k = (rec >> 9) & 3u;
+  uint32_t inc = 0;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const uint32_t op = (rec >> (3 * t)) & 7u;
+    inc += op < 4u ? 1u << (8u * op) : 0u;
+  }
+  s.u += inc;
+  s.v += imp ? inc : 0u;
+  const uint32_t kin = k ? 1u << (8u * (k - 1u)) : 0u;
+  s.uk += kin;
+  s.vk += imp ? kin : 0u;
+}
+
+template <int NO>
+__device__ __forceinline__ void packed_flush(Stats<NO> &st, PackedStats &s) {
+#pragma unroll
+  for (int i = 0; i < NO; ++i) {
+    st.u[i] += (s.u >> (8 * i)) & 0xFFu;
+    st.v[i] += (s.v >> (8 * i)) & 0xFFu;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    st.uk[i] += (s.uk >> (8 * i)) & 0xFFu;
+    st.vk[i] += (s.vk >> (8 * i)) & 0xFFu;
+  }
+  s.u = s.v = s.uk = s.vk = 0u;
+}
+
 template <int NO>
 __device__ __forceinline__ void stats_add(Stats<NO> &s, uint32_t rec) {
   const uint32_t imp = (rec >> 11) & 1u, k = (rec >> 9) & 3u;
@@ -967,6 +1005,13 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   const int span = WPM * 32;
   const int cpl = (C + span - 1) / span;
   const bool packed = 96ull * (uint64_t)cpl * (uint64_t)I.U * (uint64_t)mine < 65536ull;
+  // a member's window counts in bytes while it evolves (PackedStats)
+  const bool bytec = 3ull * (uint64_t)cpl * (uint64_t)I.U <= 255ull;
+  PackedStats ps{0u, 0u, 0u, 0u};
+  auto count = [&](uint32_t rec) {
+    if (bytec) packed_add(ps, rec);
+    else stats_add(st, rec);
+  };
 
   // generations are below 2^32 (checked on the host), so window arithmetic
   // is 32-bit
@@ -1031,7 +1076,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
                   uint32_t rec;
                   CandMoves cm;
                   if (candidate_cvrptw(X, sol, W, c, p, gm, true, d, rec, cm, cva)) {
-                    stats_add(st, rec);
+                    count(rec);
                     if (d < bd || (d == bd && c < bc)) {
                       bd = d;
                       bc = c;
@@ -1062,7 +1107,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
                 uint32_t rec;
                 CandMoves cm;
                 candidate_cvrptw(X, sol, W, c, p, gm, false, d, rec, cm, cva);
-                stats_add(st, rec);
+                count(rec);
                 if (d < bd || (d == bd && c < bc)) {
                   bd = d;
                   bc = c;
@@ -1084,7 +1129,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
               else if constexpr (MODEL == KNAPSACK)
                 d = candidate_knap(X, sol, W, sc.aw, sc.av, c, p, gm, rec);
               else d = candidate_gap(X, sol, loads, W, c, p, gm, rec);
-              if (gslot == 0) stats_add(st, rec);
+              if (gslot == 0) count(rec);
               else held = rec;  // NS > 1 runs with one candidate per lane
               if (d < bd || (d == bd && c < bc)) {
                 bd = d;
@@ -1152,7 +1197,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
           if (gs >= wend) break;
           const long long d = ds[s2];
           const int c = cs[s2], w = ws[s2];
-          if (s2 > 0 && gslot == s2) stats_add(st, held);
+          if (s2 > 0 && gslot == s2) count(held);
           // the variate is drawn only when it can decide: a worsening move that
           // even the largest variate would reject is rejected without it
           bool acc = d <= 0;
@@ -1185,6 +1230,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         }
         gg += adv;
       }
+      if (bytec) packed_flush(st, ps);
       G.sync();
       if (G.tig == 0) scal[ls] = sc;
       G.sync();
