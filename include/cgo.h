@@ -71,7 +71,10 @@ typedef enum {
   CGO_OP_INSERT = 2,   /* perm: remove a[i], re-insert so it lands at index j */
   CGO_OP_OR_OPT = 3,   /* perm: move a block of 2 or 3 elements (needs length >= 4) */
   CGO_OP_FLIP = 4,     /* binary: x_i ^= 1 */
-  CGO_OP_PERTURB = 5   /* integer: x_i <- another value of [lb, ub] */
+  CGO_OP_PERTURB = 5,  /* integer: x_i <- another value of [lb, ub] */
+  CGO_OP_THREE_OPT = 6 /* perm: exchange the adjacent segments a[i..j-1], a[j..k-1] at three
+                          distinct cut points i < j < k of 0..length (segment level,
+                          Table "operators"); off in the default mask */
 } cgo_op;
 
 #define CGO_NOPS 8

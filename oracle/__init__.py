@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 NOPS = 8
-SWAP, TWO_OPT, INSERT, OR_OPT, FLIP, PERTURB = range(6)
+SWAP, TWO_OPT, INSERT, OR_OPT, FLIP, PERTURB, THREE_OPT = range(7)
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)

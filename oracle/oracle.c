@@ -260,6 +260,7 @@ int32_t orc_enabled_ops(const orc_instance *in, uint32_t op_mask, int32_t enable
   for (int32_t i = 0; i < ORC_NOPS; i++) {
     int32_t ok = 0;
     if (enc == 0 && i <= ORC_OR_OPT) ok = (i == ORC_OR_OPT) ? (len >= 4) : 1; /* [R3] */
+    if (enc == 0 && i == ORC_THREE_OPT) ok = 1;                                /* [R26] */
     if (enc == 1 && i == ORC_FLIP) ok = 1;
     if (enc == 2 && i == ORC_PERTURB) ok = 1;
     enabled[i] = ok && ((op_mask >> i) & 1u);
@@ -318,6 +319,29 @@ int32_t orc_apply_move(const orc_instance *in, int32_t op, uint32_t a, uint32_t 
       free(rest);
       return 0;
     }
+    case ORC_THREE_OPT: { /* [R26] exchange the adjacent segments [i,j) and [j,k) */
+      /* three distinct cut points of 0..len: from len+1, len and len-1 values,
+       * each later draw skipping the points already taken */
+      int32_t c1 = (int32_t)orc_pos(a, (uint32_t)(len + 1));
+      int32_t c2 = (int32_t)orc_pos(b, (uint32_t)len);
+      if (c2 >= c1) c2++;
+      int32_t lo = c1 < c2 ? c1 : c2, hi = c1 < c2 ? c2 : c1;
+      int32_t c3 = (int32_t)orc_pos(x >> 16, (uint32_t)(len - 1));
+      if (c3 >= lo) c3++;
+      if (c3 >= hi) c3++;
+      int32_t ci = lo < c3 ? lo : c3;
+      int32_t ck = hi > c3 ? hi : c3;
+      int32_t cj = c1 + c2 + c3 - ci - ck;
+      int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
+      int32_t o = 0;
+      for (int32_t q = 0; q < ci; q++) t[o++] = s[q];
+      for (int32_t q = cj; q < ck; q++) t[o++] = s[q];
+      for (int32_t q = ci; q < cj; q++) t[o++] = s[q];
+      for (int32_t q = ck; q < len; q++) t[o++] = s[q];
+      memcpy(s, t, sizeof(int32_t) * (size_t)len);
+      free(t);
+      return 0;
+    }
     case ORC_FLIP: { /* x_i ^= 1 */
       i = (int32_t)orc_pos(a, (uint32_t)len);
       s[i] ^= 1;
@@ -373,16 +397,21 @@ void orc_params_default(const orc_instance *in, orc_params *pr) {
   pr->P = 32;
   pr->C = 128;
   pr->op_mask = 0x3Fu;
+  /* priors of every applicable operator (Table "weight_preset"); the
+   * normaliser is taken over the default mask (3-opt off by default) */
+  int32_t app[ORC_NOPS];
   orc_enabled_ops(in, pr->op_mask, en);
+  orc_enabled_ops(in, 0xFFu, app);
   uint64_t S = 0;
   for (int32_t i = 0; i < ORC_NOPS; i++) {
     uint32_t w = 0;
-    if (en[i]) {
+    if (app[i]) {
       w = 65536u;
       if (i == ORC_OR_OPT) w = len <= 100 ? 52429u : (len <= 250 ? 45875u : 19661u);
+      if (i == ORC_THREE_OPT) w = len <= 100 ? 32768u : (len <= 250 ? 19661u : 3277u);
     }
     pr->w_op[i] = w;
-    S += w;
+    if (en[i]) S += w;
     pr->op_cap[i] = 65536u;
   }
   for (int32_t i = 0; i < ORC_NOPS; i++) pr->w_op[i] = (uint32_t)(((uint64_t)pr->w_op[i] << 16) / S);

@@ -235,7 +235,7 @@ uint32_t applicable_mask(const cgo_problem *p) {
   const int enc = encoding_of(p->model);
   if (enc == CGO_ENC_BINARY) return 1u << FLIP;
   if (enc == CGO_ENC_INTEGER) return 1u << PERTURB;
-  uint32_t m = (1u << SWAP) | (1u << TWO_OPT) | (1u << INSERT);
+  uint32_t m = (1u << SWAP) | (1u << TWO_OPT) | (1u << INSERT) | (1u << THREE_OPT);
   if (p->len >= 4) m |= 1u << OR_OPT;
   return m;
 }
@@ -712,16 +712,19 @@ cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
   q->population = 32;
   q->candidates = 128;
   q->generations = 2000;
-  const uint32_t en = applicable_mask(p);
+  const uint32_t app = applicable_mask(p);
+  const uint32_t en = app & ~(1u << THREE_OPT);  // 3-opt is off by default
   q->op_mask = en;
-  // Table "weight_preset": O(1) operators 1.0; or-opt by scale of the length
+  // Table "weight_preset": O(1) operators 1.0; or-opt and 3-opt by scale of
+  // the length; the normaliser is taken over the default mask
   uint64_t S = 0;
   uint32_t w[kNops] = {0};
   for (int i = 0; i < kNops; ++i) {
-    if (!((en >> i) & 1u)) continue;
+    if (!((app >> i) & 1u)) continue;
     w[i] = 65536u;
     if (i == OR_OPT) w[i] = p->len <= 100 ? 52429u : (p->len <= 250 ? 45875u : 19661u);
-    S += w[i];
+    if (i == THREE_OPT) w[i] = p->len <= 100 ? 32768u : (p->len <= 250 ? 19661u : 3277u);
+    if ((en >> i) & 1u) S += w[i];
   }
   for (int i = 0; i < kNops; ++i) {
     q->op_w0_q16[i] = (uint32_t)(((uint64_t)w[i] << 16) / S);

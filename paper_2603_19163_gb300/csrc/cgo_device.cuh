@@ -158,17 +158,22 @@ __device__ __forceinline__ uint64_t udiv_exact(uint64_t num, uint64_t den) {
 // Eq. "ema" for both levels at once, one lane per weight: lanes 0..NO-1
 // hold the operator weights, lanes 24..26 the K weights; u/v are read from
 // the lanes that hold the window totals (u_op at lane o, v_op at 8+o, u_k at
-// 16+i, v_k at 19+i).  Every lane ends with the new weights.
-template <int NO, int BASE>
-__device__ __forceinline__ void aos_update_lanes(uint32_t (&wop)[NO], uint32_t (&wk)[3],
+// 16+i, v_k at 19+i, o the global operator E::glob(l) of local operator l).
+// Every lane ends with the new weights.
+template <class E>
+__device__ __forceinline__ void aos_update_lanes(uint32_t (&wop)[E::NO], uint32_t (&wk)[3],
                                                  uint32_t total, uint32_t en_local,
-                                                 const uint32_t (&capl)[NO], uint32_t a,
+                                                 const uint32_t (&capl)[E::NO], uint32_t a,
                                                  uint32_t wfloor, uint32_t wcap) {
+  constexpr int NO = E::NO;
   const int lane = threadIdx.x & 31;
   const bool is_op = lane < NO, is_k = lane >= 24 && lane < 27;
   const int li = is_op ? lane : lane - 24;
-  const uint32_t u = __shfl_sync(kFull, total, is_op ? BASE + li : (is_k ? 16 + li : 0));
-  const uint32_t v = __shfl_sync(kFull, total, is_op ? 8 + BASE + li : (is_k ? 19 + li : 0));
+  int go = 0;
+#pragma unroll
+  for (int l = 0; l < NO; ++l) go = li == l ? E::glob(l) : go;
+  const uint32_t u = __shfl_sync(kFull, total, is_op ? go : (is_k ? 16 + li : 0));
+  const uint32_t v = __shfl_sync(kFull, total, is_op ? 8 + go : (is_k ? 19 + li : 0));
   uint32_t w = 0, cap = 65536u;
   bool en = false;
 #pragma unroll
@@ -272,18 +277,29 @@ __device__ __forceinline__ PMove perm_decode(int op, uint32_t r1, uint32_t r2, i
   j += (j >= i);
   const int lo = min(i, j), hi = max(i, j);
   const bool ob = q < io;
-  const bool oo = op == OR_OPT, sw = op == SWAP, two = op == TWO_OPT, fw = i < j;
+  // local operator 4 of a permutation is 3-opt: three distinct cut points of
+  // 0..m (from m+1, m and m-1 values, each later draw stepping over the
+  // points already taken); the segments between them change places
+  const bool oo = op == OR_OPT, sw = op == SWAP, two = op == TWO_OPT, fw = i < j, t3 = op == 4;
+  const int c1 = posm(a, (uint32_t)(m + 1));
+  int c2 = posm(b, (uint32_t)m);
+  c2 += (c2 >= c1);
+  const int clo = min(c1, c2), chi = max(c1, c2);
+  int c3 = posm(r2 >> 16, (uint32_t)(m - 1));
+  c3 += (c3 >= clo);
+  c3 += (c3 >= chi);
+  const int ci = min(clo, c3), ck = max(chi, c3), cj = c1 + c2 + c3 - ci - ck;
   PMove mv;
   const int o1 = ob ? q : io, o2 = ob ? io : io + L, o4 = ob ? io + L : q + L;
   const int p1 = (sw || two) ? lo : (fw ? i : j);
   const int p2 = sw ? lo + 1 : (two ? hi + 1 : (fw ? i + 1 : i));
   const int p3 = sw ? hi : (two ? hi + 1 : (fw ? i + 1 : i));
   const int p4 = sw ? hi + 1 : (two ? hi + 1 : (fw ? j + 1 : i + 1));
-  mv.b1 = oo ? o1 : p1;
-  mv.b2 = oo ? o2 : p2;
-  mv.b3 = oo ? o2 : p3;
-  mv.b4 = oo ? o4 : p4;
-  mv.rev = (!oo && two) ? 1 : 0;
+  mv.b1 = t3 ? ci : (oo ? o1 : p1);
+  mv.b2 = t3 ? cj : (oo ? o2 : p2);
+  mv.b3 = t3 ? cj : (oo ? o2 : p3);
+  mv.b4 = t3 ? ck : (oo ? o4 : p4);
+  mv.rev = (!oo && !t3 && two) ? 1 : 0;
   return mv;
 }
 

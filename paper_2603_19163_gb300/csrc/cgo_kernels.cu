@@ -154,19 +154,20 @@ constexpr uint32_t kNoRecord = 0x1FFu;  // no step taken, k = 0
 // counts when its window ends; valid while a lane counts at most 255 uses of
 // one kind in a member window (3 * candidates per lane * U <= 255).
 struct PackedStats {
-  uint32_t u, v, uk, vk;
+  uint64_t u, v;  // one byte per local operator
+  uint32_t uk, vk;
 };
 
 __device__ __forceinline__ void packed_add(PackedStats &s, uint32_t rec) {
   const uint32_t imp = (rec >> 11) & 1u, k = (rec >> 9) & 3u;
-  uint32_t inc = 0;
+  uint64_t inc = 0;
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
     const uint32_t op = (rec >> (3 * t)) & 7u;
-    inc += op < 4u ? 1u << (8u * op) : 0u;
+    inc += op < 7u ? 1ull << (8u * op) : 0ull;
   }
   s.u += inc;
-  s.v += imp ? inc : 0u;
+  s.v += imp ? inc : 0ull;
   const uint32_t kin = k ? 1u << (8u * (k - 1u)) : 0u;
   s.uk += kin;
   s.vk += imp ? kin : 0u;
@@ -176,15 +177,16 @@ template <int NO>
 __device__ __forceinline__ void packed_flush(Stats<NO> &st, PackedStats &s) {
 #pragma unroll
   for (int i = 0; i < NO; ++i) {
-    st.u[i] += (s.u >> (8 * i)) & 0xFFu;
-    st.v[i] += (s.v >> (8 * i)) & 0xFFu;
+    st.u[i] += (uint32_t)(s.u >> (8 * i)) & 0xFFu;
+    st.v[i] += (uint32_t)(s.v >> (8 * i)) & 0xFFu;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     st.uk[i] += (s.uk >> (8 * i)) & 0xFFu;
     st.vk[i] += (s.vk >> (8 * i)) & 0xFFu;
   }
-  s.u = s.v = s.uk = s.vk = 0u;
+  s.u = s.v = 0ull;
+  s.uk = s.vk = 0u;
 }
 
 template <int NO>
@@ -208,19 +210,24 @@ __device__ __forceinline__ void stats_add(Stats<NO> &s, uint32_t rec) {
   }
 }
 
-// per-encoding operator block: local op l is global op (base + l)
+// per-encoding operator set: local op l is global op glob(l) (permutations:
+// swap, 2-opt, insertion, or-opt, 3-opt; binary: flip; integer: reset)
+struct PermOps {
+  static constexpr int NO = 5;
+  __host__ __device__ static constexpr int glob(int l) { return l < 4 ? l : (int)THREE_OPT; }
+};
 template <int MODEL>
-struct Enc;
+struct Enc : PermOps {};
 template <>
-struct Enc<TSP> { static constexpr int NO = 4, BASE = 0; };
+struct Enc<KNAPSACK> {
+  static constexpr int NO = 1;
+  __host__ __device__ static constexpr int glob(int) { return (int)FLIP; }
+};
 template <>
-struct Enc<QAP> { static constexpr int NO = 4, BASE = 0; };
-template <>
-struct Enc<CVRPTW> { static constexpr int NO = 4, BASE = 0; };
-template <>
-struct Enc<KNAPSACK> { static constexpr int NO = 1, BASE = 4; };
-template <>
-struct Enc<GAP> { static constexpr int NO = 1, BASE = 5; };
+struct Enc<GAP> {
+  static constexpr int NO = 1;
+  __host__ __device__ static constexpr int glob(int) { return (int)PERTURB; }
+};
 
 template <int NO>
 struct Weights {
@@ -592,7 +599,7 @@ __device__ long long cvrptw_composite(const View &X, const PermEl *sol, const Ca
 // sequence against their cached old cost.  With `defer` set, a candidate of
 // k >= 2 steps is not evaluated and false is returned.
 __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *sol,
-                                                 const Weights<4> &W, uint32_t c, uint32_t p,
+                                                 const Weights<5> &W, uint32_t c, uint32_t p,
                                                  uint32_t g, bool defer, long long &d,
                                                  uint32_t &rec, CandMoves &cm, const CvAux &aux) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
@@ -625,7 +632,7 @@ __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *so
 // deltas), so the steps overlap; k selects how many count.
 template <int MODEL, bool T16>
 __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl *sol,
-                                                    const Weights<4> &W, uint32_t c, uint32_t p,
+                                                    const Weights<5> &W, uint32_t c, uint32_t p,
                                                     uint32_t g, uint32_t &rec, CandMoves &cm,
                                                     const CvAux &aux) {
   if constexpr (MODEL == CVRPTW) {
@@ -930,7 +937,7 @@ struct __align__(16) Partial {
 template <int MODEL, bool T16, int WPM, int NS>
 __device__ void evolve_members(const KInst &I, const View &X, unsigned char *smem, const Layout &Lo,
                                int p0, int nsol, int warps, uint64_t timeout_ns) {
-  constexpr int NO = Enc<MODEL>::NO, BASE = Enc<MODEL>::BASE;
+  constexpr int NO = Enc<MODEL>::NO;
   constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW);
   using El = typename SolEl<MODEL>::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -983,14 +990,16 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   uint32_t capl[NO];
 #pragma unroll
   for (int l = 0; l < NO; ++l) {
-    W.op[l] = A->w_op[BASE + l];
-    capl[l] = I.op_cap[BASE + l];
+    W.op[l] = A->w_op[Enc<MODEL>::glob(l)];
+    capl[l] = I.op_cap[Enc<MODEL>::glob(l)];
   }
   W.k[0] = A->w_k[0];
   W.k[1] = A->w_k[1];
   W.k[2] = A->w_k[2];
   weights_sum(W);
-  const uint32_t en_local = (I.enabled >> BASE) & ((1u << NO) - 1u);
+  uint32_t en_local = 0;
+#pragma unroll
+  for (int l = 0; l < NO; ++l) en_local |= ((I.enabled >> Enc<MODEL>::glob(l)) & 1u) << l;
   uint32_t stag = A->stag;
   long long elite_prev = A->elite_prev;
   uint32_t pend = lane < kStats ? A->pend[lane] : 0u;
@@ -1007,7 +1016,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   const bool packed = 96ull * (uint64_t)cpl * (uint64_t)I.U * (uint64_t)mine < 65536ull;
   // a member's window counts in bytes while it evolves (PackedStats)
   const bool bytec = 3ull * (uint64_t)cpl * (uint64_t)I.U <= 255ull;
-  PackedStats ps{0u, 0u, 0u, 0u};
+  PackedStats ps{0ull, 0ull, 0u, 0u};
   auto count = [&](uint32_t rec) {
     if (bytec) packed_add(ps, rec);
     else stats_add(st, rec);
@@ -1272,8 +1281,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     uint32_t my = 0;
 #pragma unroll
     for (int l = 0; l < NO; ++l) {
-      my = (lane == BASE + l) ? tot[l] : my;
-      my = (lane == 8 + BASE + l) ? tot[NO + l] : my;
+      my = (lane == Enc<MODEL>::glob(l)) ? tot[l] : my;
+      my = (lane == 8 + Enc<MODEL>::glob(l)) ? tot[NO + l] : my;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -1311,7 +1320,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     const long long elite = ld_relaxed64((const long long *)&S->elite[slot]);
     ++wi;
 
-    aos_update_lanes<NO, BASE>(W.op, W.k, total, en_local, capl, I.ema_a, I.w_floor, I.w_cap);
+    aos_update_lanes<Enc<MODEL>>(W.op, W.k, total, en_local, capl, I.ema_a, I.w_floor, I.w_cap);
     if (elite < elite_prev) stag = 0;
     else ++stag;
     elite_prev = elite;
@@ -1385,8 +1394,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
 #pragma unroll
     for (int l = 0; l < NO; ++l) {
       const uint32_t tu = __reduce_add_sync(kFull, st.u[l]), tv = __reduce_add_sync(kFull, st.v[l]);
-      my = (lane == BASE + l) ? tu : my;
-      my = (lane == 8 + BASE + l) ? tv : my;
+      my = (lane == Enc<MODEL>::glob(l)) ? tu : my;
+      my = (lane == 8 + Enc<MODEL>::glob(l)) ? tv : my;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -1425,7 +1434,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     O->g = I.g_end;
     for (int i = 0; i < kNops; ++i) O->w_op[i] = 0;
 #pragma unroll
-    for (int l = 0; l < NO; ++l) O->w_op[BASE + l] = W.op[l];
+    for (int l = 0; l < NO; ++l) O->w_op[Enc<MODEL>::glob(l)] = W.op[l];
     O->w_k[0] = W.k[0];
     O->w_k[1] = W.k[1];
     O->w_k[2] = W.k[2];

@@ -46,6 +46,11 @@ def mixed_batch():
     items.append((dict(I.qap_random(12, 253), tag=43),
                   dict(P=5, C=48, G=19, ops=[SW], init_oversample=2, init_heuristic=1)))
     items.append((dict(I.knapsack(80, 254), tag=44), dict(P=7, C=64, G=15, init_oversample=4)))
+    # 3-opt with the other permutation operators
+    items.append((dict(I.tsp_uniform(70, 255), tag=45),
+                  dict(P=6, C=96, G=23, ops=[0, 1, 2, 3, O.THREE_OPT])))
+    items.append((dict(I.cvrptw(22, 256, vehicles=5, capacity=100), tag=46),
+                  dict(P=5, C=64, G=19, ops=[0, 1, 2, 3, O.THREE_OPT])))
     return items
 
 

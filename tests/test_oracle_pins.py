@@ -246,6 +246,42 @@ def test_move_invariants_random():
         assert (t != s).sum() == 1 and t.min() >= 0 and t.max() <= 4
 
 
+def _exchange_cuts(s, t):
+    """All (i, j, k) with t = s[:i] + s[j:k] + s[i:j] + s[k:], i < j < k."""
+    m = len(s)
+    s, t = list(s), list(t)
+    return [(i, j, k) for i in range(m) for j in range(i + 1, m) for k in range(j + 1, m + 1)
+            if s[:i] + s[j:k] + s[i:j] + s[k:] == t]
+
+
+def test_three_opt_is_an_adjacent_segment_exchange_with_uniform_cuts():
+    """3-opt (Table "operators", segment level): the result is the original
+    with two adjacent segments exchanged, and the cut triples are (nearly)
+    uniform over all C(m+1, 3) choices."""
+    rng = np.random.default_rng(21)
+    for m in (2, 3, 5, 8, 13):
+        inst = dict(model=0, n=m)
+        seen = {}
+        s = np.arange(m, dtype=np.int32)
+        draws = 6000 if m == 5 else 300
+        for _ in range(draws):
+            a, b = (int(v) for v in rng.integers(0, 65536, 2))
+            x = int(rng.integers(0, 2**32))
+            t = O.apply_move(inst, O.THREE_OPT, a, b, x, s)
+            cuts = _exchange_cuts(s, t)
+            assert cuts, (m, a, b, x, t)
+            seen[tuple(t.tolist())] = seen.get(tuple(t.tolist()), 0) + 1
+        if m == 5:
+            # every exchange is reachable; frequencies within 30% of uniform
+            # (distinct triples can give the same array only for equal lengths)
+            total = sum(seen.values())
+            assert len(seen) >= 15
+            per_triple = draws / 20
+            for arr, cnt in seen.items():
+                n_tr = len(_exchange_cuts(s, np.array(arr)))
+                assert abs(cnt - n_tr * per_triple) < 0.3 * n_tr * per_triple, (arr, cnt, n_tr)
+
+
 # ------------------------------------------------------------- golden costs
 def _inst_from_case(c):
     inst = {k: v for k, v in c.items() if k not in ("name", "sol", "cost", "work")}

@@ -265,14 +265,17 @@ def test_thread_count_does_not_change_results():
 
 
 def test_default_priors_by_scale():
-    # Table "weight_preset": or-opt prior 0.80 / 0.70 / 0.30 by scale, the
-    # O(1) operators 1.0, all normalised to Q16
-    for n, oro in ((50, 52429), (200, 45875), (442, 19661)):
+    # Table "weight_preset": or-opt prior 0.80 / 0.70 / 0.30 and 3-opt prior
+    # 0.50 / 0.30 / 0.05 by scale, the O(1) operators 1.0, normalised to Q16
+    # over the default mask (3-opt off by default, its prior kept on the same
+    # scale for callers that enable it)
+    for n, oro, tro in ((50, 52429, 32768), (200, 45875, 19661), (442, 19661, 3277)):
         inst = I.tsp_uniform(n, 10)
         p = O.default_params(inst)
         S = 3 * 65536 + oro
         assert p["w_op"][:4] == [(65536 << 16) // S] * 3 + [(oro << 16) // S]
-        assert p["w_op"][4:] == [0, 0, 0, 0]
+        assert p["w_op"][4:] == [0, 0, (tro << 16) // S, 0]
+        assert not (p["op_mask"] >> O.THREE_OPT) & 1
         assert p["w_k"] == [52429, 9830, 3277]
 
 

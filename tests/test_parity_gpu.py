@@ -16,7 +16,7 @@ from helpers import assert_same_state, oracle_run, params_for
 
 pytestmark = pytest.mark.gpu
 
-SW, TO, INS, OR = O.SWAP, O.TWO_OPT, O.INSERT, O.OR_OPT
+SW, TO, INS, OR, TH = O.SWAP, O.TWO_OPT, O.INSERT, O.OR_OPT, O.THREE_OPT
 
 
 @pytest.fixture(scope="module")
@@ -54,12 +54,23 @@ def test_tsp_n20_config(cgo, seed, ns):
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 33])
 def test_tsp_small_n_all_ops(cgo, n):
     inst = I.tsp_uniform(n, 10 + n)
-    p = params_for(inst, P=5, C=40, G=37, U=3, ops=[SW, TO, INS, OR])
+    p = params_for(inst, P=5, C=40, G=37, U=3, ops=[SW, TO, INS, OR, TH])
     _, g, o = run_both(cgo, inst, p, 3)
     assert_same_state(g, o, "n=%d" % n)
 
 
-@pytest.mark.parametrize("op", [SW, TO, INS, OR])
+@pytest.mark.parametrize("ns,C", [(1, 100), (2, 64), (1, 300)])
+def test_three_opt_tsp_and_cvrptw(cgo, ns, C):
+    """3-opt (segment exchange) with the other operators, alone and composed,
+    on TSP and on the routing model's separator sequence."""
+    for inst in (I.tsp_clustered(90, 60), I.cvrptw(30, 61, vehicles=6, capacity=90)):
+        for ops in ([TH], [SW, TO, INS, OR, TH]):
+            p = params_for(inst, P=6, C=C, G=27, U=5, ops=ops, T0=30 << 32)
+            _, g, o = run_both(cgo, inst, p, 5, ns=ns)
+            assert_same_state(g, o, "model %d ops %s ns %d" % (inst["model"], ops, ns))
+
+
+@pytest.mark.parametrize("op", [SW, TO, INS, OR, TH])
 @pytest.mark.parametrize("kw", [(65536, 0, 0), (0, 65536, 0), (0, 0, 65536)])
 def test_tsp_each_op_each_k(cgo, op, kw):
     inst = I.tsp_uniform(17, 21)
