@@ -73,17 +73,14 @@ __device__ __forceinline__ void philox3(uint32_t a0, uint32_t b0, uint32_t e0, u
 __device__ __forceinline__ int posm(uint32_t h16, uint32_t m) { return (int)((h16 * m) >> 16); }
 
 // Roulette choice: r = floor(word * W / 2^32), first i with r < w_0 + .. + w_i.
-// Counting the prefix sums <= r gives that index for non-decreasing sums.
+// Counting the prefix sums cum_i = w_0 + .. + w_i that are <= r gives that
+// index (the sums do not decrease).
 template <int N>
-__device__ __forceinline__ int wsample(const uint32_t (&w)[N], uint32_t W, uint32_t word) {
+__device__ __forceinline__ int wpick(const uint32_t (&cum)[N], uint32_t W, uint32_t word) {
   const uint32_t r = __umulhi(word, W);
-  uint32_t acc = 0;
   int idx = 0;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    acc += w[i];
-    idx += (r >= acc);
-  }
+  for (int i = 0; i < N; ++i) idx += (r >= cum[i]);
   return idx;
 }
 
@@ -264,6 +261,7 @@ struct PMove {
   int rev;
 };
 
+template <bool T3>
 __device__ __forceinline__ PMove perm_decode(int op, uint32_t r1, uint32_t r2, int m) {
   // every variant is computed and the operator selects one (no branches:
   // lanes of a warp draw different operators)
@@ -279,16 +277,25 @@ __device__ __forceinline__ PMove perm_decode(int op, uint32_t r1, uint32_t r2, i
   const bool ob = q < io;
   // local operator 4 of a permutation is 3-opt: three distinct cut points of
   // 0..m (from m+1, m and m-1 values, each later draw stepping over the
-  // points already taken); the segments between them change places
-  const bool oo = op == OR_OPT, sw = op == SWAP, two = op == TWO_OPT, fw = i < j, t3 = op == 4;
-  const int c1 = posm(a, (uint32_t)(m + 1));
-  int c2 = posm(b, (uint32_t)m);
-  c2 += (c2 >= c1);
-  const int clo = min(c1, c2), chi = max(c1, c2);
-  int c3 = posm(r2 >> 16, (uint32_t)(m - 1));
-  c3 += (c3 >= clo);
-  c3 += (c3 >= chi);
-  const int ci = min(clo, c3), ck = max(chi, c3), cj = c1 + c2 + c3 - ci - ck;
+  // points already taken); the segments between them change places.  Its
+  // variant is compiled in only where the instance enables it (T3), so
+  // other instances run the same straight-line code as without it.
+  const bool oo = op == OR_OPT, sw = op == SWAP, two = op == TWO_OPT, fw = i < j;
+  bool t3 = false;
+  int ci = 0, cj = 0, ck = 0;
+  if constexpr (T3) {
+    t3 = op == 4;
+    const int c1 = posm(a, (uint32_t)(m + 1));
+    int c2 = posm(b, (uint32_t)m);
+    c2 += (c2 >= c1);
+    const int clo = min(c1, c2), chi = max(c1, c2);
+    int c3 = posm(r2 >> 16, (uint32_t)(m - 1));
+    c3 += (c3 >= clo);
+    c3 += (c3 >= chi);
+    ci = min(clo, c3);
+    ck = max(chi, c3);
+    cj = c1 + c2 + c3 - ci - ck;
+  }
   PMove mv;
   const int o1 = ob ? q : io, o2 = ob ? io : io + L, o4 = ob ? io + L : q + L;
   const int p1 = (sw || two) ? lo : (fw ? i : j);

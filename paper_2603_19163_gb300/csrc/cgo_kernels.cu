@@ -121,6 +121,7 @@ struct View {
   const int4 *node;                           // CVRPTW: {ready, due, service, demand}
   long long lam1;
   bool cv32;
+  bool t3;  // 3-opt enabled for this instance
 };
 
 template <int NO>
@@ -154,39 +155,38 @@ constexpr uint32_t kNoRecord = 0x1FFu;  // no step taken, k = 0
 // counts when its window ends; valid while a lane counts at most 255 uses of
 // one kind in a member window (3 * candidates per lane * U <= 255).
 struct PackedStats {
-  uint64_t u, v;  // one byte per local operator
-  uint32_t uk, vk;
+  uint32_t u, v;    // local operators 0..3, one byte each
+  uint32_t uk, vk;  // k levels 1..3 in bytes 0..2, local operator 4 in byte 3
 };
 
 __device__ __forceinline__ void packed_add(PackedStats &s, uint32_t rec) {
   const uint32_t imp = (rec >> 11) & 1u, k = (rec >> 9) & 3u;
-  uint64_t inc = 0;
+  uint32_t inc = 0, inck = k ? 1u << (8u * (k - 1u)) : 0u;
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
     const uint32_t op = (rec >> (3 * t)) & 7u;
-    inc += op < 7u ? 1ull << (8u * op) : 0ull;
+    inc += op < 4u ? 1u << (8u * op) : 0u;
+    inck += op == 4u ? 1u << 24 : 0u;
   }
   s.u += inc;
-  s.v += imp ? inc : 0ull;
-  const uint32_t kin = k ? 1u << (8u * (k - 1u)) : 0u;
-  s.uk += kin;
-  s.vk += imp ? kin : 0u;
+  s.v += imp ? inc : 0u;
+  s.uk += inck;
+  s.vk += imp ? inck : 0u;
 }
 
 template <int NO>
 __device__ __forceinline__ void packed_flush(Stats<NO> &st, PackedStats &s) {
 #pragma unroll
   for (int i = 0; i < NO; ++i) {
-    st.u[i] += (uint32_t)(s.u >> (8 * i)) & 0xFFu;
-    st.v[i] += (uint32_t)(s.v >> (8 * i)) & 0xFFu;
+    st.u[i] += (i < 4 ? s.u >> (8 * i) : s.uk >> 24) & 0xFFu;
+    st.v[i] += (i < 4 ? s.v >> (8 * i) : s.vk >> 24) & 0xFFu;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     st.uk[i] += (s.uk >> (8 * i)) & 0xFFu;
     st.vk[i] += (s.vk >> (8 * i)) & 0xFFu;
   }
-  s.u = s.v = 0ull;
-  s.uk = s.vk = 0u;
+  s.u = s.v = s.uk = s.vk = 0u;
 }
 
 template <int NO>
@@ -231,16 +231,36 @@ struct Enc<GAP> {
 
 template <int NO>
 struct Weights {
-  uint32_t op[NO], k[3];
+  // prefix sums only (the roulette's thresholds): op[i] = cop[i] - cop[i-1]
+  uint32_t cop[NO], ck[3];
   uint32_t Wop, Wk;
 };
 
+// the prefix sums and totals of both levels from the weights (when the
+// weights change, i.e. once per window), and the weights back
 template <int NO>
-__device__ __forceinline__ void weights_sum(Weights<NO> &w) {
+__device__ __forceinline__ void weights_set(Weights<NO> &w, const uint32_t (&op)[NO],
+                                            const uint32_t (&k)[3]) {
   w.Wop = 0;
 #pragma unroll
-  for (int i = 0; i < NO; ++i) w.Wop += w.op[i];
-  w.Wk = w.k[0] + w.k[1] + w.k[2];
+  for (int i = 0; i < NO; ++i) {
+    w.Wop += op[i];
+    w.cop[i] = w.Wop;
+  }
+  w.ck[0] = k[0];
+  w.ck[1] = w.ck[0] + k[1];
+  w.ck[2] = w.ck[1] + k[2];
+  w.Wk = w.ck[2];
+}
+
+template <int NO>
+__device__ __forceinline__ void weights_get(const Weights<NO> &w, uint32_t (&op)[NO],
+                                            uint32_t (&k)[3]) {
+#pragma unroll
+  for (int i = 0; i < NO; ++i) op[i] = w.cop[i] - (i ? w.cop[i - 1] : 0u);
+  k[0] = w.ck[0];
+  k[1] = w.ck[1] - w.ck[0];
+  k[2] = w.ck[2] - w.ck[1];
 }
 
 __device__ __forceinline__ long long overp(long long x) { return x > 0 ? x : 0; }
@@ -603,13 +623,14 @@ __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *so
                                                  uint32_t g, bool defer, long long &d,
                                                  uint32_t &rec, CandMoves &cm, const CvAux &aux) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
-  const int k = 1 + wsample(W.k, W.Wk, R0.w);
+  const int k = 1 + wpick(W.ck, W.Wk, R0.w);
   if (defer && k >= 2) return false;
   int ops[3] = {-1, -1, -1};
   cm.k = k;
   cm.m[1] = cm.m[2] = PMove{0, 0, 0, 0, 0};
-  ops[0] = wsample(W.op, W.Wop, R0.x);
-  cm.m[0] = perm_decode(ops[0], R0.y, R0.z, X.len);
+  ops[0] = wpick(W.cop, W.Wop, R0.x);
+  cm.m[0] = X.t3 ? perm_decode<true>(ops[0], R0.y, R0.z, X.len)
+                 : perm_decode<false>(ops[0], R0.y, R0.z, X.len);
   if (k == 1) {
     d = cvrptw_step0(X, sol, cm.m[0], aux);
   } else {
@@ -617,8 +638,9 @@ __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *so
     for (int t = 1; t < 3; ++t) {
       if (t < k) {
         const uint4 R = philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
-        ops[t] = wsample(W.op, W.Wop, R.x);
-        cm.m[t] = perm_decode(ops[t], R.y, R.z, X.len);
+        ops[t] = wpick(W.cop, W.Wop, R.x);
+        cm.m[t] = X.t3 ? perm_decode<true>(ops[t], R.y, R.z, X.len)
+                       : perm_decode<false>(ops[t], R.y, R.z, X.len);
       }
     }
     d = cvrptw_composite(X, sol, cm, aux);
@@ -643,7 +665,7 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
   if constexpr (MODEL == QAP) {
     // O(n) deltas: evaluate only the k steps that count
     const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
-    const int k = 1 + wsample(W.k, W.Wk, R0.w);
+    const int k = 1 + wpick(W.ck, W.Wk, R0.w);
     int ops[3] = {-1, -1, -1};
     long long d = 0;
     cm.k = k;
@@ -652,8 +674,9 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
     for (int t = 0; t < 3; ++t) {
       if (t < k) {
         const uint4 R = t == 0 ? R0 : philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
-        ops[t] = wsample(W.op, W.Wop, R.x);
-        cm.m[t] = perm_decode(ops[t], R.y, R.z, X.len);
+        ops[t] = wpick(W.cop, W.Wop, R.x);
+        cm.m[t] = X.t3 ? perm_decode<true>(ops[t], R.y, R.z, X.len)
+                       : perm_decode<false>(ops[t], R.y, R.z, X.len);
         d += qap_step(X, sol, cm.m[t], cm.m[0], cm.m[1], t);
       }
     }
@@ -663,13 +686,19 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
   uint4 R0, R1, R2;
   philox3(ctr_word(c, 0, kKindMove), ctr_word(c, 1, kKindMove), ctr_word(c, 2, kKindMove), X.tag,
           p, g, X.k0, X.k1, R0, R1, R2);
-  const int k = 1 + wsample(W.k, W.Wk, R0.w);
-  const int op0 = wsample(W.op, W.Wop, R0.x);
-  const int op1 = wsample(W.op, W.Wop, R1.x);
-  const int op2 = wsample(W.op, W.Wop, R2.x);
-  cm.m[0] = perm_decode(op0, R0.y, R0.z, X.len);
-  cm.m[1] = perm_decode(op1, R1.y, R1.z, X.len);
-  cm.m[2] = perm_decode(op2, R2.y, R2.z, X.len);
+  const int k = 1 + wpick(W.ck, W.Wk, R0.w);
+  const int op0 = wpick(W.cop, W.Wop, R0.x);
+  const int op1 = wpick(W.cop, W.Wop, R1.x);
+  const int op2 = wpick(W.cop, W.Wop, R2.x);
+  if (X.t3) {
+    cm.m[0] = perm_decode<true>(op0, R0.y, R0.z, X.len);
+    cm.m[1] = perm_decode<true>(op1, R1.y, R1.z, X.len);
+    cm.m[2] = perm_decode<true>(op2, R2.y, R2.z, X.len);
+  } else {
+    cm.m[0] = perm_decode<false>(op0, R0.y, R0.z, X.len);
+    cm.m[1] = perm_decode<false>(op1, R1.y, R1.z, X.len);
+    cm.m[2] = perm_decode<false>(op2, R2.y, R2.z, X.len);
+  }
   cm.k = k;
   const long long d = tsp_three_steps<T16>(X, sol, cm, k);
   rec = stats_record(op0, k >= 2 ? op1 : -1, k >= 3 ? op2 : -1, k, d < 0);
@@ -682,7 +711,7 @@ __device__ long long candidate_knap(const View &X, const ByteEl *x, const Weight
                                     long long W0, long long V0, uint32_t c, uint32_t p,
                                     uint32_t g, uint32_t &rec) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
-  const int k = 1 + wsample(W.k, W.Wk, R0.w);
+  const int k = 1 + wpick(W.ck, W.Wk, R0.w);
   long long Wt = W0, Vt = V0;
   int i0 = -1, i1 = -1;
 #pragma unroll
@@ -709,7 +738,7 @@ __device__ long long candidate_gap(const View &X, const ByteEl *x, const long lo
                                    const Weights<1> &W, uint32_t c, uint32_t p, uint32_t g,
                                    uint32_t &rec) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
-  const int k = 1 + wsample(W.k, W.Wk, R0.w);
+  const int k = 1 + wpick(W.ck, W.Wk, R0.w);
   const int n = X.n, m = X.m;
   int xj[2] = {-1, -1}, xv[2] = {0, 0};
   int la[4] = {-1, -1, -1, -1};
@@ -786,7 +815,7 @@ template <int NO>
 __device__ __forceinline__ int regen_k(const View &X, const Weights<NO> &W, uint32_t c,
                                        uint32_t p, uint32_t g, uint4 &R0) {
   R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
-  return 1 + wsample(W.k, W.Wk, R0.w);
+  return 1 + wpick(W.ck, W.Wk, R0.w);
 }
 
 __device__ void apply_perm(PermEl *sol, PermEl *scr, const CandMoves &cm, const Group &G) {
@@ -988,15 +1017,18 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   uint64_t T = A->T;
   Weights<NO> W;
   uint32_t capl[NO];
+  {
+    uint32_t wo[NO], wk[3];
 #pragma unroll
-  for (int l = 0; l < NO; ++l) {
-    W.op[l] = A->w_op[Enc<MODEL>::glob(l)];
-    capl[l] = I.op_cap[Enc<MODEL>::glob(l)];
+    for (int l = 0; l < NO; ++l) {
+      wo[l] = A->w_op[Enc<MODEL>::glob(l)];
+      capl[l] = I.op_cap[Enc<MODEL>::glob(l)];
+    }
+    wk[0] = A->w_k[0];
+    wk[1] = A->w_k[1];
+    wk[2] = A->w_k[2];
+    weights_set(W, wo, wk);
   }
-  W.k[0] = A->w_k[0];
-  W.k[1] = A->w_k[1];
-  W.k[2] = A->w_k[2];
-  weights_sum(W);
   uint32_t en_local = 0;
 #pragma unroll
   for (int l = 0; l < NO; ++l) en_local |= ((I.enabled >> Enc<MODEL>::glob(l)) & 1u) << l;
@@ -1016,7 +1048,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   const bool packed = 96ull * (uint64_t)cpl * (uint64_t)I.U * (uint64_t)mine < 65536ull;
   // a member's window counts in bytes while it evolves (PackedStats)
   const bool bytec = 3ull * (uint64_t)cpl * (uint64_t)I.U <= 255ull;
-  PackedStats ps{0ull, 0ull, 0u, 0u};
+  PackedStats ps{0u, 0u, 0u, 0u};
   auto count = [&](uint32_t rec) {
     if (bytec) packed_add(ps, rec);
     else stats_add(st, rec);
@@ -1320,17 +1352,19 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     const long long elite = ld_relaxed64((const long long *)&S->elite[slot]);
     ++wi;
 
-    aos_update_lanes<Enc<MODEL>>(W.op, W.k, total, en_local, capl, I.ema_a, I.w_floor, I.w_cap);
+    uint32_t wo[NO], wk[3];
+    weights_get(W, wo, wk);
+    aos_update_lanes<Enc<MODEL>>(wo, wk, total, en_local, capl, I.ema_a, I.w_floor, I.w_cap);
     if (elite < elite_prev) stag = 0;
     else ++stag;
     elite_prev = elite;
     if (I.stag_limit > 0 && stag >= I.stag_limit) {
-      W.k[0] = 52429u;
-      W.k[1] = 9830u;
-      W.k[2] = 3277u;
+      wk[0] = 52429u;
+      wk[1] = 9830u;
+      wk[2] = 3277u;
       stag = 0;
     }
-    weights_sum(W);
+    weights_set(W, wo, wk);
     stats_zero(st);
 
     if (inject) {
@@ -1434,10 +1468,13 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     O->g = I.g_end;
     for (int i = 0; i < kNops; ++i) O->w_op[i] = 0;
 #pragma unroll
-    for (int l = 0; l < NO; ++l) O->w_op[Enc<MODEL>::glob(l)] = W.op[l];
-    O->w_k[0] = W.k[0];
-    O->w_k[1] = W.k[1];
-    O->w_k[2] = W.k[2];
+    uint32_t wo[NO], wk[3];
+    weights_get(W, wo, wk);
+#pragma unroll
+    for (int l = 0; l < NO; ++l) O->w_op[Enc<MODEL>::glob(l)] = wo[l];
+    O->w_k[0] = wk[0];
+    O->w_k[1] = wk[1];
+    O->w_k[2] = wk[2];
     O->stag = stag;
     O->elite_prev = elite_prev;
   }
@@ -1471,6 +1508,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.svc = I.vec3;
   X.node = I.node;
   X.cv32 = I.cv32 != 0;
+  X.t3 = ((I.enabled >> THREE_OPT) & 1u) != 0;
   X.lam1 = I.lam1;
   if (!staged) return X;
   auto copy = [&](const void *src, int64_t bytes, int64_t off) {
