@@ -658,8 +658,8 @@ OPS_QAP_K = 17            # QAP, per k of the O(n) swap delta: 9 loads, 2 multip
 # the tsp442 workload, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass; profiles/evolve_tsp442_g200000_dram.md),
 # valid only for the kernel sources it was taken on.
-TRAFFIC_BYTES = 1.31e6 + 13.82e3
-TRAFFIC_SOURCES = "4dcadff11e6fea0f"
+TRAFFIC_BYTES = 1.13e6 + 67.58e3
+TRAFFIC_SOURCES = "532058c0b7387fe5"
 
 
 def kernel_sources_hash() -> str:
