@@ -169,8 +169,15 @@ def cpu_baseline(inst, cfg, desc, budget_s: float):
     O.solve(inst, p, 1, gens)
     dt = time.perf_counter() - t0
     evals = cfg["P"] * cfg["C"] * gens
+    # one host thread, on a quarter of the sample (same generations from 0)
+    g1 = max(2, gens // 4)
+    t0 = time.perf_counter()
+    O.solve(inst, p, 1, g1, threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": evals / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
-            "sample": "first %d generations of the %s solve (%.1f s)" % (gens, desc, dt)}
+            "sample": "first %d generations of the %s solve (%.1f s)" % (gens, desc, dt),
+            "single_thread": {"value": cfg["P"] * cfg["C"] * g1 / dt1, "cores": 1,
+                              "sample": "first %d generations (%.1f s)" % (g1, dt1)}}
 
 
 # ------------------------------------------------------------------- ours
@@ -323,7 +330,11 @@ def main():
                                       "autotuner (%d trial shapes)" % len(
                                           tuner.solve_shapes(params))},
                            "best_cost": int(best_cost), "start_best_cost": int(start_cost),
-                           "gens_per_s": cfg["G"] / (total_ms / args.steps / 1000.0)},
+                           "gens_per_s": cfg["G"] / (total_ms / args.steps / 1000.0),
+                           # operator applications: each evaluation applies k
+                           # operators, E[k] from the run's last K counts
+                           "operator_applications_per_s":
+                               value * roof["ops_per_eval_steps"]},
                 "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
@@ -713,7 +724,8 @@ def roofline(evals_launch, kernel_ms, prob, clocks):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": traffic,
             "kernel": "evolve_kernel<%s>" % ("QAP" if qap else "TSP,int16"), "kernel_ms": kernel_ms,
-            "ops_per_eval": ops_eval, "peak_basis": "%d SMs x 128 lanes x %.0f MHz" % (sms, fmax),
+            "ops_per_eval": ops_eval, "ops_per_eval_steps": ek,
+            "peak_basis": "%d SMs x 128 lanes x %.0f MHz" % (sms, fmax),
             "gather": {"achieved": g_achieved / 1e9, "peak": g_peak / 1e9, "unit": "G gathers/s",
                        "frac": g_achieved / g_peak, "gathers_per_eval": gathers_eval,
                        "executed_per_eval": executed,
