@@ -89,7 +89,7 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
 int64_t instance_data_bytes(const KInst &h) {
   switch (h.model) {
     case TSP: return align16((int64_t)h.n * (h.n + 1) / 2 * (h.tri16 ? 2 : 4));
-    case QAP: return 2 * align16((int64_t)h.n * (h.n | 1) * 4);
+    case QAP: return 4 * align16((int64_t)h.n * (h.n | 1) * 4);  // F, D and their transposes
     case KNAPSACK: return 2 * align16((int64_t)h.n * 4);
     case GAP: return 2 * align16((int64_t)h.m * h.n * 4) + align16((int64_t)h.m * 4);
     case CVRPTW: {
@@ -114,6 +114,7 @@ struct View {
   const void *tri;
   int n2m1;
   const int32_t *F, *D;        // QAP (row stride qs)
+  const int32_t *FT, *DT;      // QAP transposes when staged (else null)
   int qs;
   const int32_t *w, *v;        // knapsack
   const int32_t *gc, *gr, *gcap;  // GAP
@@ -307,12 +308,25 @@ __device__ __forceinline__ long long qap_step_t(const View &X, const PermEl *sol
   const int32_t *Fr = F + (size_t)r * qs, *Fs = F + (size_t)s * qs;
   const int32_t *Dr = D + (size_t)pr * qs, *Ds = D + (size_t)ps * qs;
   Q acc = 0;
-  for (int k = 0; k < n; ++k) {
-    const int pk = vlook(sol, k, p0, p1, np);
-    const Q t1 = ((Q)Fr[k] - (Q)Fs[k]) * ((Q)Ds[pk] - (Q)Dr[pk]);
-    const int32_t *Fk = F + (size_t)k * qs, *Dk = D + (size_t)pk * qs;
-    const Q t2 = ((Q)Fk[r] - (Q)Fk[s]) * ((Q)Dk[ps] - (Q)Dk[pr]);
-    acc += (k != r && k != s) ? t1 + t2 : (Q)0;
+  if (X.FT) {
+    // F[k][r] = FT[r][k], D[pk][ps] = DT[ps][pk]: every read is a row read,
+    // lanes on different rows of an odd stride hit different banks
+    const int32_t *FTr = X.FT + (size_t)r * qs, *FTs = X.FT + (size_t)s * qs;
+    const int32_t *DTr = X.DT + (size_t)pr * qs, *DTs = X.DT + (size_t)ps * qs;
+    for (int k = 0; k < n; ++k) {
+      const int pk = vlook(sol, k, p0, p1, np);
+      const Q t1 = ((Q)Fr[k] - (Q)Fs[k]) * ((Q)Ds[pk] - (Q)Dr[pk]);
+      const Q t2 = ((Q)FTr[k] - (Q)FTs[k]) * ((Q)DTs[pk] - (Q)DTr[pk]);
+      acc += (k != r && k != s) ? t1 + t2 : (Q)0;
+    }
+  } else {
+    for (int k = 0; k < n; ++k) {
+      const int pk = vlook(sol, k, p0, p1, np);
+      const Q t1 = ((Q)Fr[k] - (Q)Fs[k]) * ((Q)Ds[pk] - (Q)Dr[pk]);
+      const int32_t *Fk = F + (size_t)k * qs, *Dk = D + (size_t)pk * qs;
+      const Q t2 = ((Q)Fk[r] - (Q)Fk[s]) * ((Q)Dk[ps] - (Q)Dk[pr]);
+      acc += (k != r && k != s) ? t1 + t2 : (Q)0;
+    }
   }
   acc += ((Q)Fr[r] - (Q)Fs[s]) * ((Q)Ds[ps] - (Q)Dr[pr]);
   acc += ((Q)Fr[s] - (Q)Fs[r]) * ((Q)Ds[pr] - (Q)Dr[ps]);
@@ -1495,6 +1509,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.tri = I.tri;
   X.F = I.mat0;
   X.D = I.mat1;
+  X.FT = X.DT = nullptr;
   X.qs = I.n;
   X.w = I.vec0;
   X.v = I.vec1;
@@ -1525,16 +1540,23 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
     case QAP: {
       // rows re-strided to an odd length so that lanes reading different rows
       // at the same column hit different banks
+      // (and transposed, so that the column reads of the delta are row reads)
       const int n = I.n, qs = I.n | 1;
       const int64_t b = align16((int64_t)n * qs * 4);
       int32_t *Fs = (int32_t *)smem, *Ds = (int32_t *)(smem + b);
+      int32_t *FTs = (int32_t *)(smem + 2 * b), *DTs = (int32_t *)(smem + 3 * b);
       for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
         const int i = (int)(t / n), j = (int)(t % n);
-        Fs[(int64_t)i * qs + j] = I.mat0[t];
-        Ds[(int64_t)i * qs + j] = I.mat1[t];
+        const int32_t f = I.mat0[t], d = I.mat1[t];
+        Fs[(int64_t)i * qs + j] = f;
+        Ds[(int64_t)i * qs + j] = d;
+        FTs[(int64_t)j * qs + i] = f;
+        DTs[(int64_t)j * qs + i] = d;
       }
       X.F = Fs;
       X.D = Ds;
+      X.FT = FTs;
+      X.DT = DTs;
       X.qs = qs;
       break;
     }
