@@ -38,7 +38,9 @@ class OrcParams(ctypes.Structure):
                 ("U", ctypes.c_uint32), ("ema_a", ctypes.c_uint32), ("w_floor", ctypes.c_uint32),
                 ("w_cap", ctypes.c_uint32), ("op_cap", ctypes.c_uint32 * NOPS),
                 ("stag_limit", ctypes.c_uint32), ("elite_period", ctypes.c_uint32),
-                ("init_oversample", ctypes.c_uint32), ("init_heuristic", ctypes.c_uint32)]
+                ("init_oversample", ctypes.c_uint32), ("init_heuristic", ctypes.c_uint32),
+                ("islands", ctypes.c_uint32), ("migrate_period", ctypes.c_uint32),
+                ("migrate_strategy", ctypes.c_uint32), ("migrate_n", ctypes.c_uint32)]
 
 
 class OrcState(ctypes.Structure):
@@ -91,6 +93,8 @@ def lib() -> ctypes.CDLL:
             L.orc_init.argtypes = [ctypes.POINTER(OrcInstance), ctypes.POINTER(OrcParams), u64,
                                    ctypes.POINTER(OrcState)]
             L.orc_init.restype = i32
+            L.orc_migrate.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(OrcState)]
+            L.orc_migrate.restype = i32
             L.orc_heuristic_perms.argtypes = [ctypes.POINTER(OrcInstance), _i32p]
             L.orc_heuristic_perms.restype = i32
             L.orc_run.argtypes = [ctypes.POINTER(OrcInstance), ctypes.POINTER(OrcParams), u64,
@@ -144,7 +148,8 @@ class Instance:
 
 
 PARAM_KEYS = ("P", "C", "op_mask", "w_op", "w_k", "T0", "alpha", "U", "ema_a", "w_floor",
-              "w_cap", "op_cap", "stag_limit", "elite_period", "init_oversample", "init_heuristic")
+              "w_cap", "op_cap", "stag_limit", "elite_period", "init_oversample", "init_heuristic",
+              "islands", "migrate_period", "migrate_strategy", "migrate_n")
 
 
 def default_params(inst: dict) -> dict:
@@ -186,6 +191,22 @@ def new_state(P: int, length: int) -> tuple[OrcState, dict]:
     st.cost = arrays["cost"].ctypes.data_as(_i64p)
     st.best_cost = arrays["best_cost"].ctypes.data_as(_i64p)
     return st, arrays
+
+
+def migrate(params: dict, state: dict) -> dict:
+    """One migration step (islands) applied to a copy of a state dict with
+    fields cur, best_sol, cost, best_cost, g (the rest is carried over)."""
+    P, length = int(state["cur"].shape[0]), int(state["cur"].shape[1])
+    st, arrays = new_state(P, length)
+    for k in ("cur", "best_sol", "cost", "best_cost"):
+        arrays[k][...] = state[k]
+    st.g = int(state["g"])
+    p = make_params(params)
+    if lib().orc_migrate(ctypes.byref(p), ctypes.byref(st)) != 0:
+        raise ValueError("orc_migrate failed")
+    out = dict(state)
+    out.update({k: v.copy() for k, v in arrays.items()})
+    return out
 
 
 def state_dict(st: OrcState, arrays: dict) -> dict:

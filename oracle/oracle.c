@@ -426,6 +426,10 @@ void orc_params_default(const orc_instance *in, orc_params *pr) {
   pr->elite_period = 0;
   pr->init_oversample = 1;
   pr->init_heuristic = 0;
+  pr->islands = 1;
+  pr->migrate_period = 0;
+  pr->migrate_strategy = 0;
+  pr->migrate_n = 1;
 }
 
 /* ------------------------------------------------------------- init [R15] */
@@ -639,6 +643,91 @@ static void aos_update(const orc_instance *in, const orc_params *pr, orc_state *
 
 /* elite injection (Sec. 3.4.3): the worst current solution (highest cost,
  * ties to the lowest index) becomes a copy of the instance elite [R13] */
+/* [R27] islands and migration (Sec. 3.4.3): island i holds members
+ * [i*P/I, (i+1)*P/I).  A migrant replaces a member's current solution by a
+ * source member's best solution (the rule of elite injection); sources and
+ * targets are chosen on the state before any replacement.
+ *   ring:  the best member of island i-1 (mod I) -> the worst of island i;
+ *   top-N: the N best members of the population -> the N worst of every
+ *          island, j-th best to j-th worst;
+ *   hybrid: ring at odd-numbered migrations (g / period odd), top-N at even.
+ * best = lowest (best cost, index); worst = highest (cost, -index). */
+static void replace_member(orc_state *st, int32_t target, const int32_t *sol, int64_t cost) {
+  const int32_t len = st->len;
+  memcpy(st->cur + (int64_t)target * len, sol, sizeof(int32_t) * (size_t)len);
+  st->cost[target] = cost;
+  if (cost < st->best_cost[target]) {
+    st->best_cost[target] = cost;
+    memcpy(st->best_sol + (int64_t)target * len, sol, sizeof(int32_t) * (size_t)len);
+  }
+}
+
+/* the k-th worst member (0 = worst) of [lo, hi) by (cost desc, index asc) */
+static int32_t kth_worst(const int64_t *cost, int32_t lo, int32_t hi, int32_t k) {
+  int32_t *taken = (int32_t *)calloc((size_t)(hi - lo), sizeof(int32_t)), w = -1;
+  for (int32_t r = 0; r <= k; r++) {
+    w = -1;
+    for (int32_t q = lo; q < hi; q++)
+      if (!taken[q - lo] && (w < 0 || cost[q] > cost[w])) w = q;
+    taken[w - lo] = 1;
+  }
+  free(taken);
+  return w;
+}
+
+static void migrate(const orc_params *pr, orc_state *st) {
+  const int32_t P = st->P, I = (int32_t)pr->islands, S = P / I, len = st->len;
+  const int64_t event = st->g / pr->migrate_period;
+  const int32_t ring = pr->migrate_strategy == 0 || (pr->migrate_strategy == 2 && (event & 1));
+  /* snapshot of the state the sources are taken from */
+  int32_t *bsol = (int32_t *)malloc(sizeof(int32_t) * (size_t)P * len);
+  int64_t *bcost = (int64_t *)malloc(sizeof(int64_t) * (size_t)P);
+  int64_t *ccost = (int64_t *)malloc(sizeof(int64_t) * (size_t)P);
+  memcpy(bsol, st->best_sol, sizeof(int32_t) * (size_t)P * len);
+  memcpy(bcost, st->best_cost, sizeof(int64_t) * (size_t)P);
+  memcpy(ccost, st->cost, sizeof(int64_t) * (size_t)P);
+  if (ring) {
+    for (int32_t i = 0; i < I; i++) {
+      const int32_t from = (i + I - 1) % I;
+      int32_t b = from * S;
+      for (int32_t q = from * S; q < (from + 1) * S; q++)
+        if (bcost[q] < bcost[b]) b = q;
+      const int32_t t = kth_worst(ccost, i * S, (i + 1) * S, 0);
+      replace_member(st, t, bsol + (int64_t)b * len, bcost[b]);
+    }
+  } else {
+    const int32_t N = (int32_t)pr->migrate_n;
+    int32_t *src = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t *taken = (int32_t *)calloc((size_t)P, sizeof(int32_t));
+    for (int32_t j = 0; j < N; j++) {   /* the N best, by (best cost, index) */
+      int32_t b = -1;
+      for (int32_t q = 0; q < P; q++)
+        if (!taken[q] && (b < 0 || bcost[q] < bcost[b])) b = q;
+      taken[b] = 1;
+      src[j] = b;
+    }
+    for (int32_t i = 0; i < I; i++)
+      for (int32_t j = 0; j < N; j++) {
+        const int32_t t = kth_worst(ccost, i * S, (i + 1) * S, j);
+        replace_member(st, t, bsol + (int64_t)src[j] * len, bcost[src[j]]);
+      }
+    free(src);
+    free(taken);
+  }
+  free(bsol);
+  free(bcost);
+  free(ccost);
+}
+
+int32_t orc_migrate(const orc_params *pr, orc_state *st) {
+  if (pr->islands < 2 || pr->migrate_period < 1 || (uint32_t)st->P % pr->islands != 0 ||
+      pr->migrate_strategy > 2 ||
+      (pr->migrate_strategy != 0 && (pr->migrate_n < 1 || pr->migrate_n > (uint32_t)st->P / pr->islands)))
+    return -1;
+  migrate(pr, st);
+  return 0;
+}
+
 static void inject(orc_state *st) {
   int32_t e = orc_elite(st), wv = 0, len = st->len;
   for (int32_t p = 1; p < st->P; p++)
@@ -657,6 +746,10 @@ int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc
                 int64_t generations, int32_t threads) {
   int32_t P = st->P, len = st->len, C = pr->C;
   if (C < 1 || pr->U < 1) return -1;
+  if (pr->islands > 1 && pr->migrate_period > 0 &&
+      ((uint32_t)P % pr->islands != 0 || pr->migrate_strategy > 2 ||
+       (pr->migrate_strategy != 0 && (pr->migrate_n < 1 || pr->migrate_n > (uint32_t)P / pr->islands))))
+    return -1;
   uint32_t *cnt = (uint32_t *)calloc((size_t)P * 22, sizeof(uint32_t));
   int32_t nthreads = orc_threads(threads);
   for (int64_t it = 0; it < generations; it++) {
@@ -684,6 +777,7 @@ int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc
     st->T = orc_cool(st->T, pr->alpha);
     st->g++;
     if (st->g % pr->U == 0) aos_update(in, pr, st);
+    if (pr->islands > 1 && pr->migrate_period > 0 && st->g % pr->migrate_period == 0) migrate(pr, st);
     if (pr->elite_period > 0 && st->g % pr->elite_period == 0) inject(st);
   }
   free(cnt);

@@ -53,6 +53,10 @@ typedef struct {
   uint32_t U, ema_a, w_floor, w_cap, op_cap[ORC_NOPS], stag_limit, elite_period;
   uint32_t init_oversample;        /* K of the oversampled start (Sec. 3.4.1); 0 or 1 = off */
   uint32_t init_heuristic;         /* 1 = add the row/column-sum permutations (Sec. 3.4.2) */
+  uint32_t islands;                /* islands (Sec. 3.4.3); 0 or 1 = one population */
+  uint32_t migrate_period;         /* migration after every such generation; 0 = off */
+  uint32_t migrate_strategy;       /* 0 ring, 1 global top-N, 2 hybrid (alternating) */
+  uint32_t migrate_n;              /* N of the top-N strategy */
 } orc_params;
 
 /* Complete search state.  Arrays are caller-owned: cur/best_sol P*len,
@@ -98,6 +102,10 @@ int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc
                 int64_t generations, int32_t threads);
 /* index of the instance elite (lowest best cost, ties to the lowest index) */
 int32_t orc_elite(const orc_state *st);
+/* one migration between islands on the state as it stands (the step the
+ * search takes after every migrate_period-th generation); exported for the
+ * oracle's own pins.  Returns -1 for invalid island parameters. */
+int32_t orc_migrate(const orc_params *pr, orc_state *st);
 /* the attribute-agnostic start permutations of an instance (TSP: D; QAP: F,
  * then D): per matrix the orders of ascending and descending row sums, then
  * ascending and descending column sums.  out: 8 * n entries; returns their
