@@ -199,6 +199,9 @@ def main():
                     help="single solve: K of the oversampled start (1 = plain start)")
     ap.add_argument("--init-heuristic", type=int, default=0,
                     help="single solve: 1 = add the row/column-sum start permutations")
+    ap.add_argument("--islands", default="",
+                    help="single solve: islands 'I,period,strategy,N' (strategy 0 ring, "
+                         "1 top-N, 2 hybrid)")
     ap.add_argument("--launch", default="",
                     help="single solve: fixed launch shape 'warps,wpm,staging,gens_in_flight' "
                          "instead of the autotuner (profiling runs)")
@@ -245,6 +248,11 @@ def main():
         cfg["init_oversample"] = args.init_oversample
         cfg["init_heuristic"] = args.init_heuristic
         desc += " start=K%d%s" % (args.init_oversample, "+heuristic" if args.init_heuristic else "")
+    if args.islands:
+        isl, per, strat, nmig = (int(x) for x in args.islands.split(","))
+        cfg.update(islands=isl, migrate_period=per, migrate_strategy=strat, migrate_n=nmig)
+        desc += " islands=%d period=%d %s" % (isl, per, ["ring", "top-%d" % nmig,
+                                                          "hybrid-%d" % nmig][strat])
     prob = cgo.Problem(inst)
     params = lib_params(prob, cfg)
     from paper_2603_19163_gb300.autotune import Autotuner
@@ -669,8 +677,8 @@ OPS_QAP_K = 17            # QAP, per k of the O(n) swap delta: 9 loads, 2 multip
 # the tsp442 workload, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass; profiles/evolve_tsp442_g200000_dram.md),
 # valid only for the kernel sources it was taken on.
-TRAFFIC_BYTES = 1.13e6 + 67.58e3
-TRAFFIC_SOURCES = "532058c0b7387fe5"
+TRAFFIC_BYTES = 1.19e6 + 71.94e3
+TRAFFIC_SOURCES = "afea288978d777e9"
 
 
 def kernel_sources_hash() -> str:

@@ -124,6 +124,14 @@ typedef struct {
                                   K <= 64 and K*P <= 16384 */
   uint32_t init_heuristic;     /* 1: the row/column-sum permutations of each square
                                   data matrix (Sec. 3.4.2; TSP, QAP) join the pool */
+  uint32_t islands;            /* I islands of P/I consecutive members (Sec. 3.4.3);
+                                  0 or 1 = one population; I divides P */
+  uint32_t migrate_period;     /* migration after every such generation (a multiple of
+                                  aos_interval on the GPU); 0 = off */
+  uint32_t migrate_strategy;   /* 0 ring: each island's best to the next island's worst;
+                                  1 top-N: the population's N best to every island's N
+                                  worst; 2 hybrid: ring and top-N alternate */
+  uint32_t migrate_n;          /* N of top-N, 1 .. P/I */
 } cgo_params;
 
 /* Full search state (checkpoint).  Scalars are filled/read by value; the

@@ -49,7 +49,9 @@ class cgo_params(ctypes.Structure):
                 ("ema_alpha_q16", ctypes.c_uint32), ("w_floor_q16", ctypes.c_uint32),
                 ("w_cap_q16", ctypes.c_uint32), ("op_cap_q16", ctypes.c_uint32 * NOPS),
                 ("stag_limit", ctypes.c_uint32), ("elite_period", ctypes.c_uint32),
-                ("init_oversample", ctypes.c_uint32), ("init_heuristic", ctypes.c_uint32)]
+                ("init_oversample", ctypes.c_uint32), ("init_heuristic", ctypes.c_uint32),
+                ("islands", ctypes.c_uint32), ("migrate_period", ctypes.c_uint32),
+                ("migrate_strategy", ctypes.c_uint32), ("migrate_n", ctypes.c_uint32)]
 
 
 class cgo_state(ctypes.Structure):
@@ -170,7 +172,9 @@ PARAM_MAP = [("P", "population"), ("C", "candidates"), ("G", "generations"),
              ("ema_a", "ema_alpha_q16"), ("w_floor", "w_floor_q16"), ("w_cap", "w_cap_q16"),
              ("op_cap", "op_cap_q16"), ("stag_limit", "stag_limit"),
              ("elite_period", "elite_period"), ("init_oversample", "init_oversample"),
-             ("init_heuristic", "init_heuristic")]
+             ("init_heuristic", "init_heuristic"), ("islands", "islands"),
+             ("migrate_period", "migrate_period"), ("migrate_strategy", "migrate_strategy"),
+             ("migrate_n", "migrate_n")]
 
 
 def params_struct(d: dict) -> cgo_params:

@@ -278,6 +278,16 @@ cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *
   if ((uint64_t)(q->init_oversample > 1 ? q->init_oversample : 1) * q->population > 16384u)
     return fail(CGO_ERR_INVALID, "init_oversample * population must be <= 16384");
   if (q->init_heuristic > 1) return fail(CGO_ERR_INVALID, "init_heuristic must be 0 or 1");
+  if (q->islands > 1 && q->migrate_period > 0) {
+    if ((uint32_t)q->population % q->islands != 0)
+      return fail(CGO_ERR_INVALID, "islands must divide the population");
+    if (q->migrate_period % q->aos_interval != 0)
+      return fail(CGO_ERR_UNSUPPORTED, "migrate_period must be a multiple of aos_interval on the GPU");
+    if (q->migrate_strategy > 2) return fail(CGO_ERR_INVALID, "migrate_strategy must be 0, 1 or 2");
+    if (q->migrate_strategy != 0 &&
+        (q->migrate_n < 1 || q->migrate_n > (uint32_t)q->population / q->islands))
+      return fail(CGO_ERR_INVALID, "migrate_n must be in [1, population / islands]");
+  }
   *enabled = en;
   return CGO_OK;
 }
@@ -324,6 +334,11 @@ KInst base_kinst(const cgo_problem *p) {
   h.cost = p->d_cost;
   h.best = p->d_best;
   h.sync = p->d_sync;
+  const bool mig = q.islands > 1 && q.migrate_period > 0;
+  h.islands = mig ? (int32_t)q.islands : 1;
+  h.mperiod = mig ? q.migrate_period : 0u;
+  h.mstrat = (int32_t)q.migrate_strategy;
+  h.mN = q.migrate_n;
   h.K_over = q.init_oversample > 1 ? (int32_t)q.init_oversample : 1;
   h.n_heur = q.init_heuristic ? p->n_heur : 0;
   h.heur = p->d_heur;
@@ -743,6 +758,10 @@ cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
   q->elite_period = 0;
   q->init_oversample = 1;
   q->init_heuristic = 0;
+  q->islands = 1;
+  q->migrate_period = 0;
+  q->migrate_strategy = 0;
+  q->migrate_n = 1;
   return CGO_OK;
 }
 

@@ -80,6 +80,9 @@ struct KInst {
   // oversampled / heuristic start (pool of K*P random starts + n_heur
   // permutations, the P cheapest become the members)
   int32_t K_over, n_heur;
+  // islands and migration
+  int32_t islands, mstrat;
+  uint32_t mperiod, mN;
   const int32_t *heur;        // n_heur x n
   int32_t *pool_sol;          // (K*P + n_heur) x len
   int64_t *pool_cost;

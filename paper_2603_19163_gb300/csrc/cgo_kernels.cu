@@ -1296,6 +1296,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
 
     // ------------------------------------------------ AOS window end
     const bool inject = I.E > 0 && (g % (uint32_t)I.E) == 0;
+    const bool migr = I.islands > 1 && (g % I.mperiod) == 0;
     uint32_t tot[NO * 2 + 6];
     if (packed) {
       // a lane counts at most 3 * cpl * U * mine uses per window, so the warp
@@ -1348,7 +1349,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     }
     if (G.gw == 0 && lane < kStats && my) atomicAdd(&S->acc[slot][lane], my);
     if (G.gw == 0 && lane == 0) atomicMin((long long *)&S->elite[slot], minbest);
-    if (inject && G.tig == 0) {
+    if ((inject || migr) && G.tig == 0) {
       for (int e = 0; e < mine; ++e) {
         const int ls = G.grp + e * ngroups;
         I.cost[p0 + ls] = scal[ls].cost;
@@ -1380,6 +1381,88 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     }
     weights_set(W, wo, wk);
     stats_zero(st);
+
+    if (migr) {
+      // [R27] islands of S consecutive members (Sec. 3.4.3).  Phase 1: every
+      // target takes its source's best solution as its current one, in shared
+      // memory only, so that all sources are read as they stood at the window
+      // end.  Phase 2, after a barrier: bests a migrant improved go to global
+      // memory and every member's cost and best are published again.
+      const int S_ = P / I.islands;
+      const bool ring = I.mstrat == 0 || (I.mstrat == 2 && ((g / I.mperiod) & 1u));
+      const int need = ring ? 1 : (int)I.mN;
+      const long long *gc = (const long long *)I.cost, *gb = (const long long *)I.best;
+      for (int e = 0; e < mine; ++e) {
+        const int ls = G.grp + e * ngroups, p = p0 + ls;
+        const int isl = p / S_, lo = isl * S_;
+        // the member's rank in its island, worst first: (cost desc, index asc)
+        const long long cp = ld_relaxed64(gc + p);
+        int r = 0;
+        for (int q = lo + lane; q < lo + S_; q += 32) {
+          const long long cq = ld_relaxed64(gc + q);
+          r += (cq > cp || (cq == cp && q < p)) ? 1 : 0;
+        }
+        r = __reduce_add_sync(kFull, r);
+        if (r >= need) continue;
+        // its source: ring, the best of the previous island; top-N, the r-th
+        // best of the population by (best, index), found by r + 1 successor scans
+        long long kb = LLONG_MIN;
+        int ki = -1;
+        const int qlo = ring ? ((isl + I.islands - 1) % I.islands) * S_ : 0;
+        const int qhi = ring ? qlo + S_ : P;
+        for (int j = 0; j <= (ring ? 0 : r); ++j) {
+          long long bb = LLONG_MAX;
+          int be = INT_MAX;
+          for (int q = qlo + lane; q < qhi; q += 32) {
+            const long long b = ld_relaxed64(gb + q);
+            if ((b > kb || (b == kb && q > ki)) && b < bb) {
+              bb = b;
+              be = q;
+            }
+          }
+          warp_argmin(bb, be);
+          kb = bb;
+          ki = be;
+        }
+        El *sol = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+        const int32_t *src = I.bestsol + (int64_t)ki * len;
+        for (int i = G.tig; i < len; i += G.nthr) sol[i] = (El)__ldcg(src + i);
+        G.sync();
+        SolScal sc = scal[ls];
+        sc.cost = kb;
+        sc.best = min(sc.best, kb);
+        G.sync();
+        if (G.tig == 0) scal[ls] = sc;
+        G.sync();
+        aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
+        if constexpr (MODEL == CVRPTW)
+          cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len), G);
+      }
+      if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
+        return;
+      ++nb;
+      for (int e = 0; e < mine; ++e) {
+        const int ls = G.grp + e * ngroups, p = p0 + ls;
+        if (scal[ls].best < ld_relaxed64(gb + p)) {
+          const El *sol = (const El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+          int32_t *dst = I.bestsol + (int64_t)p * len;
+          for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
+        }
+      }
+      G.sync();
+      if (G.tig == 0) {
+        for (int e = 0; e < mine; ++e) {
+          const int ls = G.grp + e * ngroups;
+          I.cost[p0 + ls] = scal[ls].cost;
+          I.best[p0 + ls] = scal[ls].best;
+        }
+      }
+      if (inject) {
+        if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
+          return;
+        ++nb;
+      }
+    }
 
     if (inject) {
       // elite = lowest best (lowest index on ties), worst = highest cost

@@ -51,6 +51,13 @@ def mixed_batch():
                   dict(P=6, C=96, G=23, ops=[0, 1, 2, 3, O.THREE_OPT])))
     items.append((dict(I.cvrptw(22, 256, vehicles=5, capacity=100), tag=46),
                   dict(P=5, C=64, G=19, ops=[0, 1, 2, 3, O.THREE_OPT])))
+    # islands and migration (Sec. 3.4.3), members in one CTA
+    items.append((dict(I.tsp_uniform(50, 257), tag=47),
+                  dict(P=12, C=64, G=31, U=5, islands=4, migrate_period=10, migrate_strategy=2,
+                       migrate_n=2, elite_period=15)))
+    items.append((dict(I.gap(30, 258, m=5), tag=48),
+                  dict(P=9, C=48, G=22, U=3, islands=3, migrate_period=6, migrate_strategy=1,
+                       migrate_n=3)))
     return items
 
 

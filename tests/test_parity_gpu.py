@@ -333,6 +333,68 @@ def test_pool_start_init_only_and_limits(cgo):
         assert e.value.status == cgo.ERR_INVALID
 
 
+# ------------------------------------------------------ islands and migration
+ISLAND_CASES = [(I.tsp_uniform(30, 310), None), (I.qap_random(11, 311), [SW]),
+                (I.knapsack(60, 312), None), (I.gap(25, 313, m=4), None),
+                (I.cvrptw(14, 314, vehicles=4, capacity=70), None)]
+
+
+@pytest.mark.parametrize("strategy,n", [(0, 1), (1, 1), (1, 3), (2, 2)])
+@pytest.mark.parametrize("ns", [1, 2])
+def test_islands_every_model(cgo, strategy, n, ns):
+    """Sec. 3.4.3: ring, top-N and hybrid migration between 3 islands of 4
+    members every 2 AOS windows, elite injection at every third window (both
+    at generation 30)."""
+    for inst, ops in ISLAND_CASES:
+        over = dict(P=12, C=64, G=37, U=5, islands=3, migrate_period=10, migrate_strategy=strategy,
+                    migrate_n=n, elite_period=15)
+        if ops:
+            over["ops"] = ops
+        p = params_for(inst, **over)
+        _, g, o = run_both(cgo, inst, p, 4, ns=ns)
+        assert_same_state(g, o, "model %d strategy %d n %d ns %d" % (inst["model"], strategy, n, ns))
+
+
+@pytest.mark.parametrize("warps,wpm", [(1, 1), (2, 1), (8, 2), (8, 4)])
+def test_islands_across_ctas(cgo, warps, wpm):
+    """Islands whose members sit in different CTAs (one to eight member groups
+    per CTA), so that migration crosses the cooperative grid barrier."""
+    inst = I.tsp_clustered(60, 315)
+    for strategy, n in ((0, 1), (1, 4), (2, 2)):
+        p = params_for(inst, P=48, C=96, G=61, U=4, islands=6, migrate_period=12,
+                       migrate_strategy=strategy, migrate_n=n, elite_period=8)
+        _, g, o = run_both(cgo, inst, p, 11, warps=warps, wpm=wpm)
+        assert_same_state(g, o, "strategy %d warps %d wpm %d" % (strategy, warps, wpm))
+
+
+def test_islands_degenerate_shapes(cgo):
+    """One member per island (ring: each member takes its predecessor's best)
+    and top-N with N = P/I (every member of every island is replaced)."""
+    inst = I.tsp_uniform(25, 316)
+    for over in (dict(P=5, islands=5, migrate_strategy=0), dict(P=6, islands=2, migrate_strategy=1, migrate_n=3),
+                 dict(P=8, islands=8, migrate_strategy=2, migrate_n=1)):
+        p = params_for(inst, C=40, G=25, U=3, migrate_period=3, **over)
+        _, g, o = run_both(cgo, inst, p, 6)
+        assert_same_state(g, o, str(over))
+
+
+def test_islands_invalid_parameters(cgo):
+    inst = I.tsp_uniform(20, 317)
+    p = params_for(inst, P=12, C=32, G=10, U=5, islands=3, migrate_period=10)
+    prob = cgo.Problem(inst)
+    for bad, status in ((dict(islands=5), cgo.ERR_INVALID), (dict(migrate_period=7), cgo.ERR_UNSUPPORTED),
+                        (dict(migrate_strategy=3), cgo.ERR_INVALID),
+                        (dict(migrate_strategy=1, migrate_n=0), cgo.ERR_INVALID),
+                        (dict(migrate_strategy=1, migrate_n=5), cgo.ERR_INVALID)):
+        with pytest.raises(cgo.CgoError) as e:
+            prob.solve(dict(p, **bad), 1)
+        assert e.value.status == status, bad
+    # islands without a migration period is one population
+    q = dict(p, migrate_period=0)
+    _, g, o = run_both(cgo, inst, q, 2)
+    assert_same_state(g, o, "no migration")
+
+
 # ----------------------------------------------------- state and resume
 @pytest.mark.parametrize("maker", [lambda: I.tsp_uniform(25, 60), lambda: I.knapsack(60, 61),
                                    lambda: I.gap(40, 62, m=6), lambda: I.qap_random(8, 63),

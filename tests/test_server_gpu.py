@@ -41,6 +41,9 @@ def request_mix():
         (dict(I.tsp_clustered(70, 308), tag=9), dict(P=5, C=64, G=31, init_oversample=4,
                                                      init_heuristic=1)),
         (dict(I.gap(25, 309, m=4), tag=10), dict(P=6, C=48, G=22, init_oversample=3)),
+        # islands with ring migration
+        (dict(I.tsp_uniform(40, 310), tag=11), dict(P=8, C=64, G=29, U=4, islands=4,
+                                                    migrate_period=8, migrate_strategy=0)),
     ]
 
 
