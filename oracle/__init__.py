@@ -15,7 +15,8 @@ import numpy as np
 from . import build as _build
 
 NOPS = 8
-SWAP, TWO_OPT, INSERT, OR_OPT, FLIP, PERTURB, THREE_OPT = range(7)
+SWAP, TWO_OPT, INSERT, OR_OPT, FLIP, PERTURB, THREE_OPT, SEGMENT = range(8)
+SEG_FLIP = SEG_RESET = SEGMENT     # slot 7: the binary and the integer segment operator
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -284,6 +285,14 @@ def apply_move(inst: dict, op: int, a: int, b: int, x: int, sol) -> np.ndarray:
     if rc != 0:
         raise ValueError("move not applicable")
     return s
+
+
+def enabled_ops(inst: dict, op_mask: int) -> list:
+    """Which operators of the mask apply to the instance's encoding (0/1 per slot)."""
+    I = Instance(inst)
+    e = np.zeros(NOPS, np.int32)
+    lib().orc_enabled_ops(I.ref, op_mask, e.ctypes.data_as(_i32p))
+    return e.tolist()
 
 
 def aos_level(w, u, v, enabled, cap_i, a, w_floor, w_cap):

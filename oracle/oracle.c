@@ -254,7 +254,8 @@ int32_t orc_valid(const orc_instance *in, const int32_t *sol) {
 }
 
 /* Operators per encoding (Table "operators"): permutation -> swap, reverse
- * (2-opt), insert, or-opt; binary -> flip; integer -> random reset. */
+ * (2-opt), insert, or-opt, 3-opt; binary -> flip, seg_flip; integer ->
+ * random reset, seg_reset. */
 int32_t orc_enabled_ops(const orc_instance *in, uint32_t op_mask, int32_t enabled[ORC_NOPS]) {
   int32_t enc = encoding_of(in->model), len = orc_solution_length(in), count = 0;
   for (int32_t i = 0; i < ORC_NOPS; i++) {
@@ -263,6 +264,7 @@ int32_t orc_enabled_ops(const orc_instance *in, uint32_t op_mask, int32_t enable
     if (enc == 0 && i == ORC_THREE_OPT) ok = 1;                                /* [R26] */
     if (enc == 1 && i == ORC_FLIP) ok = 1;
     if (enc == 2 && i == ORC_PERTURB) ok = 1;
+    if (enc != 0 && i == ORC_SEGMENT) ok = (len >= 2);                         /* [R28] */
     enabled[i] = ok && ((op_mask >> i) & 1u);
     count += enabled[i];
   }
@@ -356,6 +358,22 @@ int32_t orc_apply_move(const orc_instance *in, int32_t op, uint32_t a, uint32_t 
       s[i] = (int32_t)(lb + (((int64_t)s[i] - lb + d) % R));
       return 0;
     }
+    case ORC_SEGMENT: { /* [R28] a segment of L = 2 + (x & 3) elements (at most len) */
+      if (len < 2) return -1;
+      int32_t L = 2 + (int32_t)(x & 3u);
+      if (L > len) L = len;
+      i = (int32_t)orc_pos(a, (uint32_t)(len - L + 1));          /* segment start */
+      if (encoding_of(in->model) == 1) {                          /* seg_flip */
+        for (int32_t q = i; q < i + L; q++) s[q] ^= 1;
+      } else {                                                    /* seg_reset */
+        int32_t lb, ub;
+        int_bounds(in, &lb, &ub);
+        int64_t R = (int64_t)ub - lb + 1;
+        int64_t d = 1 + (int64_t)orc_pos(b, (uint32_t)(R - 1));  /* one offset for all */
+        for (int32_t q = i; q < i + L; q++) s[q] = (int32_t)(lb + (((int64_t)s[q] - lb + d) % R));
+      }
+      return 0;
+    }
   }
   return -1;
 }
@@ -398,7 +416,8 @@ void orc_params_default(const orc_instance *in, orc_params *pr) {
   pr->C = 128;
   pr->op_mask = 0x3Fu;
   /* priors of every applicable operator (Table "weight_preset"); the
-   * normaliser is taken over the default mask (3-opt off by default) */
+   * normaliser is taken over the default mask (3-opt and the segment
+   * operators off by default) */
   int32_t app[ORC_NOPS];
   orc_enabled_ops(in, pr->op_mask, en);
   orc_enabled_ops(in, 0xFFu, app);
@@ -409,6 +428,9 @@ void orc_params_default(const orc_instance *in, orc_params *pr) {
       w = 65536u;
       if (i == ORC_OR_OPT) w = len <= 100 ? 52429u : (len <= 250 ? 45875u : 19661u);
       if (i == ORC_THREE_OPT) w = len <= 100 ? 32768u : (len <= 250 ? 19661u : 3277u);
+      /* [R28] segment-level operators of the binary and integer sets take
+       * the segment-level (or-opt) preset */
+      if (i == ORC_SEGMENT) w = len <= 100 ? 52429u : (len <= 250 ? 45875u : 19661u);
     }
     pr->w_op[i] = w;
     if (en[i]) S += w;

@@ -30,7 +30,9 @@ extern "C" {
 
 enum { ORC_TSP = 0, ORC_QAP = 1, ORC_KNAPSACK = 2, ORC_GAP = 3, ORC_CVRPTW = 4 };
 enum { ORC_SWAP = 0, ORC_TWO_OPT = 1, ORC_INSERT = 2, ORC_OR_OPT = 3,
-       ORC_FLIP = 4, ORC_PERTURB = 5, ORC_THREE_OPT = 6, ORC_NOPS = 8 };
+       ORC_FLIP = 4, ORC_PERTURB = 5, ORC_THREE_OPT = 6,
+       ORC_SEGMENT = 7, /* binary: seg_flip; integer: seg_reset [R28] */
+       ORC_NOPS = 8 };
 
 typedef struct {
   int32_t model;      /* ORC_TSP ... ORC_CVRPTW */

@@ -246,6 +246,52 @@ def test_move_invariants_random():
         assert (t != s).sum() == 1 and t.min() >= 0 and t.max() <= 4
 
 
+def _preimage(q, m):
+    """a 16-bit field a with pos(a, m) = q"""
+    return -(-(q << 16) // m)
+
+
+def test_segment_operators_are_runs_of_the_element_operators():
+    """seg_flip is L flips and seg_reset L random resets with one offset, at
+    the L consecutive positions from i = pos(a, n-L+1), L = min(2 + (x & 3), n);
+    segment starts are (nearly) uniform over the n-L+1 choices."""
+    rng = np.random.default_rng(22)
+    L_ = O.lib()
+    for n in (2, 3, 5, 9, 40):
+        ki = dict(model=2, n=n)
+        gi = dict(model=3, n=n, m=5, mat0=np.zeros((5, n), np.int32),
+                  mat1=np.zeros((5, n), np.int32), vec0=np.zeros(5, np.int32))
+        starts = {}
+        for _ in range(1500 if n == 9 else 200):
+            a, b = (int(v) for v in rng.integers(0, 65536, 2))
+            x = int(rng.integers(0, 2**32))
+            L = min(2 + (x & 3), n)
+            i = L_.orc_pos(a, n - L + 1)
+            s = rng.integers(0, 2, n).astype(np.int32)
+            t = O.apply_move(ki, O.SEGMENT, a, b, x, s)
+            want = s.copy()
+            for q in range(i, i + L):
+                want = O.apply_move(ki, O.FLIP, _preimage(q, n), 0, 0, want)
+            assert (t == want).all() and (t != s).sum() == L
+            s = rng.integers(0, 5, n).astype(np.int32)
+            t = O.apply_move(gi, O.SEGMENT, a, b, x, s)
+            want = s.copy()
+            for q in range(i, i + L):
+                want = O.apply_move(gi, O.PERTURB, _preimage(q, n), b, 0, want)
+            assert (t == want).all()
+            d = (t - s) % 5
+            assert (d[i:i + L] == d[i]).all() and d[i] != 0 and (d[:i] == 0).all() and (d[i + L:] == 0).all()
+            if n == 9:
+                starts[(L, i)] = starts.get((L, i), 0) + 1
+        if n == 9:
+            for L in (2, 3, 4, 5):
+                cnt = [starts.get((L, i), 0) for i in range(n - L + 1)]
+                mean = sum(cnt) / len(cnt)
+                assert min(cnt) > 0.6 * mean and max(cnt) < 1.4 * mean, (L, cnt)
+    # a single element has no segment: the operator is not applicable
+    assert O.enabled_ops(dict(model=2, n=1), 0xFF)[O.SEGMENT] == 0
+
+
 def _exchange_cuts(s, t):
     """All (i, j, k) with t = s[:i] + s[j:k] + s[i:j] + s[k:], i < j < k."""
     m = len(s)

@@ -155,6 +155,24 @@ def test_gap_reaches_bruteforce_optimum(seed):
 
 
 @pytest.mark.parametrize("seed", SEEDS)
+@pytest.mark.parametrize("model", ["knapsack", "gap"])
+def test_segment_operators_alone_reach_bruteforce_optimum(seed, model):
+    """seg_flip (binary) and seg_reset (integer) as the only operator: every
+    assignment stays reachable (a segment of 2 and one of 3 overlapping in
+    all but one element change a single element), so the optimum is found."""
+    if model == "knapsack":
+        inst = I.knapsack(12, 102)
+        opt = bf_knapsack(inst["vec0"].tolist(), inst["vec1"].tolist(), inst["capacity"])
+    else:
+        inst = I.gap(7, 103, m=3)
+        opt = bf_gap(inst["mat0"], inst["mat1"], inst["vec0"], 1 + int(inst["mat0"].max()))
+    p = equal_weights(O.default_params(inst), [O.SEGMENT])
+    p.update(P=8, C=32)
+    st = _run(inst, p, seed, 400)
+    assert st["best_cost"].min() == opt
+
+
+@pytest.mark.parametrize("seed", SEEDS)
 def test_cvrptw_reaches_bruteforce_optimum(seed):
     inst = I.cvrptw(5, 104, vehicles=2, capacity=60, box=60, horizon=300, width=80)
     opt = bf_cvrptw(inst)
@@ -277,6 +295,15 @@ def test_default_priors_by_scale():
         assert p["w_op"][4:] == [0, 0, (tro << 16) // S, 0]
         assert not (p["op_mask"] >> O.THREE_OPT) & 1
         assert p["w_k"] == [52429, 9830, 3277]
+    # the segment operators of the binary and integer sets take the
+    # segment-level (or-opt) preset, off by default: the element operator
+    # alone normalises to 1.0
+    for n, seg in ((60, 52429), (180, 45875), (600, 19661)):
+        for inst in (I.knapsack(n, 11), I.gap(n, 12, m=4)):
+            p = O.default_params(inst)
+            el = O.FLIP if inst["model"] == 2 else O.PERTURB
+            assert p["w_op"][el] == 65536 and p["w_op"][O.SEGMENT] == (seg << 16) // 65536
+            assert not (p["op_mask"] >> O.SEGMENT) & 1
 
 
 def test_init_distributions():
