@@ -72,9 +72,16 @@ typedef enum {
   CGO_OP_OR_OPT = 3,   /* perm: move a block of 2 or 3 elements (needs length >= 4) */
   CGO_OP_FLIP = 4,     /* binary: x_i ^= 1 */
   CGO_OP_PERTURB = 5,  /* integer: x_i <- another value of [lb, ub] */
-  CGO_OP_THREE_OPT = 6 /* perm: exchange the adjacent segments a[i..j-1], a[j..k-1] at three
+  CGO_OP_THREE_OPT = 6, /* perm: exchange the adjacent segments a[i..j-1], a[j..k-1] at three
                           distinct cut points i < j < k of 0..length (segment level,
                           Table "operators"); off in the default mask */
+  /* slot 7 holds the segment-level operator of the binary and of the integer
+     set (Table "operators"): a segment of L = min(2 + (x & 3), length)
+     elements from i = pos(a, length - L + 1); needs length >= 2; off in the
+     default mask */
+  CGO_OP_SEG_FLIP = 7,  /* binary: flip every element of the segment */
+  CGO_OP_SEG_RESET = 7  /* integer: add one offset d = 1 + pos(b, R - 1) to every element of
+                           the segment, modulo the range R (the random reset's rule) */
 } cgo_op;
 
 #define CGO_NOPS 8

@@ -233,8 +233,9 @@ bool valid_solution(const cgo_problem *p, const int32_t *x) {
 
 uint32_t applicable_mask(const cgo_problem *p) {
   const int enc = encoding_of(p->model);
-  if (enc == CGO_ENC_BINARY) return 1u << FLIP;
-  if (enc == CGO_ENC_INTEGER) return 1u << PERTURB;
+  const uint32_t seg = p->len >= 2 ? 1u << SEGMENT : 0u;
+  if (enc == CGO_ENC_BINARY) return (1u << FLIP) | seg;
+  if (enc == CGO_ENC_INTEGER) return (1u << PERTURB) | seg;
   uint32_t m = (1u << SWAP) | (1u << TWO_OPT) | (1u << INSERT) | (1u << THREE_OPT);
   if (p->len >= 4) m |= 1u << OR_OPT;
   return m;
@@ -728,10 +729,12 @@ cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
   q->candidates = 128;
   q->generations = 2000;
   const uint32_t app = applicable_mask(p);
-  const uint32_t en = app & ~(1u << THREE_OPT);  // 3-opt is off by default
+  // 3-opt and the segment operators of the binary / integer sets are off by default
+  const uint32_t en = app & ~((1u << THREE_OPT) | (1u << SEGMENT));
   q->op_mask = en;
   // Table "weight_preset": O(1) operators 1.0; or-opt and 3-opt by scale of
-  // the length; the normaliser is taken over the default mask
+  // the length, seg_flip / seg_reset with or-opt's segment-level preset; the
+  // normaliser is taken over the default mask
   uint64_t S = 0;
   uint32_t w[kNops] = {0};
   for (int i = 0; i < kNops; ++i) {
@@ -739,6 +742,7 @@ cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
     w[i] = 65536u;
     if (i == OR_OPT) w[i] = p->len <= 100 ? 52429u : (p->len <= 250 ? 45875u : 19661u);
     if (i == THREE_OPT) w[i] = p->len <= 100 ? 32768u : (p->len <= 250 ? 19661u : 3277u);
+    if (i == SEGMENT) w[i] = p->len <= 100 ? 52429u : (p->len <= 250 ? 45875u : 19661u);
     if ((en >> i) & 1u) S += w[i];
   }
   for (int i = 0; i < kNops; ++i) {

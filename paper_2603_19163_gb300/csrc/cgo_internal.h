@@ -12,7 +12,8 @@ constexpr int kMaxWarps = 8;    // warps per CTA (kernel launch bound 256 thread
 constexpr int kMaxAgents = 64;  // GAP agents
 
 enum Model { TSP = 0, QAP = 1, KNAPSACK = 2, GAP = 3, CVRPTW = 4 };
-enum Op { SWAP = 0, TWO_OPT = 1, INSERT = 2, OR_OPT = 3, FLIP = 4, PERTURB = 5, THREE_OPT = 6 };
+enum Op { SWAP = 0, TWO_OPT = 1, INSERT = 2, OR_OPT = 3, FLIP = 4, PERTURB = 5, THREE_OPT = 6,
+          SEGMENT = 7 /* seg_flip (binary), seg_reset (integer) */ };
 enum Staging { STAGE_AUTO = 0, STAGE_SMEM = 1, STAGE_GLOBAL = 2 };
 
 // Per-instance search scalars (device memory, double-buffered in/out per launch).

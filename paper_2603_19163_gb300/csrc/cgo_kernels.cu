@@ -122,7 +122,8 @@ struct View {
   const int4 *node;                           // CVRPTW: {ready, due, service, demand}
   long long lam1;
   bool cv32;
-  bool t3;  // 3-opt enabled for this instance
+  bool t3;   // 3-opt enabled for this instance
+  bool seg;  // seg_flip / seg_reset enabled for this instance
 };
 
 template <int NO>
@@ -212,7 +213,8 @@ __device__ __forceinline__ void stats_add(Stats<NO> &s, uint32_t rec) {
 }
 
 // per-encoding operator set: local op l is global op glob(l) (permutations:
-// swap, 2-opt, insertion, or-opt, 3-opt; binary: flip; integer: reset)
+// swap, 2-opt, insertion, or-opt, 3-opt; binary: flip, seg_flip; integer:
+// reset, seg_reset), in the order of the global slots
 struct PermOps {
   static constexpr int NO = 5;
   __host__ __device__ static constexpr int glob(int l) { return l < 4 ? l : (int)THREE_OPT; }
@@ -221,14 +223,21 @@ template <int MODEL>
 struct Enc : PermOps {};
 template <>
 struct Enc<KNAPSACK> {
-  static constexpr int NO = 1;
-  __host__ __device__ static constexpr int glob(int) { return (int)FLIP; }
+  static constexpr int NO = 2;
+  __host__ __device__ static constexpr int glob(int l) { return l == 0 ? (int)FLIP : (int)SEGMENT; }
 };
 template <>
 struct Enc<GAP> {
-  static constexpr int NO = 1;
-  __host__ __device__ static constexpr int glob(int) { return (int)PERTURB; }
+  static constexpr int NO = 2;
+  __host__ __device__ static constexpr int glob(int l) { return l == 0 ? (int)PERTURB : (int)SEGMENT; }
 };
+
+// [R28] elements a step of the binary / integer sets touches: 1 for the
+// element operator, min(2 + (x & 3), n) for the segment operator; the
+// segment starts at pos(a, n - L + 1) (the element operator's pos(a, n))
+__device__ __forceinline__ int seg_len(int op, uint32_t x, int n) {
+  return op == 0 ? 1 : min(2 + (int)(x & 3u), n);
+}
 
 template <int NO>
 struct Weights {
@@ -719,11 +728,12 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
   return d;
 }
 
-// Knapsack: k flips on x (a flip of an index flipped earlier in the same
-// candidate undoes it); delta from the running weight/value sums.
-__device__ long long candidate_knap(const View &X, const ByteEl *x, const Weights<1> &W,
-                                    long long W0, long long V0, uint32_t c, uint32_t p,
-                                    uint32_t g, uint32_t &rec) {
+// Knapsack with the flip alone: k flips on x (a flip of an index flipped
+// earlier in the same candidate undoes it); delta from the running
+// weight/value sums.
+__device__ long long candidate_knap_flip(const View &X, const ByteEl *x, const Weights<2> &W,
+                                         long long W0, long long V0, uint32_t c, uint32_t p,
+                                         uint32_t g, uint32_t &rec) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
   const int k = 1 + wpick(W.ck, W.Wk, R0.w);
   long long Wt = W0, Vt = V0;
@@ -746,11 +756,60 @@ __device__ long long candidate_knap(const View &X, const ByteEl *x, const Weight
   return d;
 }
 
-// GAP: k random resets of a job's agent; loads of touched agents tracked
-// through small override lists.
-__device__ long long candidate_gap(const View &X, const ByteEl *x, const long long *loads,
-                                   const Weights<1> &W, uint32_t c, uint32_t p, uint32_t g,
-                                   uint32_t &rec) {
+// Knapsack with seg_flip enabled: k flips or segment flips on x (an element an
+// earlier step of the same candidate covered is read with that flip applied).
+__device__ long long candidate_knap_seg(const View &X, const ByteEl *x, const Weights<2> &W,
+                                        long long W0, long long V0, uint32_t c, uint32_t p,
+                                        uint32_t g, uint32_t &rec) {
+  const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+  const int k = 1 + wpick(W.ck, W.Wk, R0.w);
+  long long Wt = W0, Vt = V0;
+  int s0 = 0, e0 = 0, s1 = 0, e1 = 0;  // [start, end) of steps 0 and 1
+  int op[3] = {0, 0, 0};
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    if (t < k) {
+      const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
+      op[t] = wpick(W.cop, W.Wop, R.x);
+      const int L = seg_len(op[t], R.z, X.n);
+      const int i = posm(R.y >> 16, (uint32_t)(X.n - L + 1));
+#pragma unroll
+      for (int e = 0; e < 5; ++e) {
+        if (e < L) {
+          const int q = i + e;
+          const int xi = x[q] ^ (int)(t >= 1 && q >= s0 && q < e0) ^ (int)(t >= 2 && q >= s1 && q < e1);
+          const long long wi = X.w[q], vi = X.v[q];
+          Wt += xi ? -wi : wi;
+          Vt += xi ? -vi : vi;
+        }
+      }
+      if (t == 0) {
+        s0 = i;
+        e0 = i + L;
+      } else if (t == 1) {
+        s1 = i;
+        e1 = i + L;
+      }
+    }
+  }
+  const long long d = (-Vt + X.lam0 * overp(Wt - X.cap)) - (-V0 + X.lam0 * overp(W0 - X.cap));
+  rec = stats_record(op[0], k >= 2 ? op[1] : -1, k >= 3 ? op[2] : -1, k, d < 0);
+  return d;
+}
+
+__device__ __forceinline__ long long candidate_knap(const View &X, const ByteEl *x,
+                                                    const Weights<2> &W, long long W0, long long V0,
+                                                    uint32_t c, uint32_t p, uint32_t g,
+                                                    uint32_t &rec) {
+  return X.seg ? candidate_knap_seg(X, x, W, W0, V0, c, p, g, rec)
+               : candidate_knap_flip(X, x, W, W0, V0, c, p, g, rec);
+}
+
+// GAP with the random reset alone: k resets of a job's agent; loads of
+// touched agents tracked through small override lists.
+__device__ long long candidate_gap_reset(const View &X, const ByteEl *x, const long long *loads,
+                                         const Weights<2> &W, uint32_t c, uint32_t p, uint32_t g,
+                                         uint32_t &rec) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
   const int k = 1 + wpick(W.ck, W.Wk, R0.w);
   const int n = X.n, m = X.m;
@@ -791,6 +850,85 @@ __device__ long long candidate_gap(const View &X, const ByteEl *x, const long lo
   }
   rec = stats_record(0, k >= 2 ? 0 : -1, k >= 3 ? 0 : -1, k, d < 0);
   return d;
+}
+
+// GAP with seg_reset enabled: k steps, each a random reset of one job or of a segment of jobs by one
+// offset [R28].  The move is taken as its sequence of single-job
+// reassignments (steps in order, jobs in index order); the delta is the sum
+// of their exact deltas (the costs telescope).  A job's agent before step t
+// is its stored agent plus the offsets of the earlier steps covering it; an
+// agent's load before a reassignment is its stored load plus the changes of
+// the earlier reassignments, found by scanning them.
+struct GapSteps {
+  int s0, s1, s2, l0, l1, l2, d0, d1, d2;  // start, length, offset of each step
+  __device__ __forceinline__ int agent_before(const ByteEl *x, int j, int t, int m) const {
+    int a = x[j] + ((t >= 1 && j >= s0 && j < s0 + l0) ? d0 : 0) +
+            ((t >= 2 && j >= s1 && j < s1 + l1) ? d1 : 0);
+    a -= a >= 2 * m ? 2 * m : 0;
+    return a - (a >= m ? m : 0);
+  }
+  // reassignment u (0 .. l0+l1+l2-1): its step, job and offset
+  __device__ __forceinline__ void at(int u, int &t, int &j, int &d) const {
+    t = (u >= l0) + (u >= l0 + l1);
+    j = t == 0 ? s0 + u : (t == 1 ? s1 + u - l0 : s2 + u - l0 - l1);
+    d = t == 0 ? d0 : (t == 1 ? d1 : d2);
+  }
+};
+
+__device__ long long candidate_gap_seg(const View &X, const ByteEl *x, const long long *loads,
+                                       const Weights<2> &W, uint32_t c, uint32_t p, uint32_t g,
+                                       uint32_t &rec) {
+  const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+  const int k = 1 + wpick(W.ck, W.Wk, R0.w);
+  const int n = X.n, m = X.m;
+  GapSteps S{0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int op[3] = {0, 0, 0};
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    if (t < k) {
+      const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
+      op[t] = wpick(W.cop, W.Wop, R.x);
+      const int L = seg_len(op[t], R.z, n);
+      const int i = posm(R.y >> 16, (uint32_t)(n - L + 1));
+      const int dd = 1 + posm(R.y & 0xFFFFu, (uint32_t)(m - 1));
+      if (t == 0) { S.s0 = i; S.l0 = L; S.d0 = dd; }
+      else if (t == 1) { S.s1 = i; S.l1 = L; S.d1 = dd; }
+      else { S.s2 = i; S.l2 = L; S.d2 = dd; }
+    }
+  }
+  long long d = 0;
+  const int V = S.l0 + S.l1 + S.l2;
+  for (int u = 0; u < V; ++u) {
+    int t, j, dd;
+    S.at(u, t, j, dd);
+    const int ao = S.agent_before(x, j, t, m);
+    const int an = ao + dd - (ao + dd >= m ? m : 0);
+    long long Lo = loads[ao], Ln = loads[an];
+    for (int v = 0; v < u; ++v) {
+      int t2, j2, d2;
+      S.at(v, t2, j2, d2);
+      const int bo = S.agent_before(x, j2, t2, m);
+      const int bn = bo + d2 - (bo + d2 >= m ? m : 0);
+      if (bo == ao) Lo -= X.gr[(size_t)ao * n + j2];
+      else if (bn == ao) Lo += X.gr[(size_t)ao * n + j2];
+      if (bo == an) Ln -= X.gr[(size_t)an * n + j2];
+      else if (bn == an) Ln += X.gr[(size_t)an * n + j2];
+    }
+    const long long ro = X.gr[(size_t)ao * n + j], rn = X.gr[(size_t)an * n + j];
+    const long long co = X.gcap[ao], cn = X.gcap[an];
+    d += (long long)X.gc[(size_t)an * n + j] - X.gc[(size_t)ao * n + j];
+    d += X.lam0 * (overp(Lo - ro - co) - overp(Lo - co) + overp(Ln + rn - cn) - overp(Ln - cn));
+  }
+  rec = stats_record(op[0], k >= 2 ? op[1] : -1, k >= 3 ? op[2] : -1, k, d < 0);
+  return d;
+}
+
+__device__ __forceinline__ long long candidate_gap(const View &X, const ByteEl *x,
+                                                   const long long *loads, const Weights<2> &W,
+                                                   uint32_t c, uint32_t p, uint32_t g,
+                                                   uint32_t &rec) {
+  return X.seg ? candidate_gap_seg(X, x, loads, W, c, p, g, rec)
+               : candidate_gap_reset(X, x, loads, W, c, p, g, rec);
 }
 
 // ------------------------------------------------------------ member group
@@ -836,40 +974,51 @@ __device__ void apply_perm(PermEl *sol, PermEl *scr, const CandMoves &cm, const 
   for (int t = 0; t < cm.k; ++t) perm_materialise(sol, scr, cm.m[t], G);
 }
 
-__device__ void apply_knap(const View &X, ByteEl *x, const Weights<1> &W, uint32_t c,
+__device__ void apply_knap(const View &X, ByteEl *x, const Weights<2> &W, uint32_t c,
                            uint32_t p, uint32_t g, const Group &G, long long &aw, long long &av) {
   uint4 R0;
   const int k = regen_k(X, W, c, p, g, R0);
   for (int t = 0; t < k; ++t) {
     const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
-    const int i = posm(R.y >> 16, (uint32_t)X.n);
-    const int xi = x[i];
+    const int L = seg_len(wpick(W.cop, W.Wop, R.x), R.z, X.n);
+    const int i = posm(R.y >> 16, (uint32_t)(X.n - L + 1));
+    int xs[5];
+#pragma unroll
+    for (int e = 0; e < 5; ++e) xs[e] = e < L ? x[i + e] : 0;
     G.sync();
-    if (G.tig == 0) x[i] = (ByteEl)(xi ^ 1);
-    aw += xi ? -(long long)X.w[i] : (long long)X.w[i];
-    av += xi ? -(long long)X.v[i] : (long long)X.v[i];
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+      if (e < L) {
+        if (G.tig == 0) x[i + e] = (ByteEl)(xs[e] ^ 1);
+        aw += xs[e] ? -(long long)X.w[i + e] : (long long)X.w[i + e];
+        av += xs[e] ? -(long long)X.v[i + e] : (long long)X.v[i + e];
+      }
+    }
     G.sync();
   }
 }
 
-__device__ void apply_gap(const View &X, ByteEl *x, long long *loads, const Weights<1> &W,
+__device__ void apply_gap(const View &X, ByteEl *x, long long *loads, const Weights<2> &W,
                           uint32_t c, uint32_t p, uint32_t g, const Group &G) {
   uint4 R0;
   const int k = regen_k(X, W, c, p, g, R0);
-  for (int t = 0; t < k; ++t) {
-    const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
-    const int j = posm(R.y >> 16, (uint32_t)X.n);
-    const int dd = 1 + posm(R.y & 0xFFFFu, (uint32_t)(X.m - 1));
-    const int ao = x[j];
-    const int an = (ao + dd) % X.m;
-    G.sync();
-    if (G.tig == 0) {
-      x[j] = (ByteEl)an;
-      loads[ao] -= X.gr[(size_t)ao * X.n + j];
-      loads[an] += X.gr[(size_t)an * X.n + j];
+  G.sync();
+  if (G.tig == 0) {
+    for (int t = 0; t < k; ++t) {
+      const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
+      const int L = seg_len(wpick(W.cop, W.Wop, R.x), R.z, X.n);
+      const int i = posm(R.y >> 16, (uint32_t)(X.n - L + 1));
+      const int dd = 1 + posm(R.y & 0xFFFFu, (uint32_t)(X.m - 1));
+      for (int j = i; j < i + L; ++j) {
+        const int ao = x[j];
+        const int an = (ao + dd) % X.m;
+        x[j] = (ByteEl)an;
+        loads[ao] -= X.gr[(size_t)ao * X.n + j];
+        loads[an] += X.gr[(size_t)an * X.n + j];
+      }
     }
-    G.sync();
   }
+  G.sync();
 }
 
 // auxiliary sums of one member (knapsack W/V, GAP loads), computed by the
@@ -1607,6 +1756,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.node = I.node;
   X.cv32 = I.cv32 != 0;
   X.t3 = ((I.enabled >> THREE_OPT) & 1u) != 0;
+  X.seg = ((I.enabled >> SEGMENT) & 1u) != 0;
   X.lam1 = I.lam1;
   if (!staged) return X;
   auto copy = [&](const void *src, int64_t bytes, int64_t off) {

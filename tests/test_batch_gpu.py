@@ -58,6 +58,11 @@ def mixed_batch():
     items.append((dict(I.gap(30, 258, m=5), tag=48),
                   dict(P=9, C=48, G=22, U=3, islands=3, migrate_period=6, migrate_strategy=1,
                        migrate_n=3)))
+    # seg_flip / seg_reset beside the element operators
+    items.append((dict(I.knapsack(150, 259), tag=49),
+                  dict(P=8, C=64, G=25, ops=[O.FLIP, O.SEGMENT])))
+    items.append((dict(I.gap(40, 260, m=6), tag=50),
+                  dict(P=6, C=64, G=23, ops=[O.PERTURB, O.SEGMENT], w_k=[20000, 30000, 15536])))
     return items
 
 

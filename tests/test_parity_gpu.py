@@ -268,6 +268,56 @@ def test_gap300_prefix(cgo):
     assert_same_state(g, o, "gap300")
 
 
+# ------------------------------------- seg_flip / seg_reset (segment level)
+SEGMENT_K = [(65536, 0, 0), (0, 65536, 0), (0, 0, 65536), None]
+
+
+@pytest.mark.parametrize("kw", SEGMENT_K)
+@pytest.mark.parametrize("n", [2, 3, 5, 40, 300])
+def test_knapsack_seg_flip(cgo, n, kw):
+    """Segments of 2..5 items (clamped to n), alone and beside the flip, with
+    one, two or three steps (overlapping segments of one candidate)."""
+    inst = I.knapsack(n, 70 + n)
+    for ops in ([O.SEGMENT], [O.FLIP, O.SEGMENT]):
+        over = dict(P=6, C=80, G=29, U=4, ops=ops)
+        if kw:
+            over["w_k"] = list(kw)
+        p = params_for(inst, **over)
+        _, g, o = run_both(cgo, inst, p, 14)
+        assert_same_state(g, o, "knapsack n=%d ops %s kw %s" % (n, ops, kw))
+
+
+@pytest.mark.parametrize("kw", SEGMENT_K)
+@pytest.mark.parametrize("n,m", [(2, 2), (4, 3), (7, 2), (30, 5), (120, 12)])
+def test_gap_seg_reset(cgo, n, m, kw):
+    inst = I.gap(n, 90 + n, m=m)
+    for ops in ([O.SEGMENT], [O.PERTURB, O.SEGMENT]):
+        over = dict(P=6, C=64, G=27, U=3, ops=ops, elite_period=9)
+        if kw:
+            over["w_k"] = list(kw)
+        p = params_for(inst, **over)
+        _, g, o = run_both(cgo, inst, p, 15)
+        assert_same_state(g, o, "gap n=%d m=%d ops %s kw %s" % (n, m, ops, kw))
+
+
+@pytest.mark.parametrize("ns,wpm", [(2, 1), (2, 2), (1, 4)])
+def test_segment_operators_launch_shapes(cgo, ns, wpm):
+    for inst, ops in ((I.knapsack(500, 97), [O.FLIP, O.SEGMENT]),
+                      (I.gap(200, 98, m=8), [O.PERTURB, O.SEGMENT])):
+        p = params_for(inst, P=9, C=32 * wpm, G=41, U=5, ops=ops)
+        prob, g, o = run_both(cgo, inst, p, 16, wpm=wpm, ns=ns)
+        assert prob.get_launch()[3] == ns
+        assert_same_state(g, o, "model %d ns %d wpm %d" % (inst["model"], ns, wpm))
+
+
+def test_segment_operator_needs_two_elements(cgo):
+    inst = I.knapsack(1, 99)
+    p = params_for(inst, P=3, C=8, G=5, ops=[O.SEGMENT])
+    with pytest.raises(cgo.CgoError) as e:
+        cgo.Problem(inst).solve(p, 1)
+    assert e.value.status == cgo.ERR_INVALID
+
+
 # ------------------------------------------------------------------ CVRPTW
 @pytest.mark.parametrize("n,V,kw", [(2, 1, None), (5, 2, None), (12, 3, (0, 0, 65536)),
                                     (30, 6, None)])

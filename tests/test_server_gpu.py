@@ -44,6 +44,8 @@ def request_mix():
         # islands with ring migration
         (dict(I.tsp_uniform(40, 310), tag=11), dict(P=8, C=64, G=29, U=4, islands=4,
                                                     migrate_period=8, migrate_strategy=0)),
+        # segment operators
+        (dict(I.gap(35, 311, m=5), tag=12), dict(P=6, C=48, G=26, ops=[O.PERTURB, O.SEGMENT])),
     ]
 
 
