@@ -37,6 +37,7 @@ import numpy as np  # noqa: E402
 import instances as I  # noqa: E402
 
 TO, INS, OR = 1, 2, 3
+O_THREE_OPT, O_SEGMENT = 6, 7     # operator slots of the C ABI (cgo_op)
 
 
 def workload(name: str):
@@ -64,8 +65,42 @@ def workload(name: str):
 
 def lib_params(prob, cfg):
     p = prob.default_params()
-    p.update(cfg)
+    extra = cfg.get("extra_mask", 0)
+    p.update({k: v for k, v in cfg.items() if k != "extra_mask"})
+    p["op_mask"] |= extra
     return p
+
+
+def solve_variant(args, model: int, cfg: dict, desc: str):
+    """The single-solve options beyond the workload's own configuration
+    (start pool, islands, extra operators), applied alike by both arms."""
+    cfg = dict(cfg)
+    if args.init_oversample > 1 or args.init_heuristic:
+        cfg["init_oversample"] = args.init_oversample
+        cfg["init_heuristic"] = args.init_heuristic
+        desc += " start=K%d%s" % (args.init_oversample, "+heuristic" if args.init_heuristic else "")
+    if args.islands:
+        isl, per, strat, nmig = (int(x) for x in args.islands.split(","))
+        cfg.update(islands=isl, migrate_period=per, migrate_strategy=strat, migrate_n=nmig)
+        desc += " islands=%d period=%d %s" % (isl, per, ["ring", "top-%d" % nmig,
+                                                          "hybrid-%d" % nmig][strat])
+    if args.extra_ops:
+        cfg["extra_mask"] = extra_ops_mask(model, args.extra_ops)
+        desc += " +ops=" + args.extra_ops
+    return cfg, desc
+
+
+def extra_ops_mask(model: int, extra: str) -> int:
+    """Operator bits that --extra-ops adds for a model (QAP's GPU path is swap-only)."""
+    bits = 0
+    for name in filter(None, extra.split(",")):
+        if name == "three_opt" and model in (I.TSP, I.CVRPTW):
+            bits |= 1 << O_THREE_OPT
+        elif name == "segment" and model in (I.KNAPSACK, I.GAP):
+            bits |= 1 << O_SEGMENT
+        elif name not in ("three_opt", "segment"):
+            raise SystemExit("unknown operator " + name)
+    return bits
 
 
 # ------------------------------------------------------------------ clocks
@@ -129,18 +164,31 @@ def run_reference(args, rank, world):
         return
     import oracle as O
     inst, cfg, desc = workload(args.workload)
-    p = O.default_params(inst)
-    p.update({k: v for k, v in cfg.items() if k != "G"})
+    if inst is None:
+        # batched / served workloads: a stratified sample of the instance mix
+        insts = [dict(x, tag=i) for i, x in enumerate(I.batch_mix(512, 0))][::64]
+        desc += " (oracle on every 64th instance)"
+    else:
+        insts = [inst]
+        cfg, desc = solve_variant(args, inst["model"], cfg, desc)
+    plist = []
+    for x in insts:
+        p = O.default_params(x)
+        p.update({k: v for k, v in cfg.items() if k not in ("G", "extra_mask")})
+        p["op_mask"] |= cfg.get("extra_mask", 0)
+        plist.append(p)
     gens = args.ref_generations
     cores = O.lib().orc_threads(0)
     for _ in range(args.warmup):
-        O.solve(inst, p, 1, max(1, gens // 4))
+        for x, p in zip(insts, plist):
+            O.solve(x, p, 1, max(1, gens // 4))
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        O.solve(inst, p, 1, gens)
+        for x, p in zip(insts, plist):
+            O.solve(x, p, 1, gens)
         times.append(time.perf_counter() - t0)
-    evals = cfg["P"] * cfg["C"] * gens
+    evals = cfg["P"] * cfg["C"] * gens * len(insts)
     value = evals * args.steps / sum(times)
     line = {"metric": "move_evals_per_s", "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -159,7 +207,8 @@ def cpu_baseline(inst, cfg, desc, budget_s: float):
     """Time the oracle as it stands on a bounded prefix of the workload."""
     import oracle as O
     p = O.default_params(inst)
-    p.update({k: v for k, v in cfg.items() if k != "G"})
+    p.update({k: v for k, v in cfg.items() if k not in ("G", "extra_mask")})
+    p["op_mask"] |= cfg.get("extra_mask", 0)
     cores = O.lib().orc_threads(0)
     t0 = time.perf_counter()
     O.solve(inst, p, 1, 2)
@@ -199,6 +248,9 @@ def main():
                     help="single solve: K of the oversampled start (1 = plain start)")
     ap.add_argument("--init-heuristic", type=int, default=0,
                     help="single solve: 1 = add the row/column-sum start permutations")
+    ap.add_argument("--extra-ops", default="",
+                    help="enable operators beyond the default mask where they apply: "
+                         "'three_opt' (TSP, CVRPTW), 'segment' (seg_flip / seg_reset: knapsack, GAP)")
     ap.add_argument("--islands", default="",
                     help="single solve: islands 'I,period,strategy,N' (strategy 0 ring, "
                          "1 top-N, 2 hybrid)")
@@ -244,15 +296,7 @@ def main():
     inst = dict(inst, tag=0)
     seed = 1 + rank
     stream = torch.cuda.Stream()
-    if args.init_oversample > 1 or args.init_heuristic:
-        cfg["init_oversample"] = args.init_oversample
-        cfg["init_heuristic"] = args.init_heuristic
-        desc += " start=K%d%s" % (args.init_oversample, "+heuristic" if args.init_heuristic else "")
-    if args.islands:
-        isl, per, strat, nmig = (int(x) for x in args.islands.split(","))
-        cfg.update(islands=isl, migrate_period=per, migrate_strategy=strat, migrate_n=nmig)
-        desc += " islands=%d period=%d %s" % (isl, per, ["ring", "top-%d" % nmig,
-                                                          "hybrid-%d" % nmig][strat])
+    cfg, desc = solve_variant(args, inst["model"], cfg, desc)
     prob = cgo.Problem(inst)
     params = lib_params(prob, cfg)
     from paper_2603_19163_gb300.autotune import Autotuner
@@ -372,10 +416,13 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
         desc = desc.replace("batch512-mix", "batch-%s%d" % (args.batch_class, len(mix)))
     probs = [cgo.Problem(x) for x in mix]
     params = []
-    for pr in probs:
+    for pr, x in zip(probs, mix):
         q = pr.default_params()
         q.update(P=cfg["P"], C=cfg["C"], G=G)
+        q["op_mask"] |= extra_ops_mask(x["model"], args.extra_ops)
         params.append(q)
+    if args.extra_ops:
+        desc += " +ops=" + args.extra_ops
     seeds = [1000 * rank + 1 + i for i in range(len(mix))]
     if args.wpm:
         for pr in probs:
@@ -408,6 +455,11 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
     launches = cgo.kernel_launches() - launches0
     barrier()
     clocks = sampler.stop() if rank == 0 else None
+    # solution quality of the last step: the sum of the instances' best costs per model
+    best_sum = {}
+    for pr, x in zip(probs, mix):
+        key = {I.TSP: "tsp", I.KNAPSACK: "knapsack", I.GAP: "gap", I.CVRPTW: "cvrptw"}[x["model"]]
+        best_sum[key] = best_sum.get(key, 0) + int(pr.best()[1])
     t = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -449,6 +501,7 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
                            "solves_per_s_one_launch_per_solve": seq_solves_s,
                            "batched_over_sequential": solves_s / seq_solves_s,
                            "sequential_sample": "%d of %d instances" % (len(sample), len(mix)),
+                           "best_cost_sum_by_model": best_sum,
                            "autotuner": tuned},
                 "e2e": {"value": evals * world / e2e_s, "unit": "evals/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

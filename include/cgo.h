@@ -76,7 +76,7 @@ typedef enum {
                           distinct cut points i < j < k of 0..length (segment level,
                           Table "operators"); off in the default mask */
   /* slot 7 holds the segment-level operator of the binary and of the integer
-     set (Table "operators"): a segment of L = min(2 + (x & 3), length)
+     set (Table "operators"): a segment of L = min(2 + (x & 1), length)
      elements from i = pos(a, length - L + 1); needs length >= 2; off in the
      default mask */
   CGO_OP_SEG_FLIP = 7,  /* binary: flip every element of the segment */

@@ -358,9 +358,9 @@ int32_t orc_apply_move(const orc_instance *in, int32_t op, uint32_t a, uint32_t 
       s[i] = (int32_t)(lb + (((int64_t)s[i] - lb + d) % R));
       return 0;
     }
-    case ORC_SEGMENT: { /* [R28] a segment of L = 2 + (x & 3) elements (at most len) */
+    case ORC_SEGMENT: { /* [R28] a segment of L = 2 + (x & 1) elements (at most len) */
       if (len < 2) return -1;
-      int32_t L = 2 + (int32_t)(x & 3u);
+      int32_t L = 2 + (int32_t)(x & 1u);
       if (L > len) L = len;
       i = (int32_t)orc_pos(a, (uint32_t)(len - L + 1));          /* segment start */
       if (encoding_of(in->model) == 1) {                          /* seg_flip */

@@ -233,10 +233,11 @@ struct Enc<GAP> {
 };
 
 // [R28] elements a step of the binary / integer sets touches: 1 for the
-// element operator, min(2 + (x & 3), n) for the segment operator; the
+// element operator, min(2 + (x & 1), n) for the segment operator; the
 // segment starts at pos(a, n - L + 1) (the element operator's pos(a, n))
+constexpr int kSegMax = 3;
 __device__ __forceinline__ int seg_len(int op, uint32_t x, int n) {
-  return op == 0 ? 1 : min(2 + (int)(x & 3u), n);
+  return op == 0 ? 1 : min(2 + (int)(x & 1u), n);
 }
 
 template <int NO>
@@ -774,7 +775,7 @@ __device__ long long candidate_knap_seg(const View &X, const ByteEl *x, const We
       const int L = seg_len(op[t], R.z, X.n);
       const int i = posm(R.y >> 16, (uint32_t)(X.n - L + 1));
 #pragma unroll
-      for (int e = 0; e < 5; ++e) {
+      for (int e = 0; e < kSegMax; ++e) {
         if (e < L) {
           const int q = i + e;
           const int xi = x[q] ^ (int)(t >= 1 && q >= s0 && q < e0) ^ (int)(t >= 2 && q >= s1 && q < e1);
@@ -898,22 +899,27 @@ __device__ long long candidate_gap_seg(const View &X, const ByteEl *x, const lon
   }
   long long d = 0;
   const int V = S.l0 + S.l1 + S.l2;
-  for (int u = 0; u < V; ++u) {
+  // the reassignments already taken: job << 16 | new agent << 8 | old agent
+  // (both loops unrolled so that the array stays in registers)
+  uint32_t done[3 * kSegMax];
+#pragma unroll
+  for (int u = 0; u < 3 * kSegMax; ++u) {
+    if (u >= V) break;
     int t, j, dd;
     S.at(u, t, j, dd);
     const int ao = S.agent_before(x, j, t, m);
     const int an = ao + dd - (ao + dd >= m ? m : 0);
     long long Lo = loads[ao], Ln = loads[an];
+#pragma unroll
     for (int v = 0; v < u; ++v) {
-      int t2, j2, d2;
-      S.at(v, t2, j2, d2);
-      const int bo = S.agent_before(x, j2, t2, m);
-      const int bn = bo + d2 - (bo + d2 >= m ? m : 0);
+      const uint32_t w = done[v];
+      const int bo = (int)(w & 0xFFu), bn = (int)((w >> 8) & 0xFFu), j2 = (int)(w >> 16);
       if (bo == ao) Lo -= X.gr[(size_t)ao * n + j2];
       else if (bn == ao) Lo += X.gr[(size_t)ao * n + j2];
       if (bo == an) Ln -= X.gr[(size_t)an * n + j2];
       else if (bn == an) Ln += X.gr[(size_t)an * n + j2];
     }
+    done[u] = (uint32_t)ao | ((uint32_t)an << 8) | ((uint32_t)j << 16);
     const long long ro = X.gr[(size_t)ao * n + j], rn = X.gr[(size_t)an * n + j];
     const long long co = X.gcap[ao], cn = X.gcap[an];
     d += (long long)X.gc[(size_t)an * n + j] - X.gc[(size_t)ao * n + j];
@@ -982,12 +988,12 @@ __device__ void apply_knap(const View &X, ByteEl *x, const Weights<2> &W, uint32
     const uint4 R = t == 0 ? R0 : philox(ctr_word(c, t, kKindMove), X.tag, p, g, X.k0, X.k1);
     const int L = seg_len(wpick(W.cop, W.Wop, R.x), R.z, X.n);
     const int i = posm(R.y >> 16, (uint32_t)(X.n - L + 1));
-    int xs[5];
+    int xs[kSegMax];
 #pragma unroll
-    for (int e = 0; e < 5; ++e) xs[e] = e < L ? x[i + e] : 0;
+    for (int e = 0; e < kSegMax; ++e) xs[e] = e < L ? x[i + e] : 0;
     G.sync();
 #pragma unroll
-    for (int e = 0; e < 5; ++e) {
+    for (int e = 0; e < kSegMax; ++e) {
       if (e < L) {
         if (G.tig == 0) x[i + e] = (ByteEl)(xs[e] ^ 1);
         aw += xs[e] ? -(long long)X.w[i + e] : (long long)X.w[i + e];

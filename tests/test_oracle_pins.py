@@ -253,7 +253,7 @@ def _preimage(q, m):
 
 def test_segment_operators_are_runs_of_the_element_operators():
     """seg_flip is L flips and seg_reset L random resets with one offset, at
-    the L consecutive positions from i = pos(a, n-L+1), L = min(2 + (x & 3), n);
+    the L consecutive positions from i = pos(a, n-L+1), L = min(2 + (x & 1), n);
     segment starts are (nearly) uniform over the n-L+1 choices."""
     rng = np.random.default_rng(22)
     L_ = O.lib()
@@ -265,7 +265,7 @@ def test_segment_operators_are_runs_of_the_element_operators():
         for _ in range(1500 if n == 9 else 200):
             a, b = (int(v) for v in rng.integers(0, 65536, 2))
             x = int(rng.integers(0, 2**32))
-            L = min(2 + (x & 3), n)
+            L = min(2 + (x & 1), n)
             i = L_.orc_pos(a, n - L + 1)
             s = rng.integers(0, 2, n).astype(np.int32)
             t = O.apply_move(ki, O.SEGMENT, a, b, x, s)
@@ -284,7 +284,7 @@ def test_segment_operators_are_runs_of_the_element_operators():
             if n == 9:
                 starts[(L, i)] = starts.get((L, i), 0) + 1
         if n == 9:
-            for L in (2, 3, 4, 5):
+            for L in (2, 3):
                 cnt = [starts.get((L, i), 0) for i in range(n - L + 1)]
                 mean = sum(cnt) / len(cnt)
                 assert min(cnt) > 0.6 * mean and max(cnt) < 1.4 * mean, (L, cnt)
