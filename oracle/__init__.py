@@ -41,7 +41,8 @@ class OrcParams(ctypes.Structure):
                 ("stag_limit", ctypes.c_uint32), ("elite_period", ctypes.c_uint32),
                 ("init_oversample", ctypes.c_uint32), ("init_heuristic", ctypes.c_uint32),
                 ("islands", ctypes.c_uint32), ("migrate_period", ctypes.c_uint32),
-                ("migrate_strategy", ctypes.c_uint32), ("migrate_n", ctypes.c_uint32)]
+                ("migrate_strategy", ctypes.c_uint32), ("migrate_n", ctypes.c_uint32),
+                ("cross_q16", ctypes.c_uint32)]
 
 
 class OrcState(ctypes.Structure):
@@ -96,6 +97,10 @@ def lib() -> ctypes.CDLL:
             L.orc_init.restype = i32
             L.orc_migrate.argtypes = [ctypes.POINTER(OrcParams), ctypes.POINTER(OrcState)]
             L.orc_migrate.restype = i32
+            L.orc_crossover.argtypes = [ctypes.POINTER(OrcInstance), ctypes.POINTER(OrcParams), u64,
+                                        ctypes.POINTER(OrcState)]
+            L.orc_crossover.restype = i32
+            L.orc_ox.argtypes = [_i32p, _i32p, i32, i32, i32, _i32p]
             L.orc_heuristic_perms.argtypes = [ctypes.POINTER(OrcInstance), _i32p]
             L.orc_heuristic_perms.restype = i32
             L.orc_run.argtypes = [ctypes.POINTER(OrcInstance), ctypes.POINTER(OrcParams), u64,
@@ -150,7 +155,7 @@ class Instance:
 
 PARAM_KEYS = ("P", "C", "op_mask", "w_op", "w_k", "T0", "alpha", "U", "ema_a", "w_floor",
               "w_cap", "op_cap", "stag_limit", "elite_period", "init_oversample", "init_heuristic",
-              "islands", "migrate_period", "migrate_strategy", "migrate_n")
+              "islands", "migrate_period", "migrate_strategy", "migrate_n", "cross_q16")
 
 
 def default_params(inst: dict) -> dict:
@@ -205,6 +210,33 @@ def migrate(params: dict, state: dict) -> dict:
     p = make_params(params)
     if lib().orc_migrate(ctypes.byref(p), ctypes.byref(st)) != 0:
         raise ValueError("orc_migrate failed")
+    out = dict(state)
+    out.update({k: v.copy() for k, v in arrays.items()})
+    return out
+
+
+def ox(A, B, lo: int, hi: int) -> np.ndarray:
+    """Order crossover of two permutations keeping A[lo..hi]."""
+    A = np.ascontiguousarray(A, dtype=np.int32)
+    B = np.ascontiguousarray(B, dtype=np.int32)
+    out = np.zeros(len(A), np.int32)
+    lib().orc_ox(A.ctypes.data_as(_i32p), B.ctypes.data_as(_i32p), len(A), lo, hi,
+                 out.ctypes.data_as(_i32p))
+    return out
+
+
+def crossover(inst: dict, params: dict, seed: int, state: dict) -> dict:
+    """One crossover step of the population applied to a copy of a state dict
+    with fields cur, best_sol, cost, best_cost, g, T (the rest is carried over)."""
+    P, length = int(state["cur"].shape[0]), int(state["cur"].shape[1])
+    st, arrays = new_state(P, length)
+    for k in ("cur", "best_sol", "cost", "best_cost"):
+        arrays[k][...] = state[k]
+    st.g, st.T = int(state["g"]), int(state["T"])
+    I = Instance(inst)
+    p = make_params(params)
+    if lib().orc_crossover(I.ref, ctypes.byref(p), seed, ctypes.byref(st)) != 0:
+        raise ValueError("orc_crossover failed")
     out = dict(state)
     out.update({k: v.copy() for k, v in arrays.items()})
     return out

@@ -53,6 +53,7 @@ static void draw(uint32_t w0, uint32_t tag, uint32_t p, uint32_t g, uint64_t see
 #define KIND_MOVE 0u
 #define KIND_ACCEPT 1u
 #define KIND_INIT 2u
+#define KIND_CROSS 3u
 #define W0(cand, step, kind) ((uint32_t)(cand) | ((uint32_t)(step) << 20) | ((uint32_t)(kind) << 24))
 #define INIT_GEN 0xFFFFFFFFu
 
@@ -750,6 +751,86 @@ int32_t orc_migrate(const orc_params *pr, orc_state *st) {
   return 0;
 }
 
+/* [R29] crossover (Table "operators", crossover level: OX for permutations,
+ * uniform crossover for binary and integer vectors), taken after every AOS
+ * update and migration, before elite injection.  With R = Philox(0 | 3<<24,
+ * tag, p, g): member p crosses when hi16(R.r0) < cross_q16, with partner
+ * q = (p + 1 + pos(hi16(R.r1), P-1)) mod P.  The parents are p's current
+ * solution A and q's best solution B, both as they stood before any
+ * crossover of this window.
+ *   OX: cut points i = pos(hi16(R.r2), n), j = pos(lo16(R.r2), n-1) + (j >= i),
+ *       lo = min, hi = max; the child keeps A[lo..hi] in place and fills the
+ *       positions hi+1, ..., n-1, 0, ..., lo-1 with the elements of B that
+ *       are not in A[lo..hi], in B's order from B[hi+1] on (wrapping).
+ *   uniform: element k comes from B when bit k mod 32 of word (k/32) mod 4
+ *       of Philox((k/128) | 1<<20 | 3<<24, tag, p, g) is set, else from A.
+ * The child's cost is evaluated in full; it replaces A under the Metropolis
+ * rule [R7] at the current temperature with the variate R.r3, and lowers
+ * p's best like an accepted move. */
+void orc_ox(const int32_t *A, const int32_t *B, int32_t len, int32_t lo, int32_t hi,
+            int32_t *child) {
+  char *mark = (char *)calloc((size_t)len, 1);
+  for (int32_t k = lo; k <= hi; k++) {
+    child[k] = A[k];
+    mark[A[k]] = 1;
+  }
+  int32_t o = (hi + 1) % len;                           /* next free position */
+  for (int32_t t = 0; t < len; t++) {
+    const int32_t e = B[(hi + 1 + t) % len];
+    if (!mark[e]) {
+      child[o] = e;
+      o = (o + 1) % len;
+    }
+  }
+  free(mark);
+}
+
+static void crossover(const orc_instance *in, const orc_params *pr, uint64_t seed,
+                      orc_state *st) {
+  const int32_t P = st->P, len = st->len, enc = encoding_of(in->model);
+  const uint32_t g = (uint32_t)st->g;
+  int32_t *bsol = (int32_t *)malloc(sizeof(int32_t) * (size_t)P * len);
+  int32_t *child = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
+  memcpy(bsol, st->best_sol, sizeof(int32_t) * (size_t)P * len);
+  for (int32_t p = 0; p < P; p++) {
+    uint32_t R[4];
+    draw(W0(0, 0, KIND_CROSS), in->tag, (uint32_t)p, g, seed, R);
+    if ((R[0] >> 16) >= pr->cross_q16) continue;
+    const int32_t q = (p + 1 + (int32_t)orc_pos(R[1] >> 16, (uint32_t)(P - 1))) % P;
+    const int32_t *A = st->cur + (int64_t)p * len, *B = bsol + (int64_t)q * len;
+    if (enc == 0) {                                     /* OX */
+      int32_t i = (int32_t)orc_pos(R[2] >> 16, (uint32_t)len);
+      int32_t j = (int32_t)orc_pos(R[2] & 0xFFFFu, (uint32_t)(len - 1));
+      if (j >= i) j++;
+      orc_ox(A, B, len, i < j ? i : j, i < j ? j : i, child);
+    } else {                                            /* uniform */
+      uint32_t Q[4] = {0, 0, 0, 0};
+      for (int32_t k = 0; k < len; k++) {
+        if (k % 128 == 0) draw(W0(k / 128, 1, KIND_CROSS), in->tag, (uint32_t)p, g, seed, Q);
+        child[k] = ((Q[(k / 32) % 4] >> (k % 32)) & 1u) ? B[k] : A[k];
+      }
+    }
+    const int64_t c = orc_cost(in, child);
+    if (orc_accept(c - st->cost[p], st->T, R[3])) {
+      memcpy(st->cur + (int64_t)p * len, child, sizeof(int32_t) * (size_t)len);
+      st->cost[p] = c;
+      if (c < st->best_cost[p]) {
+        st->best_cost[p] = c;
+        memcpy(st->best_sol + (int64_t)p * len, child, sizeof(int32_t) * (size_t)len);
+      }
+    }
+  }
+  free(bsol);
+  free(child);
+}
+
+int32_t orc_crossover(const orc_instance *in, const orc_params *pr, uint64_t seed,
+                      orc_state *st) {
+  if (pr->cross_q16 > 65536u) return -1;
+  if (st->P >= 2 && pr->cross_q16 > 0) crossover(in, pr, seed, st);
+  return 0;
+}
+
 static void inject(orc_state *st) {
   int32_t e = orc_elite(st), wv = 0, len = st->len;
   for (int32_t p = 1; p < st->P; p++)
@@ -772,6 +853,7 @@ int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc
       ((uint32_t)P % pr->islands != 0 || pr->migrate_strategy > 2 ||
        (pr->migrate_strategy != 0 && (pr->migrate_n < 1 || pr->migrate_n > (uint32_t)P / pr->islands))))
     return -1;
+  if (pr->cross_q16 > 65536u) return -1;
   uint32_t *cnt = (uint32_t *)calloc((size_t)P * 22, sizeof(uint32_t));
   int32_t nthreads = orc_threads(threads);
   for (int64_t it = 0; it < generations; it++) {
@@ -800,6 +882,7 @@ int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc
     st->g++;
     if (st->g % pr->U == 0) aos_update(in, pr, st);
     if (pr->islands > 1 && pr->migrate_period > 0 && st->g % pr->migrate_period == 0) migrate(pr, st);
+    if (pr->cross_q16 > 0 && P >= 2 && st->g % pr->U == 0) crossover(in, pr, seed, st);
     if (pr->elite_period > 0 && st->g % pr->elite_period == 0) inject(st);
   }
   free(cnt);

@@ -59,6 +59,8 @@ typedef struct {
   uint32_t migrate_period;         /* migration after every such generation; 0 = off */
   uint32_t migrate_strategy;       /* 0 ring, 1 global top-N, 2 hybrid (alternating) */
   uint32_t migrate_n;              /* N of the top-N strategy */
+  uint32_t cross_q16;              /* crossover probability per member and AOS window
+                                      (Table "operators", crossover level); 0 = off */
 } orc_params;
 
 /* Complete search state.  Arrays are caller-owned: cur/best_sol P*len,
@@ -108,6 +110,15 @@ int32_t orc_elite(const orc_state *st);
  * search takes after every migrate_period-th generation); exported for the
  * oracle's own pins.  Returns -1 for invalid island parameters. */
 int32_t orc_migrate(const orc_params *pr, orc_state *st);
+/* order crossover [R29]: child keeps A[lo..hi] in place and fills positions
+ * hi+1, ..., len-1, 0, ..., lo-1 with the elements of B outside that segment,
+ * in B's order from B[hi+1] on (wrapping); 0 <= lo <= hi < len */
+void orc_ox(const int32_t *A, const int32_t *B, int32_t len, int32_t lo, int32_t hi,
+            int32_t *child);
+/* One crossover step of the whole population at the state's generation
+ * (normally run by orc_run at each AOS window end); 0 or -1. */
+int32_t orc_crossover(const orc_instance *in, const orc_params *pr, uint64_t seed,
+                      orc_state *st);
 /* the attribute-agnostic start permutations of an instance (TSP: D; QAP: F,
  * then D): per matrix the orders of ascending and descending row sums, then
  * ascending and descending column sums.  out: 8 * n entries; returns their
