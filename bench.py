@@ -87,6 +87,9 @@ def solve_variant(args, model: int, cfg: dict, desc: str):
     if args.extra_ops:
         cfg["extra_mask"] = extra_ops_mask(model, args.extra_ops)
         desc += " +ops=" + args.extra_ops
+    if args.cross:
+        cfg["cross_q16"] = args.cross
+        desc += " cross=%.3f" % (args.cross / 65536.0)
     return cfg, desc
 
 
@@ -251,6 +254,8 @@ def main():
     ap.add_argument("--extra-ops", default="",
                     help="enable operators beyond the default mask where they apply: "
                          "'three_opt' (TSP, CVRPTW), 'segment' (seg_flip / seg_reset: knapsack, GAP)")
+    ap.add_argument("--cross", type=int, default=0,
+                    help="crossover probability per member and AOS window, Q16 (0 = off)")
     ap.add_argument("--islands", default="",
                     help="single solve: islands 'I,period,strategy,N' (strategy 0 ring, "
                          "1 top-N, 2 hybrid)")
@@ -420,9 +425,12 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
         q = pr.default_params()
         q.update(P=cfg["P"], C=cfg["C"], G=G)
         q["op_mask"] |= extra_ops_mask(x["model"], args.extra_ops)
+        q["cross_q16"] = args.cross
         params.append(q)
     if args.extra_ops:
         desc += " +ops=" + args.extra_ops
+    if args.cross:
+        desc += " cross=%.3f" % (args.cross / 65536.0)
     seeds = [1000 * rank + 1 + i for i in range(len(mix))]
     if args.wpm:
         for pr in probs:

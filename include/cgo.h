@@ -139,6 +139,10 @@ typedef struct {
                                   1 top-N: the population's N best to every island's N
                                   worst; 2 hybrid: ring and top-N alternate */
   uint32_t migrate_n;          /* N of top-N, 1 .. P/I */
+  uint32_t cross_q16;          /* crossover probability per member and AOS window, Q16
+                                  (<= 65536; 0 = off): order crossover for permutations,
+                                  uniform crossover for binary / integer vectors (Table
+                                  "operators", crossover level) with another member's best */
 } cgo_params;
 
 /* Full search state (checkpoint).  Scalars are filled/read by value; the

@@ -51,7 +51,8 @@ class cgo_params(ctypes.Structure):
                 ("stag_limit", ctypes.c_uint32), ("elite_period", ctypes.c_uint32),
                 ("init_oversample", ctypes.c_uint32), ("init_heuristic", ctypes.c_uint32),
                 ("islands", ctypes.c_uint32), ("migrate_period", ctypes.c_uint32),
-                ("migrate_strategy", ctypes.c_uint32), ("migrate_n", ctypes.c_uint32)]
+                ("migrate_strategy", ctypes.c_uint32), ("migrate_n", ctypes.c_uint32),
+                ("cross_q16", ctypes.c_uint32)]
 
 
 class cgo_state(ctypes.Structure):
@@ -174,7 +175,7 @@ PARAM_MAP = [("P", "population"), ("C", "candidates"), ("G", "generations"),
              ("elite_period", "elite_period"), ("init_oversample", "init_oversample"),
              ("init_heuristic", "init_heuristic"), ("islands", "islands"),
              ("migrate_period", "migrate_period"), ("migrate_strategy", "migrate_strategy"),
-             ("migrate_n", "migrate_n")]
+             ("migrate_n", "migrate_n"), ("cross_q16", "cross_q16")]
 
 
 def params_struct(d: dict) -> cgo_params:

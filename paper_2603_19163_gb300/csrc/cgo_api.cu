@@ -176,11 +176,14 @@ void heuristic_perms(const std::vector<int32_t> &M, int64_t n, std::vector<int32
   }
 }
 
-// entries of the start pool (0: plain start)
+// rows of the scratch solution buffer: the start pool's entries (0: plain
+// start), or one crossover child per member, whichever is more
 int64_t pool_size(const cgo_problem *p, const cgo_params &q) {
   const int64_t K = q.init_oversample > 1 ? q.init_oversample : 1;
   const int64_t H = q.init_heuristic ? p->n_heur : 0;
-  return (K > 1 || H > 0) ? K * q.population + H : 0;
+  const int64_t pool = (K > 1 || H > 0) ? K * q.population + H : 0;
+  const int64_t cross = (q.cross_q16 > 0 && q.population >= 2) ? q.population : 0;
+  return pool > cross ? pool : cross;
 }
 
 cgo_status ensure_pool(cgo_problem *p, const cgo_params &q) {
@@ -279,6 +282,7 @@ cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *
   if ((uint64_t)(q->init_oversample > 1 ? q->init_oversample : 1) * q->population > 16384u)
     return fail(CGO_ERR_INVALID, "init_oversample * population must be <= 16384");
   if (q->init_heuristic > 1) return fail(CGO_ERR_INVALID, "init_heuristic must be 0 or 1");
+  if (q->cross_q16 > 65536u) return fail(CGO_ERR_INVALID, "cross_q16 must be <= 65536");
   if (q->islands > 1 && q->migrate_period > 0) {
     if ((uint32_t)q->population % q->islands != 0)
       return fail(CGO_ERR_INVALID, "islands must divide the population");
@@ -340,6 +344,7 @@ KInst base_kinst(const cgo_problem *p) {
   h.mperiod = mig ? q.migrate_period : 0u;
   h.mstrat = (int32_t)q.migrate_strategy;
   h.mN = q.migrate_n;
+  h.cross_q16 = q.population >= 2 ? q.cross_q16 : 0u;
   h.K_over = q.init_oversample > 1 ? (int32_t)q.init_oversample : 1;
   h.n_heur = q.init_heuristic ? p->n_heur : 0;
   h.heur = p->d_heur;
@@ -766,6 +771,7 @@ cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
   q->migrate_period = 0;
   q->migrate_strategy = 0;
   q->migrate_n = 1;
+  q->cross_q16 = 0;
   return CGO_OK;
 }
 
@@ -1161,6 +1167,8 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
   if (s != CGO_OK) return s;
   if (q->init_oversample > 1 || q->init_heuristic)
     return fail(CGO_ERR_UNSUPPORTED, "the allocation-free solve starts from the plain random population");
+  if (q->cross_q16 > 0)
+    return fail(CGO_ERR_UNSUPPORTED, "the allocation-free solve has no buffer for crossover children");
   const int n = d->n, P = q->population;
   // carve the scratch; the triangle is sized for int32 entries (worst case)
   const size_t tri_b = up256((size_t)n * (n + 1) / 2 * 4 + 16);

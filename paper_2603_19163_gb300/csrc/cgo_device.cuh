@@ -10,7 +10,7 @@
 namespace cgo {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint32_t kKindMove = 0u, kKindAccept = 1u, kKindInit = 2u;
+constexpr uint32_t kKindMove = 0u, kKindAccept = 1u, kKindInit = 2u, kKindCross = 3u;
 constexpr uint32_t kInitGen = 0xFFFFFFFFu;
 
 __device__ __forceinline__ uint32_t ctr_word(uint32_t cand, uint32_t step, uint32_t kind) {

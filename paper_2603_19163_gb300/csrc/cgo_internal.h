@@ -84,8 +84,10 @@ struct KInst {
   // islands and migration
   int32_t islands, mstrat;
   uint32_t mperiod, mN;
+  // crossover probability per window (Q16); children go to pool_sol (P x len)
+  uint32_t cross_q16;
   const int32_t *heur;        // n_heur x n
-  int32_t *pool_sol;          // (K*P + n_heur) x len
+  int32_t *pool_sol;          // (K*P + n_heur) x len; crossover children (P x len)
   int64_t *pool_cost;
 };
 

@@ -1131,8 +1131,308 @@ struct __align__(16) Partial {
   int c, pad;
 };
 
+__device__ long long full_cost(const KInst &I, const int32_t *x);
+
+// [R27] migration at a window end (its two phases and barriers), kept out of
+// line so that the generation loop's register allocation does not carry it.
+// Returns the number of barriers passed, or -1 when one timed out.
+template <int MODEL, int NW>
+__device__ __noinline__ int window_migrate(const KInst &I, const View X, unsigned char *smem,
+                                           const Layout Lo, const Group G, int p0, int mine,
+                                           int ngroups, uint32_t g, uint32_t nb,
+                                           uint64_t timeout_ns, int nact, bool more) {
+  using El = typename SolEl<MODEL>::T;
+  const int lane = threadIdx.x & 31, len = I.len, P = I.P;
+  DevSync *S = I.sync;
+  SolScal *scal = (SolScal *)(smem + Lo.scal_off);
+  unsigned char *gmem = smem + Lo.part_off + (int64_t)G.grp * group_bytes(NW);
+  int *flag = (int *)(gmem + 2 * NW * sizeof(Partial));
+  const uint32_t nb0 = nb;
+  // [R27] islands of S consecutive members (Sec. 3.4.3).  Phase 1: every
+  // target takes its source's best solution as its current one, in shared
+  // memory only, so that all sources are read as they stood at the window
+  // end.  Phase 2, after a barrier: bests a migrant improved go to global
+  // memory and every member's cost and best are published again.
+  const int S_ = P / I.islands;
+  const bool ring = I.mstrat == 0 || (I.mstrat == 2 && ((g / I.mperiod) & 1u));
+  const int need = ring ? 1 : (int)I.mN;
+  const long long *gc = (const long long *)I.cost, *gb = (const long long *)I.best;
+  for (int e = 0; e < mine; ++e) {
+    const int ls = G.grp + e * ngroups, p = p0 + ls;
+    const int isl = p / S_, lo = isl * S_;
+    // the member's rank in its island, worst first: (cost desc, index asc)
+    const long long cp = ld_relaxed64(gc + p);
+    int r = 0;
+    for (int q = lo + lane; q < lo + S_; q += 32) {
+      const long long cq = ld_relaxed64(gc + q);
+      r += (cq > cp || (cq == cp && q < p)) ? 1 : 0;
+    }
+    r = __reduce_add_sync(kFull, r);
+    if (r >= need) continue;
+    // its source: ring, the best of the previous island; top-N, the r-th
+    // best of the population by (best, index), found by r + 1 successor scans
+    long long kb = LLONG_MIN;
+    int ki = -1;
+    const int qlo = ring ? ((isl + I.islands - 1) % I.islands) * S_ : 0;
+    const int qhi = ring ? qlo + S_ : P;
+    for (int j = 0; j <= (ring ? 0 : r); ++j) {
+      long long bb = LLONG_MAX;
+      int be = INT_MAX;
+      for (int q = qlo + lane; q < qhi; q += 32) {
+        const long long b = ld_relaxed64(gb + q);
+        if ((b > kb || (b == kb && q > ki)) && b < bb) {
+          bb = b;
+          be = q;
+        }
+      }
+      warp_argmin(bb, be);
+      kb = bb;
+      ki = be;
+    }
+    El *sol = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+    const int32_t *src = I.bestsol + (int64_t)ki * len;
+    for (int i = G.tig; i < len; i += G.nthr) sol[i] = (El)__ldcg(src + i);
+    G.sync();
+    SolScal sc = scal[ls];
+    sc.cost = kb;
+    sc.best = min(sc.best, kb);
+    G.sync();
+    if (G.tig == 0) scal[ls] = sc;
+    G.sync();
+    aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
+    if constexpr (MODEL == CVRPTW)
+      cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len), G);
+  }
+  if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
+    return -1;
+  ++nb;
+  for (int e = 0; e < mine; ++e) {
+    const int ls = G.grp + e * ngroups, p = p0 + ls;
+    if (scal[ls].best < ld_relaxed64(gb + p)) {
+      const El *sol = (const El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+      int32_t *dst = I.bestsol + (int64_t)p * len;
+      for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
+    }
+  }
+  G.sync();
+  if (G.tig == 0) {
+    for (int e = 0; e < mine; ++e) {
+      const int ls = G.grp + e * ngroups;
+      I.cost[p0 + ls] = scal[ls].cost;
+      I.best[p0 + ls] = scal[ls].best;
+    }
+  }
+  if (more) {
+    if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
+      return -1;
+    ++nb;
+  }
+  return (int)(nb - nb0);
+}
+
+// sum of one value over a member group (every thread gets the total)
+template <int NW>
+__device__ __forceinline__ long long group_sum(long long v, const Group &G, Partial *part) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  G.sync();
+  if ((threadIdx.x & 31) == 0) part[G.gw].d = v;
+  G.sync();
+  long long t = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) t += part[w].d;
+  G.sync();
+  return t;
+}
+
+// exact cost of a crossover child held in global memory (R16), computed by
+// the member group together; a CVRPTW route walk is serial (one thread)
+template <int MODEL, int NW>
+__device__ long long child_cost(const KInst &I, const int32_t *x, const Group &G, Partial *part) {
+  const int n = I.n, lane = threadIdx.x & 31;
+  if constexpr (MODEL == TSP) {
+    long long s = 0;
+    for (int k = G.tig; k < n; k += G.nthr)
+      s += I.mat0[(size_t)__ldcg(x + k) * n + __ldcg(x + (k + 1 == n ? 0 : k + 1))];
+    return group_sum<NW>(s, G, part);
+  } else if constexpr (MODEL == QAP) {
+    long long s = 0;
+    for (int i = G.tig; i < n; i += G.nthr) {
+      const int xi = __ldcg(x + i);
+      for (int j = 0; j < n; ++j)
+        s += (long long)I.mat0[(size_t)i * n + j] * I.mat1[(size_t)xi * n + __ldcg(x + j)];
+    }
+    return group_sum<NW>(s, G, part);
+  } else if constexpr (MODEL == KNAPSACK) {
+    long long W = 0, V = 0;
+    for (int k = G.tig; k < n; k += G.nthr)
+      if (__ldcg(x + k)) {
+        W += I.vec0[k];
+        V += I.vec1[k];
+      }
+    W = group_sum<NW>(W, G, part);
+    V = group_sum<NW>(V, G, part);
+    return -V + I.lam0 * overp(W - I.capacity);
+  } else if constexpr (MODEL == GAP) {
+    long long s = 0;
+    for (int j = G.tig; j < n; j += G.nthr) s += I.mat0[(size_t)__ldcg(x + j) * n + j];
+    s = group_sum<NW>(s, G, part);
+    // loads: the group's warps take the agents in turn
+    long long pen = 0;
+    for (int a = G.gw; a < I.m; a += NW) {
+      long long L = 0;
+      for (int j = lane; j < n; j += 32)
+        if (__ldcg(x + j) == a) L += I.mat1[(size_t)a * n + j];
+#pragma unroll
+      for (int off = 16; off; off >>= 1) L += __shfl_xor_sync(kFull, L, off);
+      pen += overp(L - I.vec0[a]);
+    }
+    // every lane of a warp holds its warp's penalty sum; count it once
+    pen = group_sum<NW>(lane == 0 ? pen : 0, G, part);
+    return s + I.lam0 * pen;
+  } else {
+    if (G.tig == 0) part[0].d = full_cost(I, x);
+    G.sync();
+    const long long c = part[0].d;
+    G.sync();
+    return c;
+  }
+}
+
+// [R29] crossover at a window end (both phases and barriers), out of line
+// like migration.  Returns the number of barriers passed, or -1.
+template <int MODEL, int NW>
+__device__ __noinline__ int window_cross(const KInst &I, const View X, unsigned char *smem,
+                                         const Layout Lo, const Group G, int p0, int mine,
+                                         int ngroups, uint32_t g, uint64_t T, uint32_t nb,
+                                         uint64_t timeout_ns, int nact, bool more) {
+  constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW);
+  using El = typename SolEl<MODEL>::T;
+  const int lane = threadIdx.x & 31, len = I.len, P = I.P;
+  DevSync *S = I.sync;
+  SolScal *scal = (SolScal *)(smem + Lo.scal_off);
+  El *scr = (El *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.sol_stride);
+  unsigned char *gmem = smem + Lo.part_off + (int64_t)G.grp * group_bytes(NW);
+  Partial *part = (Partial *)gmem;
+  int *flag = (int *)(gmem + 2 * NW * sizeof(Partial));
+  const uint32_t nb0 = nb;
+  // [R29] crossover of every member, with probability cross_q16 / 2^16,
+  // with another member's best solution as it stood at the window end.
+  // Phase 1 builds each child in the member's global scratch row, costs
+  // it and takes it into shared memory if the Metropolis rule accepts it;
+  // phase 2, after a barrier, writes the bests the children lowered and
+  // publishes every member's cost and best.
+  const long long *gb = (const long long *)I.best;
+  int *wt = (int *)part;  // per-warp counts of the order crossover's compaction
+  for (int e = 0; e < mine; ++e) {
+    const int ls = G.grp + e * ngroups, p = p0 + ls;
+    const uint4 R = philox(ctr_word(0, 0, kKindCross), X.tag, (uint32_t)p, g, X.k0, X.k1);
+    if ((R.x >> 16) >= I.cross_q16) continue;
+    int q = p + 1 + posm(R.y >> 16, (uint32_t)(P - 1));
+    q -= q >= P ? P : 0;
+    const int32_t *B = I.bestsol + (int64_t)q * len;
+    int32_t *child = I.pool_sol + (int64_t)p * len;
+    El *A = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+    if constexpr (PERM) {
+      // order crossover: A[lo..hi] stays; the other positions, from hi+1
+      // on (wrapping), take B's elements outside that segment in B's order
+      int i = posm(R.z >> 16, (uint32_t)len), j = posm(R.z & 0xFFFFu, (uint32_t)(len - 1));
+      j += j >= i ? 1 : 0;
+      const int lo = min(i, j), hi = max(i, j);
+      unsigned char *mark = (unsigned char *)scr;  // len bytes (the row holds len 16-bit entries)
+      for (int k = G.tig; k < len; k += G.nthr) mark[k] = 0;
+      G.sync();
+      for (int k = lo + G.tig; k <= hi; k += G.nthr) {
+        mark[A[k]] = 1;
+        child[k] = A[k];
+      }
+      G.sync();
+      int base = 0;
+      for (int c0 = 0; c0 < len; c0 += G.nthr) {
+        const int idx = c0 + G.tig;
+        int el = 0;
+        bool keep = false;
+        if (idx < len) {
+          int bi = hi + 1 + idx;
+          bi -= bi >= len ? len : 0;
+          el = __ldcg(B + bi);
+          keep = mark[el] == 0;
+        }
+        const unsigned bal = __ballot_sync(kFull, keep);
+        if (lane == 0) wt[G.gw] = __popc(bal);
+        G.sync();
+        int off = 0, tot_w = 0;
+        for (int w = 0; w < NW; ++w) {
+          const int v = wt[w];
+          off += w < G.gw ? v : 0;
+          tot_w += v;
+        }
+        if (keep) {
+          int pos = hi + 1 + base + off + __popc(bal & ((1u << lane) - 1u));
+          pos -= pos >= len ? len : 0;
+          child[pos] = el;
+        }
+        base += tot_w;
+        G.sync();
+      }
+    } else {
+      // uniform crossover: element k from B where bit k of the stream is set
+      for (int k = G.tig; k < len; k += G.nthr) {
+        const uint4 Q = philox(ctr_word((uint32_t)k >> 7, 1, kKindCross), X.tag, (uint32_t)p, g,
+                               X.k0, X.k1);
+        const int wsel = (k >> 5) & 3;
+        const uint32_t w = wsel == 0 ? Q.x : wsel == 1 ? Q.y : wsel == 2 ? Q.z : Q.w;
+        child[k] = ((w >> (k & 31)) & 1u) ? __ldcg(B + k) : (int32_t)A[k];
+      }
+    }
+    G.sync();
+    const long long cc = child_cost<MODEL, NW>(I, child, G, part);
+    if (accept_move(cc - scal[ls].cost, T, exp_variate_q32(R.w))) {
+      for (int k = G.tig; k < len; k += G.nthr) A[k] = (El)__ldcg(child + k);
+      G.sync();
+      SolScal sc = scal[ls];
+      sc.cost = cc;
+      sc.best = min(sc.best, cc);
+      G.sync();
+      if (G.tig == 0) scal[ls] = sc;
+      G.sync();
+      aux_init(MODEL, X, A, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
+      if constexpr (MODEL == CVRPTW)
+        cv_build(X, A, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len), G);
+    }
+  }
+  if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
+    return -1;
+  ++nb;
+  for (int e = 0; e < mine; ++e) {
+    const int ls = G.grp + e * ngroups, p = p0 + ls;
+    if (scal[ls].best < ld_relaxed64(gb + p)) {
+      const El *sol = (const El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+      int32_t *dst = I.bestsol + (int64_t)p * len;
+      for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
+    }
+  }
+  G.sync();
+  if (G.tig == 0) {
+    for (int e = 0; e < mine; ++e) {
+      const int ls = G.grp + e * ngroups;
+      I.cost[p0 + ls] = scal[ls].cost;
+      I.best[p0 + ls] = scal[ls].best;
+    }
+  }
+  if (more) {
+    if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
+      return -1;
+    ++nb;
+  }
+  return (int)(nb - nb0);
+}
+
 // ---------------------------------------------------------- evolve unit
-template <int MODEL, bool T16, int WPM, int NS>
+// XF: the population steps beyond AOS and injection (island migration,
+// crossover) are compiled in; single solves without them use kernels
+// without that code, whose generation loop then allocates registers alone.
+template <int MODEL, bool T16, int WPM, int NS, bool XF>
 __device__ void evolve_members(const KInst &I, const View &X, unsigned char *smem, const Layout &Lo,
                                int p0, int nsol, int warps, uint64_t timeout_ns) {
   constexpr int NO = Enc<MODEL>::NO;
@@ -1451,7 +1751,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
 
     // ------------------------------------------------ AOS window end
     const bool inject = I.E > 0 && (g % (uint32_t)I.E) == 0;
-    const bool migr = I.islands > 1 && (g % I.mperiod) == 0;
+    const bool migr = XF && I.islands > 1 && (g % I.mperiod) == 0;
+    const bool cross = XF && I.cross_q16 > 0;
     uint32_t tot[NO * 2 + 6];
     if (packed) {
       // a lane counts at most 3 * cpl * U * mine uses per window, so the warp
@@ -1504,7 +1805,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     }
     if (G.gw == 0 && lane < kStats && my) atomicAdd(&S->acc[slot][lane], my);
     if (G.gw == 0 && lane == 0) atomicMin((long long *)&S->elite[slot], minbest);
-    if ((inject || migr) && G.tig == 0) {
+    if ((inject || migr || cross) && G.tig == 0) {
       for (int e = 0; e < mine; ++e) {
         const int ls = G.grp + e * ngroups;
         I.cost[p0 + ls] = scal[ls].cost;
@@ -1537,85 +1838,18 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     weights_set(W, wo, wk);
     stats_zero(st);
 
-    if (migr) {
-      // [R27] islands of S consecutive members (Sec. 3.4.3).  Phase 1: every
-      // target takes its source's best solution as its current one, in shared
-      // memory only, so that all sources are read as they stood at the window
-      // end.  Phase 2, after a barrier: bests a migrant improved go to global
-      // memory and every member's cost and best are published again.
-      const int S_ = P / I.islands;
-      const bool ring = I.mstrat == 0 || (I.mstrat == 2 && ((g / I.mperiod) & 1u));
-      const int need = ring ? 1 : (int)I.mN;
-      const long long *gc = (const long long *)I.cost, *gb = (const long long *)I.best;
-      for (int e = 0; e < mine; ++e) {
-        const int ls = G.grp + e * ngroups, p = p0 + ls;
-        const int isl = p / S_, lo = isl * S_;
-        // the member's rank in its island, worst first: (cost desc, index asc)
-        const long long cp = ld_relaxed64(gc + p);
-        int r = 0;
-        for (int q = lo + lane; q < lo + S_; q += 32) {
-          const long long cq = ld_relaxed64(gc + q);
-          r += (cq > cp || (cq == cp && q < p)) ? 1 : 0;
-        }
-        r = __reduce_add_sync(kFull, r);
-        if (r >= need) continue;
-        // its source: ring, the best of the previous island; top-N, the r-th
-        // best of the population by (best, index), found by r + 1 successor scans
-        long long kb = LLONG_MIN;
-        int ki = -1;
-        const int qlo = ring ? ((isl + I.islands - 1) % I.islands) * S_ : 0;
-        const int qhi = ring ? qlo + S_ : P;
-        for (int j = 0; j <= (ring ? 0 : r); ++j) {
-          long long bb = LLONG_MAX;
-          int be = INT_MAX;
-          for (int q = qlo + lane; q < qhi; q += 32) {
-            const long long b = ld_relaxed64(gb + q);
-            if ((b > kb || (b == kb && q > ki)) && b < bb) {
-              bb = b;
-              be = q;
-            }
-          }
-          warp_argmin(bb, be);
-          kb = bb;
-          ki = be;
-        }
-        El *sol = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
-        const int32_t *src = I.bestsol + (int64_t)ki * len;
-        for (int i = G.tig; i < len; i += G.nthr) sol[i] = (El)__ldcg(src + i);
-        G.sync();
-        SolScal sc = scal[ls];
-        sc.cost = kb;
-        sc.best = min(sc.best, kb);
-        G.sync();
-        if (G.tig == 0) scal[ls] = sc;
-        G.sync();
-        aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
-        if constexpr (MODEL == CVRPTW)
-          cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len), G);
+    if constexpr (XF) {
+      if (migr) {
+        const int nbar = window_migrate<MODEL, NW>(I, X, smem, Lo, G, p0, mine, ngroups, g, nb,
+                                                   timeout_ns, nact, inject || cross);
+        if (nbar < 0) return;
+        nb += (uint32_t)nbar;
       }
-      if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
-        return;
-      ++nb;
-      for (int e = 0; e < mine; ++e) {
-        const int ls = G.grp + e * ngroups, p = p0 + ls;
-        if (scal[ls].best < ld_relaxed64(gb + p)) {
-          const El *sol = (const El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
-          int32_t *dst = I.bestsol + (int64_t)p * len;
-          for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
-        }
-      }
-      G.sync();
-      if (G.tig == 0) {
-        for (int e = 0; e < mine; ++e) {
-          const int ls = G.grp + e * ngroups;
-          I.cost[p0 + ls] = scal[ls].cost;
-          I.best[p0 + ls] = scal[ls].best;
-        }
-      }
-      if (inject) {
-        if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
-          return;
-        ++nb;
+      if (cross) {
+        const int nbar = window_cross<MODEL, NW>(I, X, smem, Lo, G, p0, mine, ngroups, g, T, nb,
+                                                 timeout_ns, nact, inject);
+        if (nbar < 0) return;
+        nb += (uint32_t)nbar;
       }
     }
 
@@ -1825,7 +2059,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
 // Single solve: CTA b covers members [b * groups, (b+1) * groups) of the
 // instance, one member per group of WPM warps (cooperative launch, so that
 // all members are resident together for the window barriers).
-template <int MODEL, bool T16, int WPM, int NS>
+template <int MODEL, bool T16, int WPM, int NS, bool XF>
 __global__ void __launch_bounds__(kMaxWarps * 32, 1)
     evolve_kernel(const __grid_constant__ KInst I, int warps, uint64_t timeout_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1837,7 +2071,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
   const int nsol = min(groups, I.P - p0);
   const Layout Lo =
       make_layout(staged ? I.shared_bytes : 0, I.len, I.m, groups, warps, WPM * NS, I.model);
-  evolve_members<MODEL, T16, WPM, NS>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
+  evolve_members<MODEL, T16, WPM, NS, XF>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
 }
 
 // Batched persistent kernel: each CTA takes the next instance of the work
@@ -1882,7 +2116,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
       const int groups = warps / WPM;
       const Layout Lo =
           make_layout(staged ? I.shared_bytes : 0, I.len, I.m, I.P, warps, WPM, I.model);
-      evolve_members<MODEL, T16, WPM, 1>(I, X, smem, Lo, 0, I.P, warps, timeout_ns);
+      evolve_members<MODEL, T16, WPM, 1, true>(I, X, smem, Lo, 0, I.P, warps, timeout_ns);
       (void)groups;
     }
     __syncthreads();
@@ -2214,25 +2448,33 @@ cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri, 
   return counted(cudaGetLastError());
 }
 
-template <int MODEL, bool T16>
-static const void *evolve_fn(int wpm, int ns) {
+template <int MODEL, bool T16, bool XF>
+static const void *evolve_fn_xf(int wpm, int ns) {
   if (ns == 2) {
-    if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2>;
-    if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 2>;
-    return (const void *)evolve_kernel<MODEL, T16, 1, 2>;
+    if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2, XF>;
+    if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 2, XF>;
+    return (const void *)evolve_kernel<MODEL, T16, 1, 2, XF>;
   }
-  if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 1>;
-  if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 1>;
-  return (const void *)evolve_kernel<MODEL, T16, 1, 1>;
+  if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 1, XF>;
+  if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 1, XF>;
+  return (const void *)evolve_kernel<MODEL, T16, 1, 1, XF>;
 }
 
+template <int MODEL, bool T16>
+static const void *evolve_fn(int wpm, int ns, bool xf) {
+  return xf ? evolve_fn_xf<MODEL, T16, true>(wpm, ns) : evolve_fn_xf<MODEL, T16, false>(wpm, ns);
+}
+
+// the kernel of a single solve: with the migration / crossover code only when
+// the solve takes either
 static const void *pick_evolve(const KInst &h, int wpm, int ns) {
+  const bool xf = h.islands > 1 || h.cross_q16 > 0;
   switch (h.model) {
-    case TSP: return h.tri16 ? evolve_fn<TSP, true>(wpm, ns) : evolve_fn<TSP, false>(wpm, ns);
-    case QAP: return evolve_fn<QAP, false>(wpm, ns);
-    case CVRPTW: return evolve_fn<CVRPTW, false>(wpm, ns);
-    case KNAPSACK: return evolve_fn<KNAPSACK, false>(wpm, ns);
-    case GAP: return evolve_fn<GAP, false>(wpm, ns);
+    case TSP: return h.tri16 ? evolve_fn<TSP, true>(wpm, ns, xf) : evolve_fn<TSP, false>(wpm, ns, xf);
+    case QAP: return evolve_fn<QAP, false>(wpm, ns, xf);
+    case CVRPTW: return evolve_fn<CVRPTW, false>(wpm, ns, xf);
+    case KNAPSACK: return evolve_fn<KNAPSACK, false>(wpm, ns, xf);
+    case GAP: return evolve_fn<GAP, false>(wpm, ns, xf);
   }
   return nullptr;
 }

@@ -63,6 +63,12 @@ def mixed_batch():
                   dict(P=8, C=64, G=25, ops=[O.FLIP, O.SEGMENT])))
     items.append((dict(I.gap(40, 260, m=6), tag=50),
                   dict(P=6, C=64, G=23, ops=[O.PERTURB, O.SEGMENT], w_k=[20000, 30000, 15536])))
+    # crossover (with islands on one of them)
+    items.append((dict(I.tsp_uniform(45, 261), tag=51),
+                  dict(P=10, C=64, G=27, U=3, cross_q16=40000, islands=2, migrate_period=9)))
+    items.append((dict(I.knapsack(90, 262), tag=52), dict(P=7, C=48, G=21, U=7, cross_q16=65536)))
+    items.append((dict(I.cvrptw(16, 263, vehicles=4, capacity=80), tag=53),
+                  dict(P=6, C=48, G=20, U=4, cross_q16=65536)))
     return items
 
 

@@ -428,6 +428,55 @@ def test_islands_degenerate_shapes(cgo):
         assert_same_state(g, o, str(over))
 
 
+# ------------------------------------------------------------------ crossover
+CROSS_CASES = [(I.tsp_uniform(30, 320), None), (I.qap_random(11, 321), [SW]),
+               (I.knapsack(60, 322), None), (I.gap(25, 323, m=4), None),
+               (I.cvrptw(14, 324, vehicles=4, capacity=70), None)]
+
+
+@pytest.mark.parametrize("q16", [65536, 30000])
+@pytest.mark.parametrize("ns", [1, 2])
+def test_crossover_every_model(cgo, q16, ns):
+    """Order crossover (permutations) and uniform crossover (binary,
+    integer) at every AOS window end, certain or with probability 0.46;
+    elite injection in the same windows as every third crossover."""
+    for inst, ops in CROSS_CASES:
+        over = dict(P=8, C=64, G=37, U=5, cross_q16=q16, elite_period=15)
+        if ops:
+            over["ops"] = ops
+        p = params_for(inst, **over)
+        _, g, o = run_both(cgo, inst, p, 5, ns=ns)
+        assert_same_state(g, o, "model %d q16 %d ns %d" % (inst["model"], q16, ns))
+
+
+@pytest.mark.parametrize("warps,wpm", [(1, 1), (2, 1), (8, 2), (8, 4)])
+def test_crossover_across_ctas_with_islands(cgo, warps, wpm):
+    """Partners in other CTAs; migration and crossover in the same windows."""
+    inst = I.tsp_clustered(80, 325)
+    p = params_for(inst, P=24, C=96, G=49, U=4, cross_q16=50000, islands=4, migrate_period=8,
+                   migrate_strategy=2, migrate_n=2, elite_period=12)
+    _, g, o = run_both(cgo, inst, p, 12, warps=warps, wpm=wpm)
+    assert_same_state(g, o, "warps %d wpm %d" % (warps, wpm))
+    inst = I.knapsack(300, 326)
+    p = params_for(inst, P=20, C=64, G=31, U=3, cross_q16=65536, ops=[O.FLIP, O.SEGMENT])
+    _, g, o = run_both(cgo, inst, p, 13, warps=warps, wpm=wpm)
+    assert_same_state(g, o, "knapsack warps %d wpm %d" % (warps, wpm))
+
+
+def test_crossover_edge_cases(cgo):
+    """One member (nothing to cross with), two members (each other's only
+    partner), a permutation of length 2 and a launch that ends mid-window."""
+    for inst, P, G in ((I.tsp_uniform(12, 327), 1, 20), (I.tsp_uniform(12, 328), 2, 20),
+                       (I.tsp_uniform(2, 329), 3, 15), (I.gap(9, 330, m=3), 5, 23)):
+        p = params_for(inst, P=P, C=16, G=G, U=5, cross_q16=65536)
+        _, g, o = run_both(cgo, inst, p, 14)
+        assert_same_state(g, o, "n %d P %d" % (inst["n"], P))
+    prob = cgo.Problem(I.tsp_uniform(12, 331))
+    with pytest.raises(cgo.CgoError) as e:
+        prob.solve(params_for(I.tsp_uniform(12, 331), P=4, C=16, G=5, cross_q16=65537), 1)
+    assert e.value.status == cgo.ERR_INVALID
+
+
 def test_islands_invalid_parameters(cgo):
     inst = I.tsp_uniform(20, 317)
     p = params_for(inst, P=12, C=32, G=10, U=5, islands=3, migrate_period=10)

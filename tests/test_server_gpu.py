@@ -46,6 +46,8 @@ def request_mix():
                                                     migrate_period=8, migrate_strategy=0)),
         # segment operators
         (dict(I.gap(35, 311, m=5), tag=12), dict(P=6, C=48, G=26, ops=[O.PERTURB, O.SEGMENT])),
+        # crossover
+        (dict(I.tsp_uniform(35, 312), tag=13), dict(P=6, C=48, G=24, U=4, cross_q16=50000)),
     ]
 
 

@@ -73,7 +73,7 @@ def test_static_solve_matches_cgo_solve_twice(env):
 def test_static_solve_rejects_the_pool_start(env):
     torch, cgo = env
     inst = I.tsp_uniform(30, 3)
-    for over in (dict(init_oversample=2), dict(init_heuristic=1)):
+    for over in (dict(init_oversample=2), dict(init_heuristic=1), dict(cross_q16=30000)):
         p = params_for(inst, P=8, C=32, G=5, **over)
         rc, _, _ = _static_solve(torch, cgo, inst, p, 1)
         assert rc == cgo.ERR_UNSUPPORTED
