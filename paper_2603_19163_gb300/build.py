@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcgo.so")
-SOURCES = ["cgo_api.cu", "cgo_kernels.cu", "cgo_server.cu", "cgo_peaks.cu"]
+SOURCES = ["cgo_kernels.cu", "cgo_kernels_xf.cu", "cgo_api.cu", "cgo_server.cu", "cgo_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

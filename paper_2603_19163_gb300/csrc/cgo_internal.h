@@ -94,6 +94,9 @@ struct KInst {
 // host-side launchers (cgo_kernels.cu)
 cudaError_t launch_init(const KInst &h, cudaStream_t st);
 cudaError_t launch_init_aos(const KInst &h, const DevAos &a0, cudaStream_t st);
+// the single-solve kernel with island migration and crossover compiled in
+// (cgo_kernels_xf.cu); nullptr for an unknown shape
+const void *pick_evolve_xf(int model, int tri16, int wpm, int ns);
 cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int ns, int64_t smem_bytes,
                                  uint64_t timeout_ns, cudaStream_t st);
 cudaError_t launch_finalize(const KInst &h, cudaStream_t st);

@@ -22,6 +22,10 @@
 #include "cgo_device.cuh"
 
 namespace cgo {
+#ifdef CGO_XF_UNIT
+// the second instantiation unit keeps its copies of the device code local
+namespace {
+#endif
 
 // ---------------------------------------------------------------- layout
 // Solutions in shared memory use compact elements: permutation symbols
@@ -86,6 +90,7 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   return L;
 }
 
+#ifndef CGO_XF_UNIT
 int64_t instance_data_bytes(const KInst &h) {
   switch (h.model) {
     case TSP: return align16((int64_t)h.n * (h.n + 1) / 2 * (h.tri16 ? 2 : 4));
@@ -105,6 +110,7 @@ int64_t smem_per_warp(const KInst &h) {
   Layout a = make_layout(0, h.len, h.m, 1, 1, 1, h.model);
   return a.total;
 }
+#endif
 
 // ------------------------------------------------------------- instance view
 struct View {
@@ -2172,6 +2178,7 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
   return 0;
 }
 
+#ifndef CGO_XF_UNIT
 // Philox-seeded Fisher-Yates / random bits / random integers for member p,
 // then its exact cost
 // Random start j (member j of a plain start, candidate j of a start pool):
@@ -2449,7 +2456,7 @@ cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri, 
 }
 
 template <int MODEL, bool T16, bool XF>
-static const void *evolve_fn_xf(int wpm, int ns) {
+static const void *evolve_fn(int wpm, int ns) {
   if (ns == 2) {
     if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2, XF>;
     if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 2, XF>;
@@ -2460,21 +2467,18 @@ static const void *evolve_fn_xf(int wpm, int ns) {
   return (const void *)evolve_kernel<MODEL, T16, 1, 1, XF>;
 }
 
-template <int MODEL, bool T16>
-static const void *evolve_fn(int wpm, int ns, bool xf) {
-  return xf ? evolve_fn_xf<MODEL, T16, true>(wpm, ns) : evolve_fn_xf<MODEL, T16, false>(wpm, ns);
-}
-
-// the kernel of a single solve: with the migration / crossover code only when
-// the solve takes either
+// the kernel of a single solve: with the migration / crossover code (built in
+// the translation unit of its own, cgo_kernels_xf.cu) only when the solve
+// takes either
 static const void *pick_evolve(const KInst &h, int wpm, int ns) {
-  const bool xf = h.islands > 1 || h.cross_q16 > 0;
+  if (h.islands > 1 || h.cross_q16 > 0) return pick_evolve_xf(h.model, h.tri16, wpm, ns);
   switch (h.model) {
-    case TSP: return h.tri16 ? evolve_fn<TSP, true>(wpm, ns, xf) : evolve_fn<TSP, false>(wpm, ns, xf);
-    case QAP: return evolve_fn<QAP, false>(wpm, ns, xf);
-    case CVRPTW: return evolve_fn<CVRPTW, false>(wpm, ns, xf);
-    case KNAPSACK: return evolve_fn<KNAPSACK, false>(wpm, ns, xf);
-    case GAP: return evolve_fn<GAP, false>(wpm, ns, xf);
+    case TSP:
+      return h.tri16 ? evolve_fn<TSP, true, false>(wpm, ns) : evolve_fn<TSP, false, false>(wpm, ns);
+    case QAP: return evolve_fn<QAP, false, false>(wpm, ns);
+    case CVRPTW: return evolve_fn<CVRPTW, false, false>(wpm, ns);
+    case KNAPSACK: return evolve_fn<KNAPSACK, false, false>(wpm, ns);
+    case GAP: return evolve_fn<GAP, false, false>(wpm, ns);
   }
   return nullptr;
 }
@@ -2587,5 +2591,31 @@ int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, int ns, bool stage
                                warps, wpm * ns, h.model);
   return L.total;
 }
+
+#else   // CGO_XF_UNIT: the single-solve kernels with migration and crossover
+template <int MODEL, bool T16>
+static const void *evolve_fn_xf(int wpm, int ns) {
+  if (ns == 2) {
+    if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2, true>;
+    if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 2, true>;
+    return (const void *)evolve_kernel<MODEL, T16, 1, 2, true>;
+  }
+  if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 1, true>;
+  if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 1, true>;
+  return (const void *)evolve_kernel<MODEL, T16, 1, 1, true>;
+}
+}  // namespace
+
+const void *pick_evolve_xf(int model, int tri16, int wpm, int ns) {
+  switch (model) {
+    case TSP: return tri16 ? evolve_fn_xf<TSP, true>(wpm, ns) : evolve_fn_xf<TSP, false>(wpm, ns);
+    case QAP: return evolve_fn_xf<QAP, false>(wpm, ns);
+    case CVRPTW: return evolve_fn_xf<CVRPTW, false>(wpm, ns);
+    case KNAPSACK: return evolve_fn_xf<KNAPSACK, false>(wpm, ns);
+    case GAP: return evolve_fn_xf<GAP, false>(wpm, ns);
+  }
+  return nullptr;
+}
+#endif  // CGO_XF_UNIT
 
 }  // namespace cgo

@@ -95,6 +95,38 @@ def test_batch512_full_run_sample(cgo):
         check_state(mix[i], params[i], probs[i].state(), probs[i].best(), "batch %d" % i)
 
 
+def test_tsp442_islands_crossover_full_run(cgo):
+    """The n=442 solve at 20,000 generations with every population step on:
+    4 islands with hybrid migration every 1,000 generations, crossover at
+    probability 0.1 per window, elite injection every 500 generations, and
+    3-opt beside the benchmark's operators."""
+    inst = I.tsp_clustered(442, 0)
+    p = params_for(inst, P=128, C=128, G=20000,
+                   op_mask=(1 << TO) | (1 << OR) | (1 << INS) | (1 << O.THREE_OPT),
+                   islands=4, migrate_period=1000, migrate_strategy=2, migrate_n=4,
+                   cross_q16=6554, elite_period=500)
+    prob = cgo.Problem(inst)
+    prob.solve(p, 3)
+    check_state(inst, p, prob.state(), prob.best(), "tsp442 islands+crossover")
+
+
+def test_batch_extra_operators_and_crossover_sample(cgo):
+    """A 64-instance slice of the batch mix at 5,000 generations with the
+    segment operators, 3-opt, crossover and ring migration enabled."""
+    mix = [dict(x, tag=i) for i, x in enumerate(I.batch_mix(512, 0)[:64])]
+    probs = [cgo.Problem(x) for x in mix]
+    params = []
+    for pr, x in zip(probs, mix):
+        q = pr.default_params()
+        extra = {I.TSP: 1 << O.THREE_OPT, I.KNAPSACK: 1 << O.SEGMENT, I.GAP: 1 << O.SEGMENT}
+        q.update(P=32, C=128, G=5000, cross_q16=20000, islands=4, migrate_period=500)
+        q["op_mask"] |= extra.get(x["model"], 0)
+        params.append(q)
+    cgo.solve_batch(probs, params, [7 + i for i in range(len(mix))])
+    for i in range(0, 64, 4):
+        check_state(mix[i], params[i], probs[i].state(), probs[i].best(), "batch %d" % i)
+
+
 def test_tsp_beyond_shared_memory(cgo):
     """n = 1,500: the int16 triangle (2.25 MB) does not fit shared memory and
     is read through L2; the search matches the oracle over a prefix."""
