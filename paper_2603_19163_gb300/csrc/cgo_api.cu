@@ -430,6 +430,9 @@ cgo_status check_sync_error(cgo_problem *p, cudaStream_t st) {
 cgo_status run_generations(cgo_problem *p, int64_t G, cudaStream_t st) {
   if (G == 0) return CGO_OK;
   if (p->g + G >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "generation index would exceed 2^32 - 2");
+  // crossover children need one scratch row per member
+  if (p->params.cross_q16 > 0 && p->params.population >= 2 && p->pool_cap < p->params.population)
+    return fail(CGO_ERR_STATE, "no crossover buffer for this population");
   KInst h = base_kinst(p);
   int warps = 0, wpm = 1, ns = 1;
   int64_t smem = 0;
@@ -922,6 +925,7 @@ cgo_status cgo_state_set(cgo_problem *p, const cgo_params *q, uint64_t seed, con
     if (!valid_solution(p, x)) return fail(CGO_ERR_INVALID, "state row %d is not a valid solution", r);
   }
   if ((s = ensure_state(p, q->population)) != CGO_OK) return s;
+  if ((s = ensure_pool(p, *q)) != CGO_OK) return s;
   const size_t sb = (size_t)P * p->len * 4;
   CUDA_TRY(copy_sync(p->d_cur, in->cur, sb, cudaMemcpyHostToDevice), "writing state");
   CUDA_TRY(copy_sync(p->d_bestsol, in->best_sol, sb, cudaMemcpyHostToDevice), "writing state");

@@ -518,6 +518,28 @@ def test_split_solve_and_checkpoint_resume(cgo, maker):
     assert_same_state(prob.state(), oracle_run(inst, p, 21, 43), "resume vs oracle")
 
 
+@pytest.mark.parametrize("maker", [lambda: I.tsp_uniform(28, 65), lambda: I.gap(30, 66, m=5),
+                                   lambda: I.cvrptw(15, 67, vehicles=4, capacity=80)])
+def test_split_and_resume_with_population_steps(cgo, maker):
+    """Islands, crossover, injection and the extra operators across launches
+    that end mid-window and a checkpoint restored on a fresh handle."""
+    inst = maker()
+    extra = [O.SEGMENT] if inst["model"] == 3 else [O.THREE_OPT]
+    base = [O.PERTURB] if inst["model"] == 3 else [SW, TO, INS, OR]
+    p = params_for(inst, P=12, C=48, G=11, U=4, elite_period=12, islands=3, migrate_period=8,
+                   migrate_strategy=2, migrate_n=2, cross_q16=40000, ops=base + extra)
+    prob = cgo.Problem(inst)
+    prob.solve(p, 23)
+    prob.solve_continue(7)
+    prob.solve_continue(13)
+    g = prob.state()
+    assert_same_state(g, oracle_run(inst, p, 23, 31), "split")
+    prob2 = cgo.Problem(inst)
+    prob2.set_state(p, 23, g)
+    prob2.solve_continue(10)
+    assert_same_state(prob2.state(), oracle_run(inst, p, 23, 41), "resume vs oracle")
+
+
 def test_best_is_the_elite(cgo):
     inst = I.tsp_uniform(35, 64)
     p = params_for(inst, P=10, C=64, G=50)
