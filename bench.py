@@ -221,8 +221,8 @@ def cpu_baseline(inst, cfg, desc, budget_s: float):
     O.solve(inst, p, 1, gens)
     dt = time.perf_counter() - t0
     evals = cfg["P"] * cfg["C"] * gens
-    # one host thread, on a quarter of the sample (same generations from 0)
-    g1 = max(2, gens // 4)
+    # one host thread, on an eighth of the sample (same generations from 0)
+    g1 = max(2, gens // 8)
     t0 = time.perf_counter()
     O.solve(inst, p, 1, g1, threads=1)
     dt1 = time.perf_counter() - t0
