@@ -29,7 +29,7 @@ class OrcInstance(ctypes.Structure):
                 ("vec0", _i32p), ("vec1", _i32p), ("vec2", _i32p), ("vec3", _i32p),
                 ("capacity", ctypes.c_int64), ("lb", ctypes.c_int32), ("ub", ctypes.c_int32),
                 ("penalty0", ctypes.c_int64), ("penalty1", ctypes.c_int64),
-                ("tag", ctypes.c_uint32)]
+                ("tag", ctypes.c_uint32), ("weight0", ctypes.c_int64), ("weight1", ctypes.c_int64)]
 
 
 class OrcParams(ctypes.Structure):
@@ -142,6 +142,8 @@ class Instance:
         s.ub = int(inst.get("ub", 0))
         s.penalty0 = int(inst.get("penalty0", 0))
         s.penalty1 = int(inst.get("penalty1", 0))
+        s.weight0 = int(inst.get("weight_distance", 0))
+        s.weight1 = int(inst.get("weight_vehicles", 0))
         s.tag = int(inst.get("tag", 0)) & 0xFFFFFFFF
         self.s = s
 

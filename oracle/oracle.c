@@ -195,7 +195,9 @@ static int64_t cost_cvrptw(const orc_instance *in, const int32_t *x) {
                 *svc = in->vec3;
   int64_t lcap = in->penalty0 > 0 ? in->penalty0 : 100;
   int64_t ltw = in->penalty1 > 0 ? in->penalty1 : 100;
-  int64_t dist = 0, capx = 0, late = 0;
+  /* [R30] weighted objectives (Sec. 6.8): distance and vehicles used */
+  int64_t wd = in->weight0 > 0 ? in->weight0 : 1, wv = in->weight1;
+  int64_t dist = 0, capx = 0, late = 0, used = 0;
   int32_t k = 0;
   while (k <= len) {
     /* one route: symbols until a separator or the end */
@@ -218,10 +220,11 @@ static int64_t cost_cvrptw(const orc_instance *in, const int32_t *x) {
       t += back;
       late += over(t - due[0]);
       capx += over(load - in->capacity);
+      used++;
     }
     k++; /* skip the separator (or step past the end) */
   }
-  return dist + lcap * capx + ltw * late;
+  return wd * dist + lcap * capx + ltw * late + wv * used;
 }
 
 int64_t orc_cost(const orc_instance *in, const int32_t *sol) {

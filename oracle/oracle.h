@@ -45,6 +45,7 @@ typedef struct {
   int32_t lb, ub;     /* integer-encoding bounds (GAP: 0 .. m-1) */
   int64_t penalty0, penalty1; /* 0 = default lambda */
   uint32_t tag;       /* instance tag (Philox counter word 1) */
+  int64_t weight0, weight1; /* CVRPTW objective weights: distance (0 = 1), vehicles used */
 } orc_instance;
 
 typedef struct {

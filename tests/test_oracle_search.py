@@ -74,7 +74,9 @@ def bf_gap(c, r, cap, lam):
     return best
 
 
-def bf_cvrptw(inst):
+def bf_cvrptw(inst, wd=1, wv=0):
+    """Brute-force optimum of the separator encoding; wd, wv weigh distance
+    and the vehicles used (routes that visit a customer)."""
     n, V = inst["n"], inst["vehicles"]
     d, dem, rdy, due, svc = (inst[k] for k in ("mat0", "vec0", "vec1", "vec2", "vec3"))
     Q = inst["capacity"]
@@ -88,10 +90,11 @@ def bf_cvrptw(inst):
             else:
                 cur.append(s + 1)
         routes.append(cur)
-        dist = excess = late = 0
+        dist = excess = late = used = 0
         for rt in routes:
             if not rt:
                 continue
+            used += 1
             t, load, prev = 0, 0, 0
             for c in rt:
                 dist += int(d[prev][c])
@@ -104,7 +107,7 @@ def bf_cvrptw(inst):
             t += int(d[prev][0])
             late += max(0, t - int(due[0]))
             excess += max(0, load - Q)
-        cost = dist + 100 * excess + 100 * late
+        cost = wd * dist + 100 * excess + 100 * late + wv * used
         best = cost if best is None else min(best, cost)
     return best
 
@@ -167,6 +170,22 @@ def test_segment_operators_alone_reach_bruteforce_optimum(seed, model):
         inst = I.gap(7, 103, m=3)
         opt = bf_gap(inst["mat0"], inst["mat1"], inst["vec0"], 1 + int(inst["mat0"].max()))
     p = equal_weights(O.default_params(inst), [O.SEGMENT])
+    p.update(P=8, C=32)
+    st = _run(inst, p, seed, 400)
+    assert st["best_cost"].min() == opt
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+@pytest.mark.parametrize("wd,wv", [(1, 10 ** 6), (10 ** 6, 1), (2, 35)])
+def test_cvrptw_weighted_objectives_reach_bruteforce_optimum(seed, wd, wv):
+    """Weighted distance and vehicle count (Sec. 6.8): a vehicle weight above
+    any distance difference orders vehicles first (lexicographic), a distance
+    weight above any vehicle count orders distance first; both and a mixed
+    weighting reach the brute-force optimum of the weighted cost."""
+    inst = dict(I.cvrptw(5, 104, vehicles=3, capacity=60, box=60, horizon=300, width=80),
+                weight_distance=wd, weight_vehicles=wv)
+    opt = bf_cvrptw(inst, wd, wv)
+    p = O.default_params(inst)
     p.update(P=8, C=32)
     st = _run(inst, p, seed, 400)
     assert st["best_cost"].min() == opt
