@@ -104,6 +104,11 @@ typedef struct {
   int32_t pointers_on_device;  /* 0: host pointers; 1: device pointers (e.g. a
                                   torch tensor's data_ptr) on the current device */
   uint32_t instance_tag;       /* word 1 of every Philox counter of this instance */
+  /* CVRPTW objective weights (Sec. 6.8, weighted mode; a weight above every
+     difference of the lower-priority terms gives the lexicographic order):
+     cost = weight_distance * distance + penalties + weight_vehicles * routes
+     that visit a customer.  0 = default (1 and 0); other models ignore them. */
+  int64_t weight_distance, weight_vehicles;
 } cgo_problem_desc;
 
 /* Search parameters.  Fixed point: Q16 weights (65536 = 1.0), Q32.32

@@ -37,7 +37,8 @@ class cgo_problem_desc(ctypes.Structure):
                 ("capacity", ctypes.c_int64), ("lb", ctypes.c_int32), ("ub", ctypes.c_int32),
                 ("m", ctypes.c_int32), ("vehicles", ctypes.c_int32),
                 ("penalty0", ctypes.c_int64), ("penalty1", ctypes.c_int64),
-                ("pointers_on_device", ctypes.c_int32), ("instance_tag", ctypes.c_uint32)]
+                ("pointers_on_device", ctypes.c_int32), ("instance_tag", ctypes.c_uint32),
+                ("weight_distance", ctypes.c_int64), ("weight_vehicles", ctypes.c_int64)]
 
 
 class cgo_params(ctypes.Structure):
@@ -232,6 +233,8 @@ class Problem:
         d.vehicles = int(inst.get("vehicles", 0))
         d.penalty0 = int(inst.get("penalty0", 0))
         d.penalty1 = int(inst.get("penalty1", 0))
+        d.weight_distance = int(inst.get("weight_distance", 0))
+        d.weight_vehicles = int(inst.get("weight_vehicles", 0))
         d.pointers_on_device = 1 if on_device else 0
         d.instance_tag = int(inst.get("tag", 0)) & 0xFFFFFFFF
         h = ctypes.c_void_p()

@@ -307,6 +307,8 @@ KInst base_kinst(const cgo_problem *p) {
   h.capacity = p->capacity;
   h.lam0 = p->lam0;
   h.lam1 = p->lam1;
+  h.wdist = p->wdist;
+  h.wveh = p->wveh;
   h.lb = p->lb;
   h.ub = p->ub;
   h.tag = p->tag;
@@ -664,11 +666,15 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
       if (d->penalty0 < 0 || d->penalty1 < 0) return bail(fail(CGO_ERR_INVALID, "penalties < 0"));
       p->lam0 = d->penalty0 > 0 ? d->penalty0 : 100;
       p->lam1 = d->penalty1 > 0 ? d->penalty1 : 100;
+      if (d->weight_distance < 0 || d->weight_vehicles < 0)
+        return bail(fail(CGO_ERR_INVALID, "objective weights < 0"));
+      p->wdist = d->weight_distance > 0 ? d->weight_distance : 1;
+      p->wveh = d->weight_vehicles;
       // bound every route quantity: time, lateness, distance, load
       const double maxd = (double)absmax(a), tmax = (double)absmax(v[1]) + (double)N * (maxd + (double)absmax(v[3]));
       const double late = (double)N * (tmax + (double)absmax(v[2]));
       if ((double)p->lam1 * late + (double)p->lam0 * ((double)abssum(v[0]) + std::fabs((double)d->capacity) * N) +
-              (double)(len + 1) * maxd > kLimit)
+              (double)p->wdist * (double)(len + 1) * maxd + (double)p->wveh * (double)d->vehicles > kLimit)
         return bail(fail(CGO_ERR_INVALID, "CVRPTW data could overflow an int64 cost"));
       // route quantities (time, lateness, distance, load) fit in int32?
       p->cv32 = (late < 2.0e9 && (double)abssum(v[0]) < 2.0e9 && (double)N * maxd < 2.0e9) ? 1 : 0;

@@ -46,6 +46,7 @@ struct KInst {
   // instance
   int32_t model, n, len, m;
   int64_t capacity, lam0, lam1;
+  int64_t wdist, wveh;  // CVRPTW objective weights (distance, vehicles used)
   int32_t lb, ub;
   uint32_t tag;
   int32_t tri16;              // TSP triangle stored as int16

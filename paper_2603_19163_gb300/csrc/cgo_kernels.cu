@@ -127,6 +127,7 @@ struct View {
   const int32_t *rd, *dem, *rdy, *due, *svc;  // CVRPTW: travel (n+1)^2, vectors n+1
   const int4 *node;                           // CVRPTW: {ready, due, service, demand}
   long long lam1;
+  long long wd, wv;  // CVRPTW objective weights (distance, vehicles used)
   bool cv32;
   bool t3;   // 3-opt enabled for this instance
   bool seg;  // seg_flip / seg_reset enabled for this instance
@@ -360,7 +361,8 @@ __device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
 // sequence (symbols < n are customers 1..n, others end a route); R acts as
 // a separator.  Per route from the depot at t = 0: t = max(t + d, ready),
 // late += max(0, t - due), t += service; back at the depot t += d and
-// late += max(0, t - due_0); empty routes cost nothing.
+// late += max(0, t - due_0); empty routes cost nothing.  A route that visits
+// a customer costs wd * distance + penalties + wv (R30's objective weights).
 // Up to three jumps (from separator position jf_i to separator position
 // jt_i, in increasing order) leave out whole routes known to cancel.
 struct Jumps {
@@ -390,7 +392,8 @@ __device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int 
     load += sep ? (Q)0 : (Q)nd.w;
     if (sep) {
       if (prev != 0)
-        total += (long long)dist + X.lam0 * overp((long long)load - X.cap) + X.lam1 * (long long)late;
+        total += X.wd * (long long)dist + X.lam0 * overp((long long)load - X.cap) +
+                 X.lam1 * (long long)late + X.wv;
       t = load = dist = late = 0;
       prev = 0;
       if (q == J.f0) {
@@ -2004,6 +2007,8 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.t3 = ((I.enabled >> THREE_OPT) & 1u) != 0;
   X.seg = ((I.enabled >> SEGMENT) & 1u) != 0;
   X.lam1 = I.lam1;
+  X.wd = I.wdist;
+  X.wv = I.wveh;
   if (!staged) return X;
   auto copy = [&](const void *src, int64_t bytes, int64_t off) {
     const int4 *s = (const int4 *)src;
@@ -2160,6 +2165,8 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
       X.cap = I.capacity;
       X.lam0 = I.lam0;
       X.lam1 = I.lam1;
+      X.wd = I.wdist;
+      X.wv = I.wveh;
       X.rd = I.mat0;
       X.node = I.node;
       return cvrptw_routes(X, [&](int q) { return (int)x[q]; }, 0, I.len, false);

@@ -69,6 +69,9 @@ def mixed_batch():
     items.append((dict(I.knapsack(90, 262), tag=52), dict(P=7, C=48, G=21, U=7, cross_q16=65536)))
     items.append((dict(I.cvrptw(16, 263, vehicles=4, capacity=80), tag=53),
                   dict(P=6, C=48, G=20, U=4, cross_q16=65536)))
+    # weighted CVRPTW objectives (vehicles first)
+    items.append((dict(I.cvrptw(18, 264, vehicles=5, capacity=90), tag=54, weight_vehicles=10 ** 6),
+                  dict(P=6, C=48, G=22)))
     return items
 
 

@@ -331,6 +331,27 @@ def test_cvrptw(cgo, n, V, kw):
     assert_same_state(g, o, "cvrptw n=%d V=%d" % (n, V))
 
 
+@pytest.mark.parametrize("wd,wv", [(1, 10 ** 6), (10 ** 6, 1), (3, 40)])
+@pytest.mark.parametrize("ns", [1, 2])
+def test_cvrptw_weighted_objectives(cgo, wd, wv, ns):
+    """Distance and vehicles used weighted (Sec. 6.8): vehicles first,
+    distance first and a mixed weighting, every permutation operator."""
+    for n, V in ((8, 3), (30, 6)):
+        inst = dict(I.cvrptw(n, 340 + n, vehicles=V, capacity=70), weight_distance=wd,
+                    weight_vehicles=wv)
+        p = params_for(inst, P=8, C=64, G=33, U=4, ops=[SW, TO, INS, OR, TH], elite_period=8)
+        _, g, o = run_both(cgo, inst, p, 17, ns=ns)
+        assert_same_state(g, o, "n %d wd %d wv %d ns %d" % (n, wd, wv, ns))
+
+
+def test_cvrptw_weights_validated(cgo):
+    base = I.cvrptw(6, 349, vehicles=2, capacity=60)
+    for bad in (dict(weight_distance=-1), dict(weight_vehicles=-5), dict(weight_distance=1 << 58)):
+        with pytest.raises(cgo.CgoError) as e:
+            cgo.Problem(dict(base, **bad))
+        assert e.value.status == cgo.ERR_INVALID, bad
+
+
 @pytest.mark.parametrize("C,wpm,kw", [(150, 1, None), (150, 2, (20000, 30000, 15536)),
                                        (100, 4, None), (300, 1, (0, 0, 65536)), (256, 1, (0, 65536, 0))])
 def test_cvrptw_candidates_per_lane(cgo, C, wpm, kw):

@@ -48,6 +48,9 @@ def request_mix():
         (dict(I.gap(35, 311, m=5), tag=12), dict(P=6, C=48, G=26, ops=[O.PERTURB, O.SEGMENT])),
         # crossover
         (dict(I.tsp_uniform(35, 312), tag=13), dict(P=6, C=48, G=24, U=4, cross_q16=50000)),
+        # weighted CVRPTW objectives
+        (dict(I.cvrptw(16, 313, vehicles=4, capacity=80), tag=14, weight_distance=2,
+              weight_vehicles=300), dict(P=5, C=48, G=21)),
     ]
 
 
