@@ -988,7 +988,7 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
   std::vector<DevAos> a0((size_t)count);
   std::vector<int> bucket_of((size_t)count);
   struct Bucket {
-    int model, tri16, wpm, warps;
+    int model, tri16, xf, wpm, warps;
     int64_t smem;
     std::vector<int> members;
   };
@@ -1018,12 +1018,13 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
     if ((s = batch_shape(p, per[i], h, &wpm, &warps, &need, &cls)) != CGO_OK)
       return fail(s, "problem %d: %s", i, cgo_last_error());
     int b = -1;
+    const int xf = takes_xf(h);
     for (size_t k = 0; k < buckets.size(); ++k)
-      if (buckets[k].model == p->model && buckets[k].tri16 == p->tri16 && buckets[k].wpm == wpm &&
-          buckets[k].warps == warps && buckets[k].smem == cls)
+      if (buckets[k].model == p->model && buckets[k].tri16 == p->tri16 && buckets[k].xf == xf &&
+          buckets[k].wpm == wpm && buckets[k].warps == warps && buckets[k].smem == cls)
         b = (int)k;
     if (b < 0) {
-      buckets.push_back(Bucket{p->model, p->tri16, wpm, warps, cls, {}});
+      buckets.push_back(Bucket{p->model, p->tri16, xf, wpm, warps, cls, {}});
       b = (int)buckets.size() - 1;
     }
     buckets[(size_t)b].members.push_back(i);
@@ -1101,7 +1102,7 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
   std::vector<int> grids(nb, 0);
   for (size_t b = 0; b < nb && e == cudaSuccess; ++b) {
     const Bucket &bk = buckets[b];
-    const int per_sm = batch_ctas_per_sm(bk.model, bk.tri16, bk.warps, bk.wpm, bk.smem);
+    const int per_sm = batch_ctas_per_sm(bk.model, bk.tri16, bk.xf, bk.warps, bk.wpm, bk.smem);
     if (per_sm <= 0) {
       cleanup();
       return fail(CGO_ERR_UNSUPPORTED, "no CTA of the batched kernel fits (model %d)", bk.model);
@@ -1120,7 +1121,7 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
         ce = cudaStreamWaitEvent(side[b], fork, 0);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(d_next + b, 0, sizeof(int), side[b]);
         if (ce == cudaSuccess)
-          ce = launch_batch(bk.model, bk.tri16, d_k, d_lists + list_off[b], d_counts + b,
+          ce = launch_batch(bk.model, bk.tri16, bk.xf, d_k, d_lists + list_off[b], d_counts + b,
                             d_next + b, bk.warps, bk.wpm, bk.smem, grids[b], slice,
                             probs[0]->timeout_ns, side[b]);
         if (ce == cudaSuccess) ce = cudaEventRecord(evs[b], side[b]);

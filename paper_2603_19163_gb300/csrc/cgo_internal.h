@@ -107,10 +107,15 @@ cudaError_t launch_tsp_check(const int32_t *d_mat, int n, uint32_t *d_flags, cud
 cudaError_t launch_copy_elite(const DevAos *d_aos, const int32_t *d_bestsol, int len,
                               int32_t *out_sol, int64_t *out_cost, cudaStream_t st);
 cudaError_t launch_init_batch(const KInst *d_insts, const DevAos *d_a0s, int count, cudaStream_t st);
-int batch_ctas_per_sm(int model, int tri16, int warps, int wpm, int64_t smem_bytes);
-cudaError_t launch_batch(int model, int tri16, const KInst *d_insts, const int *d_list,
+// batched kernels: xf = 1 for instances that take island migration or crossover
+int batch_ctas_per_sm(int model, int tri16, int xf, int warps, int wpm, int64_t smem_bytes);
+cudaError_t launch_batch(int model, int tri16, int xf, const KInst *d_insts, const int *d_list,
                          const int *d_count, int *d_next, int warps, int wpm, int64_t smem_bytes,
                          int grid, int64_t slice, uint64_t timeout_ns, cudaStream_t st);
+// the batched kernel with island migration and crossover (cgo_kernels_xf.cu)
+const void *pick_batch_xf(int model, int tri16, int wpm);
+// whether an instance's search takes island migration or crossover
+inline int takes_xf(const KInst &h) { return (h.islands > 1 || h.cross_q16 > 0) ? 1 : 0; }
 int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged);
 // shared-memory needs of the evolve kernel
 int64_t smem_per_warp(const KInst &h);

@@ -2090,7 +2090,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
 // loop over them) for up to `slice` generations, with CTA-local window
 // barriers; the instance's scalars are updated in place.  Instances that
 // have reached their generation budget are skipped.
-template <int MODEL, bool T16, int WPM>
+template <int MODEL, bool T16, int WPM, bool XF>
 __global__ void __launch_bounds__(kMaxWarps * 32, 1)
     batch_kernel(const KInst *__restrict__ insts, const int *__restrict__ list,
                  const int *__restrict__ count_ptr, int *next, int warps, int64_t slice,
@@ -2127,7 +2127,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
       const int groups = warps / WPM;
       const Layout Lo =
           make_layout(staged ? I.shared_bytes : 0, I.len, I.m, I.P, warps, WPM, I.model);
-      evolve_members<MODEL, T16, WPM, 1, true>(I, X, smem, Lo, 0, I.P, warps, timeout_ns);
+      evolve_members<MODEL, T16, WPM, 1, XF>(I, X, smem, Lo, 0, I.P, warps, timeout_ns);
       (void)groups;
     }
     __syncthreads();
@@ -2478,7 +2478,7 @@ static const void *evolve_fn(int wpm, int ns) {
 // the translation unit of its own, cgo_kernels_xf.cu) only when the solve
 // takes either
 static const void *pick_evolve(const KInst &h, int wpm, int ns) {
-  if (h.islands > 1 || h.cross_q16 > 0) return pick_evolve_xf(h.model, h.tri16, wpm, ns);
+  if (takes_xf(h)) return pick_evolve_xf(h.model, h.tri16, wpm, ns);
   switch (h.model) {
     case TSP:
       return h.tri16 ? evolve_fn<TSP, true, false>(wpm, ns) : evolve_fn<TSP, false, false>(wpm, ns);
@@ -2547,12 +2547,15 @@ cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int ns, int
 
 template <int MODEL, bool T16>
 static const void *batch_fn(int wpm) {
-  if (wpm == 4) return (const void *)batch_kernel<MODEL, T16, 4>;
-  if (wpm == 2) return (const void *)batch_kernel<MODEL, T16, 2>;
-  return (const void *)batch_kernel<MODEL, T16, 1>;
+  if (wpm == 4) return (const void *)batch_kernel<MODEL, T16, 4, false>;
+  if (wpm == 2) return (const void *)batch_kernel<MODEL, T16, 2, false>;
+  return (const void *)batch_kernel<MODEL, T16, 1, false>;
 }
 
-static const void *pick_batch(int model, int tri16, int wpm) {
+// the batched kernel of a bucket: with the migration / crossover code only
+// for instances that take either
+static const void *pick_batch(int model, int tri16, int xf, int wpm) {
+  if (xf) return pick_batch_xf(model, tri16, wpm);
   switch (model) {
     case TSP: return tri16 ? batch_fn<TSP, true>(wpm) : batch_fn<TSP, false>(wpm);
     case QAP: return batch_fn<QAP, false>(wpm);
@@ -2563,8 +2566,8 @@ static const void *pick_batch(int model, int tri16, int wpm) {
   return nullptr;
 }
 
-int batch_ctas_per_sm(int model, int tri16, int warps, int wpm, int64_t smem_bytes) {
-  const void *fn = pick_batch(model, tri16, wpm);
+int batch_ctas_per_sm(int model, int tri16, int xf, int warps, int wpm, int64_t smem_bytes) {
+  const void *fn = pick_batch(model, tri16, xf, wpm);
   if (!fn) return 0;
   if (open_smem(fn) != cudaSuccess) return 0;
   int per_sm = 0;
@@ -2574,10 +2577,10 @@ int batch_ctas_per_sm(int model, int tri16, int warps, int wpm, int64_t smem_byt
   return per_sm;
 }
 
-cudaError_t launch_batch(int model, int tri16, const KInst *d_insts, const int *d_list,
+cudaError_t launch_batch(int model, int tri16, int xf, const KInst *d_insts, const int *d_list,
                          const int *d_count, int *d_next, int warps, int wpm, int64_t smem_bytes,
                          int grid, int64_t slice, uint64_t timeout_ns, cudaStream_t st) {
-  const void *fn = pick_batch(model, tri16, wpm);
+  const void *fn = pick_batch(model, tri16, xf, wpm);
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = open_smem(fn);
   if (e != cudaSuccess) return e;
@@ -2599,7 +2602,7 @@ int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, int ns, bool stage
   return L.total;
 }
 
-#else   // CGO_XF_UNIT: the single-solve kernels with migration and crossover
+#else   // CGO_XF_UNIT: the single-solve and batched kernels with migration and crossover
 template <int MODEL, bool T16>
 static const void *evolve_fn_xf(int wpm, int ns) {
   if (ns == 2) {
@@ -2611,7 +2614,25 @@ static const void *evolve_fn_xf(int wpm, int ns) {
   if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 1, true>;
   return (const void *)evolve_kernel<MODEL, T16, 1, 1, true>;
 }
+
+template <int MODEL, bool T16>
+static const void *batch_fn_xf(int wpm) {
+  if (wpm == 4) return (const void *)batch_kernel<MODEL, T16, 4, true>;
+  if (wpm == 2) return (const void *)batch_kernel<MODEL, T16, 2, true>;
+  return (const void *)batch_kernel<MODEL, T16, 1, true>;
+}
 }  // namespace
+
+const void *pick_batch_xf(int model, int tri16, int wpm) {
+  switch (model) {
+    case TSP: return tri16 ? batch_fn_xf<TSP, true>(wpm) : batch_fn_xf<TSP, false>(wpm);
+    case QAP: return batch_fn_xf<QAP, false>(wpm);
+    case CVRPTW: return batch_fn_xf<CVRPTW, false>(wpm);
+    case KNAPSACK: return batch_fn_xf<KNAPSACK, false>(wpm);
+    case GAP: return batch_fn_xf<GAP, false>(wpm);
+  }
+  return nullptr;
+}
 
 const void *pick_evolve_xf(int model, int tri16, int wpm, int ns) {
   switch (model) {

@@ -46,7 +46,7 @@ struct Req {
 };
 
 struct SBucket {
-  int model, tri16, wpm, warps;
+  int model, tri16, xf, wpm, warps;
   int64_t smem;
   int grid;
 };
@@ -120,7 +120,7 @@ cudaError_t capture_slice(cgo_server *S) {
       ce = cudaStreamWaitEvent(S->side[b], S->evs[kMaxBuckets], 0);
       if (ce == cudaSuccess) ce = cudaMemsetAsync(S->d_next + b, 0, sizeof(int), S->side[b]);
       if (ce == cudaSuccess)
-        ce = launch_batch(bk.model, bk.tri16, S->d_k, S->d_lists + b * S->cfg.max_slots,
+        ce = launch_batch(bk.model, bk.tri16, bk.xf, S->d_k, S->d_lists + b * S->cfg.max_slots,
                           S->d_counts + b, S->d_next + b, bk.warps, bk.wpm, bk.smem, bk.grid,
                           S->cfg.slice_generations, 10ull * 1000 * 1000 * 1000, S->side[b]);
       if (ce == cudaSuccess) ce = cudaEventRecord(S->evs[b], S->side[b]);
@@ -136,16 +136,17 @@ cudaError_t capture_slice(cgo_server *S) {
 }
 
 // bucket of a request (created on first use; the graph is recaptured then)
-int bucket_for(cgo_server *S, int model, int tri16, int wpm, int warps, int64_t smem) {
+int bucket_for(cgo_server *S, int model, int tri16, int xf, int wpm, int warps, int64_t smem) {
   for (size_t b = 0; b < S->buckets.size(); ++b) {
     const SBucket &k = S->buckets[b];
-    if (k.model == model && k.tri16 == tri16 && k.wpm == wpm && k.warps == warps && k.smem == smem)
+    if (k.model == model && k.tri16 == tri16 && k.xf == xf && k.wpm == wpm && k.warps == warps &&
+        k.smem == smem)
       return (int)b;
   }
   if ((int)S->buckets.size() >= kMaxBuckets) return -1;
-  const int per_sm = batch_ctas_per_sm(model, tri16, warps, wpm, smem);
+  const int per_sm = batch_ctas_per_sm(model, tri16, xf, warps, wpm, smem);
   if (per_sm <= 0) return -1;
-  S->buckets.push_back(SBucket{model, tri16, wpm, warps, smem,
+  S->buckets.push_back(SBucket{model, tri16, xf, wpm, warps, smem,
                                std::max(1, std::min(S->cfg.max_slots, per_sm * S->sms))});
   S->dirty = true;
   return (int)S->buckets.size() - 1;
@@ -215,7 +216,7 @@ void server_loop(cgo_server *S) {
       int wpm = 1, warps = 1;
       int64_t need = 0, cls = 0;
       if (batch_shape(p, r->params, h, &wpm, &warps, &need, &cls) != CGO_OK ||
-          (r->bucket = bucket_for(S, p->model, p->tri16, wpm, warps, cls)) < 0) {
+          (r->bucket = bucket_for(S, p->model, p->tri16, takes_xf(h), wpm, warps, cls)) < 0) {
         fail_all(S, CGO_ERR_UNSUPPORTED, "no batched launch shape for a request");
         return;
       }
