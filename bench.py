@@ -54,6 +54,10 @@ def workload(name: str):
         inst = I.qap_grid(64, 0)
         cfg = dict(P=256, C=128, G=100000, op_mask=1, w_op=[65536, 0, 0, 0, 0, 0, 0, 0])
         desc = "qap64-grid P=256 C=128 G=100000 ops=swap"
+    elif name == "cvrptw100":
+        inst = I.cvrptw(100, 0)
+        cfg = dict(P=32, C=128, G=20000)
+        desc = "cvrptw100-solomon-r P=32 C=128 G=20000 V=25 Q=200"
     elif name == "serve":
         return None, dict(P=32, C=128, G=20000), "serve-poisson200x60s mix+15%cvrptw P=32 C=128 G=20000"
     elif name == "batch512":
@@ -91,6 +95,23 @@ def solve_variant(args, model: int, cfg: dict, desc: str):
         cfg["cross_q16"] = args.cross
         desc += " cross=%.3f" % (args.cross / 65536.0)
     return cfg, desc
+
+
+def cvrptw_objectives(inst: dict, sol) -> dict:
+    """Travel distance and vehicles used by a separator-encoded CVRPTW
+    solution (for the report; the search's own cost adds the penalties)."""
+    n, d = int(inst["n"]), np.asarray(inst["mat0"])
+    dist, used, prev = 0, 0, 0
+    for s in list(sol) + [n]:
+        if s >= n:
+            if prev:
+                dist += int(d[prev][0])
+                used += 1
+            prev = 0
+        else:
+            dist += int(d[prev][s + 1])
+            prev = s + 1
+    return {"distance": dist, "vehicles": used}
 
 
 def extra_ops_mask(model: int, extra: str) -> int:
@@ -172,6 +193,10 @@ def run_reference(args, rank, world):
         insts = [dict(x, tag=i) for i, x in enumerate(I.batch_mix(512, 0))][::64]
         desc += " (oracle on every 64th instance)"
     else:
+        if args.cvrptw_weights and inst["model"] == I.CVRPTW:
+            wd, wv = (int(x) for x in args.cvrptw_weights.split(","))
+            inst = dict(inst, weight_distance=wd, weight_vehicles=wv)
+            desc += " weights=(%d,%d)" % (wd, wv)
         insts = [inst]
         cfg, desc = solve_variant(args, inst["model"], cfg, desc)
     plist = []
@@ -254,6 +279,8 @@ def main():
     ap.add_argument("--extra-ops", default="",
                     help="enable operators beyond the default mask where they apply: "
                          "'three_opt' (TSP, CVRPTW), 'segment' (seg_flip / seg_reset: knapsack, GAP)")
+    ap.add_argument("--cvrptw-weights", default="",
+                    help="cvrptw100: objective weights 'distance,vehicles' (0,0 = distance only)")
     ap.add_argument("--cross", type=int, default=0,
                     help="crossover probability per member and AOS window, Q16 (0 = off)")
     ap.add_argument("--islands", default="",
@@ -299,6 +326,10 @@ def main():
         cfg["G"] = args.generations
         desc = desc.replace("G=", "G(full)=") + " G=%d" % cfg["G"]
     inst = dict(inst, tag=0)
+    if args.cvrptw_weights and inst["model"] == I.CVRPTW:
+        wd, wv = (int(x) for x in args.cvrptw_weights.split(","))
+        inst.update(weight_distance=wd, weight_vehicles=wv)
+        desc += " weights=(%d,%d)" % (wd, wv)
     seed = 1 + rank
     stream = torch.cuda.Stream()
     cfg, desc = solve_variant(args, inst["model"], cfg, desc)
@@ -353,7 +384,8 @@ def main():
 
     # end to end through the public API: host arrays in, best solution out
     e2e_ms = []
-    h2d = int(inst["mat0"].nbytes)
+    h2d = sum(int(np.asarray(inst[k]).nbytes) for k in ("mat0", "mat1", "vec0", "vec1", "vec2", "vec3")
+              if inst.get(k) is not None)
     d2h = 0
     for _ in range(max(1, min(args.steps, 3))):
         barrier()
@@ -373,7 +405,12 @@ def main():
     if rank == 0:
         kms = sum(kern_ms) / len(kern_ms)
         evals_launch = cfg["P"] * cfg["C"] * cfg["G"]
-        roof = roofline(evals_launch, kms, prob, clocks)
+        cv = inst["model"] == I.CVRPTW
+        # the roofline model covers the TSP and QAP deltas; a CVRPTW delta is a
+        # route walk of data-dependent length (reported without one)
+        roof = None if cv else roofline(evals_launch, kms, prob, clocks)
+        uk = prob.state()["u_k"]
+        ek = (uk[0] + 2 * uk[1] + 3 * uk[2]) / max(1, sum(uk))
         line = {"metric": "move_evals_per_s", "value": value, "unit": "evals/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -390,12 +427,13 @@ def main():
                            "gens_per_s": cfg["G"] / (total_ms / args.steps / 1000.0),
                            # operator applications: each evaluation applies k
                            # operators, E[k] from the run's last K counts
-                           "operator_applications_per_s":
-                               value * roof["ops_per_eval_steps"]},
+                           "operator_applications_per_s": value * ek},
                 "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
                 "clocks": clocks, "roofline": roof}
+        if cv:
+            line["config"]["elite_objectives"] = cvrptw_objectives(inst, prob.best()[0])
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(inst, cfg, desc, args.cpu_budget)
         print(json.dumps(line), flush=True)
