@@ -409,8 +409,11 @@ def main():
         # the roofline model covers the TSP and QAP deltas; a CVRPTW delta is a
         # route walk of data-dependent length (reported without one)
         roof = None if cv else roofline(evals_launch, kms, prob, clocks)
+        # mean steps per candidate: the roofline's figure (the open window's K
+        # counts, 1.25 when the run ends on a window boundary)
         uk = prob.state()["u_k"]
-        ek = (uk[0] + 2 * uk[1] + 3 * uk[2]) / max(1, sum(uk))
+        ek = roof["ops_per_eval_steps"] if roof else (
+            (uk[0] + 2 * uk[1] + 3 * uk[2]) / sum(uk) if sum(uk) else 1.25)
         line = {"metric": "move_evals_per_s", "value": value, "unit": "evals/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
