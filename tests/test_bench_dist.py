@@ -54,3 +54,45 @@ def test_reference_arm_under_torchrun_runs_on_rank0_only():
     import json
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+# ------------------------------------------------------ bench option helpers
+def test_extra_operator_masks_per_model():
+    import bench
+    import instances as I
+    assert bench.extra_ops_mask(I.TSP, "three_opt,segment") == 1 << bench.O_THREE_OPT
+    assert bench.extra_ops_mask(I.CVRPTW, "three_opt") == 1 << bench.O_THREE_OPT
+    assert bench.extra_ops_mask(I.QAP, "three_opt") == 0          # the QAP path is swap-only
+    assert bench.extra_ops_mask(I.KNAPSACK, "segment,three_opt") == 1 << bench.O_SEGMENT
+    assert bench.extra_ops_mask(I.GAP, "segment") == 1 << bench.O_SEGMENT
+    assert bench.extra_ops_mask(I.TSP, "") == 0
+    with pytest.raises(SystemExit):
+        bench.extra_ops_mask(I.TSP, "two_and_a_half_opt")
+
+
+def test_solve_variant_applies_to_both_arms():
+    import argparse
+    import bench
+    import instances as I
+    args = argparse.Namespace(init_oversample=4, init_heuristic=1, islands="4,1000,2,3",
+                              extra_ops="three_opt", cross=6554)
+    cfg, desc = bench.solve_variant(args, I.TSP, dict(P=128, C=128, G=10), "w")
+    assert cfg["init_oversample"] == 4 and cfg["init_heuristic"] == 1
+    assert (cfg["islands"], cfg["migrate_period"], cfg["migrate_strategy"], cfg["migrate_n"]) == (4, 1000, 2, 3)
+    assert cfg["extra_mask"] == 1 << bench.O_THREE_OPT and cfg["cross_q16"] == 6554
+    assert "islands=4" in desc and "hybrid-3" in desc and "cross=0.100" in desc
+    none = argparse.Namespace(init_oversample=1, init_heuristic=0, islands="", extra_ops="", cross=0)
+    cfg2, desc2 = bench.solve_variant(none, I.TSP, dict(P=1), "w")
+    assert cfg2 == dict(P=1) and desc2 == "w"
+
+
+def test_cvrptw_objectives_of_a_separator_sequence():
+    import numpy as np
+    import bench
+    # depot 0, customers 1..3; symbols 0..2 are customers, 3 and 4 separators
+    d = np.array([[0, 10, 20, 15], [10, 0, 12, 25], [20, 12, 0, 8], [15, 25, 8, 0]], np.int32)
+    inst = dict(n=3, mat0=d)
+    # routes (1, 2) and (3), one empty route
+    assert bench.cvrptw_objectives(inst, [0, 1, 3, 2, 4]) == {"distance": 42 + 30, "vehicles": 2}
+    assert bench.cvrptw_objectives(inst, [3, 4, 2, 0, 1]) == {"distance": 15 + 25 + 12 + 20,
+                                                             "vehicles": 1}
