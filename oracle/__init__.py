@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(OrcState)]
             L.orc_crossover.restype = i32
             L.orc_ox.argtypes = [_i32p, _i32p, i32, i32, i32, _i32p]
+            L.orc_row_move.argtypes = [ctypes.POINTER(OrcInstance), i32, u32, u32, _i32p, i32]
+            L.orc_row_move.restype = i32
             L.orc_heuristic_perms.argtypes = [ctypes.POINTER(OrcInstance), _i32p]
             L.orc_heuristic_perms.restype = i32
             L.orc_run.argtypes = [ctypes.POINTER(OrcInstance), ctypes.POINTER(OrcParams), u64,
@@ -215,6 +217,18 @@ def migrate(params: dict, state: dict) -> dict:
     out = dict(state)
     out.update({k: v.copy() for k, v in arrays.items()})
     return out
+
+
+ROW_SWAP, ROW_MERGE, ROW_SPLIT = range(3)
+
+
+def row_move(inst: dict, kind: int, a: int, b: int, sol) -> np.ndarray:
+    """A row operator (row_swap / row_merge / row_split) on a CVRPTW solution."""
+    I = Instance(inst)
+    s = np.ascontiguousarray(np.asarray(sol, dtype=np.int32).copy())
+    if lib().orc_row_move(I.ref, kind, a, b, s.ctypes.data_as(_i32p), len(s)) != 0:
+        raise ValueError("row operators need a CVRPTW instance")
+    return s
 
 
 def ox(A, B, lo: int, hi: int) -> np.ndarray:

@@ -770,6 +770,82 @@ int32_t orc_migrate(const orc_params *pr, orc_state *st) {
  * The child's cost is evaluated in full; it replaces A under the Metropolis
  * rule [R7] at the current temperature with the variate R.r3, and lowers
  * p's best like an accepted move. */
+/* [R31] row operators (Table "operators", row level; the paper names
+ * row_swap, row_split and row_merge and says nothing more).  Rows are the V
+ * routes of the separator encoding: route r spans [b_r, e_r) with b_0 = 0,
+ * e_r = the r-th separator's position (e_(V-1) = len), b_r = e_(r-1) + 1.
+ *   row_swap:  r1 = pos(a, V), r2 = pos(b, V-1) stepped over r1; the two
+ *              routes' contents exchange places.
+ *   row_merge: r = pos(a, V-1); the separator ending route r moves to the
+ *              end of route r+1, so r takes r+1's customers and an empty
+ *              route follows it.
+ *   row_split: r = pos(a, V); with c >= 2 customers on r and an empty route
+ *              z (the lowest-index one), the separator that closes z (or,
+ *              for the last route, opens it) moves inside r, after its first
+ *              k = 1 + pos(b, c-1) customers.  Otherwise nothing changes. */
+static void route_bounds(const int32_t *s, int32_t len, int32_t n, int32_t *bb, int32_t *ee,
+                         int32_t V) {
+  int32_t r = 0;
+  bb[0] = 0;
+  for (int32_t q = 0; q < len; q++)
+    if (s[q] >= n) {
+      ee[r] = q;
+      bb[++r] = q + 1;
+    }
+  ee[V - 1] = len;
+}
+
+static void move_element(int32_t *s, int32_t from, int32_t to) {
+  /* remove s[from]; re-insert it so that it lands at index to */
+  const int32_t v = s[from];
+  if (from < to)
+    for (int32_t k = from; k < to; k++) s[k] = s[k + 1];
+  else
+    for (int32_t k = from; k > to; k--) s[k] = s[k - 1];
+  s[to] = v;
+}
+
+int32_t orc_row_move(const orc_instance *in, int32_t kind, uint32_t a, uint32_t b, int32_t *s,
+                     int32_t len) {
+  if (in->model != ORC_CVRPTW) return -1;
+  const int32_t n = in->n, V = in->vehicles;
+  if (V < 2) return 0;
+  int32_t *bb = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
+  int32_t *ee = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
+  route_bounds(s, len, n, bb, ee, V);
+  if (kind == 0) {                                      /* row_swap */
+    int32_t r1 = (int32_t)orc_pos(a, (uint32_t)V), r2 = (int32_t)orc_pos(b, (uint32_t)(V - 1));
+    if (r2 >= r1) r2++;
+    const int32_t lo = r1 < r2 ? r1 : r2, hi = r1 < r2 ? r2 : r1;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
+    int32_t o = 0;
+    for (int32_t q = 0; q < bb[lo]; q++) t[o++] = s[q];
+    for (int32_t q = bb[hi]; q < ee[hi]; q++) t[o++] = s[q];
+    for (int32_t q = ee[lo]; q < bb[hi]; q++) t[o++] = s[q];
+    for (int32_t q = bb[lo]; q < ee[lo]; q++) t[o++] = s[q];
+    for (int32_t q = ee[hi]; q < len; q++) t[o++] = s[q];
+    memcpy(s, t, sizeof(int32_t) * (size_t)len);
+    free(t);
+  } else if (kind == 1) {                               /* row_merge */
+    const int32_t r = (int32_t)orc_pos(a, (uint32_t)(V - 1));
+    move_element(s, ee[r], ee[r + 1] - 1);
+  } else {                                              /* row_split */
+    const int32_t r = (int32_t)orc_pos(a, (uint32_t)V), c = ee[r] - bb[r];
+    int32_t z = -1;
+    for (int32_t q = 0; q < V && z < 0; q++)
+      if (ee[q] == bb[q]) z = q;
+    if (c >= 2 && z >= 0) {
+      const int32_t k = 1 + (int32_t)orc_pos(b, (uint32_t)(c - 1));
+      const int32_t from = z < V - 1 ? ee[z] : bb[z] - 1;  /* the separator that goes */
+      const int32_t gap = bb[r] + k;                        /* before s[gap] */
+      move_element(s, from, from < gap ? gap - 1 : gap);
+    }
+  }
+  free(bb);
+  free(ee);
+  return 0;
+}
+
 void orc_ox(const int32_t *A, const int32_t *B, int32_t len, int32_t lo, int32_t hi,
             int32_t *child) {
   char *mark = (char *)calloc((size_t)len, 1);

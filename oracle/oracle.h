@@ -111,6 +111,13 @@ int32_t orc_elite(const orc_state *st);
  * search takes after every migrate_period-th generation); exported for the
  * oracle's own pins.  Returns -1 for invalid island parameters. */
 int32_t orc_migrate(const orc_params *pr, orc_state *st);
+/* Row operators [R31] of CVRPTW's separator encoding (rows = routes; Table
+ * "operators", row level): kind 0 row_swap, 1 row_merge, 2 row_split, drawn
+ * from the 16-bit fields a, b; edits s in place (an identity when the row
+ * operator has nothing to do).  Not yet part of the search: primitives for
+ * the row level's pins.  Returns -1 for other models. */
+int32_t orc_row_move(const orc_instance *in, int32_t kind, uint32_t a, uint32_t b, int32_t *s,
+                     int32_t len);
 /* order crossover [R29]: child keeps A[lo..hi] in place and fills positions
  * hi+1, ..., len-1, 0, ..., lo-1 with the elements of B outside that segment,
  * in B's order from B[hi+1] on (wrapping); 0 <= lo <= hi < len */
