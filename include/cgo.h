@@ -274,7 +274,9 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_prob
  *                cgo_best for the same inputs.
  * out_best_sol:  device buffer of n int32: the elite solution.
  * out_best_cost: device buffer of one int64: its cost.
- * The call waits for its work on cuda_stream before it returns.
+ * The call synchronises cuda_stream twice (after checking the matrix, and at
+ * the end), so its work is complete when it returns.  Argument errors
+ * (sizes, generations, parameters) are returned before any GPU work.
  *
  * The first call on a device resolves the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call

@@ -226,8 +226,13 @@ def row_move(inst: dict, kind: int, a: int, b: int, sol) -> np.ndarray:
     """A row operator (row_swap / row_merge / row_split) on a CVRPTW solution."""
     I = Instance(inst)
     s = np.ascontiguousarray(np.asarray(sol, dtype=np.int32).copy())
-    if lib().orc_row_move(I.ref, kind, a, b, s.ctypes.data_as(_i32p), len(s)) != 0:
+    if int(inst["model"]) == 4 and len(s) != int(inst["n"]) + int(inst.get("vehicles", 0)) - 1:
+        raise ValueError("a CVRPTW solution has n + vehicles - 1 symbols")
+    rc = lib().orc_row_move(I.ref, kind, a, b, s.ctypes.data_as(_i32p), len(s))
+    if rc == -1:
         raise ValueError("row operators need a CVRPTW instance")
+    if rc != 0:
+        raise ValueError("malformed CVRPTW solution (need exactly vehicles - 1 separators)")
     return s
 
 

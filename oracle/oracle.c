@@ -754,22 +754,6 @@ int32_t orc_migrate(const orc_params *pr, orc_state *st) {
   return 0;
 }
 
-/* [R29] crossover (Table "operators", crossover level: OX for permutations,
- * uniform crossover for binary and integer vectors), taken after every AOS
- * update and migration, before elite injection.  With R = Philox(0 | 3<<24,
- * tag, p, g): member p crosses when hi16(R.r0) < cross_q16, with partner
- * q = (p + 1 + pos(hi16(R.r1), P-1)) mod P.  The parents are p's current
- * solution A and q's best solution B, both as they stood before any
- * crossover of this window.
- *   OX: cut points i = pos(hi16(R.r2), n), j = pos(lo16(R.r2), n-1) + (j >= i),
- *       lo = min, hi = max; the child keeps A[lo..hi] in place and fills the
- *       positions hi+1, ..., n-1, 0, ..., lo-1 with the elements of B that
- *       are not in A[lo..hi], in B's order from B[hi+1] on (wrapping).
- *   uniform: element k comes from B when bit k mod 32 of word (k/32) mod 4
- *       of Philox((k/128) | 1<<20 | 3<<24, tag, p, g) is set, else from A.
- * The child's cost is evaluated in full; it replaces A under the Metropolis
- * rule [R7] at the current temperature with the variate R.r3, and lowers
- * p's best like an accepted move. */
 /* [R31] row operators (Table "operators", row level; the paper names
  * row_swap, row_split and row_merge and says nothing more).  Rows are the V
  * routes of the separator encoding: route r spans [b_r, e_r) with b_0 = 0,
@@ -783,16 +767,21 @@ int32_t orc_migrate(const orc_params *pr, orc_state *st) {
  *              z (the lowest-index one), the separator that closes z (or,
  *              for the last route, opens it) moves inside r, after its first
  *              k = 1 + pos(b, c-1) customers.  Otherwise nothing changes. */
-static void route_bounds(const int32_t *s, int32_t len, int32_t n, int32_t *bb, int32_t *ee,
-                         int32_t V) {
+/* Route r spans [bb[r], ee[r]).  Returns -2 unless s holds exactly V-1
+ * separators (symbols >= n). */
+static int32_t route_bounds(const int32_t *s, int32_t len, int32_t n, int32_t *bb, int32_t *ee,
+                            int32_t V) {
   int32_t r = 0;
   bb[0] = 0;
   for (int32_t q = 0; q < len; q++)
     if (s[q] >= n) {
+      if (r == V - 1) return -2;
       ee[r] = q;
       bb[++r] = q + 1;
     }
+  if (r != V - 1) return -2;
   ee[V - 1] = len;
+  return 0;
 }
 
 static void move_element(int32_t *s, int32_t from, int32_t to) {
@@ -809,15 +798,21 @@ int32_t orc_row_move(const orc_instance *in, int32_t kind, uint32_t a, uint32_t 
                      int32_t len) {
   if (in->model != ORC_CVRPTW) return -1;
   const int32_t n = in->n, V = in->vehicles;
+  if (len != n + V - 1) return -2;
   if (V < 2) return 0;
   int32_t *bb = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
   int32_t *ee = (int32_t *)malloc(sizeof(int32_t) * (size_t)V);
-  route_bounds(s, len, n, bb, ee, V);
+  int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
+  if (!bb || !ee || !t || route_bounds(s, len, n, bb, ee, V) != 0) {
+    free(bb);
+    free(ee);
+    free(t);
+    return !bb || !ee || !t ? -3 : -2;
+  }
   if (kind == 0) {                                      /* row_swap */
     int32_t r1 = (int32_t)orc_pos(a, (uint32_t)V), r2 = (int32_t)orc_pos(b, (uint32_t)(V - 1));
     if (r2 >= r1) r2++;
     const int32_t lo = r1 < r2 ? r1 : r2, hi = r1 < r2 ? r2 : r1;
-    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
     int32_t o = 0;
     for (int32_t q = 0; q < bb[lo]; q++) t[o++] = s[q];
     for (int32_t q = bb[hi]; q < ee[hi]; q++) t[o++] = s[q];
@@ -825,7 +820,6 @@ int32_t orc_row_move(const orc_instance *in, int32_t kind, uint32_t a, uint32_t 
     for (int32_t q = bb[lo]; q < ee[lo]; q++) t[o++] = s[q];
     for (int32_t q = ee[hi]; q < len; q++) t[o++] = s[q];
     memcpy(s, t, sizeof(int32_t) * (size_t)len);
-    free(t);
   } else if (kind == 1) {                               /* row_merge */
     const int32_t r = (int32_t)orc_pos(a, (uint32_t)(V - 1));
     move_element(s, ee[r], ee[r + 1] - 1);
@@ -843,9 +837,26 @@ int32_t orc_row_move(const orc_instance *in, int32_t kind, uint32_t a, uint32_t 
   }
   free(bb);
   free(ee);
+  free(t);
   return 0;
 }
 
+/* [R29] crossover (Table "operators", crossover level: OX for permutations,
+ * uniform crossover for binary and integer vectors), taken after every AOS
+ * update and migration, before elite injection.  With R = Philox(0 | 3<<24,
+ * tag, p, g): member p crosses when hi16(R.r0) < cross_q16, with partner
+ * q = (p + 1 + pos(hi16(R.r1), P-1)) mod P.  The parents are p's current
+ * solution A and q's best solution B, both as they stood before any
+ * crossover of this window.
+ *   OX: cut points i = pos(hi16(R.r2), n), j = pos(lo16(R.r2), n-1) + (j >= i),
+ *       lo = min, hi = max; the child keeps A[lo..hi] in place and fills the
+ *       positions hi+1, ..., n-1, 0, ..., lo-1 with the elements of B that
+ *       are not in A[lo..hi], in B's order from B[hi+1] on (wrapping).
+ *   uniform: element k comes from B when bit k mod 32 of word (k/32) mod 4
+ *       of Philox((k/128) | 1<<20 | 3<<24, tag, p, g) is set, else from A.
+ * The child's cost is evaluated in full; it replaces A under the Metropolis
+ * rule [R7] at the current temperature with the variate R.r3, and lowers
+ * p's best like an accepted move. */
 void orc_ox(const int32_t *A, const int32_t *B, int32_t len, int32_t lo, int32_t hi,
             int32_t *child) {
   char *mark = (char *)calloc((size_t)len, 1);

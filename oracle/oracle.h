@@ -115,7 +115,8 @@ int32_t orc_migrate(const orc_params *pr, orc_state *st);
  * "operators", row level): kind 0 row_swap, 1 row_merge, 2 row_split, drawn
  * from the 16-bit fields a, b; edits s in place (an identity when the row
  * operator has nothing to do).  Not yet part of the search: primitives for
- * the row level's pins.  Returns -1 for other models. */
+ * the row level's pins.  Returns -1 for other models, -2 unless len = n + V - 1
+ * with exactly V - 1 separators, -3 when memory runs out. */
 int32_t orc_row_move(const orc_instance *in, int32_t kind, uint32_t a, uint32_t b, int32_t *s,
                      int32_t len);
 /* order crossover [R29]: child keeps A[lo..hi] in place and fills positions

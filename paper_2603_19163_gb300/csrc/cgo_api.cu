@@ -1168,8 +1168,10 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
     return fail(CGO_ERR_INVALID, "the allocation-free solve needs the distance matrix on the device");
   if (!out_best_sol || !out_best_cost) return fail(CGO_ERR_INVALID, "output buffers are required");
   if (d->n < 2 || d->n > 65535) return fail(CGO_ERR_INVALID, "n must be in [2, 65535]");
+  if (q && q->struct_size == sizeof(cgo_params) && q->generations >= 0xFFFFFFFFll)
+    return fail(CGO_ERR_INVALID, "too many generations");
   cgo_problem p;  // a description on the stack: no device state of its own
-  cudaGetDevice(&p.device);
+  CUDA_TRY(cudaGetDevice(&p.device), "current device");
   p.model = TSP;
   p.n = p.len = d->n;
   p.tag = d->instance_tag;
@@ -1241,11 +1243,14 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
   CUDA_TRY(launch_init_aos(h, a0, st), "init launch");
   int cur_aos = 0;
   if (q->generations > 0) {
-    if (q->generations >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "too many generations");
     int warps = 0, wpm = 1, ns = 1;
     int64_t smem = 0;
     h = base_kinst(&p);
-    if ((s = choose_launch(&p, h, &warps, &wpm, &ns, &smem)) != CGO_OK) return s;
+    if ((s = choose_launch(&p, h, &warps, &wpm, &ns, &smem)) != CGO_OK) {
+      // leave no queued work behind in the shared array
+      cudaStreamSynchronize(st);
+      return s;
+    }
     h.g_begin = 0;
     h.g_end = q->generations;
     h.aos_in = aos;

@@ -91,3 +91,14 @@ def test_row_move_semantics_random():
 def test_row_moves_only_for_cvrptw():
     with pytest.raises(ValueError):
         O.row_move(I.tsp_uniform(6, 1), O.ROW_SWAP, 0, 0, list(range(6)))
+
+
+@pytest.mark.parametrize("sol", [
+    [0, 1, 5, 2, 6, 3],            # one symbol short
+    [0, 1, 5, 2, 6, 3, 4, 4],      # one symbol too many
+    [0, 1, 5, 2, 6, 5, 4],         # three separators in a length-7 sequence
+    [0, 1, 2, 2, 6, 3, 4],         # one separator
+])
+def test_row_moves_reject_malformed(sol):
+    with pytest.raises(ValueError):
+        O.row_move(INST, O.ROW_SWAP, 0, 0, sol)
