@@ -594,7 +594,10 @@ int32_t orc_threads(int32_t threads) {
 }
 
 /* ---------------------------------------------------- one generation of one
- * solution: Alg. "evolve" for block p.  Writes its AOS counts to u/v/uk/vk. */
+ * solution: Alg. "evolve" for block p.  Writes its AOS counts to u/v/uk/vk.
+ * Pinned by generations worked by hand (step draws, k from word r3, the
+ * argmin's tie rule, every candidate's counts, the acceptance draw; a TSP
+ * and a GAP case, tests/golden/generation.json). */
 static void evolve_one(const orc_instance *in, const orc_params *pr, uint64_t seed,
                        orc_state *st, int32_t p, const uint32_t *w_op, const uint32_t *w_k,
                        uint64_t T, uint32_t g, int32_t *work, int64_t *delta, int32_t *ops,
