@@ -14,6 +14,16 @@ with nvidia-smi during the timed region.  ``e2e`` repeats the step through the
 public API from host buffers: problem creation (host->device copy of the
 matrix), the solve and the read-back of the best solution (device->host).
 
+With N=1 the line also carries the batched and served forms of the metric
+(``config.batched``: the 512-instance uneven batch, solves/s against one
+launch per solve on every 8th instance; ``config.served``: 10 s of the
+200 requests/s Poisson trace through the continuous-batching server, p50/p99
+latency, against one launch per solve replayed live on the trace's first
+second and modelled over the whole trace), each with its own clock record.
+The roofline counts the algorithmic distance gathers of the operators the
+solve applied (whole-solve counts from the library) against the measured
+shared-memory random-gather rate.
+
 --impl reference times the CPU oracle on the host cores on a bounded sample
 (a prefix of the same solve), the only other place this file runs it.
 Under torchrun every rank solves its own replica (seed 1 + rank).
@@ -289,7 +299,14 @@ def main():
     ap.add_argument("--launch", default="",
                     help="single solve: fixed launch shape 'warps,wpm,staging,gens_in_flight' "
                          "instead of the autotuner (profiling runs)")
-    ap.add_argument("--seq-sample", type=int, default=24)
+    ap.add_argument("--seq-live-seconds", type=float, default=1.0,
+                    help="serving: seconds of the trace replayed live by one launch per solve")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="tsp442: leave out the batched and served results of the default line")
+    ap.add_argument("--extra-steps", type=int, default=2,
+                    help="tsp442 line: timed batches of the 512-instance mix")
+    ap.add_argument("--extra-serve-seconds", type=float, default=10.0,
+                    help="tsp442 line: seconds of the Poisson trace served")
     ap.add_argument("--generations", type=int, default=0,
                     help="override G (small cases for profiler captures)")
     args = ap.parse_args()
@@ -402,18 +419,30 @@ def main():
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_value = cfg["P"] * cfg["C"] * cfg["G"] * world / (float(e2e_t.item()) / 1000.0)
 
+    extras = {}
+    if world == 1 and args.workload == "tsp442" and not args.no_extras and args.generations == 0:
+        # the batched and served forms of the metric (configs of the 512-instance
+        # batch and the Poisson serving trace), each against one launch per solve
+        t_x = time.perf_counter()
+        b = batch_run(args, cgo, torch, local, args.extra_steps, 1, 20000)
+        extras["batched"] = {k: b[k] for k in (
+            "desc", "solves_per_s", "evals_per_s", "one_launch_per_solve_solves_per_s",
+            "batched_over_one_launch_per_solve", "same_final_costs", "one_launch_per_solve_sample",
+            "autotuner", "clocks", "gpu_launches", "steps", "total_ms")}
+        sv = serve_run(args, cgo, torch, local, args.extra_serve_seconds, 20000,
+                       args.seq_live_seconds)
+        extras["served"] = {k: v for k, v in sv.items() if k not in ("h2d_bytes", "d2h_bytes")}
+        extras["seconds"] = time.perf_counter() - t_x
+
     if rank == 0:
         kms = sum(kern_ms) / len(kern_ms)
-        evals_launch = cfg["P"] * cfg["C"] * cfg["G"]
         cv = inst["model"] == I.CVRPTW
         # the roofline model covers the TSP and QAP deltas; a CVRPTW delta is a
         # route walk of data-dependent length (reported without one)
-        roof = None if cv else roofline(evals_launch, kms, prob, clocks)
-        # mean steps per candidate: the roofline's figure (the open window's K
-        # counts, 1.25 when the run ends on a window boundary)
-        uk = prob.state()["u_k"]
-        ek = roof["ops_per_eval_steps"] if roof else (
-            (uk[0] + 2 * uk[1] + 3 * uk[2]) / sum(uk) if sum(uk) else 1.25)
+        roof = None if cv else roofline(kms, prob, clocks)
+        # mean steps per candidate over the whole solve (measured counts)
+        mix = op_mix(prob.op_counts())
+        ek = mix["steps_per_eval"]
         line = {"metric": "move_evals_per_s", "value": value, "unit": "evals/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -429,14 +458,16 @@ def main():
                            "best_cost": int(best_cost), "start_best_cost": int(start_cost),
                            "gens_per_s": cfg["G"] / (total_ms / args.steps / 1000.0),
                            # operator applications: each evaluation applies k
-                           # operators, E[k] from the run's last K counts
-                           "operator_applications_per_s": value * ek},
+                           # operators, E[k] counted over the whole solve
+                           "operator_applications_per_s": value * ek,
+                           "op_mix": mix},
                 "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
                 "clocks": clocks, "roofline": roof}
         if cv:
             line["config"]["elite_objectives"] = cvrptw_objectives(inst, prob.best()[0])
+        line["config"].update({k: v for k, v in extras.items()})
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(inst, cfg, desc, args.cpu_budget)
         print(json.dumps(line), flush=True)
@@ -444,14 +475,15 @@ def main():
         dist.destroy_process_group()
 
 
-def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
+def batch_run(args, cgo, torch, local, steps, warmup, G, rank=0, world=1, dist=None,
+              barrier=lambda: None) -> dict:
     """512 uneven instances (40% TSP n~U[50,500], 40% knapsack n~U[100,2000],
     20% GAP n~U[50,300]) advanced together by the batched persistent kernel
     under a CUDA graph; one step = one cgo_solve_batch of all of them.  The
     one-launch-per-solve form (cgo_solve of each instance in turn, same P, C,
-    G, seeds) is timed on every 8th instance."""
+    G, seeds, each with its own default launch shape) runs on every 8th
+    instance; both forms reach the same final costs (bit-identical results)."""
     _, cfg, desc = workload("batch512")
-    G = args.generations if args.generations > 0 else cfg["G"]
     mix = [dict(x, tag=i) for i, x in enumerate(I.batch_mix(512, 0))]
     if args.batch_class != "mix":
         cls = {"tsp": I.TSP, "knapsack": I.KNAPSACK, "gap": I.GAP, "cvrptw": I.CVRPTW}[args.batch_class]
@@ -483,7 +515,7 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
                  for k, v in Autotuner(trial_generations=min(G, 300)).tune_batch(
                      probs, params).items()}
     stream = torch.cuda.Stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         cgo.solve_batch(probs, params, seeds, stream)
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
@@ -492,7 +524,7 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
         sampler.start()
     ms = []
     launches0 = cgo.kernel_launches()
-    for _ in range(args.steps):
+    for _ in range(steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -505,17 +537,19 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
     barrier()
     clocks = sampler.stop() if rank == 0 else None
     # solution quality of the last step: the sum of the instances' best costs per model
-    best_sum = {}
+    best_sum, batched_best = {}, []
     for pr, x in zip(probs, mix):
         key = {I.TSP: "tsp", I.KNAPSACK: "knapsack", I.GAP: "gap", I.CVRPTW: "cvrptw"}[x["model"]]
-        best_sum[key] = best_sum.get(key, 0) + int(pr.best()[1])
+        c = int(pr.best()[1])
+        batched_best.append(c)
+        best_sum[key] = best_sum.get(key, 0) + c
     t = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
-    if world > 1:
+    if dist is not None and world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     evals = sum(q["P"] * q["C"] * q["G"] for q in params)
-    value = evals * args.steps * world / (total_ms / 1000.0)
-    solves_s = len(probs) * args.steps * world / (total_ms / 1000.0)
+    value = evals * steps * world / (total_ms / 1000.0)
+    solves_s = len(probs) * steps * world / (total_ms / 1000.0)
     # one launch per solve, on a stratified sample (every 8th instance)
     sample = list(range(0, len(probs), 8))
     for i in sample:
@@ -525,6 +559,7 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
     for i in sample:
         probs[i].solve(params[i], seeds[i], stream)
     seq_s = time.perf_counter() - t0
+    same = all(int(probs[i].best()[1]) == batched_best[i] for i in sample)
     seq_solves_s = len(sample) / seq_s
     # end to end: create from host arrays (H2D), batch solve, read every best (D2H)
     torch.cuda.synchronize()
@@ -537,40 +572,66 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
                                                          "vec3") if x.get(k) is not None))
               for x in mix)
     d2h = sum(int(o[0].nbytes) + 8 for o in outs)
-    for pp in p2:
+    for pp in p2 + probs:
         pp.close()
+    return {"desc": desc.replace("G=20000", "G=%d" % G), "value": value, "total_ms": total_ms,
+            "steps": steps, "evals_per_s": value, "solves_per_s": solves_s,
+            "one_launch_per_solve_solves_per_s": seq_solves_s,
+            "batched_over_one_launch_per_solve": solves_s / seq_solves_s,
+            "same_final_costs": same,
+            "one_launch_per_solve_sample": "%d of %d instances (every 8th)" % (len(sample), len(mix)),
+            "best_cost_sum_by_model": best_sum, "autotuner": tuned, "clocks": clocks,
+            "gpu_launches": launches, "e2e_evals_per_s": evals * world / e2e_s,
+            "h2d_bytes": h2d, "d2h_bytes": d2h}
+
+
+def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
+    G = args.generations if args.generations > 0 else workload("batch512")[1]["G"]
+    r = batch_run(args, cgo, torch, local, args.steps, args.warmup, G, rank, world, dist, barrier)
     if rank == 0:
-        line = {"metric": "move_evals_per_s", "value": value, "unit": "evals/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        line = {"metric": "move_evals_per_s", "value": r["value"], "unit": "evals/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": {"workload": desc.replace("G=20000", "G=%d" % G),
+                "config": {"workload": r["desc"],
                            "l2": "inputs > L2 in total (512 instances); no flush",
-                           "solves_per_s_batched": solves_s,
-                           "solves_per_s_one_launch_per_solve": seq_solves_s,
-                           "batched_over_sequential": solves_s / seq_solves_s,
-                           "sequential_sample": "%d of %d instances" % (len(sample), len(mix)),
-                           "best_cost_sum_by_model": best_sum,
-                           "autotuner": tuned},
-                "e2e": {"value": evals * world / e2e_s, "unit": "evals/s",
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "clocks": clocks}
+                           "solves_per_s_batched": r["solves_per_s"],
+                           "solves_per_s_one_launch_per_solve": r["one_launch_per_solve_solves_per_s"],
+                           "batched_over_sequential": r["batched_over_one_launch_per_solve"],
+                           "same_final_costs": r["same_final_costs"],
+                           "sequential_sample": r["one_launch_per_solve_sample"],
+                           "best_cost_sum_by_model": r["best_cost_sum_by_model"],
+                           "autotuner": r["autotuner"]},
+                "e2e": {"value": r["e2e_evals_per_s"], "unit": "evals/s",
+                        "h2d_bytes_per_step": r["h2d_bytes"], "d2h_bytes_per_step": r["d2h_bytes"]},
+                "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
         print(json.dumps(line), flush=True)
 
 
-def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
-    """Serving: Poisson arrivals at 200 requests/s for 60 s (sizes from the
-    batch mix, 15% CVRPTW with 100 customers); each request is created from
-    host arrays when it arrives (host->device copy), submitted to the
-    continuous-batching server and waited for; latency = completion - arrival.
-    The one-launch-per-solve form is timed on sampled requests (cgo_solve of
-    each in turn) and its queueing under the same arrival trace follows from
-    the Lindley recursion W_i = max(0, W_(i-1) + S_(i-1) - A_i) with those
-    measured service times."""
+def lindley(trace, service_of) -> np.ndarray:
+    """Latencies of one server taking requests first come, first served:
+    W_i = max(0, W_(i-1) + S_(i-1) - A_i) (Lindley), latency = W_i + S_i."""
+    W, prev_t, prev_s, out = 0.0, None, 0.0, []
+    for ta, k in trace:
+        s_i = service_of(k)
+        if prev_t is not None:
+            W = max(0.0, W + prev_s - (ta - prev_t))
+        out.append(W + s_i)
+        prev_t, prev_s = ta, s_i
+    return np.array(out)
+
+
+def serve_run(args, cgo, torch, local, duration, G, seq_live_s, rank=0) -> dict:
+    """Serving: Poisson arrivals at 200 requests/s (sizes from the batch mix,
+    15% CVRPTW with 100 customers); each request is created from host arrays
+    when it arrives (host->device copy), submitted to the continuous-batching
+    server and waited for; latency = completion - arrival.  The
+    one-launch-per-solve form replays the first seq_live_s seconds of the
+    same trace for real (one worker, first come first served, cgo_solve of
+    each request with its own default launch shape); its measured service
+    times per class also drive the Lindley recursion over the whole trace."""
     import threading
     _, cfg, desc = workload("serve")
-    G = args.generations if args.generations > 0 else cfg["G"]
-    duration = args.serve_seconds
     pool = I.serving_pool(0)
     trace = I.poisson_arrivals(200.0, duration, 7)
     params_of = {}
@@ -595,14 +656,12 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
     sample_probs, sample_params = [], []
     fill = 2 * torch.cuda.get_device_properties(local).multi_processor_count
     for mdl, ks in models.items():
-        pick = ks[:: max(1, len(ks) // 8)][:8]
+        pick = sorted(ks)[:: max(1, len(ks) // 8)][:8]
         for j in range(fill):           # a trial batch large enough to fill the GPU
             k = pick[j % len(pick)]
             sample_probs.append(cgo.Problem(dict(pool[k], tag=j)))
             sample_params.append(params_for(k))
-    t_phase = time.perf_counter()
     tuned = tuner.tune_batch(sample_probs, sample_params, sample=fill)
-    print("serve: autotune %.1f s" % (time.perf_counter() - t_phase), file=sys.stderr, flush=True)
     for pr in sample_probs:
         pr.close()
     share = {}
@@ -615,7 +674,7 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
     for k in params_of:
         params_of[k]["P"] = pops[pool[k]["model"]]
     srv = cgo.Server(max_slots=4096, hbm_budget_bytes=96 << 30, slice_generations=args.slice)
-    # warm-up: a few requests end to end
+
     def make(k, tag):
         pr = cgo.Problem(dict(pool[k], tag=tag))
         pr.set_launch(0, 0, wpm_of[pool[k]["model"]])
@@ -645,18 +704,6 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
 
     th = threading.Thread(target=producer)
     th.start()
-    stop_mon = [False]
-
-    def monitor():
-        while True:
-            time.sleep(5.0)
-            if stop_mon[0]:
-                return
-            print("serve: t=%.0f s %s" % (time.perf_counter() - t_start, srv.stats()),
-                  file=sys.stderr, flush=True)
-
-    mon = threading.Thread(target=monitor, daemon=True)
-    mon.start()
     done_at = [0.0] * len(trace)
     for i in range(len(trace)):
         while tickets[i] is None:
@@ -666,82 +713,96 @@ def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
         done_at[i] = time.perf_counter() - t_start
     th.join()
     launches = cgo.kernel_launches() - launches0
-    stop_mon[0] = True
     wall = max(done_at) - trace[0][0]
+    clocks = sampler.stop() if rank == 0 else None
+    stats = srv.stats()
+    srv.close()
     # every request's instance arrays go host -> device when it arrives; its
     # elite cost (int64) comes back when it completes
     h2d = sum(int(sum(np.asarray(pool[k][f]).nbytes for f in ("mat0", "mat1", "vec0", "vec1", "vec2",
                                                                "vec3") if pool[k].get(f) is not None))
               for _, k in trace)
-    d2h = 8 * len(trace)
-    print("serve: trace done %.1f s" % (time.perf_counter() - t_start), file=sys.stderr, flush=True)
-    clocks = sampler.stop() if rank == 0 else None
-    stats = srv.stats()
-    srv.close()
     lats = np.array([r[1] for r in results])
     served_solves_s = len(trace) / wall
     evals = sum(params_for(k)["P"] * params_for(k)["C"] * G for _, k in trace)
-    # one launch per solve: per-class service times measured on a stratified
-    # sample of the trace's requests, queueing by the Lindley recursion
+
     def cls_of(k):
         return "cvrptw" if k >= 512 else ("tsp", "qap", "knapsack", "gap")[pool[k]["model"]]
-    by_cls = {}
-    for i, (_, k) in enumerate(trace):
-        by_cls.setdefault(cls_of(k), []).append(i)
-    per = max(2, args.seq_sample // max(1, len(by_cls)))
-    service = {}
-    for c, idx in by_cls.items():
-        for i in idx[::max(1, len(idx) // per)][:per]:
-            k = trace[i][1]
-            pr = cgo.Problem(dict(pool[k], tag=i))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            pr.solve(params_for(k), 1 + i)
-            service.setdefault(c, []).append(time.perf_counter() - t0)
-            pr.close()
-    mean_cls = {c: float(np.mean(v)) for c, v in service.items()}
-    overall = float(np.mean([mean_cls[cls_of(k)] for _, k in trace]))
-    rng_pick = [x for v in service.values() for x in v]
-    W, prev_t, prev_s, seq_lat = 0.0, None, 0.0, []
-    for ta, k in trace:
-        s_i = mean_cls[cls_of(k)]
-        if prev_t is not None:
-            W = max(0.0, W + prev_s - (ta - prev_t))
-        seq_lat.append(W + s_i)
-        prev_t, prev_s = ta, s_i
+
+    # one launch per solve, live: the trace's first seq_live_s seconds
+    live = [(i, ta, k) for i, (ta, k) in enumerate(trace) if ta < trace[0][0] + seq_live_s]
+    seq_lat, service, same = [], {}, True
+    torch.cuda.synchronize()
+    t_live = time.perf_counter() - trace[0][0]
+    for i, ta, k in live:
+        now = time.perf_counter() - t_live
+        if ta > now:
+            time.sleep(ta - now)
+        pr = cgo.Problem(dict(pool[k], tag=i))
+        t0 = time.perf_counter()
+        pr.solve(params_for(k), 1 + i)
+        c = int(pr.best()[1])
+        t1 = time.perf_counter()
+        service.setdefault(cls_of(k), []).append(t1 - t0)
+        seq_lat.append(t1 - t_live - ta)
+        same = same and c == int(results[i][0])
+        pr.close()
     seq_lat = np.array(seq_lat)
-    seq_solves_s = 1.0 / overall
+    mean_cls = {c: float(np.mean(v)) for c, v in service.items()}
+    overall = float(np.mean([mean_cls.get(cls_of(k), max(mean_cls.values())) for _, k in trace]))
+    model_lat = lindley(trace, lambda k: mean_cls.get(cls_of(k), max(mean_cls.values())))
+    model_prefix = lindley([(ta, k) for _, ta, k in live],
+                           lambda k: mean_cls.get(cls_of(k), max(mean_cls.values())))
+    served_prefix = np.array([results[i][1] for i, _, _ in live])
     for pr in probs + warm:
         if pr is not None:
             pr.close()
+    return {"desc": desc.replace("G=20000", "G=%d" % G).replace("x60s", "x%ds" % int(duration)),
+            "requests": len(trace), "wall_s": wall, "solves_per_s": served_solves_s,
+            "move_evals_per_s": evals / wall,
+            "latency_p50_s": float(np.percentile(lats, 50)),
+            "latency_p99_s": float(np.percentile(lats, 99)),
+            "latency_max_s": float(lats.max()),
+            "slice_generations": args.slice,
+            "autotuner": {"population_by_model": {str(m): v for m, v in pops.items()},
+                          "predicted_load": load,
+                          "warps_per_member_by_model": {str(m): v for m, v in wpm_of.items()},
+                          "trial_evals_per_s_by_model": {str(m): tuned[m][1] for m in tuned}},
+            "one_launch_per_solve": {
+                "live": {"requests": len(live), "arrivals_s": seq_live_s,
+                         "solves_per_s": len(live) / float(sum(sum(v) for v in service.values())),
+                         "latency_p50_s": float(np.percentile(seq_lat, 50)),
+                         "latency_p99_s": float(np.percentile(seq_lat, 99)),
+                         "served_latency_p50_s_same_requests": float(np.percentile(served_prefix, 50)),
+                         "served_latency_p99_s_same_requests": float(np.percentile(served_prefix, 99)),
+                         "lindley_p50_s_same_requests": float(np.percentile(model_prefix, 50)),
+                         "lindley_p99_s_same_requests": float(np.percentile(model_prefix, 99)),
+                         "same_final_costs": same},
+                "modelled_whole_trace": {"solves_per_s": 1.0 / overall,
+                                         "latency_p50_s": float(np.percentile(model_lat, 50)),
+                                         "latency_p99_s": float(np.percentile(model_lat, 99)),
+                                         "service_s_by_class": mean_cls,
+                                         "how": "Lindley recursion over the whole trace with the "
+                                                "live run's mean service time per class"}},
+            "served_over_one_launch_per_solve": served_solves_s * overall,
+            "server": stats, "clocks": clocks, "gpu_launches": launches,
+            "h2d_bytes": h2d, "d2h_bytes": 8 * len(trace)}
+
+
+def bench_serve(args, rank, world, local, cgo, torch, dist, barrier):
+    G = args.generations if args.generations > 0 else workload("serve")[1]["G"]
+    r = serve_run(args, cgo, torch, local, args.serve_seconds, G, args.seq_live_seconds, rank)
     if rank == 0:
-        line = {"metric": "served_solves_per_s", "value": served_solves_s, "unit": "solves/s",
-                "n_gpus": world, "steps": 1, "warmup": len(warm), "ms_per_step": 1000 * wall,
+        cfg = {k: v for k, v in r.items()
+               if k not in ("desc", "clocks", "gpu_launches", "h2d_bytes", "d2h_bytes", "wall_s")}
+        cfg["workload"] = r["desc"]
+        line = {"metric": "served_solves_per_s", "value": r["solves_per_s"], "unit": "solves/s",
+                "n_gpus": world, "steps": 1, "warmup": 4, "ms_per_step": 1000 * r["wall_s"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "int64", "data": "synthetic",
-                "config": {"workload": desc.replace("G=20000", "G=%d" % G).replace(
-                               "x60s", "x%ds" % int(duration)),
-                           "requests": len(trace), "slice_generations": args.slice,
-                           "autotuner": {"population_by_model": {str(m): v for m, v in pops.items()},
-                                         "predicted_load": load,
-                                         "warps_per_member_by_model": {str(m): v for m, v in wpm_of.items()},
-                                         "trial_evals_per_s_by_model": {str(m): tuned[m][1] for m in tuned}},
-                           "move_evals_per_s": evals / wall,
-                           "latency_p50_s": float(np.percentile(lats, 50)),
-                           "latency_p99_s": float(np.percentile(lats, 99)),
-                           "latency_max_s": float(lats.max()),
-                           "one_launch_per_solve": {
-                               "solves_per_s": seq_solves_s,
-                               "latency_p50_s": float(np.percentile(seq_lat, 50)),
-                               "latency_p99_s": float(np.percentile(seq_lat, 99)),
-                               "service_s_by_class": mean_cls,
-                               "how": "per-class service times of %d sampled requests, Lindley "
-                                      "recursion over the same arrivals" % len(rng_pick)},
-                           "served_over_one_launch_per_solve": served_solves_s / seq_solves_s,
-                           "server": stats},
-                "e2e": {"value": served_solves_s, "unit": "solves/s",
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "clocks": clocks}
+                "dtype": "int64", "data": "synthetic", "config": cfg,
+                "e2e": {"value": r["solves_per_s"], "unit": "solves/s",
+                        "h2d_bytes_per_step": r["h2d_bytes"], "d2h_bytes_per_step": r["d2h_bytes"]},
+                "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
         print(json.dumps(line), flush=True)
 
 
@@ -761,14 +822,18 @@ def aggregate(local_ms: float, local_units: float, dist=None, device="cpu") -> d
             "world": world}
 
 
-# Issue-slot roofline of the evolve kernel: the kernel is bound by integer
-# instruction issue and latency (instance data are staged in shared memory,
-# nothing streams from HBM), so the peak is one instruction per lane per clock
-# on every SM sub-partition: SMs x 128 lanes x f_max.  The algorithmic work of
-# one move evaluation is counted in integer operations as stated in
-# the design notes (Philox4x32-10 calls, roulette choices, position mapping,
-# junction lookups and distance gathers), with the mean number of steps per
-# candidate taken from the run's own K-step statistics.
+# Roofline of the evolve kernel.  The hot-path table's measure is the
+# distance gathers a move's delta needs (algorithmic, per operator
+# application): swap 8, 2-opt 4, insertion 6, or-opt 6, 3-opt 6 entries of
+# D; a QAP swap reads about 8n entries of F and D.  The operator mix and the
+# steps per candidate come from the run's own counts (cgo_op_counts: every
+# operator application of the whole solve).  The denominator is the random
+# 16-bit gather rate of shared memory measured on this GPU by the library's
+# microbenchmark (the triangle of D is staged in shared memory); the L2
+# random-gather rate is reported beside it.  The integer-issue view counts
+# the algorithmic integer operations of an evaluation against one
+# instruction per lane per clock on every SM sub-partition.
+D_GATHERS = {0: 8, 1: 4, 2: 6, 3: 6, 6: 6}
 OPS_PHILOX = 100          # 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key add)
 OPS_STEP = 120            # TSP: roulette 10 + decode 15 + 10 lookups x 5 + 10 gathers x 4 + sums 5
 OPS_CAND = 20             # K roulette, argmin share, stats
@@ -792,10 +857,24 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def roofline(evals_launch, kernel_ms, prob, clocks):
+def op_mix(counts: dict) -> dict:
+    """Measured operator mix and steps per candidate from whole-solve counts."""
+    u, uk = counts["u_op"], counts["u_k"]
+    apps, cands = sum(u), sum(uk)
+    names = {0: "swap", 1: "2opt", 2: "insert", 3: "oropt", 4: "flip", 5: "reset", 6: "3opt",
+             7: "segment"}
+    return {"evals": cands, "applications": apps,
+            "steps_per_eval": (uk[0] + 2 * uk[1] + 3 * uk[2]) / cands if cands else 0.0,
+            "k_share": [x / cands for x in uk] if cands else [],
+            "op_share": {names[i]: u[i] / apps for i in range(8) if u[i]} if apps else {}}
+
+
+def roofline(kernel_ms, prob, clocks):
     import torch
-    st = prob.state()
-    uk = st["u_k"]
+    from paper_2603_19163_gb300 import cgo
+    counts = prob.op_counts()
+    mix = op_mix(counts)
+    evals = mix["evals"]
     props = torch.cuda.get_device_properties(0)
     sms = props.multi_processor_count
     fmax = 2070.0
@@ -804,45 +883,43 @@ def roofline(evals_launch, kernel_ms, prob, clocks):
         fmax = float(pk.get("sm_max_mhz", fmax))
     except (OSError, ValueError):
         pass
-    # mean steps per candidate from the final window's K counts (fallback 1.25)
-    tot = sum(uk)
-    ek = (uk[0] + 2 * uk[1] + 3 * uk[2]) / tot if tot else 1.25
-    model = int(prob.inst["model"])
-    n = int(prob.inst["n"])
+    model, n = int(prob.inst["model"]), int(prob.inst["n"])
     qap = model == 1
-    step_ops = 25 + OPS_QAP_K * n if qap else OPS_STEP
-    ops_eval = ek * (OPS_PHILOX + step_ops) + OPS_CAND
-    achieved = evals_launch * ops_eval / (kernel_ms / 1000.0) / 1e12
-    peak = sms * 128 * fmax * 1e6 / 1e12
-    traffic = TRAFFIC_BYTES if kernel_sources_hash() == TRAFFIC_SOURCES else None
-    # the gather view: per counted step 8 tour positions and 8 distances
-    # (algorithmic; the kernel executes all 3 steps of every candidate: 48),
-    # against the random-gather rate measured on this GPU from a shared
-    # buffer (the triangle and tours are staged in shared memory)
-    from paper_2603_19163_gb300 import cgo
+    sec = kernel_ms / 1000.0
+    # algorithmic gathers of the whole launch, from the counted applications
+    if qap:
+        gathers = 8.0 * n * counts["u_op"][0]
+    else:
+        gathers = float(sum(D_GATHERS.get(i, 0) * counts["u_op"][i] for i in range(8)))
+    # what the kernel executes: TSP evaluates all three steps of every
+    # candidate (8 distance gathers and 8 tour reads each); QAP only the k
+    # steps that count
+    executed_d = 8.0 * n * counts["u_op"][0] if qap else 24.0 * evals
     g_peak, _ = cgo.gather_peak(0, 16)
     l2_peak, _ = cgo.gather_peak(1, 18)
-    # (QAP: 9 shared loads per k of the O(n) delta)
-    per_step = 9.0 * n + 2 if qap else 16.0
-    gathers_eval = per_step * ek
-    executed = per_step * (ek if qap else 3.0)
-    g_achieved = evals_launch * gathers_eval / (kernel_ms / 1000.0)
-    if not qap and kernel_sources_hash() != TRAFFIC_SOURCES:
-        traffic = None
-    if qap:
-        traffic = None
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "kernel": "evolve_kernel<%s>" % ("QAP" if qap else "TSP,int16"), "kernel_ms": kernel_ms,
-            "ops_per_eval": ops_eval, "ops_per_eval_steps": ek,
-            "peak_basis": "%d SMs x 128 lanes x %.0f MHz" % (sms, fmax),
-            "gather": {"achieved": g_achieved / 1e9, "peak": g_peak / 1e9, "unit": "G gathers/s",
-                       "frac": g_achieved / g_peak, "gathers_per_eval": gathers_eval,
-                       "executed_per_eval": executed,
-                       "executed_frac": evals_launch * executed / (kernel_ms / 1000.0) / g_peak,
-                       "peak_basis": "measured: random 16-bit gathers from a 128 KB shared buffer, "
-                                     "one 1024-thread CTA per SM (cgo_gather_peak kind 0)",
-                       "l2_random_gather_peak": l2_peak / 1e9}}
+    ek = mix["steps_per_eval"]
+    step_ops = 25 + OPS_QAP_K * n if qap else OPS_STEP
+    ops_eval = ek * (OPS_PHILOX + step_ops) + OPS_CAND
+    alu_peak = sms * 128 * fmax * 1e6
+    traffic = TRAFFIC_BYTES if (not qap and kernel_sources_hash() == TRAFFIC_SOURCES) else None
+    achieved = gathers / sec
+    return {"bound": "gather", "achieved": achieved / 1e9, "peak": g_peak / 1e9,
+            "unit": "G gathers/s", "frac": achieved / g_peak, "traffic": traffic,
+            "kernel": "evolve_kernel<%s>" % ("QAP" if qap else "TSP,int16"),
+            "kernel_ms": kernel_ms, "evals_per_launch": evals,
+            "gathers_per_launch": gathers, "gathers_per_eval": gathers / evals,
+            "gathers_per_application": ("8n per QAP swap" if qap else
+                                        "swap 8, 2opt 4, insert 6, oropt 6, 3opt 6"),
+            "op_mix": mix,
+            "peak_basis": "measured on this GPU: random 16-bit gathers from a 128 KB shared "
+                          "buffer, one 1024-thread CTA per SM (cgo_gather_peak kind 0)",
+            "executed_gathers_per_eval": executed_d / evals,
+            "executed_frac": executed_d / sec / g_peak,
+            "l2_random_gather_peak": l2_peak / 1e9,
+            "alu": {"achieved": evals * ops_eval / sec / 1e12, "peak": alu_peak / 1e12,
+                    "unit": "T int-ops/s", "frac": evals * ops_eval / sec / alu_peak,
+                    "ops_per_eval": ops_eval,
+                    "peak_basis": "%d SMs x 128 lanes x %.0f MHz" % (sms, fmax)}}
 
 
 if __name__ == "__main__":

@@ -246,6 +246,18 @@ cgo_status cgo_state_get(const cgo_problem *prob, cgo_state *out);
 cgo_status cgo_state_set(cgo_problem *prob, const cgo_params *params, uint64_t seed,
                          const cgo_state *state);
 
+/* Operator statistics of the search so far (Sec. 4.2.2 counts the uses of
+ * every operator and how many improved, for the AOS update; this call sums
+ * them over every generation since the last cgo_solve or cgo_state_set,
+ * closed AOS windows and the open one).  out[0..7]: steps that applied
+ * operator slot i (cgo_op order); out[8..15]: of those, steps of an
+ * improving candidate (delta < 0); out[16..18]: candidates of k = 1, 2, 3
+ * steps; out[19..21]: of those, improving candidates.  cap >= 22, else
+ * CGO_ERR_INVALID; CGO_ERR_STATE before any solve.  The counts are the ones
+ * the AOS update reads, so sum(out[16..18]) = population x candidates x
+ * generations. */
+cgo_status cgo_op_counts(const cgo_problem *prob, uint64_t *out, int32_t cap);
+
 /* Batched solve: `count` independent problems (different models and sizes
  * allowed) advance together in persistent kernels; problem i uses
  * per_prob[i] and seeds[i].  Each result is bit-identical to cgo_solve of

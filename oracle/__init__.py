@@ -52,7 +52,9 @@ class OrcState(ctypes.Structure):
                 ("elite_prev", ctypes.c_int64),
                 ("u_op", ctypes.c_uint32 * NOPS), ("v_op", ctypes.c_uint32 * NOPS),
                 ("u_k", ctypes.c_uint32 * 3), ("v_k", ctypes.c_uint32 * 3),
-                ("cur", _i32p), ("best_sol", _i32p), ("cost", _i64p), ("best_cost", _i64p)]
+                ("cur", _i32p), ("best_sol", _i32p), ("cost", _i64p), ("best_cost", _i64p),
+                ("all_u_op", ctypes.c_uint64 * NOPS), ("all_v_op", ctypes.c_uint64 * NOPS),
+                ("all_u_k", ctypes.c_uint64 * 3), ("all_v_k", ctypes.c_uint64 * 3)]
 
 
 _LIB = None
@@ -267,7 +269,9 @@ def state_dict(st: OrcState, arrays: dict) -> dict:
     d = {k: v.copy() for k, v in arrays.items()}
     d.update(P=st.P, len=st.len, g=st.g, T=st.T, w_op=list(st.w_op), w_k=list(st.w_k),
              stag=st.stag, elite_prev=st.elite_prev, u_op=list(st.u_op), v_op=list(st.v_op),
-             u_k=list(st.u_k), v_k=list(st.v_k))
+             u_k=list(st.u_k), v_k=list(st.v_k),
+             op_counts=dict(u_op=list(st.all_u_op), v_op=list(st.all_v_op), u_k=list(st.all_u_k),
+                            v_k=list(st.all_v_k)))
     return d
 
 

@@ -531,6 +531,8 @@ int32_t orc_init(const orc_instance *in, const orc_params *pr, uint64_t seed, or
     st->u_op[i] = st->v_op[i] = 0;
   }
   for (int32_t i = 0; i < 3; i++) { st->w_k[i] = pr->w_k[i]; st->u_k[i] = st->v_k[i] = 0; }
+  for (int32_t i = 0; i < ORC_NOPS; i++) st->all_u_op[i] = st->all_v_op[i] = 0;
+  for (int32_t i = 0; i < 3; i++) st->all_u_k[i] = st->all_v_k[i] = 0;
   st->stag = 0;
   int32_t lb = 0, ub = 1;
   if (enc == 2) int_bounds(in, &lb, &ub);
@@ -970,6 +972,8 @@ int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc
       const uint32_t *c = cnt + (int64_t)p * 22;
       for (int32_t i = 0; i < ORC_NOPS; i++) { st->u_op[i] += c[i]; st->v_op[i] += c[8 + i]; }
       for (int32_t i = 0; i < 3; i++) { st->u_k[i] += c[16 + i]; st->v_k[i] += c[19 + i]; }
+      for (int32_t i = 0; i < ORC_NOPS; i++) { st->all_u_op[i] += c[i]; st->all_v_op[i] += c[8 + i]; }
+      for (int32_t i = 0; i < 3; i++) { st->all_u_k[i] += c[16 + i]; st->all_v_k[i] += c[19 + i]; }
     }
     st->T = orc_cool(st->T, pr->alpha);
     st->g++;

@@ -76,6 +76,9 @@ typedef struct {
   uint32_t u_op[ORC_NOPS], v_op[ORC_NOPS], u_k[3], v_k[3]; /* open window */
   int32_t *cur, *best_sol;
   int64_t *cost, *best_cost;
+  /* the same counts summed over every generation since init (statistics for
+   * the caller; the search never reads them) */
+  uint64_t all_u_op[ORC_NOPS], all_v_op[ORC_NOPS], all_u_k[3], all_v_k[3];
 } orc_state;
 
 /* building blocks, exported for the oracle's own pin tests */

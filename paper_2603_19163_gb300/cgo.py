@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
                 "cgo_best": ([vp, _i32p, c.c_int32, _i64p], c.c_int),
                 "cgo_solution_length": ([vp, _i32p], c.c_int),
                 "cgo_state_get": ([vp, P(cgo_state)], c.c_int),
+                "cgo_op_counts": ([vp, P(c.c_uint64), c.c_int32], c.c_int),
                 "cgo_state_set": ([vp, P(cgo_params), c.c_uint64, P(cgo_state)], c.c_int),
                 "cgo_solve_batch": ([P(vp), P(cgo_params), P(c.c_uint64), c.c_int32, vp], c.c_int),
                 "cgo_last_error": ([], c.c_char_p),
@@ -307,6 +308,13 @@ class Problem:
                    w_k=list(s.w_k_q16), stag=s.stag, elite_prev=s.elite_prev,
                    u_op=list(s.u_op), v_op=list(s.v_op), u_k=list(s.u_k), v_k=list(s.v_k))
         return arr
+
+    def op_counts(self) -> dict:
+        """Operator and k-level counts over every generation of the solve so far."""
+        out = (ctypes.c_uint64 * 22)()
+        check(lib().cgo_op_counts(self.h, out, 22), "cgo_op_counts")
+        v = list(out)
+        return dict(u_op=v[0:8], v_op=v[8:16], u_k=v[16:19], v_k=v[19:22])
 
     def set_state(self, params: dict, seed: int, st: dict):
         s = cgo_state()

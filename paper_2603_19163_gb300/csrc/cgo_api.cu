@@ -879,6 +879,19 @@ cgo_status cgo_best(const cgo_problem *p, int32_t *out_sol, int32_t cap, int64_t
   return CGO_OK;
 }
 
+cgo_status cgo_op_counts(const cgo_problem *p, uint64_t *out, int32_t cap) {
+  if (!p || !out) return fail(CGO_ERR_INVALID, "NULL argument");
+  if (cap < kStats) return fail(CGO_ERR_INVALID, "cap %d < %d", cap, kStats);
+  Guard gd(p);
+  if (!gd.ok) return fail(CGO_ERR_BUSY, "problem handle in use");
+  if (!p->has_state) return fail(CGO_ERR_STATE, "no search state");
+  cudaSetDevice(p->device);
+  DevAos a;
+  CUDA_TRY(copy_sync(&a, p->d_aos + p->aos_cur, sizeof a, cudaMemcpyDeviceToHost), "reading counts");
+  for (int i = 0; i < kStats; ++i) out[i] = a.cum[i] + a.pend[i];
+  return CGO_OK;
+}
+
 cgo_status cgo_state_get(const cgo_problem *p, cgo_state *o) {
   if (!p || !o || o->struct_size != sizeof(cgo_state)) return fail(CGO_ERR_INVALID, "bad state struct");
   Guard gd(p);

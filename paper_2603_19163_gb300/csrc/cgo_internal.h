@@ -29,6 +29,8 @@ struct DevAos {
   int32_t elite;              // member index of the elite (after finalize)
   int32_t pad1;
   int64_t elite_cost;
+  uint64_t cum[kStats];       // counts of every closed window since the solve began
+                              // (reported to the caller; the search never reads them)
 };
 
 // Per-launch synchronisation block (zeroed/reset by the host before a launch).

@@ -1513,6 +1513,9 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   uint32_t stag = A->stag;
   long long elite_prev = A->elite_prev;
   uint32_t pend = lane < kStats ? A->pend[lane] : 0u;
+  // the first warp of member 0 keeps the cumulative window counts
+  const bool cum_owner = p0 + G.grp == 0 && G.gw == 0;
+  if (cum_owner && lane < kStats && I.aos_out != A) I.aos_out->cum[lane] = A->cum[lane];
   // the instance scalars are updated in place by a CTA-local unit: everyone
   // reads them before anyone can write them back
   if (nact > 0) cta_bar(kLocalBar, nact);
@@ -1829,6 +1832,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     prev_acc[slot] = cum;
     if (!pend_used) total += pend;
     pend_used = true;
+    if (cum_owner && lane < kStats) I.aos_out->cum[lane] += total;
     const long long elite = ld_relaxed64((const long long *)&S->elite[slot]);
     ++wi;
 

@@ -37,3 +37,11 @@ def assert_same_state(g, o, where=""):
 
 def oracle_run(inst, params, seed, G, threads=0):
     return O.solve(inst, params, seed, G, threads=threads)
+
+
+def assert_same_counts(prob, o, where=""):
+    """Operator and k-level counts over the whole solve (cgo_op_counts) equal
+    the oracle's, and the k-level counts add up to P x C x G."""
+    g = prob.op_counts()
+    for k in ("u_op", "v_op", "u_k", "v_k"):
+        assert g[k] == o["op_counts"][k], "%s: %s gpu %r oracle %r" % (where, k, g[k], o["op_counts"][k])

@@ -10,7 +10,7 @@ import pytest
 
 import instances as I
 import oracle as O
-from helpers import assert_same_state, oracle_run, params_for
+from helpers import assert_same_counts, assert_same_state, oracle_run, params_for
 
 pytestmark = pytest.mark.gpu
 SW = O.SWAP
@@ -90,8 +90,10 @@ def test_batch_matches_oracle(cgo, slice_len):
         seeds = [100 + i for i in range(len(items))]
         probs, params = run_batch(cgo, items, seeds)
         for (inst, _), prob, p, seed in zip(items, probs, params, seeds):
-            assert_same_state(prob.state(), oracle_run(inst, p, seed, p["G"]),
-                              "model %d n %d slice %d" % (inst["model"], inst["n"], slice_len))
+            o = oracle_run(inst, p, seed, p["G"])
+            where = "model %d n %d slice %d" % (inst["model"], inst["n"], slice_len)
+            assert_same_state(prob.state(), o, where)
+            assert_same_counts(prob, o, where)
     finally:
         cgo.lib().cgo_debug_inject(None, 3, 2000)
 

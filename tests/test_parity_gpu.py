@@ -12,7 +12,7 @@ import pytest
 import instances as I
 import oracle as O
 from conftest import SEEDS
-from helpers import assert_same_state, oracle_run, params_for
+from helpers import assert_same_counts, assert_same_state, oracle_run, params_for
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +49,8 @@ def test_tsp_n20_config(cgo, seed, ns):
     prob, g, o = run_both(cgo, inst, p, seed, ns=ns)
     assert prob.get_launch()[3] == ns
     assert_same_state(g, o, "tsp20 seed %d ns %d" % (seed, ns))
+    assert_same_counts(prob, o, "tsp20 seed %d ns %d" % (seed, ns))
+    assert sum(prob.op_counts()["u_k"]) == 32 * 128 * 2000
 
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 33])
@@ -530,13 +532,16 @@ def test_split_solve_and_checkpoint_resume(cgo, maker):
     g = prob.state()
     o = oracle_run(inst, p, 21, 34)
     assert_same_state(g, o, "split")
+    assert_same_counts(prob, o, "split")
     # checkpoint at g=34, resume on a fresh handle
     prob2 = cgo.Problem(inst)
     prob2.set_state(p, 21, g)
     prob2.solve_continue(9)
     prob.solve_continue(9)
     assert_same_state(prob2.state(), prob.state(), "resume")
-    assert_same_state(prob.state(), oracle_run(inst, p, 21, 43), "resume vs oracle")
+    o43 = oracle_run(inst, p, 21, 43)
+    assert_same_state(prob.state(), o43, "resume vs oracle")
+    assert_same_counts(prob, o43, "split, 43 generations")
 
 
 @pytest.mark.parametrize("maker", [lambda: I.tsp_uniform(28, 65), lambda: I.gap(30, 66, m=5),
