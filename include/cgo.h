@@ -169,22 +169,24 @@ typedef struct {
 
 /* Launch shape (the autotuner's choice, or a caller override).  The C
  * candidates of a member's generation are split over warps_per_member warps.
- * With gens_in_flight = 2 a member has two such warp sets: one evaluates
- * generation g, the other generation g + 1 against the same solution, which
- * stands unless g accepts a move (then g + 1 is evaluated again); the
- * results are the same either way.  A CTA holds
+ * With gens_in_flight = s > 1 a member has s such warp sets: set i evaluates
+ * generation g + i against the same solution, which stands unless an
+ * earlier generation of the set accepts a move (the later ones are then
+ * evaluated again); the results are the same either way.  A CTA holds
  * warps_per_cta / (warps_per_member * gens_in_flight) members.  Launch
  * shapes never change results. */
 typedef struct {
   uint32_t struct_size;        /* = sizeof(cgo_launch) */
-  int32_t warps_per_cta;       /* 0 = auto; else 1 .. 8, a multiple of
+  int32_t warps_per_cta;       /* 0 = auto; else 1 .. 8 (1 .. 16 with 3 or 4
+                                  generations in flight), a multiple of
                                   warps_per_member * gens_in_flight */
   int32_t warps_per_member;    /* 0 = auto; else 1, 2 or 4 */
   int32_t staging;             /* 0 = auto, 1 = instance data in shared memory,
                                   2 = instance data read through L2 */
-  int32_t gens_in_flight;      /* 0 = auto; 1; or 2 (single solves with at most
-                                  32 * warps_per_member candidates; batched
-                                  solves use 1) */
+  int32_t gens_in_flight;      /* 0 = auto; 1 .. 4 for single solves with at
+                                  most 32 * warps_per_member candidates (3 and 4
+                                  with warps_per_member = 4 and neither island
+                                  migration nor crossover); batched solves use 1 */
 } cgo_launch;
 
 /* Create a problem: validates the description and deep-copies the data to

@@ -35,14 +35,17 @@ class Autotuner:
         """(warps per CTA, warps per member generation, staging, generations
         in flight) candidates for a single solve."""
         out = []
+        xf = int(params.get("islands", 1)) > 1 or int(params.get("cross_q16", 0)) > 0
         for wpm in (4, 2, 1):
             if wpm * 32 > max(32, params["C"]) * 2:
                 continue
-            for ns in (2, 1):
-                if ns == 2 and params["C"] > 32 * wpm:
+            for ns in (4, 3, 2, 1):
+                if ns >= 2 and params["C"] > 32 * wpm:
+                    continue
+                if ns > 2 and (wpm != 4 or xf):
                     continue
                 for mpc in (1, 2):
-                    if wpm * ns * mpc <= 8:
+                    if wpm * ns * mpc <= (16 if ns > 2 else 8) and (ns <= 2 or mpc == 1):
                         for staging in (SMEM, GLOBAL):
                             out.append((wpm * ns * mpc, wpm, staging, ns))
         return out

@@ -366,23 +366,34 @@ cgo_status choose_launch(cgo_problem *p, KInst &h, int *warps_out, int *wpm_out,
   const int P = h.P, C = h.C;
   int wpm = p->wpm_override;
   if (wpm == 0) wpm = C >= 128 ? 4 : (C >= 64 ? 2 : 1);
-  // a second generation in flight holds one candidate's counts per lane
-  const bool two_ok = C <= 32 * wpm && 2 * wpm <= kMaxWarps;
-  int ns_try[2] = {2, 1}, nns = 2;
-  if (p->ns_override == 2) {
-    if (!two_ok)
+  // a later generation in flight holds one candidate's counts per lane; three
+  // or four in flight take 4 warps per generation (migration and crossover
+  // kernels take at most two)
+  auto ns_ok = [&](int ns) {
+    if (ns == 1) return true;
+    if (C > 32 * wpm) return false;
+    if (ns == 2) return 2 * wpm <= kMaxWarps;
+    return wpm == 4 && !takes_xf(h);
+  };
+  int ns_try[4] = {2, 1, 0, 0}, nns = 2;
+  if (p->ns_override > 0) {
+    if (!ns_ok(p->ns_override))
       return fail(CGO_ERR_UNSUPPORTED,
-                  "two generations in flight need C <= 32 * warps_per_member and 2 * warps_per_member <= %d",
-                  kMaxWarps);
+                  "%d generations in flight need C <= 32 * warps_per_member (and, for 3 or 4, "
+                  "warps_per_member = 4 without migration or crossover)",
+                  p->ns_override);
+    ns_try[0] = p->ns_override;
     nns = 1;
-  } else if (p->ns_override == 1 || !two_ok) {
+  } else if (!ns_ok(2)) {
     ns_try[0] = 1;
     nns = 1;
   }
   int fit_seen = 0, grid_seen = 0;
   for (int t = 0; t < nns; ++t) {
     const int ns = ns_try[t];
-    for (int mpc = 1; mpc * wpm * ns <= kMaxWarps; mpc *= 2) {
+    const int max_warps = ns > 2 ? kMaxWarpsDeep : kMaxWarps;
+    for (int mpc = 1; mpc * wpm * ns <= max_warps; mpc *= 2) {
+      if (ns > 2 && mpc > 1) break;  // one member per CTA
       const int warps = mpc * wpm * ns;
       if (p->warps_override > 0 && warps != p->warps_override) continue;
       const int64_t staged = evolve_smem_bytes(h, warps, wpm, ns, true);
@@ -786,13 +797,16 @@ cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
 
 cgo_status cgo_set_launch(cgo_problem *p, const cgo_launch *l) {
   if (!p || !l || l->struct_size != sizeof(cgo_launch)) return fail(CGO_ERR_INVALID, "bad launch struct");
-  if (l->warps_per_cta < 0 || l->warps_per_cta > kMaxWarps)
-    return fail(CGO_ERR_INVALID, "warps_per_cta must be in [0, %d]", kMaxWarps);
+  if (l->gens_in_flight < 0 || l->gens_in_flight > 4)
+    return fail(CGO_ERR_INVALID, "gens_in_flight must be in [0, 4]");
+  const int max_warps = l->gens_in_flight > 2 ? kMaxWarpsDeep : kMaxWarps;
+  if (l->warps_per_cta < 0 || l->warps_per_cta > max_warps)
+    return fail(CGO_ERR_INVALID, "warps_per_cta must be in [0, %d]", max_warps);
   if (l->warps_per_member != 0 && l->warps_per_member != 1 && l->warps_per_member != 2 &&
       l->warps_per_member != 4)
     return fail(CGO_ERR_INVALID, "warps_per_member must be 0, 1, 2 or 4");
-  if (l->gens_in_flight < 0 || l->gens_in_flight > 2)
-    return fail(CGO_ERR_INVALID, "gens_in_flight must be 0, 1 or 2");
+  if (l->gens_in_flight > 2 && l->warps_per_member != 4 && l->warps_per_member != 0)
+    return fail(CGO_ERR_INVALID, "3 or 4 generations in flight take warps_per_member = 4");
   const int unit = (l->warps_per_member > 0 ? l->warps_per_member : 1) *
                    (l->gens_in_flight > 0 ? l->gens_in_flight : 1);
   if (l->warps_per_cta > 0 && l->warps_per_cta % unit)

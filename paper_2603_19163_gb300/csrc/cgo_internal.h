@@ -9,6 +9,9 @@ namespace cgo {
 constexpr int kNops = 8;
 constexpr int kStats = 22;      // u_op[8] v_op[8] u_k[3] v_k[3]
 constexpr int kMaxWarps = 8;    // warps per CTA (kernel launch bound 256 threads)
+// warps per CTA of a single solve with 3 or 4 generations in flight (one
+// member of 4 warps per generation; launch bound 32 x that)
+constexpr int kMaxWarpsDeep = 16;
 constexpr int kMaxAgents = 64;  // GAP agents
 
 enum Model { TSP = 0, QAP = 1, KNAPSACK = 2, GAP = 3, CVRPTW = 4 };

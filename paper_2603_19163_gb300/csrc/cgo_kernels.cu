@@ -2075,7 +2075,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
 // instance, one member per group of WPM warps (cooperative launch, so that
 // all members are resident together for the window barriers).
 template <int MODEL, bool T16, int WPM, int NS, bool XF>
-__global__ void __launch_bounds__(kMaxWarps * 32, 1)
+__global__ void __launch_bounds__((WPM * NS > kMaxWarps ? WPM * NS : kMaxWarps) * 32, 1)
     evolve_kernel(const __grid_constant__ KInst I, int warps, uint64_t timeout_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const bool staged = I.shared_bytes > 0;
@@ -2468,6 +2468,10 @@ cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri, 
 
 template <int MODEL, bool T16, bool XF>
 static const void *evolve_fn(int wpm, int ns) {
+  // three or four generations in flight: one candidate per lane of 4 warps
+  if (ns == 4) return wpm == 4 ? (const void *)evolve_kernel<MODEL, T16, 4, 4, XF> : nullptr;
+  if (ns == 3) return wpm == 4 ? (const void *)evolve_kernel<MODEL, T16, 4, 3, XF> : nullptr;
+  if (ns != 1 && ns != 2) return nullptr;
   if (ns == 2) {
     if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2, XF>;
     if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 2, XF>;
@@ -2609,6 +2613,7 @@ int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, int ns, bool stage
 #else   // CGO_XF_UNIT: the single-solve and batched kernels with migration and crossover
 template <int MODEL, bool T16>
 static const void *evolve_fn_xf(int wpm, int ns) {
+  if (ns != 1 && ns != 2) return nullptr;  // built with one or two generations in flight
   if (ns == 2) {
     if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2, true>;
     if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 2, true>;

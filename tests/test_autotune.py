@@ -1,5 +1,5 @@
-"""Host logic of the autotuner's serving-population rule (no GPU)."""
-from paper_2603_19163_gb300.autotune import population_for_load
+"""Host logic of the autotuner (no GPU): trial shapes and the serving-population rule."""
+from paper_2603_19163_gb300.autotune import Autotuner, population_for_load
 
 
 def test_population_rule_keeps_everything_at_the_top_when_it_fits():
@@ -22,3 +22,12 @@ def test_population_rule_steps_down_the_heaviest_class_first():
 def test_population_rule_reports_overload_at_the_bottom():
     P, load = population_for_load({"x": 1e6}, {"x": 1.0}, 1000.0, 20000, 128)
     assert P == {"x": 8} and load > 0.8
+
+
+def test_solve_shapes_cover_deep_generations_only_where_they_run():
+    t = Autotuner()
+    shapes = t.solve_shapes(dict(C=128))
+    assert (12, 4, 1, 3) in shapes and (16, 4, 1, 4) in shapes and (8, 4, 1, 2) in shapes
+    assert all(s[3] <= 2 or (s[1] == 4 and s[0] == 4 * s[3]) for s in shapes)
+    assert all(s[3] <= 2 for s in t.solve_shapes(dict(C=128, cross_q16=100)))
+    assert all(s[3] == 1 for s in t.solve_shapes(dict(C=300)))

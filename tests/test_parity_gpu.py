@@ -132,6 +132,56 @@ def test_two_generations_in_flight_every_model(cgo):
             assert_same_state(g, o, "model %d T0 %d" % (inst["model"], T0))
 
 
+@pytest.mark.parametrize("ns", [3, 4])
+@pytest.mark.parametrize("T0", [0, 40 << 32, 1 << 44])
+@pytest.mark.parametrize("C", [1, 77, 128])
+def test_deep_generations_in_flight(cgo, ns, T0, C):
+    """Three or four generations evaluated against the same solution and
+    decided in order (later ones redone after an accepted move), over odd
+    windows, windows across 32-generation blocks and split launches."""
+    inst = I.tsp_uniform(37, 87)
+    p = params_for(inst, P=9, C=C, G=45, U=7, elite_period=14, T0=T0, ops=[SW, TO, INS, OR])
+    prob, g, o = run_both(cgo, inst, p, 11, wpm=4, ns=ns)
+    assert prob.get_launch()[3] == ns and prob.get_launch()[0] == 4 * ns
+    assert_same_state(g, o, "ns=%d C=%d T0=%d" % (ns, C, T0))
+    prob.solve_continue(13)
+    prob.solve_continue(1)
+    prob.solve_continue(22)
+    o81 = oracle_run(inst, p, 11, 81)
+    assert_same_state(prob.state(), o81, "continued")
+    assert_same_counts(prob, o81, "ns=%d" % ns)
+
+
+@pytest.mark.parametrize("ns", [3, 4])
+def test_deep_generations_every_model(cgo, ns):
+    for inst, ops in ((I.tsp_uniform(31, 88), None), (I.qap_random(11, 89), [SW]),
+                      (I.knapsack(90, 90), None), (I.gap(45, 91, m=7), None),
+                      (I.cvrptw(14, 92, vehicles=4, capacity=80), None),
+                      (I.tsp_clustered(90, 93), [SW, TO, INS, OR, TH])):
+        for T0 in (0, 30 << 32):
+            over = dict(P=6, C=128, G=33, U=5, elite_period=10, T0=T0)
+            if ops:
+                over["ops"] = ops
+            p = params_for(inst, **over)
+            prob, g, o = run_both(cgo, inst, p, 4, wpm=4, ns=ns)
+            assert prob.get_launch()[3] == ns
+            assert_same_state(g, o, "model %d T0 %d ns %d" % (inst["model"], T0, ns))
+
+
+def test_deep_generations_limits(cgo):
+    inst = I.tsp_uniform(20, 94)
+    prob = cgo.Problem(inst)
+    with pytest.raises(cgo.CgoError):
+        prob.set_launch(0, 0, 2, 3)              # 3 in flight take 4 warps per generation
+    with pytest.raises(cgo.CgoError):
+        prob.set_launch(20, 0, 4, 4)             # beyond 16 warps per CTA
+    prob.set_launch(0, 0, 4, 3)
+    with pytest.raises(cgo.CgoError):            # more candidates than lanes
+        prob.solve(params_for(inst, P=4, C=129, G=5), 1)
+    with pytest.raises(cgo.CgoError):            # crossover kernels take at most two
+        prob.solve(params_for(inst, P=4, C=128, G=5, cross_q16=30000), 1)
+
+
 def test_two_generations_need_one_candidate_per_lane(cgo):
     inst = I.tsp_uniform(20, 86)
     p = params_for(inst, P=4, C=65, G=5)
@@ -196,6 +246,9 @@ def test_tsp442_clustered_prefix(cgo):
     p = params_for(inst, P=128, C=128, G=60, op_mask=(1 << TO) | (1 << OR) | (1 << INS))
     _, g, o = run_both(cgo, inst, p, 1)
     assert_same_state(g, o, "tsp442")
+    for ns in (3, 4):
+        _, g, _ = run_both(cgo, inst, p, 1, wpm=4, ns=ns)
+        assert_same_state(g, o, "tsp442 ns %d" % ns)
 
 
 # --------------------------------------------------------------------- QAP
