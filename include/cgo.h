@@ -80,11 +80,27 @@ typedef enum {
      elements from i = pos(a, length - L + 1); needs length >= 2; off in the
      default mask */
   CGO_OP_SEG_FLIP = 7,  /* binary: flip every element of the segment */
-  CGO_OP_SEG_RESET = 7  /* integer: add one offset d = 1 + pos(b, R - 1) to every element of
+  CGO_OP_SEG_RESET = 7, /* integer: add one offset d = 1 + pos(b, R - 1) to every element of
                            the segment, modulo the range R (the random reset's rule) */
+  /* row level (Table "operators"; Sec. 3.1's multi-row solutions): the rows
+     of CVRPTW's separator encoding are its V routes, route r running from
+     just after the r-th separator to the next one; they need V >= 2 and
+     are off in the default mask */
+  CGO_OP_ROW_SWAP = 8,  /* routes r1 = pos(a, V), r2 = pos(b, V - 1) stepped over r1 exchange
+                           their customers */
+  CGO_OP_ROW_MERGE = 9, /* r = pos(a, V - 1): route r takes route r + 1's customers (the
+                           separator between them moves to the end of route r + 1) */
+  CGO_OP_ROW_SPLIT = 10 /* r = pos(a, V): with c >= 2 customers on r and an empty route, the
+                           separator of the lowest-index empty route moves inside r after its
+                           first 1 + pos(b, c - 1) customers; otherwise nothing changes */
 } cgo_op;
 
+/* operator slots in cgo_params.op_w0_q16 / op_cap_q16 and cgo_state's
+   arrays (slots 0 .. 7); the row level's slots 8 .. 10 have arrays of their
+   own appended to those structs */
 #define CGO_NOPS 8
+#define CGO_NROW 3
+#define CGO_NOPS_ALL (CGO_NOPS + CGO_NROW)
 
 typedef struct cgo_problem cgo_problem;  /* opaque; owns device copies + search state */
 
@@ -148,7 +164,20 @@ typedef struct {
                                   (<= 65536; 0 = off): order crossover for permutations,
                                   uniform crossover for binary / integer vectors (Table
                                   "operators", crossover level) with another member's best */
+  /* --- appended: the row level (operator slots 8 .. 10) --- */
+  uint32_t row_w0_q16[CGO_NROW];  /* initial weights of CGO_OP_ROW_SWAP .. _SPLIT */
+  uint32_t row_cap_q16[CGO_NROW]; /* their caps */
 } cgo_params;
+
+/* The size of cgo_params and cgo_state before the row-level fields were
+ * appended.  Calls that take these structs accept that size too: an
+ * earlier cgo_params leaves the row operators off, an earlier cgo_state
+ * carries no row-level weights or counts (so it cannot be written back
+ * while row operators are on).  cgo_params_default fills the earlier
+ * layout when the caller sets struct_size to it before the call.  (Both
+ * sizes are the earlier structs' sizeof, tail padding included.) */
+#define CGO_PARAMS_SIZE_V1 ((uint32_t)((offsetof(cgo_params, row_w0_q16) + 7u) & ~(size_t)7u))
+#define CGO_STATE_SIZE_V1 ((uint32_t)((offsetof(cgo_state, w_row_q16) + 7u) & ~(size_t)7u))
 
 /* Full search state (checkpoint).  Scalars are filled/read by value; the
  * four arrays are caller-owned host buffers (NULL = skip on get). */
@@ -165,6 +194,9 @@ typedef struct {
   int32_t *best_sol;           /* [P * length] best solution of each member */
   int64_t *cost;               /* [P] current costs */
   int64_t *best_cost;          /* [P] best costs */
+  /* --- appended: the row level (operator slots 8 .. 10) --- */
+  uint32_t w_row_q16[CGO_NROW];
+  uint32_t u_row[CGO_NROW], v_row[CGO_NROW];  /* counts of the open window */
 } cgo_state;
 
 /* Launch shape (the autotuner's choice, or a caller override).  The C
@@ -205,7 +237,11 @@ cgo_status cgo_problem_destroy(cgo_problem *prob);
  * solution length <= 100 / <= 250 / > 250, normalised to Q16),
  * K weights (0.8, 0.15, 0.05), T0 = 100, alpha = 0.999, U = 10 (I = 10,
  * Sec. 4.2.2), EMA a = 0.8, floor 0.05, cap 0.6, stagnation after 5
- * updates, no elite injection. */
+ * updates, no elite injection.  3-opt, the segment operators and the row
+ * operators are off in the default mask; their priors are filled in (the
+ * row level takes the O(1) prior 1.0), normalised with the default set.
+ * out->struct_size = CGO_PARAMS_SIZE_V1 before the call asks for the earlier
+ * layout; otherwise the current one is written. */
 cgo_status cgo_params_default(const cgo_problem *prob, cgo_params *out);
 
 /* Override the launch shape (warps per CTA, staging mode) used by the next
@@ -251,13 +287,13 @@ cgo_status cgo_state_set(cgo_problem *prob, const cgo_params *params, uint64_t s
 /* Operator statistics of the search so far (Sec. 4.2.2 counts the uses of
  * every operator and how many improved, for the AOS update; this call sums
  * them over every generation since the last cgo_solve or cgo_state_set,
- * closed AOS windows and the open one).  out[0..7]: steps that applied
- * operator slot i (cgo_op order); out[8..15]: of those, steps of an
- * improving candidate (delta < 0); out[16..18]: candidates of k = 1, 2, 3
- * steps; out[19..21]: of those, improving candidates.  cap >= 22, else
- * CGO_ERR_INVALID; CGO_ERR_STATE before any solve.  The counts are the ones
- * the AOS update reads, so sum(out[16..18]) = population x candidates x
- * generations. */
+ * closed AOS windows and the open one).  out[0..10]: steps that applied
+ * operator slot i (cgo_op order, CGO_NOPS_ALL slots); out[11..21]: of those,
+ * steps of an improving candidate (delta < 0); out[22..24]: candidates of
+ * k = 1, 2, 3 steps; out[25..27]: of those, improving candidates.
+ * cap >= 28, else CGO_ERR_INVALID; CGO_ERR_STATE before any solve.  The
+ * counts are the ones the AOS update reads, so sum(out[22..24]) =
+ * population x candidates x generations. */
 cgo_status cgo_op_counts(const cgo_problem *prob, uint64_t *out, int32_t cap);
 
 /* Batched solve: `count` independent problems (different models and sizes

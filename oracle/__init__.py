@@ -14,8 +14,9 @@ import numpy as np
 
 from . import build as _build
 
-NOPS = 8
+NOPS = 11
 SWAP, TWO_OPT, INSERT, OR_OPT, FLIP, PERTURB, THREE_OPT, SEGMENT = range(8)
+ROW_SWAP_OP, ROW_MERGE_OP, ROW_SPLIT_OP = 8, 9, 10     # operator slots of the row level
 SEG_FLIP = SEG_RESET = SEGMENT     # slot 7: the binary and the integer segment operator
 
 _i32p = ctypes.POINTER(ctypes.c_int32)

@@ -259,7 +259,8 @@ int32_t orc_valid(const orc_instance *in, const int32_t *sol) {
 
 /* Operators per encoding (Table "operators"): permutation -> swap, reverse
  * (2-opt), insert, or-opt, 3-opt; binary -> flip, seg_flip; integer ->
- * random reset, seg_reset. */
+ * random reset, seg_reset; the row level (row_swap, row_merge, row_split)
+ * applies to CVRPTW, whose rows are its V >= 2 routes [R32]. */
 int32_t orc_enabled_ops(const orc_instance *in, uint32_t op_mask, int32_t enabled[ORC_NOPS]) {
   int32_t enc = encoding_of(in->model), len = orc_solution_length(in), count = 0;
   for (int32_t i = 0; i < ORC_NOPS; i++) {
@@ -269,6 +270,7 @@ int32_t orc_enabled_ops(const orc_instance *in, uint32_t op_mask, int32_t enable
     if (enc == 1 && i == ORC_FLIP) ok = 1;
     if (enc == 2 && i == ORC_PERTURB) ok = 1;
     if (enc != 0 && i == ORC_SEGMENT) ok = (len >= 2);                         /* [R28] */
+    if (i >= ORC_ROW_SWAP) ok = in->model == ORC_CVRPTW && in->vehicles >= 2;  /* [R32] */
     enabled[i] = ok && ((op_mask >> i) & 1u);
     count += enabled[i];
   }
@@ -287,6 +289,8 @@ static void pick_ij(uint32_t a, uint32_t b, int32_t len, int32_t *i, int32_t *j)
 int32_t orc_apply_move(const orc_instance *in, int32_t op, uint32_t a, uint32_t b, uint32_t x,
                        int32_t *s, int32_t len) {
   int32_t i, j;
+  if (op >= ORC_ROW_SWAP && op <= ORC_ROW_SPLIT)   /* [R32] the row level */
+    return orc_row_move(in, op - ORC_ROW_SWAP, a, b, s, len) == 0 ? 0 : -1;
   switch (op) {
     case ORC_SWAP: { /* exchange two elements */
       pick_ij(a, b, len, &i, &j);
@@ -420,11 +424,12 @@ void orc_params_default(const orc_instance *in, orc_params *pr) {
   pr->C = 128;
   pr->op_mask = 0x3Fu;
   /* priors of every applicable operator (Table "weight_preset"); the
-   * normaliser is taken over the default mask (3-opt and the segment
-   * operators off by default) */
+   * normaliser is taken over the default mask (3-opt, the segment and the
+   * row operators off by default).  The row operators take the O(1) prior
+   * 1.0: the table scales only the listed high-complexity operators [R32]. */
   int32_t app[ORC_NOPS];
   orc_enabled_ops(in, pr->op_mask, en);
-  orc_enabled_ops(in, 0xFFu, app);
+  orc_enabled_ops(in, (1u << ORC_NOPS) - 1u, app);
   uint64_t S = 0;
   for (int32_t i = 0; i < ORC_NOPS; i++) {
     uint32_t w = 0;
@@ -949,11 +954,11 @@ int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc
        (pr->migrate_strategy != 0 && (pr->migrate_n < 1 || pr->migrate_n > (uint32_t)P / pr->islands))))
     return -1;
   if (pr->cross_q16 > 65536u) return -1;
-  uint32_t *cnt = (uint32_t *)calloc((size_t)P * 22, sizeof(uint32_t));
+  uint32_t *cnt = (uint32_t *)calloc((size_t)P * ORC_NSTATS, sizeof(uint32_t));
   int32_t nthreads = orc_threads(threads);
   for (int64_t it = 0; it < generations; it++) {
     uint32_t g = (uint32_t)st->g;
-    memset(cnt, 0, sizeof(uint32_t) * (size_t)P * 22);
+    memset(cnt, 0, sizeof(uint32_t) * (size_t)P * ORC_NSTATS);
 #pragma omp parallel num_threads(nthreads)
     {
       int32_t *work = (int32_t *)malloc(sizeof(int32_t) * (size_t)len);
@@ -962,18 +967,19 @@ int32_t orc_run(const orc_instance *in, const orc_params *pr, uint64_t seed, orc
       int32_t *ks = (int32_t *)malloc(sizeof(int32_t) * (size_t)C);
 #pragma omp for schedule(dynamic, 1)
       for (int32_t p = 0; p < P; p++) {
-        uint32_t *c = cnt + (int64_t)p * 22;
+        uint32_t *c = cnt + (int64_t)p * ORC_NSTATS;
         evolve_one(in, pr, seed, st, p, st->w_op, st->w_k, st->T, g, work, delta, ops, ks, c,
-                   c + 8, c + 16, c + 19);
+                   c + ORC_NOPS, c + 2 * ORC_NOPS, c + 2 * ORC_NOPS + 3);
       }
       free(work); free(delta); free(ops); free(ks);
     }
     for (int32_t p = 0; p < P; p++) {
-      const uint32_t *c = cnt + (int64_t)p * 22;
-      for (int32_t i = 0; i < ORC_NOPS; i++) { st->u_op[i] += c[i]; st->v_op[i] += c[8 + i]; }
-      for (int32_t i = 0; i < 3; i++) { st->u_k[i] += c[16 + i]; st->v_k[i] += c[19 + i]; }
-      for (int32_t i = 0; i < ORC_NOPS; i++) { st->all_u_op[i] += c[i]; st->all_v_op[i] += c[8 + i]; }
-      for (int32_t i = 0; i < 3; i++) { st->all_u_k[i] += c[16 + i]; st->all_v_k[i] += c[19 + i]; }
+      const uint32_t *c = cnt + (int64_t)p * ORC_NSTATS;
+      const uint32_t *cv = c + ORC_NOPS, *ck = c + 2 * ORC_NOPS, *cvk = ck + 3;
+      for (int32_t i = 0; i < ORC_NOPS; i++) { st->u_op[i] += c[i]; st->v_op[i] += cv[i]; }
+      for (int32_t i = 0; i < 3; i++) { st->u_k[i] += ck[i]; st->v_k[i] += cvk[i]; }
+      for (int32_t i = 0; i < ORC_NOPS; i++) { st->all_u_op[i] += c[i]; st->all_v_op[i] += cv[i]; }
+      for (int32_t i = 0; i < 3; i++) { st->all_u_k[i] += ck[i]; st->all_v_k[i] += cvk[i]; }
     }
     st->T = orc_cool(st->T, pr->alpha);
     st->g++;

@@ -32,7 +32,11 @@ enum { ORC_TSP = 0, ORC_QAP = 1, ORC_KNAPSACK = 2, ORC_GAP = 3, ORC_CVRPTW = 4 }
 enum { ORC_SWAP = 0, ORC_TWO_OPT = 1, ORC_INSERT = 2, ORC_OR_OPT = 3,
        ORC_FLIP = 4, ORC_PERTURB = 5, ORC_THREE_OPT = 6,
        ORC_SEGMENT = 7, /* binary: seg_flip; integer: seg_reset [R28] */
-       ORC_NOPS = 8 };
+       /* row level of CVRPTW's separator encoding [R31, R32] */
+       ORC_ROW_SWAP = 8, ORC_ROW_MERGE = 9, ORC_ROW_SPLIT = 10,
+       ORC_NOPS = 11 };
+/* counts per member per generation: u_op, v_op (ORC_NOPS each), u_k, v_k */
+enum { ORC_NSTATS = 2 * ORC_NOPS + 6 };
 
 typedef struct {
   int32_t model;      /* ORC_TSP ... ORC_CVRPTW */
@@ -117,9 +121,9 @@ int32_t orc_migrate(const orc_params *pr, orc_state *st);
 /* Row operators [R31] of CVRPTW's separator encoding (rows = routes; Table
  * "operators", row level): kind 0 row_swap, 1 row_merge, 2 row_split, drawn
  * from the 16-bit fields a, b; edits s in place (an identity when the row
- * operator has nothing to do).  Not yet part of the search: primitives for
- * the row level's pins.  Returns -1 for other models, -2 unless len = n + V - 1
- * with exactly V - 1 separators, -3 when memory runs out. */
+ * operator has nothing to do).  The search applies them as operator slots
+ * ORC_ROW_SWAP .. ORC_ROW_SPLIT [R32].  Returns -1 for other models, -2 unless
+ * len = n + V - 1 with exactly V - 1 separators, -3 when memory runs out. */
 int32_t orc_row_move(const orc_instance *in, int32_t kind, uint32_t a, uint32_t b, int32_t *s,
                      int32_t len);
 /* order crossover [R29]: child keeps A[lo..hi] in place and fills positions

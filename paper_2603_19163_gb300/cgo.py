@@ -16,7 +16,9 @@ import numpy as np
 
 from . import build as _build
 
-NOPS = 8
+NOPS = 8        # slots of the first operator arrays of cgo_params / cgo_state
+NROW = 3        # the row level's slots (8 .. 10), in arrays of their own
+NOPS_ALL = NOPS + NROW
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_BUSY, ERR_STATE = range(8)
 STATUS_NAMES = ["OK", "INVALID", "NOMEM", "CUDA", "UNSUPPORTED", "TIMEOUT", "BUSY", "STATE"]
 TSP, QAP, KNAPSACK, GAP, CVRPTW = range(5)
@@ -53,7 +55,8 @@ class cgo_params(ctypes.Structure):
                 ("init_oversample", ctypes.c_uint32), ("init_heuristic", ctypes.c_uint32),
                 ("islands", ctypes.c_uint32), ("migrate_period", ctypes.c_uint32),
                 ("migrate_strategy", ctypes.c_uint32), ("migrate_n", ctypes.c_uint32),
-                ("cross_q16", ctypes.c_uint32)]
+                ("cross_q16", ctypes.c_uint32), ("row_w0_q16", ctypes.c_uint32 * NROW),
+                ("row_cap_q16", ctypes.c_uint32 * NROW)]
 
 
 class cgo_state(ctypes.Structure):
@@ -64,7 +67,8 @@ class cgo_state(ctypes.Structure):
                 ("elite_prev", ctypes.c_int64), ("u_op", ctypes.c_uint32 * NOPS),
                 ("v_op", ctypes.c_uint32 * NOPS), ("u_k", ctypes.c_uint32 * 3),
                 ("v_k", ctypes.c_uint32 * 3), ("cur", _i32p), ("best_sol", _i32p),
-                ("cost", _i64p), ("best_cost", _i64p)]
+                ("cost", _i64p), ("best_cost", _i64p), ("w_row_q16", ctypes.c_uint32 * NROW),
+                ("u_row", ctypes.c_uint32 * NROW), ("v_row", ctypes.c_uint32 * NROW)]
 
 
 class cgo_server_cfg(ctypes.Structure):
@@ -180,17 +184,26 @@ PARAM_MAP = [("P", "population"), ("C", "candidates"), ("G", "generations"),
              ("migrate_n", "migrate_n"), ("cross_q16", "cross_q16")]
 
 
+# per-slot lists of the dict (NOPS_ALL entries) and the two C arrays they fill
+SLOT_ARRAYS = {"op_w0_q16": "row_w0_q16", "op_cap_q16": "row_cap_q16"}
+
+
 def params_struct(d: dict) -> cgo_params:
     q = cgo_params()
     q.struct_size = ctypes.sizeof(cgo_params)
+    for i in range(NROW):
+        q.row_cap_q16[i] = 65536
     for k, f in PARAM_MAP:
         if k not in d:
             continue
         v = d[k]
         if isinstance(v, (list, tuple, np.ndarray)):
-            arr = getattr(q, f)
+            arr, row = getattr(q, f), getattr(q, SLOT_ARRAYS[f]) if f in SLOT_ARRAYS else None
             for i, x in enumerate(v):
-                arr[i] = int(x)
+                if i < len(arr):
+                    arr[i] = int(x)
+                else:
+                    row[i - len(arr)] = int(x)
         else:
             setattr(q, f, int(v))
     return q
@@ -201,6 +214,8 @@ def params_dict(q: cgo_params) -> dict:
     for k, f in PARAM_MAP:
         v = getattr(q, f)
         d[k] = list(v) if hasattr(v, "__len__") else int(v)
+        if f in SLOT_ARRAYS:
+            d[k] += list(getattr(q, SLOT_ARRAYS[f]))
     return d
 
 
@@ -304,27 +319,35 @@ class Problem:
         s.cost = arr["cost"].ctypes.data_as(_i64p)
         s.best_cost = arr["best_cost"].ctypes.data_as(_i64p)
         check(lib().cgo_state_get(self.h, ctypes.byref(s)), "cgo_state_get")
-        arr.update(P=P, len=n, g=s.generation, T=s.T_q32, w_op=list(s.w_op_q16),
+        arr.update(P=P, len=n, g=s.generation, T=s.T_q32,
+                   w_op=list(s.w_op_q16) + list(s.w_row_q16),
                    w_k=list(s.w_k_q16), stag=s.stag, elite_prev=s.elite_prev,
-                   u_op=list(s.u_op), v_op=list(s.v_op), u_k=list(s.u_k), v_k=list(s.v_k))
+                   u_op=list(s.u_op) + list(s.u_row), v_op=list(s.v_op) + list(s.v_row),
+                   u_k=list(s.u_k), v_k=list(s.v_k))
         return arr
 
     def op_counts(self) -> dict:
         """Operator and k-level counts over every generation of the solve so far."""
-        out = (ctypes.c_uint64 * 22)()
-        check(lib().cgo_op_counts(self.h, out, 22), "cgo_op_counts")
+        n = NOPS_ALL
+        out = (ctypes.c_uint64 * (2 * n + 6))()
+        check(lib().cgo_op_counts(self.h, out, 2 * n + 6), "cgo_op_counts")
         v = list(out)
-        return dict(u_op=v[0:8], v_op=v[8:16], u_k=v[16:19], v_k=v[19:22])
+        return dict(u_op=v[0:n], v_op=v[n:2 * n], u_k=v[2 * n:2 * n + 3],
+                    v_k=v[2 * n + 3:2 * n + 6])
 
     def set_state(self, params: dict, seed: int, st: dict):
         s = cgo_state()
         s.struct_size = ctypes.sizeof(cgo_state)
         s.population, s.length, s.generation, s.T_q32 = st["P"], st["len"], st["g"], st["T"]
+        rows = {"w_op_q16": "w_row_q16", "u_op": "u_row", "v_op": "v_row"}
         for f_py, f_c in (("w_op", "w_op_q16"), ("w_k", "w_k_q16"), ("u_op", "u_op"),
                           ("v_op", "v_op"), ("u_k", "u_k"), ("v_k", "v_k")):
             arr = getattr(s, f_c)
             for i, x in enumerate(st[f_py]):
-                arr[i] = int(x)
+                if i < len(arr):
+                    arr[i] = int(x)
+                else:
+                    getattr(s, rows[f_c])[i - len(arr)] = int(x)
         s.stag, s.elite_prev = st["stag"], st["elite_prev"]
         keep = {k: np.ascontiguousarray(st[k], dtype=np.int32 if k in ("cur", "best_sol")
                                         else np.int64) for k in ("cur", "best_sol", "cost",

@@ -241,7 +241,28 @@ uint32_t applicable_mask(const cgo_problem *p) {
   if (enc == CGO_ENC_INTEGER) return (1u << PERTURB) | seg;
   uint32_t m = (1u << SWAP) | (1u << TWO_OPT) | (1u << INSERT) | (1u << THREE_OPT);
   if (p->len >= 4) m |= 1u << OR_OPT;
+  // the row level: CVRPTW's routes, at least two of them
+  if (p->model == CVRPTW && p->len - p->n + 1 >= 2)
+    m |= (1u << ROW_SWAP) | (1u << ROW_MERGE) | (1u << ROW_SPLIT);
   return m;
+}
+
+cgo_status load_params(const cgo_params *in, cgo_params *out) {
+  if (!in) return fail(CGO_ERR_INVALID, "NULL params");
+  if (in->struct_size == sizeof(cgo_params)) {
+    *out = *in;
+    return CGO_OK;
+  }
+  if (in->struct_size == CGO_PARAMS_SIZE_V1) {
+    // the earlier fields only (its tail padding overlaps the appended ones)
+    memset(out, 0, sizeof *out);
+    memcpy(out, in, offsetof(cgo_params, row_w0_q16));
+    out->struct_size = sizeof(cgo_params);
+    out->op_mask &= (1u << CGO_NOPS) - 1u;
+    for (int i = 0; i < CGO_NROW; ++i) out->row_cap_q16[i] = 65536u;
+    return CGO_OK;
+  }
+  return fail(CGO_ERR_INVALID, "params: struct_size must be sizeof(cgo_params) or CGO_PARAMS_SIZE_V1");
 }
 
 cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *enabled) {
@@ -257,9 +278,9 @@ cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *
   uint64_t ws = 0;
   for (int i = 0; i < kNops; ++i) {
     if (!((en >> i) & 1u)) continue;
-    if (q->op_w0_q16[i] > 65536u) return fail(CGO_ERR_INVALID, "operator weight > 1.0");
-    if (q->op_cap_q16[i] < q->w_floor_q16) return fail(CGO_ERR_INVALID, "operator cap below floor");
-    ws += q->op_w0_q16[i];
+    if (op_w0(*q, i) > 65536u) return fail(CGO_ERR_INVALID, "operator weight > 1.0");
+    if (op_capq(*q, i) < q->w_floor_q16) return fail(CGO_ERR_INVALID, "operator cap below floor");
+    ws += op_w0(*q, i);
   }
   if (ws == 0) return fail(CGO_ERR_INVALID, "enabled operator weights sum to zero");
   uint64_t ks = 0;
@@ -333,7 +354,7 @@ KInst base_kinst(const cgo_problem *p) {
   h.w_floor = q.w_floor_q16;
   h.w_cap = q.w_cap_q16;
   h.stag_limit = q.stag_limit;
-  for (int i = 0; i < kNops; ++i) h.op_cap[i] = q.op_cap_q16[i];
+  for (int i = 0; i < kNops; ++i) h.op_cap[i] = op_capq(q, i);
   h.enabled = p->enabled;
   h.seed = p->seed;
   h.cur = p->d_cur;
@@ -522,7 +543,7 @@ DevAos initial_aos(const cgo_params &q, uint32_t en) {
   DevAos a;
   memset(&a, 0, sizeof a);
   a.T = q.T0_q32;
-  for (int k = 0; k < kNops; ++k) a.w_op[k] = ((en >> k) & 1u) ? q.op_w0_q16[k] : 0u;
+  for (int k = 0; k < kNops; ++k) a.w_op[k] = ((en >> k) & 1u) ? op_w0(q, k) : 0u;
   for (int k = 0; k < 3; ++k) a.w_k[k] = q.k_w0_q16[k];
   return a;
 }
@@ -746,16 +767,21 @@ cgo_status cgo_solution_length(const cgo_problem *p, int32_t *out) {
   return CGO_OK;
 }
 
-cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
-  if (!p || !q) return fail(CGO_ERR_INVALID, "NULL argument");
+cgo_status cgo_params_default(const cgo_problem *p, cgo_params *out) {
+  if (!p || !out) return fail(CGO_ERR_INVALID, "NULL argument");
+  const bool v1 = out->struct_size == CGO_PARAMS_SIZE_V1;
+  cgo_params full;
+  cgo_params *q = &full;
   memset(q, 0, sizeof *q);
   q->struct_size = sizeof(cgo_params);
   q->population = 32;
   q->candidates = 128;
   q->generations = 2000;
   const uint32_t app = applicable_mask(p);
-  // 3-opt and the segment operators of the binary / integer sets are off by default
-  const uint32_t en = app & ~((1u << THREE_OPT) | (1u << SEGMENT));
+  // 3-opt, the segment operators of the binary / integer sets and the row
+  // level are off by default
+  const uint32_t en =
+      app & ~((1u << THREE_OPT) | (1u << SEGMENT) | (1u << ROW_SWAP) | (1u << ROW_MERGE) | (1u << ROW_SPLIT));
   q->op_mask = en;
   // Table "weight_preset": O(1) operators 1.0; or-opt and 3-opt by scale of
   // the length, seg_flip / seg_reset with or-opt's segment-level preset; the
@@ -770,9 +796,17 @@ cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
     if (i == SEGMENT) w[i] = p->len <= 100 ? 52429u : (p->len <= 250 ? 45875u : 19661u);
     if ((en >> i) & 1u) S += w[i];
   }
+  // (the row level takes the O(1) prior 1.0: the table scales only the
+  // operators of higher complexity)
   for (int i = 0; i < kNops; ++i) {
-    q->op_w0_q16[i] = (uint32_t)(((uint64_t)w[i] << 16) / S);
-    q->op_cap_q16[i] = 65536u;
+    const uint32_t wi = (uint32_t)(((uint64_t)w[i] << 16) / S);
+    if (i < CGO_NOPS) {
+      q->op_w0_q16[i] = wi;
+      q->op_cap_q16[i] = 65536u;
+    } else {
+      q->row_w0_q16[i - CGO_NOPS] = wi;
+      q->row_cap_q16[i - CGO_NOPS] = 65536u;
+    }
   }
   q->k_w0_q16[0] = 52429u;
   q->k_w0_q16[1] = 9830u;
@@ -792,6 +826,12 @@ cgo_status cgo_params_default(const cgo_problem *p, cgo_params *q) {
   q->migrate_strategy = 0;
   q->migrate_n = 1;
   q->cross_q16 = 0;
+  if (v1) {
+    memcpy(out, q, offsetof(cgo_params, row_w0_q16));
+    out->struct_size = CGO_PARAMS_SIZE_V1;
+  } else {
+    *out = *q;
+  }
   return CGO_OK;
 }
 
@@ -829,13 +869,17 @@ cgo_status cgo_get_launch(const cgo_problem *p, cgo_launch *l) {
   return CGO_OK;
 }
 
-cgo_status cgo_solve(cgo_problem *p, const cgo_params *q, uint64_t seed, void *stream) {
+cgo_status cgo_solve(cgo_problem *p, const cgo_params *qin, uint64_t seed, void *stream) {
   if (!p) return fail(CGO_ERR_INVALID, "NULL problem");
   Guard gd(p);
   if (!gd.ok) return fail(CGO_ERR_BUSY, "problem handle in use");
   cudaSetDevice(p->device);
+  cgo_params qq;
+  cgo_status s = load_params(qin, &qq);
+  if (s != CGO_OK) return s;
+  const cgo_params *q = &qq;
   uint32_t en = 0;
-  cgo_status s = validate_params(p, q, &en);
+  s = validate_params(p, q, &en);
   if (s != CGO_OK) return s;
   if ((s = ensure_state(p, q->population)) != CGO_OK) return s;
   if ((s = ensure_pool(p, *q)) != CGO_OK) return s;
@@ -907,7 +951,9 @@ cgo_status cgo_op_counts(const cgo_problem *p, uint64_t *out, int32_t cap) {
 }
 
 cgo_status cgo_state_get(const cgo_problem *p, cgo_state *o) {
-  if (!p || !o || o->struct_size != sizeof(cgo_state)) return fail(CGO_ERR_INVALID, "bad state struct");
+  if (!p || !o || (o->struct_size != sizeof(cgo_state) && o->struct_size != CGO_STATE_SIZE_V1))
+    return fail(CGO_ERR_INVALID, "bad state struct");
+  const bool has_rows = o->struct_size == sizeof(cgo_state);
   Guard gd(p);
   if (!gd.ok) return fail(CGO_ERR_BUSY, "problem handle in use");
   if (!p->has_state) return fail(CGO_ERR_STATE, "no search state");
@@ -920,14 +966,20 @@ cgo_status cgo_state_get(const cgo_problem *p, cgo_state *o) {
   o->generation = a.g;
   o->T_q32 = a.T;
   for (int i = 0; i < kNops; ++i) {
-    o->w_op_q16[i] = a.w_op[i];
-    o->u_op[i] = a.pend[i];
-    o->v_op[i] = a.pend[8 + i];
+    if (i < CGO_NOPS) {
+      o->w_op_q16[i] = a.w_op[i];
+      o->u_op[i] = a.pend[i];
+      o->v_op[i] = a.pend[kStatV + i];
+    } else if (has_rows) {
+      o->w_row_q16[i - CGO_NOPS] = a.w_op[i];
+      o->u_row[i - CGO_NOPS] = a.pend[i];
+      o->v_row[i - CGO_NOPS] = a.pend[kStatV + i];
+    }
   }
   for (int i = 0; i < 3; ++i) {
     o->w_k_q16[i] = a.w_k[i];
-    o->u_k[i] = a.pend[16 + i];
-    o->v_k[i] = a.pend[19 + i];
+    o->u_k[i] = a.pend[kStatUK + i];
+    o->v_k[i] = a.pend[kStatVK + i];
   }
   o->stag = a.stag;
   o->elite_prev = a.elite_prev;
@@ -939,14 +991,22 @@ cgo_status cgo_state_get(const cgo_problem *p, cgo_state *o) {
   return CGO_OK;
 }
 
-cgo_status cgo_state_set(cgo_problem *p, const cgo_params *q, uint64_t seed, const cgo_state *in) {
-  if (!p || !in || in->struct_size != sizeof(cgo_state)) return fail(CGO_ERR_INVALID, "bad state struct");
+cgo_status cgo_state_set(cgo_problem *p, const cgo_params *qin, uint64_t seed, const cgo_state *in) {
+  if (!p || !in || (in->struct_size != sizeof(cgo_state) && in->struct_size != CGO_STATE_SIZE_V1))
+    return fail(CGO_ERR_INVALID, "bad state struct");
   Guard gd(p);
   if (!gd.ok) return fail(CGO_ERR_BUSY, "problem handle in use");
   cudaSetDevice(p->device);
-  uint32_t en = 0;
-  cgo_status s = validate_params(p, q, &en);
+  cgo_params qq;
+  cgo_status s = load_params(qin, &qq);
   if (s != CGO_OK) return s;
+  const cgo_params *q = &qq;
+  uint32_t en = 0;
+  s = validate_params(p, q, &en);
+  if (s != CGO_OK) return s;
+  const bool has_rows = in->struct_size == sizeof(cgo_state);
+  if (!has_rows && (en >> CGO_NOPS))
+    return fail(CGO_ERR_INVALID, "a state without the row level cannot resume a search with row operators");
   if (in->population != q->population || in->length != p->len)
     return fail(CGO_ERR_INVALID, "state shape does not match params/problem");
   if (!in->cur || !in->best_sol || !in->cost || !in->best_cost)
@@ -969,14 +1029,15 @@ cgo_status cgo_state_set(cgo_problem *p, const cgo_params *q, uint64_t seed, con
   a.T = in->T_q32;
   a.g = in->generation;
   for (int i = 0; i < kNops; ++i) {
-    a.w_op[i] = in->w_op_q16[i];
-    a.pend[i] = in->u_op[i];
-    a.pend[8 + i] = in->v_op[i];
+    const bool row = i >= CGO_NOPS;
+    a.w_op[i] = row ? (has_rows ? in->w_row_q16[i - CGO_NOPS] : 0u) : in->w_op_q16[i];
+    a.pend[i] = row ? (has_rows ? in->u_row[i - CGO_NOPS] : 0u) : in->u_op[i];
+    a.pend[kStatV + i] = row ? (has_rows ? in->v_row[i - CGO_NOPS] : 0u) : in->v_op[i];
   }
   for (int i = 0; i < 3; ++i) {
     a.w_k[i] = in->w_k_q16[i];
-    a.pend[16 + i] = in->u_k[i];
-    a.pend[19 + i] = in->v_k[i];
+    a.pend[kStatUK + i] = in->u_k[i];
+    a.pend[kStatVK + i] = in->v_k[i];
   }
   a.stag = in->stag;
   a.elite_prev = in->elite_prev;
@@ -995,9 +1056,9 @@ cgo_status cgo_state_set(cgo_problem *p, const cgo_params *q, uint64_t seed, con
   return CGO_OK;
 }
 
-cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, const uint64_t *seeds,
+cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_in, const uint64_t *seeds,
                            int32_t count, void *stream) {
-  if (count < 0 || (count > 0 && (!probs || !per || !seeds))) return fail(CGO_ERR_INVALID, "bad batch arguments");
+  if (count < 0 || (count > 0 && (!probs || !per_in || !seeds))) return fail(CGO_ERR_INVALID, "bad batch arguments");
   if (count == 0) return CGO_OK;
   cudaStream_t st = (cudaStream_t)stream;
   // every handle distinct and free
@@ -1021,6 +1082,15 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per, con
   };
   std::vector<Bucket> buckets;
   int64_t Gmax = 0;
+  // per_prob is an array of structs of one size: the current or the earlier one
+  const size_t stride = per_in[0].struct_size == CGO_PARAMS_SIZE_V1 ? CGO_PARAMS_SIZE_V1
+                                                                     : sizeof(cgo_params);
+  std::vector<cgo_params> per((size_t)count);
+  for (int32_t i = 0; i < count; ++i) {
+    cgo_status s = load_params((const cgo_params *)((const char *)per_in + (size_t)i * stride),
+                               &per[(size_t)i]);
+    if (s != CGO_OK) return s;
+  }
   for (int32_t i = 0; i < count; ++i) {
     cgo_problem *p = probs[i];
     if (p->device != dev) return fail(CGO_ERR_INVALID, "problem %d lives on another device", i);
@@ -1195,8 +1265,13 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
     return fail(CGO_ERR_INVALID, "the allocation-free solve needs the distance matrix on the device");
   if (!out_best_sol || !out_best_cost) return fail(CGO_ERR_INVALID, "output buffers are required");
   if (d->n < 2 || d->n > 65535) return fail(CGO_ERR_INVALID, "n must be in [2, 65535]");
-  if (q && q->struct_size == sizeof(cgo_params) && q->generations >= 0xFFFFFFFFll)
-    return fail(CGO_ERR_INVALID, "too many generations");
+  cgo_params qq;
+  {
+    const cgo_status ls = load_params(q, &qq);
+    if (ls != CGO_OK) return ls;
+  }
+  q = &qq;
+  if (q->generations >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "too many generations");
   cgo_problem p;  // a description on the stack: no device state of its own
   CUDA_TRY(cudaGetDevice(&p.device), "current device");
   p.model = TSP;
@@ -1264,7 +1339,7 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
   DevAos a0;
   memset(&a0, 0, sizeof a0);
   a0.T = q->T0_q32;
-  for (int i = 0; i < kNops; ++i) a0.w_op[i] = ((en >> i) & 1u) ? q->op_w0_q16[i] : 0u;
+  for (int i = 0; i < kNops; ++i) a0.w_op[i] = ((en >> i) & 1u) ? op_w0(*q, i) : 0u;
   for (int i = 0; i < 3; ++i) a0.w_k[i] = q->k_w0_q16[i];
   h.aos_out = aos;
   CUDA_TRY(launch_init_aos(h, a0, st), "init launch");

@@ -154,9 +154,9 @@ __device__ __forceinline__ uint64_t udiv_exact(uint64_t num, uint64_t den) {
 
 // Eq. "ema" for both levels at once, one lane per weight: lanes 0..NO-1
 // hold the operator weights, lanes 24..26 the K weights; u/v are read from
-// the lanes that hold the window totals (u_op at lane o, v_op at 8+o, u_k at
-// 16+i, v_k at 19+i, o the global operator E::glob(l) of local operator l).
-// Every lane ends with the new weights.
+// the lanes that hold the window totals (u_op at lane o, v_op at kStatV + o,
+// u_k at kStatUK + i, v_k at kStatVK + i, o the global operator E::glob(l)
+// of local operator l).  Every lane ends with the new weights.
 template <class E>
 __device__ __forceinline__ void aos_update_lanes(uint32_t (&wop)[E::NO], uint32_t (&wk)[3],
                                                  uint32_t total, uint32_t en_local,
@@ -169,8 +169,9 @@ __device__ __forceinline__ void aos_update_lanes(uint32_t (&wop)[E::NO], uint32_
   int go = 0;
 #pragma unroll
   for (int l = 0; l < NO; ++l) go = li == l ? E::glob(l) : go;
-  const uint32_t u = __shfl_sync(kFull, total, is_op ? go : (is_k ? 16 + li : 0));
-  const uint32_t v = __shfl_sync(kFull, total, is_op ? 8 + go : (is_k ? 19 + li : 0));
+  static_assert(NO <= 24, "operator lanes must stay below the K lanes");
+  const uint32_t u = __shfl_sync(kFull, total, is_op ? go : (is_k ? kStatUK + li : 0));
+  const uint32_t v = __shfl_sync(kFull, total, is_op ? kStatV + go : (is_k ? kStatVK + li : 0));
   uint32_t w = 0, cap = 65536u;
   bool en = false;
 #pragma unroll

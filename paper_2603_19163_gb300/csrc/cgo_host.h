@@ -76,6 +76,18 @@ struct Guard {
 };
 
 cudaStream_t host_stream();
+// A cgo_params of the current or the earlier size (CGO_PARAMS_SIZE_V1, without
+// the row level) as a full current struct; the earlier size leaves the row
+// operators off.
+cgo_status load_params(const cgo_params *in, cgo_params *out);
+// weight / cap of operator slot i (0 .. kNops - 1)
+inline uint32_t op_w0(const cgo_params &q, int i) {
+  return i < CGO_NOPS ? q.op_w0_q16[i] : q.row_w0_q16[i - CGO_NOPS];
+}
+inline uint32_t op_capq(const cgo_params &q, int i) {
+  return i < CGO_NOPS ? q.op_cap_q16[i] : q.row_cap_q16[i - CGO_NOPS];
+}
+// q must be a current-size struct (load_params)
 cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *enabled);
 cgo_status ensure_state(cgo_problem *p, int P);
 int64_t pool_size(const cgo_problem *p, const cgo_params &q);

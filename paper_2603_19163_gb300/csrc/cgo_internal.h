@@ -6,8 +6,12 @@
 
 namespace cgo {
 
-constexpr int kNops = 8;
-constexpr int kStats = 22;      // u_op[8] v_op[8] u_k[3] v_k[3]
+constexpr int kNops = 11;      // operator slots (cgo_op), the row level in 8 .. 10
+// window counts, one per lane of a warp: u_op[kNops] at lanes 0.., v_op at
+// kStatV.., u_k[3] at kStatUK.., v_k[3] at kStatVK..
+constexpr int kStatV = kNops, kStatUK = 2 * kNops, kStatVK = 2 * kNops + 3;
+constexpr int kStats = 2 * kNops + 6;
+static_assert(kStats <= 32, "window counts must fit the lanes of a warp");
 constexpr int kMaxWarps = 8;    // warps per CTA (kernel launch bound 256 threads)
 // warps per CTA of a single solve with 3 or 4 generations in flight (one
 // member of 4 warps per generation; launch bound 32 x that)
@@ -16,7 +20,8 @@ constexpr int kMaxAgents = 64;  // GAP agents
 
 enum Model { TSP = 0, QAP = 1, KNAPSACK = 2, GAP = 3, CVRPTW = 4 };
 enum Op { SWAP = 0, TWO_OPT = 1, INSERT = 2, OR_OPT = 3, FLIP = 4, PERTURB = 5, THREE_OPT = 6,
-          SEGMENT = 7 /* seg_flip (binary), seg_reset (integer) */ };
+          SEGMENT = 7 /* seg_flip (binary), seg_reset (integer) */,
+          ROW_SWAP = 8, ROW_MERGE = 9, ROW_SPLIT = 10 /* CVRPTW's routes */ };
 enum Staging { STAGE_AUTO = 0, STAGE_SMEM = 1, STAGE_GLOBAL = 2 };
 
 // Per-instance search scalars (device memory, double-buffered in/out per launch).

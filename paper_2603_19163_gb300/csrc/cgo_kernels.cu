@@ -63,10 +63,13 @@ __host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64
 // each) and each warp's window counts (32 x 4 B)
 __host__ __device__ inline int64_t group_bytes(int nw) { return 2 * nw * 16 + 16 + 2 * nw * 64 + nw * 128; }
 
-// CVRPTW route cache of one member: route-cost prefix sums (len + 2 int64)
-// and the next / previous separator of every position (len + 1, len int32)
+// CVRPTW route cache of one member: route-cost prefix sums (len + 2 int64),
+// the next / previous separator of every position (len + 1, len int32) and
+// the separators' positions in order with the lowest-index empty route
+// (len + 1 int32)
 __host__ __device__ inline int64_t cv_aux_bytes(int len) {
-  return align16(8 * (int64_t)(len + 2) + 4 * (int64_t)(len + 1) + 4 * (int64_t)len);
+  return align16(8 * (int64_t)(len + 2) + 4 * (int64_t)(len + 1) + 4 * (int64_t)len +
+                 4 * (int64_t)(len + 1));
 }
 
 // Shared memory of one CTA: [instance data][members' solutions][one scratch
@@ -147,17 +150,17 @@ __device__ __forceinline__ void stats_zero(Stats<NO> &s) {
 }
 
 // What one candidate adds to the window counts, packed in a word: the local
-// operator of each of its three steps (bits 3t..3t+2, 7 = step not taken),
-// its step count k (bits 9-10) and whether it improves (bit 11).  A record
+// operator of each of its three steps (bits 4t..4t+3, 15 = step not taken),
+// its step count k (bits 12-13) and whether it improves (bit 14).  A record
 // is added to the counts only once its generation is decided on the solution
 // it was evaluated against.
 __device__ __forceinline__ uint32_t stats_record(int op0, int op1, int op2, int k, uint32_t imp) {
-  const uint32_t a = op0 < 0 ? 7u : (uint32_t)op0, b = op1 < 0 ? 7u : (uint32_t)op1,
-                 c = op2 < 0 ? 7u : (uint32_t)op2;
-  return a | (b << 3) | (c << 6) | ((uint32_t)k << 9) | (imp << 11);
+  const uint32_t a = op0 < 0 ? 15u : (uint32_t)op0, b = op1 < 0 ? 15u : (uint32_t)op1,
+                 c = op2 < 0 ? 15u : (uint32_t)op2;
+  return a | (b << 4) | (c << 8) | ((uint32_t)k << 12) | (imp << 14);
 }
 
-constexpr uint32_t kNoRecord = 0x1FFu;  // no step taken, k = 0
+constexpr uint32_t kNoRecord = 0xFFFu;  // no step taken, k = 0
 
 // Window counts of one member kept in bytes while it evolves (one byte per
 // operator or k level, uses and improvements apart), added to the full
@@ -166,44 +169,51 @@ constexpr uint32_t kNoRecord = 0x1FFu;  // no step taken, k = 0
 struct PackedStats {
   uint32_t u, v;    // local operators 0..3, one byte each
   uint32_t uk, vk;  // k levels 1..3 in bytes 0..2, local operator 4 in byte 3
+  uint32_t u2, v2;  // local operators 5..7 (the row level of CVRPTW)
 };
 
+template <int NO>
 __device__ __forceinline__ void packed_add(PackedStats &s, uint32_t rec) {
-  const uint32_t imp = (rec >> 11) & 1u, k = (rec >> 9) & 3u;
-  uint32_t inc = 0, inck = k ? 1u << (8u * (k - 1u)) : 0u;
+  const uint32_t imp = (rec >> 14) & 1u, k = (rec >> 12) & 3u;
+  uint32_t inc = 0, inck = k ? 1u << (8u * (k - 1u)) : 0u, inc2 = 0;
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
-    const uint32_t op = (rec >> (3 * t)) & 7u;
+    const uint32_t op = (rec >> (4 * t)) & 15u;
     inc += op < 4u ? 1u << (8u * op) : 0u;
     inck += op == 4u ? 1u << 24 : 0u;
+    if constexpr (NO > 5) inc2 += (op >= 5u && op < 8u) ? 1u << (8u * (op - 5u)) : 0u;
   }
   s.u += inc;
   s.v += imp ? inc : 0u;
   s.uk += inck;
   s.vk += imp ? inck : 0u;
+  if constexpr (NO > 5) {
+    s.u2 += inc2;
+    s.v2 += imp ? inc2 : 0u;
+  }
 }
 
 template <int NO>
 __device__ __forceinline__ void packed_flush(Stats<NO> &st, PackedStats &s) {
 #pragma unroll
   for (int i = 0; i < NO; ++i) {
-    st.u[i] += (i < 4 ? s.u >> (8 * i) : s.uk >> 24) & 0xFFu;
-    st.v[i] += (i < 4 ? s.v >> (8 * i) : s.vk >> 24) & 0xFFu;
+    st.u[i] += (i < 4 ? s.u >> (8 * i) : (i == 4 ? s.uk >> 24 : s.u2 >> (8 * (i - 5)))) & 0xFFu;
+    st.v[i] += (i < 4 ? s.v >> (8 * i) : (i == 4 ? s.vk >> 24 : s.v2 >> (8 * (i - 5)))) & 0xFFu;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     st.uk[i] += (s.uk >> (8 * i)) & 0xFFu;
     st.vk[i] += (s.vk >> (8 * i)) & 0xFFu;
   }
-  s.u = s.v = s.uk = s.vk = 0u;
+  s.u = s.v = s.uk = s.vk = s.u2 = s.v2 = 0u;
 }
 
 template <int NO>
 __device__ __forceinline__ void stats_add(Stats<NO> &s, uint32_t rec) {
-  const uint32_t imp = (rec >> 11) & 1u, k = (rec >> 9) & 3u;
+  const uint32_t imp = (rec >> 14) & 1u, k = (rec >> 12) & 3u;
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
-    const uint32_t op = (rec >> (3 * t)) & 7u;
+    const uint32_t op = (rec >> (4 * t)) & 15u;
 #pragma unroll
     for (int i = 0; i < NO; ++i) {
       const uint32_t hit = (op == (uint32_t)i);
@@ -220,7 +230,8 @@ __device__ __forceinline__ void stats_add(Stats<NO> &s, uint32_t rec) {
 }
 
 // per-encoding operator set: local op l is global op glob(l) (permutations:
-// swap, 2-opt, insertion, or-opt, 3-opt; binary: flip, seg_flip; integer:
+// swap, 2-opt, insertion, or-opt, 3-opt; CVRPTW's separator sequence adds the
+// row level: row_swap, row_merge, row_split; binary: flip, seg_flip; integer:
 // reset, seg_reset), in the order of the global slots
 struct PermOps {
   static constexpr int NO = 5;
@@ -228,6 +239,13 @@ struct PermOps {
 };
 template <int MODEL>
 struct Enc : PermOps {};
+template <>
+struct Enc<CVRPTW> {
+  static constexpr int NO = 8;
+  __host__ __device__ static constexpr int glob(int l) {
+    return l < 4 ? l : (l == 4 ? (int)THREE_OPT : (int)ROW_SWAP + (l - 5));
+  }
+};
 template <>
 struct Enc<KNAPSACK> {
   static constexpr int NO = 2;
@@ -421,10 +439,12 @@ __device__ __forceinline__ long long cvrptw_routes(const View &X, Look V, int L,
 // Route cache of one member's (actual) sequence: cum[q] = cost of the routes
 // ended by a terminator (separator, or the virtual one at len) before q;
 // nxt[q] = first separator at or after q (len if none, nxt[len] = len);
-// prv[q] = last separator at or before q (-1 if none).
+// prv[q] = last separator at or before q (-1 if none); sep[r] = position of
+// the r-th separator (r < V - 1) and sep[len] = the lowest-index empty route
+// (-1 if none).
 struct CvAux {
   long long *cum;
-  int *nxt, *prv;
+  int *nxt, *prv, *sep;
 };
 
 __device__ __forceinline__ CvAux cv_aux_at(unsigned char *p, int len) {
@@ -432,6 +452,7 @@ __device__ __forceinline__ CvAux cv_aux_at(unsigned char *p, int len) {
   a.cum = (long long *)p;
   a.nxt = (int *)(p + 8 * (int64_t)(len + 2));
   a.prv = a.nxt + (len + 1);
+  a.sep = a.prv + len;
   return a;
 }
 
@@ -469,6 +490,26 @@ __device__ void cv_build(const View &X, const El *sol, const CvAux &a, const G_t
     }
     if (lane == 0) a.nxt[m] = m;
     for (int q = lane; q <= m + 1; q += 32) a.cum[q] = 0;
+    // separators in order, and the lowest-index empty route: route r runs
+    // from just after separator r - 1 (from 0 for r = 0) to separator r (to
+    // len for the last one)
+    int rank = 0, zmin = INT_MAX;
+    for (int base = 0; base < m; base += 32) {
+      const int q = base + lane;
+      const bool sp = q < m && (int)sol[q] >= n;
+      const uint32_t bal = __ballot_sync(kFull, sp);
+      const int r = rank + __popc(bal & ((1u << lane) - 1u));
+      if (sp) {
+        a.sep[r] = q;
+        // route r is empty when it starts here (q = 0, or a separator before)
+        if (q == 0 || (int)sol[q - 1] >= n) zmin = min(zmin, r);
+      }
+      rank += __popc(bal);
+    }
+    // the last route is empty when the sequence ends with a separator
+    if (lane == 0 && m > 0 && (int)sol[m - 1] >= n) zmin = min(zmin, rank);
+    zmin = __reduce_min_sync(kFull, zmin);
+    if (lane == 0) a.sep[m] = zmin == INT_MAX ? -1 : zmin;
     __syncwarp();
     // each non-empty route's cost, stored one past its terminator
     for (int q = lane; q < m; q += 32) {
@@ -624,6 +665,102 @@ __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl
   return total;
 }
 
+// ------------------------------------------------- row level [R31, R32]
+// The rows of CVRPTW's separator sequence are its V routes: route r spans
+// [b_r, e_r), b_0 = 0, e_r = the r-th separator's position (e_(V-1) = len),
+// b_r = e_(r-1) + 1.  Each row operator is a cut-and-reorder move once the
+// bounds of the routes it names are known: row_swap exchanges two routes'
+// contents (P0 B M A P4 with A, B the routes), row_merge and row_split move
+// one separator (an insertion).
+struct RouteBounds {
+  int b[2], e[2];  // the routes the operator names
+  int z, zb, ze;   // the lowest-index empty route (z = -1 if none) and its bounds
+};
+
+// element i removed and re-inserted so that it lands at index j
+__device__ __forceinline__ PMove insert_move(int i, int j) {
+  return i < j ? PMove{i, i + 1, i + 1, j + 1, 0} : PMove{j, i, i, i + 1, 0};
+}
+
+// the routes a row operator (local 5 swap, 6 merge, 7 split) names
+__device__ __forceinline__ void row_routes(int op, uint32_t r1, int V, int &ra, int &rb) {
+  const uint32_t a = r1 >> 16, b = r1 & 0xFFFFu;
+  if (op == 5) {
+    const int x = posm(a, (uint32_t)V);
+    int y = posm(b, (uint32_t)(V - 1));
+    y += (y >= x);
+    ra = min(x, y);
+    rb = max(x, y);
+  } else if (op == 6) {
+    ra = posm(a, (uint32_t)(V - 1));
+    rb = ra + 1;
+  } else {
+    ra = posm(a, (uint32_t)V);
+    rb = -1;
+  }
+}
+
+__device__ __forceinline__ PMove row_move(int op, uint32_t r1, int V, const RouteBounds &S) {
+  if (op == 5) return PMove{S.b[0], S.e[0], S.b[1], S.e[1], 0};
+  if (op == 6) return insert_move(S.e[0], S.e[1] - 1);
+  const int c = S.e[0] - S.b[0];
+  if (c >= 2 && S.z >= 0) {
+    const int k = 1 + posm(r1 & 0xFFFFu, (uint32_t)(c - 1));
+    // the separator that closes the empty route (opens it, for the last one)
+    const int from = S.z < V - 1 ? S.ze : S.zb - 1;
+    const int gap = S.b[0] + k;  // it goes before the element now at gap
+    return insert_move(from, from < gap ? gap - 1 : gap);
+  }
+  return PMove{0, 0, 0, 0, 0};  // nothing to split: identity
+}
+
+// bounds on the actual sequence, from the route cache
+__device__ __forceinline__ RouteBounds row_bounds_cached(const CvAux &a, int len, int V, int ra,
+                                                         int rb) {
+  auto bb = [&](int r) { return r == 0 ? 0 : a.sep[r - 1] + 1; };
+  auto ee = [&](int r) { return r == V - 1 ? len : a.sep[r]; };
+  RouteBounds S;
+  S.b[0] = bb(ra);
+  S.e[0] = ee(ra);
+  S.b[1] = rb >= 0 ? bb(rb) : 0;
+  S.e[1] = rb >= 0 ? ee(rb) : 0;
+  S.z = a.sep[len];
+  S.zb = S.z >= 0 ? bb(S.z) : 0;
+  S.ze = S.z >= 0 ? ee(S.z) : 0;
+  return S;
+}
+
+// bounds on the sequence as earlier steps left it (position q holds Vq(q)):
+// one pass over the positions
+template <class Look>
+__device__ RouteBounds row_bounds_scan(Look Vq, int n, int len, int ra, int rb) {
+  RouteBounds S;
+  S.b[0] = S.e[0] = S.b[1] = S.e[1] = 0;
+  S.z = -1;
+  S.zb = S.ze = 0;
+  int r = 0, start = 0;
+  for (int q = 0; q <= len; ++q) {
+    if (q < len && Vq(q) < n) continue;
+    // route r spans [start, q)
+    if (r == ra) {
+      S.b[0] = start;
+      S.e[0] = q;
+    }
+    if (r == rb) {
+      S.b[1] = start;
+      S.e[1] = q;
+    }
+    if (S.z < 0 && q == start) {
+      S.z = r;
+      S.zb = start;
+      S.ze = q;
+    }
+    ++r;
+    start = q + 1;
+  }
+  return S;
+}
+
 // Delta of a CVRPTW candidate of k >= 2 steps on the actual sequence: the
 // routes over the hull of the moves' ranges, walked in the final sequence
 // (position q of it holds sol[inv_1(.. inv_k(q))]), minus their cached cost.
@@ -652,8 +789,8 @@ __device__ long long cvrptw_composite(const View &X, const PermEl *sol, const Ca
 // sequence against their cached old cost.  With `defer` set, a candidate of
 // k >= 2 steps is not evaluated and false is returned.
 __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *sol,
-                                                 const Weights<5> &W, uint32_t c, uint32_t p,
-                                                 uint32_t g, bool defer, long long &d,
+                                                 const Weights<Enc<CVRPTW>::NO> &W, uint32_t c,
+                                                 uint32_t p, uint32_t g, bool defer, long long &d,
                                                  uint32_t &rec, CandMoves &cm, const CvAux &aux) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
   const int k = 1 + wpick(W.ck, W.Wk, R0.w);
@@ -661,9 +798,16 @@ __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *so
   int ops[3] = {-1, -1, -1};
   cm.k = k;
   cm.m[1] = cm.m[2] = PMove{0, 0, 0, 0, 0};
+  const int V = X.len - X.n + 1;
   ops[0] = wpick(W.cop, W.Wop, R0.x);
-  cm.m[0] = X.t3 ? perm_decode<true>(ops[0], R0.y, R0.z, X.len)
-                 : perm_decode<false>(ops[0], R0.y, R0.z, X.len);
+  if (ops[0] >= 5) {
+    int ra, rb;
+    row_routes(ops[0], R0.y, V, ra, rb);
+    cm.m[0] = row_move(ops[0], R0.y, V, row_bounds_cached(aux, X.len, V, ra, rb));
+  } else {
+    cm.m[0] = X.t3 ? perm_decode<true>(ops[0], R0.y, R0.z, X.len)
+                   : perm_decode<false>(ops[0], R0.y, R0.z, X.len);
+  }
   if (k == 1) {
     d = cvrptw_step0(X, sol, cm.m[0], aux);
   } else {
@@ -672,8 +816,19 @@ __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *so
       if (t < k) {
         const uint4 R = philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
         ops[t] = wpick(W.cop, W.Wop, R.x);
-        cm.m[t] = X.t3 ? perm_decode<true>(ops[t], R.y, R.z, X.len)
-                       : perm_decode<false>(ops[t], R.y, R.z, X.len);
+        if (ops[t] >= 5) {
+          // the routes of the sequence as the earlier steps left it
+          int ra, rb;
+          row_routes(ops[t], R.y, V, ra, rb);
+          auto Vq = [&](int q) {
+            if (t == 2) q = perm_inv(cm.m[1], q);
+            return (int)sol[perm_inv(cm.m[0], q)];
+          };
+          cm.m[t] = row_move(ops[t], R.y, V, row_bounds_scan(Vq, X.n, X.len, ra, rb));
+        } else {
+          cm.m[t] = X.t3 ? perm_decode<true>(ops[t], R.y, R.z, X.len)
+                         : perm_decode<false>(ops[t], R.y, R.z, X.len);
+        }
       }
     }
     d = cvrptw_composite(X, sol, cm, aux);
@@ -687,7 +842,8 @@ __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *so
 // deltas), so the steps overlap; k selects how many count.
 template <int MODEL, bool T16>
 __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl *sol,
-                                                    const Weights<5> &W, uint32_t c, uint32_t p,
+                                                    const Weights<Enc<MODEL>::NO> &W, uint32_t c,
+                                                    uint32_t p,
                                                     uint32_t g, uint32_t &rec, CandMoves &cm,
                                                     const CvAux &aux) {
   if constexpr (MODEL == CVRPTW) {
@@ -1529,9 +1685,9 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   const bool packed = 96ull * (uint64_t)cpl * (uint64_t)I.U * (uint64_t)mine < 65536ull;
   // a member's window counts in bytes while it evolves (PackedStats)
   const bool bytec = 3ull * (uint64_t)cpl * (uint64_t)I.U <= 255ull;
-  PackedStats ps{0u, 0u, 0u, 0u};
+  PackedStats ps{0u, 0u, 0u, 0u, 0u, 0u};
   auto count = [&](uint32_t rec) {
-    if (bytec) packed_add(ps, rec);
+    if (bytec) packed_add<NO>(ps, rec);
     else stats_add(st, rec);
   };
 
@@ -1797,12 +1953,12 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
 #pragma unroll
     for (int l = 0; l < NO; ++l) {
       my = (lane == Enc<MODEL>::glob(l)) ? tot[l] : my;
-      my = (lane == 8 + Enc<MODEL>::glob(l)) ? tot[NO + l] : my;
+      my = (lane == kStatV + Enc<MODEL>::glob(l)) ? tot[NO + l] : my;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      my = (lane == 16 + i) ? tot[2 * NO + i] : my;
-      my = (lane == 19 + i) ? tot[2 * NO + 3 + i] : my;
+      my = (lane == kStatUK + i) ? tot[2 * NO + i] : my;
+      my = (lane == kStatVK + i) ? tot[2 * NO + 3 + i] : my;
     }
     const int slot = wi & 1;
     if constexpr (NW > 1) {
@@ -1928,13 +2084,13 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     for (int l = 0; l < NO; ++l) {
       const uint32_t tu = __reduce_add_sync(kFull, st.u[l]), tv = __reduce_add_sync(kFull, st.v[l]);
       my = (lane == Enc<MODEL>::glob(l)) ? tu : my;
-      my = (lane == 8 + Enc<MODEL>::glob(l)) ? tv : my;
+      my = (lane == kStatV + Enc<MODEL>::glob(l)) ? tv : my;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const uint32_t tu = __reduce_add_sync(kFull, st.uk[i]), tv = __reduce_add_sync(kFull, st.vk[i]);
-      my = (lane == 16 + i) ? tu : my;
-      my = (lane == 19 + i) ? tv : my;
+      my = (lane == kStatUK + i) ? tu : my;
+      my = (lane == kStatVK + i) ? tv : my;
     }
     if (p0 + G.grp == 0 && G.gw == 0 && !pend_used) my += pend;
     if (lane < kStats && my) atomicAdd(&S->pend_out[lane], my);

@@ -333,12 +333,16 @@ cgo_status cgo_server_create(const cgo_server_cfg *cfg, cgo_server **out) {
   return CGO_OK;
 }
 
-cgo_status cgo_submit(cgo_server *S, cgo_problem *p, const cgo_params *q, uint64_t seed,
+cgo_status cgo_submit(cgo_server *S, cgo_problem *p, const cgo_params *qin, uint64_t seed,
                       uint64_t *ticket) {
   if (!S || !p || !ticket) return fail(CGO_ERR_INVALID, "NULL argument");
   if (p->device != S->device) return fail(CGO_ERR_INVALID, "problem lives on another device");
+  cgo_params qq;
+  cgo_status s = load_params(qin, &qq);
+  if (s != CGO_OK) return s;
+  const cgo_params *q = &qq;
   uint32_t en = 0;
-  cgo_status s = validate_params(p, q, &en);
+  s = validate_params(p, q, &en);
   if (s != CGO_OK) return s;
   if (q->generations >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "too many generations");
   {

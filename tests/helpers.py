@@ -14,7 +14,7 @@ def params_for(inst, **over):
     p["G"] = 0
     ops = over.pop("ops", None)
     if ops is not None:
-        w = [0] * 8
+        w = [0] * O.NOPS
         for o in ops:
             w[o] = 65536 // len(ops)
         p["w_op"] = w

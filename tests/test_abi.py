@@ -94,3 +94,38 @@ def test_gather_peak_rejects_bad_sizes_without_a_gpu():
     assert L.cgo_gather_peak(1, 29, ctypes.byref(g), None) == cgo.ERR_INVALID
     assert L.cgo_gather_peak(2, 12, ctypes.byref(g), None) == cgo.ERR_INVALID
     assert L.cgo_gather_peak(0, 12, None, None) == cgo.ERR_INVALID
+
+
+def test_earlier_struct_sizes():
+    """The structs before the row level was appended: their sizeof (tail
+    padding included) is what CGO_PARAMS_SIZE_V1 / CGO_STATE_SIZE_V1 give."""
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    src = r"""
+#include <stdio.h>
+#include "cgo.h"
+typedef struct {
+  uint32_t struct_size; int32_t population, candidates; int64_t generations; uint32_t op_mask;
+  uint32_t op_w0_q16[8], k_w0_q16[3]; uint64_t T0_q32, alpha_q32;
+  uint32_t aos_interval, ema_alpha_q16, w_floor_q16, w_cap_q16, op_cap_q16[8], stag_limit,
+      elite_period, init_oversample, init_heuristic, islands, migrate_period, migrate_strategy,
+      migrate_n, cross_q16;
+} params_v1;
+typedef struct {
+  uint32_t struct_size; int32_t population, length; int64_t generation; uint64_t T_q32;
+  uint32_t w_op_q16[8], w_k_q16[3], stag; int64_t elite_prev;
+  uint32_t u_op[8], v_op[8], u_k[3], v_k[3]; int32_t *cur, *best_sol; int64_t *cost, *best_cost;
+} state_v1;
+int main(void) {
+  printf("%zu %u %zu %u\n", sizeof(params_v1), CGO_PARAMS_SIZE_V1, sizeof(state_v1), CGO_STATE_SIZE_V1);
+  return 0;
+}
+"""
+    d = os.path.join(ROOT, "tests", "_build")
+    os.makedirs(d, exist_ok=True)
+    c, exe = os.path.join(d, "v1.c"), os.path.join(d, "v1")
+    open(c, "w").write(src)
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+    a, b, x, y = (int(v) for v in subprocess.run([exe], capture_output=True, text=True,
+                                                   check=True).stdout.split())
+    assert a == b and x == y

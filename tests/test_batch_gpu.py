@@ -69,6 +69,11 @@ def mixed_batch():
     items.append((dict(I.knapsack(90, 262), tag=52), dict(P=7, C=48, G=21, U=7, cross_q16=65536)))
     items.append((dict(I.cvrptw(16, 263, vehicles=4, capacity=80), tag=53),
                   dict(P=6, C=48, G=20, U=4, cross_q16=65536)))
+    # the row level of CVRPTW (routes as rows), with and without the others
+    items.append((dict(I.cvrptw(20, 265, vehicles=6, capacity=80), tag=55),
+                  dict(P=6, C=64, G=26, U=4, ops=[O.SWAP, O.TWO_OPT, O.INSERT] + [O.ROW_SWAP_OP, O.ROW_MERGE_OP, O.ROW_SPLIT_OP])))
+    items.append((dict(I.cvrptw(12, 266, vehicles=7, capacity=60), tag=56),
+                  dict(P=5, C=48, G=21, ops=[O.ROW_SWAP_OP, O.ROW_MERGE_OP, O.ROW_SPLIT_OP], w_k=[20000, 30000, 15536])))
     # weighted CVRPTW objectives (vehicles first)
     items.append((dict(I.cvrptw(18, 264, vehicles=5, capacity=90), tag=54, weight_vehicles=10 ** 6),
                   dict(P=6, C=48, G=22)))

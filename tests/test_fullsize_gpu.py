@@ -52,7 +52,7 @@ def check_state(inst, p, st, best, where):
     assert c == st["best_cost"][e] and (np.asarray(sol) == st["best_sol"][e]).all(), where
     # weights: after the last update the enabled operators' Q16 weights sum
     # to 2^16 less at most one unit each (floor division); disabled ones are 0
-    on = [(p["op_mask"] >> i) & 1 for i in range(8)]
+    on = [(p["op_mask"] >> i) & 1 for i in range(len(st["w_op"]))]
     w = [x for x, e in zip(st["w_op"], on) if e]
     assert all(x > 0 for x in w) and all(x == 0 for x, e in zip(st["w_op"], on) if not e), where
     assert 65536 - len(w) <= sum(w) <= 65536, (where, w)

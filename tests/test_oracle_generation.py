@@ -106,7 +106,7 @@ def test_fixture_arithmetic(case):
 
 
 def _counts(gens, only_winner=False):
-    u, v, uk, vk = [0] * 8, [0] * 8, [0] * 3, [0] * 3
+    u, v, uk, vk = [0] * O.NOPS, [0] * O.NOPS, [0] * 3, [0] * 3
     for gen in gens:
         for cd in gen["candidates"]:
             if only_winner and cd["c"] != gen["winner"]:

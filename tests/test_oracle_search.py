@@ -20,7 +20,7 @@ from conftest import SEEDS
 
 
 def equal_weights(p, ops):
-    w = [0] * 8
+    w = [0] * O.NOPS
     for o in ops:
         w[o] = 65536 // len(ops)
     p["w_op"] = w
@@ -311,7 +311,7 @@ def test_default_priors_by_scale():
         p = O.default_params(inst)
         S = 3 * 65536 + oro
         assert p["w_op"][:4] == [(65536 << 16) // S] * 3 + [(oro << 16) // S]
-        assert p["w_op"][4:] == [0, 0, (tro << 16) // S, 0]
+        assert p["w_op"][4:] == [0, 0, (tro << 16) // S, 0, 0, 0, 0]   # no row level for TSP
         assert not (p["op_mask"] >> O.THREE_OPT) & 1
         assert p["w_k"] == [52429, 9830, 3277]
     # the segment operators of the binary and integer sets take the

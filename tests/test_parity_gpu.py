@@ -570,6 +570,66 @@ def test_islands_invalid_parameters(cgo):
     assert_same_state(g, o, "no migration")
 
 
+# ------------------------------------------------------------ row level
+ROWS = [O.ROW_SWAP_OP, O.ROW_MERGE_OP, O.ROW_SPLIT_OP]
+
+
+@pytest.mark.parametrize("ns", [1, 2])
+@pytest.mark.parametrize("kw", [(65536, 0, 0), (0, 65536, 0), (0, 0, 65536), None])
+@pytest.mark.parametrize("ops", [ROWS, [SW, TO, INS, OR, TH] + ROWS, [INS, O.ROW_SPLIT_OP],
+                                 [O.ROW_SWAP_OP], [O.ROW_MERGE_OP, TO]])
+def test_cvrptw_row_operators(cgo, ns, kw, ops):
+    """The row level of CVRPTW's separator sequence (row_swap, row_merge,
+    row_split; Table "operators"), alone and composed with the permutation
+    operators in k-step moves: a row step after earlier steps finds its
+    routes in the sequence those steps left."""
+    inst = I.cvrptw(20, 95, vehicles=7, capacity=70)
+    over = dict(P=6, C=64, G=30, U=5, ops=ops, T0=30 << 32)
+    if kw:
+        over.update(w_k=list(kw), stag_limit=0)
+    p = params_for(inst, **over)
+    prob, g, o = run_both(cgo, inst, p, 7, wpm=2, ns=ns)
+    where = "ops %s k %s ns %d" % (ops, kw, ns)
+    assert_same_state(g, o, where)
+    assert_same_counts(prob, o, where)
+
+
+@pytest.mark.parametrize("n,V", [(3, 2), (6, 6), (30, 3), (40, 12)])
+def test_cvrptw_row_operators_sizes(cgo, n, V):
+    """Two routes, more routes than customers (many empty routes), long
+    routes; several candidates per lane and the deep generations."""
+    inst = I.cvrptw(n, 96 + n, vehicles=V, capacity=90)
+    for C, wpm, ns in ((150, 1, 1), (128, 4, 2), (128, 4, 3)):
+        p = params_for(inst, P=5, C=C, G=23, U=4, ops=[SW, INS, OR] + ROWS)
+        prob, g, o = run_both(cgo, inst, p, 3, wpm=wpm, ns=ns)
+        assert_same_state(g, o, "n %d V %d C %d ns %d" % (n, V, C, ns))
+
+
+def test_earlier_struct_sizes_are_accepted(cgo):
+    """cgo_params / cgo_state of the size before the row level was appended:
+    solves run with the row operators off; a state without the row level is
+    refused only while row operators are on."""
+    import ctypes
+    inst = I.cvrptw(15, 97, vehicles=4, capacity=80)
+    prob = cgo.Problem(inst)
+    v1 = (cgo.cgo_params.row_w0_q16.offset + 7) & ~7     # the earlier sizeof
+    q = cgo.cgo_params()
+    q.struct_size = v1
+    cgo.check(cgo.lib().cgo_params_default(prob.h, ctypes.byref(q)), "default")
+    assert q.struct_size == v1 and list(q.row_w0_q16) == [0, 0, 0]
+    q.generations = 17
+    cgo.check(cgo.lib().cgo_solve(prob.h, ctypes.byref(q), 5, None), "solve")
+    p = params_for(inst, P=32, C=128, G=17)
+    assert_same_state(prob.state(), oracle_run(inst, p, 5, 17), "v1 params")
+    # the full defaults carry the row priors, off in the mask
+    full = prob.default_params()
+    assert full["w_op"][8:] == [full["w_op"][0]] * 3 and not full["op_mask"] >> 8
+    bad = cgo.cgo_params()
+    bad.struct_size = v1 - 4
+    with pytest.raises(cgo.CgoError):
+        cgo.check(cgo.lib().cgo_solve(prob.h, ctypes.byref(bad), 5, None), "solve")
+
+
 # ----------------------------------------------------- state and resume
 @pytest.mark.parametrize("maker", [lambda: I.tsp_uniform(25, 60), lambda: I.knapsack(60, 61),
                                    lambda: I.gap(40, 62, m=6), lambda: I.qap_random(8, 63),
