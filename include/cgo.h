@@ -37,7 +37,8 @@ typedef enum {
   CGO_ERR_UNSUPPORTED = 4,  /* valid, but outside what the GPU path implements */
   CGO_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
   CGO_ERR_BUSY = 6,         /* the handle (or server slot) is in use */
-  CGO_ERR_STATE = 7         /* no search state yet, or it was lost to an error */
+  CGO_ERR_STATE = 7,        /* no search state yet, or it was lost to an error */
+  CGO_ERR_CANCELLED = 8     /* the request was cancelled (cgo_cancel) */
 } cgo_status;
 
 /* Encodings (Sec. 3.1.1). */
@@ -356,7 +357,15 @@ typedef struct {
   int64_t smem_budget_bytes;   /* largest shared-memory footprint of one request (0 = the
                                   CTA limit); larger requests are refused at submit */
   int64_t slice_generations;   /* generations per time slice, >= 1 */
+  /* --- appended --- */
+  int32_t max_queued;          /* requests waiting for admission at most; cgo_submit
+                                  returns CGO_ERR_BUSY beyond it (0 = no bound) */
+  int32_t reserved;            /* 0 */
 } cgo_server_cfg;
+
+/* The size of cgo_server_cfg before max_queued was appended (accepted by
+ * cgo_server_create: no queue bound). */
+#define CGO_SERVER_CFG_SIZE_V1 ((uint32_t)offsetof(cgo_server_cfg, max_queued))
 
 typedef struct {
   uint32_t struct_size;        /* = sizeof(cgo_server_info) */
@@ -372,15 +381,27 @@ cgo_status cgo_server_create(const cgo_server_cfg *cfg, cgo_server **out);
  * seed; the handle is in use (CGO_ERR_BUSY for other calls) until the
  * request finishes, after which it holds the final state (cgo_best,
  * cgo_state_get).  Validation errors are returned here; a request whose
- * shared-memory footprint exceeds the budget returns CGO_ERR_UNSUPPORTED. */
+ * shared-memory footprint exceeds the budget returns CGO_ERR_UNSUPPORTED;
+ * CGO_ERR_BUSY when max_queued requests already wait for admission.  A
+ * request whose device state cannot be allocated at admission finishes with
+ * CGO_ERR_NOMEM (cgo_wait returns it); the server carries on with the rest. */
 cgo_status cgo_submit(cgo_server *srv, cgo_problem *prob, const cgo_params *params, uint64_t seed,
                       uint64_t *ticket);
 
 /* Wait for a ticket (timeout_ms < 0: forever).  On CGO_OK fills the elite
  * cost and the latency from submit to completion (seconds) and forgets the
- * ticket; CGO_ERR_TIMEOUT leaves it pending.  Each ticket is waited once. */
+ * ticket; CGO_ERR_TIMEOUT leaves it pending.  Each ticket is waited once.
+ * A cancelled request returns CGO_ERR_CANCELLED (and is forgotten). */
 cgo_status cgo_wait(cgo_server *srv, uint64_t ticket, int32_t timeout_ms, int64_t *cost,
                     double *latency_s);
+
+/* Cancel a request.  A request still waiting for admission finishes at
+ * once; a resident one runs no further slice and finishes at the next slice
+ * boundary, freeing its slot and memory.  Its handle keeps no search state
+ * (CGO_ERR_STATE from cgo_best) and is free again once the request has
+ * finished.  CGO_ERR_INVALID for an unknown ticket, CGO_ERR_STATE if it has
+ * already finished.  The serving loop has no counterpart in the paper. */
+cgo_status cgo_cancel(cgo_server *srv, uint64_t ticket);
 
 /* Counters of the request loop. */
 cgo_status cgo_server_stats(const cgo_server *srv, cgo_server_info *out);
@@ -423,7 +444,10 @@ cgo_status cgo_kernel_launches(uint64_t *out);
  *           10000);
  * what = 3: batched solves advance in time slices of `value` generations
  *           (default 2000; process-wide, prob may be NULL).  Results do not
- *           depend on it.
+ *           depend on it;
+ * what = 4: the value-th device allocation the library makes from now on
+ *           (1 = the next one) fails as out of memory, without allocating;
+ *           0 disarms it (process-wide, prob may be NULL).
  * Errors: CGO_ERR_INVALID for an unknown `what` or a value out of range. */
 cgo_status cgo_debug_inject(cgo_problem *prob, int32_t what, int64_t value);
 

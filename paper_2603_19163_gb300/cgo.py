@@ -19,8 +19,10 @@ from . import build as _build
 NOPS = 8        # slots of the first operator arrays of cgo_params / cgo_state
 NROW = 3        # the row level's slots (8 .. 10), in arrays of their own
 NOPS_ALL = NOPS + NROW
-OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_BUSY, ERR_STATE = range(8)
-STATUS_NAMES = ["OK", "INVALID", "NOMEM", "CUDA", "UNSUPPORTED", "TIMEOUT", "BUSY", "STATE"]
+OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, \
+    ERR_CANCELLED = range(9)
+STATUS_NAMES = ["OK", "INVALID", "NOMEM", "CUDA", "UNSUPPORTED", "TIMEOUT", "BUSY", "STATE",
+                "CANCELLED"]
 TSP, QAP, KNAPSACK, GAP, CVRPTW = range(5)
 ENC_PERM, ENC_BINARY, ENC_INTEGER = range(3)
 MODEL_ENCODING = {TSP: ENC_PERM, QAP: ENC_PERM, KNAPSACK: ENC_BINARY, GAP: ENC_INTEGER,
@@ -74,7 +76,8 @@ class cgo_state(ctypes.Structure):
 class cgo_server_cfg(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("max_slots", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("smem_budget_bytes", ctypes.c_int64),
-                ("slice_generations", ctypes.c_int64)]
+                ("slice_generations", ctypes.c_int64), ("max_queued", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class cgo_server_info(ctypes.Structure):
@@ -134,6 +137,7 @@ def lib() -> ctypes.CDLL:
                 "cgo_wait": ([vp, c.c_uint64, c.c_int32, _i64p, P(c.c_double)], c.c_int),
                 "cgo_server_stats": ([vp, P(cgo_server_info)], c.c_int),
                 "cgo_server_destroy": ([vp], c.c_int),
+                "cgo_cancel": ([vp, c.c_uint64], c.c_int),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(L, name)
@@ -396,9 +400,9 @@ class Server:
     """A cgo_server: continuous batching of solve requests."""
 
     def __init__(self, max_slots: int = 1024, hbm_budget_bytes: int = 64 << 30,
-                 smem_budget_bytes: int = 0, slice_generations: int = 2000):
+                 smem_budget_bytes: int = 0, slice_generations: int = 2000, max_queued: int = 0):
         cfg = cgo_server_cfg(ctypes.sizeof(cgo_server_cfg), max_slots, hbm_budget_bytes,
-                             smem_budget_bytes, slice_generations)
+                             smem_budget_bytes, slice_generations, max_queued, 0)
         h = ctypes.c_void_p()
         check(lib().cgo_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cgo_server_create")
         self.h = h
@@ -416,6 +420,9 @@ class Server:
         check(lib().cgo_wait(self.h, int(ticket), int(timeout_ms), ctypes.byref(c),
                              ctypes.byref(lat)), "cgo_wait")
         return c.value, lat.value
+
+    def cancel(self, ticket: int):
+        check(lib().cgo_cancel(self.h, int(ticket)), "cgo_cancel")
 
     def stats(self) -> dict:
         i = cgo_server_info()

@@ -87,7 +87,22 @@ cudaError_t copy_sync(void *dst, const void *src, size_t bytes, cudaMemcpyKind k
   return e != cudaSuccess ? e : cudaStreamSynchronize(host_stream());
 }
 
-cudaError_t dev_alloc(void **p, size_t bytes) { return cudaMallocAsync(p, bytes, host_stream()); }
+// test hook: the n-th device allocation from now on fails (0 = off)
+static std::atomic<int64_t> g_alloc_fail{0};
+bool alloc_fails() {
+  int64_t v = g_alloc_fail.load();
+  while (v > 0)
+    if (g_alloc_fail.compare_exchange_weak(v, v - 1)) return v == 1;
+  return false;
+}
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+  if (alloc_fails()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, st);
+}
+cudaError_t dev_alloc(void **p, size_t bytes) { return lib_malloc_async(p, bytes, host_stream()); }
 void dev_free(void *p) {
   if (p) cudaFreeAsync(p, host_stream());
 }
@@ -95,7 +110,7 @@ void dev_free(void *p) {
 cudaError_t copy_in(int32_t **dst, const int32_t *src, int64_t count, bool on_device) {
   const int64_t bytes = pad16(count * 4);
   cudaStream_t hs = host_stream();
-  cudaError_t e = cudaMallocAsync((void **)dst, (size_t)bytes, hs);
+  cudaError_t e = lib_malloc_async((void **)dst, (size_t)bytes, hs);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(*dst, 0, (size_t)bytes, hs);
   if (e != cudaSuccess) return e;
@@ -194,9 +209,16 @@ cgo_status ensure_pool(cgo_problem *p, const cgo_params &q) {
   p->d_pool = nullptr;
   p->d_pool_cost = nullptr;
   p->pool_cap = 0;
-  CUDA_TRY(dev_alloc((void **)&p->d_pool, (size_t)N * p->len * 4), "start pool");
-  CUDA_TRY(dev_alloc((void **)&p->d_pool_cost, (size_t)N * 8), "start pool");
-  CUDA_TRY(cudaStreamSynchronize(host_stream()), "start pool");
+  cudaError_t e = dev_alloc((void **)&p->d_pool, (size_t)N * p->len * 4);
+  if (e == cudaSuccess) e = dev_alloc((void **)&p->d_pool_cost, (size_t)N * 8);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(host_stream());
+  if (e != cudaSuccess) {
+    dev_free(p->d_pool);
+    dev_free(p->d_pool_cost);
+    p->d_pool = nullptr;
+    p->d_pool_cost = nullptr;
+    return cuda_fail(e, "start pool");
+  }
   p->pool_cap = N;
   return CGO_OK;
 }
@@ -205,14 +227,18 @@ cgo_status ensure_state(cgo_problem *p, int P) {
   if (p->P_alloc == P && p->d_cur) return CGO_OK;
   free_state(p);
   const size_t sol = (size_t)P * p->len * 4;
-  CUDA_TRY(dev_alloc((void **)&p->d_cur, sol), "state alloc");
-  CUDA_TRY(dev_alloc((void **)&p->d_bestsol, sol), "state alloc");
-  CUDA_TRY(dev_alloc((void **)&p->d_cost, (size_t)P * 8), "state alloc");
-  CUDA_TRY(dev_alloc((void **)&p->d_best, (size_t)P * 8), "state alloc");
-  CUDA_TRY(dev_alloc((void **)&p->d_aos, 2 * sizeof(DevAos)), "state alloc");
-  CUDA_TRY(dev_alloc((void **)&p->d_sync, sizeof(DevSync)), "state alloc");
-  CUDA_TRY(cudaMemsetAsync(p->d_aos, 0, 2 * sizeof(DevAos), host_stream()), "state init");
-  CUDA_TRY(cudaStreamSynchronize(host_stream()), "state alloc");
+  cudaError_t e = dev_alloc((void **)&p->d_cur, sol);
+  if (e == cudaSuccess) e = dev_alloc((void **)&p->d_bestsol, sol);
+  if (e == cudaSuccess) e = dev_alloc((void **)&p->d_cost, (size_t)P * 8);
+  if (e == cudaSuccess) e = dev_alloc((void **)&p->d_best, (size_t)P * 8);
+  if (e == cudaSuccess) e = dev_alloc((void **)&p->d_aos, 2 * sizeof(DevAos));
+  if (e == cudaSuccess) e = dev_alloc((void **)&p->d_sync, sizeof(DevSync));
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_aos, 0, 2 * sizeof(DevAos), host_stream());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(host_stream());
+  if (e != cudaSuccess) {
+    free_state(p);  // nothing half-allocated stays behind
+    return cuda_fail(e, "state alloc");
+  }
   p->P_alloc = P;
   return CGO_OK;
 }
@@ -1155,11 +1181,11 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_in, 
     lists.insert(lists.end(), bk.members.begin(), bk.members.end());
   }
   cudaError_t e;
-  if ((e = cudaMallocAsync((void **)&d_k, sizeof(KInst) * (size_t)count, st)) != cudaSuccess ||
-      (e = cudaMallocAsync((void **)&d_a0, sizeof(DevAos) * (size_t)count, st)) != cudaSuccess ||
-      (e = cudaMallocAsync((void **)&d_lists, sizeof(int) * lists.size(), st)) != cudaSuccess ||
-      (e = cudaMallocAsync((void **)&d_next, sizeof(int) * nb, st)) != cudaSuccess ||
-      (e = cudaMallocAsync((void **)&d_counts, sizeof(int) * nb, st)) != cudaSuccess) {
+  if ((e = lib_malloc_async((void **)&d_k, sizeof(KInst) * (size_t)count, st)) != cudaSuccess ||
+      (e = lib_malloc_async((void **)&d_a0, sizeof(DevAos) * (size_t)count, st)) != cudaSuccess ||
+      (e = lib_malloc_async((void **)&d_lists, sizeof(int) * lists.size(), st)) != cudaSuccess ||
+      (e = lib_malloc_async((void **)&d_next, sizeof(int) * nb, st)) != cudaSuccess ||
+      (e = lib_malloc_async((void **)&d_counts, sizeof(int) * nb, st)) != cudaSuccess) {
     release();
     return cuda_fail(e, "batch descriptors");
   }
@@ -1376,7 +1402,7 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
  * so the barrier cannot complete and the bounded wait must give up;
  * what = 2 sets the barrier wait limit to `value` milliseconds. */
 cgo_status cgo_debug_inject(cgo_problem *p, int32_t what, int64_t value) {
-  if (!p && what != 3) return fail(CGO_ERR_INVALID, "NULL problem");
+  if (!p && what != 3 && what != 4) return fail(CGO_ERR_INVALID, "NULL problem");
   if (what == 1) {
     if (value < 0 || value > 1024) return fail(CGO_ERR_INVALID, "phantom members out of range");
     p->phantom_members = (uint32_t)value;
@@ -1386,6 +1412,9 @@ cgo_status cgo_debug_inject(cgo_problem *p, int32_t what, int64_t value) {
   } else if (what == 3) {
     if (value < 1 || value > (1ll << 31)) return fail(CGO_ERR_INVALID, "slice out of range");
     g_batch_slice = value;
+  } else if (what == 4) {
+    if (value < 0 || value > (1ll << 31)) return fail(CGO_ERR_INVALID, "allocation index out of range");
+    g_alloc_fail.store(value);
   } else {
     return fail(CGO_ERR_INVALID, "unknown injection");
   }

@@ -11,6 +11,7 @@
 // Populations, AOS weights, temperatures and generation counters stay in
 // device memory across slices.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -42,6 +43,7 @@ struct Req {
   int64_t cost = 0;
   cgo_status status = CGO_OK;
   bool done = false;
+  std::atomic<bool> cancel{false};  // cgo_cancel of a resident request
   KInst h{};
 };
 
@@ -201,8 +203,19 @@ void server_loop(cgo_server *S) {
       cgo_status s = ensure_state(p, r->params.population);
       if (s == CGO_OK) s = ensure_pool(p, r->params);
       if (s != CGO_OK) {
-        fail_all(S, s, "state allocation failed");
-        return;
+        // this request ends with the allocation error; the others carry on
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->status = s;
+        r->done = true;
+        r->t_done = Clock::now();
+        S->slot_req[(size_t)r->slot] = nullptr;
+        S->free_slots.push_back(r->slot);
+        S->hbm_used -= r->bytes;
+        S->active--;
+        r->slot = -1;
+        p->busy.store(0);
+        S->cv_done.notify_all();
+        continue;
       }
       p->params = r->params;
       p->seed = r->seed;
@@ -233,7 +246,7 @@ void server_loop(cgo_server *S) {
     std::fill(counts.begin(), counts.end(), 0);
     for (size_t sl = 0; sl < S->slot_req.size(); ++sl) {
       Req *r = S->slot_req[sl];
-      if (!r || r->g >= r->params.generations) continue;
+      if (!r || r->g >= r->params.generations || r->cancel.load()) continue;
       lists[(size_t)r->bucket * S->cfg.max_slots + (size_t)counts[(size_t)r->bucket]++] = (int)sl;
     }
     cudaError_t e = cudaSuccess;
@@ -256,8 +269,13 @@ void server_loop(cgo_server *S) {
     // retire the requests that reached their budget
     const Clock::time_point now = Clock::now();
     std::vector<Req *> finished;
+    std::vector<Req *> cancelled;
     for (Req *r : S->slot_req) {
       if (!r) continue;
+      if (r->cancel.load()) {
+        cancelled.push_back(r);
+        continue;
+      }
       r->g = std::min<int64_t>(r->params.generations, r->g + S->cfg.slice_generations);
       if (r->g >= r->params.generations) finished.push_back(r);
     }
@@ -287,7 +305,18 @@ void server_loop(cgo_server *S) {
       S->active--;
       S->completed++;
     }
-    if (!finished.empty()) S->cv_done.notify_all();
+    for (Req *r : cancelled) {
+      r->prob->has_state = false;
+      r->prob->busy.store(0);
+      r->status = CGO_ERR_CANCELLED;
+      r->t_done = now;
+      r->done = true;
+      S->slot_req[(size_t)r->slot] = nullptr;
+      S->free_slots.push_back(r->slot);
+      S->hbm_used -= r->bytes;
+      S->active--;
+    }
+    if (!finished.empty() || !cancelled.empty()) S->cv_done.notify_all();
   }
 }
 
@@ -298,8 +327,13 @@ extern "C" {
 cgo_status cgo_server_create(const cgo_server_cfg *cfg, cgo_server **out) {
   if (!out) return fail(CGO_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (!cfg || cfg->struct_size != sizeof(cgo_server_cfg))
+  if (!cfg || (cfg->struct_size != sizeof(cgo_server_cfg) && cfg->struct_size != CGO_SERVER_CFG_SIZE_V1))
     return fail(CGO_ERR_INVALID, "cfg: struct_size must be sizeof(cgo_server_cfg)");
+  cgo_server_cfg c{};
+  memcpy(&c, cfg, cfg->struct_size);
+  c.struct_size = sizeof c;
+  if (c.max_queued < 0) return fail(CGO_ERR_INVALID, "max_queued < 0");
+  cfg = &c;
   if (cfg->max_slots < 1 || cfg->max_slots > 65536) return fail(CGO_ERR_INVALID, "max_slots out of [1, 65536]");
   if (cfg->slice_generations < 1) return fail(CGO_ERR_INVALID, "slice_generations < 1");
   if (cfg->hbm_budget_bytes < 1) return fail(CGO_ERR_INVALID, "hbm_budget_bytes < 1");
@@ -371,6 +405,11 @@ cgo_status cgo_submit(cgo_server *S, cgo_problem *p, const cgo_params *qin, uint
       delete r;
       return fail(CGO_ERR_STATE, "server is stopping or failed");
     }
+    if (S->cfg.max_queued > 0 && (int64_t)S->queue.size() >= S->cfg.max_queued) {
+      p->busy.store(0);
+      delete r;
+      return fail(CGO_ERR_BUSY, "the submit queue holds %d requests (max_queued)", S->cfg.max_queued);
+    }
     r->ticket = S->next_ticket++;
     S->reqs[r->ticket] = r;
     S->queue.push_back(r);
@@ -396,7 +435,32 @@ cgo_status cgo_wait(cgo_server *S, uint64_t ticket, int32_t timeout_ms, int64_t 
   if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
   S->reqs.erase(it);
   delete r;
+  if (st == CGO_ERR_CANCELLED) return fail(st, "ticket %llu was cancelled", (unsigned long long)ticket);
+  if (st == CGO_ERR_NOMEM) return fail(st, "ticket %llu: no device memory for its state", (unsigned long long)ticket);
   if (st != CGO_OK) return fail(st, "request failed: %s", S->fatal_msg.c_str());
+  return CGO_OK;
+}
+
+cgo_status cgo_cancel(cgo_server *S, uint64_t ticket) {
+  if (!S) return fail(CGO_ERR_INVALID, "NULL server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return fail(CGO_ERR_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+  Req *r = it->second;
+  if (r->done) return fail(CGO_ERR_STATE, "ticket %llu has finished", (unsigned long long)ticket);
+  auto q = std::find(S->queue.begin(), S->queue.end(), r);
+  if (q != S->queue.end()) {
+    // not admitted yet: it finishes now
+    S->queue.erase(q);
+    r->prob->has_state = false;
+    r->prob->busy.store(0);
+    r->status = CGO_ERR_CANCELLED;
+    r->t_done = Clock::now();
+    r->done = true;
+    S->cv_done.notify_all();
+    return CGO_OK;
+  }
+  r->cancel.store(true);  // resident: retired at the next slice boundary
   return CGO_OK;
 }
 
