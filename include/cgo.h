@@ -300,7 +300,9 @@ cgo_status cgo_op_counts(const cgo_problem *prob, uint64_t *out, int32_t cap);
 /* Batched solve: `count` independent problems (different models and sizes
  * allowed) advance together in persistent kernels; problem i uses
  * per_prob[i] and seeds[i].  Each result is bit-identical to cgo_solve of
- * that problem alone.  The GPU path needs population <= 32 here. */
+ * that problem alone.  All members of a problem share one CTA: its
+ * solutions (and, for CVRPTW, route caches) must fit the shared memory of
+ * one CTA beside the staged instance data, else CGO_ERR_UNSUPPORTED. */
 cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_prob,
                            const uint64_t *seeds, int32_t count, void *cuda_stream);
 
