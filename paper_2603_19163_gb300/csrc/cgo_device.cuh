@@ -69,32 +69,6 @@ __device__ __forceinline__ void philox3(uint32_t a0, uint32_t b0, uint32_t e0, u
   E = make_uint4(e[0], e[1], e[2], e[3]);
 }
 
-// Two Philox4x32-10 blocks whose counters differ only in word 0, advanced
-// round by round together (as philox3).
-__device__ __forceinline__ void philox2(uint32_t a0, uint32_t b0, uint32_t c1, uint32_t c2,
-                                        uint32_t c3, uint32_t k0, uint32_t k1, uint4 &A, uint4 &B) {
-  uint32_t a[4] = {a0, c1, c2, c3}, b[4] = {b0, c1, c2, c3};
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t alo0 = 0xD2511F53u * a[0], ahi0 = __umulhi(0xD2511F53u, a[0]);
-    const uint32_t blo0 = 0xD2511F53u * b[0], bhi0 = __umulhi(0xD2511F53u, b[0]);
-    const uint32_t alo1 = 0xCD9E8D57u * a[2], ahi1 = __umulhi(0xCD9E8D57u, a[2]);
-    const uint32_t blo1 = 0xCD9E8D57u * b[2], bhi1 = __umulhi(0xCD9E8D57u, b[2]);
-    a[0] = ahi1 ^ a[1] ^ k0;
-    b[0] = bhi1 ^ b[1] ^ k0;
-    a[2] = ahi0 ^ a[3] ^ k1;
-    b[2] = bhi0 ^ b[3] ^ k1;
-    a[1] = alo1;
-    b[1] = blo1;
-    a[3] = alo0;
-    b[3] = blo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  A = make_uint4(a[0], a[1], a[2], a[3]);
-  B = make_uint4(b[0], b[1], b[2], b[3]);
-}
-
 // A 16-bit field scaled to [0, m): floor(h * m / 2^16), m <= 65536.
 __device__ __forceinline__ int posm(uint32_t h16, uint32_t m) { return (int)((h16 * m) >> 16); }
 

@@ -54,7 +54,6 @@ struct SolScal {
 
 struct Layout {
   int64_t inst, sol_off, sol_stride, scr_off, scal_off, load_off, aux_off, aux_stride, part_off, total;
-  int64_t q_off;  // TSP candidate queues (two-phase evaluation), -1 if none
 };
 
 __host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64_t(15); }
@@ -91,7 +90,6 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   L.aux_stride = model == CVRPTW ? cv_aux_bytes(len) : 0;
   L.part_off = L.aux_off + (int64_t)nsol * L.aux_stride;
   L.total = L.part_off + (int64_t)groups * group_bytes(wpm);
-  L.q_off = -1;
   return L;
 }
 
@@ -597,7 +595,7 @@ struct CandMoves {
 // (positions, inverse maps, solution loads, triangle gathers, sums) so that
 // independent work is adjacent in program order.  With the int16 triangle
 // every junction sum fits comfortably in 32 bits.
-template <bool T16, int TB = 0, int TE = 3>
+template <bool T16>
 __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl *sol,
                                                      const CandMoves &cm, int k) {
   using Acc = typename std::conditional<T16, int, long long>::type;
@@ -605,7 +603,7 @@ __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl
   int pos[3][8];
   bool rev[3], mn[3], remp[3];
 #pragma unroll
-  for (int t = TB; t < TE; ++t) {
+  for (int t = 0; t < 3; ++t) {
     const PMove &mv = cm.m[t];
     rev[t] = mv.rev != 0;
     mn[t] = mv.b3 > mv.b2;
@@ -621,12 +619,12 @@ __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl
   }
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
-    if (TB <= 1 && TE > 1) pos[1][e] = perm_inv(cm.m[0], pos[1][e]);
-    if (TE > 2) pos[2][e] = perm_inv(cm.m[0], perm_inv(cm.m[1], pos[2][e]));
+    pos[1][e] = perm_inv(cm.m[0], pos[1][e]);
+    pos[2][e] = perm_inv(cm.m[0], perm_inv(cm.m[1], pos[2][e]));
   }
   int v[3][8];
 #pragma unroll
-  for (int t = TB; t < TE; ++t)
+  for (int t = 0; t < 3; ++t)
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[t][e] = sol[pos[t][e]];
   // gather pairs: (rl,x1) (y2,rf) (rl,af) (z4,rf) (bl,mf|af) (ml,af) (al,mf|bf) (ml,bf).
@@ -634,7 +632,7 @@ __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl
   // exist: pairs 0 and 2 become (al,bf) and (bl,af), pairs 1 and 3 cancel.
   uint32_t idx[3][8];
 #pragma unroll
-  for (int t = TB; t < TE; ++t) {
+  for (int t = 0; t < 3; ++t) {
     const int rl = v[t][0], rf = v[t][1], af = v[t][2], al = v[t][3], bf = v[t][4], bl = v[t][5],
               mf = v[t][6], ml = v[t][7];
     const bool re = remp[t];
@@ -649,13 +647,13 @@ __device__ __forceinline__ long long tsp_three_steps(const View &X, const PermEl
   }
   Acc dv[3][8];
 #pragma unroll
-  for (int t = TB; t < TE; ++t)
+  for (int t = 0; t < 3; ++t)
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       dv[t][e] = T16 ? (Acc)((const int16_t *)X.tri)[idx[t][e]] : (Acc)((const int32_t *)X.tri)[idx[t][e]];
   long long total = 0;
 #pragma unroll
-  for (int t = TB; t < TE; ++t) {
+  for (int t = 0; t < 3; ++t) {
     const Acc mid_n = dv[t][4] + (mn[t] ? dv[t][5] : (Acc)0);
     const Acc mid_o = dv[t][6] + (mn[t] ? dv[t][7] : (Acc)0);
     Acc d = dv[t][0] + dv[t][1] - dv[t][2] - dv[t][3] + (rev[t] ? (Acc)0 : mid_n - mid_o);
@@ -894,68 +892,6 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
   const long long d = tsp_three_steps<T16>(X, sol, cm, k);
   rec = stats_record(op0, k >= 2 ? op1 : -1, k >= 3 ? op2 : -1, k, d < 0);
   return d;
-}
-
-// ------------------------------------ TSP candidates in two phases
-// Phase A takes step 0 of every candidate (one Philox block, one decode, the
-// junction delta on the actual tour); the candidates of k >= 2 steps (a
-// quarter or so) go to a shared-memory queue, and phase B finishes them on
-// as few warps as their number needs: the later steps' Philox blocks, moves
-// and deltas on the virtual tour.  The arithmetic of every step is the same
-// as in candidate_perm; only who computes it changes.
-struct TspA {
-  int k, op0;
-  PMove m0;
-  long long d0;
-};
-
-template <bool T16>
-__device__ __forceinline__ TspA tsp_phase_a(const View &X, const PermEl *sol, const Weights<5> &W,
-                                            uint32_t c, uint32_t p, uint32_t g) {
-  const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
-  TspA a;
-  a.k = 1 + wpick(W.ck, W.Wk, R0.w);
-  a.op0 = wpick(W.cop, W.Wop, R0.x);
-  a.m0 = X.t3 ? perm_decode<true>(a.op0, R0.y, R0.z, X.len)
-              : perm_decode<false>(a.op0, R0.y, R0.z, X.len);
-  CandMoves cm;
-  cm.m[0] = a.m0;
-  a.d0 = tsp_three_steps<T16, 0, 1>(X, sol, cm, 1);
-  return a;
-}
-
-// steps 1 .. k-1 of a queued candidate; fills its moves and returns their delta
-template <bool T16>
-__device__ __forceinline__ long long tsp_phase_b(const View &X, const PermEl *sol, const Weights<5> &W,
-                                                 uint32_t c, uint32_t p, uint32_t g, int k,
-                                                 CandMoves &cm, int &op1, int &op2) {
-  uint4 R1, R2;
-  philox2(ctr_word(c, 1, kKindMove), ctr_word(c, 2, kKindMove), X.tag, p, g, X.k0, X.k1, R1, R2);
-  op1 = wpick(W.cop, W.Wop, R1.x);
-  op2 = wpick(W.cop, W.Wop, R2.x);
-  if (X.t3) {
-    cm.m[1] = perm_decode<true>(op1, R1.y, R1.z, X.len);
-    cm.m[2] = perm_decode<true>(op2, R2.y, R2.z, X.len);
-  } else {
-    cm.m[1] = perm_decode<false>(op1, R1.y, R1.z, X.len);
-    cm.m[2] = perm_decode<false>(op2, R2.y, R2.z, X.len);
-  }
-  cm.k = k;
-  return tsp_three_steps<T16, 1, 3>(X, sol, cm, k);
-}
-
-// One queue entry: candidate, k, operator of step 0 and the reversal flag
-// packed in a word, the step-0 move's cut points as 16-bit pairs, and the
-// step-0 delta (32 bits with the int16 triangle, else 64).
-template <bool T16>
-struct TspQ {
-  static constexpr int kInts = T16 ? 4 : 6;
-};
-__host__ __device__ inline int64_t tsp_queue_bytes(int model, int C, int tri16, int wpm, int ns,
-                                                   int groups) {
-  if (model != TSP || C > 32 * wpm) return 0;
-  const int64_t per = 16 + (int64_t)32 * wpm * 4 * (tri16 ? 4 : 6);  // counter + entries
-  return (int64_t)groups * ns * 2 * align16(per);
 }
 
 // Knapsack with the flip alone: k flips on x (a flip of an index flipped
@@ -1690,16 +1626,6 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   int *flag = (int *)(gmem + 2 * NW * sizeof(Partial));
   CandMoves *mvw = (CandMoves *)(gmem + 2 * NW * sizeof(Partial) + 16);
   uint32_t *cnt_smem = (uint32_t *)(gmem + 2 * NW * sizeof(Partial) + 16 + 2 * NW * sizeof(CandMoves));
-  // TSP two-phase evaluation: per generation slot and step parity, a counter
-  // and the queue of the step's candidates of k >= 2 steps
-  constexpr int kQInts = TspQ<T16>::kInts;
-  const int64_t qslot = align16(16 + (int64_t)WPM * 32 * 4 * kQInts);
-  unsigned char *qgrp = nullptr;
-  if constexpr (MODEL == TSP)
-    if (Lo.q_off >= 0 && I.C <= WPM * 32) {
-      qgrp = smem + Lo.q_off + (int64_t)G.grp * NS * 2 * qslot;
-      if (G.tig < NS * 2) *(int *)(qgrp + (int64_t)G.tig * qslot) = 0;  // a G.sync follows
-    }
 
   // load this group's members
   for (int e = 0; e < mine; ++e) {
@@ -1756,13 +1682,9 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   stats_zero(st);
   const int span = WPM * 32;
   const int cpl = (C + span - 1) / span;
-  // operator uses a lane counts per generation: 3 per candidate it holds; in
-  // the two-phase evaluation a lane holds up to two candidates (one of one
-  // step, one of up to three)
-  const uint64_t uses = qgrp ? 4ull : 3ull * (uint64_t)cpl;
-  const bool packed = 32ull * uses * (uint64_t)I.U * (uint64_t)mine < 65536ull;
+  const bool packed = 96ull * (uint64_t)cpl * (uint64_t)I.U * (uint64_t)mine < 65536ull;
   // a member's window counts in bytes while it evolves (PackedStats)
-  const bool bytec = uses * (uint64_t)I.U <= 255ull;
+  const bool bytec = 3ull * (uint64_t)cpl * (uint64_t)I.U <= 255ull;
   PackedStats ps{0u, 0u, 0u, 0u, 0u, 0u};
   auto count = [&](uint32_t rec) {
     if (bytec) packed_add<NO>(ps, rec);
@@ -1813,75 +1735,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         CandMoves cbest;
         // a later slot's counts wait for its generation to be decided (lanes
         // without a candidate hold the empty record)
-        uint32_t held = kNoRecord, held2 = kNoRecord;
+        uint32_t held = kNoRecord;
         bool done = false;
-        if constexpr (MODEL == TSP) {
-          if (qgrp) {
-            // phase A: step 0 of this lane's candidate; those of k >= 2
-            // steps join the slot's queue
-            unsigned char *qs = qgrp + (int64_t)(gslot * 2 + (int)gpar) * qslot;
-            int *qcnt = (int *)qs, *qe = (int *)(qs + 16);
-            const int c = gwi * 32 + lane;
-            const bool has = gm < wend && c < C;
-            TspA a;
-            a.k = 0;
-            if (has) a = tsp_phase_a<T16>(X, sol, W, (uint32_t)c, p, gm);
-            const bool multi = has && a.k >= 2;
-            if (has && !multi) {
-              const uint32_t r1 = stats_record(a.op0, -1, -1, 1, a.d0 < 0);
-              if (gslot == 0) count(r1);
-              else held = r1;
-              if (a.d0 < bd || (a.d0 == bd && c < bc)) {
-                bd = a.d0;
-                bc = c;
-                cbest.m[0] = a.m0;
-                cbest.k = 1;
-              }
-            }
-            const uint32_t mb = __ballot_sync(kFull, multi);
-            int base = 0;
-            if (lane == 0 && mb) base = atomicAdd(qcnt, __popc(mb));
-            base = __shfl_sync(kFull, base, 0);
-            if (multi) {
-              int *e = qe + (base + __popc(mb & ((1u << lane) - 1u))) * kQInts;
-              e[0] = c | (a.k << 16) | (a.op0 << 20) | (a.m0.rev << 24);
-              e[1] = a.m0.b1 | (a.m0.b2 << 16);
-              e[2] = a.m0.b3 | (a.m0.b4 << 16);
-              e[3] = (int)(uint32_t)(unsigned long long)a.d0;
-              if constexpr (!T16) e[4] = (int)(uint32_t)((unsigned long long)a.d0 >> 32);
-            }
-            G.sync();
-            // phase B: the queued candidates, 32 per warp in order, on as few
-            // warps of the slot as their number needs
-            const int nq = *(volatile int *)qcnt;
-            if (gwi * 32 < nq) {
-              const int j = gwi * 32 + lane;
-              const bool act = j < nq;
-              const int *e = qe + (act ? j : 0) * kQInts;
-              const int e0 = e[0];
-              const int c2 = e0 & 0xFFFF, k2 = (e0 >> 16) & 0xF, o0 = (e0 >> 20) & 0xF;
-              CandMoves cm2;
-              cm2.m[0] = PMove{e[1] & 0xFFFF, (int)((uint32_t)e[1] >> 16), e[2] & 0xFFFF,
-                               (int)((uint32_t)e[2] >> 16), (e0 >> 24) & 1};
-              long long d0 = (long long)e[3];
-              if constexpr (!T16)
-                d0 = (long long)(((unsigned long long)(uint32_t)e[4] << 32) | (uint32_t)e[3]);
-              int o1, o2;
-              const long long d2 = d0 + tsp_phase_b<T16>(X, sol, W, (uint32_t)c2, p, gm, k2, cm2, o1, o2);
-              if (act) {
-                const uint32_t r2 = stats_record(o0, o1, k2 >= 3 ? o2 : -1, k2, d2 < 0);
-                if (gslot == 0) count(r2);
-                else held2 = r2;
-                if (d2 < bd || (d2 == bd && c2 < bc)) {
-                  bd = d2;
-                  bc = c2;
-                  cbest = cm2;
-                }
-              }
-            }
-            done = true;
-          }
-        }
         if constexpr (MODEL == CVRPTW && NS == 1) {
           if (gm < wend && cpl > 1 && cpl <= 8) {
             // one-step candidates in place; the multi-step ones (a fifth or
@@ -1978,9 +1833,6 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         }
         G.sync();
         gpar ^= 1u;
-        // the queues of the step just evaluated are read: clear their counters
-        // (the next use of that parity is two steps on, past another G.sync)
-        if (qgrp && G.tig < NS) *(int *)(qgrp + (int64_t)(G.tig * 2 + (int)(gpar ^ 1u)) * qslot) = 0;
         // every slot's minimum over its warps: all partials read at once
         // (one 16-byte load each), then a pairwise tree
         long long ds[NS];
@@ -2023,10 +1875,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
           if (gs >= wend) break;
           const long long d = ds[s2];
           const int c = cs[s2], w = ws[s2];
-          if (s2 > 0 && gslot == s2) {
-            count(held);
-            count(held2);
-          }
+          if (s2 > 0 && gslot == s2) count(held);
           // the variate is drawn only when it can decide: a worsening move that
           // even the largest variate would reject is rejected without it
           bool acc = d <= 0;
@@ -2391,8 +2240,8 @@ __global__ void __launch_bounds__((WPM * NS > kMaxWarps ? WPM * NS : kMaxWarps) 
   const int groups = warps / (WPM * NS);
   const int p0 = blockIdx.x * groups;
   const int nsol = min(groups, I.P - p0);
-  Layout Lo = make_layout(staged ? I.shared_bytes : 0, I.len, I.m, groups, warps, WPM * NS, I.model);
-  if (tsp_queue_bytes(I.model, I.C, I.tri16, WPM, NS, groups) > 0) Lo.q_off = Lo.total;
+  const Layout Lo =
+      make_layout(staged ? I.shared_bytes : 0, I.len, I.m, groups, warps, WPM * NS, I.model);
   evolve_members<MODEL, T16, WPM, NS, XF>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
 }
 
@@ -2912,10 +2761,9 @@ int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged) {
 }
 
 int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, int ns, bool staged) {
-  const int groups = warps / (wpm * ns);
-  const Layout L = make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, groups, warps,
-                               wpm * ns, h.model);
-  return L.total + tsp_queue_bytes(h.model, h.C, h.tri16, wpm, ns, groups);
+  const Layout L = make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, warps / (wpm * ns),
+                               warps, wpm * ns, h.model);
+  return L.total;
 }
 
 #else   // CGO_XF_UNIT: the single-solve and batched kernels with migration and crossover
