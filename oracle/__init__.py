@@ -30,7 +30,8 @@ class OrcInstance(ctypes.Structure):
                 ("vec0", _i32p), ("vec1", _i32p), ("vec2", _i32p), ("vec3", _i32p),
                 ("capacity", ctypes.c_int64), ("lb", ctypes.c_int32), ("ub", ctypes.c_int32),
                 ("penalty0", ctypes.c_int64), ("penalty1", ctypes.c_int64),
-                ("tag", ctypes.c_uint32), ("weight0", ctypes.c_int64), ("weight1", ctypes.c_int64)]
+                ("tag", ctypes.c_uint32), ("weight0", ctypes.c_int64), ("weight1", ctypes.c_int64),
+                ("weight2", ctypes.c_int64)]
 
 
 class OrcParams(ctypes.Structure):
@@ -149,6 +150,7 @@ class Instance:
         s.penalty1 = int(inst.get("penalty1", 0))
         s.weight0 = int(inst.get("weight_distance", 0))
         s.weight1 = int(inst.get("weight_vehicles", 0))
+        s.weight2 = int(inst.get("weight_longest", 0))
         s.tag = int(inst.get("tag", 0)) & 0xFFFFFFFF
         self.s = s
 

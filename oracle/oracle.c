@@ -188,7 +188,8 @@ static int64_t cost_gap(const orc_instance *in, const int32_t *x) {
  * ready); late += max(0, t - due); t += service; load += demand; back at the
  * depot t += d(last, 0), late += max(0, t - due_0).  A route with no customer
  * costs nothing.
- * cost = distance + lambda_cap * sum max(0, load - Q) + lambda_tw * late. */
+ * cost = distance + lambda_cap * sum max(0, load - Q) + lambda_tw * late,
+ * with the objective weights of [R30] and [R34] (longest route). */
 static int64_t cost_cvrptw(const orc_instance *in, const int32_t *x) {
   int32_t n = in->n, len = orc_solution_length(in), N = n + 1;
   const int32_t *d = in->mat0, *dem = in->vec0, *rdy = in->vec1, *due = in->vec2,
@@ -197,16 +198,20 @@ static int64_t cost_cvrptw(const orc_instance *in, const int32_t *x) {
   int64_t ltw = in->penalty1 > 0 ? in->penalty1 : 100;
   /* [R30] weighted objectives (Sec. 6.8): distance and vehicles used */
   int64_t wd = in->weight0 > 0 ? in->weight0 : 1, wv = in->weight1;
+  /* [R34] the third objective of Sec. 6.8's tri-objective VRP: the longest
+   * route, as the largest distance driven by one vehicle */
+  int64_t wl = in->weight2, longest = 0;
   int64_t dist = 0, capx = 0, late = 0, used = 0;
   int32_t k = 0;
   while (k <= len) {
     /* one route: symbols until a separator or the end */
-    int64_t t = 0, load = 0;
+    int64_t t = 0, load = 0, rd = 0;
     int32_t prev = 0;
     while (k < len && x[k] < n) {
       int32_t c = x[k] + 1;
       int64_t dd = d[(int64_t)prev * N + c];
       dist += dd;
+      rd += dd;
       t = t + dd > rdy[c] ? t + dd : rdy[c];
       late += over(t - due[c]);
       t += svc[c];
@@ -217,6 +222,8 @@ static int64_t cost_cvrptw(const orc_instance *in, const int32_t *x) {
     if (prev != 0) { /* a route that visits no customer costs nothing */
       int64_t back = d[(int64_t)prev * N + 0];
       dist += back;
+      rd += back;
+      if (rd > longest) longest = rd;
       t += back;
       late += over(t - due[0]);
       capx += over(load - in->capacity);
@@ -224,7 +231,7 @@ static int64_t cost_cvrptw(const orc_instance *in, const int32_t *x) {
     }
     k++; /* skip the separator (or step past the end) */
   }
-  return wd * dist + lcap * capx + ltw * late + wv * used;
+  return wd * dist + lcap * capx + ltw * late + wv * used + wl * longest;
 }
 
 int64_t orc_cost(const orc_instance *in, const int32_t *sol) {

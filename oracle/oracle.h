@@ -50,6 +50,7 @@ typedef struct {
   int64_t penalty0, penalty1; /* 0 = default lambda */
   uint32_t tag;       /* instance tag (Philox counter word 1) */
   int64_t weight0, weight1; /* CVRPTW objective weights: distance (0 = 1), vehicles used */
+  int64_t weight2;          /* CVRPTW: weight of the longest route's distance [R34] (0 = off) */
 } orc_instance;
 
 typedef struct {

@@ -74,9 +74,10 @@ def bf_gap(c, r, cap, lam):
     return best
 
 
-def bf_cvrptw(inst, wd=1, wv=0):
-    """Brute-force optimum of the separator encoding; wd, wv weigh distance
-    and the vehicles used (routes that visit a customer)."""
+def bf_cvrptw(inst, wd=1, wv=0, wl=0):
+    """Brute-force optimum of the separator encoding; wd, wv, wl weigh
+    distance, the vehicles used (routes that visit a customer) and the
+    longest route's distance."""
     n, V = inst["n"], inst["vehicles"]
     d, dem, rdy, due, svc = (inst[k] for k in ("mat0", "vec0", "vec1", "vec2", "vec3"))
     Q = inst["capacity"]
@@ -90,24 +91,27 @@ def bf_cvrptw(inst, wd=1, wv=0):
             else:
                 cur.append(s + 1)
         routes.append(cur)
-        dist = excess = late = used = 0
+        dist = excess = late = used = longest = 0
         for rt in routes:
             if not rt:
                 continue
             used += 1
-            t, load, prev = 0, 0, 0
+            t, load, prev, rd = 0, 0, 0, 0
             for c in rt:
                 dist += int(d[prev][c])
+                rd += int(d[prev][c])
                 t = max(t + int(d[prev][c]), int(rdy[c]))
                 late += max(0, t - int(due[c]))
                 t += int(svc[c])
                 load += int(dem[c])
                 prev = c
             dist += int(d[prev][0])
+            rd += int(d[prev][0])
+            longest = max(longest, rd)
             t += int(d[prev][0])
             late += max(0, t - int(due[0]))
             excess += max(0, load - Q)
-        cost = wd * dist + 100 * excess + 100 * late + wv * used
+        cost = wd * dist + 100 * excess + 100 * late + wv * used + wl * longest
         best = cost if best is None else min(best, cost)
     return best
 
@@ -185,6 +189,22 @@ def test_cvrptw_weighted_objectives_reach_bruteforce_optimum(seed, wd, wv):
     inst = dict(I.cvrptw(5, 104, vehicles=3, capacity=60, box=60, horizon=300, width=80),
                 weight_distance=wd, weight_vehicles=wv)
     opt = bf_cvrptw(inst, wd, wv)
+    p = O.default_params(inst)
+    p.update(P=8, C=32)
+    st = _run(inst, p, seed, 400)
+    assert st["best_cost"].min() == opt
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+@pytest.mark.parametrize("wd,wv,wl", [(1, 0, 3), (1, 10 ** 4, 2), (0, 0, 1)])
+def test_cvrptw_longest_route_reaches_bruteforce_optimum(seed, wd, wv, wl):
+    """The tri-objective VRP of Sec. 6.8 (distance, vehicles, longest route)
+    as weights: the longest route's distance enters the cost with weight wl;
+    the search reaches the brute-force optimum of the weighted cost (wd = 0
+    takes the default distance weight 1)."""
+    inst = dict(I.cvrptw(5, 104, vehicles=3, capacity=60, box=60, horizon=300, width=80),
+                weight_distance=wd, weight_vehicles=wv, weight_longest=wl)
+    opt = bf_cvrptw(inst, wd or 1, wv, wl)
     p = O.default_params(inst)
     p.update(P=8, C=32)
     st = _run(inst, p, seed, 400)
