@@ -126,7 +126,16 @@ typedef struct {
      cost = weight_distance * distance + penalties + weight_vehicles * routes
      that visit a customer.  0 = default (1 and 0); other models ignore them. */
   int64_t weight_distance, weight_vehicles;
+  /* --- appended --- */
+  /* CVRPTW: weight of the longest route's distance (the third objective of
+     Sec. 6.8's tri-objective VRP; 0 = off): cost += weight_longest * the
+     largest distance driven by one vehicle */
+  int64_t weight_longest;
 } cgo_problem_desc;
+
+/* The size of cgo_problem_desc before weight_longest was appended (accepted
+ * by the calls that take a description: no longest-route term). */
+#define CGO_DESC_SIZE_V1 ((uint32_t)offsetof(cgo_problem_desc, weight_longest))
 
 /* Search parameters.  Fixed point: Q16 weights (65536 = 1.0), Q32.32
  * temperature, Q0.32 cooling factor. */

@@ -42,7 +42,8 @@ class cgo_problem_desc(ctypes.Structure):
                 ("m", ctypes.c_int32), ("vehicles", ctypes.c_int32),
                 ("penalty0", ctypes.c_int64), ("penalty1", ctypes.c_int64),
                 ("pointers_on_device", ctypes.c_int32), ("instance_tag", ctypes.c_uint32),
-                ("weight_distance", ctypes.c_int64), ("weight_vehicles", ctypes.c_int64)]
+                ("weight_distance", ctypes.c_int64), ("weight_vehicles", ctypes.c_int64),
+                ("weight_longest", ctypes.c_int64)]
 
 
 class cgo_params(ctypes.Structure):
@@ -255,6 +256,7 @@ class Problem:
         d.penalty1 = int(inst.get("penalty1", 0))
         d.weight_distance = int(inst.get("weight_distance", 0))
         d.weight_vehicles = int(inst.get("weight_vehicles", 0))
+        d.weight_longest = int(inst.get("weight_longest", 0))
         d.pointers_on_device = 1 if on_device else 0
         d.instance_tag = int(inst.get("tag", 0)) & 0xFFFFFFFF
         h = ctypes.c_void_p()

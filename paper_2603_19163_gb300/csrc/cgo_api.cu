@@ -356,6 +356,7 @@ KInst base_kinst(const cgo_problem *p) {
   h.lam1 = p->lam1;
   h.wdist = p->wdist;
   h.wveh = p->wveh;
+  h.wlong = p->wlong;
   h.lb = p->lb;
   h.ub = p->ub;
   h.tag = p->tag;
@@ -627,8 +628,12 @@ cgo_status cgo_kernel_launches(uint64_t *out) {
 cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
   if (!out) return fail(CGO_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (!d || d->struct_size != sizeof(cgo_problem_desc))
+  cgo_problem_desc dd;
+  if (!d || (d->struct_size != sizeof(cgo_problem_desc) && d->struct_size != CGO_DESC_SIZE_V1))
     return fail(CGO_ERR_INVALID, "desc: struct_size must be sizeof(cgo_problem_desc)");
+  memset(&dd, 0, sizeof dd);
+  memcpy(&dd, d, d->struct_size);  // an earlier description has no longest-route weight
+  d = &dd;
   if (d->model < CGO_TSP || d->model > CGO_CVRPTW) return fail(CGO_ERR_INVALID, "unknown model");
   if (d->encoding != encoding_of(d->model))
     return fail(CGO_ERR_INVALID, "encoding %d does not match model %d", d->encoding, d->model);
@@ -724,15 +729,17 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
       if (d->penalty0 < 0 || d->penalty1 < 0) return bail(fail(CGO_ERR_INVALID, "penalties < 0"));
       p->lam0 = d->penalty0 > 0 ? d->penalty0 : 100;
       p->lam1 = d->penalty1 > 0 ? d->penalty1 : 100;
-      if (d->weight_distance < 0 || d->weight_vehicles < 0)
+      if (d->weight_distance < 0 || d->weight_vehicles < 0 || d->weight_longest < 0)
         return bail(fail(CGO_ERR_INVALID, "objective weights < 0"));
       p->wdist = d->weight_distance > 0 ? d->weight_distance : 1;
       p->wveh = d->weight_vehicles;
+      p->wlong = d->weight_longest;
       // bound every route quantity: time, lateness, distance, load
       const double maxd = (double)absmax(a), tmax = (double)absmax(v[1]) + (double)N * (maxd + (double)absmax(v[3]));
       const double late = (double)N * (tmax + (double)absmax(v[2]));
       if ((double)p->lam1 * late + (double)p->lam0 * ((double)abssum(v[0]) + std::fabs((double)d->capacity) * N) +
-              (double)p->wdist * (double)(len + 1) * maxd + (double)p->wveh * (double)d->vehicles > kLimit)
+              (double)(p->wdist + p->wlong) * (double)(len + 1) * maxd + (double)p->wveh * (double)d->vehicles >
+          kLimit)
         return bail(fail(CGO_ERR_INVALID, "CVRPTW data could overflow an int64 cost"));
       // route quantities (time, lateness, distance, load) fit in int32?
       p->cv32 = (late < 2.0e9 && (double)abssum(v[0]) < 2.0e9 && (double)N * maxd < 2.0e9) ? 1 : 0;
@@ -1283,8 +1290,12 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_in, 
 
 cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint64_t seed,
                             int32_t *out_best_sol, int64_t *out_best_cost, void *stream) {
-  if (!d || d->struct_size != sizeof(cgo_problem_desc))
+  cgo_problem_desc dd;
+  if (!d || (d->struct_size != sizeof(cgo_problem_desc) && d->struct_size != CGO_DESC_SIZE_V1))
     return fail(CGO_ERR_INVALID, "desc: struct_size must be sizeof(cgo_problem_desc)");
+  memset(&dd, 0, sizeof dd);
+  memcpy(&dd, d, d->struct_size);  // an earlier description has no longest-route weight
+  d = &dd;
   if (d->model != CGO_TSP || d->encoding != CGO_ENC_PERM)
     return fail(CGO_ERR_UNSUPPORTED, "the allocation-free solve supports TSP only");
   if (!d->pointers_on_device || !d->mat0)

@@ -15,6 +15,7 @@ struct cgo_problem {
   int model = 0, n = 0, len = 0, m = 0, V = 0;
   int64_t capacity = 0, lam0 = 0, lam1 = 0;
   int64_t wdist = 1, wveh = 0;  // CVRPTW objective weights
+  int64_t wlong = 0;            // CVRPTW: weight of the longest route
   int lb = 0, ub = 0;
   uint32_t tag = 0;
   int32_t *d_mat0 = nullptr, *d_mat1 = nullptr, *d_vec[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -57,6 +57,7 @@ struct KInst {
   int32_t model, n, len, m;
   int64_t capacity, lam0, lam1;
   int64_t wdist, wveh;  // CVRPTW objective weights (distance, vehicles used)
+  int64_t wlong;        // CVRPTW: weight of the longest route's distance (0 = off)
   int32_t lb, ub;
   uint32_t tag;
   int32_t tri16;              // TSP triangle stored as int16

@@ -67,16 +67,19 @@ __host__ __device__ inline int64_t group_bytes(int nw) { return 2 * nw * 16 + 16
 // the next / previous separator of every position (len + 1, len int32) and
 // the separators' positions in order with the lowest-index empty route
 // (len + 1 int32)
-__host__ __device__ inline int64_t cv_aux_bytes(int len) {
+// (+ with the longest-route objective: prefix and suffix maxima of the route
+// distances, len + 2 int64 each)
+__host__ __device__ inline int64_t cv_aux_bytes(int len, bool cvmax = false) {
   return align16(8 * (int64_t)(len + 2) + 4 * (int64_t)(len + 1) + 4 * (int64_t)len +
-                 4 * (int64_t)(len + 1));
+                 4 * (int64_t)(len + 1)) +
+         (cvmax ? align16(16 * (int64_t)(len + 2)) : 0);
 }
 
 // Shared memory of one CTA: [instance data][members' solutions][one scratch
 // array per member group][member scalars][GAP loads][CVRPTW route caches]
 // [per-group partials]
 __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m, int nsol,
-                                              int warps, int wpm, int model) {
+                                              int warps, int wpm, int model, bool cvmax = false) {
   Layout L;
   const int groups = warps / wpm;
   L.inst = align16(inst_bytes);
@@ -87,7 +90,7 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   L.scal_off = L.scr_off + (perm ? (int64_t)groups * L.sol_stride : 0);
   L.load_off = L.scal_off + align16((int64_t)nsol * 32);
   L.aux_off = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
-  L.aux_stride = model == CVRPTW ? cv_aux_bytes(len) : 0;
+  L.aux_stride = model == CVRPTW ? cv_aux_bytes(len, cvmax) : 0;
   L.part_off = L.aux_off + (int64_t)nsol * L.aux_stride;
   L.total = L.part_off + (int64_t)groups * group_bytes(wpm);
   return L;
@@ -110,7 +113,7 @@ int64_t instance_data_bytes(const KInst &h) {
 
 int64_t smem_instance(const KInst &h) { return instance_data_bytes(h); }
 int64_t smem_per_warp(const KInst &h) {
-  Layout a = make_layout(0, h.len, h.m, 1, 1, 1, h.model);
+  Layout a = make_layout(0, h.len, h.m, 1, 1, 1, h.model, h.wlong > 0);
   return a.total;
 }
 #endif
@@ -131,6 +134,7 @@ struct View {
   const int4 *node;                           // CVRPTW: {ready, due, service, demand}
   long long lam1;
   long long wd, wv;  // CVRPTW objective weights (distance, vehicles used)
+  long long wl;      // CVRPTW: weight of the longest route's distance
   bool cv32;
   bool t3;   // 3-opt enabled for this instance
   bool seg;  // seg_flip / seg_reset enabled for this instance
@@ -389,7 +393,7 @@ struct Jumps {
 
 template <class Look, class Q>
 __device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int L, int R,
-                                                     Jumps J = Jumps()) {
+                                                     Jumps J = Jumps(), long long *mx = nullptr) {
   const int n = X.n, N = n + 1;
   long long total = 0;
   Q t = 0, load = 0, dist = 0, late = 0;
@@ -409,9 +413,11 @@ __device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int 
     t += sep ? (Q)0 : (Q)nd.z;
     load += sep ? (Q)0 : (Q)nd.w;
     if (sep) {
-      if (prev != 0)
+      if (prev != 0) {
         total += X.wd * (long long)dist + X.lam0 * overp((long long)load - X.cap) +
                  X.lam1 * (long long)late + X.wv;
+        if (mx) *mx = max(*mx, (long long)dist);
+      }
       t = load = dist = late = 0;
       prev = 0;
       if (q == J.f0) {
@@ -431,9 +437,9 @@ __device__ __forceinline__ long long cvrptw_routes_t(const View &X, Look V, int 
 
 template <class Look>
 __device__ __forceinline__ long long cvrptw_routes(const View &X, Look V, int L, int R, bool q32,
-                                                   Jumps J = Jumps()) {
-  return q32 ? cvrptw_routes_t<Look, int>(X, V, L, R, J)
-             : cvrptw_routes_t<Look, long long>(X, V, L, R, J);
+                                                   Jumps J = Jumps(), long long *mx = nullptr) {
+  return q32 ? cvrptw_routes_t<Look, int>(X, V, L, R, J, mx)
+             : cvrptw_routes_t<Look, long long>(X, V, L, R, J, mx);
 }
 
 // Route cache of one member's (actual) sequence: cum[q] = cost of the routes
@@ -442,17 +448,26 @@ __device__ __forceinline__ long long cvrptw_routes(const View &X, Look V, int L,
 // prv[q] = last separator at or before q (-1 if none); sep[r] = position of
 // the r-th separator (r < V - 1) and sep[len] = the lowest-index empty route
 // (-1 if none).
+// With the longest-route objective also pmx[q] = the largest distance of a
+// route that ends (at its terminator) before q and smx[q] = that of a route
+// that starts at or after q (q = 0 .. len + 1; 0 where there is none).
 struct CvAux {
   long long *cum;
   int *nxt, *prv, *sep;
+  long long *pmx, *smx;
 };
 
-__device__ __forceinline__ CvAux cv_aux_at(unsigned char *p, int len) {
+__device__ __forceinline__ CvAux cv_aux_at(unsigned char *p, int len, bool cvmax = false) {
   CvAux a;
   a.cum = (long long *)p;
   a.nxt = (int *)(p + 8 * (int64_t)(len + 2));
   a.prv = a.nxt + (len + 1);
   a.sep = a.prv + len;
+  a.pmx = a.smx = nullptr;
+  if (cvmax) {
+    a.pmx = (long long *)(p + cv_aux_bytes(len));
+    a.smx = a.pmx + (len + 2);
+  }
   return a;
 }
 
@@ -511,14 +526,56 @@ __device__ void cv_build(const View &X, const El *sol, const CvAux &a, const G_t
     zmin = __reduce_min_sync(kFull, zmin);
     if (lane == 0) a.sep[m] = zmin == INT_MAX ? -1 : zmin;
     __syncwarp();
-    // each non-empty route's cost, stored one past its terminator
+    if (a.pmx)
+      for (int q = lane; q <= m + 1; q += 32) a.pmx[q] = a.smx[q] = 0;
+    __syncwarp();
+    // each non-empty route's cost, stored one past its terminator (and its
+    // distance at the same place and at its start, for the maxima)
     for (int q = lane; q < m; q += 32) {
       if ((q == 0 || (int)sol[q - 1] >= n) && (int)sol[q] < n) {
         const int s = a.nxt[q];
-        a.cum[s + 1] = cvrptw_routes(X, [&](int r) { return (int)sol[r]; }, q, s, X.cv32);
+        long long rd = 0;
+        a.cum[s + 1] = cvrptw_routes(X, [&](int r) { return (int)sol[r]; }, q, s, X.cv32, Jumps(),
+                                     a.pmx ? &rd : nullptr);
+        if (a.pmx) {
+          a.pmx[s + 1] = rd;
+          a.smx[q] = rd;
+        }
       }
     }
     __syncwarp();
+    if (a.pmx) {
+      // prefix maxima over pmx, suffix maxima over smx
+      long long c1 = 0;
+      for (int base = 0; base <= m + 1; base += 32) {
+        const int q = base + lane;
+        long long v = q <= m + 1 ? a.pmx[q] : 0ll;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const long long u = __shfl_up_sync(kFull, v, off);
+          if (lane >= off) v = max(v, u);
+        }
+        v = max(v, c1);
+        __syncwarp();
+        if (q <= m + 1) a.pmx[q] = v;
+        c1 = __shfl_sync(kFull, v, 31);
+      }
+      long long c2s = 0;
+      for (int top = m + 1; top >= 0; top -= 32) {
+        const int q = top - lane;
+        long long v = q >= 0 ? a.smx[q] : 0ll;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const long long u = __shfl_up_sync(kFull, v, off);
+          if (lane >= off) v = max(v, u);
+        }
+        v = max(v, c2s);
+        __syncwarp();
+        if (q >= 0) a.smx[q] = v;
+        c2s = __shfl_sync(kFull, v, 31);
+      }
+      __syncwarp();
+    }
     long long c2 = 0;
     for (int base = 0; base <= m + 1; base += 32) {
       const int q = base + lane;
@@ -547,6 +604,14 @@ __device__ long long cvrptw_step0(const View &X, const PermEl *sol, const PMove 
   const int L = b1 > 0 ? a.prv[b1 - 1] + 1 : 0;
   const int R = a.nxt[b4];
   long long old = a.cum[R + 1] - a.cum[L];
+  if (X.wl > 0) {
+    // the longest route: the routes outside [L, R] keep their distances
+    // (prefix / suffix maxima); the new ones over [L, R] are walked whole
+    long long mx = max(a.pmx[L], a.smx[R + 1]);
+    auto Vn = [&](int q) { return (int)sol[perm_inv(mv, q)]; };
+    const long long nw = cvrptw_routes(X, Vn, L, R, X.cv32, Jumps(), &mx);
+    return nw - old + X.wl * (mx - a.pmx[X.len + 1]);
+  }
   Jumps J;
   if (!mv.rev) {
     const int lb = b4 - b3, lm = b3 - b2;
@@ -780,6 +845,11 @@ __device__ long long cvrptw_composite(const View &X, const PermEl *sol, const Ca
     q = perm_inv(cm.m[1], q);
     return (int)sol[perm_inv(cm.m[0], q)];
   };
+  if (X.wl > 0) {
+    long long mx = max(a.pmx[L], a.smx[R + 1]);
+    const long long nw = cvrptw_routes(X, Vf, L, R, X.cv32, Jumps(), &mx);
+    return nw - old + X.wl * (mx - a.pmx[X.len + 1]);
+  }
   return cvrptw_routes(X, Vf, L, R, X.cv32) - old;
 }
 
@@ -1366,7 +1436,7 @@ __device__ __noinline__ int window_migrate(const KInst &I, const View X, unsigne
     G.sync();
     aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
     if constexpr (MODEL == CVRPTW)
-      cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len), G);
+      cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, X.wl > 0), G);
   }
   if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
     return -1;
@@ -1563,7 +1633,7 @@ __device__ __noinline__ int window_cross(const KInst &I, const View X, unsigned 
       G.sync();
       aux_init(MODEL, X, A, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
       if constexpr (MODEL == CVRPTW)
-        cv_build(X, A, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len), G);
+        cv_build(X, A, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, X.wl > 0), G);
     }
   }
   if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
@@ -1641,7 +1711,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     G.sync();
     aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
     if constexpr (MODEL == CVRPTW)
-      cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len), G);
+      cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, X.wl > 0), G);
   }
 
   // instance-wide scalars (identical in every warp)
@@ -1709,7 +1779,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       const uint32_t p = (uint32_t)(p0 + ls);
       El *sol = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
       long long *loads = (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m;
-      const CvAux cva = cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len);
+      const CvAux cva = cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, X.wl > 0);
       SolScal sc = scal[ls];
       T = Tw;
       if (mine > 1) eblk = -1;
@@ -2058,7 +2128,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         G.sync();
         aux_init(MODEL, X, sol, &scal[lw], (long long *)(smem + Lo.load_off) + (int64_t)lw * X.m, G);
         if constexpr (MODEL == CVRPTW)
-          cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)lw * Lo.aux_stride, len), G);
+          cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)lw * Lo.aux_stride, len, X.wl > 0), G);
       }
       if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
         return;
@@ -2169,6 +2239,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.lam1 = I.lam1;
   X.wd = I.wdist;
   X.wv = I.wveh;
+  X.wl = I.wlong;
   if (!staged) return X;
   auto copy = [&](const void *src, int64_t bytes, int64_t off) {
     const int4 *s = (const int4 *)src;
@@ -2240,8 +2311,8 @@ __global__ void __launch_bounds__((WPM * NS > kMaxWarps ? WPM * NS : kMaxWarps) 
   const int groups = warps / (WPM * NS);
   const int p0 = blockIdx.x * groups;
   const int nsol = min(groups, I.P - p0);
-  const Layout Lo =
-      make_layout(staged ? I.shared_bytes : 0, I.len, I.m, groups, warps, WPM * NS, I.model);
+  const Layout Lo = make_layout(staged ? I.shared_bytes : 0, I.len, I.m, groups, warps, WPM * NS,
+                                I.model, I.wlong > 0);
   evolve_members<MODEL, T16, WPM, NS, XF>(I, X, smem, Lo, p0, nsol, warps, timeout_ns);
 }
 
@@ -2286,7 +2357,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
       __syncthreads();
       const int groups = warps / WPM;
       const Layout Lo =
-          make_layout(staged ? I.shared_bytes : 0, I.len, I.m, I.P, warps, WPM, I.model);
+          make_layout(staged ? I.shared_bytes : 0, I.len, I.m, I.P, warps, WPM, I.model, I.wlong > 0);
       evolve_members<MODEL, T16, WPM, 1, XF>(I, X, smem, Lo, 0, I.P, warps, timeout_ns);
       (void)groups;
     }
@@ -2329,7 +2400,10 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
       X.wv = I.wveh;
       X.rd = I.mat0;
       X.node = I.node;
-      return cvrptw_routes(X, [&](int q) { return (int)x[q]; }, 0, I.len, false);
+      long long mx = 0;
+      const long long c = cvrptw_routes(X, [&](int q) { return (int)x[q]; }, 0, I.len, false, Jumps(),
+                                        I.wlong > 0 ? &mx : nullptr);
+      return c + I.wlong * mx;
     }
     case GAP: {
       for (int j = 0; j < n; ++j) s += I.mat0[(size_t)x[j] * n + j];
@@ -2756,13 +2830,13 @@ cudaError_t launch_batch(int model, int tri16, int xf, const KInst *d_insts, con
 // shared memory of a batched unit: all P members of an instance in one CTA
 int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged) {
   const Layout L =
-      make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, h.P, warps, wpm, h.model);
+      make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, h.P, warps, wpm, h.model, h.wlong > 0);
   return L.total;
 }
 
 int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, int ns, bool staged) {
   const Layout L = make_layout(staged ? instance_data_bytes(h) : 0, h.len, h.m, warps / (wpm * ns),
-                               warps, wpm * ns, h.model);
+                               warps, wpm * ns, h.model, h.wlong > 0);
   return L.total;
 }
 

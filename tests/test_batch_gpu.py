@@ -74,6 +74,9 @@ def mixed_batch():
                   dict(P=6, C=64, G=26, U=4, ops=[O.SWAP, O.TWO_OPT, O.INSERT] + [O.ROW_SWAP_OP, O.ROW_MERGE_OP, O.ROW_SPLIT_OP])))
     items.append((dict(I.cvrptw(12, 266, vehicles=7, capacity=60), tag=56),
                   dict(P=5, C=48, G=21, ops=[O.ROW_SWAP_OP, O.ROW_MERGE_OP, O.ROW_SPLIT_OP], w_k=[20000, 30000, 15536])))
+    # the longest route as a third objective
+    items.append((dict(I.cvrptw(16, 267, vehicles=5, capacity=80), tag=57, weight_longest=4),
+                  dict(P=6, C=48, G=23, U=4)))
     # weighted CVRPTW objectives (vehicles first)
     items.append((dict(I.cvrptw(18, 264, vehicles=5, capacity=90), tag=54, weight_vehicles=10 ** 6),
                   dict(P=6, C=48, G=22)))

@@ -605,6 +605,47 @@ def test_cvrptw_row_operators_sizes(cgo, n, V):
         assert_same_state(g, o, "n %d V %d C %d ns %d" % (n, V, C, ns))
 
 
+@pytest.mark.parametrize("ns", [1, 2])
+@pytest.mark.parametrize("wd,wv,wl", [(1, 0, 3), (2, 500, 1), (1, 0, 40)])
+def test_cvrptw_longest_route(cgo, ns, wd, wv, wl):
+    """The longest route (Sec. 6.8's third objective) as a weighted term:
+    its delta takes the routes outside the changed span from prefix and
+    suffix maxima of the route cache and walks the changed span whole."""
+    inst = dict(I.cvrptw(25, 98, vehicles=6, capacity=90), weight_distance=wd, weight_vehicles=wv,
+                weight_longest=wl)
+    for ops in (None, [SW, TO, INS, OR, TH] + ROWS):
+        over = dict(P=6, C=64, G=31, U=5, T0=40 << 32)
+        if ops:
+            over["ops"] = ops
+        p = params_for(inst, **over)
+        prob, g, o = run_both(cgo, inst, p, 2, wpm=2, ns=ns)
+        assert_same_state(g, o, "wl %d ops %s ns %d" % (wl, ops, ns))
+
+
+def test_earlier_descriptor_size_is_accepted(cgo):
+    import ctypes
+    inst = I.cvrptw(12, 99, vehicles=3, capacity=80)
+    desc = cgo.cgo_problem_desc()
+    keep = []
+    for f in ("mat0", "vec0", "vec1", "vec2", "vec3"):
+        a = np.ascontiguousarray(np.asarray(inst[f], np.int32).reshape(-1))
+        keep.append(a)
+        setattr(desc, f, a.ctypes.data)
+    desc.struct_size = cgo.cgo_problem_desc.weight_longest.offset
+    desc.encoding, desc.model, desc.n = 0, 4, 12
+    desc.capacity, desc.vehicles = int(inst["capacity"]), 3
+    desc.weight_longest = 99                      # beyond the earlier size: ignored
+    h = ctypes.c_void_p()
+    cgo.check(cgo.lib().cgo_problem_create(ctypes.byref(desc), ctypes.byref(h)), "create")
+    q = cgo.params_struct(params_for(inst, P=4, C=32, G=11))
+    cgo.check(cgo.lib().cgo_solve(h, ctypes.byref(q), 3, None), "solve")
+    c = ctypes.c_int64()
+    cgo.check(cgo.lib().cgo_best(h, None, 0, ctypes.byref(c)), "best")
+    o = oracle_run(inst, params_for(inst, P=4, C=32, G=11), 3, 11)
+    assert c.value == int(o["best_cost"].min())
+    cgo.lib().cgo_problem_destroy(h)
+
+
 def test_earlier_struct_sizes_are_accepted(cgo):
     """cgo_params / cgo_state of the size before the row level was appended:
     solves run with the row operators off; a state without the row level is

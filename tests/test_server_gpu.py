@@ -51,6 +51,9 @@ def request_mix():
         # weighted CVRPTW objectives
         (dict(I.cvrptw(16, 313, vehicles=4, capacity=80), tag=14, weight_distance=2,
               weight_vehicles=300), dict(P=5, C=48, G=21)),
+        # the longest route as a third objective
+        (dict(I.cvrptw(15, 315, vehicles=5, capacity=80), tag=16, weight_longest=6),
+         dict(P=5, C=48, G=22)),
         # the row level (routes as rows) beside the permutation operators
         (dict(I.cvrptw(18, 314, vehicles=6, capacity=80), tag=15),
          dict(P=6, C=64, G=26, U=4, ops=[O.SWAP, O.INSERT, O.OR_OPT] + [O.ROW_SWAP_OP, O.ROW_MERGE_OP, O.ROW_SPLIT_OP])),
