@@ -198,10 +198,23 @@ def run_reference(args, rank, world):
         return
     import oracle as O
     inst, cfg, desc = workload(args.workload)
+    pops = None
     if inst is None:
-        # batched / served workloads: a stratified sample of the instance mix
-        insts = [dict(x, tag=i) for i, x in enumerate(I.batch_mix(512, 0))][::64]
+        # batched / served workloads: a stratified sample of the instance mix,
+        # with the populations the batched arm's autotuner gives the classes
+        mix = I.batch_mix(512, 0)
+        insts = [dict(x, tag=i) for i, x in enumerate(mix)][::64]
         desc += " (oracle on every 64th instance)"
+        if args.workload == "batch512" and args.batch_pop <= 0:
+            from paper_2603_19163_gb300.autotune import batch_populations
+            l2 = 126 << 20
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    l2 = int(getattr(torch.cuda.get_device_properties(0), "L2_cache_size", l2))
+            except ImportError:
+                pass
+            pops = batch_populations(mix, l2)[0]
     else:
         if args.cvrptw_weights and inst["model"] == I.CVRPTW:
             wd, wv = (int(x) for x in args.cvrptw_weights.split(","))
@@ -213,6 +226,8 @@ def run_reference(args, rank, world):
     for x in insts:
         p = O.default_params(x)
         p.update({k: v for k, v in cfg.items() if k not in ("G", "extra_mask")})
+        if pops is not None:
+            p["P"] = pops[int(x["model"])]
         p["op_mask"] |= cfg.get("extra_mask", 0)
         plist.append(p)
     gens = args.ref_generations
@@ -226,7 +241,7 @@ def run_reference(args, rank, world):
         for x, p in zip(insts, plist):
             O.solve(x, p, 1, gens)
         times.append(time.perf_counter() - t0)
-    evals = cfg["P"] * cfg["C"] * gens * len(insts)
+    evals = sum(p["P"] for p in plist) * cfg["C"] * gens
     value = evals * args.steps / sum(times)
     line = {"metric": "move_evals_per_s", "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -281,6 +296,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--batch-class", default="mix")
     ap.add_argument("--wpm", type=int, default=0, help="warps per member override (batched)")
+    ap.add_argument("--batch-pop", type=int, default=0,
+                    help="batched: one population for every class instead of the autotuner's")
     ap.add_argument("--slice", type=int, default=2000)
     ap.add_argument("--init-oversample", type=int, default=1,
                     help="single solve: K of the oversampled start (1 = plain start)")
@@ -426,7 +443,7 @@ def main():
         t_x = time.perf_counter()
         b = batch_run(args, cgo, torch, local, args.extra_steps, 1, 20000)
         extras["batched"] = {k: b[k] for k in (
-            "desc", "solves_per_s", "evals_per_s", "one_launch_per_solve_solves_per_s",
+            "desc", "population", "solves_per_s", "evals_per_s", "one_launch_per_solve_solves_per_s",
             "batched_over_one_launch_per_solve", "same_final_costs", "one_launch_per_solve_sample",
             "autotuner", "clocks", "gpu_launches", "steps", "total_ms")}
         sv = serve_run(args, cgo, torch, local, args.extra_serve_seconds, 20000,
@@ -493,10 +510,17 @@ def batch_run(args, cgo, torch, local, steps, warmup, G, rank=0, world=1, dist=N
             mix = [x for x in mix if x["model"] == cls]
         desc = desc.replace("batch512-mix", "batch-%s%d" % (args.batch_class, len(mix)))
     probs = [cgo.Problem(x) for x in mix]
+    # population per model class: fixed, or the autotuner's L2-aware rule
+    from paper_2603_19163_gb300.autotune import batch_populations
+    if args.batch_pop > 0:
+        pops, ws = {int(x["model"]): args.batch_pop for x in mix}, None
+    else:
+        l2 = int(getattr(torch.cuda.get_device_properties(local), "L2_cache_size", 126 << 20))
+        pops, ws = batch_populations(mix, l2)
     params = []
     for pr, x in zip(probs, mix):
         q = pr.default_params()
-        q.update(P=cfg["P"], C=cfg["C"], G=G)
+        q.update(P=pops[int(x["model"])], C=cfg["C"], G=G)
         q["op_mask"] |= extra_ops_mask(x["model"], args.extra_ops)
         q["cross_q16"] = args.cross
         params.append(q)
@@ -574,7 +598,12 @@ def batch_run(args, cgo, torch, local, steps, warmup, G, rank=0, world=1, dist=N
     d2h = sum(int(o[0].nbytes) + 8 for o in outs)
     for pp in p2 + probs:
         pp.close()
-    return {"desc": desc.replace("G=20000", "G=%d" % G), "value": value, "total_ms": total_ms,
+    pop_note = {"population_by_model": {str(m): v for m, v in pops.items()},
+                "rule": ("fixed (--batch-pop)" if ws is None else
+                         "L2-aware: largest per class whose batch working set fits L2 (%.1f MB)"
+                         % (ws / 2 ** 20))}
+    return {"desc": desc.replace("G=20000", "G=%d" % G).replace("P=32 ", ""), "value": value,
+            "total_ms": total_ms, "population": pop_note,
             "steps": steps, "evals_per_s": value, "solves_per_s": solves_s,
             "one_launch_per_solve_solves_per_s": seq_solves_s,
             "batched_over_one_launch_per_solve": solves_s / seq_solves_s,
@@ -601,6 +630,7 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
                            "same_final_costs": r["same_final_costs"],
                            "sequential_sample": r["one_launch_per_solve_sample"],
                            "best_cost_sum_by_model": r["best_cost_sum_by_model"],
+                           "population": r["population"],
                            "autotuner": r["autotuner"]},
                 "e2e": {"value": r["e2e_evals_per_s"], "unit": "evals/s",
                         "h2d_bytes_per_step": r["h2d_bytes"], "d2h_bytes_per_step": r["d2h_bytes"]},

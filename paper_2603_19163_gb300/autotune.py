@@ -6,11 +6,14 @@ the C ABI and keeps the fastest shape; choices are cached by a shape key.
 For serving it also picks the population per instance class: the largest
 population from a ladder whose predicted device load at the offered arrival
 rate stays under a utilisation target (the largest classes are halved first),
-using the batched throughput measured per class.
+using the batched throughput measured per class.  For a batch it picks the
+population per class by the L2-aware rule (batch_populations).
 """
 from __future__ import annotations
 
 import time
+
+import numpy as np
 
 from . import cgo as C
 
@@ -141,3 +144,50 @@ def population_for_load(class_rate: dict, share: dict, arrivals_per_s: float,
         if c is None:
             return P, load
         P[c] = ladder[ladder.index(P[c]) + 1]
+
+
+def instance_data_bytes(inst: dict) -> int:
+    """Device bytes of an instance's data as the library holds them (the
+    caller's arrays, plus the int16 or int32 upper triangle of a TSP)."""
+    b = sum(int(np.asarray(inst[k]).nbytes) for k in ("mat0", "mat1", "vec0", "vec1", "vec2", "vec3")
+            if inst.get(k) is not None)
+    if int(inst["model"]) == 0:
+        n = int(inst["n"])
+        b += n * (n + 1) // 2 * (2 if int(np.abs(np.asarray(inst["mat0"])).max()) < 32768 else 4)
+    return b
+
+
+def state_bytes(length: int, P: int) -> int:
+    """Device bytes of a population's search state: current and best
+    solutions (int32), current and best costs (int64)."""
+    return 2 * P * length * 4 + 16 * P
+
+
+def batch_populations(insts: list, l2_bytes: int, ladder=(64, 32, 16, 8)) -> tuple[dict, int]:
+    """Populations of a batch by model class, L2-aware (the paper's adaptive
+    population sizing, Sec. "Adaptive Population Sizing": the population is
+    cut to the largest size whose working set the L2 cache sustains, in
+    powers of two).  For a batch the working set is every instance's data
+    plus every population's state, all resident across the time slices:
+    start every class at the top of the ladder and, while the total exceeds
+    L2, halve the class whose populations hold the most state.  Returns
+    ({model: P}, working-set bytes)."""
+    data = sum(instance_data_bytes(x) for x in insts)
+    lens = {}
+    for x in insts:
+        n = int(x["n"])
+        ln = n + int(x.get("vehicles", 1)) - 1 if int(x["model"]) == 4 else n
+        lens.setdefault(int(x["model"]), []).append(ln)
+    P = {m: ladder[0] for m in lens}
+
+    def state_of(m):
+        return sum(state_bytes(ln, P[m]) for ln in lens[m])
+
+    while True:
+        total = data + sum(state_of(m) for m in P)
+        if total <= l2_bytes:
+            return P, total
+        m = max((m for m in P if P[m] > ladder[-1]), key=state_of, default=None)
+        if m is None:
+            return P, total
+        P[m] = ladder[ladder.index(P[m]) + 1]

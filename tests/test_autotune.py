@@ -31,3 +31,21 @@ def test_solve_shapes_cover_deep_generations_only_where_they_run():
     assert all(s[3] <= 2 or (s[1] == 4 and s[0] == 4 * s[3]) for s in shapes)
     assert all(s[3] <= 2 for s in t.solve_shapes(dict(C=128, cross_q16=100)))
     assert all(s[3] == 1 for s in t.solve_shapes(dict(C=300)))
+
+
+def test_batch_populations_fit_the_l2_working_set():
+    import instances as I
+    from paper_2603_19163_gb300.autotune import batch_populations, instance_data_bytes, state_bytes
+    mix = I.batch_mix(64, 0)
+    big, total = batch_populations(mix, 1 << 40)
+    assert set(big.values()) == {64} and total > 0            # everything fits: the top
+    small, total = batch_populations(mix, 1 << 20)
+    assert set(small.values()) == {8}                          # nothing fits: the bottom
+    data = sum(instance_data_bytes(x) for x in mix)
+    mid, total = batch_populations(mix, data + 3 * (total - data))
+    assert total <= data + 3 * (total - data)
+    # the class with the most state is cut first: knapsack (n up to 2000) before GAP
+    assert mid[2] <= mid[3]
+    # the working set adds every instance's state at its class's population
+    lens = [(int(x["model"]), int(x["n"])) for x in mix]
+    assert total == data + sum(state_bytes(n, mid[m]) for m, n in lens)
