@@ -294,6 +294,20 @@ cgo_status cgo_state_get(const cgo_problem *prob, cgo_state *out);
 cgo_status cgo_state_set(cgo_problem *prob, const cgo_params *params, uint64_t seed,
                          const cgo_state *state);
 
+/* The search state as one opaque, versioned byte buffer (a checkpoint
+ * file's contents): a header (magic "CGO1", format version, population,
+ * solution length, generation), the scalars of cgo_state including the row
+ * level, then the four arrays.  cgo_state_export writes it into buf (cap
+ * bytes; *used gets the size, which is also returned with
+ * CGO_ERR_INVALID when cap is too small or buf is NULL, so a first call can
+ * size the buffer).  cgo_state_import checks the header and resumes from
+ * it exactly as cgo_state_set would (CGO_ERR_INVALID for a foreign, older
+ * or truncated buffer, or one whose shape does not match the problem and
+ * params).  Host buffers; both calls synchronise. */
+cgo_status cgo_state_export(const cgo_problem *prob, void *buf, size_t cap, size_t *used);
+cgo_status cgo_state_import(cgo_problem *prob, const cgo_params *params, uint64_t seed,
+                            const void *buf, size_t len);
+
 /* Operator statistics of the search so far (Sec. 4.2.2 counts the uses of
  * every operator and how many improved, for the AOS update; this call sums
  * them over every generation since the last cgo_solve or cgo_state_set,
@@ -308,7 +322,8 @@ cgo_status cgo_op_counts(const cgo_problem *prob, uint64_t *out, int32_t cap);
 
 /* Batched solve: `count` independent problems (different models and sizes
  * allowed) advance together in persistent kernels; problem i uses
- * per_prob[i] and seeds[i].  Each result is bit-identical to cgo_solve of
+ * per_prob[i] and seeds[i].  The paper has no counterpart: it solves one
+ * problem per launch; this is the library's batching interface.  Each result is bit-identical to cgo_solve of
  * that problem alone.  All members of a problem share one CTA: its
  * solutions (and, for CVRPTW, route caches) must fit the shared memory of
  * one CTA beside the staged instance data, else CGO_ERR_UNSUPPORTED. */
@@ -356,7 +371,8 @@ cgo_status cgo_solve_static(const cgo_problem_desc *desc, const cgo_params *para
  * persistent batched kernels replayed from a CUDA graph, and requests that
  * arrive during a slice join at the next slice boundary.  Populations, AOS
  * state and generation counters stay in device memory across slices.  Each
- * result is bit-identical to cgo_solve of the same problem alone. */
+ * result is bit-identical to cgo_solve of the same problem alone.  The paper
+ * has no counterpart: this is the library's serving interface. */
 typedef struct cgo_server cgo_server;
 
 typedef struct {

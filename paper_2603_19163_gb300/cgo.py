@@ -123,6 +123,8 @@ def lib() -> ctypes.CDLL:
                 "cgo_solution_length": ([vp, _i32p], c.c_int),
                 "cgo_state_get": ([vp, P(cgo_state)], c.c_int),
                 "cgo_op_counts": ([vp, P(c.c_uint64), c.c_int32], c.c_int),
+                "cgo_state_export": ([vp, vp, c.c_size_t, P(c.c_size_t)], c.c_int),
+                "cgo_state_import": ([vp, P(cgo_params), c.c_uint64, vp, c.c_size_t], c.c_int),
                 "cgo_state_set": ([vp, P(cgo_params), c.c_uint64, P(cgo_state)], c.c_int),
                 "cgo_solve_batch": ([P(vp), P(cgo_params), P(c.c_uint64), c.c_int32, vp], c.c_int),
                 "cgo_last_error": ([], c.c_char_p),
@@ -331,6 +333,20 @@ class Problem:
                    u_op=list(s.u_op) + list(s.u_row), v_op=list(s.v_op) + list(s.v_row),
                    u_k=list(s.u_k), v_k=list(s.v_k))
         return arr
+
+    def export_state(self) -> bytes:
+        """The search state as a versioned byte buffer (cgo_state_export)."""
+        used = ctypes.c_size_t()
+        lib().cgo_state_export(self.h, None, 0, ctypes.byref(used))    # sizes the buffer
+        buf = ctypes.create_string_buffer(used.value)
+        check(lib().cgo_state_export(self.h, buf, used.value, ctypes.byref(used)), "cgo_state_export")
+        return buf.raw[:used.value]
+
+    def import_state(self, params: dict, seed: int, blob: bytes):
+        q = params_struct(params)
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        check(lib().cgo_state_import(self.h, ctypes.byref(q), int(seed), buf, len(blob)),
+              "cgo_state_import")
 
     def op_counts(self) -> dict:
         """Operator and k-level counts over every generation of the solve so far."""

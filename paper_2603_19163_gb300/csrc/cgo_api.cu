@@ -970,6 +970,113 @@ cgo_status cgo_best(const cgo_problem *p, int32_t *out_sol, int32_t cap, int64_t
   return CGO_OK;
 }
 
+// ------------------------------------------------ state as a byte buffer
+namespace {
+constexpr uint32_t kBlobMagic = 0x314F4743u;  // "CGO1"
+constexpr uint32_t kBlobVersion = 1;
+struct BlobHead {
+  uint32_t magic, version, population, length;
+  int64_t generation;
+  uint64_t T_q32;
+  uint32_t w_op[CGO_NOPS_ALL], w_k[3], stag, pad;
+  int64_t elite_prev;
+  uint32_t u_op[CGO_NOPS_ALL], v_op[CGO_NOPS_ALL], u_k[3], v_k[3];
+};
+size_t blob_bytes(int P, int len) { return sizeof(BlobHead) + (size_t)P * len * 8 + (size_t)P * 16; }
+}  // namespace
+
+cgo_status cgo_state_export(const cgo_problem *p, void *buf, size_t cap, size_t *used) {
+  if (!p || !used) return fail(CGO_ERR_INVALID, "NULL argument");
+  if (!p->has_state) return fail(CGO_ERR_STATE, "no search state");
+  const int P = p->params.population, len = p->len;
+  *used = blob_bytes(P, len);
+  if (!buf || cap < *used) return fail(CGO_ERR_INVALID, "buffer of %zu bytes; the state needs %zu", cap, *used);
+  unsigned char *b = (unsigned char *)buf;
+  BlobHead h;
+  memset(&h, 0, sizeof h);
+  cgo_state s;
+  memset(&s, 0, sizeof s);
+  s.struct_size = sizeof s;
+  s.cur = (int32_t *)(b + sizeof h);
+  s.best_sol = s.cur + (size_t)P * len;
+  s.cost = (int64_t *)(s.best_sol + (size_t)P * len);
+  s.best_cost = s.cost + P;
+  cgo_status st = cgo_state_get(p, &s);
+  if (st != CGO_OK) return st;
+  h.magic = kBlobMagic;
+  h.version = kBlobVersion;
+  h.population = (uint32_t)P;
+  h.length = (uint32_t)len;
+  h.generation = s.generation;
+  h.T_q32 = s.T_q32;
+  for (int i = 0; i < CGO_NOPS_ALL; ++i) {
+    const bool row = i >= CGO_NOPS;
+    h.w_op[i] = row ? s.w_row_q16[i - CGO_NOPS] : s.w_op_q16[i];
+    h.u_op[i] = row ? s.u_row[i - CGO_NOPS] : s.u_op[i];
+    h.v_op[i] = row ? s.v_row[i - CGO_NOPS] : s.v_op[i];
+  }
+  for (int i = 0; i < 3; ++i) {
+    h.w_k[i] = s.w_k_q16[i];
+    h.u_k[i] = s.u_k[i];
+    h.v_k[i] = s.v_k[i];
+  }
+  h.stag = s.stag;
+  h.elite_prev = s.elite_prev;
+  memcpy(b, &h, sizeof h);
+  return CGO_OK;
+}
+
+cgo_status cgo_state_import(cgo_problem *p, const cgo_params *q, uint64_t seed, const void *buf,
+                            size_t blen) {
+  if (!p || !buf) return fail(CGO_ERR_INVALID, "NULL argument");
+  BlobHead h;
+  if (blen < sizeof h) return fail(CGO_ERR_INVALID, "buffer shorter than the state header");
+  memcpy(&h, buf, sizeof h);
+  if (h.magic != kBlobMagic) return fail(CGO_ERR_INVALID, "not a cgo state buffer");
+  if (h.version != kBlobVersion) return fail(CGO_ERR_INVALID, "state format version %u, expected %u", h.version, kBlobVersion);
+  if (h.length != (uint32_t)p->len) return fail(CGO_ERR_INVALID, "state of length %u for a problem of length %d", h.length, p->len);
+  if (h.population < 1 || h.population > 65536 || blen < blob_bytes((int)h.population, p->len))
+    return fail(CGO_ERR_INVALID, "truncated state buffer");
+  const int P = (int)h.population, len = p->len;
+  const unsigned char *b = (const unsigned char *)buf;
+  std::vector<int32_t> cur((size_t)P * len), best((size_t)P * len);
+  std::vector<int64_t> cost((size_t)P), bcost((size_t)P);
+  memcpy(cur.data(), b + sizeof h, cur.size() * 4);
+  memcpy(best.data(), b + sizeof h + cur.size() * 4, best.size() * 4);
+  memcpy(cost.data(), b + sizeof h + 2 * cur.size() * 4, (size_t)P * 8);
+  memcpy(bcost.data(), b + sizeof h + 2 * cur.size() * 4 + (size_t)P * 8, (size_t)P * 8);
+  cgo_state s;
+  memset(&s, 0, sizeof s);
+  s.struct_size = sizeof s;
+  s.population = P;
+  s.length = len;
+  s.generation = h.generation;
+  s.T_q32 = h.T_q32;
+  for (int i = 0; i < CGO_NOPS_ALL; ++i) {
+    if (i < CGO_NOPS) {
+      s.w_op_q16[i] = h.w_op[i];
+      s.u_op[i] = h.u_op[i];
+      s.v_op[i] = h.v_op[i];
+    } else {
+      s.w_row_q16[i - CGO_NOPS] = h.w_op[i];
+      s.u_row[i - CGO_NOPS] = h.u_op[i];
+      s.v_row[i - CGO_NOPS] = h.v_op[i];
+    }
+  }
+  for (int i = 0; i < 3; ++i) {
+    s.w_k_q16[i] = h.w_k[i];
+    s.u_k[i] = h.u_k[i];
+    s.v_k[i] = h.v_k[i];
+  }
+  s.stag = h.stag;
+  s.elite_prev = h.elite_prev;
+  s.cur = cur.data();
+  s.best_sol = best.data();
+  s.cost = cost.data();
+  s.best_cost = bcost.data();
+  return cgo_state_set(p, q, seed, &s);
+}
+
 cgo_status cgo_op_counts(const cgo_problem *p, uint64_t *out, int32_t cap) {
   if (!p || !out) return fail(CGO_ERR_INVALID, "NULL argument");
   if (cap < kStats) return fail(CGO_ERR_INVALID, "cap %d < %d", cap, kStats);

@@ -698,6 +698,29 @@ def test_split_solve_and_checkpoint_resume(cgo, maker):
     assert_same_counts(prob, o43, "split, 43 generations")
 
 
+def test_state_blob_round_trip(cgo):
+    """The opaque checkpoint: export, import on a fresh handle, resume; a
+    foreign, truncated or mismatched buffer is refused."""
+    inst = I.cvrptw(14, 69, vehicles=4, capacity=80)
+    p = params_for(inst, P=6, C=48, G=17, U=4, ops=[SW, INS, OR] + ROWS)
+    prob = cgo.Problem(inst)
+    prob.solve(p, 4)
+    blob = prob.export_state()
+    assert blob[:4] == b"CGO1"
+    fresh = cgo.Problem(inst)
+    fresh.import_state(p, 4, blob)
+    assert_same_state(fresh.state(), prob.state(), "imported")
+    fresh.solve_continue(9)
+    assert_same_state(fresh.state(), oracle_run(inst, p, 4, 26), "resumed from the buffer")
+    for bad in (b"XXXX" + blob[4:], blob[:len(blob) // 2], blob[:10]):
+        with pytest.raises(cgo.CgoError) as e:
+            fresh.import_state(p, 4, bad)
+        assert e.value.status == cgo.ERR_INVALID
+    other = cgo.Problem(I.cvrptw(15, 69, vehicles=4, capacity=80))
+    with pytest.raises(cgo.CgoError):
+        other.import_state(p, 4, blob)
+
+
 @pytest.mark.parametrize("maker", [lambda: I.tsp_uniform(28, 65), lambda: I.gap(30, 66, m=5),
                                    lambda: I.cvrptw(15, 67, vehicles=4, capacity=80)])
 def test_split_and_resume_with_population_steps(cgo, maker):
