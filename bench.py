@@ -326,6 +326,9 @@ def main():
                     help="tsp442 line: seconds of the Poisson trace served")
     ap.add_argument("--generations", type=int, default=0,
                     help="override G (small cases for profiler captures)")
+    ap.add_argument("--warm-start", type=int, default=0,
+                    help="single solve: time G generations resumed from the state after this many "
+                         "(a multiple of the AOS interval; profiles of the late phase)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -378,9 +381,29 @@ def main():
         shape = tuner.tune_solve(prob, params, seed)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
+    # --warm-start W: each timed solve resumes from the state after W
+    # generations (the late phase of the search, where a long run spends
+    # most of its time); the state is written before the timed region
+    warm = None
+    if args.warm_start > 0:
+        prob.solve(dict(params, G=args.warm_start), seed, stream)
+        warm = prob.state()
+        desc += " resumed after %d generations" % args.warm_start
+
+    def prepare():
+        if warm is not None:
+            prob.set_state(params, seed, warm)
+
+    def run_step():
+        if warm is None:
+            prob.solve(params, seed, stream)
+        else:
+            prob.solve_continue(cfg["G"], stream)
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            prob.solve(params, seed, stream)
+            prepare()
+            run_step()
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -392,11 +415,12 @@ def main():
     launches0 = cgo.kernel_launches()
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
+            prepare()
             flush.fill_(1)                       # evict L2 between steps
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            prob.solve(params, seed, stream)
+            run_step()
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -437,7 +461,8 @@ def main():
     e2e_value = cfg["P"] * cfg["C"] * cfg["G"] * world / (float(e2e_t.item()) / 1000.0)
 
     extras = {}
-    if world == 1 and args.workload == "tsp442" and not args.no_extras and args.generations == 0:
+    if (world == 1 and args.workload == "tsp442" and not args.no_extras and args.generations == 0
+            and args.warm_start == 0):
         # the batched and served forms of the metric (configs of the 512-instance
         # batch and the Poisson serving trace), each against one launch per solve
         t_x = time.perf_counter()
