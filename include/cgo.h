@@ -281,6 +281,21 @@ cgo_status cgo_best(const cgo_problem *prob, int32_t *out_sol, int32_t cap, int6
  * it, and the generations that launch ran.  CGO_ERR_STATE if none yet. */
 cgo_status cgo_last_kernel_time(const cgo_problem *prob, double *ms, int64_t *generations);
 
+/* The elite as a multi-row solution (Sec. 3.1: rows of variable length,
+ * "dim2_sizes", over a partition of the elements; the Perm-Partition
+ * structure).  CVRPTW's rows are its vehicles' routes: the separator
+ * sequence the search works on is this solution laid out flat, route r
+ * running from just after the r-th separator to the next one.  Fills
+ * out_rows with the customers (0 .. n-1) row after row (cap >= n),
+ * row_lengths[r] with each row's length (max_rows >= vehicles) and
+ * *out_rows_count with the number of rows (vehicles; empty routes are rows
+ * of length 0) and *out_cost with the elite's cost.  Other models have one
+ * row: the whole solution.  Host buffers; CGO_ERR_INVALID for short
+ * buffers, CGO_ERR_STATE before the first solve. */
+cgo_status cgo_best_rows(const cgo_problem *prob, int32_t *out_rows, int32_t cap,
+                         int32_t *row_lengths, int32_t max_rows, int32_t *out_rows_count,
+                         int64_t *out_cost);
+
 /* Solution length of this problem (n, or n + vehicles - 1 for CVRPTW). */
 cgo_status cgo_solution_length(const cgo_problem *prob, int32_t *out_len);
 

@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
                 "cgo_solve_continue": ([vp, c.c_int64, vp], c.c_int),
                 "cgo_best": ([vp, _i32p, c.c_int32, _i64p], c.c_int),
                 "cgo_solution_length": ([vp, _i32p], c.c_int),
+                "cgo_best_rows": ([vp, _i32p, c.c_int32, _i32p, c.c_int32, _i32p, _i64p], c.c_int),
                 "cgo_state_get": ([vp, P(cgo_state)], c.c_int),
                 "cgo_op_counts": ([vp, P(c.c_uint64), c.c_int32], c.c_int),
                 "cgo_state_export": ([vp, vp, c.c_size_t, P(c.c_size_t)], c.c_int),
@@ -314,6 +315,22 @@ class Problem:
         check(lib().cgo_best(self.h, sol.ctypes.data_as(_i32p), self.length, ctypes.byref(c)),
               "cgo_best")
         return sol, c.value
+
+    def best_rows(self) -> tuple[list, int]:
+        """The elite as rows (CVRPTW: one list of customers per route)."""
+        n = int(self.inst["n"])
+        rows = int(self.inst.get("vehicles", 1)) if int(self.inst["model"]) == CVRPTW else 1
+        flat = np.zeros(max(n, self.length), np.int32)
+        lens = np.zeros(rows, np.int32)
+        cnt, c = ctypes.c_int32(), ctypes.c_int64()
+        check(lib().cgo_best_rows(self.h, flat.ctypes.data_as(_i32p), len(flat),
+                                  lens.ctypes.data_as(_i32p), rows, ctypes.byref(cnt),
+                                  ctypes.byref(c)), "cgo_best_rows")
+        out, o = [], 0
+        for L in lens[:cnt.value]:
+            out.append(flat[o:o + L].tolist())
+            o += int(L)
+        return out, c.value
 
     def state(self) -> dict:
         s = cgo_state()

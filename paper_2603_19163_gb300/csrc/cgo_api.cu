@@ -1090,6 +1090,32 @@ cgo_status cgo_op_counts(const cgo_problem *p, uint64_t *out, int32_t cap) {
   return CGO_OK;
 }
 
+cgo_status cgo_best_rows(const cgo_problem *p, int32_t *out_rows, int32_t cap, int32_t *row_lengths,
+                         int32_t max_rows, int32_t *out_rows_count, int64_t *out_cost) {
+  if (!p || !out_rows || !row_lengths || !out_rows_count) return fail(CGO_ERR_INVALID, "NULL argument");
+  const bool cv = p->model == CVRPTW;
+  const int rows = cv ? p->len - p->n + 1 : 1, elems = cv ? p->n : p->len;
+  if (cap < elems) return fail(CGO_ERR_INVALID, "cap %d < %d elements", cap, elems);
+  if (max_rows < rows) return fail(CGO_ERR_INVALID, "max_rows %d < %d rows", max_rows, rows);
+  std::vector<int32_t> seq((size_t)p->len);
+  int64_t c = 0;
+  const cgo_status s = cgo_best(p, seq.data(), p->len, &c);
+  if (s != CGO_OK) return s;
+  int o = 0, r = 0;
+  for (int r0 = 0; r0 < rows; ++r0) row_lengths[r0] = 0;
+  for (int q = 0; q < p->len; ++q) {
+    if (cv && seq[(size_t)q] >= p->n) {
+      ++r;  // a separator closes route r
+      continue;
+    }
+    out_rows[o++] = seq[(size_t)q];
+    row_lengths[r]++;
+  }
+  *out_rows_count = rows;
+  if (out_cost) *out_cost = c;
+  return CGO_OK;
+}
+
 cgo_status cgo_state_get(const cgo_problem *p, cgo_state *o) {
   if (!p || !o || (o->struct_size != sizeof(cgo_state) && o->struct_size != CGO_STATE_SIZE_V1))
     return fail(CGO_ERR_INVALID, "bad state struct");

@@ -698,6 +698,29 @@ def test_split_solve_and_checkpoint_resume(cgo, maker):
     assert_same_counts(prob, o43, "split, 43 generations")
 
 
+def test_best_rows_are_the_routes(cgo):
+    """The elite as a multi-row solution: CVRPTW's routes as rows, equal to
+    decoding the separator sequence; other models have one row."""
+    inst = I.cvrptw(16, 70, vehicles=5, capacity=80)
+    prob = cgo.Problem(inst)
+    prob.solve(params_for(inst, P=6, C=48, G=15, ops=[SW, INS] + ROWS), 3)
+    seq, c = prob.best()
+    rows, c2 = prob.best_rows()
+    want, cur = [], []
+    for s in seq.tolist():
+        if s >= 16:
+            want.append(cur)
+            cur = []
+        else:
+            cur.append(s)
+    want.append(cur)
+    assert rows == want and c2 == c and len(rows) == 5
+    assert sorted(x for r in rows for x in r) == list(range(16))
+    t = cgo.Problem(I.tsp_uniform(12, 71))
+    t.solve(params_for(I.tsp_uniform(12, 71), P=4, C=32, G=5), 1)
+    assert t.best_rows()[0] == [t.best()[0].tolist()]
+
+
 def test_state_blob_round_trip(cgo):
     """The opaque checkpoint: export, import on a fresh handle, resume; a
     foreign, truncated or mismatched buffer is refused."""
