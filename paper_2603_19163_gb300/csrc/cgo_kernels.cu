@@ -50,9 +50,6 @@ struct SolEl<GAP> {
 
 struct SolScal {
   long long cost, best, aw, av;  // aw/av: knapsack sum of weights / values
-  // 1: the member's best solution is the crossover child in its global
-  // scratch row, not yet copied to bestsol (copied before the next barrier)
-  long long xb;
 };
 
 struct Layout {
@@ -91,7 +88,7 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   L.scr_off = L.sol_off + (int64_t)nsol * L.sol_stride;
   const bool perm = (model == TSP || model == QAP || model == CVRPTW);
   L.scal_off = L.scr_off + (perm ? (int64_t)groups * L.sol_stride : 0);
-  L.load_off = L.scal_off + align16((int64_t)nsol * (int64_t)sizeof(SolScal));
+  L.load_off = L.scal_off + align16((int64_t)nsol * 32);
   L.aux_off = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
   L.aux_stride = model == CVRPTW ? cv_aux_bytes(len, cvmax) : 0;
   L.part_off = L.aux_off + (int64_t)nsol * L.aux_stride;
@@ -1460,9 +1457,11 @@ __device__ __noinline__ int window_migrate(const KInst &I, const View X, unsigne
       I.best[p0 + ls] = scal[ls].best;
     }
   }
-  if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
-    return -1;
-  ++nb;
+  if (more) {
+    if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
+      return -1;
+    ++nb;
+  }
   return (int)(nb - nb0);
 }
 
@@ -1557,10 +1556,7 @@ __device__ __noinline__ int window_cross(const KInst &I, const View X, unsigned 
   // Phase 1 builds each child in the member's global scratch row, costs
   // it and takes it into shared memory if the Metropolis rule accepts it;
   // phase 2, after a barrier, writes the bests the children lowered and
-  // publishes every member's cost and best.  When no elite injection
-  // follows in this window, nobody reads bestsol before the next window
-  // barrier: phase 2 is left out and a lowered best stays in the scratch
-  // row (xb), copied to bestsol before that barrier.
+  // publishes every member's cost and best.
   const long long *gb = (const long long *)I.best;
   int *wt = (int *)part;  // per-warp counts of the order crossover's compaction
   for (int e = 0; e < mine; ++e) {
@@ -1631,7 +1627,6 @@ __device__ __noinline__ int window_cross(const KInst &I, const View X, unsigned 
       G.sync();
       SolScal sc = scal[ls];
       sc.cost = cc;
-      if (cc < sc.best && !more) sc.xb = 1;
       sc.best = min(sc.best, cc);
       G.sync();
       if (G.tig == 0) scal[ls] = sc;
@@ -1641,7 +1636,6 @@ __device__ __noinline__ int window_cross(const KInst &I, const View X, unsigned 
         cv_build(X, A, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, X.wl > 0), G);
     }
   }
-  if (!more) return 0;
   if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
     return -1;
   ++nb;
@@ -1713,7 +1707,6 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       scal[ls].cost = I.cost[p];
       scal[ls].best = I.best[p];
       scal[ls].aw = scal[ls].av = 0;
-      scal[ls].xb = 0;
     }
     G.sync();
     aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
@@ -1977,7 +1970,6 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
             sc.cost += d;
             if (sc.cost < sc.best) {
               sc.best = sc.cost;
-              sc.xb = 0;  // this copy supersedes a pending crossover best
               int32_t *dst = I.bestsol + (int64_t)p * len;
               for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
             }
@@ -2051,21 +2043,6 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     }
     if (G.gw == 0 && lane < kStats && my) atomicAdd(&S->acc[slot][lane], my);
     if (G.gw == 0 && lane == 0) atomicMin((long long *)&S->elite[slot], minbest);
-    if constexpr (XF) {
-      // bests that the last window's crossover children lowered, kept in the
-      // scratch rows until now, go to bestsol before anyone reads it again
-      for (int e = 0; e < mine; ++e) {
-        const int ls = G.grp + e * ngroups, p = p0 + ls;
-        if (scal[ls].xb) {
-          const int32_t *src = I.pool_sol + (int64_t)p * len;
-          int32_t *dst = I.bestsol + (int64_t)p * len;
-          for (int i = G.tig; i < len; i += G.nthr) dst[i] = __ldcg(src + i);
-        }
-      }
-      G.sync();
-      if (G.tig == 0)
-        for (int e = 0; e < mine; ++e) scal[G.grp + e * ngroups].xb = 0;
-    }
     if ((inject || migr || cross) && G.tig == 0) {
       for (int e = 0; e < mine; ++e) {
         const int ls = G.grp + e * ngroups;
@@ -2165,12 +2142,6 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     const El *sol = (const El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
     int32_t *dst = I.cur + (int64_t)p * len;
     for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
-    if constexpr (XF)
-      if (scal[ls].xb) {  // a pending crossover best
-        const int32_t *src = I.pool_sol + (int64_t)p * len;
-        int32_t *bdst = I.bestsol + (int64_t)p * len;
-        for (int i = G.tig; i < len; i += G.nthr) bdst[i] = __ldcg(src + i);
-      }
     if (G.tig == 0) {
       I.cost[p] = scal[ls].cost;
       I.best[p] = scal[ls].best;
