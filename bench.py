@@ -125,10 +125,11 @@ def cvrptw_objectives(inst: dict, sol) -> dict:
 
 
 def extra_ops_mask(model: int, extra: str) -> int:
-    """Operator bits that --extra-ops adds for a model (QAP's GPU path is swap-only)."""
+    """Operator bits that --extra-ops adds for a model (3-opt for the
+    permutation models, the segment operator for binary and integer ones)."""
     bits = 0
     for name in filter(None, extra.split(",")):
-        if name == "three_opt" and model in (I.TSP, I.CVRPTW):
+        if name == "three_opt" and model in (I.TSP, I.QAP, I.CVRPTW):
             bits |= 1 << O_THREE_OPT
         elif name == "segment" and model in (I.KNAPSACK, I.GAP):
             bits |= 1 << O_SEGMENT

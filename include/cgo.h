@@ -46,9 +46,10 @@ typedef enum { CGO_ENC_PERM = 0, CGO_ENC_BINARY = 1, CGO_ENC_INTEGER = 2 } cgo_e
 
 /* Cost models.  Costs are int64 and minimised.
  *  TSP      perm of n cities; sum of D[a_k][a_(k+1) mod n]; mat0 = D (n*n).
- *           The GPU path needs D symmetric.
+ *           D may be asymmetric (the tour's direction then counts; the
+ *           library keeps the full matrix instead of its triangle).
  *  QAP      perm of n; sum_i sum_j F[i][j]*D[a_i][a_j]; mat0 = F, mat1 = D (n*n).
- *           The GPU path implements the swap operator only.
+ *           F and D may be asymmetric with a non-zero diagonal.
  *  KNAPSACK binary n; -sum v x + lambda*max(0, sum w x - capacity);
  *           vec0 = w, vec1 = v (n); lambda = penalty0, or 1 + max v if 0.
  *  GAP      integer n jobs in [0, m-1]; sum_j c[x_j][j] +
@@ -228,14 +229,15 @@ typedef struct {
   int32_t gens_in_flight;      /* 0 = auto; 1 .. 4 for single solves with at
                                   most 32 * warps_per_member candidates (3 and 4
                                   with warps_per_member = 4 and neither island
-                                  migration nor crossover); batched solves use 1 */
+                                  migration nor crossover, not for an asymmetric
+                                  TSP matrix); batched solves use 1 */
 } cgo_launch;
 
 /* Create a problem: validates the description and deep-copies the data to
  * the current device, so the caller may free its arrays on return.
  * Errors: CGO_ERR_INVALID (sizes, encoding/model mismatch, data that could
- * overflow an int64 cost), CGO_ERR_UNSUPPORTED (e.g. asymmetric TSP),
- * CGO_ERR_NOMEM, CGO_ERR_CUDA.  *out is NULL on error. */
+ * overflow an int64 cost), CGO_ERR_NOMEM, CGO_ERR_CUDA.  *out is NULL on
+ * error. */
 cgo_status cgo_problem_create(const cgo_problem_desc *desc, cgo_problem **out);
 
 /* Free the problem and its device memory.  NULL is accepted. */

@@ -95,6 +95,17 @@ def tsp_uniform(n: int, index: int, box: int = 1000) -> dict:
     return dict(model=TSP, n=n, mat0=euclid_matrix(xy), coords=xy)
 
 
+def tsp_asym(n: int, index: int, box: int = 1000, skew: int = 300) -> dict:
+    """TSP of an asymmetric matrix: the Euclidean distances of n integer
+    points uniform in [0, box]^2 plus an independent offset uniform in
+    [0, skew] for every ordered pair i != j (diagonal 0)."""
+    st = Stream(index, 11)
+    xy = st.ints(0, box, 2 * n).reshape(n, 2)
+    D = euclid_matrix(xy).astype(np.int64) + st.ints(0, skew, n * n).reshape(n, n)
+    np.fill_diagonal(D, 0)
+    return dict(model=TSP, n=n, mat0=D.astype(np.int32), coords=xy)
+
+
 def tsp_clustered(n: int, index: int, box: int = 4000, clusters: int = 6,
                   sigma: float = 40.0, noise: float = 0.10) -> dict:
     """TSP: Gaussian clusters plus uniform noise (pcb442-shaped stand-in).

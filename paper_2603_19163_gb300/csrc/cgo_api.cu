@@ -299,8 +299,6 @@ cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *
   if (q->generations < 0) return fail(CGO_ERR_INVALID, "generations < 0");
   const uint32_t en = q->op_mask & applicable_mask(p);
   if (!en) return fail(CGO_ERR_INVALID, "no operator of this encoding is enabled");
-  if (p->model == QAP && en != (1u << SWAP))
-    return fail(CGO_ERR_UNSUPPORTED, "QAP on the GPU implements the swap operator only");
   uint64_t ws = 0;
   for (int i = 0; i < kNops; ++i) {
     if (!((en >> i) & 1u)) continue;
@@ -347,7 +345,7 @@ cgo_status validate_params(const cgo_problem *p, const cgo_params *q, uint32_t *
 KInst base_kinst(const cgo_problem *p) {
   KInst h;
   memset(&h, 0, sizeof h);
-  h.model = p->model;
+  h.model = (p->model == TSP && p->asym) ? (int32_t)ATSP : p->model;
   h.n = p->n;
   h.len = p->len;
   h.m = p->m;
@@ -421,14 +419,17 @@ cgo_status choose_launch(cgo_problem *p, KInst &h, int *warps_out, int *wpm_out,
     if (ns == 1) return true;
     if (C > 32 * wpm) return false;
     if (ns == 2) return 2 * wpm <= kMaxWarps;
-    return wpm == 4 && !takes_xf(h);
+    // three or four: one member per CTA of four warps each, no window code;
+    // the asymmetric TSP keeps one or two
+    return wpm == 4 && !takes_xf(h) && h.model != ATSP;
   };
   int ns_try[4] = {2, 1, 0, 0}, nns = 2;
   if (p->ns_override > 0) {
     if (!ns_ok(p->ns_override))
       return fail(CGO_ERR_UNSUPPORTED,
                   "%d generations in flight need C <= 32 * warps_per_member (and, for 3 or 4, "
-                  "warps_per_member = 4 without migration or crossover)",
+                  "warps_per_member = 4 without migration or crossover, and a symmetric TSP "
+                  "matrix)",
                   p->ns_override);
     ns_try[0] = p->ns_override;
     nns = 1;
@@ -664,20 +665,37 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
   switch (d->model) {
     case CGO_TSP: {
       if ((s = host_copy(d->mat0, n * n, dev, a)) != CGO_OK) return bail(s);
-      for (int64_t i = 0; i < n; ++i)
+      for (int64_t i = 0; i < n && !p->asym; ++i)
         for (int64_t j = i + 1; j < n; ++j)
-          if (a[i * n + j] != a[j * n + i])
-            return bail(fail(CGO_ERR_UNSUPPORTED, "the GPU TSP path needs a symmetric distance matrix"));
+          if (a[i * n + j] != a[j * n + i]) {
+            p->asym = 1;  // the kernels' ATSP path: the full matrix, piece deltas
+            break;
+          }
       const int64_t mx = absmax(a);
       if ((double)mx * (double)n > kLimit) return bail(fail(CGO_ERR_INVALID, "distances could overflow"));
       p->tri16 = mx <= 32767 ? 1 : 0;
       cudaError_t e = copy_in(&p->d_mat0, a.data(), n * n, false);
       if (e != cudaSuccess) return bail(cuda_fail(e, "copying D"));
-      const int64_t tb = pad16(n * (n + 1) / 2 * (p->tri16 ? 2 : 4));
-      if ((e = dev_alloc(&p->d_tri, (size_t)tb)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
-      if ((e = cudaMemsetAsync(p->d_tri, 0, (size_t)tb, host_stream())) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
-      if ((e = build_triangle(p->d_mat0, (int)n, p->tri16, p->d_tri, host_stream())) != cudaSuccess)
-        return bail(cuda_fail(e, "triangle"));
+      if (p->asym) {
+        // the full matrix in the kernels' element width
+        const int64_t fb = pad16(n * n * (p->tri16 ? 2 : 4));
+        std::vector<int16_t> h16;
+        if (p->tri16) {
+          h16.resize((size_t)(n * n));
+          for (int64_t t = 0; t < n * n; ++t) h16[(size_t)t] = (int16_t)a[(size_t)t];
+        }
+        if ((e = dev_alloc(&p->d_tri, (size_t)fb)) != cudaSuccess) return bail(cuda_fail(e, "matrix"));
+        if ((e = cudaMemcpyAsync(p->d_tri, p->tri16 ? (const void *)h16.data() : (const void *)a.data(),
+                                 (size_t)(n * n * (p->tri16 ? 2 : 4)), cudaMemcpyHostToDevice,
+                                 host_stream())) != cudaSuccess)
+          return bail(cuda_fail(e, "matrix"));
+      } else {
+        const int64_t tb = pad16(n * (n + 1) / 2 * (p->tri16 ? 2 : 4));
+        if ((e = dev_alloc(&p->d_tri, (size_t)tb)) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+        if ((e = cudaMemsetAsync(p->d_tri, 0, (size_t)tb, host_stream())) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
+        if ((e = build_triangle(p->d_mat0, (int)n, p->tri16, p->d_tri, host_stream())) != cudaSuccess)
+          return bail(cuda_fail(e, "triangle"));
+      }
       if ((e = cudaStreamSynchronize(host_stream())) != cudaSuccess) return bail(cuda_fail(e, "triangle"));
       std::vector<int32_t> hp;
       heuristic_perms(a, n, hp);
@@ -1283,11 +1301,11 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_in, 
     int b = -1;
     const int xf = takes_xf(h);
     for (size_t k = 0; k < buckets.size(); ++k)
-      if (buckets[k].model == p->model && buckets[k].tri16 == p->tri16 && buckets[k].xf == xf &&
+      if (buckets[k].model == h.model && buckets[k].tri16 == p->tri16 && buckets[k].xf == xf &&
           buckets[k].wpm == wpm && buckets[k].warps == warps && buckets[k].smem == cls)
         b = (int)k;
     if (b < 0) {
-      buckets.push_back(Bucket{p->model, p->tri16, xf, wpm, warps, cls, {}});
+      buckets.push_back(Bucket{h.model, p->tri16, xf, wpm, warps, cls, {}});  // the kernels' model
       b = (int)buckets.size() - 1;
     }
     buckets[(size_t)b].members.push_back(i);
@@ -1489,7 +1507,7 @@ cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint
   uint32_t hf[2] = {0, 0};
   CUDA_TRY(cudaMemcpyAsync(hf, flags, sizeof hf, cudaMemcpyDeviceToHost, st), "matrix check");
   CUDA_TRY(cudaStreamSynchronize(st), "matrix check");
-  if (hf[0]) return fail(CGO_ERR_UNSUPPORTED, "the GPU TSP path needs a symmetric distance matrix");
+  if (hf[0]) return fail(CGO_ERR_UNSUPPORTED, "the allocation-free solve needs a symmetric distance matrix");
   p.tri16 = hf[1] <= 32767u ? 1 : 0;
   CUDA_TRY(cudaMemsetAsync(tri, 0, tri_b, st), "scratch reset");
   CUDA_TRY(build_triangle(d->mat0, n, p.tri16, tri, st), "triangle");

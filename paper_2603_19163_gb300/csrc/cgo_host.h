@@ -16,6 +16,7 @@ struct cgo_problem {
   int64_t capacity = 0, lam0 = 0, lam1 = 0;
   int64_t wdist = 1, wveh = 0;  // CVRPTW objective weights
   int64_t wlong = 0;            // CVRPTW: weight of the longest route
+  int asym = 0;                 // TSP with an asymmetric matrix (the kernels' ATSP path)
   int lb = 0, ub = 0;
   uint32_t tag = 0;
   int32_t *d_mat0 = nullptr, *d_mat1 = nullptr, *d_vec[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -18,7 +18,9 @@ constexpr int kMaxWarps = 8;    // warps per CTA (kernel launch bound 256 thread
 constexpr int kMaxWarpsDeep = 16;
 constexpr int kMaxAgents = 64;  // GAP agents
 
-enum Model { TSP = 0, QAP = 1, KNAPSACK = 2, GAP = 3, CVRPTW = 4 };
+// ATSP: the TSP of an asymmetric matrix (the kernels' own model id; the
+// public model stays CGO_TSP)
+enum Model { TSP = 0, QAP = 1, KNAPSACK = 2, GAP = 3, CVRPTW = 4, ATSP = 5 };
 enum Op { SWAP = 0, TWO_OPT = 1, INSERT = 2, OR_OPT = 3, FLIP = 4, PERTURB = 5, THREE_OPT = 6,
           SEGMENT = 7 /* seg_flip (binary), seg_reset (integer) */,
           ROW_SWAP = 8, ROW_MERGE = 9, ROW_SPLIT = 10 /* CVRPTW's routes */ };

@@ -86,11 +86,12 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   L.sol_stride = align16((int64_t)len * sol_esize(model));
   L.sol_off = L.inst;
   L.scr_off = L.sol_off + (int64_t)nsol * L.sol_stride;
-  const bool perm = (model == TSP || model == QAP || model == CVRPTW);
+  const bool perm = (model == TSP || model == QAP || model == CVRPTW || model == ATSP);
   L.scal_off = L.scr_off + (perm ? (int64_t)groups * L.sol_stride : 0);
   L.load_off = L.scal_off + align16((int64_t)nsol * 32);
   L.aux_off = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
-  L.aux_stride = model == CVRPTW ? cv_aux_bytes(len, cvmax) : 0;
+  L.aux_stride = model == CVRPTW ? cv_aux_bytes(len, cvmax)
+                                 : (model == ATSP ? align16(16 * (int64_t)(len + 1)) : 0);
   L.part_off = L.aux_off + (int64_t)nsol * L.aux_stride;
   L.total = L.part_off + (int64_t)groups * group_bytes(wpm);
   return L;
@@ -100,6 +101,7 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
 int64_t instance_data_bytes(const KInst &h) {
   switch (h.model) {
     case TSP: return align16((int64_t)h.n * (h.n + 1) / 2 * (h.tri16 ? 2 : 4));
+    case ATSP: return align16((int64_t)h.n * h.n * (h.tri16 ? 2 : 4));
     case QAP: return 4 * align16((int64_t)h.n * (h.n | 1) * 4);  // F, D and their transposes
     case KNAPSACK: return 2 * align16((int64_t)h.n * 4);
     case GAP: return 2 * align16((int64_t)h.m * h.n * 4) + align16((int64_t)h.m * 4);
@@ -137,6 +139,7 @@ struct View {
   long long wl;      // CVRPTW: weight of the longest route's distance
   bool cv32;
   bool t3;   // 3-opt enabled for this instance
+  bool t16;  // TSP / ATSP matrix entries stored as int16
   bool seg;  // seg_flip / seg_reset enabled for this instance
 };
 
@@ -376,6 +379,35 @@ __device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
                               const PMove &p0, const PMove &p1, int np) {
   return X.cv32 ? qap_step_t<int>(X, sol, mv, p0, p1, np)
                 : qap_step_t<long long>(X, sol, mv, p0, p1, np);
+}
+
+// Any other permutation move (2-opt, insertion, or-opt, 3-opt) on the
+// (virtual) permutation V: only the positions H = [b1, b4) change, so
+//   delta = sum_{i in H} sum_j F[i][j] (D[V'_i][V'_j] - D[V_i][V_j])
+//         + sum_{i not in H} sum_{j in H} F[i][j] (D[V_i][V'_j] - D[V_i][V_j]),
+// with V'_q = V_{inv(q)} (64-bit arithmetic: O(n |H|) terms).
+__device__ long long qap_block_step(const View &X, const PermEl *sol, const PMove &mv,
+                                    const PMove &p0, const PMove &p1, int np) {
+  const int n = X.n, lo = mv.b1, hi = mv.b4, qs = X.qs;
+  const int32_t *F = X.F, *D = X.D;
+  auto V = [&](int q) { return vlook(sol, q, p0, p1, np); };
+  long long acc = 0;
+  for (int i = lo; i < hi; ++i) {
+    const int vi = V(i), wi = V(perm_inv(mv, i));
+    const int32_t *Fi = F + (size_t)i * qs, *Dv = D + (size_t)vi * qs, *Dw = D + (size_t)wi * qs;
+    for (int j = 0; j < n; ++j) {
+      const int vj = V(j), wj = (j >= lo && j < hi) ? V(perm_inv(mv, j)) : vj;
+      acc += (long long)Fi[j] * ((long long)Dw[wj] - (long long)Dv[vj]);
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    if (i >= lo && i < hi) continue;
+    const int vi = V(i);
+    const int32_t *Fi = F + (size_t)i * qs, *Dv = D + (size_t)vi * qs;
+    for (int j = lo; j < hi; ++j)
+      acc += (long long)Fi[j] * ((long long)Dv[V(perm_inv(mv, j))] - (long long)Dv[V(j)]);
+  }
+  return acc;
 }
 
 // ---------------------------------------------------------------- CVRPTW
@@ -648,7 +680,6 @@ __device__ long long cvrptw_step0(const View &X, const PermEl *sol, const PMove 
   return cvrptw_routes(X, Vn, L, R, X.cv32, J) - old;
 }
 
-// ------------------------------------------------- candidate evaluation
 // The moves of one candidate, kept by the lane that may win the argmin so
 // that the group can apply it without redrawing.
 struct CandMoves {
@@ -656,6 +687,163 @@ struct CandMoves {
   int k;
 };
 
+// ---------------------------------------------------------------- ATSP
+// TSP of an asymmetric matrix (Sec. 3.1's TSP asks no symmetry of D).  A
+// reversed piece of the tour changes the direction of its inner edges, so
+// the junction delta of the symmetric case does not hold.  Each member
+// keeps the prefix sums of its tour's forward and backward edge costs:
+// F[q] = sum_{i<q} D[s_i][s_(i+1)], B[q] = sum_{i<q} D[s_(i+1)][s_i]
+// (q < len) and F[len] = the whole cyclic tour.  A candidate's k moves turn
+// the tour into at most 13 pieces of the current one, each traversed forward
+// or backward; its cost is the pieces' inner edges (from the prefix sums)
+// plus the edges that join them.
+struct TsAux {
+  long long *F, *B;
+};
+__device__ __forceinline__ TsAux ts_aux_at(unsigned char *p, int len) {
+  TsAux a;
+  a.F = (long long *)p;
+  a.B = a.F + (len + 1);
+  return a;
+}
+
+template <bool T16>
+__device__ __forceinline__ long long dfull(const View &X, int a, int b) {
+  const size_t i = (size_t)a * X.n + b;
+  return T16 ? (long long)((const int16_t *)X.tri)[i] : (long long)((const int32_t *)X.tri)[i];
+}
+
+template <bool T16, class El, class G_t>
+__device__ void ts_build(const View &X, const El *sol, const TsAux &a, const G_t &G) {
+  const int m = X.len, lane = threadIdx.x & 31;
+  if (G.gw == 0) {
+    long long cf = 0, cb = 0;
+    for (int base = 0; base < m; base += 32) {
+      const int q = base + lane;
+      long long f = 0, b = 0;
+      if (q + 1 < m) {
+        f = dfull<T16>(X, (int)sol[q], (int)sol[q + 1]);
+        b = dfull<T16>(X, (int)sol[q + 1], (int)sol[q]);
+      }
+      // inclusive scans, then shifted by one position (exclusive prefix)
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const long long uf = __shfl_up_sync(kFull, f, off), ub = __shfl_up_sync(kFull, b, off);
+        if (lane >= off) {
+          f += uf;
+          b += ub;
+        }
+      }
+      if (q + 1 < m) {
+        a.F[q + 1] = cf + f;
+        a.B[q + 1] = cb + b;
+      }
+      cf += __shfl_sync(kFull, f, 31);
+      cb += __shfl_sync(kFull, b, 31);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      a.F[0] = 0;
+      a.B[0] = 0;
+      a.F[m] = (m > 1 ? a.F[m - 1] : 0) + dfull<T16>(X, (int)sol[m - 1], (int)sol[0]);
+    }
+  }
+  G.sync();
+}
+
+struct Piece {
+  int s, e, r;  // positions s .. e of the current tour, traversed backward when r
+};
+constexpr int kMaxPieces = 16;
+
+// cut the piece holding virtual position x (0 < x < len) so that a piece starts there
+__device__ __forceinline__ void piece_split(Piece *pc, int &np, int x) {
+  int vs = 0;
+  for (int i = 0; i < np; ++i) {
+    const int L = pc[i].e - pc[i].s + 1;
+    if (x > vs && x < vs + L) {
+      for (int j = np; j > i + 1; --j) pc[j] = pc[j - 1];
+      const int c = x - vs;  // elements of the first part
+      Piece a = pc[i], b = pc[i];
+      if (!pc[i].r) {
+        a.e = a.s + c - 1;
+        b.s = a.s + c;
+      } else {
+        a.s = pc[i].e - c + 1;  // backward: the first part is the top c positions
+        b.e = pc[i].e - c;
+      }
+      pc[i] = a;
+      pc[i + 1] = b;
+      ++np;
+      return;
+    }
+    vs += L;
+  }
+}
+
+// the pieces after one cut-and-reorder move P0 A M B P4 -> P0 B M A' P4
+__device__ void piece_move(Piece *pc, int &np, const PMove &mv, int m) {
+  const int cuts[4] = {mv.b1, mv.b2, mv.b3, mv.b4};
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (cuts[t] > 0 && cuts[t] < m) piece_split(pc, np, cuts[t]);
+  int cls[kMaxPieces];
+  int vs = 0;
+  for (int i = 0; i < np; ++i) {
+    cls[i] = vs < mv.b1 ? 0 : (vs < mv.b2 ? 1 : (vs < mv.b3 ? 2 : (vs < mv.b4 ? 3 : 4)));
+    vs += pc[i].e - pc[i].s + 1;
+  }
+  Piece out[kMaxPieces];
+  int no = 0;
+  const int order[5] = {0, 3, 2, 1, 4};
+#pragma unroll
+  for (int o = 0; o < 5; ++o) {
+    const int c = order[o];
+    const bool flip = c == 1 && mv.rev;
+    for (int t = 0; t < np; ++t) {
+      const int i = flip ? np - 1 - t : t;
+      if (cls[i] != c) continue;
+      out[no] = pc[i];
+      if (flip) out[no].r ^= 1;
+      ++no;
+    }
+  }
+  for (int i = 0; i < no; ++i) pc[i] = out[i];
+  np = no;
+}
+
+// delta of the k-step candidate: cost of the new cyclic tour minus F[len]
+template <bool T16>
+__device__ long long atsp_delta(const View &X, const PermEl *sol, const TsAux &a, const CandMoves &cm,
+                                int k) {
+  const int m = X.len;
+  Piece pc[kMaxPieces];
+  int np = 1;
+  pc[0] = Piece{0, m - 1, 0};
+  for (int t = 0; t < k; ++t) piece_move(pc, np, cm.m[t], m);
+  long long total = 0;
+  for (int i = 0; i < np; ++i) {
+    const Piece p = pc[i], q = pc[i + 1 < np ? i + 1 : 0];
+    total += p.r ? a.B[p.e] - a.B[p.s] : a.F[p.e] - a.F[p.s];
+    total += dfull<T16>(X, (int)sol[p.r ? p.s : p.e], (int)sol[q.r ? q.e : q.s]);
+  }
+  return total - a.F[m];
+}
+
+// rebuild a member's cache after its solution changed (CVRPTW's route
+// cache, ATSP's edge-cost prefix sums; nothing for the other models)
+template <int MODEL, class El, class G_t>
+__device__ __forceinline__ void model_aux_build(const View &X, const El *sol, unsigned char *auxp,
+                                                int len, const G_t &G) {
+  if constexpr (MODEL == CVRPTW) {
+    cv_build(X, sol, cv_aux_at(auxp, len, X.wl > 0), G);
+  } else if constexpr (MODEL == ATSP) {
+    if (X.t16) ts_build<true>(X, sol, ts_aux_at(auxp, len), G);
+    else ts_build<false>(X, sol, ts_aux_at(auxp, len), G);
+  }
+}
+
+// ------------------------------------------------- candidate evaluation
 // The three steps of a TSP candidate, evaluated in phases across the steps
 // (positions, inverse maps, solution loads, triangle gathers, sums) so that
 // independent work is adjacent in program order.  With the int16 triangle
@@ -921,6 +1109,26 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
     candidate_cvrptw(X, sol, W, c, p, g, false, d, rec, cm, aux);
     return d;
   }
+  if constexpr (MODEL == ATSP) {
+    // the k steps' moves, then the tour they give as pieces of this one
+    const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
+    const int k = 1 + wpick(W.ck, W.Wk, R0.w);
+    int ops[3] = {-1, -1, -1};
+    cm.k = k;
+    cm.m[1] = cm.m[2] = PMove{0, 0, 0, 0, 0};
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      if (t < k) {
+        const uint4 R = t == 0 ? R0 : philox(ctr_word(c, (uint32_t)t, kKindMove), X.tag, p, g, X.k0, X.k1);
+        ops[t] = wpick(W.cop, W.Wop, R.x);
+        cm.m[t] = X.t3 ? perm_decode<true>(ops[t], R.y, R.z, X.len)
+                       : perm_decode<false>(ops[t], R.y, R.z, X.len);
+      }
+    }
+    const long long d = atsp_delta<T16>(X, sol, ts_aux_at((unsigned char *)aux.cum, X.len), cm, k);
+    rec = stats_record(ops[0], ops[1], ops[2], k, d < 0);
+    return d;
+  }
   if constexpr (MODEL == QAP) {
     // O(n) deltas: evaluate only the k steps that count
     const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
@@ -936,7 +1144,8 @@ __device__ __forceinline__ long long candidate_perm(const View &X, const PermEl 
         ops[t] = wpick(W.cop, W.Wop, R.x);
         cm.m[t] = X.t3 ? perm_decode<true>(ops[t], R.y, R.z, X.len)
                        : perm_decode<false>(ops[t], R.y, R.z, X.len);
-        d += qap_step(X, sol, cm.m[t], cm.m[0], cm.m[1], t);
+        d += ops[t] == SWAP ? qap_step(X, sol, cm.m[t], cm.m[0], cm.m[1], t)
+                            : qap_block_step(X, sol, cm.m[t], cm.m[0], cm.m[1], t);
       }
     }
     rec = stats_record(ops[0], ops[1], ops[2], k, d < 0);
@@ -1435,8 +1644,7 @@ __device__ __noinline__ int window_migrate(const KInst &I, const View X, unsigne
     if (G.tig == 0) scal[ls] = sc;
     G.sync();
     aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
-    if constexpr (MODEL == CVRPTW)
-      cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, X.wl > 0), G);
+    model_aux_build<MODEL>(X, sol, smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, G);
   }
   if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
     return -1;
@@ -1485,7 +1693,7 @@ __device__ __forceinline__ long long group_sum(long long v, const Group &G, Part
 template <int MODEL, int NW>
 __device__ long long child_cost(const KInst &I, const int32_t *x, const Group &G, Partial *part) {
   const int n = I.n, lane = threadIdx.x & 31;
-  if constexpr (MODEL == TSP) {
+  if constexpr (MODEL == TSP || MODEL == ATSP) {
     long long s = 0;
     for (int k = G.tig; k < n; k += G.nthr)
       s += I.mat0[(size_t)__ldcg(x + k) * n + __ldcg(x + (k + 1 == n ? 0 : k + 1))];
@@ -1541,7 +1749,7 @@ __device__ __noinline__ int window_cross(const KInst &I, const View X, unsigned 
                                          const Layout Lo, const Group G, int p0, int mine,
                                          int ngroups, uint32_t g, uint64_t T, uint32_t nb,
                                          uint64_t timeout_ns, int nact, bool more) {
-  constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW);
+  constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW || MODEL == ATSP);
   using El = typename SolEl<MODEL>::T;
   const int lane = threadIdx.x & 31, len = I.len, P = I.P;
   DevSync *S = I.sync;
@@ -1632,8 +1840,7 @@ __device__ __noinline__ int window_cross(const KInst &I, const View X, unsigned 
       if (G.tig == 0) scal[ls] = sc;
       G.sync();
       aux_init(MODEL, X, A, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
-      if constexpr (MODEL == CVRPTW)
-        cv_build(X, A, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, X.wl > 0), G);
+      model_aux_build<MODEL>(X, A, smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, G);
     }
   }
   if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
@@ -1671,7 +1878,7 @@ template <int MODEL, bool T16, int WPM, int NS, bool XF>
 __device__ void evolve_members(const KInst &I, const View &X, unsigned char *smem, const Layout &Lo,
                                int p0, int nsol, int warps, uint64_t timeout_ns) {
   constexpr int NO = Enc<MODEL>::NO;
-  constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW);
+  constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW || MODEL == ATSP);
   using El = typename SolEl<MODEL>::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // a member group: NS generation slots of WPM warps each (slot s evaluates
@@ -1710,8 +1917,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     }
     G.sync();
     aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
-    if constexpr (MODEL == CVRPTW)
-      cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, X.wl > 0), G);
+    model_aux_build<MODEL>(X, sol, smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, G);
   }
 
   // instance-wide scalars (identical in every warp)
@@ -1963,7 +2169,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
           if (acc) {
             if constexpr (PERM) {
               apply_perm(sol, scr, mv[w], G);
-              if constexpr (MODEL == CVRPTW) cv_build(X, sol, cva, G);
+              model_aux_build<MODEL>(X, sol, (unsigned char *)cva.cum, len, G);
             }
             else if constexpr (MODEL == KNAPSACK) apply_knap(X, sol, W, c, p, gs, G, sc.aw, sc.av);
             else apply_gap(X, sol, loads, W, c, p, gs, G);
@@ -2127,8 +2333,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         if (G.tig == 0) scal[lw] = sc;
         G.sync();
         aux_init(MODEL, X, sol, &scal[lw], (long long *)(smem + Lo.load_off) + (int64_t)lw * X.m, G);
-        if constexpr (MODEL == CVRPTW)
-          cv_build(X, sol, cv_aux_at(smem + Lo.aux_off + (int64_t)lw * Lo.aux_stride, len, X.wl > 0), G);
+        model_aux_build<MODEL>(X, sol, smem + Lo.aux_off + (int64_t)lw * Lo.aux_stride, len, G);
       }
       if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
         return;
@@ -2235,6 +2440,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.node = I.node;
   X.cv32 = I.cv32 != 0;
   X.t3 = ((I.enabled >> THREE_OPT) & 1u) != 0;
+  X.t16 = I.tri16 != 0;
   X.seg = ((I.enabled >> SEGMENT) & 1u) != 0;
   X.lam1 = I.lam1;
   X.wd = I.wdist;
@@ -2251,6 +2457,9 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   switch (I.model) {
     case TSP:
       X.tri = copy(I.tri, (int64_t)I.n * (I.n + 1) / 2 * (I.tri16 ? 2 : 4), 0);
+      break;
+    case ATSP:
+      X.tri = copy(I.tri, (int64_t)I.n * I.n * (I.tri16 ? 2 : 4), 0);
       break;
     case QAP: {
       // rows re-strided to an odd length so that lanes reading different rows
@@ -2374,6 +2583,7 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
   long long s = 0;
   switch (I.model) {
     case TSP:
+    case ATSP:
       for (int k = 0; k < n; ++k) s += I.mat0[(size_t)x[k] * n + x[(k + 1) % n]];
       return s;
     case QAP:
@@ -2427,7 +2637,7 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
 __device__ void random_start(const KInst &I, int p, int32_t *x) {
   const int len = I.len;
   const uint32_t k0 = (uint32_t)I.seed, k1 = (uint32_t)(I.seed >> 32);
-  const bool perm = (I.model == TSP || I.model == QAP || I.model == CVRPTW);
+  const bool perm = (I.model == TSP || I.model == QAP || I.model == CVRPTW || I.model == ATSP);
   if (perm) {
     for (int i = 0; i < len; ++i) x[i] = i;
     uint4 R = make_uint4(0, 0, 0, 0);
@@ -2699,8 +2909,11 @@ cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri, 
 template <int MODEL, bool T16, bool XF>
 static const void *evolve_fn(int wpm, int ns) {
   // three or four generations in flight: one candidate per lane of 4 warps
-  if (ns == 4) return wpm == 4 ? (const void *)evolve_kernel<MODEL, T16, 4, 4, XF> : nullptr;
-  if (ns == 3) return wpm == 4 ? (const void *)evolve_kernel<MODEL, T16, 4, 3, XF> : nullptr;
+  // (not built for ATSP)
+  if constexpr (MODEL != ATSP) {
+    if (ns == 4) return wpm == 4 ? (const void *)evolve_kernel<MODEL, T16, 4, 4, XF> : nullptr;
+    if (ns == 3) return wpm == 4 ? (const void *)evolve_kernel<MODEL, T16, 4, 3, XF> : nullptr;
+  }
   if (ns != 1 && ns != 2) return nullptr;
   if (ns == 2) {
     if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2, XF>;
@@ -2724,6 +2937,9 @@ static const void *pick_evolve(const KInst &h, int wpm, int ns) {
     case CVRPTW: return evolve_fn<CVRPTW, false, false>(wpm, ns);
     case KNAPSACK: return evolve_fn<KNAPSACK, false, false>(wpm, ns);
     case GAP: return evolve_fn<GAP, false, false>(wpm, ns);
+    case ATSP:  // one or two generations in flight
+      if (ns > 2) return nullptr;
+      return h.tri16 ? evolve_fn<ATSP, true, false>(wpm, ns) : evolve_fn<ATSP, false, false>(wpm, ns);
   }
   return nullptr;
 }
@@ -2800,6 +3016,7 @@ static const void *pick_batch(int model, int tri16, int xf, int wpm) {
     case CVRPTW: return batch_fn<CVRPTW, false>(wpm);
     case KNAPSACK: return batch_fn<KNAPSACK, false>(wpm);
     case GAP: return batch_fn<GAP, false>(wpm);
+    case ATSP: return tri16 ? batch_fn<ATSP, true>(wpm) : batch_fn<ATSP, false>(wpm);
   }
   return nullptr;
 }
@@ -2869,6 +3086,7 @@ const void *pick_batch_xf(int model, int tri16, int wpm) {
     case CVRPTW: return batch_fn_xf<CVRPTW, false>(wpm);
     case KNAPSACK: return batch_fn_xf<KNAPSACK, false>(wpm);
     case GAP: return batch_fn_xf<GAP, false>(wpm);
+    case ATSP: return tri16 ? batch_fn_xf<ATSP, true>(wpm) : batch_fn_xf<ATSP, false>(wpm);
   }
   return nullptr;
 }
@@ -2880,6 +3098,7 @@ const void *pick_evolve_xf(int model, int tri16, int wpm, int ns) {
     case CVRPTW: return evolve_fn_xf<CVRPTW, false>(wpm, ns);
     case KNAPSACK: return evolve_fn_xf<KNAPSACK, false>(wpm, ns);
     case GAP: return evolve_fn_xf<GAP, false>(wpm, ns);
+    case ATSP: return tri16 ? evolve_fn_xf<ATSP, true>(wpm, ns) : evolve_fn_xf<ATSP, false>(wpm, ns);
   }
   return nullptr;
 }

@@ -94,7 +94,10 @@ int64_t request_bytes(const cgo_problem *p, const cgo_params &q) {
   const int64_t P = q.population, len = p->len;
   int64_t data = 0;
   switch (p->model) {
-    case TSP: data = (int64_t)p->n * p->n * 4 + (int64_t)p->n * (p->n + 1) / 2 * (p->tri16 ? 2 : 4); break;
+    case TSP:
+      data = (int64_t)p->n * p->n * 4 +
+             (p->asym ? (int64_t)p->n * p->n : (int64_t)p->n * (p->n + 1) / 2) * (p->tri16 ? 2 : 4);
+      break;
     case QAP: data = 2ll * p->n * p->n * 4; break;
     case KNAPSACK: data = 2ll * p->n * 4; break;
     case GAP: data = 2ll * p->m * p->n * 4 + 4ll * p->m; break;
@@ -229,7 +232,7 @@ void server_loop(cgo_server *S) {
       int wpm = 1, warps = 1;
       int64_t need = 0, cls = 0;
       if (batch_shape(p, r->params, h, &wpm, &warps, &need, &cls) != CGO_OK ||
-          (r->bucket = bucket_for(S, p->model, p->tri16, takes_xf(h), wpm, warps, cls)) < 0) {
+          (r->bucket = bucket_for(S, h.model, p->tri16, takes_xf(h), wpm, warps, cls)) < 0) {
         fail_all(S, CGO_ERR_UNSUPPORTED, "no batched launch shape for a request");
         return;
       }

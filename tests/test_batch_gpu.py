@@ -80,6 +80,12 @@ def mixed_batch():
     # weighted CVRPTW objectives (vehicles first)
     items.append((dict(I.cvrptw(18, 264, vehicles=5, capacity=90), tag=54, weight_vehicles=10 ** 6),
                   dict(P=6, C=48, G=22)))
+    # asymmetric TSP (the full matrix, piece deltas) and QAP with every
+    # permutation operator
+    items.append((dict(I.tsp_asym(35, 268), tag=58), dict(P=6, C=64, G=27, U=4, cross_q16=30000)))
+    items.append((dict(I.tsp_asym(80, 269, skew=50000), tag=59),
+                  dict(P=5, C=48, G=19, ops=[0, 1, 2, 3, O.THREE_OPT])))
+    items.append((dict(I.qap_random(13, 270), tag=60), dict(P=5, C=48, G=21, ops=[0, 1, 2, 3, O.THREE_OPT])))
     return items
 
 

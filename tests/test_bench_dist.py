@@ -62,7 +62,7 @@ def test_extra_operator_masks_per_model():
     import instances as I
     assert bench.extra_ops_mask(I.TSP, "three_opt,segment") == 1 << bench.O_THREE_OPT
     assert bench.extra_ops_mask(I.CVRPTW, "three_opt") == 1 << bench.O_THREE_OPT
-    assert bench.extra_ops_mask(I.QAP, "three_opt") == 0          # the QAP path is swap-only
+    assert bench.extra_ops_mask(I.QAP, "three_opt") == 1 << bench.O_THREE_OPT
     assert bench.extra_ops_mask(I.KNAPSACK, "segment,three_opt") == 1 << bench.O_SEGMENT
     assert bench.extra_ops_mask(I.GAP, "segment") == 1 << bench.O_SEGMENT
     assert bench.extra_ops_mask(I.TSP, "") == 0

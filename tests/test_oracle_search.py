@@ -130,6 +130,34 @@ def test_tsp_reaches_bruteforce_optimum(seed):
     assert st["best_cost"].min() == opt
 
 
+def test_asymmetric_tsp_cost_follows_the_tour_direction():
+    # an asymmetric matrix: a tour and its reverse cost differently, each the
+    # sum of its directed edges
+    inst = I.tsp_asym(7, 3)
+    D = inst["mat0"]
+    t = [0, 3, 1, 6, 2, 5, 4]
+    fwd = sum(int(D[t[k]][t[(k + 1) % 7]]) for k in range(7))
+    bwd = sum(int(D[t[(k + 1) % 7]][t[k]]) for k in range(7))
+    assert fwd != bwd
+    assert O.cost(inst, t) == fwd
+    assert O.cost(inst, t[::-1]) == bwd
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_asymmetric_tsp_reaches_bruteforce_optimum(seed):
+    # every permutation operator, 2-opt and 3-opt included, on a matrix where
+    # reversing a piece changes its inner edges
+    inst = I.tsp_asym(8, 102)
+    opt = bf_tsp(inst["mat0"])
+    p = equal_weights(O.default_params(inst),
+                      [O.SWAP, O.TWO_OPT, O.INSERT, O.OR_OPT, O.THREE_OPT])
+    p.update(P=8, C=32)
+    st = _run(inst, p, seed, 300)
+    assert st["best_cost"].min() == opt
+    x = st["best_sol"][int(np.argmin(st["best_cost"]))]
+    assert O.cost(inst, x) == opt
+
+
 @pytest.mark.parametrize("seed", SEEDS)
 def test_qap_reaches_bruteforce_optimum(seed):
     inst = I.qap_random(7, 101)            # asymmetric, non-zero diagonals

@@ -211,6 +211,54 @@ def test_tsp_staging_modes(cgo, staging):
     assert_same_state(g, o, "staging %d" % staging)
 
 
+# ------------------------------------------------------- asymmetric TSP
+@pytest.mark.parametrize("ns", [1, 2])
+@pytest.mark.parametrize("n,skew", [(2, 50), (3, 50), (4, 300), (5, 300), (9, 300), (40, 300),
+                                    (40, 60000)])
+def test_atsp_all_operators(cgo, n, skew, ns):
+    """TSP of an asymmetric matrix: every operator alone and composed, the
+    candidate's tour as pieces of the current one over prefix sums of its
+    forward and backward edge costs; 16-bit and (skew 60000) 32-bit entries."""
+    inst = I.tsp_asym(n, 40 + n, skew=skew)
+    assert (inst["mat0"] != inst["mat0"].T).any()
+    p = params_for(inst, P=5, C=40, G=37, U=3, ops=[SW, TO, INS, OR, TH], T0=60 << 32)
+    _, g, o = run_both(cgo, inst, p, 3, wpm=2 if ns == 2 else 0, ns=ns)
+    assert_same_state(g, o, "atsp n=%d skew=%d ns=%d" % (n, skew, ns))
+
+
+@pytest.mark.parametrize("op", [SW, TO, INS, OR, TH])
+@pytest.mark.parametrize("kw", [(65536, 0, 0), (0, 65536, 0), (0, 0, 65536)])
+def test_atsp_each_op_each_k(cgo, op, kw):
+    inst = I.tsp_asym(17, 41)
+    p = params_for(inst, P=4, C=64, G=30, U=5, ops=[op], w_k=list(kw), stag_limit=0)
+    prob, g, o = run_both(cgo, inst, p, 9)
+    assert_same_state(g, o, "atsp op %d k %s" % (op, kw))
+    assert_same_counts(prob, o, "atsp op %d k %s" % (op, kw))
+
+
+@pytest.mark.parametrize("staging", [1, 2])
+@pytest.mark.parametrize("warps,wpm", [(0, 0), (2, 1), (8, 2), (8, 4)])
+def test_atsp_staging_and_launch_shape(cgo, staging, warps, wpm):
+    """The full matrix in shared or in global memory; one to eight member
+    groups per CTA; elite injection, crossover, heuristic starts and islands
+    (each rebuilds the prefix sums of the members it replaces)."""
+    inst = I.tsp_asym(60, 42)
+    p = params_for(inst, P=12, C=96, G=41, U=4, elite_period=8, cross_q16=40000,
+                   init_heuristic=1, islands=3, migrate_period=8, migrate_strategy=1, migrate_n=2)
+    _, g, o = run_both(cgo, inst, p, 4, warps=warps, staging=staging, wpm=wpm)
+    assert_same_state(g, o, "atsp staging %d warps %d wpm %d" % (staging, warps, wpm))
+
+
+def test_atsp_large_global_matrix(cgo):
+    """n = 300: the 180 KB matrix of 16-bit entries; continued launches."""
+    inst = I.tsp_asym(300, 43)
+    p = params_for(inst, P=16, C=128, G=25, U=5)
+    prob, g, o = run_both(cgo, inst, p, 6)
+    assert_same_state(g, o, "atsp300")
+    prob.solve_continue(14)
+    assert_same_state(prob.state(), oracle_run(inst, p, 6, 39), "atsp300 continued")
+
+
 def test_tsp_wide_distances_int32_triangle(cgo):
     inst = I.tsp_uniform(30, 25, box=100000)     # distances > 32767
     assert inst["mat0"].max() > 32767
@@ -277,12 +325,27 @@ def test_qap64_grid_prefix(cgo):
     assert_same_state(g, o, "qap64")
 
 
-def test_qap_rejects_other_operators(cgo):
-    inst = I.qap_random(6, 39)
-    prob = cgo.Problem(inst)
-    with pytest.raises(cgo.CgoError) as e:
-        prob.solve(params_for(inst, P=2, C=8, G=1, ops=[SW, TO]), 1)
-    assert e.value.status == cgo.ERR_UNSUPPORTED
+@pytest.mark.parametrize("ops", [[TO], [INS], [OR], [TH], [SW, TO, INS, OR, TH]])
+@pytest.mark.parametrize("kw", [(65536, 0, 0), (0, 0, 65536), None])
+def test_qap_every_permutation_operator(cgo, ops, kw):
+    """QAP with 2-opt, insertion, or-opt and 3-opt beside the swap: a block
+    move's exact delta over the positions it changes (asymmetric F and D with
+    a nonzero diagonal), alone and in k-step composites."""
+    inst = I.qap_random(11, 39)
+    over = dict(P=5, C=40, G=19, U=4, ops=ops, T0=20 << 32)
+    if kw:
+        over.update(w_k=list(kw), stag_limit=0)
+    p = params_for(inst, **over)
+    for ns, wpm in ((1, 1), (2, 2)):
+        _, g, o = run_both(cgo, inst, p, 6, wpm=wpm, ns=ns)
+        assert_same_state(g, o, "qap ops %s k %s ns %d" % (ops, kw, ns))
+
+
+def test_qap_grid_block_moves(cgo):
+    inst = I.qap_grid(36, 5)
+    p = params_for(inst, P=8, C=64, G=12, ops=[SW, TO, INS, OR])
+    _, g, o = run_both(cgo, inst, p, 2)
+    assert_same_state(g, o, "qap36 block moves")
 
 
 # ---------------------------------------------------------------- knapsack
@@ -505,7 +568,8 @@ def test_islands_degenerate_shapes(cgo):
 
 
 # ------------------------------------------------------------------ crossover
-CROSS_CASES = [(I.tsp_uniform(30, 320), None), (I.qap_random(11, 321), [SW]),
+CROSS_CASES = [(I.tsp_uniform(30, 320), None), (I.qap_random(11, 321), None),
+               (I.tsp_asym(30, 329), None),
                (I.knapsack(60, 322), None), (I.gap(25, 323, m=4), None),
                (I.cvrptw(14, 324, vehicles=4, capacity=70), None)]
 
@@ -833,10 +897,15 @@ def test_invalid_inputs(cgo):
     with pytest.raises(cgo.CgoError) as e:
         prob.solve(params_for(inst, P=4, C=8, G=1, U=4, elite_period=6), 1)
     assert e.value.status == cgo.ERR_UNSUPPORTED
-    asym = dict(inst, mat0=inst["mat0"] + np.triu(np.ones_like(inst["mat0"]), 1))
-    with pytest.raises(cgo.CgoError) as e:
-        cgo.Problem(asym)
-    assert e.value.status == cgo.ERR_UNSUPPORTED
     with pytest.raises(cgo.CgoError) as e:
         prob.best()
     assert e.value.status == cgo.ERR_STATE
+
+
+def test_atsp_refuses_three_generations_in_flight(cgo):
+    inst = I.tsp_asym(20, 44)
+    prob = cgo.Problem(inst)
+    prob.set_launch(12, 0, 4, 3)
+    with pytest.raises(cgo.CgoError) as e:
+        prob.solve(params_for(inst, P=2, C=64, G=3), 1)
+    assert e.value.status == cgo.ERR_UNSUPPORTED

@@ -57,6 +57,9 @@ def request_mix():
         # the row level (routes as rows) beside the permutation operators
         (dict(I.cvrptw(18, 314, vehicles=6, capacity=80), tag=15),
          dict(P=6, C=64, G=26, U=4, ops=[O.SWAP, O.INSERT, O.OR_OPT] + [O.ROW_SWAP_OP, O.ROW_MERGE_OP, O.ROW_SPLIT_OP])),
+        # asymmetric TSP; QAP with block moves
+        (dict(I.tsp_asym(40, 316), tag=17), dict(P=6, C=64, G=25, U=4)),
+        (dict(I.qap_random(10, 317), tag=18), dict(P=5, C=48, G=23, ops=[O.TWO_OPT, O.INSERT, O.OR_OPT])),
     ]
 
 

@@ -86,3 +86,14 @@ def test_static_solve_rejects_oversized_requests(env):
     rc, _, _ = _static_solve(torch, cgo, inst, p, 1)
     assert rc == cgo.ERR_INVALID
     assert b"scratch" in cgo.lib().cgo_last_error()
+
+
+def test_static_solve_refuses_an_asymmetric_matrix(env):
+    # the fixed array holds the triangle of a symmetric matrix; cgo_solve
+    # takes the asymmetric case
+    torch, cgo = env
+    inst = I.tsp_asym(30, 4)
+    p = params_for(inst, P=8, C=32, G=5)
+    rc, _, _ = _static_solve(torch, cgo, inst, p, 1)
+    assert rc == cgo.ERR_UNSUPPORTED
+    assert b"symmetric" in cgo.lib().cgo_last_error()
