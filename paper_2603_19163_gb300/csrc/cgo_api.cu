@@ -192,12 +192,13 @@ void heuristic_perms(const std::vector<int32_t> &M, int64_t n, std::vector<int32
 }
 
 // rows of the scratch solution buffer: the start pool's entries (0: plain
-// start), or one crossover child per member, whichever is more
+// start), or with crossover three rows per member (its child, and its best
+// as a crossover parent in two alternating rows), whichever is more
 int64_t pool_size(const cgo_problem *p, const cgo_params &q) {
   const int64_t K = q.init_oversample > 1 ? q.init_oversample : 1;
   const int64_t H = q.init_heuristic ? p->n_heur : 0;
   const int64_t pool = (K > 1 || H > 0) ? K * q.population + H : 0;
-  const int64_t cross = (q.cross_q16 > 0 && q.population >= 2) ? q.population : 0;
+  const int64_t cross = (q.cross_q16 > 0 && q.population >= 2) ? 3 * (int64_t)q.population : 0;
   return pool > cross ? pool : cross;
 }
 
@@ -492,8 +493,9 @@ cgo_status check_sync_error(cgo_problem *p, cudaStream_t st) {
 cgo_status run_generations(cgo_problem *p, int64_t G, cudaStream_t st) {
   if (G == 0) return CGO_OK;
   if (p->g + G >= 0xFFFFFFFFll) return fail(CGO_ERR_INVALID, "generation index would exceed 2^32 - 2");
-  // crossover children need one scratch row per member
-  if (p->params.cross_q16 > 0 && p->params.population >= 2 && p->pool_cap < p->params.population)
+  // crossover needs three scratch rows per member
+  if (p->params.cross_q16 > 0 && p->params.population >= 2 &&
+      p->pool_cap < 3 * (int64_t)p->params.population)
     return fail(CGO_ERR_STATE, "no crossover buffer for this population");
   KInst h = base_kinst(p);
   int warps = 0, wpm = 1, ns = 1;

@@ -98,10 +98,12 @@ struct KInst {
   // islands and migration
   int32_t islands, mstrat;
   uint32_t mperiod, mN;
-  // crossover probability per window (Q16); children go to pool_sol (P x len)
+  // crossover probability per window (Q16); pool_sol rows 0..P-1 hold the
+  // children of models without a shared-memory child, rows P..3P-1 the
+  // members' bests as crossover parents (two alternating sets of P rows)
   uint32_t cross_q16;
   const int32_t *heur;        // n_heur x n
-  int32_t *pool_sol;          // (K*P + n_heur) x len; crossover children (P x len)
+  int32_t *pool_sol;          // (K*P + n_heur) x len, or 3P x len with crossover
   int64_t *pool_cost;
 };
 

@@ -53,7 +53,8 @@ struct SolScal {
 };
 
 struct Layout {
-  int64_t inst, sol_off, sol_stride, scr_off, scal_off, load_off, aux_off, aux_stride, part_off, total;
+  int64_t inst, sol_off, sol_stride, scr_off, scr_stride, scal_off, snap_off, load_off, aux_off,
+      aux_stride, part_off, total;
 };
 
 __host__ __device__ inline int64_t align16(int64_t x) { return (x + 15) & ~int64_t(15); }
@@ -76,7 +77,9 @@ __host__ __device__ inline int64_t cv_aux_bytes(int len, bool cvmax = false) {
 }
 
 // Shared memory of one CTA: [instance data][members' solutions][one scratch
-// array per member group][member scalars][GAP loads][CVRPTW route caches]
+// array per member group (permutations: a solution row and a bitmask)]
+// [member scalars][parent-row costs][GAP loads][CVRPTW route caches / ATSP
+// prefix sums]
 // [per-group partials]
 __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m, int nsol,
                                               int warps, int wpm, int model, bool cvmax = false) {
@@ -87,8 +90,12 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   L.sol_off = L.inst;
   L.scr_off = L.sol_off + (int64_t)nsol * L.sol_stride;
   const bool perm = (model == TSP || model == QAP || model == CVRPTW || model == ATSP);
-  L.scal_off = L.scr_off + (perm ? (int64_t)groups * L.sol_stride : 0);
-  L.load_off = L.scal_off + align16((int64_t)nsol * 32);
+  // a permutation's scratch row, then a bitmask of len bits (crossover)
+  L.scr_stride = perm ? L.sol_stride + align16(4 * (int64_t)((len + 31) / 32)) : 0;
+  L.scal_off = L.scr_off + (int64_t)groups * L.scr_stride;
+  // per member, the best cost held by each of its two crossover-parent rows
+  L.snap_off = L.scal_off + align16((int64_t)nsol * 32);
+  L.load_off = L.snap_off + align16((int64_t)nsol * 16);
   L.aux_off = L.load_off + (model == GAP ? align16((int64_t)nsol * m * 8) : 0);
   L.aux_stride = model == CVRPTW ? cv_aux_bytes(len, cvmax)
                                  : (model == ATSP ? align16(16 * (int64_t)(len + 1)) : 0);
@@ -1577,6 +1584,33 @@ struct __align__(16) Partial {
 
 __device__ long long full_cost(const KInst &I, const int32_t *x);
 
+// [R29] the crossover parents of a window: each member's best solution as
+// it stands at the barrier before the crossovers, in the parent row of the
+// window's parity (rows P + b*P + p of the scratch buffer).  The search
+// writes a best that it lowers into the coming window's row at once; this
+// copies the best in only when the row does not hold it yet (a best changes
+// only by decreasing, so its cost identifies it).  A row of parity b is read
+// by the crossovers of one window and written again only after the barrier
+// of the next window, which every member reaches once its reads are over;
+// so no barrier is needed after the crossovers themselves.
+__device__ void snapshot_best(const KInst &I, unsigned char *smem, const Layout &Lo, const Group &G,
+                              int p0, int mine, int ngroups, uint32_t b) {
+  const SolScal *scal = (const SolScal *)(smem + Lo.scal_off);
+  long long *snap = (long long *)(smem + Lo.snap_off);
+  const int len = I.len;
+  for (int e = 0; e < mine; ++e) {
+    const int ls = G.grp + e * ngroups, p = p0 + ls;
+    const long long bc = scal[ls].best;
+    if (snap[2 * ls + (int)b] == bc) continue;
+    const int32_t *src = I.bestsol + (int64_t)p * len;
+    int32_t *dst = I.pool_sol + ((int64_t)I.P * (1 + (int64_t)b) + p) * len;
+    for (int i = G.tig; i < len; i += G.nthr) dst[i] = __ldcg(src + i);
+    G.sync();
+    if (G.tig == 0) snap[2 * ls + (int)b] = bc;
+  }
+  G.sync();
+}
+
 // [R27] migration at a window end (its two phases and barriers), kept out of
 // line so that the generation loop's register allocation does not carry it.
 // Returns the number of barriers passed, or -1 when one timed out.
@@ -1584,7 +1618,7 @@ template <int MODEL, int NW>
 __device__ __noinline__ int window_migrate(const KInst &I, const View X, unsigned char *smem,
                                            const Layout Lo, const Group G, int p0, int mine,
                                            int ngroups, uint32_t g, uint32_t nb,
-                                           uint64_t timeout_ns, int nact, bool more) {
+                                           uint64_t timeout_ns, int nact, bool more, bool snap) {
   using El = typename SolEl<MODEL>::T;
   const int lane = threadIdx.x & 31, len = I.len, P = I.P;
   DevSync *S = I.sync;
@@ -1665,6 +1699,8 @@ __device__ __noinline__ int window_migrate(const KInst &I, const View X, unsigne
       I.best[p0 + ls] = scal[ls].best;
     }
   }
+  // crossovers follow: their parents are the bests after migration
+  if (snap) snapshot_best(I, smem, Lo, G, p0, mine, ngroups, (g / I.U) & 1u);
   if (more) {
     if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
       return -1;
@@ -1688,25 +1724,13 @@ __device__ __forceinline__ long long group_sum(long long v, const Group &G, Part
   return t;
 }
 
-// exact cost of a crossover child held in global memory (R16), computed by
-// the member group together; a CVRPTW route walk is serial (one thread)
+// exact cost of a binary or integer crossover child held in global memory
+// (R16), computed by the member group together
 template <int MODEL, int NW>
 __device__ long long child_cost(const KInst &I, const int32_t *x, const Group &G, Partial *part) {
   const int n = I.n, lane = threadIdx.x & 31;
-  if constexpr (MODEL == TSP || MODEL == ATSP) {
-    long long s = 0;
-    for (int k = G.tig; k < n; k += G.nthr)
-      s += I.mat0[(size_t)__ldcg(x + k) * n + __ldcg(x + (k + 1 == n ? 0 : k + 1))];
-    return group_sum<NW>(s, G, part);
-  } else if constexpr (MODEL == QAP) {
-    long long s = 0;
-    for (int i = G.tig; i < n; i += G.nthr) {
-      const int xi = __ldcg(x + i);
-      for (int j = 0; j < n; ++j)
-        s += (long long)I.mat0[(size_t)i * n + j] * I.mat1[(size_t)xi * n + __ldcg(x + j)];
-    }
-    return group_sum<NW>(s, G, part);
-  } else if constexpr (MODEL == KNAPSACK) {
+  static_assert(MODEL == KNAPSACK || MODEL == GAP, "permutation children are costed by perm_cost");
+  if constexpr (MODEL == KNAPSACK) {
     long long W = 0, V = 0;
     for (int k = G.tig; k < n; k += G.nthr)
       if (__ldcg(x + k)) {
@@ -1733,93 +1757,187 @@ __device__ long long child_cost(const KInst &I, const int32_t *x, const Group &G
     // every lane of a warp holds its warp's penalty sum; count it once
     pen = group_sum<NW>(lane == 0 ? pen : 0, G, part);
     return s + I.lam0 * pen;
-  } else {
-    if (G.tig == 0) part[0].d = full_cost(I, x);
-    G.sync();
-    const long long c = part[0].d;
-    G.sync();
-    return c;
   }
 }
 
-// [R29] crossover at a window end (both phases and barriers), out of line
-// like migration.  Returns the number of barriers passed, or -1.
+// largest of one value over a member group (every thread gets it)
+template <int NW>
+__device__ __forceinline__ long long group_max(long long v, const Group &G, Partial *part) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v = max(v, __shfl_xor_sync(kFull, v, off));
+  G.sync();
+  if ((threadIdx.x & 31) == 0) part[G.gw].d = v;
+  G.sync();
+  long long t = LLONG_MIN;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) t = max(t, part[w].d);
+  G.sync();
+  return t;
+}
+
+// exact cost (R16) of a permutation held in shared memory, read through the
+// kernel's view of the instance, computed by the member group together;
+// CVRPTW's routes are walked in parallel (one thread per route)
 template <int MODEL, int NW>
-__device__ __noinline__ int window_cross(const KInst &I, const View X, unsigned char *smem,
-                                         const Layout Lo, const Group G, int p0, int mine,
-                                         int ngroups, uint32_t g, uint64_t T, uint32_t nb,
-                                         uint64_t timeout_ns, int nact, bool more) {
+__device__ long long perm_cost(const View &X, const PermEl *x, const Group &G, Partial *part) {
+  const int len = X.len;
+  long long s = 0;
+  if constexpr (MODEL == TSP) {
+    for (int k = G.tig; k < len; k += G.nthr) {
+      const int a = (int)x[k], b = (int)x[k + 1 == len ? 0 : k + 1];
+      const int lo = min(a, b), hi = max(a, b);
+      const uint32_t i = (((uint32_t)lo * (uint32_t)(X.n2m1 - lo)) >> 1) + (uint32_t)hi;
+      s += X.t16 ? (long long)((const int16_t *)X.tri)[i] : (long long)((const int32_t *)X.tri)[i];
+    }
+    return group_sum<NW>(s, G, part);
+  } else if constexpr (MODEL == ATSP) {
+    for (int k = G.tig; k < len; k += G.nthr) {
+      const int a = (int)x[k], b = (int)x[k + 1 == len ? 0 : k + 1];
+      s += X.t16 ? dfull<true>(X, a, b) : dfull<false>(X, a, b);
+    }
+    return group_sum<NW>(s, G, part);
+  } else if constexpr (MODEL == QAP) {
+    const int n = X.n, qs = X.qs;
+    for (int i = G.tig; i < n; i += G.nthr) {
+      const int32_t *Fi = X.F + (size_t)i * qs, *Dx = X.D + (size_t)x[i] * qs;
+      for (int j = 0; j < n; ++j) s += (long long)Fi[j] * (long long)Dx[x[j]];
+    }
+    return group_sum<NW>(s, G, part);
+  } else {
+    static_assert(MODEL == CVRPTW, "permutation models only");
+    const int n = X.n;
+    long long mx = 0;
+    for (int q = G.tig; q < len; q += G.nthr) {
+      if ((q == 0 || (int)x[q - 1] >= n) && (int)x[q] < n) {
+        int e = q + 1;
+        while (e < len && (int)x[e] < n) ++e;
+        long long rd = 0;
+        s += cvrptw_routes(X, [&](int r) { return (int)x[r]; }, q, e, X.cv32, Jumps(),
+                           X.wl > 0 ? &rd : nullptr);
+        mx = max(mx, rd);
+      }
+    }
+    s = group_sum<NW>(s, G, part);
+    if (X.wl > 0) s += X.wl * group_max<NW>(mx, G, part);
+    return s;
+  }
+}
+
+// [R29] crossover at a window end, out of line like migration: each member
+// crosses, with probability cross_q16 / 2^16, with another member's best as
+// it stood before the window's crossovers (its parent row).  A permutation
+// child is built and costed in the group's shared scratch row; the others
+// in the member's global scratch row.  A best lowered by a child is written
+// at once (also into the member's other parent row).  The caller calls it
+// only for groups with a member that crosses; it is inlined (an out-of-line
+// call saves registers to local memory, which beside a large shared-memory
+// instance spills to L2).
+template <int MODEL, int NW>
+__device__ __forceinline__ void window_cross(const KInst &I, const View X, unsigned char *smem,
+                                          const Layout Lo, const Group G, int p0, int mine,
+                                          int ngroups, uint32_t g, uint64_t T, uint4 R0) {
   constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW || MODEL == ATSP);
   using El = typename SolEl<MODEL>::T;
   const int lane = threadIdx.x & 31, len = I.len, P = I.P;
-  DevSync *S = I.sync;
   SolScal *scal = (SolScal *)(smem + Lo.scal_off);
-  El *scr = (El *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.sol_stride);
+  El *scr = (El *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.scr_stride);
   unsigned char *gmem = smem + Lo.part_off + (int64_t)G.grp * group_bytes(NW);
   Partial *part = (Partial *)gmem;
-  int *flag = (int *)(gmem + 2 * NW * sizeof(Partial));
-  const uint32_t nb0 = nb;
-  // [R29] crossover of every member, with probability cross_q16 / 2^16,
-  // with another member's best solution as it stood at the window end.
-  // Phase 1 builds each child in the member's global scratch row, costs
-  // it and takes it into shared memory if the Metropolis rule accepts it;
-  // phase 2, after a barrier, writes the bests the children lowered and
-  // publishes every member's cost and best.
-  const long long *gb = (const long long *)I.best;
+  const uint32_t b = (g / I.U) & 1u;
   int *wt = (int *)part;  // per-warp counts of the order crossover's compaction
   for (int e = 0; e < mine; ++e) {
     const int ls = G.grp + e * ngroups, p = p0 + ls;
-    const uint4 R = philox(ctr_word(0, 0, kKindCross), X.tag, (uint32_t)p, g, X.k0, X.k1);
+    const uint4 R =
+        e == 0 ? R0 : philox(ctr_word(0, 0, kKindCross), X.tag, (uint32_t)p, g, X.k0, X.k1);
     if ((R.x >> 16) >= I.cross_q16) continue;
     int q = p + 1 + posm(R.y >> 16, (uint32_t)(P - 1));
     q -= q >= P ? P : 0;
-    const int32_t *B = I.bestsol + (int64_t)q * len;
-    int32_t *child = I.pool_sol + (int64_t)p * len;
+    const int32_t *B = I.pool_sol + ((int64_t)P * (1 + (int64_t)b) + q) * len;
     El *A = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
+    long long cc;
+    bool took;
     if constexpr (PERM) {
       // order crossover: A[lo..hi] stays; the other positions, from hi+1
       // on (wrapping), take B's elements outside that segment in B's order
+      El *child = scr;
+      uint32_t *mark = (uint32_t *)((unsigned char *)scr + Lo.sol_stride);  // len bits
       int i = posm(R.z >> 16, (uint32_t)len), j = posm(R.z & 0xFFFFu, (uint32_t)(len - 1));
       j += j >= i ? 1 : 0;
       const int lo = min(i, j), hi = max(i, j);
-      unsigned char *mark = (unsigned char *)scr;  // len bytes (the row holds len 16-bit entries)
-      for (int k = G.tig; k < len; k += G.nthr) mark[k] = 0;
-      G.sync();
+      // thread t of the group takes B's positions hi+1+c0+4t .. +3 (wrapping):
+      // the kept ones go, in order, to the child's positions from hi+1 on.
+      // The first chunk's loads are issued before the segment is marked.
+      int el[4];
+      auto load_chunk = [&](int c0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = c0 + 4 * G.tig + u;
+          el[u] = -1;
+          if (idx < len) {
+            int bi = hi + 1 + idx;
+            bi -= bi >= len ? len : 0;
+            el[u] = __ldcg(B + bi);
+          }
+        }
+      };
+      load_chunk(0);
+      // the bitmask is all zero between crossovers (cleared at the load of
+      // the members and after each use)
       for (int k = lo + G.tig; k <= hi; k += G.nthr) {
-        mark[A[k]] = 1;
+        const int a = (int)A[k];
+        atomicOr(&mark[a >> 5], 1u << (a & 31));
         child[k] = A[k];
       }
       G.sync();
       int base = 0;
-      for (int c0 = 0; c0 < len; c0 += G.nthr) {
-        const int idx = c0 + G.tig;
-        int el = 0;
-        bool keep = false;
-        if (idx < len) {
-          int bi = hi + 1 + idx;
-          bi -= bi >= len ? len : 0;
-          el = __ldcg(B + bi);
-          keep = mark[el] == 0;
+      for (int c0 = 0; c0 < len; c0 += 4 * G.nthr) {
+        int cnt = 0;
+        unsigned km = 0u;
+        if (c0 > 0) load_chunk(c0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int a = el[u];
+          if ((unsigned)a < (unsigned)len && !((mark[a >> 5] >> (a & 31)) & 1u)) {
+            km |= 1u << u;
+            ++cnt;
+          }
         }
-        const unsigned bal = __ballot_sync(kFull, keep);
-        if (lane == 0) wt[G.gw] = __popc(bal);
+        int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int v = __shfl_up_sync(kFull, incl, off);
+          if (lane >= off) incl += v;
+        }
+        if (lane == 31) wt[G.gw] = incl;
         G.sync();
-        int off = 0, tot_w = 0;
+        int off = 0, tot = 0;
+#pragma unroll
         for (int w = 0; w < NW; ++w) {
           const int v = wt[w];
           off += w < G.gw ? v : 0;
-          tot_w += v;
+          tot += v;
         }
-        if (keep) {
-          int pos = hi + 1 + base + off + __popc(bal & ((1u << lane) - 1u));
-          pos -= pos >= len ? len : 0;
-          child[pos] = el;
+        int pos = base + off + incl - cnt;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if ((km >> u) & 1u) {
+            int d = hi + 1 + pos;
+            d -= d >= len ? len : 0;
+            child[d] = (El)el[u];
+            ++pos;
+          }
         }
-        base += tot_w;
+        base += tot;
         G.sync();
       }
+      for (int k = lo + G.tig; k <= hi; k += G.nthr) mark[(int)child[k] >> 5] = 0u;
+      cc = perm_cost<MODEL, NW>(X, child, G, part);
+      took = accept_move(cc - scal[ls].cost, T, exp_variate_q32(R.w));
+      if (took)
+        for (int k = G.tig; k < len; k += G.nthr) A[k] = child[k];
     } else {
       // uniform crossover: element k from B where bit k of the stream is set
+      int32_t *child = I.pool_sol + (int64_t)p * len;
       for (int k = G.tig; k < len; k += G.nthr) {
         const uint4 Q = philox(ctr_word((uint32_t)k >> 7, 1, kKindCross), X.tag, (uint32_t)p, g,
                                X.k0, X.k1);
@@ -1827,47 +1945,39 @@ __device__ __noinline__ int window_cross(const KInst &I, const View X, unsigned 
         const uint32_t w = wsel == 0 ? Q.x : wsel == 1 ? Q.y : wsel == 2 ? Q.z : Q.w;
         child[k] = ((w >> (k & 31)) & 1u) ? __ldcg(B + k) : (int32_t)A[k];
       }
+      G.sync();
+      cc = child_cost<MODEL, NW>(I, child, G, part);
+      took = accept_move(cc - scal[ls].cost, T, exp_variate_q32(R.w));
+      if (took)
+        for (int k = G.tig; k < len; k += G.nthr) A[k] = (El)__ldcg(child + k);
     }
-    G.sync();
-    const long long cc = child_cost<MODEL, NW>(I, child, G, part);
-    if (accept_move(cc - scal[ls].cost, T, exp_variate_q32(R.w))) {
-      for (int k = G.tig; k < len; k += G.nthr) A[k] = (El)__ldcg(child + k);
+    if (took) {
       G.sync();
       SolScal sc = scal[ls];
+      const bool lowered = cc < sc.best;
       sc.cost = cc;
       sc.best = min(sc.best, cc);
+      if (lowered) {
+        // the new best to global memory, and into the parent row of the next
+        // crossover window (its readers finished before this window's barrier)
+        int32_t *dst = I.bestsol + (int64_t)p * len;
+        int32_t *pr = I.pool_sol + ((int64_t)P * (2 - (int64_t)b) + p) * len;
+        for (int k = G.tig; k < len; k += G.nthr) {
+          const int32_t v = (int32_t)A[k];
+          dst[k] = v;
+          pr[k] = v;
+        }
+      }
       G.sync();
-      if (G.tig == 0) scal[ls] = sc;
+      if (G.tig == 0) {
+        scal[ls] = sc;
+        if (lowered) ((long long *)(smem + Lo.snap_off))[2 * ls + (1 - (int)b)] = sc.best;
+      }
       G.sync();
       aux_init(MODEL, X, A, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
       model_aux_build<MODEL>(X, A, smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, G);
     }
   }
-  if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
-    return -1;
-  ++nb;
-  for (int e = 0; e < mine; ++e) {
-    const int ls = G.grp + e * ngroups, p = p0 + ls;
-    if (scal[ls].best < ld_relaxed64(gb + p)) {
-      const El *sol = (const El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
-      int32_t *dst = I.bestsol + (int64_t)p * len;
-      for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
-    }
-  }
-  G.sync();
-  if (G.tig == 0) {
-    for (int e = 0; e < mine; ++e) {
-      const int ls = G.grp + e * ngroups;
-      I.cost[p0 + ls] = scal[ls].cost;
-      I.best[p0 + ls] = scal[ls].best;
-    }
-  }
-  if (more) {
-    if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
-      return -1;
-    ++nb;
-  }
-  return (int)(nb - nb0);
 }
 
 // ---------------------------------------------------------- evolve unit
@@ -1896,7 +2006,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   if (mine == 0) return;
   const int len = I.len, P = I.P, C = I.C;
   DevSync *S = I.sync;
-  El *scr = (El *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.sol_stride);
+  El *scr = (El *)(smem + Lo.scr_off + (int64_t)G.grp * Lo.scr_stride);
   SolScal *scal = (SolScal *)(smem + Lo.scal_off);
   unsigned char *gmem = smem + Lo.part_off + (int64_t)G.grp * group_bytes(NW);
   Partial *part = (Partial *)gmem;
@@ -1904,7 +2014,10 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   CandMoves *mvw = (CandMoves *)(gmem + 2 * NW * sizeof(Partial) + 16);
   uint32_t *cnt_smem = (uint32_t *)(gmem + 2 * NW * sizeof(Partial) + 16 + 2 * NW * sizeof(CandMoves));
 
-  // load this group's members
+  // load this group's members (and clear the group's crossover bitmask)
+  if constexpr (PERM)
+    for (int k = G.tig; k < (len + 31) >> 5; k += G.nthr)
+      ((uint32_t *)((unsigned char *)scr + Lo.sol_stride))[k] = 0u;
   for (int e = 0; e < mine; ++e) {
     const int ls = G.grp + e * ngroups, p = p0 + ls;
     El *sol = (El *)(smem + Lo.sol_off + (int64_t)ls * Lo.sol_stride);
@@ -1914,6 +2027,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       scal[ls].cost = I.cost[p];
       scal[ls].best = I.best[p];
       scal[ls].aw = scal[ls].av = 0;
+      long long *snap = (long long *)(smem + Lo.snap_off) + 2 * (int64_t)ls;
+      snap[0] = snap[1] = LLONG_MIN;  // the parent rows hold nothing of this launch yet
     }
     G.sync();
     aux_init(MODEL, X, sol, &scal[ls], (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m, G);
@@ -1987,6 +2102,7 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       long long *loads = (long long *)(smem + Lo.load_off) + (int64_t)ls * X.m;
       const CvAux cva = cv_aux_at(smem + Lo.aux_off + (int64_t)ls * Lo.aux_stride, len, X.wl > 0);
       SolScal sc = scal[ls];
+      const long long best0 = sc.best;
       T = Tw;
       if (mine > 1) eblk = -1;
       uint32_t gg = g;
@@ -2178,6 +2294,14 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
               sc.best = sc.cost;
               int32_t *dst = I.bestsol + (int64_t)p * len;
               for (int i = G.tig; i < len; i += G.nthr) dst[i] = sol[i];
+              if constexpr (XF) {
+                // [R29] and into the parent row of the coming crossover window
+                if (I.cross_q16 > 0) {
+                  int32_t *pr =
+                      I.pool_sol + ((int64_t)P * (1 + (int64_t)((g / U + 1u) & 1u)) + p) * len;
+                  for (int i = G.tig; i < len; i += G.nthr) pr[i] = sol[i];
+                }
+              }
             }
             break;
           }
@@ -2186,7 +2310,12 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       }
       if (bytec) packed_flush(st, ps);
       G.sync();
-      if (G.tig == 0) scal[ls] = sc;
+      if (G.tig == 0) {
+        scal[ls] = sc;
+        if constexpr (XF)
+          if (I.cross_q16 > 0 && sc.best < best0)
+            ((long long *)(smem + Lo.snap_off))[2 * ls + (int)((g / U + 1u) & 1u)] = sc.best;
+      }
       G.sync();
       minbest = min(minbest, sc.best);
     }
@@ -2249,13 +2378,16 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     }
     if (G.gw == 0 && lane < kStats && my) atomicAdd(&S->acc[slot][lane], my);
     if (G.gw == 0 && lane == 0) atomicMin((long long *)&S->elite[slot], minbest);
-    if ((inject || migr || cross) && G.tig == 0) {
+    if ((inject || migr) && G.tig == 0) {
       for (int e = 0; e < mine; ++e) {
         const int ls = G.grp + e * ngroups;
         I.cost[p0 + ls] = scal[ls].cost;
         I.best[p0 + ls] = scal[ls].best;
       }
     }
+    // crossover parents (after migration instead, when the window migrates)
+    if constexpr (XF)
+      if (cross && !migr) snapshot_best(I, smem, Lo, G, p0, mine, ngroups, (g / I.U) & 1u);
     if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag, nact))
       return;
     ++nb;
@@ -2286,15 +2418,36 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     if constexpr (XF) {
       if (migr) {
         const int nbar = window_migrate<MODEL, NW>(I, X, smem, Lo, G, p0, mine, ngroups, g, nb,
-                                                   timeout_ns, nact, inject || cross);
+                                                   timeout_ns, nact, inject || cross, cross);
         if (nbar < 0) return;
         nb += (uint32_t)nbar;
       }
       if (cross) {
-        const int nbar = window_cross<MODEL, NW>(I, X, smem, Lo, G, p0, mine, ngroups, g, T, nb,
-                                                 timeout_ns, nact, inject);
-        if (nbar < 0) return;
-        nb += (uint32_t)nbar;
+        // [R29] the members' crossover draws; the crossovers of a group that
+        // has a member crossing
+        bool any = false;
+        uint4 R0 = make_uint4(0u, 0u, 0u, 0u);
+        for (int e = 0; e < mine; ++e) {
+          const uint4 R = philox(ctr_word(0, 0, kKindCross), X.tag, (uint32_t)(p0 + G.grp + e * ngroups),
+                                 g, X.k0, X.k1);
+          if (e == 0) R0 = R;
+          any = any || (R.x >> 16) < I.cross_q16;
+        }
+        if (any) window_cross<MODEL, NW>(I, X, smem, Lo, G, p0, mine, ngroups, g, T, R0);
+        if (inject) {
+          // injection reads every member's cost and best after the crossovers
+          if (G.tig == 0) {
+            for (int e = 0; e < mine; ++e) {
+              const int ls = G.grp + e * ngroups;
+              I.cost[p0 + ls] = scal[ls].cost;
+              I.best[p0 + ls] = scal[ls].best;
+            }
+          }
+          if (!group_barrier(S, (uint32_t)mine, (uint32_t)I.members * (nb + 1), timeout_ns, G, flag,
+                             nact))
+            return;
+          ++nb;
+        }
       }
     }
 
@@ -2397,7 +2550,6 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     O->T = T;
     O->g = I.g_end;
     for (int i = 0; i < kNops; ++i) O->w_op[i] = 0;
-#pragma unroll
     uint32_t wo[NO], wk[3];
     weights_get(W, wo, wk);
 #pragma unroll

@@ -617,6 +617,27 @@ def test_crossover_edge_cases(cgo):
     assert e.value.status == cgo.ERR_INVALID
 
 
+@pytest.mark.parametrize("ns,warps,wpm", [(1, 0, 0), (2, 4, 2), (1, 8, 1)])
+def test_crossover_parent_rows_across_launches(cgo, ns, warps, wpm):
+    """Crossover parents are each member's best as it stood before the
+    window's crossovers.  Many windows in which bests fall by moves, by
+    children, by migrants and by injected elites, in launches that end
+    inside windows and at their ends (each launch starts its parent rows
+    afresh), with one and two generations in flight."""
+    for inst in (I.tsp_clustered(70, 332), I.cvrptw(15, 333, vehicles=4, capacity=80),
+                 I.knapsack(90, 334)):
+        p = params_for(inst, P=16, C=64, G=33, U=3, cross_q16=52000, elite_period=9, islands=4,
+                       migrate_period=6, migrate_strategy=2, migrate_n=2, T0=50 << 32)
+        prob, g, o = run_both(cgo, inst, p, 15, warps=warps, wpm=wpm, ns=ns)
+        assert_same_state(g, o, "model %d ns %d" % (inst["model"], ns))
+        G = 33
+        for extra in (1, 2, 3, 7, 12):
+            prob.solve_continue(extra)
+            G += extra
+            assert_same_state(prob.state(), oracle_run(inst, p, 15, G),
+                              "model %d ns %d G %d" % (inst["model"], ns, G))
+
+
 def test_islands_invalid_parameters(cgo):
     inst = I.tsp_uniform(20, 317)
     p = params_for(inst, P=12, C=32, G=10, U=5, islands=3, migrate_period=10)
