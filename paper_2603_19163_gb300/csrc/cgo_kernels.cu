@@ -1584,6 +1584,30 @@ struct __align__(16) Partial {
 
 __device__ long long full_cost(const KInst &I, const int32_t *x);
 
+// [R29] the first loads of member p's order crossover at the window ending
+// at g (its partner's parent row, positions hi+1+4t .. +3 for group thread t)
+__device__ __forceinline__ void cross_first_loads(const KInst &I, const uint4 &R, int p, uint32_t g,
+                                                  int tig, int (&el)[4]) {
+  const int P = I.P, len = I.len;
+  int q = p + 1 + posm(R.y >> 16, (uint32_t)(P - 1));
+  q -= q >= P ? P : 0;
+  const int i = posm(R.z >> 16, (uint32_t)len);
+  int j = posm(R.z & 0xFFFFu, (uint32_t)(len - 1));
+  j += j >= i ? 1 : 0;
+  const int hi = max(i, j);
+  const int32_t *B = I.pool_sol + ((int64_t)P * (1 + (int64_t)((g / I.U) & 1u)) + q) * len;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int idx = 4 * tig + u;
+    el[u] = -1;
+    if (idx < len) {
+      int bi = hi + 1 + idx;
+      bi -= bi >= len ? len : 0;
+      el[u] = __ldcg(B + bi);
+    }
+  }
+}
+
 // [R29] the crossover parents of a window: each member's best solution as
 // it stands at the barrier before the crossovers, in the parent row of the
 // window's parity (rows P + b*P + p of the scratch buffer).  The search
@@ -1835,7 +1859,8 @@ __device__ long long perm_cost(const View &X, const PermEl *x, const Group &G, P
 template <int MODEL, int NW>
 __device__ __forceinline__ void window_cross(const KInst &I, const View X, unsigned char *smem,
                                           const Layout Lo, const Group G, int p0, int mine,
-                                          int ngroups, uint32_t g, uint64_t T, uint4 R0) {
+                                          int ngroups, uint32_t g, uint64_t T, uint4 R0,
+                                          const int (&el0)[4], bool have_el0) {
   constexpr bool PERM = (MODEL == TSP || MODEL == QAP || MODEL == CVRPTW || MODEL == ATSP);
   using El = typename SolEl<MODEL>::T;
   const int lane = threadIdx.x & 31, len = I.len, P = I.P;
@@ -1866,7 +1891,8 @@ __device__ __forceinline__ void window_cross(const KInst &I, const View X, unsig
       const int lo = min(i, j), hi = max(i, j);
       // thread t of the group takes B's positions hi+1+c0+4t .. +3 (wrapping):
       // the kept ones go, in order, to the child's positions from hi+1 on.
-      // The first chunk's loads are issued before the segment is marked.
+      // The first chunk's loads are issued before the segment is marked (the
+      // first member's by the caller, right after the window barrier).
       int el[4];
       auto load_chunk = [&](int c0) {
 #pragma unroll
@@ -1880,7 +1906,12 @@ __device__ __forceinline__ void window_cross(const KInst &I, const View X, unsig
           }
         }
       };
-      load_chunk(0);
+      if (e == 0 && have_el0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) el[u] = el0[u];
+      } else {
+        load_chunk(0);
+      }
       // the bitmask is all zero between crossovers (cleared at the load of
       // the members and after each use)
       for (int k = lo + G.tig; k <= hi; k += G.nthr) {
@@ -2392,12 +2423,31 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
       return;
     ++nb;
     uint32_t cum = lane < kStats ? ld_relaxed(&S->acc[slot][lane]) : 0u;
+    const long long elite = ld_relaxed64((const long long *)&S->elite[slot]);
+    // [R29] the members' crossover draws, and the first loads of the first
+    // member's parent row (final now unless migration comes first), while
+    // the window's totals are on their way
+    bool cany = false;
+    uint4 cR0 = make_uint4(0u, 0u, 0u, 0u);
+    int cel[4] = {-1, -1, -1, -1};
+    if constexpr (XF) {
+      if (cross) {
+        for (int e = 0; e < mine; ++e) {
+          const uint4 R = philox(ctr_word(0, 0, kKindCross), X.tag,
+                                 (uint32_t)(p0 + G.grp + e * ngroups), g, X.k0, X.k1);
+          if (e == 0) cR0 = R;
+          cany = cany || (R.x >> 16) < I.cross_q16;
+        }
+        if constexpr (PERM)
+          if (!migr && (cR0.x >> 16) < I.cross_q16)
+            cross_first_loads(I, cR0, p0 + G.grp, g, G.tig, cel);
+      }
+    }
     uint32_t total = cum - prev_acc[slot];
     prev_acc[slot] = cum;
     if (!pend_used) total += pend;
     pend_used = true;
     if (cum_owner && lane < kStats) I.aos_out->cum[lane] += total;
-    const long long elite = ld_relaxed64((const long long *)&S->elite[slot]);
     ++wi;
 
     uint32_t wo[NO], wk[3];
@@ -2423,17 +2473,9 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         nb += (uint32_t)nbar;
       }
       if (cross) {
-        // [R29] the members' crossover draws; the crossovers of a group that
-        // has a member crossing
-        bool any = false;
-        uint4 R0 = make_uint4(0u, 0u, 0u, 0u);
-        for (int e = 0; e < mine; ++e) {
-          const uint4 R = philox(ctr_word(0, 0, kKindCross), X.tag, (uint32_t)(p0 + G.grp + e * ngroups),
-                                 g, X.k0, X.k1);
-          if (e == 0) R0 = R;
-          any = any || (R.x >> 16) < I.cross_q16;
-        }
-        if (any) window_cross<MODEL, NW>(I, X, smem, Lo, G, p0, mine, ngroups, g, T, R0);
+        // [R29] the crossovers of a group that has a member crossing
+        if (cany)
+          window_cross<MODEL, NW>(I, X, smem, Lo, G, p0, mine, ngroups, g, T, cR0, cel, !migr);
         if (inject) {
           // injection reads every member's cost and best after the crossovers
           if (G.tig == 0) {
