@@ -132,11 +132,33 @@ typedef struct {
      Sec. 6.8's tri-objective VRP; 0 = off): cost += weight_longest * the
      largest distance driven by one vehicle */
   int64_t weight_longest;
+  /* --- appended --- */
+  /* CVRPTW lexicographic mode (Sec. 6.8, Table "lexicographic_mode"): the
+     first lex_n (0 = off, the weighted cost above; 1..3) entries of lex_obj
+     name the objectives in priority order (CGO_LEX_DISTANCE,
+     CGO_LEX_VEHICLES, CGO_LEX_LONGEST, each at most once), lex_tol their
+     tolerances (>= 0).  Solutions compare by their penalty (penalty0 *
+     capacity excess + penalty1 * lateness) first, then by each objective o
+     in buckets of width tol + 1 (values in one bucket tie and the next
+     objective decides).  The cost is then this order's key:
+       key = ((penalty * R_1 + o_1 / (tol_1 + 1)) * R_2 + o_2 / (tol_2 + 1)) ...
+       R_i = omax_i / (tol_i + 1) + 1, omax = (n + vehicles) * the largest
+       travel time for the two distances, vehicles for the vehicle count.
+     Needs travel times >= 0 and the three weights left at 0; a mode whose
+     key could exceed 2^62 returns CGO_ERR_UNSUPPORTED. */
+  int32_t lex_n;
+  int32_t lex_obj[3];
+  int64_t lex_tol[3];
 } cgo_problem_desc;
 
 /* The size of cgo_problem_desc before weight_longest was appended (accepted
  * by the calls that take a description: no longest-route term). */
 #define CGO_DESC_SIZE_V1 ((uint32_t)offsetof(cgo_problem_desc, weight_longest))
+/* The size before the lexicographic mode was appended (accepted: mode off). */
+#define CGO_DESC_SIZE_V2 ((uint32_t)offsetof(cgo_problem_desc, lex_n))
+
+/* CVRPTW objectives of the lexicographic mode. */
+enum { CGO_LEX_DISTANCE = 0, CGO_LEX_VEHICLES = 1, CGO_LEX_LONGEST = 2 };
 
 /* Search parameters.  Fixed point: Q16 weights (65536 = 1.0), Q32.32
  * temperature, Q0.32 cooling factor. */

@@ -31,7 +31,12 @@ class OrcInstance(ctypes.Structure):
                 ("capacity", ctypes.c_int64), ("lb", ctypes.c_int32), ("ub", ctypes.c_int32),
                 ("penalty0", ctypes.c_int64), ("penalty1", ctypes.c_int64),
                 ("tag", ctypes.c_uint32), ("weight0", ctypes.c_int64), ("weight1", ctypes.c_int64),
-                ("weight2", ctypes.c_int64)]
+                ("weight2", ctypes.c_int64), ("lex_n", ctypes.c_int32),
+                ("lex_obj", ctypes.c_int32 * 3), ("lex_tol", ctypes.c_int64 * 3),
+                ("lex_dmax", ctypes.c_int64)]
+
+# CVRPTW objectives of the lexicographic mode [R37]
+LEX_DISTANCE, LEX_VEHICLES, LEX_LONGEST = 0, 1, 2
 
 
 class OrcParams(ctypes.Structure):
@@ -151,6 +156,15 @@ class Instance:
         s.weight0 = int(inst.get("weight_distance", 0))
         s.weight1 = int(inst.get("weight_vehicles", 0))
         s.weight2 = int(inst.get("weight_longest", 0))
+        # [R37] lexicographic mode: [(objective, tolerance), ...] in priority order
+        lex = list(inst.get("lexicographic", ()))
+        s.lex_n = len(lex)
+        for i, (obj, tol) in enumerate(lex):
+            s.lex_obj[i] = int(obj)
+            s.lex_tol[i] = int(tol)
+        if lex:
+            maxd = int(np.max(np.asarray(inst["mat0"], np.int64)))
+            s.lex_dmax = (int(inst["n"]) + int(inst["vehicles"])) * max(maxd, 0)
         s.tag = int(inst.get("tag", 0)) & 0xFFFFFFFF
         self.s = s
 

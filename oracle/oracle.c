@@ -183,13 +183,34 @@ static int64_t cost_gap(const orc_instance *in, const int32_t *x) {
   return s;
 }
 
+/* [R37] CVRPTW's lexicographic key (Sec. 6.8, Table "lexicographic_mode"):
+ * the penalty first, then the prioritised objectives in order, objective i
+ * in buckets of width tol_i + 1 (values in one bucket tie and the next
+ * objective decides), as one integer in mixed radix:
+ *   key = (((pen * R_1 + q_1) * R_2 + q_2) ...),  q_i = o_i / (tol_i + 1),
+ *   R_i = omax_i / (tol_i + 1) + 1,
+ * omax = lex_dmax for the two distances and the fleet size for vehicles. */
+static int64_t lex_key(const orc_instance *in, int64_t pen, int64_t dist, int64_t used,
+                       int64_t longest) {
+  int64_t key = pen;
+  for (int32_t i = 0; i < in->lex_n; i++) {
+    int32_t obj = in->lex_obj[i];
+    int64_t o = obj == 0 ? dist : (obj == 1 ? used : longest);
+    int64_t omax = obj == 1 ? (int64_t)in->vehicles : in->lex_dmax;
+    int64_t w = in->lex_tol[i] + 1;
+    key = key * (omax / w + 1) + o / w;
+  }
+  return key;
+}
+
 /* CVRPTW, separator encoding: symbols < n are customers 1..n, symbols >= n
  * end a route.  Per route from the depot at t = 0: arrive t = max(t + d,
  * ready); late += max(0, t - due); t += service; load += demand; back at the
  * depot t += d(last, 0), late += max(0, t - due_0).  A route with no customer
  * costs nothing.
  * cost = distance + lambda_cap * sum max(0, load - Q) + lambda_tw * late,
- * with the objective weights of [R30] and [R34] (longest route). */
+ * with the objective weights of [R30] and [R34] (longest route), or the
+ * lexicographic key of [R37]. */
 static int64_t cost_cvrptw(const orc_instance *in, const int32_t *x) {
   int32_t n = in->n, len = orc_solution_length(in), N = n + 1;
   const int32_t *d = in->mat0, *dem = in->vec0, *rdy = in->vec1, *due = in->vec2,
@@ -231,6 +252,7 @@ static int64_t cost_cvrptw(const orc_instance *in, const int32_t *x) {
     }
     k++; /* skip the separator (or step past the end) */
   }
+  if (in->lex_n > 0) return lex_key(in, lcap * capx + ltw * late, dist, used, longest);
   return wd * dist + lcap * capx + ltw * late + wv * used + wl * longest;
 }
 

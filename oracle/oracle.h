@@ -51,6 +51,15 @@ typedef struct {
   uint32_t tag;       /* instance tag (Philox counter word 1) */
   int64_t weight0, weight1; /* CVRPTW objective weights: distance (0 = 1), vehicles used */
   int64_t weight2;          /* CVRPTW: weight of the longest route's distance [R34] (0 = off) */
+  /* CVRPTW lexicographic mode [R37] (Sec. 6.8, Table "lexicographic_mode"):
+   * lex_n objectives in priority order (0 distance, 1 vehicles used, 2 the
+   * longest route's distance), each with an integer tolerance; lex_n = 0
+   * keeps the weighted cost.  lex_dmax = (n + vehicles) * the largest travel
+   * time, the bound on the distances that sets the key's radices. */
+  int32_t lex_n;
+  int32_t lex_obj[3];
+  int64_t lex_tol[3];
+  int64_t lex_dmax;
 } orc_instance;
 
 typedef struct {

@@ -43,7 +43,13 @@ class cgo_problem_desc(ctypes.Structure):
                 ("penalty0", ctypes.c_int64), ("penalty1", ctypes.c_int64),
                 ("pointers_on_device", ctypes.c_int32), ("instance_tag", ctypes.c_uint32),
                 ("weight_distance", ctypes.c_int64), ("weight_vehicles", ctypes.c_int64),
-                ("weight_longest", ctypes.c_int64)]
+                ("weight_longest", ctypes.c_int64),
+                ("lex_n", ctypes.c_int32), ("lex_obj", ctypes.c_int32 * 3),
+                ("lex_tol", ctypes.c_int64 * 3)]
+
+
+# CVRPTW objectives of the lexicographic mode (cgo_problem_desc.lex_obj)
+LEX_DISTANCE, LEX_VEHICLES, LEX_LONGEST = 0, 1, 2
 
 
 class cgo_params(ctypes.Structure):
@@ -260,6 +266,12 @@ class Problem:
         d.weight_distance = int(inst.get("weight_distance", 0))
         d.weight_vehicles = int(inst.get("weight_vehicles", 0))
         d.weight_longest = int(inst.get("weight_longest", 0))
+        # lexicographic mode: [(objective, tolerance), ...] in priority order
+        lex = list(inst.get("lexicographic", ()))
+        d.lex_n = len(lex)
+        for i, (obj, tol) in enumerate(lex[:3]):
+            d.lex_obj[i] = int(obj)
+            d.lex_tol[i] = int(tol)
         d.pointers_on_device = 1 if on_device else 0
         d.instance_tag = int(inst.get("tag", 0)) & 0xFFFFFFFF
         h = ctypes.c_void_p()

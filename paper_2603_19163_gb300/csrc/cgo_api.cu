@@ -356,6 +356,13 @@ KInst base_kinst(const cgo_problem *p) {
   h.wdist = p->wdist;
   h.wveh = p->wveh;
   h.wlong = p->wlong;
+  h.lex_n = p->lex_n;
+  for (int i = 0; i < 3; ++i) {
+    h.lex_obj[i] = p->lex_obj[i];
+    h.lex_w[i] = p->lex_w[i];
+    h.lex_R[i] = p->lex_R[i];
+    h.lex_sh[i] = p->lex_sh[i];
+  }
   h.lb = p->lb;
   h.ub = p->ub;
   h.tag = p->tag;
@@ -628,14 +635,75 @@ cgo_status cgo_kernel_launches(uint64_t *out) {
   return CGO_OK;
 }
 
+// [R37] CVRPTW's lexicographic mode.  The kernels keep computing one integer
+// cost per route set, with power-of-two weights that pack the objectives
+// into separate bit fields of it: distance in bits [0, a), vehicles used in
+// [a, b), the longest route's distance in [b, c) (when it is an objective)
+// and the penalty from bit c on.  The kernels read the fields back and turn
+// them into the key of the lexicographic order (bucketed objectives in mixed
+// radix), which is the cost the search works with.
+static int bits_for(int64_t x) {
+  int b = 0;
+  while (b < 62 && (x >> b) != 0) ++b;
+  return b;
+}
+
+cgo_status set_lexicographic(cgo_problem *p, const cgo_problem_desc *d, const std::vector<int32_t> &travel,
+                             double pen_max) {
+  if (d->lex_n < 0 || d->lex_n > 3) return fail(CGO_ERR_INVALID, "lex_n must be in [0, 3]");
+  if (d->weight_distance != 0 || d->weight_vehicles != 0 || d->weight_longest != 0)
+    return fail(CGO_ERR_INVALID, "the lexicographic mode takes no objective weights");
+  int64_t maxd = 0;
+  for (int32_t t : travel) {
+    if (t < 0) return fail(CGO_ERR_INVALID, "the lexicographic mode needs travel times >= 0");
+    maxd = std::max<int64_t>(maxd, t);
+  }
+  bool seen[3] = {false, false, false};
+  for (int i = 0; i < d->lex_n; ++i) {
+    const int o = d->lex_obj[i];
+    if (o < 0 || o > 2 || seen[o]) return fail(CGO_ERR_INVALID, "lex_obj: each objective at most once");
+    if (d->lex_tol[i] < 0) return fail(CGO_ERR_INVALID, "lex_tol must be >= 0");
+    seen[o] = true;
+  }
+  const int64_t dmax = ((int64_t)p->n + p->V) * maxd;
+  const int a = bits_for(dmax), b = a + bits_for(p->V), c = b + (seen[2] ? bits_for(dmax) : 0);
+  // the packed cost and the key both stay below 2^62
+  if (c > 61 || pen_max * std::ldexp(1.0, c) + std::ldexp(1.0, c) > kLimit)
+    return fail(CGO_ERR_UNSUPPORTED, "the objectives of this instance do not fit the packed cost");
+  double radix = 1.0;
+  p->lex_n = d->lex_n;
+  for (int i = 0; i < 3; ++i) {
+    const bool on = i < d->lex_n;
+    const int o = on ? d->lex_obj[i] : 0;
+    const int64_t w = on ? d->lex_tol[i] + 1 : 1;
+    const int64_t omax = o == 1 ? (int64_t)p->V : dmax;
+    p->lex_obj[i] = o;
+    p->lex_w[i] = w;
+    p->lex_R[i] = on ? omax / w + 1 : 1;
+    radix *= (double)p->lex_R[i];
+  }
+  if ((pen_max + 1.0) * radix > kLimit)
+    return fail(CGO_ERR_UNSUPPORTED, "the lexicographic key of this instance could exceed 2^62");
+  p->lex_sh[0] = a;
+  p->lex_sh[1] = b;
+  p->lex_sh[2] = c;
+  p->wdist = 1;
+  p->wveh = (int64_t)1 << a;
+  p->wlong = seen[2] ? (int64_t)1 << b : 0;
+  p->lam0 <<= c;
+  p->lam1 <<= c;
+  return CGO_OK;
+}
+
 cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
   if (!out) return fail(CGO_ERR_INVALID, "out is NULL");
   *out = nullptr;
   cgo_problem_desc dd;
-  if (!d || (d->struct_size != sizeof(cgo_problem_desc) && d->struct_size != CGO_DESC_SIZE_V1))
+  if (!d || (d->struct_size != sizeof(cgo_problem_desc) && d->struct_size != CGO_DESC_SIZE_V1 &&
+             d->struct_size != CGO_DESC_SIZE_V2))
     return fail(CGO_ERR_INVALID, "desc: struct_size must be sizeof(cgo_problem_desc)");
   memset(&dd, 0, sizeof dd);
-  memcpy(&dd, d, d->struct_size);  // an earlier description has no longest-route weight
+  memcpy(&dd, d, d->struct_size);  // an earlier description has the fields appended since off
   d = &dd;
   if (d->model < CGO_TSP || d->model > CGO_CVRPTW) return fail(CGO_ERR_INVALID, "unknown model");
   if (d->encoding != encoding_of(d->model))
@@ -763,6 +831,9 @@ cgo_status cgo_problem_create(const cgo_problem_desc *d, cgo_problem **out) {
         return bail(fail(CGO_ERR_INVALID, "CVRPTW data could overflow an int64 cost"));
       // route quantities (time, lateness, distance, load) fit in int32?
       p->cv32 = (late < 2.0e9 && (double)abssum(v[0]) < 2.0e9 && (double)N * maxd < 2.0e9) ? 1 : 0;
+      if (d->lex_n != 0 && (s = set_lexicographic(p, d, a, (double)p->lam0 * (double)abssum(v[0]) +
+                                                              (double)p->lam1 * late)) != CGO_OK)
+        return bail(s);
       std::vector<int4> node((size_t)N);
       for (int64_t k = 0; k < N; ++k) node[(size_t)k] = make_int4(v[1][(size_t)k], v[2][(size_t)k], v[3][(size_t)k], v[0][(size_t)k]);
       cudaError_t e;
@@ -1444,7 +1515,8 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_in, 
 cgo_status cgo_solve_static(const cgo_problem_desc *d, const cgo_params *q, uint64_t seed,
                             int32_t *out_best_sol, int64_t *out_best_cost, void *stream) {
   cgo_problem_desc dd;
-  if (!d || (d->struct_size != sizeof(cgo_problem_desc) && d->struct_size != CGO_DESC_SIZE_V1))
+  if (!d || (d->struct_size != sizeof(cgo_problem_desc) && d->struct_size != CGO_DESC_SIZE_V1 &&
+             d->struct_size != CGO_DESC_SIZE_V2))
     return fail(CGO_ERR_INVALID, "desc: struct_size must be sizeof(cgo_problem_desc)");
   memset(&dd, 0, sizeof dd);
   memcpy(&dd, d, d->struct_size);  // an earlier description has no longest-route weight

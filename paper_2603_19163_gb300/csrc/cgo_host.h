@@ -17,6 +17,12 @@ struct cgo_problem {
   int64_t wdist = 1, wveh = 0;  // CVRPTW objective weights
   int64_t wlong = 0;            // CVRPTW: weight of the longest route
   int asym = 0;                 // TSP with an asymmetric matrix (the kernels' ATSP path)
+  // CVRPTW lexicographic mode: objectives, bucket widths, radices and the
+  // bit positions of the packed cost's fields
+  int lex_n = 0;
+  int lex_obj[3] = {0, 0, 0};
+  int64_t lex_w[3] = {1, 1, 1}, lex_R[3] = {1, 1, 1};
+  int lex_sh[3] = {0, 0, 0};
   int lb = 0, ub = 0;
   uint32_t tag = 0;
   int32_t *d_mat0 = nullptr, *d_mat1 = nullptr, *d_vec[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -60,6 +60,10 @@ struct KInst {
   int64_t capacity, lam0, lam1;
   int64_t wdist, wveh;  // CVRPTW objective weights (distance, vehicles used)
   int64_t wlong;        // CVRPTW: weight of the longest route's distance (0 = off)
+  // CVRPTW lexicographic mode (lex_n > 0): the cost is the key of the
+  // order; the packed route cost's fields start at bits 0, lex_sh[0..2]
+  int32_t lex_n, lex_obj[3], lex_sh[3];
+  int64_t lex_w[3], lex_R[3];
   int32_t lb, ub;
   uint32_t tag;
   int32_t tri16;              // TSP triangle stored as int16

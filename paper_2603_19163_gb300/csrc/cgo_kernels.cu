@@ -144,6 +144,7 @@ struct View {
   long long lam1;
   long long wd, wv;  // CVRPTW objective weights (distance, vehicles used)
   long long wl;      // CVRPTW: weight of the longest route's distance
+  const KInst *ki;   // the instance (the CVRPTW lexicographic mode's constants)
   bool cv32;
   bool t3;   // 3-opt enabled for this instance
   bool t16;  // TSP / ATSP matrix entries stored as int16
@@ -1048,6 +1049,20 @@ __device__ long long cvrptw_composite(const View &X, const PermEl *sol, const Ca
   return cvrptw_routes(X, Vf, L, R, X.cv32) - old;
 }
 
+// [R37] CVRPTW's lexicographic key from a packed route cost: the fields
+// (distance, vehicles used, longest route, penalty from the top) are read
+// back and each prioritised objective goes in as its bucket, in mixed radix
+__device__ __forceinline__ long long lex_key(const KInst &K, long long P) {
+  const unsigned long long u = (unsigned long long)P;
+  const int a = K.lex_sh[0], b = K.lex_sh[1], c = K.lex_sh[2];
+  const long long o[3] = {(long long)(u & ((1ull << a) - 1ull)),
+                          (long long)((u >> a) & ((1ull << (b - a)) - 1ull)),
+                          (long long)((u >> b) & ((1ull << (c - b)) - 1ull))};
+  long long key = (long long)(u >> c);
+  for (int i = 0; i < K.lex_n; ++i) key = key * K.lex_R[i] + o[K.lex_obj[i]] / K.lex_w[i];
+  return key;
+}
+
 // CVRPTW candidate.  One step: from the route cache; k steps: every changed
 // position lies in the hull of the moves' ranges (a move permutes only inside
 // its own range), so the routes over that hull are walked once in the final
@@ -1097,6 +1112,11 @@ __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *so
       }
     }
     d = cvrptw_composite(X, sol, cm, aux);
+  }
+  if (X.ki->lex_n > 0) {
+    // the change of the key: the packed cost of the current routes is in the cache
+    const long long cur = aux.cum[X.len + 1] + (X.wl > 0 ? X.wl * aux.pmx[X.len + 1] : 0ll);
+    d = lex_key(*X.ki, cur + d) - lex_key(*X.ki, cur);
   }
   rec = stats_record(ops[0], ops[1], ops[2], k, d < 0);
   return true;
@@ -1843,7 +1863,7 @@ __device__ long long perm_cost(const View &X, const PermEl *x, const Group &G, P
     }
     s = group_sum<NW>(s, G, part);
     if (X.wl > 0) s += X.wl * group_max<NW>(mx, G, part);
-    return s;
+    return X.ki->lex_n > 0 ? lex_key(*X.ki, s) : s;
   }
 }
 
@@ -2640,6 +2660,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
   X.wd = I.wdist;
   X.wv = I.wveh;
   X.wl = I.wlong;
+  X.ki = &I;
   if (!staged) return X;
   auto copy = [&](const void *src, int64_t bytes, int64_t off) {
     const int4 *s = (const int4 *)src;
@@ -2807,7 +2828,7 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
       long long mx = 0;
       const long long c = cvrptw_routes(X, [&](int q) { return (int)x[q]; }, 0, I.len, false, Jumps(),
                                         I.wlong > 0 ? &mx : nullptr);
-      return c + I.wlong * mx;
+      return I.lex_n > 0 ? lex_key(I, c + I.wlong * mx) : c + I.wlong * mx;
     }
     case GAP: {
       for (int j = 0; j < n; ++j) s += I.mat0[(size_t)x[j] * n + j];

@@ -48,6 +48,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(cgo_params, generations), offsetof(cgo_params, T0_q32),
          offsetof(cgo_params, op_cap_q16), offsetof(cgo_state, cur));
   printf("%zu %zu\n", offsetof(cgo_problem_desc, capacity), offsetof(cgo_problem_desc, instance_tag));
+  printf("%zu %zu %u %u\n", offsetof(cgo_problem_desc, lex_n), offsetof(cgo_problem_desc, lex_tol),
+         CGO_DESC_SIZE_V1, CGO_DESC_SIZE_V2);
   return 0;
 }
 """
@@ -62,7 +64,9 @@ int main(void) {
             ctypes.sizeof(cgo.cgo_state), ctypes.sizeof(cgo.cgo_launch),
             cgo.cgo_params.generations.offset, cgo.cgo_params.T0_q32.offset,
             cgo.cgo_params.op_cap_q16.offset, cgo.cgo_state.cur.offset,
-            cgo.cgo_problem_desc.capacity.offset, cgo.cgo_problem_desc.instance_tag.offset]
+            cgo.cgo_problem_desc.capacity.offset, cgo.cgo_problem_desc.instance_tag.offset,
+            cgo.cgo_problem_desc.lex_n.offset, cgo.cgo_problem_desc.lex_tol.offset,
+            cgo.cgo_problem_desc.weight_longest.offset, cgo.cgo_problem_desc.lex_n.offset]
     assert [int(x) for x in out] == want
 
 

@@ -86,6 +86,13 @@ def mixed_batch():
     items.append((dict(I.tsp_asym(80, 269, skew=50000), tag=59),
                   dict(P=5, C=48, G=19, ops=[0, 1, 2, 3, O.THREE_OPT])))
     items.append((dict(I.qap_random(13, 270), tag=60), dict(P=5, C=48, G=21, ops=[0, 1, 2, 3, O.THREE_OPT])))
+    # CVRPTW's lexicographic mode
+    items.append((dict(I.cvrptw(18, 271, vehicles=5, capacity=90), tag=61,
+                       lexicographic=[(O.LEX_VEHICLES, 0), (O.LEX_DISTANCE, 30)]),
+                  dict(P=6, C=48, G=24, U=4, cross_q16=30000)))
+    items.append((dict(I.cvrptw(15, 272, vehicles=4, capacity=80), tag=62,
+                       lexicographic=[(O.LEX_DISTANCE, 20), (O.LEX_VEHICLES, 0), (O.LEX_LONGEST, 5)]),
+                  dict(P=5, C=64, G=21)))
     return items
 
 

@@ -567,6 +567,50 @@ def test_islands_degenerate_shapes(cgo):
         assert_same_state(g, o, str(over))
 
 
+# ----------------------------------------------- lexicographic CVRPTW (R37)
+LEX_MODES = [[(0, 0), (1, 0)], [(0, 50), (1, 0)], [(1, 0), (0, 100)], [(0, 0), (1, 0), (2, 0)],
+             [(1, 0), (0, 30), (2, 20)], [(2, 15)]]
+
+
+@pytest.mark.parametrize("ns", [1, 2])
+@pytest.mark.parametrize("lex", LEX_MODES)
+def test_cvrptw_lexicographic_mode(cgo, lex, ns):
+    """The lexicographic mode (penalty first, then each objective in buckets
+    of width tolerance + 1): the kernels' packed route cost turned into the
+    order's key for every candidate; the element operators, 3-opt and the
+    row level, at every k level, one and two generations in flight."""
+    inst = dict(I.cvrptw(30, 70, vehicles=6, capacity=90), lexicographic=lex)
+    ops = [SW, TO, INS, OR, TH, O.ROW_SWAP_OP, O.ROW_MERGE_OP, O.ROW_SPLIT_OP]
+    p = params_for(inst, P=6, C=64, G=31, U=4, ops=ops, T0=30 << 32)
+    prob, g, o = run_both(cgo, inst, p, 5, wpm=2 if ns == 2 else 0, ns=ns)
+    assert_same_state(g, o, "lex %s ns %d" % (lex, ns))
+    assert_same_counts(prob, o, "lex %s ns %d" % (lex, ns))
+
+
+def test_cvrptw_lexicographic_population_steps(cgo):
+    """With crossover (children costed as keys), islands and injection."""
+    inst = dict(I.cvrptw(25, 71, vehicles=5, capacity=100), lexicographic=[(1, 0), (0, 40)])
+    p = params_for(inst, P=12, C=64, G=37, U=3, cross_q16=50000, islands=3, migrate_period=6,
+                   migrate_strategy=1, migrate_n=2, elite_period=9, init_oversample=2)
+    _, g, o = run_both(cgo, inst, p, 8)
+    assert_same_state(g, o, "lex population steps")
+
+
+def test_cvrptw_lexicographic_invalid(cgo):
+    base = I.cvrptw(12, 72, vehicles=3, capacity=80)
+    for lex, extra in (([(0, 0), (0, 5)], {}), ([(3, 0)], {}), ([(0, -1)], {}),
+                       ([(0, 0)], dict(weight_vehicles=5)), ([(0, 0)] * 4, {})):
+        with pytest.raises(cgo.CgoError) as e:
+            cgo.Problem(dict(base, lexicographic=lex, **extra))
+        assert e.value.status == cgo.ERR_INVALID, lex
+    # objectives too wide for the packed cost
+    wide = dict(I.cvrptw(30, 73, vehicles=6, capacity=90, box=1000000, horizon=10 ** 9),
+                lexicographic=[(0, 0), (1, 0), (2, 0)])
+    with pytest.raises(cgo.CgoError) as e:
+        cgo.Problem(wide)
+    assert e.value.status == cgo.ERR_UNSUPPORTED
+
+
 # ------------------------------------------------------------------ crossover
 CROSS_CASES = [(I.tsp_uniform(30, 320), None), (I.qap_random(11, 321), None),
                (I.tsp_asym(30, 329), None),

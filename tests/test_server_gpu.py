@@ -60,6 +60,9 @@ def request_mix():
         # asymmetric TSP; QAP with block moves
         (dict(I.tsp_asym(40, 316), tag=17), dict(P=6, C=64, G=25, U=4)),
         (dict(I.qap_random(10, 317), tag=18), dict(P=5, C=48, G=23, ops=[O.TWO_OPT, O.INSERT, O.OR_OPT])),
+        # CVRPTW's lexicographic mode
+        (dict(I.cvrptw(16, 318, vehicles=4, capacity=80), tag=19,
+              lexicographic=[(O.LEX_VEHICLES, 0), (O.LEX_DISTANCE, 25)]), dict(P=5, C=48, G=22)),
     ]
 
 
