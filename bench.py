@@ -107,21 +107,45 @@ def solve_variant(args, model: int, cfg: dict, desc: str):
     return cfg, desc
 
 
+LEX_NAMES = {"d": 0, "v": 1, "l": 2}      # distance, vehicles used, longest route
+
+
+def cvrptw_variant(args, inst: dict, desc: str):
+    """CVRPTW objective modes applied alike by both arms: weights
+    'distance,vehicles', or the lexicographic mode 'd:tol,v:tol[,l:tol]'
+    (objectives in priority order with their tolerances)."""
+    if inst is None or inst["model"] != I.CVRPTW:
+        return inst, desc
+    if args.cvrptw_weights:
+        wd, wv = (int(x) for x in args.cvrptw_weights.split(","))
+        inst = dict(inst, weight_distance=wd, weight_vehicles=wv)
+        desc += " weights=(%d,%d)" % (wd, wv)
+    if args.cvrptw_lex:
+        lex = [(LEX_NAMES[t.split(":")[0]], int(t.split(":")[1])) for t in args.cvrptw_lex.split(",")]
+        inst = dict(inst, lexicographic=lex)
+        desc += " lexicographic=" + args.cvrptw_lex
+    return inst, desc
+
+
 def cvrptw_objectives(inst: dict, sol) -> dict:
-    """Travel distance and vehicles used by a separator-encoded CVRPTW
-    solution (for the report; the search's own cost adds the penalties)."""
+    """Travel distance, vehicles used and the longest route's distance of a
+    separator-encoded CVRPTW solution (for the report; the search's own cost
+    adds the penalties)."""
     n, d = int(inst["n"]), np.asarray(inst["mat0"])
-    dist, used, prev = 0, 0, 0
+    dist, used, prev, rd, longest = 0, 0, 0, 0, 0
     for s in list(sol) + [n]:
         if s >= n:
             if prev:
                 dist += int(d[prev][0])
+                rd += int(d[prev][0])
+                longest = max(longest, rd)
                 used += 1
-            prev = 0
+            prev, rd = 0, 0
         else:
             dist += int(d[prev][s + 1])
+            rd += int(d[prev][s + 1])
             prev = s + 1
-    return {"distance": dist, "vehicles": used}
+    return {"distance": dist, "vehicles": used, "longest": longest}
 
 
 def extra_ops_mask(model: int, extra: str) -> int:
@@ -217,10 +241,7 @@ def run_reference(args, rank, world):
                 pass
             pops = batch_populations(mix, l2)[0]
     else:
-        if args.cvrptw_weights and inst["model"] == I.CVRPTW:
-            wd, wv = (int(x) for x in args.cvrptw_weights.split(","))
-            inst = dict(inst, weight_distance=wd, weight_vehicles=wv)
-            desc += " weights=(%d,%d)" % (wd, wv)
+        inst, desc = cvrptw_variant(args, inst, desc)
         insts = [inst]
         cfg, desc = solve_variant(args, inst["model"], cfg, desc)
     plist = []
@@ -309,6 +330,9 @@ def main():
                          "'three_opt' (TSP, CVRPTW), 'segment' (seg_flip / seg_reset: knapsack, GAP)")
     ap.add_argument("--cvrptw-weights", default="",
                     help="cvrptw100: objective weights 'distance,vehicles' (0,0 = distance only)")
+    ap.add_argument("--cvrptw-lex", default="",
+                    help="cvrptw100: lexicographic mode, objectives in priority order with "
+                         "tolerances, e.g. 'd:50,v:0' (d distance, v vehicles, l longest route)")
     ap.add_argument("--cross", type=int, default=0,
                     help="crossover probability per member and AOS window, Q16 (0 = off)")
     ap.add_argument("--islands", default="",
@@ -364,10 +388,7 @@ def main():
         cfg["G"] = args.generations
         desc = desc.replace("G=", "G(full)=") + " G=%d" % cfg["G"]
     inst = dict(inst, tag=0)
-    if args.cvrptw_weights and inst["model"] == I.CVRPTW:
-        wd, wv = (int(x) for x in args.cvrptw_weights.split(","))
-        inst.update(weight_distance=wd, weight_vehicles=wv)
-        desc += " weights=(%d,%d)" % (wd, wv)
+    inst, desc = cvrptw_variant(args, inst, desc)
     seed = 1 + rank
     stream = torch.cuda.Stream()
     cfg, desc = solve_variant(args, inst["model"], cfg, desc)

@@ -93,6 +93,7 @@ def test_cvrptw_objectives_of_a_separator_sequence():
     d = np.array([[0, 10, 20, 15], [10, 0, 12, 25], [20, 12, 0, 8], [15, 25, 8, 0]], np.int32)
     inst = dict(n=3, mat0=d)
     # routes (1, 2) and (3), one empty route
-    assert bench.cvrptw_objectives(inst, [0, 1, 3, 2, 4]) == {"distance": 42 + 30, "vehicles": 2}
+    assert bench.cvrptw_objectives(inst, [0, 1, 3, 2, 4]) == {"distance": 42 + 30, "vehicles": 2,
+                                                             "longest": 42}
     assert bench.cvrptw_objectives(inst, [3, 4, 2, 0, 1]) == {"distance": 15 + 25 + 12 + 20,
-                                                             "vehicles": 1}
+                                                             "vehicles": 1, "longest": 72}
