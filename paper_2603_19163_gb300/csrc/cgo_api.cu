@@ -667,8 +667,10 @@ cgo_status set_lexicographic(cgo_problem *p, const cgo_problem_desc *d, const st
   }
   const int64_t dmax = ((int64_t)p->n + p->V) * maxd;
   const int a = bits_for(dmax), b = a + bits_for(p->V), c = b + (seen[2] ? bits_for(dmax) : 0);
-  // the packed cost and the key both stay below 2^62
-  if (c > 61 || pen_max * std::ldexp(1.0, c) + std::ldexp(1.0, c) > kLimit)
+  // the packed cost, the shifted penalty weights and the key stay below 2^62
+  const double top = std::ldexp(1.0, c);
+  if (c > 61 || (pen_max + 1.0) * top > kLimit || (double)p->lam0 * top > kLimit ||
+      (double)p->lam1 * top > kLimit)
     return fail(CGO_ERR_UNSUPPORTED, "the objectives of this instance do not fit the packed cost");
   double radix = 1.0;
   p->lex_n = d->lex_n;
