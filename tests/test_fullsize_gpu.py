@@ -136,3 +136,42 @@ def test_tsp_beyond_shared_memory(cgo):
     prob.solve(p, 5)
     assert prob.get_launch()[2] == 2          # staged through L2
     assert_same_state(prob.state(), oracle_run(inst, p, 5, 6), "tsp1500")
+
+
+def test_atsp442_full_run(cgo):
+    """An asymmetric n = 442 matrix in the benchmark's shape (P = 128, C = 128,
+    20,000 generations, every permutation operator): the full matrix (390 KB
+    of int16) is read through L2, each member keeps its edge-cost prefix
+    sums, and every member's cost is the oracle's directed tour cost."""
+    inst = I.tsp_asym(442, 5)
+    p = params_for(inst, P=128, C=128, G=20000,
+                   op_mask=(1 << O.SWAP) | (1 << TO) | (1 << OR) | (1 << INS) | (1 << O.THREE_OPT))
+    prob = cgo.Problem(inst)
+    prob.solve(p, 2)
+    assert prob.get_launch()[2] == 2          # staged through L2
+    check_state(inst, p, prob.state(), prob.best(), "atsp442")
+
+
+def test_cvrptw100_lexicographic_full_run(cgo):
+    """The 100-customer CVRPTW workload (P = 32, C = 128, 20,000 generations)
+    in the lexicographic mode with every objective (vehicles, then distance
+    with tolerance 50, then the longest route), the row level on: each
+    member's cost is the oracle's key of its routes."""
+    inst = dict(I.cvrptw(100, 0), lexicographic=[(O.LEX_VEHICLES, 0), (O.LEX_DISTANCE, 50),
+                                                 (O.LEX_LONGEST, 0)])
+    p = params_for(inst, P=32, C=128, G=20000)
+    p["op_mask"] = ((1 << O.SWAP) | (1 << TO) | (1 << INS) | (1 << OR) | (1 << O.ROW_SWAP_OP) |
+                    (1 << O.ROW_MERGE_OP) | (1 << O.ROW_SPLIT_OP))
+    prob = cgo.Problem(inst)
+    prob.solve(p, 4)
+    check_state(inst, p, prob.state(), prob.best(), "cvrptw100 lexicographic")
+
+
+def test_qap64_block_moves_full_run(cgo):
+    """QAP n = 64 (P = 256, 2,000 generations) with every permutation
+    operator: the block moves' exact deltas keep every cost the oracle's."""
+    inst = I.qap_grid(64, 0)
+    p = params_for(inst, P=256, C=128, G=2000, ops=[O.SWAP, TO, INS, OR, O.THREE_OPT])
+    prob = cgo.Problem(inst)
+    prob.solve(p, 1)
+    check_state(inst, p, prob.state(), prob.best(), "qap64 block moves")
