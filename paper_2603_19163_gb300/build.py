@@ -16,7 +16,49 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcgo.so")
-SOURCES = ["cgo_kernels.cu", "cgo_kernels_xf.cu", "cgo_api.cu", "cgo_server.cu", "cgo_peaks.cu"]
+# Kernel units: cgo_kernels.cu compiled again with CGO_UNIT defined, each
+# instantiating a share of the kernel sets, so that they compile in parallel
+# (cgo_kernels.cu itself keeps the host code and the benchmark's TSP set).
+# Entry: object name, population-step code compiled in, then the sets as
+# (name, model, int16 matrix, evolve shape mask, batch shape mask); the names
+# are those declared in cgo_kernels.cu.  CVRPTW's kernels are the slowest to
+# compile and are spread over several units.
+ALL_E, ALL_B = "0xFFu", "0x7u"
+UNITS = [
+    ("x_cvrptw_a", True, [("x_cvrptw_a", "CVRPTW", "false", "0x03u", "0u")]),
+    ("x_cvrptw_b", True, [("x_cvrptw_b", "CVRPTW", "false", "0x0Cu", "0u")]),
+    ("x_cvrptw_c", True, [("x_cvrptw_c", "CVRPTW", "false", "0x30u", "0u")]),
+    ("x_cvrptw_d", True, [("x_cvrptw_d", "CVRPTW", "false", "0u", "0x3u")]),
+    ("x_cvrptw_e", True, [("x_cvrptw_e", "CVRPTW", "false", "0u", "0x4u")]),
+    ("p_cvrptw_a", False, [("p_cvrptw_a", "CVRPTW", "false", "0x03u", "0u")]),
+    ("p_cvrptw_b", False, [("p_cvrptw_b", "CVRPTW", "false", "0x0Cu", "0u")]),
+    ("p_cvrptw_c", False, [("p_cvrptw_c", "CVRPTW", "false", "0x30u", "0u")]),
+    ("p_cvrptw_d", False, [("p_cvrptw_d", "CVRPTW", "false", "0xC0u", "0u")]),
+    ("p_cvrptw_e", False, [("p_cvrptw_e", "CVRPTW", "false", "0u", ALL_B)]),
+    ("x_atsp16", True, [("x_atsp16", "ATSP", "true", ALL_E, ALL_B)]),
+    ("x_atsp32", True, [("x_atsp32", "ATSP", "false", ALL_E, ALL_B)]),
+    ("p_atsp", False, [("p_atsp16", "ATSP", "true", ALL_E, ALL_B),
+                       ("p_atsp32", "ATSP", "false", ALL_E, ALL_B)]),
+    ("x_qap", True, [("x_qap", "QAP", "false", ALL_E, ALL_B)]),
+    ("p_qap", False, [("p_qap", "QAP", "false", ALL_E, ALL_B)]),
+    ("x_gap", True, [("x_gap", "GAP", "false", ALL_E, ALL_B)]),
+    ("p_gap", False, [("p_gap", "GAP", "false", ALL_E, ALL_B)]),
+    ("x_knapsack", True, [("x_knapsack", "KNAPSACK", "false", ALL_E, ALL_B)]),
+    ("p_knapsack", False, [("p_knapsack", "KNAPSACK", "false", ALL_E, ALL_B)]),
+    ("x_tsp16", True, [("x_tsp16", "TSP", "true", ALL_E, ALL_B)]),
+    ("x_tsp32", True, [("x_tsp32", "TSP", "false", ALL_E, ALL_B)]),
+    ("p_tsp32", False, [("p_tsp32", "TSP", "false", ALL_E, ALL_B)]),
+]
+SOURCES = ["cgo_kernels.cu", "cgo_api.cu", "cgo_server.cu", "cgo_peaks.cu"]
+
+
+def _unit_defines(xf, sets):
+    # one value per definition (nvcc splits a definition's value at commas)
+    d = ["-DCGO_UNIT=1", "-DCGO_UNIT_XF=%s" % ("true" if xf else "false")]
+    for i, (name, model, t16, em, bm) in enumerate(sets, 1):
+        d += ["-DCGO_UNIT_S%d_%s=%s" % (i, k, v)
+              for k, v in (("NAME", name), ("MODEL", model), ("T16", t16), ("EM", em), ("BM", bm))]
+    return d
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,16 +90,21 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
-    def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
+    jobs = [("unit_%s.o" % name, "cgo_kernels.cu", _unit_defines(xf, sets))
+            for name, xf, sets in UNITS]
+    jobs += [(src.replace(".cu", ".o"), src, []) for src in SOURCES]
+
+    def compile_one(job):
+        name, src, defs = job
+        obj = os.path.join(OUT_DIR, name)
+        cmd = [cc, *_flags(extra), *defs, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError("nvcc failed for %s:\n%s" % (src, r.stderr))
+            raise RuntimeError("nvcc failed for %s (%s):\n%s" % (src, name, r.stderr))
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(max(1, min(len(jobs), 2 * (os.cpu_count() or 8)))) as ex:
+        results = list(ex.map(compile_one, jobs))
     if verbose or ptxas_info:
         for _, err in results:
             print(err)
@@ -67,6 +114,12 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s" % r.stderr)
     os.replace(tmp, LIB)
+    # every build compiles all units again: the objects are not kept
+    for o, _ in results:
+        try:
+            os.remove(o)
+        except OSError:
+            pass
     return LIB
 
 

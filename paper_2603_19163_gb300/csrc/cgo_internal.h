@@ -114,9 +114,6 @@ struct KInst {
 // host-side launchers (cgo_kernels.cu)
 cudaError_t launch_init(const KInst &h, cudaStream_t st);
 cudaError_t launch_init_aos(const KInst &h, const DevAos &a0, cudaStream_t st);
-// the single-solve kernel with island migration and crossover compiled in
-// (cgo_kernels_xf.cu); nullptr for an unknown shape
-const void *pick_evolve_xf(int model, int tri16, int wpm, int ns);
 cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int ns, int64_t smem_bytes,
                                  uint64_t timeout_ns, cudaStream_t st);
 cudaError_t launch_finalize(const KInst &h, cudaStream_t st);
@@ -131,8 +128,6 @@ int batch_ctas_per_sm(int model, int tri16, int xf, int warps, int wpm, int64_t 
 cudaError_t launch_batch(int model, int tri16, int xf, const KInst *d_insts, const int *d_list,
                          const int *d_count, int *d_next, int warps, int wpm, int64_t smem_bytes,
                          int grid, int64_t slice, uint64_t timeout_ns, cudaStream_t st);
-// the batched kernel with island migration and crossover (cgo_kernels_xf.cu)
-const void *pick_batch_xf(int model, int tri16, int wpm);
 // whether an instance's search takes island migration or crossover
 inline int takes_xf(const KInst &h) { return (h.islands > 1 || h.cross_q16 > 0) ? 1 : 0; }
 int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged);

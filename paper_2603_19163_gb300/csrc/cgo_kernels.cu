@@ -22,8 +22,8 @@
 #include "cgo_device.cuh"
 
 namespace cgo {
-#ifdef CGO_XF_UNIT
-// the second instantiation unit keeps its copies of the device code local
+#ifdef CGO_UNIT
+// a kernel unit keeps its copies of the device code local
 namespace {
 #endif
 
@@ -104,7 +104,7 @@ __host__ __device__ inline Layout make_layout(int64_t inst_bytes, int len, int m
   return L;
 }
 
-#ifndef CGO_XF_UNIT
+#ifndef CGO_UNIT
 int64_t instance_data_bytes(const KInst &h) {
   switch (h.model) {
     case TSP: return align16((int64_t)h.n * (h.n + 1) / 2 * (h.tri16 ? 2 : 4));
@@ -2844,7 +2844,45 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
   return 0;
 }
 
-#ifndef CGO_XF_UNIT
+// The kernels of one (model, matrix width, population-step code) set, by
+// launch shape: one or two generations in flight with 1, 2 or 4 warps per
+// generation, three or four with 4 (not with the population-step code, nor
+// for the asymmetric TSP); batched kernels with 1, 2 or 4 warps per member.
+// EM / BM select the shapes a translation unit instantiates (bit i of EM:
+// (wpm, ns) = (1,1) (2,1) (4,1) (1,2) (2,2) (4,2) (4,3) (4,4); bit i of BM:
+// wpm = 1, 2, 4); a shape outside them gives nullptr.
+#define CGO_EV(WPM_, NS_, BIT_)                                            \
+  if constexpr (((EM >> BIT_) & 1u) != 0u)                                 \
+    if (wpm == WPM_ && ns == NS_) return (const void *)evolve_kernel<MODEL, T16, WPM_, NS_, XF>;
+template <int MODEL, bool T16, bool XF, unsigned EM = 0xFFu>
+static const void *evolve_set(int wpm, int ns) {
+  if (wpm != 2 && wpm != 4) wpm = 1;
+  if constexpr (MODEL != ATSP && !XF) {
+    CGO_EV(4, 3, 6)
+    CGO_EV(4, 4, 7)
+  }
+  CGO_EV(1, 1, 0)
+  CGO_EV(2, 1, 1)
+  CGO_EV(4, 1, 2)
+  CGO_EV(1, 2, 3)
+  CGO_EV(2, 2, 4)
+  CGO_EV(4, 2, 5)
+  return nullptr;
+}
+#undef CGO_EV
+
+template <int MODEL, bool T16, bool XF, unsigned BM = 0x7u>
+static const void *batch_set(int wpm) {
+  if constexpr ((BM & 4u) != 0u)
+    if (wpm == 4) return (const void *)batch_kernel<MODEL, T16, 4, XF>;
+  if constexpr ((BM & 2u) != 0u)
+    if (wpm == 2) return (const void *)batch_kernel<MODEL, T16, 2, XF>;
+  if constexpr ((BM & 1u) != 0u)
+    if (wpm != 2 && wpm != 4) return (const void *)batch_kernel<MODEL, T16, 1, XF>;
+  return nullptr;
+}
+
+#ifndef CGO_UNIT
 // Philox-seeded Fisher-Yates / random bits / random integers for member p,
 // then its exact cost
 // Random start j (member j of a plain start, candidate j of a start pool):
@@ -3121,40 +3159,74 @@ cudaError_t build_triangle(const int32_t *d_mat, int n, int tri16, void *d_tri, 
   return counted(cudaGetLastError());
 }
 
-template <int MODEL, bool T16, bool XF>
-static const void *evolve_fn(int wpm, int ns) {
-  // three or four generations in flight: one candidate per lane of 4 warps
-  // (not built for ATSP)
-  if constexpr (MODEL != ATSP) {
-    if (ns == 4) return wpm == 4 ? (const void *)evolve_kernel<MODEL, T16, 4, 4, XF> : nullptr;
-    if (ns == 3) return wpm == 4 ? (const void *)evolve_kernel<MODEL, T16, 4, 3, XF> : nullptr;
-  }
-  if (ns != 1 && ns != 2) return nullptr;
-  if (ns == 2) {
-    if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2, XF>;
-    if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 2, XF>;
-    return (const void *)evolve_kernel<MODEL, T16, 1, 2, XF>;
-  }
-  if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 1, XF>;
-  if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 1, XF>;
-  return (const void *)evolve_kernel<MODEL, T16, 1, 1, XF>;
+
+// The kernel sets are instantiated in translation units of their own, which
+// compile in parallel: this file again, compiled with CGO_UNIT and the unit's
+// sets defined (the unit table in build.py names them, at most two per
+// unit); this unit keeps the
+// set the benchmark's single solve runs (TSP, int16 triangle, without the
+// population steps).  A unit returns nullptr for shapes it does not hold.
+#define CGO_UNIT_DECL(NAME)                        \
+  const void *unit_evolve_##NAME(int wpm, int ns); \
+  const void *unit_batch_##NAME(int wpm);
+CGO_UNIT_DECL(p_tsp32)
+CGO_UNIT_DECL(p_atsp16)
+CGO_UNIT_DECL(p_atsp32)
+CGO_UNIT_DECL(p_qap)
+CGO_UNIT_DECL(p_knapsack)
+CGO_UNIT_DECL(p_gap)
+CGO_UNIT_DECL(p_cvrptw_a)
+CGO_UNIT_DECL(p_cvrptw_b)
+CGO_UNIT_DECL(p_cvrptw_c)
+CGO_UNIT_DECL(p_cvrptw_d)
+CGO_UNIT_DECL(p_cvrptw_e)
+CGO_UNIT_DECL(x_tsp16)
+CGO_UNIT_DECL(x_tsp32)
+CGO_UNIT_DECL(x_atsp16)
+CGO_UNIT_DECL(x_atsp32)
+CGO_UNIT_DECL(x_qap)
+CGO_UNIT_DECL(x_knapsack)
+CGO_UNIT_DECL(x_gap)
+CGO_UNIT_DECL(x_cvrptw_a)
+CGO_UNIT_DECL(x_cvrptw_b)
+CGO_UNIT_DECL(x_cvrptw_c)
+CGO_UNIT_DECL(x_cvrptw_d)
+CGO_UNIT_DECL(x_cvrptw_e)
+#undef CGO_UNIT_DECL
+
+// the first unit of a list that holds the shape
+template <class... F>
+static const void *first_evolve(int wpm, int ns, F... units) {
+  const void *r = nullptr;
+  ((r = r ? r : units(wpm, ns)), ...);
+  return r;
+}
+template <class... F>
+static const void *first_batch(int wpm, F... units) {
+  const void *r = nullptr;
+  ((r = r ? r : units(wpm)), ...);
+  return r;
 }
 
-// the kernel of a single solve: with the migration / crossover code (built in
-// the translation unit of its own, cgo_kernels_xf.cu) only when the solve
-// takes either
+// the kernel of a single solve: with the migration / crossover code (the
+// x_ sets) only when the solve takes either
 static const void *pick_evolve(const KInst &h, int wpm, int ns) {
-  if (takes_xf(h)) return pick_evolve_xf(h.model, h.tri16, wpm, ns);
+  const bool xf = takes_xf(h) != 0, t16 = h.tri16 != 0;
   switch (h.model) {
     case TSP:
-      return h.tri16 ? evolve_fn<TSP, true, false>(wpm, ns) : evolve_fn<TSP, false, false>(wpm, ns);
-    case QAP: return evolve_fn<QAP, false, false>(wpm, ns);
-    case CVRPTW: return evolve_fn<CVRPTW, false, false>(wpm, ns);
-    case KNAPSACK: return evolve_fn<KNAPSACK, false, false>(wpm, ns);
-    case GAP: return evolve_fn<GAP, false, false>(wpm, ns);
-    case ATSP:  // one or two generations in flight
-      if (ns > 2) return nullptr;
-      return h.tri16 ? evolve_fn<ATSP, true, false>(wpm, ns) : evolve_fn<ATSP, false, false>(wpm, ns);
+      if (xf) return t16 ? unit_evolve_x_tsp16(wpm, ns) : unit_evolve_x_tsp32(wpm, ns);
+      return t16 ? evolve_set<TSP, true, false>(wpm, ns) : unit_evolve_p_tsp32(wpm, ns);
+    case ATSP:
+      if (xf) return t16 ? unit_evolve_x_atsp16(wpm, ns) : unit_evolve_x_atsp32(wpm, ns);
+      return t16 ? unit_evolve_p_atsp16(wpm, ns) : unit_evolve_p_atsp32(wpm, ns);
+    case QAP: return xf ? unit_evolve_x_qap(wpm, ns) : unit_evolve_p_qap(wpm, ns);
+    case CVRPTW:
+      return xf ? first_evolve(wpm, ns, unit_evolve_x_cvrptw_a, unit_evolve_x_cvrptw_b,
+                               unit_evolve_x_cvrptw_c)
+                : first_evolve(wpm, ns, unit_evolve_p_cvrptw_a, unit_evolve_p_cvrptw_b,
+                               unit_evolve_p_cvrptw_c, unit_evolve_p_cvrptw_d);
+    case KNAPSACK: return xf ? unit_evolve_x_knapsack(wpm, ns) : unit_evolve_p_knapsack(wpm, ns);
+    case GAP: return xf ? unit_evolve_x_gap(wpm, ns) : unit_evolve_p_gap(wpm, ns);
   }
   return nullptr;
 }
@@ -3214,24 +3286,23 @@ cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int ns, int
       cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(warps * 32), args, (size_t)smem_bytes, st));
 }
 
-template <int MODEL, bool T16>
-static const void *batch_fn(int wpm) {
-  if (wpm == 4) return (const void *)batch_kernel<MODEL, T16, 4, false>;
-  if (wpm == 2) return (const void *)batch_kernel<MODEL, T16, 2, false>;
-  return (const void *)batch_kernel<MODEL, T16, 1, false>;
-}
 
 // the batched kernel of a bucket: with the migration / crossover code only
 // for instances that take either
 static const void *pick_batch(int model, int tri16, int xf, int wpm) {
-  if (xf) return pick_batch_xf(model, tri16, wpm);
   switch (model) {
-    case TSP: return tri16 ? batch_fn<TSP, true>(wpm) : batch_fn<TSP, false>(wpm);
-    case QAP: return batch_fn<QAP, false>(wpm);
-    case CVRPTW: return batch_fn<CVRPTW, false>(wpm);
-    case KNAPSACK: return batch_fn<KNAPSACK, false>(wpm);
-    case GAP: return batch_fn<GAP, false>(wpm);
-    case ATSP: return tri16 ? batch_fn<ATSP, true>(wpm) : batch_fn<ATSP, false>(wpm);
+    case TSP:
+      if (xf) return tri16 ? unit_batch_x_tsp16(wpm) : unit_batch_x_tsp32(wpm);
+      return tri16 ? batch_set<TSP, true, false>(wpm) : unit_batch_p_tsp32(wpm);
+    case ATSP:
+      if (xf) return tri16 ? unit_batch_x_atsp16(wpm) : unit_batch_x_atsp32(wpm);
+      return tri16 ? unit_batch_p_atsp16(wpm) : unit_batch_p_atsp32(wpm);
+    case QAP: return xf ? unit_batch_x_qap(wpm) : unit_batch_p_qap(wpm);
+    case CVRPTW:
+      return xf ? first_batch(wpm, unit_batch_x_cvrptw_d, unit_batch_x_cvrptw_e)
+                : first_batch(wpm, unit_batch_p_cvrptw_e);
+    case KNAPSACK: return xf ? unit_batch_x_knapsack(wpm) : unit_batch_p_knapsack(wpm);
+    case GAP: return xf ? unit_batch_x_gap(wpm) : unit_batch_p_gap(wpm);
   }
   return nullptr;
 }
@@ -3272,51 +3343,22 @@ int64_t evolve_smem_bytes(const KInst &h, int warps, int wpm, int ns, bool stage
   return L.total;
 }
 
-#else   // CGO_XF_UNIT: the single-solve and batched kernels with migration and crossover
-template <int MODEL, bool T16>
-static const void *evolve_fn_xf(int wpm, int ns) {
-  if (ns != 1 && ns != 2) return nullptr;  // built with one or two generations in flight
-  if (ns == 2) {
-    if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 2, true>;
-    if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 2, true>;
-    return (const void *)evolve_kernel<MODEL, T16, 1, 2, true>;
-  }
-  if (wpm == 4) return (const void *)evolve_kernel<MODEL, T16, 4, 1, true>;
-  if (wpm == 2) return (const void *)evolve_kernel<MODEL, T16, 2, 1, true>;
-  return (const void *)evolve_kernel<MODEL, T16, 1, 1, true>;
-}
-
-template <int MODEL, bool T16>
-static const void *batch_fn_xf(int wpm) {
-  if (wpm == 4) return (const void *)batch_kernel<MODEL, T16, 4, true>;
-  if (wpm == 2) return (const void *)batch_kernel<MODEL, T16, 2, true>;
-  return (const void *)batch_kernel<MODEL, T16, 1, true>;
-}
+#else  // CGO_UNIT: a kernel unit exports the kernel sets it instantiates
 }  // namespace
-
-const void *pick_batch_xf(int model, int tri16, int wpm) {
-  switch (model) {
-    case TSP: return tri16 ? batch_fn_xf<TSP, true>(wpm) : batch_fn_xf<TSP, false>(wpm);
-    case QAP: return batch_fn_xf<QAP, false>(wpm);
-    case CVRPTW: return batch_fn_xf<CVRPTW, false>(wpm);
-    case KNAPSACK: return batch_fn_xf<KNAPSACK, false>(wpm);
-    case GAP: return batch_fn_xf<GAP, false>(wpm);
-    case ATSP: return tri16 ? batch_fn_xf<ATSP, true>(wpm) : batch_fn_xf<ATSP, false>(wpm);
-  }
-  return nullptr;
-}
-
-const void *pick_evolve_xf(int model, int tri16, int wpm, int ns) {
-  switch (model) {
-    case TSP: return tri16 ? evolve_fn_xf<TSP, true>(wpm, ns) : evolve_fn_xf<TSP, false>(wpm, ns);
-    case QAP: return evolve_fn_xf<QAP, false>(wpm, ns);
-    case CVRPTW: return evolve_fn_xf<CVRPTW, false>(wpm, ns);
-    case KNAPSACK: return evolve_fn_xf<KNAPSACK, false>(wpm, ns);
-    case GAP: return evolve_fn_xf<GAP, false>(wpm, ns);
-    case ATSP: return tri16 ? evolve_fn_xf<ATSP, true>(wpm, ns) : evolve_fn_xf<ATSP, false>(wpm, ns);
-  }
-  return nullptr;
-}
-#endif  // CGO_XF_UNIT
+// set i of the unit: CGO_UNIT_S<i>_NAME, _MODEL, _T16, _EM, _BM (compiler
+// definitions, one value each)
+#define CGO_UNIT_SET_(NAME, MODEL, T16, EM, BM)                                \
+  const void *unit_evolve_##NAME(int wpm, int ns) {                            \
+    return evolve_set<MODEL, T16, CGO_UNIT_XF, EM>(wpm, ns);                   \
+  }                                                                            \
+  const void *unit_batch_##NAME(int wpm) { return batch_set<MODEL, T16, CGO_UNIT_XF, BM>(wpm); }
+#define CGO_UNIT_SET(NAME, MODEL, T16, EM, BM) CGO_UNIT_SET_(NAME, MODEL, T16, EM, BM)
+CGO_UNIT_SET(CGO_UNIT_S1_NAME, CGO_UNIT_S1_MODEL, CGO_UNIT_S1_T16, CGO_UNIT_S1_EM, CGO_UNIT_S1_BM)
+#ifdef CGO_UNIT_S2_NAME
+CGO_UNIT_SET(CGO_UNIT_S2_NAME, CGO_UNIT_S2_MODEL, CGO_UNIT_S2_T16, CGO_UNIT_S2_EM, CGO_UNIT_S2_BM)
+#endif
+#undef CGO_UNIT_SET
+#undef CGO_UNIT_SET_
+#endif  // CGO_UNIT
 
 }  // namespace cgo
