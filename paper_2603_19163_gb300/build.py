@@ -19,42 +19,54 @@ LIB = os.path.join(OUT_DIR, "libcgo.so")
 # Kernel units: cgo_kernels.cu compiled again with CGO_UNIT defined, each
 # instantiating a share of the kernel sets, so that they compile in parallel
 # (cgo_kernels.cu itself keeps the host code and the benchmark's TSP set).
-# Entry: object name, population-step code compiled in, then the sets as
-# (name, model, int16 matrix, evolve shape mask, batch shape mask); the names
-# are those declared in cgo_kernels.cu.  CVRPTW's kernels are the slowest to
-# compile and are spread over several units.
-ALL_E, ALL_B = "0xFFu", "0x7u"
+# Entry: object name, the population-step code compiled in (0 none, 1
+# crossover, 2 island migration and crossover), then the sets as (name,
+# model, int16 matrix, evolve shape mask, batch shape mask); the names are
+# those declared in cgo_kernels.cu.  Batched solves use the sets 0 and 2;
+# the crossover-only sets hold single-solve kernels.  CVRPTW's kernels are
+# the slowest to compile and are spread over several units.
+ALL_E, ALL_B, NO_B = "0xFFu", "0x7u", "0u"
 UNITS = [
-    ("x_cvrptw_a", True, [("x_cvrptw_a", "CVRPTW", "false", "0x03u", "0u")]),
-    ("x_cvrptw_b", True, [("x_cvrptw_b", "CVRPTW", "false", "0x0Cu", "0u")]),
-    ("x_cvrptw_c", True, [("x_cvrptw_c", "CVRPTW", "false", "0x30u", "0u")]),
-    ("x_cvrptw_d", True, [("x_cvrptw_d", "CVRPTW", "false", "0u", "0x3u")]),
-    ("x_cvrptw_e", True, [("x_cvrptw_e", "CVRPTW", "false", "0u", "0x4u")]),
-    ("p_cvrptw_a", False, [("p_cvrptw_a", "CVRPTW", "false", "0x03u", "0u")]),
-    ("p_cvrptw_b", False, [("p_cvrptw_b", "CVRPTW", "false", "0x0Cu", "0u")]),
-    ("p_cvrptw_c", False, [("p_cvrptw_c", "CVRPTW", "false", "0x30u", "0u")]),
-    ("p_cvrptw_d", False, [("p_cvrptw_d", "CVRPTW", "false", "0xC0u", "0u")]),
-    ("p_cvrptw_e", False, [("p_cvrptw_e", "CVRPTW", "false", "0u", ALL_B)]),
-    ("x_atsp16", True, [("x_atsp16", "ATSP", "true", ALL_E, ALL_B)]),
-    ("x_atsp32", True, [("x_atsp32", "ATSP", "false", ALL_E, ALL_B)]),
-    ("p_atsp", False, [("p_atsp16", "ATSP", "true", ALL_E, ALL_B),
-                       ("p_atsp32", "ATSP", "false", ALL_E, ALL_B)]),
-    ("x_qap", True, [("x_qap", "QAP", "false", ALL_E, ALL_B)]),
-    ("p_qap", False, [("p_qap", "QAP", "false", ALL_E, ALL_B)]),
-    ("x_gap", True, [("x_gap", "GAP", "false", ALL_E, ALL_B)]),
-    ("p_gap", False, [("p_gap", "GAP", "false", ALL_E, ALL_B)]),
-    ("x_knapsack", True, [("x_knapsack", "KNAPSACK", "false", ALL_E, ALL_B)]),
-    ("p_knapsack", False, [("p_knapsack", "KNAPSACK", "false", ALL_E, ALL_B)]),
-    ("x_tsp16", True, [("x_tsp16", "TSP", "true", ALL_E, ALL_B)]),
-    ("x_tsp32", True, [("x_tsp32", "TSP", "false", ALL_E, ALL_B)]),
-    ("p_tsp32", False, [("p_tsp32", "TSP", "false", ALL_E, ALL_B)]),
+    ("x_cvrptw_a", 2, [("x_cvrptw_a", "CVRPTW", "false", "0x03u", NO_B)]),
+    ("x_cvrptw_b", 2, [("x_cvrptw_b", "CVRPTW", "false", "0x0Cu", NO_B)]),
+    ("x_cvrptw_c", 2, [("x_cvrptw_c", "CVRPTW", "false", "0x30u", NO_B)]),
+    ("x_cvrptw_d", 2, [("x_cvrptw_d", "CVRPTW", "false", "0u", "0x3u")]),
+    ("x_cvrptw_e", 2, [("x_cvrptw_e", "CVRPTW", "false", "0u", "0x4u")]),
+    ("c_cvrptw_a", 1, [("c_cvrptw_a", "CVRPTW", "false", "0x03u", NO_B)]),
+    ("c_cvrptw_b", 1, [("c_cvrptw_b", "CVRPTW", "false", "0x0Cu", NO_B)]),
+    ("c_cvrptw_c", 1, [("c_cvrptw_c", "CVRPTW", "false", "0x30u", NO_B)]),
+    ("p_cvrptw_a", 0, [("p_cvrptw_a", "CVRPTW", "false", "0x03u", NO_B)]),
+    ("p_cvrptw_b", 0, [("p_cvrptw_b", "CVRPTW", "false", "0x0Cu", NO_B)]),
+    ("p_cvrptw_c", 0, [("p_cvrptw_c", "CVRPTW", "false", "0x30u", NO_B)]),
+    ("p_cvrptw_d", 0, [("p_cvrptw_d", "CVRPTW", "false", "0xC0u", NO_B)]),
+    ("p_cvrptw_e", 0, [("p_cvrptw_e", "CVRPTW", "false", "0u", ALL_B)]),
+    ("x_atsp16", 2, [("x_atsp16", "ATSP", "true", ALL_E, ALL_B)]),
+    ("x_atsp32", 2, [("x_atsp32", "ATSP", "false", ALL_E, ALL_B)]),
+    ("c_atsp", 1, [("c_atsp16", "ATSP", "true", ALL_E, NO_B),
+                   ("c_atsp32", "ATSP", "false", ALL_E, NO_B)]),
+    ("p_atsp", 0, [("p_atsp16", "ATSP", "true", ALL_E, ALL_B),
+                   ("p_atsp32", "ATSP", "false", ALL_E, ALL_B)]),
+    ("x_qap", 2, [("x_qap", "QAP", "false", ALL_E, ALL_B)]),
+    ("c_qap", 1, [("c_qap", "QAP", "false", ALL_E, NO_B)]),
+    ("p_qap", 0, [("p_qap", "QAP", "false", ALL_E, ALL_B)]),
+    ("x_gap", 2, [("x_gap", "GAP", "false", ALL_E, ALL_B)]),
+    ("c_gap", 1, [("c_gap", "GAP", "false", ALL_E, NO_B)]),
+    ("p_gap", 0, [("p_gap", "GAP", "false", ALL_E, ALL_B)]),
+    ("x_knapsack", 2, [("x_knapsack", "KNAPSACK", "false", ALL_E, ALL_B)]),
+    ("c_knapsack", 1, [("c_knapsack", "KNAPSACK", "false", ALL_E, NO_B)]),
+    ("p_knapsack", 0, [("p_knapsack", "KNAPSACK", "false", ALL_E, ALL_B)]),
+    ("x_tsp16", 2, [("x_tsp16", "TSP", "true", ALL_E, ALL_B)]),
+    ("x_tsp32", 2, [("x_tsp32", "TSP", "false", ALL_E, ALL_B)]),
+    ("c_tsp", 1, [("c_tsp16", "TSP", "true", ALL_E, NO_B),
+                  ("c_tsp32", "TSP", "false", ALL_E, NO_B)]),
+    ("p_tsp32", 0, [("p_tsp32", "TSP", "false", ALL_E, ALL_B)]),
 ]
 SOURCES = ["cgo_kernels.cu", "cgo_api.cu", "cgo_server.cu", "cgo_peaks.cu"]
 
 
 def _unit_defines(xf, sets):
     # one value per definition (nvcc splits a definition's value at commas)
-    d = ["-DCGO_UNIT=1", "-DCGO_UNIT_XF=%s" % ("true" if xf else "false")]
+    d = ["-DCGO_UNIT=1", "-DCGO_UNIT_XF=%d" % xf]
     for i, (name, model, t16, em, bm) in enumerate(sets, 1):
         d += ["-DCGO_UNIT_S%d_%s=%s" % (i, k, v)
               for k, v in (("NAME", name), ("MODEL", model), ("T16", t16), ("EM", em), ("BM", bm))]

@@ -1374,7 +1374,7 @@ cgo_status cgo_solve_batch(cgo_problem *const *probs, const cgo_params *per_in, 
     if ((s = batch_shape(p, per[i], h, &wpm, &warps, &need, &cls)) != CGO_OK)
       return fail(s, "problem %d: %s", i, cgo_last_error());
     int b = -1;
-    const int xf = takes_xf(h);
+    const int xf = takes_xf(h) != 0 ? 1 : 0;  // batched kernels: one set with both steps
     for (size_t k = 0; k < buckets.size(); ++k)
       if (buckets[k].model == h.model && buckets[k].tri16 == p->tri16 && buckets[k].xf == xf &&
           buckets[k].wpm == wpm && buckets[k].warps == warps && buckets[k].smem == cls)

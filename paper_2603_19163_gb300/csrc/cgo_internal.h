@@ -129,7 +129,8 @@ cudaError_t launch_batch(int model, int tri16, int xf, const KInst *d_insts, con
                          const int *d_count, int *d_next, int warps, int wpm, int64_t smem_bytes,
                          int grid, int64_t slice, uint64_t timeout_ns, cudaStream_t st);
 // whether an instance's search takes island migration or crossover
-inline int takes_xf(const KInst &h) { return (h.islands > 1 || h.cross_q16 > 0) ? 1 : 0; }
+// (2: migration, and crossover if any; 1: crossover alone; 0: neither)
+inline int takes_xf(const KInst &h) { return h.islands > 1 ? 2 : (h.cross_q16 > 0 ? 1 : 0); }
 int64_t batch_smem_bytes(const KInst &h, int warps, int wpm, bool staged);
 // shared-memory needs of the evolve kernel
 int64_t smem_per_warp(const KInst &h);

@@ -2032,10 +2032,11 @@ __device__ __forceinline__ void window_cross(const KInst &I, const View X, unsig
 }
 
 // ---------------------------------------------------------- evolve unit
-// XF: the population steps beyond AOS and injection (island migration,
-// crossover) are compiled in; single solves without them use kernels
-// without that code, whose generation loop then allocates registers alone.
-template <int MODEL, bool T16, int WPM, int NS, bool XF>
+// XF: the population steps beyond AOS and injection compiled in: 0 none,
+// 1 crossover, 2 island migration and crossover.  Solves take the kernels
+// with no more of that code than they use, whose generation loop then
+// allocates registers alone.
+template <int MODEL, bool T16, int WPM, int NS, int XF>
 __device__ void evolve_members(const KInst &I, const View &X, unsigned char *smem, const Layout &Lo,
                                int p0, int nsol, int warps, uint64_t timeout_ns) {
   constexpr int NO = Enc<MODEL>::NO;
@@ -2375,8 +2376,8 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
 
     // ------------------------------------------------ AOS window end
     const bool inject = I.E > 0 && (g % (uint32_t)I.E) == 0;
-    const bool migr = XF && I.islands > 1 && (g % I.mperiod) == 0;
-    const bool cross = XF && I.cross_q16 > 0;
+    const bool migr = XF == 2 && I.islands > 1 && (g % I.mperiod) == 0;
+    const bool cross = XF != 0 && I.cross_q16 > 0;
     uint32_t tot[NO * 2 + 6];
     if (packed) {
       // a lane counts at most 3 * cpl * U * mine uses per window, so the warp
@@ -2486,11 +2487,13 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
     stats_zero(st);
 
     if constexpr (XF) {
-      if (migr) {
-        const int nbar = window_migrate<MODEL, NW>(I, X, smem, Lo, G, p0, mine, ngroups, g, nb,
-                                                   timeout_ns, nact, inject || cross, cross);
-        if (nbar < 0) return;
-        nb += (uint32_t)nbar;
+      if constexpr (XF == 2) {
+        if (migr) {
+          const int nbar = window_migrate<MODEL, NW>(I, X, smem, Lo, G, p0, mine, ngroups, g, nb,
+                                                     timeout_ns, nact, inject || cross, cross);
+          if (nbar < 0) return;
+          nb += (uint32_t)nbar;
+        }
       }
       if (cross) {
         // [R29] the crossovers of a group that has a member crossing
@@ -2725,7 +2728,7 @@ __device__ View make_view(const KInst &I, unsigned char *smem, bool staged) {
 // Single solve: CTA b covers members [b * groups, (b+1) * groups) of the
 // instance, one member per group of WPM warps (cooperative launch, so that
 // all members are resident together for the window barriers).
-template <int MODEL, bool T16, int WPM, int NS, bool XF>
+template <int MODEL, bool T16, int WPM, int NS, int XF>
 __global__ void __launch_bounds__((WPM * NS > kMaxWarps ? WPM * NS : kMaxWarps) * 32, 1)
     evolve_kernel(const __grid_constant__ KInst I, int warps, uint64_t timeout_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2745,7 +2748,7 @@ __global__ void __launch_bounds__((WPM * NS > kMaxWarps ? WPM * NS : kMaxWarps) 
 // loop over them) for up to `slice` generations, with CTA-local window
 // barriers; the instance's scalars are updated in place.  Instances that
 // have reached their generation budget are skipped.
-template <int MODEL, bool T16, int WPM, bool XF>
+template <int MODEL, bool T16, int WPM, int XF>
 __global__ void __launch_bounds__(kMaxWarps * 32, 1)
     batch_kernel(const KInst *__restrict__ insts, const int *__restrict__ list,
                  const int *__restrict__ count_ptr, int *next, int warps, int64_t slice,
@@ -2854,7 +2857,7 @@ __device__ long long full_cost(const KInst &I, const int32_t *x) {
 #define CGO_EV(WPM_, NS_, BIT_)                                            \
   if constexpr (((EM >> BIT_) & 1u) != 0u)                                 \
     if (wpm == WPM_ && ns == NS_) return (const void *)evolve_kernel<MODEL, T16, WPM_, NS_, XF>;
-template <int MODEL, bool T16, bool XF, unsigned EM = 0xFFu>
+template <int MODEL, bool T16, int XF, unsigned EM = 0xFFu>
 static const void *evolve_set(int wpm, int ns) {
   if (wpm != 2 && wpm != 4) wpm = 1;
   if constexpr (MODEL != ATSP && !XF) {
@@ -2871,7 +2874,7 @@ static const void *evolve_set(int wpm, int ns) {
 }
 #undef CGO_EV
 
-template <int MODEL, bool T16, bool XF, unsigned BM = 0x7u>
+template <int MODEL, bool T16, int XF, unsigned BM = 0x7u>
 static const void *batch_set(int wpm) {
   if constexpr ((BM & 4u) != 0u)
     if (wpm == 4) return (const void *)batch_kernel<MODEL, T16, 4, XF>;
@@ -3180,6 +3183,16 @@ CGO_UNIT_DECL(p_cvrptw_b)
 CGO_UNIT_DECL(p_cvrptw_c)
 CGO_UNIT_DECL(p_cvrptw_d)
 CGO_UNIT_DECL(p_cvrptw_e)
+CGO_UNIT_DECL(c_tsp16)
+CGO_UNIT_DECL(c_tsp32)
+CGO_UNIT_DECL(c_atsp16)
+CGO_UNIT_DECL(c_atsp32)
+CGO_UNIT_DECL(c_qap)
+CGO_UNIT_DECL(c_knapsack)
+CGO_UNIT_DECL(c_gap)
+CGO_UNIT_DECL(c_cvrptw_a)
+CGO_UNIT_DECL(c_cvrptw_b)
+CGO_UNIT_DECL(c_cvrptw_c)
 CGO_UNIT_DECL(x_tsp16)
 CGO_UNIT_DECL(x_tsp32)
 CGO_UNIT_DECL(x_atsp16)
@@ -3208,25 +3221,39 @@ static const void *first_batch(int wpm, F... units) {
   return r;
 }
 
-// the kernel of a single solve: with the migration / crossover code (the
-// x_ sets) only when the solve takes either
+// the kernel of a single solve: with the crossover code (the c_ sets) or
+// the migration and crossover code (the x_ sets) only when the solve takes
+// them
 static const void *pick_evolve(const KInst &h, int wpm, int ns) {
-  const bool xf = takes_xf(h) != 0, t16 = h.tri16 != 0;
+  const int xf = takes_xf(h);
+  const bool t16 = h.tri16 != 0;
   switch (h.model) {
     case TSP:
-      if (xf) return t16 ? unit_evolve_x_tsp16(wpm, ns) : unit_evolve_x_tsp32(wpm, ns);
-      return t16 ? evolve_set<TSP, true, false>(wpm, ns) : unit_evolve_p_tsp32(wpm, ns);
+      if (xf == 2) return t16 ? unit_evolve_x_tsp16(wpm, ns) : unit_evolve_x_tsp32(wpm, ns);
+      if (xf == 1) return t16 ? unit_evolve_c_tsp16(wpm, ns) : unit_evolve_c_tsp32(wpm, ns);
+      return t16 ? evolve_set<TSP, true, 0>(wpm, ns) : unit_evolve_p_tsp32(wpm, ns);
     case ATSP:
-      if (xf) return t16 ? unit_evolve_x_atsp16(wpm, ns) : unit_evolve_x_atsp32(wpm, ns);
+      if (xf == 2) return t16 ? unit_evolve_x_atsp16(wpm, ns) : unit_evolve_x_atsp32(wpm, ns);
+      if (xf == 1) return t16 ? unit_evolve_c_atsp16(wpm, ns) : unit_evolve_c_atsp32(wpm, ns);
       return t16 ? unit_evolve_p_atsp16(wpm, ns) : unit_evolve_p_atsp32(wpm, ns);
-    case QAP: return xf ? unit_evolve_x_qap(wpm, ns) : unit_evolve_p_qap(wpm, ns);
+    case QAP:
+      return xf == 2 ? unit_evolve_x_qap(wpm, ns)
+                     : (xf == 1 ? unit_evolve_c_qap(wpm, ns) : unit_evolve_p_qap(wpm, ns));
     case CVRPTW:
-      return xf ? first_evolve(wpm, ns, unit_evolve_x_cvrptw_a, unit_evolve_x_cvrptw_b,
-                               unit_evolve_x_cvrptw_c)
-                : first_evolve(wpm, ns, unit_evolve_p_cvrptw_a, unit_evolve_p_cvrptw_b,
-                               unit_evolve_p_cvrptw_c, unit_evolve_p_cvrptw_d);
-    case KNAPSACK: return xf ? unit_evolve_x_knapsack(wpm, ns) : unit_evolve_p_knapsack(wpm, ns);
-    case GAP: return xf ? unit_evolve_x_gap(wpm, ns) : unit_evolve_p_gap(wpm, ns);
+      if (xf == 2)
+        return first_evolve(wpm, ns, unit_evolve_x_cvrptw_a, unit_evolve_x_cvrptw_b,
+                            unit_evolve_x_cvrptw_c);
+      if (xf == 1)
+        return first_evolve(wpm, ns, unit_evolve_c_cvrptw_a, unit_evolve_c_cvrptw_b,
+                            unit_evolve_c_cvrptw_c);
+      return first_evolve(wpm, ns, unit_evolve_p_cvrptw_a, unit_evolve_p_cvrptw_b,
+                          unit_evolve_p_cvrptw_c, unit_evolve_p_cvrptw_d);
+    case KNAPSACK:
+      return xf == 2 ? unit_evolve_x_knapsack(wpm, ns)
+                     : (xf == 1 ? unit_evolve_c_knapsack(wpm, ns) : unit_evolve_p_knapsack(wpm, ns));
+    case GAP:
+      return xf == 2 ? unit_evolve_x_gap(wpm, ns)
+                     : (xf == 1 ? unit_evolve_c_gap(wpm, ns) : unit_evolve_p_gap(wpm, ns));
   }
   return nullptr;
 }
@@ -3287,13 +3314,13 @@ cudaError_t launch_evolve_single(const KInst &h, int warps, int wpm, int ns, int
 }
 
 
-// the batched kernel of a bucket: with the migration / crossover code only
-// for instances that take either
+// the batched kernel of a bucket: with the migration and crossover code
+// (the x_ sets) for instances that take either
 static const void *pick_batch(int model, int tri16, int xf, int wpm) {
   switch (model) {
     case TSP:
       if (xf) return tri16 ? unit_batch_x_tsp16(wpm) : unit_batch_x_tsp32(wpm);
-      return tri16 ? batch_set<TSP, true, false>(wpm) : unit_batch_p_tsp32(wpm);
+      return tri16 ? batch_set<TSP, true, 0>(wpm) : unit_batch_p_tsp32(wpm);
     case ATSP:
       if (xf) return tri16 ? unit_batch_x_atsp16(wpm) : unit_batch_x_atsp32(wpm);
       return tri16 ? unit_batch_p_atsp16(wpm) : unit_batch_p_atsp32(wpm);

@@ -232,7 +232,7 @@ void server_loop(cgo_server *S) {
       int wpm = 1, warps = 1;
       int64_t need = 0, cls = 0;
       if (batch_shape(p, r->params, h, &wpm, &warps, &need, &cls) != CGO_OK ||
-          (r->bucket = bucket_for(S, h.model, p->tri16, takes_xf(h), wpm, warps, cls)) < 0) {
+          (r->bucket = bucket_for(S, h.model, p->tri16, takes_xf(h) != 0 ? 1 : 0, wpm, warps, cls)) < 0) {
         fail_all(S, CGO_ERR_UNSUPPORTED, "no batched launch shape for a request");
         return;
       }
