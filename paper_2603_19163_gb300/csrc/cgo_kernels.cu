@@ -393,27 +393,39 @@ __device__ long long qap_step(const View &X, const PermEl *sol, const PMove &mv,
 // (virtual) permutation V: only the positions H = [b1, b4) change, so
 //   delta = sum_{i in H} sum_j F[i][j] (D[V'_i][V'_j] - D[V_i][V_j])
 //         + sum_{i not in H} sum_{j in H} F[i][j] (D[V_i][V'_j] - D[V_i][V_j]),
-// with V'_q = V_{inv(q)} (64-bit arithmetic: O(n |H|) terms).
+// with V'_q = V_{inv(q)} (64-bit arithmetic: O(n |H|) terms).  H is taken
+// in chunks of up to 32 positions whose old and new values are looked up
+// once; the rows of a chunk are summed column by column, so each column's
+// values are looked up once per chunk too.
 __device__ long long qap_block_step(const View &X, const PermEl *sol, const PMove &mv,
                                     const PMove &p0, const PMove &p1, int np) {
+  constexpr int kChunk = 32;
   const int n = X.n, lo = mv.b1, hi = mv.b4, qs = X.qs;
   const int32_t *F = X.F, *D = X.D;
   auto V = [&](int q) { return vlook(sol, q, p0, p1, np); };
+  int vH[kChunk], wH[kChunk];
   long long acc = 0;
-  for (int i = lo; i < hi; ++i) {
-    const int vi = V(i), wi = V(perm_inv(mv, i));
-    const int32_t *Fi = F + (size_t)i * qs, *Dv = D + (size_t)vi * qs, *Dw = D + (size_t)wi * qs;
+  for (int c0 = lo; c0 < hi; c0 += kChunk) {
+    const int len = min(hi - c0, kChunk);
+    for (int t = 0; t < len; ++t) {
+      vH[t] = V(c0 + t);
+      wH[t] = V(perm_inv(mv, c0 + t));
+    }
+    // rows in the chunk, every column
     for (int j = 0; j < n; ++j) {
       const int vj = V(j), wj = (j >= lo && j < hi) ? V(perm_inv(mv, j)) : vj;
-      acc += (long long)Fi[j] * ((long long)Dw[wj] - (long long)Dv[vj]);
+      const int32_t *Fj = F + (size_t)c0 * qs + j;
+      for (int t = 0; t < len; ++t)
+        acc += (long long)Fj[(size_t)t * qs] *
+               ((long long)D[(size_t)wH[t] * qs + wj] - (long long)D[(size_t)vH[t] * qs + vj]);
     }
-  }
-  for (int i = 0; i < n; ++i) {
-    if (i >= lo && i < hi) continue;
-    const int vi = V(i);
-    const int32_t *Fi = F + (size_t)i * qs, *Dv = D + (size_t)vi * qs;
-    for (int j = lo; j < hi; ++j)
-      acc += (long long)Fi[j] * ((long long)Dv[V(perm_inv(mv, j))] - (long long)Dv[V(j)]);
+    // rows outside H, the chunk's columns
+    for (int i = 0; i < n; ++i) {
+      if (i >= lo && i < hi) continue;
+      const int vi = V(i);
+      const int32_t *Fi = F + (size_t)i * qs + c0, *Dv = D + (size_t)vi * qs;
+      for (int t = 0; t < len; ++t) acc += (long long)Fi[t] * ((long long)Dv[wH[t]] - (long long)Dv[vH[t]]);
+    }
   }
   return acc;
 }
