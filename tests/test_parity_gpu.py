@@ -203,6 +203,47 @@ def test_every_model_every_group_width(cgo, wpm):
         assert_same_state(g, o, "model %d wpm %d" % (inst["model"], wpm))
 
 
+KERNEL_TABLE_MODELS = [
+    ("tsp int16", lambda: I.tsp_uniform(31, 74)),
+    ("tsp int32", lambda: I.tsp_uniform(31, 75, box=90000)),
+    ("atsp int16", lambda: I.tsp_asym(23, 76)),
+    ("atsp int32", lambda: I.tsp_asym(23, 77, skew=60000)),
+    ("qap", lambda: I.qap_random(11, 78)),
+    ("cvrptw", lambda: I.cvrptw(14, 79, vehicles=4, capacity=80)),
+    ("knapsack", lambda: I.knapsack(60, 80)),
+    ("gap", lambda: I.gap(30, 81, m=5)),
+]
+# (warps per member, generations in flight, candidates): every launch shape
+KERNEL_TABLE_SHAPES = [(1, 1, 150), (2, 1, 150), (4, 1, 150), (1, 2, 32), (2, 2, 64), (4, 2, 128),
+                       (4, 3, 128), (4, 4, 128)]
+
+
+@pytest.mark.parametrize("name,maker", KERNEL_TABLE_MODELS, ids=[m[0] for m in KERNEL_TABLE_MODELS])
+def test_every_kernel_set_and_shape(cgo, name, maker):
+    """Each model and matrix width, with no population step, crossover alone
+    and islands with crossover, in every launch shape its kernels are built
+    for: the host finds the kernel (built in one of the parallel units) and
+    the search equals the oracle's.  Three and four generations in flight
+    exist without population steps only, and not for the asymmetric TSP."""
+    inst = maker()
+    for xf, extra in ((0, {}), (1, dict(cross_q16=40000)),
+                      (2, dict(cross_q16=40000, islands=2, migrate_period=5))):
+        for wpm, ns, C in KERNEL_TABLE_SHAPES:
+            p = params_for(inst, P=6, C=C, G=12, U=5, elite_period=10, **extra)
+            prob = cgo.Problem(inst)
+            prob.set_launch(wpm * ns, 0, wpm, ns)
+            built = ns <= 2 or (xf == 0 and "atsp" not in name)
+            if not built:
+                with pytest.raises(cgo.CgoError) as e:
+                    prob.solve(p, 3)
+                assert e.value.status == cgo.ERR_UNSUPPORTED
+                continue
+            prob.solve(p, 3)
+            assert prob.get_launch()[1:4:2] == (wpm, ns)
+            assert_same_state(prob.state(), oracle_run(inst, p, 3, 12),
+                              "%s xf %d wpm %d ns %d" % (name, xf, wpm, ns))
+
+
 @pytest.mark.parametrize("staging", [1, 2])
 def test_tsp_staging_modes(cgo, staging):
     inst = I.tsp_uniform(60, 24)
