@@ -48,6 +48,7 @@ import instances as I  # noqa: E402
 
 TO, INS, OR = 1, 2, 3
 O_THREE_OPT, O_SEGMENT = 6, 7     # operator slots of the C ABI (cgo_op)
+O_ROW_SWAP, O_ROW_MERGE, O_ROW_SPLIT = 8, 9, 10
 
 
 def workload(name: str):
@@ -120,6 +121,9 @@ def cvrptw_variant(args, inst: dict, desc: str):
         wd, wv = (int(x) for x in args.cvrptw_weights.split(","))
         inst = dict(inst, weight_distance=wd, weight_vehicles=wv)
         desc += " weights=(%d,%d)" % (wd, wv)
+    if args.cvrptw_longest:
+        inst = dict(inst, weight_longest=args.cvrptw_longest)
+        desc += " longest-route weight=%d" % args.cvrptw_longest
     if args.cvrptw_lex:
         lex = [(LEX_NAMES[t.split(":")[0]], int(t.split(":")[1])) for t in args.cvrptw_lex.split(",")]
         inst = dict(inst, lexicographic=lex)
@@ -150,14 +154,17 @@ def cvrptw_objectives(inst: dict, sol) -> dict:
 
 def extra_ops_mask(model: int, extra: str) -> int:
     """Operator bits that --extra-ops adds for a model (3-opt for the
-    permutation models, the segment operator for binary and integer ones)."""
+    permutation models, the segment operator for binary and integer ones,
+    the row level for CVRPTW)."""
     bits = 0
     for name in filter(None, extra.split(",")):
         if name == "three_opt" and model in (I.TSP, I.QAP, I.CVRPTW):
             bits |= 1 << O_THREE_OPT
         elif name == "segment" and model in (I.KNAPSACK, I.GAP):
             bits |= 1 << O_SEGMENT
-        elif name not in ("three_opt", "segment"):
+        elif name == "rows" and model == I.CVRPTW:
+            bits |= (1 << O_ROW_SWAP) | (1 << O_ROW_MERGE) | (1 << O_ROW_SPLIT)
+        elif name not in ("three_opt", "segment", "rows"):
             raise SystemExit("unknown operator " + name)
     return bits
 
@@ -327,9 +334,12 @@ def main():
                     help="single solve: 1 = add the row/column-sum start permutations")
     ap.add_argument("--extra-ops", default="",
                     help="enable operators beyond the default mask where they apply: "
-                         "'three_opt' (TSP, CVRPTW), 'segment' (seg_flip / seg_reset: knapsack, GAP)")
+                         "'three_opt' (TSP, QAP, CVRPTW), 'segment' (seg_flip / seg_reset: "
+                         "knapsack, GAP), 'rows' (row_swap / row_merge / row_split: CVRPTW)")
     ap.add_argument("--cvrptw-weights", default="",
                     help="cvrptw100: objective weights 'distance,vehicles' (0,0 = distance only)")
+    ap.add_argument("--cvrptw-longest", type=int, default=0,
+                    help="cvrptw100: weight of the longest route's distance (0 = off)")
     ap.add_argument("--cvrptw-lex", default="",
                     help="cvrptw100: lexicographic mode, objectives in priority order with "
                          "tolerances, e.g. 'd:50,v:0' (d distance, v vehicles, l longest route)")
@@ -939,11 +949,11 @@ def op_mix(counts: dict) -> dict:
     u, uk = counts["u_op"], counts["u_k"]
     apps, cands = sum(u), sum(uk)
     names = {0: "swap", 1: "2opt", 2: "insert", 3: "oropt", 4: "flip", 5: "reset", 6: "3opt",
-             7: "segment"}
+             7: "segment", 8: "row_swap", 9: "row_merge", 10: "row_split"}
     return {"evals": cands, "applications": apps,
             "steps_per_eval": (uk[0] + 2 * uk[1] + 3 * uk[2]) / cands if cands else 0.0,
             "k_share": [x / cands for x in uk] if cands else [],
-            "op_share": {names[i]: u[i] / apps for i in range(8) if u[i]} if apps else {}}
+            "op_share": {names[i]: u[i] / apps for i in range(len(u)) if u[i]} if apps else {}}
 
 
 def roofline(kernel_ms, prob, clocks):

@@ -66,6 +66,8 @@ def test_extra_operator_masks_per_model():
     assert bench.extra_ops_mask(I.KNAPSACK, "segment,three_opt") == 1 << bench.O_SEGMENT
     assert bench.extra_ops_mask(I.GAP, "segment") == 1 << bench.O_SEGMENT
     assert bench.extra_ops_mask(I.TSP, "") == 0
+    assert bench.extra_ops_mask(I.CVRPTW, "rows") == 0x700       # row_swap, row_merge, row_split
+    assert bench.extra_ops_mask(I.TSP, "rows") == 0
     with pytest.raises(SystemExit):
         bench.extra_ops_mask(I.TSP, "two_and_a_half_opt")
 
