@@ -1078,15 +1078,22 @@ __device__ __forceinline__ long long lex_key(const KInst &K, long long P) {
 // CVRPTW candidate.  One step: from the route cache; k steps: every changed
 // position lies in the hull of the moves' ranges (a move permutes only inside
 // its own range), so the routes over that hull are walked once in the final
-// sequence against their cached old cost.  With `defer` set, a candidate of
-// k >= 2 steps is not evaluated and false is returned.
-__device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *sol,
-                                                 const Weights<Enc<CVRPTW>::NO> &W, uint32_t c,
-                                                 uint32_t p, uint32_t g, bool defer, long long &d,
-                                                 uint32_t &rec, CandMoves &cm, const CvAux &aux) {
+// sequence against their cached old cost.  With `defer` set, a candidate
+// whose walk may be long is not evaluated and its class is returned (0: it
+// was evaluated): 1 for k >= 2 steps (the hull of the moves), 2 and 3 for one
+// step whose routes over [L, R] are walked whole (a reversal, or any move
+// with the longest-route objective) at more than kWalkDefer positions,
+// 2 above kWalkLong.  A warp then evaluates its long candidates together,
+// the longest first, instead of paying its longest walk in every slot.
+constexpr int kWalkDefer = 24, kWalkLong = 64;
+
+__device__ __forceinline__ int candidate_cvrptw(const View &X, const PermEl *sol,
+                                                const Weights<Enc<CVRPTW>::NO> &W, uint32_t c,
+                                                uint32_t p, uint32_t g, bool defer, long long &d,
+                                                uint32_t &rec, CandMoves &cm, const CvAux &aux) {
   const uint4 R0 = philox(ctr_word(c, 0, kKindMove), X.tag, p, g, X.k0, X.k1);
   const int k = 1 + wpick(W.ck, W.Wk, R0.w);
-  if (defer && k >= 2) return false;
+  if (defer && k >= 2) return 1;
   int ops[3] = {-1, -1, -1};
   cm.k = k;
   cm.m[1] = cm.m[2] = PMove{0, 0, 0, 0, 0};
@@ -1101,6 +1108,11 @@ __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *so
                    : perm_decode<false>(ops[0], R0.y, R0.z, X.len);
   }
   if (k == 1) {
+    if (defer && (cm.m[0].rev || X.wl > 0)) {
+      const int L = cm.m[0].b1 > 0 ? aux.prv[cm.m[0].b1 - 1] + 1 : 0;
+      const int w = aux.nxt[cm.m[0].b4] - L + 1;
+      if (w > kWalkDefer) return w > kWalkLong ? 2 : 3;
+    }
     d = cvrptw_step0(X, sol, cm.m[0], aux);
   } else {
 #pragma unroll
@@ -1131,7 +1143,7 @@ __device__ __forceinline__ bool candidate_cvrptw(const View &X, const PermEl *so
     d = lex_key(*X.ki, cur + d) - lex_key(*X.ki, cur);
   }
   rec = stats_record(ops[0], ops[1], ops[2], k, d < 0);
-  return true;
+  return 0;
 }
 
 // Candidate c: all three steps are drawn and decoded, and the delta of every
@@ -2138,8 +2150,12 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
   const int span = WPM * 32;
   const int cpl = (C + span - 1) / span;
   const bool packed = 96ull * (uint64_t)cpl * (uint64_t)I.U * (uint64_t)mine < 65536ull;
-  // a member's window counts in bytes while it evolves (PackedStats)
-  const bool bytec = 3ull * (uint64_t)cpl * (uint64_t)I.U <= 255ull;
+  // a member's window counts in bytes while it evolves (PackedStats): a lane
+  // counts at most cpl candidates a generation, or 2 cpl where CVRPTW gathers
+  // its long candidates over the warp's lanes (in place, then one per round)
+  const uint64_t lane_cands =
+      (MODEL == CVRPTW && NS == 1 && cpl > 1 && cpl <= 8) ? 2ull * (uint64_t)cpl : (uint64_t)cpl;
+  const bool bytec = 3ull * lane_cands * (uint64_t)I.U <= 255ull;
   PackedStats ps{0u, 0u, 0u, 0u, 0u, 0u};
   auto count = [&](uint32_t rec) {
     if (bytec) packed_add<NO>(ps, rec);
@@ -2195,48 +2211,56 @@ __device__ void evolve_members(const KInst &I, const View &X, unsigned char *sme
         bool done = false;
         if constexpr (MODEL == CVRPTW && NS == 1) {
           if (gm < wend && cpl > 1 && cpl <= 8) {
-            // one-step candidates in place; the multi-step ones (a fifth or
-            // so) gathered over the warp's lanes, so that the long walks are
-            // paid in about one round rather than in every slot
-            uint32_t bal[8];
+            // candidates with short walks in place; the long ones (multi-step
+            // candidates, long reversals: about a third) gathered over the
+            // warp's lanes by class, longest class first, so that the long
+            // walks are paid in a few rounds of similar lengths rather than
+            // in every slot.  cpack: the class of the lane's candidate in
+            // each slot, 2 bits a slot.
+            uint32_t cpack = 0u;
+            int nl = 0;
 #pragma unroll
             for (int slot = 0; slot < 8; ++slot) {
-              bal[slot] = 0u;
               if (slot < cpl) {
                 const int c = slot * span + gwi * 32 + lane;
-                bool later = false;
+                int cls = 0;
                 if (c < C) {
                   long long d;
                   uint32_t rec;
                   CandMoves cm;
-                  if (candidate_cvrptw(X, sol, W, c, p, gm, true, d, rec, cm, cva)) {
+                  cls = candidate_cvrptw(X, sol, W, c, p, gm, true, d, rec, cm, cva);
+                  if (cls == 0) {
                     count(rec);
                     if (d < bd || (d == bd && c < bc)) {
                       bd = d;
                       bc = c;
                       cbest = cm;
                     }
-                  } else {
-                    later = true;
                   }
                 }
-                bal[slot] = __ballot_sync(kFull, later);
+                cpack |= (uint32_t)cls << (2 * slot);
+                nl += cls != 0;
               }
             }
-            int n2 = 0;
-#pragma unroll
-            for (int slot = 0; slot < 8; ++slot) n2 += __popc(bal[slot]);
+            const int n2 = (int)__reduce_add_sync(kFull, (uint32_t)nl);
             for (int base = 0; base < n2; base += 32) {
+              // entry i of the gathered list: class 1 first, slots in order,
+              // lanes in order within a slot
               const int i = base + lane;
-              if (i < n2) {
-                int c = 0, acc = 0;
+              int c = 0, acc = 0;
+#pragma unroll
+              for (int q = 1; q <= 3; ++q)
 #pragma unroll
                 for (int slot = 0; slot < 8; ++slot) {
-                  const int cnt = __popc(bal[slot]);
-                  if (i >= acc && i < acc + cnt)
-                    c = slot * span + gwi * 32 + (int)__fns(bal[slot], 0u, i - acc + 1);
-                  acc += cnt;
+                  if (slot < cpl) {
+                    const uint32_t b = __ballot_sync(kFull, ((cpack >> (2 * slot)) & 3u) == (uint32_t)q);
+                    const int cnt = __popc(b);
+                    if (i >= acc && i < acc + cnt)
+                      c = slot * span + gwi * 32 + (int)__fns(b, 0u, i - acc + 1);
+                    acc += cnt;
+                  }
                 }
+              if (i < n2) {
                 long long d;
                 uint32_t rec;
                 CandMoves cm;
