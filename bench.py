@@ -931,8 +931,8 @@ OPS_QAP_K = 17            # QAP, per k of the O(n) swap delta: 9 loads, 2 multip
 # the tsp442 workload, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass; profiles/evolve_tsp442_g200000_dram.md),
 # valid only for the kernel sources it was taken on.
-TRAFFIC_BYTES = 1148160 + 81920
-TRAFFIC_SOURCES = "aac16d30b7c1a0a4"
+TRAFFIC_BYTES = 1269760 + 95232
+TRAFFIC_SOURCES = "cbb57a7683deef50"
 
 
 def kernel_sources_hash() -> str:
