@@ -525,6 +525,31 @@ def test_cvrptw_candidates_per_lane(cgo, C, wpm, kw):
     assert_same_state(g, o, "cvrptw C=%d wpm=%d" % (C, wpm))
 
 
+@pytest.mark.parametrize("C,U,ops,extra", [
+    (128, 5, None, {}),                                   # four per lane, default operators
+    (128, 5, [TO], {}),                                   # reversals alone: every walk class
+    (256, 5, [TO, INS], {}),                              # eight per lane, byte counts at their bound
+    (256, 6, [TO, INS], {}),                              # eight per lane, full-width counts
+    (64, 5, [SW, INS, OR], {"weight_longest": 2}),        # longest route: any one-step move gathers
+    (96, 4, [SW, TO, INS, OR], {"lexicographic": [(1, 0), (2, 10), (0, 20)]}),
+])
+def test_cvrptw_gathered_walk_classes(cgo, C, U, ops, extra):
+    """Several candidates per lane on 100 customers and 25 routes (sequences
+    of 124 symbols): candidates whose routes span more than 24 positions
+    (multi-step hulls, reversals, and with the longest route any move) are
+    evaluated after the in-place ones, gathered over the warp in three
+    classes, so a lane may evaluate twice its share in one generation."""
+    inst = dict(I.cvrptw(100, 97, vehicles=25, capacity=200), **extra)
+    over = dict(P=4, C=C, G=25, U=U, T0=30 << 32)
+    if ops:
+        over["ops"] = ops
+    p = params_for(inst, **over)
+    prob, g, o = run_both(cgo, inst, p, 19, wpm=1, ns=1)
+    where = "C %d U %d ops %s %s" % (C, U, ops, sorted(extra))
+    assert_same_state(g, o, where)
+    assert_same_counts(prob, o, where)
+
+
 def test_cvrptw100_prefix(cgo):
     """The serving workload's routing class: 100 customers, 25 vehicles."""
     inst = I.cvrptw(100, 90)
