@@ -328,6 +328,9 @@ def main():
     ap.add_argument("--batch-pop", type=int, default=0,
                     help="batched: one population for every class instead of the autotuner's")
     ap.add_argument("--slice", type=int, default=2000)
+    ap.add_argument("--serve-fast-slice", type=int, default=20000,
+                    help="serving: generations per slice of every class but the slowest, "
+                         "at most the request budget (0 = --slice for every class)")
     ap.add_argument("--init-oversample", type=int, default=1,
                     help="single solve: K of the oversampled start (1 = plain start)")
     ap.add_argument("--init-heuristic", type=int, default=0,
@@ -760,7 +763,15 @@ def serve_run(args, cgo, torch, local, duration, G, seq_live_s, rank=0) -> dict:
     pop_of_model.update(pops)
     for k in params_of:
         params_of[k]["P"] = pops[pool[k]["model"]]
-    srv = cgo.Server(max_slots=4096, hbm_budget_bytes=96 << 30, slice_generations=args.slice)
+    # generations per slice: the class that advances slowest per request
+    # (trial rate / (population x candidates)) keeps --slice; the others take
+    # --serve-fast-slice, so that they finish in fewer slices
+    speed = {m: tuned[m][1] / (pops[m] * cfg["C"]) for m in tuned}
+    slowest = min(speed, key=speed.get)
+    slice_by_model = {int(m): (args.slice if m == slowest or args.serve_fast_slice <= 0
+                               else min(G, args.serve_fast_slice)) for m in tuned}
+    srv = cgo.Server(max_slots=4096, hbm_budget_bytes=96 << 30, slice_generations=args.slice,
+                     slice_by_model=slice_by_model)
 
     def make(k, tag):
         pr = cgo.Problem(dict(pool[k], tag=tag))
@@ -851,6 +862,7 @@ def serve_run(args, cgo, torch, local, duration, G, seq_live_s, rank=0) -> dict:
             "latency_p99_s": float(np.percentile(lats, 99)),
             "latency_max_s": float(lats.max()),
             "slice_generations": args.slice,
+            "slice_by_model": {str(m): v for m, v in slice_by_model.items()},
             "autotuner": {"population_by_model": {str(m): v for m, v in pops.items()},
                           "predicted_load": load,
                           "warps_per_member_by_model": {str(m): v for m, v in wpm_of.items()},

@@ -427,11 +427,22 @@ typedef struct {
   int32_t max_queued;          /* requests waiting for admission at most; cgo_submit
                                   returns CGO_ERR_BUSY beyond it (0 = no bound) */
   int32_t reserved;            /* 0 */
+  /* --- appended --- */
+  int64_t slice_by_model[5];   /* generations per slice for the requests of each model,
+                                  indexed by cgo_model (an asymmetric TSP counts as TSP);
+                                  0 = slice_generations.  Every bucket advances in each
+                                  slice and the slice lasts as long as its slowest
+                                  bucket, so a model whose requests cost little per
+                                  generation can take more generations per slice and
+                                  finish in fewer slices.  Results do not depend on it. */
 } cgo_server_cfg;
 
 /* The size of cgo_server_cfg before max_queued was appended (accepted by
  * cgo_server_create: no queue bound). */
 #define CGO_SERVER_CFG_SIZE_V1 ((uint32_t)offsetof(cgo_server_cfg, max_queued))
+/* The size before slice_by_model was appended (accepted: every model takes
+ * slice_generations). */
+#define CGO_SERVER_CFG_SIZE_V2 ((uint32_t)offsetof(cgo_server_cfg, slice_by_model))
 
 typedef struct {
   uint32_t struct_size;        /* = sizeof(cgo_server_info) */

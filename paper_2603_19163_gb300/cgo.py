@@ -84,7 +84,7 @@ class cgo_server_cfg(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("max_slots", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("smem_budget_bytes", ctypes.c_int64),
                 ("slice_generations", ctypes.c_int64), ("max_queued", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("slice_by_model", ctypes.c_int64 * 5)]
 
 
 class cgo_server_info(ctypes.Structure):
@@ -447,9 +447,17 @@ class Server:
     """A cgo_server: continuous batching of solve requests."""
 
     def __init__(self, max_slots: int = 1024, hbm_budget_bytes: int = 64 << 30,
-                 smem_budget_bytes: int = 0, slice_generations: int = 2000, max_queued: int = 0):
+                 smem_budget_bytes: int = 0, slice_generations: int = 2000, max_queued: int = 0,
+                 slice_by_model: dict | None = None):
+        """slice_by_model: {model: generations per slice} for the models whose
+        requests should advance further (or less far) per slice than
+        slice_generations."""
+        per = [0] * 5
+        for m, v in (slice_by_model or {}).items():
+            per[int(m)] = int(v)
         cfg = cgo_server_cfg(ctypes.sizeof(cgo_server_cfg), max_slots, hbm_budget_bytes,
-                             smem_budget_bytes, slice_generations, max_queued, 0)
+                             smem_budget_bytes, slice_generations, max_queued, 0,
+                             (ctypes.c_int64 * 5)(*per))
         h = ctypes.c_void_p()
         check(lib().cgo_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cgo_server_create")
         self.h = h

@@ -5,8 +5,10 @@
 // into free slots while their device-memory footprint fits the budget,
 // initialises their populations, rewrites the per-bucket work lists, then
 // replays one captured slice (a persistent batched kernel per bucket on
-// forked streams) that advances every resident request by up to `slice`
-// generations.  Requests that reach their budget are retired and their
+// forked streams) that advances every resident request by up to its
+// model's slice length (`slice_by_model`, else `slice_generations`).  The
+// slice lasts as long as its slowest bucket, so cheap models may take more
+// generations per slice.  Requests that reach their budget are retired and their
 // waiters woken; requests that arrive mid-slice join at the next boundary.
 // Populations, AOS weights, temperatures and generation counters stay in
 // device memory across slices.
@@ -51,6 +53,7 @@ struct SBucket {
   int model, tri16, xf, wpm, warps;
   int64_t smem;
   int grid;
+  int64_t slice;  // generations per slice of its requests
 };
 
 constexpr int kMaxBuckets = 16;
@@ -127,7 +130,7 @@ cudaError_t capture_slice(cgo_server *S) {
       if (ce == cudaSuccess)
         ce = launch_batch(bk.model, bk.tri16, bk.xf, S->d_k, S->d_lists + b * S->cfg.max_slots,
                           S->d_counts + b, S->d_next + b, bk.warps, bk.wpm, bk.smem, bk.grid,
-                          S->cfg.slice_generations, 10ull * 1000 * 1000 * 1000, S->side[b]);
+                          bk.slice, 10ull * 1000 * 1000 * 1000, S->side[b]);
       if (ce == cudaSuccess) ce = cudaEventRecord(S->evs[b], S->side[b]);
       if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, S->evs[b], 0);
     }
@@ -140,19 +143,26 @@ cudaError_t capture_slice(cgo_server *S) {
   return e;
 }
 
+// generations per slice of a request of public model `model`
+int64_t slice_of(const cgo_server *S, int model) {
+  const int64_t v = model >= 0 && model < 5 ? S->cfg.slice_by_model[model] : 0;
+  return v > 0 ? v : S->cfg.slice_generations;
+}
+
 // bucket of a request (created on first use; the graph is recaptured then)
-int bucket_for(cgo_server *S, int model, int tri16, int xf, int wpm, int warps, int64_t smem) {
+int bucket_for(cgo_server *S, int model, int tri16, int xf, int wpm, int warps, int64_t smem,
+               int64_t slice) {
   for (size_t b = 0; b < S->buckets.size(); ++b) {
     const SBucket &k = S->buckets[b];
     if (k.model == model && k.tri16 == tri16 && k.xf == xf && k.wpm == wpm && k.warps == warps &&
-        k.smem == smem)
+        k.smem == smem && k.slice == slice)
       return (int)b;
   }
   if ((int)S->buckets.size() >= kMaxBuckets) return -1;
   const int per_sm = batch_ctas_per_sm(model, tri16, xf, warps, wpm, smem);
   if (per_sm <= 0) return -1;
   S->buckets.push_back(SBucket{model, tri16, xf, wpm, warps, smem,
-                               std::max(1, std::min(S->cfg.max_slots, per_sm * S->sms))});
+                               std::max(1, std::min(S->cfg.max_slots, per_sm * S->sms)), slice});
   S->dirty = true;
   return (int)S->buckets.size() - 1;
 }
@@ -232,7 +242,8 @@ void server_loop(cgo_server *S) {
       int wpm = 1, warps = 1;
       int64_t need = 0, cls = 0;
       if (batch_shape(p, r->params, h, &wpm, &warps, &need, &cls) != CGO_OK ||
-          (r->bucket = bucket_for(S, h.model, p->tri16, takes_xf(h) != 0 ? 1 : 0, wpm, warps, cls)) < 0) {
+          (r->bucket = bucket_for(S, h.model, p->tri16, takes_xf(h) != 0 ? 1 : 0, wpm, warps, cls,
+                                  slice_of(S, p->model))) < 0) {
         fail_all(S, CGO_ERR_UNSUPPORTED, "no batched launch shape for a request");
         return;
       }
@@ -279,7 +290,7 @@ void server_loop(cgo_server *S) {
         cancelled.push_back(r);
         continue;
       }
-      r->g = std::min<int64_t>(r->params.generations, r->g + S->cfg.slice_generations);
+      r->g = std::min<int64_t>(r->params.generations, r->g + S->buckets[(size_t)r->bucket].slice);
       if (r->g >= r->params.generations) finished.push_back(r);
     }
     std::vector<DevAos> aos(finished.size());
@@ -330,12 +341,15 @@ extern "C" {
 cgo_status cgo_server_create(const cgo_server_cfg *cfg, cgo_server **out) {
   if (!out) return fail(CGO_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (!cfg || (cfg->struct_size != sizeof(cgo_server_cfg) && cfg->struct_size != CGO_SERVER_CFG_SIZE_V1))
+  if (!cfg || (cfg->struct_size != sizeof(cgo_server_cfg) && cfg->struct_size != CGO_SERVER_CFG_SIZE_V1 &&
+               cfg->struct_size != CGO_SERVER_CFG_SIZE_V2))
     return fail(CGO_ERR_INVALID, "cfg: struct_size must be sizeof(cgo_server_cfg)");
   cgo_server_cfg c{};
   memcpy(&c, cfg, cfg->struct_size);
   c.struct_size = sizeof c;
   if (c.max_queued < 0) return fail(CGO_ERR_INVALID, "max_queued < 0");
+  for (int i = 0; i < 5; ++i)
+    if (c.slice_by_model[i] < 0) return fail(CGO_ERR_INVALID, "slice_by_model < 0");
   cfg = &c;
   if (cfg->max_slots < 1 || cfg->max_slots > 65536) return fail(CGO_ERR_INVALID, "max_slots out of [1, 65536]");
   if (cfg->slice_generations < 1) return fail(CGO_ERR_INVALID, "slice_generations < 1");

@@ -50,6 +50,8 @@ int main(void) {
   printf("%zu %zu\n", offsetof(cgo_problem_desc, capacity), offsetof(cgo_problem_desc, instance_tag));
   printf("%zu %zu %u %u\n", offsetof(cgo_problem_desc, lex_n), offsetof(cgo_problem_desc, lex_tol),
          CGO_DESC_SIZE_V1, CGO_DESC_SIZE_V2);
+  printf("%zu %zu %u %u\n", sizeof(cgo_server_cfg), offsetof(cgo_server_cfg, slice_by_model),
+         CGO_SERVER_CFG_SIZE_V1, CGO_SERVER_CFG_SIZE_V2);
   return 0;
 }
 """
@@ -66,7 +68,9 @@ int main(void) {
             cgo.cgo_params.op_cap_q16.offset, cgo.cgo_state.cur.offset,
             cgo.cgo_problem_desc.capacity.offset, cgo.cgo_problem_desc.instance_tag.offset,
             cgo.cgo_problem_desc.lex_n.offset, cgo.cgo_problem_desc.lex_tol.offset,
-            cgo.cgo_problem_desc.weight_longest.offset, cgo.cgo_problem_desc.lex_n.offset]
+            cgo.cgo_problem_desc.weight_longest.offset, cgo.cgo_problem_desc.lex_n.offset,
+            ctypes.sizeof(cgo.cgo_server_cfg), cgo.cgo_server_cfg.slice_by_model.offset,
+            cgo.cgo_server_cfg.max_queued.offset, cgo.cgo_server_cfg.slice_by_model.offset]
     assert [int(x) for x in out] == want
 
 

@@ -94,6 +94,33 @@ def test_served_results_equal_oracle(cgo, slice_len):
         assert cost == st["best_cost"].min() and lat >= 0.0
 
 
+def test_slice_length_per_model(cgo):
+    """Models that advance by different numbers of generations per slice
+    (longer, shorter and the default) reach the same states as the oracle."""
+    items = request_mix()
+    srv = cgo.Server(max_slots=8, slice_generations=9,
+                     slice_by_model={I.TSP: 40, I.KNAPSACK: 3, I.CVRPTW: 17})
+    probs, params, tickets = [], [], []
+    for k, (inst, over) in enumerate(items):
+        prob = cgo.Problem(inst)
+        p = params_for(inst, **over)
+        tickets.append(srv.submit(prob, p, 50 + k))
+        probs.append(prob)
+        params.append(p)
+    for t in tickets:
+        srv.wait(t, 60000)
+    stats = srv.stats()
+    srv.close()
+    assert stats["completed"] == len(items)
+    for k, ((inst, _), prob, p) in enumerate(zip(items, probs, params)):
+        assert_same_state(prob.state(), oracle_run(inst, p, 50 + k, p["G"]), "request %d" % k)
+
+
+def test_slice_by_model_validated(cgo):
+    with pytest.raises(Exception):
+        cgo.Server(max_slots=2, slice_generations=5, slice_by_model={I.GAP: -1})
+
+
 def test_served_equals_alone_under_tight_memory(cgo):
     """A budget that fits one request at a time serialises admission;
     results do not change."""
