@@ -764,12 +764,11 @@ def serve_run(args, cgo, torch, local, duration, G, seq_live_s, rank=0) -> dict:
     for k in params_of:
         params_of[k]["P"] = pops[pool[k]["model"]]
     # generations per slice: the class that advances slowest per request
-    # (trial rate / (population x candidates)) keeps --slice; the others take
-    # --serve-fast-slice, so that they finish in fewer slices
-    speed = {m: tuned[m][1] / (pops[m] * cfg["C"]) for m in tuned}
-    slowest = min(speed, key=speed.get)
-    slice_by_model = {int(m): (args.slice if m == slowest or args.serve_fast_slice <= 0
-                               else min(G, args.serve_fast_slice)) for m in tuned}
+    # keeps --slice; the others take --serve-fast-slice (the autotuner's rule)
+    from paper_2603_19163_gb300.autotune import slices_by_class
+    slice_by_model = {int(m): v for m, v in slices_by_class(
+        {m: tuned[m][1] for m in tuned}, pops, cfg["C"], G, args.slice,
+        args.serve_fast_slice).items()}
     srv = cgo.Server(max_slots=4096, hbm_budget_bytes=96 << 30, slice_generations=args.slice,
                      slice_by_model=slice_by_model)
 

@@ -146,6 +146,20 @@ def population_for_load(class_rate: dict, share: dict, arrivals_per_s: float,
         P[c] = ladder[ladder.index(P[c]) + 1]
 
 
+def slices_by_class(class_rate: dict, population: dict, candidates: int, generations: int,
+                    base: int, fast: int) -> dict:
+    """Serving slice lengths: every bucket advances in each slice and the
+    slice lasts as long as its slowest bucket, so the class that advances
+    slowest per request (class_rate / (population x candidates), request
+    generations per second of a full batch) keeps `base` generations a slice
+    and every other class takes `fast` (at most the request budget
+    `generations`), finishing in fewer slices.  fast <= 0: `base` for all.
+    Returns {class: generations per slice}."""
+    speed = {c: class_rate[c] / (population[c] * candidates) for c in class_rate}
+    slowest = min(speed, key=speed.get) if speed else None
+    return {c: (base if c == slowest or fast <= 0 else min(generations, fast)) for c in speed}
+
+
 def instance_data_bytes(inst: dict) -> int:
     """Device bytes of an instance's data as the library holds them (the
     caller's arrays, plus the int16 or int32 upper triangle of a TSP)."""

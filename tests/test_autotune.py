@@ -1,5 +1,5 @@
 """Host logic of the autotuner (no GPU): trial shapes and the serving-population rule."""
-from paper_2603_19163_gb300.autotune import Autotuner, population_for_load
+from paper_2603_19163_gb300.autotune import Autotuner, population_for_load, slices_by_class
 
 
 def test_population_rule_keeps_everything_at_the_top_when_it_fits():
@@ -49,3 +49,19 @@ def test_batch_populations_fit_the_l2_working_set():
     # the working set adds every instance's state at its class's population
     lens = [(int(x["model"]), int(x["n"])) for x in mix]
     assert total == data + sum(state_bytes(n, mid[m]) for m, n in lens)
+
+
+def test_slice_rule_keeps_the_slowest_class_at_the_base_slice():
+    # per request and generation: a 1e9 / (8 x 128), b 1e8 / (8 x 128), c 4e9 / (32 x 128)
+    rate = {"a": 1e9, "b": 1e8, "c": 4e9}
+    pops = {"a": 8, "b": 8, "c": 32}
+    assert slices_by_class(rate, pops, 128, 20000, 2000, 50000) == {"a": 20000, "b": 2000, "c": 20000}
+    assert slices_by_class(rate, pops, 128, 20000, 2000, 6000) == {"a": 6000, "b": 2000, "c": 6000}
+    # off: every class at the base slice
+    assert slices_by_class(rate, pops, 128, 20000, 2000, 0) == {"a": 2000, "b": 2000, "c": 2000}
+
+
+def test_slice_rule_weighs_the_population():
+    # equal batch rates, but b's requests carry four times the members
+    rate = {"a": 1e9, "b": 1e9}
+    assert slices_by_class(rate, {"a": 8, "b": 32}, 128, 20000, 2000, 20000) == {"a": 20000, "b": 2000}
