@@ -698,6 +698,16 @@ def bench_batch(args, rank, world, local, cgo, torch, dist, barrier):
         print(json.dumps(line), flush=True)
 
 
+def latency_by_class(lats, classes) -> dict:
+    """Requests, p50 and p99 latency (s) per request class."""
+    out = {}
+    for c in sorted(set(classes)):
+        v = np.array([x for x, k in zip(lats, classes) if k == c], dtype=np.float64)
+        out[c] = {"requests": int(v.size), "latency_p50_s": float(np.percentile(v, 50)),
+                  "latency_p99_s": float(np.percentile(v, 99))}
+    return out
+
+
 def lindley(trace, service_of) -> np.ndarray:
     """Latencies of one server taking requests first come, first served:
     W_i = max(0, W_(i-1) + S_(i-1) - A_i) (Lindley), latency = W_i + S_i."""
@@ -860,6 +870,7 @@ def serve_run(args, cgo, torch, local, duration, G, seq_live_s, rank=0) -> dict:
             "latency_p50_s": float(np.percentile(lats, 50)),
             "latency_p99_s": float(np.percentile(lats, 99)),
             "latency_max_s": float(lats.max()),
+            "latency_by_class": latency_by_class(lats, [cls_of(k) for _, k in trace]),
             "slice_generations": args.slice,
             "slice_by_model": {str(m): v for m, v in slice_by_model.items()},
             "autotuner": {"population_by_model": {str(m): v for m, v in pops.items()},

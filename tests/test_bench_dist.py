@@ -99,3 +99,16 @@ def test_cvrptw_objectives_of_a_separator_sequence():
                                                              "longest": 42}
     assert bench.cvrptw_objectives(inst, [3, 4, 2, 0, 1]) == {"distance": 15 + 25 + 12 + 20,
                                                              "vehicles": 1, "longest": 72}
+
+
+def test_latency_by_class():
+    import json
+    import bench
+    lats = [0.1, 0.2, 3.0, 0.3, 2.5, 0.4]
+    cls = ["tsp", "gap", "cvrptw", "tsp", "cvrptw", "tsp"]
+    out = bench.latency_by_class(lats, cls)
+    assert sorted(out) == ["cvrptw", "gap", "tsp"]
+    assert out["tsp"]["requests"] == 3 and out["tsp"]["latency_p50_s"] == 0.3
+    assert abs(out["cvrptw"]["latency_p50_s"] - 2.75) < 1e-12
+    assert out["gap"] == {"requests": 1, "latency_p50_s": 0.2, "latency_p99_s": 0.2}
+    json.dumps(out)   # goes into the bench's JSON line
