@@ -85,6 +85,21 @@ def test_errors_are_reported_without_a_gpu_call():
     assert L.cgo_solve(None, None, 0, None) == cgo.ERR_INVALID
 
 
+def test_server_config_checked_without_a_gpu_call():
+    """cgo_server_create validates its configuration before any CUDA call:
+    a negative per-model slice length, an unknown struct size."""
+    from paper_2603_19163_gb300 import cgo
+    L = cgo.lib()
+    h = ctypes.c_void_p()
+    per = (ctypes.c_int64 * 5)(0, 0, 0, -1, 0)
+    cfg = cgo.cgo_server_cfg(ctypes.sizeof(cgo.cgo_server_cfg), 2, 1 << 30, 0, 100, 0, 0, per)
+    assert L.cgo_server_create(ctypes.byref(cfg), ctypes.byref(h)) == cgo.ERR_INVALID
+    assert b"slice_by_model" in L.cgo_last_error() and not h.value
+    cfg = cgo.cgo_server_cfg(ctypes.sizeof(cgo.cgo_server_cfg) - 8, 2, 1 << 30, 0, 100, 0, 0)
+    assert L.cgo_server_create(ctypes.byref(cfg), ctypes.byref(h)) == cgo.ERR_INVALID
+    assert b"struct_size" in L.cgo_last_error()
+
+
 def test_launch_counter_without_a_gpu():
     from paper_2603_19163_gb300 import cgo
     L = cgo.lib()
